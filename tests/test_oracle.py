@@ -1,0 +1,469 @@
+"""Pins of the CPU oracle against facts fixed independently of it.
+
+Each test compares the oracle with something other than itself: published known-answer
+vectors, closed forms, FP64 ray casting, quadratures, Monte Carlo convergence to exact
+integrals, and finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import shade
+from paper_2608_24109_b300 import scenes
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- helpers
+
+def fp64_closest_front(o, d, V, F):
+    """FP64 Moller-Trumbore of rays (o [R,3], d [R,3]) against every triangle.
+    Returns (tri, bary margin of the hit, depth gap to the next front hit); tri = -1 if none."""
+    P0, P1, P2 = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    e1, e2 = P1 - P0, P2 - P0
+    nrm = np.cross(e1, e2)
+    out_t, out_m, out_g = [], [], []
+    for r in range(o.shape[0]):
+        pv = np.cross(d[r], e2)
+        det = np.einsum("ij,ij->i", e1, pv)
+        s = o[r] - P0
+        b1 = np.einsum("ij,ij->i", s, pv) / det
+        qv = np.cross(s, e1)
+        b2 = (qv @ d[r]) / det
+        t = np.einsum("ij,ij->i", e2, qv) / det
+        b0 = 1 - b1 - b2
+        margin = np.minimum(np.minimum(b0, b1), b2)
+        front = (nrm @ d[r]) < 0
+        ok = (margin > -1e-9) & front & (t > 0)
+        if not ok.any():
+            out_t.append(-1)
+            out_m.append(-np.max(np.where(front & (t > 0), margin, -1.0)) if (front & (t > 0)).any() else 1.0)
+            out_g.append(np.inf)
+            continue
+        ts = np.where(ok, t, np.inf)
+        k = int(np.argmin(ts))
+        srt = np.sort(ts)
+        out_t.append(k)
+        out_m.append(margin[k])
+        out_g.append(srt[1] - srt[0] if srt.size > 1 else np.inf)
+    return np.array(out_t), np.array(out_m), np.array(out_g)
+
+
+def pixel_rays(cam, W, H, rows):
+    py, px = np.meshgrid(rows, np.arange(W), indexing="ij")
+    py, px = py.ravel(), px.ravel()
+    c = cam.astype(np.float64)
+    dx = (px + 0.5 - c[14]) / c[12]
+    dy = (c[15] - (py + 0.5)) / c[13]
+    d = c[9:12][None] + dx[:, None] * c[3:6][None] + dy[:, None] * c[6:9][None]
+    o = np.repeat(c[0:3][None], d.shape[0], 0)
+    return o, d, py, px
+
+
+def faceted(V, F):
+    """Un-welded copy: each face gets its own three vertices (flat vertex normals)."""
+    V2 = V[F].reshape(-1, 3)
+    F2 = np.arange(V2.shape[0]).reshape(-1, 3)
+    return V2, F2
+
+
+def constant_scene(V, F, albedo, env_rgb, res=128, views=1, n_direct=64, env_w=32, env_h=16,
+                   n_bounce=0, n_light=0):
+    UV, Fuv = scenes.sphere_uv(V, F)
+    maps = np.zeros((64, 64, 8), np.float32)
+    maps[..., 0:3] = albedo
+    maps[..., 3] = 0.5
+    maps[..., 4] = 0.0
+    maps[..., 7] = 1.0
+    env = np.ones((env_h, env_w, 3), np.float32) * np.asarray(env_rgb, np.float32)
+    cams = scenes.ring_cameras(views, 3.0, res, res)
+    return scenes._finish("const", V, F, UV, Fuv, maps, maps, env, cams, res, res, n_direct=n_direct,
+                          n_bounce=n_bounce, n_light=n_light, seed=7, wrap_u=True)
+
+
+def full_decisions(sc):
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, sc.width, sc.height)
+    assert st == 0
+    pix = oracle.covered_pixels(keys)
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, pix, keys[pix[:, 0], pix[:, 1], pix[:, 2]])
+    return keys, tab, dec
+
+
+# ----------------------------------------------------------------- generators
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) if l.strip() and l[0] != "#"]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox(v[0:4], v[4:6])
+        assert list(out) == v[6:10]
+
+
+def test_sincos_against_libm():
+    s = np.random.default_rng(0).random(2_000_000).astype(np.float32)
+    s = np.concatenate([s, np.float32([0, 0.125, 0.25, 0.375, 0.5, 0.625, 0.75, 0.875, 0.99999994])])
+    sn, cs = oracle.sincos2pi(s)
+    ang = 2 * np.pi * s.astype(np.float64)
+    assert np.abs(sn - np.sin(ang)).max() < 2.5e-7
+    assert np.abs(cs - np.cos(ang)).max() < 2.5e-7
+
+
+# ----------------------------------------------------------------- raster
+
+def test_raster_triangle_major_equals_pixel_brute_force():
+    sc = scenes.config("tiny", res=96, views=2)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, 96, 96)
+    allpix = np.argwhere(np.ones((2, 96, 96))).astype(np.int32)
+    st2, k2 = oracle.raster_pixels(sc.V, sc.F, sc.cams, 96, 96, allpix)
+    assert st == 0 and st2 == 0
+    assert np.array_equal(k2, keys.reshape(-1))
+
+
+def test_fill_rule_is_watertight_on_closed_mesh():
+    # culling off: every pixel centre is inside exactly as many front as back faces,
+    # at most one of each, for a closed convex mesh; and no hole inside the silhouette
+    for res in (64, 97, 256):
+        sc = scenes.config("tiny", res=res, views=4)
+        for v in range(4):
+            st, fr, bk = oracle.coverage_counts(sc.V, sc.F, sc.cams[v], res, res)
+            assert st == 0
+            assert fr.max() <= 1 and bk.max() <= 1
+            assert np.array_equal(fr, bk)
+            inner = fr[1:-1, 1:-1]
+            nb = fr[:-2, 1:-1] & fr[2:, 1:-1] & fr[1:-1, :-2] & fr[1:-1, 2:]
+            assert not np.any((nb == 1) & (inner == 0))
+
+
+@pytest.mark.parametrize("which", ["sphere", "occluded"])
+def test_raster_matches_fp64_ray_casting(which):
+    V, F = scenes.icosphere(3)
+    if which == "occluded":
+        V2, F2 = scenes.icosphere(2)
+        V = np.concatenate([V, 0.5 * V2 + np.array([0.1, 0.05, 1.2])])
+        F = np.concatenate([F, F2 + 642])
+    W = H = 80
+    cam = scenes.look_at_camera((0.0, 0.0, 3.0), W, H)
+    st, keys = oracle.raster_full(V.astype(np.float32), F.astype(np.int32), cam[None], W, H)
+    assert st == 0
+    o, d, py, px = pixel_rays(cam, W, H, np.arange(H))
+    tri, margin, gap = fp64_closest_front(o, d, V.astype(np.float32).astype(np.float64), F)
+    got = (keys[0, py, px] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    got[got == 0xFFFFFFFF] = -1
+    clear = (margin > 2e-3) & (gap > 1e-3)
+    assert clear.sum() > 0.3 * W * H
+    assert np.array_equal(got[clear], tri[clear])
+    if which == "occluded":
+        assert np.any(got[clear] >= 1280)  # the front sphere is seen
+        assert np.any((got[clear] < 1280) & (got[clear] >= 0))
+
+
+def test_guard_band_reported():
+    sc = scenes.config("tiny", res=64, views=1)
+    cam = sc.cams.copy()
+    cam[0, 0:3] = [0.0, 0.0, 0.9]  # eye inside the sphere's bounds: vertices behind the near plane
+    st, _ = oracle.raster_full(sc.V, sc.F, cam, 64, 64)
+    assert st == oracle.GUARDBAND
+
+
+# ----------------------------------------------------------------- rays
+
+def test_watertight_rays_through_vertices_and_edges():
+    V, F = scenes.icosphere(3)
+    V = V.astype(np.float32)
+    edges = np.concatenate([F[:, [0, 1]], F[:, [1, 2]], F[:, [2, 0]]])
+    mids = (V[edges[:, 0]] + V[edges[:, 1]]) * np.float32(0.5)
+    targets = np.concatenate([V, mids]).astype(np.float32)
+    O = np.zeros_like(targets)
+    assert oracle.trace(V, F, O, targets, closest=False).all()
+    tri, t, front = oracle.trace(V, F, O, targets, closest=True)
+    assert (tri >= 0).all() and not front.any()  # seen from inside: back faces
+    O2 = (targets * np.float32(3.0)).astype(np.float32)
+    D2 = (-targets).astype(np.float32)
+    tri2, t2, front2 = oracle.trace(V, F, O2, D2, closest=True)
+    assert (tri2 >= 0).all() and front2.all()
+    assert np.allclose(t2, 2.0, atol=1e-3)  # from 3p towards the origin, hit near p (|p| ~ 1)
+
+
+def test_closest_hit_matches_fp64():
+    V, F = scenes.icosphere(3)
+    rng = np.random.default_rng(3)
+    o = rng.normal(size=(400, 3))
+    o = 2.5 * o / np.linalg.norm(o, axis=1, keepdims=True)
+    tgt = rng.normal(size=(400, 3))
+    tgt = 0.7 * tgt / np.linalg.norm(tgt, axis=1, keepdims=True)
+    d = tgt - o
+    Vf = V.astype(np.float32)
+    tri, t, front = oracle.trace(Vf, F, o.astype(np.float32), d.astype(np.float32), closest=True)
+    ref, margin, gap = fp64_closest_front(o.astype(np.float32).astype(np.float64),
+                                          d.astype(np.float32).astype(np.float64), Vf.astype(np.float64), F)
+    ok = margin > 1e-4
+    assert ok.sum() > 300
+    assert np.array_equal(tri[ok], ref[ok])
+    assert front[ok].all()
+
+
+# ----------------------------------------------------------------- environment sampling
+
+def test_light_direction_spec_matches_fp64():
+    env = scenes.env_map(np.random.default_rng(0), 64, 32, 1.0)
+    tab = oracle.EnvTable(env)
+    rng = np.random.default_rng(1)
+    tex = rng.integers(0, 64 * 32, 5000).astype(np.uint32)
+    xi = (rng.integers(0, 1 << 24, (5000, 2)) * 2.0 ** -24).astype(np.float32)
+    d32 = oracle.light_dirs(tex, xi, 64, 32)
+    w64, pdf, i, j = shade.light_directions(tex.astype(np.int64), xi, 64, 32, tab.q, tab.Q)
+    assert np.abs(d32 - w64.numpy()).max() < 3e-7
+    # row 0 is the +y pole
+    top = oracle.light_dirs(np.array([5], np.uint32), np.array([[0.5, 0.0]], np.float32), 64, 32)
+    assert top[0, 1] > 0.9999
+
+
+def test_env_importance_estimator_integrates_env():
+    """E(w)/p(w) averaged over texels drawn with probability q/Q and uniform in-texel jitter
+    converges to the exact integral of the piecewise-constant map over the sphere."""
+    W, H = 48, 24
+    env = scenes.env_map(np.random.default_rng(5), W, H, 1.5)
+    tab = oracle.EnvTable(env)
+    rng = np.random.default_rng(6)
+    n = 400_000
+    tex = rng.choice(W * H, size=n, p=tab.q / tab.Q)
+    xi = rng.random((n, 2))
+    w, pdf, i, j = shade.light_directions(tex, xi, W, H, tab.q, tab.Q)
+    f = env[i.numpy(), j.numpy()].astype(np.float64) / pdf.numpy()[:, None]
+    est, sig = f.mean(0), f.std(0) / math.sqrt(n)
+    th = np.pi * np.arange(H + 1) / H
+    omega = (2 * np.pi / W) * (np.cos(th[:-1]) - np.cos(th[1:]))
+    exact = (env.astype(np.float64) * omega[:, None, None]).sum((0, 1))
+    assert np.all(np.abs(est - exact) < 5 * sig + 1e-12)
+
+
+def test_texel_choice_frequencies_follow_weights():
+    """The stratified integer-CDF picker of decide.c, fed by the Philox streams, picks texel t
+    with frequency q_t / Q (chi-square over all decisions of many pixels)."""
+    sc = scenes.config("tiny", res=48, views=1, env_w=16, env_h=8, n_direct=64)
+    keys, tab, dec = full_decisions(sc)
+    t = dec.dtex[dec.covered].ravel()
+    n = t.size
+    counts = np.bincount(t, minlength=tab.q.size)
+    expect = n * tab.q.astype(np.float64) / tab.Q
+    m = expect > 5
+    chi2 = ((counts[m] - expect[m]) ** 2 / expect[m]).sum()
+    dof = m.sum() - 1
+    assert chi2 < dof + 6 * math.sqrt(2 * dof)
+    # every pixel's 64 samples are stratified: one sample per 1/64 of the CDF
+    assert n > 10000
+
+
+# ----------------------------------------------------------------- shading pieces
+
+def test_bilinear_ramp_and_wrap():
+    H, W = 8, 16
+    ramp = np.zeros((H, W, 2))
+    ramp[..., 0] = np.arange(W)[None, :]
+    ramp[..., 1] = np.arange(H)[:, None]
+    M = torch.tensor(ramp)
+    uv = torch.tensor([[0.3, 0.6], [0.5, 0.5], [(3 + 0.5) / W, (2 + 0.5) / H]], dtype=torch.float64)
+    out = shade.bilinear(M, uv, wrap_u=False)
+    assert torch.allclose(out[:, 0], uv[:, 0] * W - 0.5)
+    assert torch.allclose(out[:, 1], uv[:, 1] * H - 0.5)
+    # wrapping: half way between the last and the first column
+    out = shade.bilinear(M, torch.tensor([[0.0, 0.5]], dtype=torch.float64), wrap_u=True)
+    assert abs(out[0, 0].item() - 0.5 * (W - 1)) < 1e-12
+    out = shade.bilinear(M, torch.tensor([[1.0, 0.5]], dtype=torch.float64), wrap_u=True)
+    assert abs(out[0, 0].item() - 0.5 * (W - 1)) < 1e-12
+
+
+def test_vertex_frames_on_sphere():
+    V, F = scenes.icosphere(3)
+    UV, Fuv = scenes.sphere_uv(V, F)
+    sgn = shade.face_uv_sign(UV.astype(np.float32), Fuv)
+    nv, tuv = shade.vertex_frames(torch.tensor(V), F, UV, Fuv, UV.shape[0], sgn)
+    assert (torch.einsum("ij,ij->i", nv, torch.tensor(V)) > 0.995).all()
+    # tangent = dP/du = direction of increasing phi: (cos phi, 0, sin phi) away from poles
+    owner = np.zeros(UV.shape[0], np.int64)
+    owner[Fuv.ravel()] = F.ravel()
+    P = V[owner]
+    phi = 2 * np.pi * UV[:, 0]
+    ref = np.stack([np.cos(phi), np.zeros_like(phi), np.sin(phi)], 1)
+    away = np.abs(P[:, 1]) < 0.9
+    assert (np.einsum("ij,ij->i", tuv.numpy()[away], ref[away]) > 0.95).all()
+    assert len(set(sgn.tolist())) == 1
+
+
+def _frame(n):
+    n = n / np.linalg.norm(n)
+    return torch.tensor(n)
+
+
+def test_brdf_normal_incidence_closed_form():
+    n = torch.tensor([[0.0, 0.0, 1.0]], dtype=torch.float64)
+    a = torch.tensor([[0.5, 0.25, 0.75]], dtype=torch.float64)
+    for r, m in [(0.5, 0.0), (0.3, 1.0), (0.9, 0.4)]:
+        rr = torch.tensor([r], dtype=torch.float64)
+        mm = torch.tensor([m], dtype=torch.float64)
+        got = shade.brdf_cos(n, n, n, a, rr, mm)
+        alpha = r * r
+        F0 = (1 - m) * 0.04 + m * a
+        want = (1 - m) * a / math.pi + F0 / (math.pi * alpha ** 2) / (4 + 1e-6)
+        assert torch.allclose(got, want, rtol=1e-12)
+
+
+def _hemisphere_quadrature(nt=800, npp=400, lobe_scale=None):
+    # midpoint rule in (theta, phi) over the upper hemisphere, theta warped towards 0
+    u = (np.arange(nt) + 0.5) / nt
+    th = (np.pi / 2) * u ** 2
+    dth = (np.pi / 2) * 2 * u / nt
+    ph = 2 * np.pi * (np.arange(npp) + 0.5) / npp
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    w = (np.sin(T) * dth[:, None] * (2 * np.pi / npp))
+    d = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1)
+    return d.reshape(-1, 3), w.ravel()
+
+
+def test_brdf_diffuse_albedo_and_reciprocity():
+    d, w = _hemisphere_quadrature()
+    n = torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64).expand(d.shape[0], 3)
+    wi = torch.tensor(d)
+    wo = _frame(np.array([0.3, -0.2, 0.8]))[None].expand_as(wi)
+    a = torch.tensor([0.2, 0.5, 0.9], dtype=torch.float64).expand_as(wi)
+    m = torch.zeros(d.shape[0], dtype=torch.float64)
+    r = torch.full((d.shape[0],), 0.5, dtype=torch.float64)
+    diff = shade.brdf_cos(n, wi, wo, a, r, m, specular=False)
+    integ = (diff * torch.tensor(w)[:, None]).sum(0)
+    assert torch.allclose(integ, torch.tensor([0.2, 0.5, 0.9], dtype=torch.float64), rtol=1e-5)
+    # reciprocity of f_r = brdf_cos / cos_i
+    rng = np.random.default_rng(2)
+    A = rng.normal(size=(200, 3)); A[:, 2] = np.abs(A[:, 2])
+    B = rng.normal(size=(200, 3)); B[:, 2] = np.abs(B[:, 2])
+    A /= np.linalg.norm(A, axis=1, keepdims=True); B /= np.linalg.norm(B, axis=1, keepdims=True)
+    nn = torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64).expand(200, 3)
+    aa = torch.tensor([0.6, 0.4, 0.2], dtype=torch.float64).expand(200, 3)
+    rr = torch.tensor(rng.uniform(0.2, 0.9, 200))
+    mm = torch.tensor(rng.uniform(0, 1, 200))
+    fab = shade.brdf_cos(nn, torch.tensor(A), torch.tensor(B), aa, rr, mm) / torch.tensor(A[:, 2:3])
+    fba = shade.brdf_cos(nn, torch.tensor(B), torch.tensor(A), aa, rr, mm) / torch.tensor(B[:, 2:3])
+    assert torch.allclose(fab, fba, rtol=1e-10)
+
+
+def test_ggx_lobe_normalisation():
+    """With F = 1 (metallic, white) and a narrow lobe, the specular term at normal
+    viewing integrates to int D (n.h) dw_h = 1 up to the Smith shadowing loss."""
+    d, w = _hemisphere_quadrature(nt=2000, npp=64)
+    h = torch.tensor(d)
+    nvec = torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64)
+    wo = nvec.expand_as(h)
+    wi = 2 * (h @ nvec)[:, None] * h - wo
+    keep = (wi @ nvec) > 0
+    jac = 4 * (h @ nvec)  # dw_i = 4 (h . w_o) dw_h
+    nn = nvec.expand_as(h)
+    one = torch.ones(h.shape[0], dtype=torch.float64)
+    for r in (0.2236, 0.3):
+        spec = shade.brdf_cos(nn, wi, wo, torch.ones_like(h), one * r, one) - 0.0
+        val = (spec[:, 0] * jac * torch.tensor(w))[keep].sum().item()
+        assert 0.97 < val < 1.0 + 1e-3, val
+
+
+# ----------------------------------------------------------------- estimators
+
+def test_furnace_diffuse_sphere_under_constant_env():
+    """Convex faceted sphere (n_s = n_g), Lambertian albedo a, constant environment c:
+    the direct estimator is unbiased for L = a * c (Eq. 12 with Vis = 1 above the surface)."""
+    V, F = faceted(*scenes.icosphere(3))
+    albedo = np.array([0.3, 0.6, 0.9], np.float32)
+    c = np.array([0.5, 1.0, 2.0], np.float32)
+    sc = constant_scene(V, F, albedo, c, res=96, n_direct=64)
+    keys, tab, dec = full_decisions(sc)
+    Vt, Mt, Et = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, Vt, Mt, Et, specular=False).numpy()
+    ratio = I / (albedo * c)
+    mean = ratio.mean(0)
+    sig = ratio.std(0) / math.sqrt(ratio.shape[0])
+    assert dec.pix.shape[0] > 3000
+    assert np.all(np.abs(mean - 1.0) < 5 * sig + 1e-9), (mean, sig)
+    # white furnace: albedo 1, E = 1 -> 1
+    sc1 = constant_scene(V, F, np.ones(3, np.float32), np.ones(3, np.float32), res=64, n_direct=64)
+    keys, tab, dec = full_decisions(sc1)
+    Vt, Mt, Et = shade.scene_tensors(sc1)
+    I1 = shade.render_image(sc1, tab, dec, Vt, Mt, Et, specular=False).numpy()[:, 0]
+    assert abs(I1.mean() - 1.0) < 5 * I1.std() / math.sqrt(I1.size)
+
+
+def test_linearity_in_env_and_albedo():
+    sc = scenes.config("tiny", res=48, views=1)
+    keys, tab, dec = full_decisions(sc)
+    Vt, Mt, Et = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, Vt, Mt, Et)
+    sc2 = scenes.config("tiny", res=48, views=1)
+    sc2.env = sc2.env * np.float32(2.0)
+    keys2, tab2, dec2 = full_decisions(sc2)
+    assert np.array_equal(dec2.dtex, dec.dtex) and np.array_equal(dec2.dvis, dec.dvis)
+    I2 = shade.render_image(sc2, tab2, dec2, Vt, Mt, Et * 2)
+    assert torch.allclose(I2, 2 * I, rtol=1e-12)
+
+
+def test_indirect_vanishes_on_convex_mesh():
+    sc = scenes.config("tiny", res=48, views=1, n_bounce=4, n_light=2)
+    keys, tab, dec = full_decisions(sc)
+    assert (dec.stri == -1).all()
+    Vt, Mt, Et = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, Vt, Mt, Et)
+    sc0 = scenes.config("tiny", res=48, views=1)
+    keys0, tab0, dec0 = full_decisions(sc0)
+    I0 = shade.render_image(sc0, tab0, dec0, Vt, Mt, Et)
+    assert torch.equal(I, I0)
+
+
+def test_indirect_sees_cavity():
+    sc = scenes.config("indirect", n=12, map_res=64, env_w=32, env_h=16, views=1, res=48, n_direct=16,
+                       n_bounce=8, n_light=4)
+    keys, tab, dec = full_decisions(sc)
+    valid = dec.stri >= 0
+    assert valid.any()
+    # near-ties between the best and second-best hit are reported, not hidden
+    assert np.isfinite(dec.sgap[valid]).any()
+
+
+# ----------------------------------------------------------------- gradients
+
+def test_autograd_matches_central_differences():
+    sc = scenes.config("tiny", res=64, views=1)
+    keys, tab, dec = full_decisions(sc)
+    rng = np.random.default_rng(11)
+    sel = rng.choice(dec.pix.shape[0], 48, replace=False)
+    sub = oracle.Decisions(sc, tab, dec.pix[sel], dec.keys[sel])
+    Vt, Mt, Et = shade.scene_tensors(sc)
+    g = torch.tensor(rng.normal(size=(48, 3)))
+    gV, gM, gE = shade.backward(sc, tab, sub, Vt, Mt, Et, g)
+
+    def loss(V, M, E):
+        return (shade.shade(sc, tab, sub, V, M, E) * g).sum().item()
+
+    def fd(which, index, h):
+        ts = [Vt.clone(), Mt.clone(), Et.clone()]
+        ts[which][index] += h
+        lp = loss(*ts)
+        ts[which][index] -= 2 * h
+        lm = loss(*ts)
+        return (lp - lm) / (2 * h)
+
+    picks = []
+    nzM = torch.nonzero(gM.abs() > 1e-6 * gM.abs().max())
+    for k in rng.choice(nzM.shape[0], 8, replace=False):
+        picks.append((1, tuple(nzM[k].tolist()), 1e-6, gM))
+    nzE = torch.nonzero(gE.abs() > 1e-6 * gE.abs().max())
+    for k in rng.choice(nzE.shape[0], 6, replace=False):
+        idx = tuple(nzE[k].tolist())
+        picks.append((2, idx, 1e-6 * float(Et[idx]), gE))
+    nzV = torch.nonzero(gV.abs() > 1e-6 * gV.abs().max())
+    for k in rng.choice(nzV.shape[0], 8, replace=False):
+        picks.append((0, tuple(nzV[k].tolist()), 1e-7, gV))
+    for which, idx, h, G in picks:
+        num = fd(which, idx, h)
+        ana = G[idx].item()
+        assert abs(num - ana) <= 1e-5 * max(abs(ana), 1e-3 * G.abs().max().item()), (which, idx, num, ana)
