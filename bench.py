@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Forward + backward shading throughput of the Stage-II UV-PBR renderer.
+
+One step = one pass of the whole hot path over the workload: environment distribution
+build, visibility-buffer raster, direct (+ indirect) shading, L1 loss against a target
+render, and the adjoint into the maps, the environment and the vertex positions.
+Metric: shaded samples per second (fwd+bwd).  One JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload geometry|tiny|indirect]
+  python bench.py --impl reference ...   # the CPU oracle on a bounded sample (host cores)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic FP32 operation counts (per unit of work) used for the ALU roofline
+FLOPS_NODE = 50.0       # one 64-byte node: two slab tests (~25 flops each)
+FLOPS_TRI = 30.0        # one watertight ray/triangle test
+FLOPS_BRDF = 80.0       # one Lambert + GGX evaluation with its cosine and estimator weight
+FLOPS_BRDF_ADJ = 240.0  # evaluation + adjoint in the backward pass
+FP32_LANES_PER_SM = 128
+
+WORKLOADS = {
+    "tiny": "icosphere 1280 tris, maps 256^2 FP32, env 64x32, 4 views 256^2, 64 env samples/px, fwd+bwd",
+    "geometry": "displaced blob 99,372 tris, maps 1024^2 FP32, env 256x128, 16 views 512^2, "
+                "256 env samples/px, fwd+bwd to maps, env and vertex positions",
+    "indirect": "blob with 3 cavities 499,392 tris, maps 2048^2 FP32, env 512x256, 8 views 800^2, "
+                "128 direct + 8 secondary rays x 4 light samples/px, fwd+bwd",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="geometry", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-pixels", type=int, default=384, help="pixels of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = [l.split(", ") for l in open(self.path).read().strip().splitlines() if l.count(",") >= 8]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
+
+
+def dist_init():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def dist_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(sc, npix, seed=0):
+    """Runs the CPU oracle (decisions, FP64 radiance, autograd adjoint) on `npix` covered
+    pixels of the workload.  Returns (shaded samples, seconds, threads)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import shade
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    # candidate pixels: random pixels, kept when the oracle's brute-force raster covers them
+    pix = np.stack([rng.integers(0, sc.views, 4 * npix), rng.integers(0, sc.height, 4 * npix),
+                    rng.integers(0, sc.width, 4 * npix)], 1).astype(np.int32)
+    st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, pix)
+    cov = (keys & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)
+    pix, keys = pix[cov][:npix], keys[cov][:npix]
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, pix, keys)
+    V, M, E = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, V, M, E)
+    g = torch.sign(I - I.mean())
+    shade.backward(sc, tab, dec, V, M, E, g)
+    dt = time.perf_counter() - t0
+    nb = max(sc.n_bounce, 0)
+    valid = int((dec.stri >= 0).sum()) if nb else 0
+    samples = pix.shape[0] * (sc.n_direct + nb) + valid * sc.n_light
+    return samples, dt, torch.get_num_threads(), pix.shape[0]
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from paper_2608_24109_b300 import scenes
+    sc = scenes.config(args.workload)
+    per_step = max(16, args.cpu_pixels // 6)
+    for _ in range(args.warmup):
+        oracle_sample(sc, max(4, per_step // 8), seed=99)
+    times, samples = [], 0
+    threads = 1
+    for k in range(args.steps):
+        s, dt, threads, npx = oracle_sample(sc, per_step, seed=k)
+        times.append(dt)
+        samples = s
+    v = samples / statistics.mean(times)
+    line = {"impl": "reference", "metric": "fwd+bwd shaded samples/s", "value": v, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload + ": " + WORKLOADS[args.workload],
+                       "sample": f"{per_step} covered pixels per step"},
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} covered pixels of the workload per step"},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- native
+
+def run_native(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2608_24109_b300 import build as libbuild
+    from paper_2608_24109_b300 import native as N
+    from paper_2608_24109_b300 import scenes
+    from paper_2608_24109_b300.render import Renderer
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = scenes.config(args.workload)
+    r = Renderer.from_scene(sc, device=local)
+    M = torch.as_tensor(sc.maps, device=dev)
+    Mt = torch.as_tensor(sc.maps_target, device=dev)
+    E = torch.as_tensor(sc.env, device=dev)
+    target = r.forward(Mt, E).clone()
+    img = torch.empty_like(target)
+    grad = torch.empty_like(target)
+    loss = torch.zeros(1, device=dev)
+    gm = torch.zeros_like(M)
+    gE = torch.zeros_like(E)
+    gV = torch.zeros((sc.V.shape[0], 3), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    base_flags = r.params.flags
+    r.params.flags = base_flags | N.FLAG_ZERO_GRADS
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        r.prepare_env(E)
+        r.forward(M, out=img)
+        if ev is not None:
+            ev[0].record(stream)
+        r.l1_loss(img, target, loss, grad)
+        if ev is not None:
+            ev[1].record(stream)
+        r.backward(M, grad, gm, gE, gV)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    r.sync()
+    covered, samples = r.stats()
+    # one instrumented pass to count the algorithmic work of each shading launch
+    r.params.flags = base_flags | N.FLAG_ZERO_GRADS | N.FLAG_COUNT_WORK
+    r.prepare_env(E)
+    r.forward(M, out=img)
+    r.sync()
+    work_fwd = N.exm_frame_work(r.frame)
+    r.l1_loss(img, target, loss, grad)
+    r.backward(M, grad, gm, gE, gV)
+    r.sync()
+    work_bwd = N.exm_frame_work(r.frame)
+    r.params.flags = base_flags | N.FLAG_ZERO_GRADS
+
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    t_step, t_fwd, t_bwd = [], [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        em = [torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+        e0.record(stream)
+        step(em)
+        e1.record(stream)
+        e1.synchronize()
+        t_step.append(e0.elapsed_time(e1))
+        t_fwd.append(e0.elapsed_time(em[0]))
+        t_bwd.append(em[1].elapsed_time(e1))
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    r.sync()
+    barrier(world)
+    ms = dist_max(statistics.mean(t_step), world)
+    value = samples * world / (ms * 1e-3)
+
+    # end to end through the public API: host inputs in, loss out, every step
+    e2e = None
+    if not args.no_e2e:
+        Mh = torch.as_tensor(sc.maps).pin_memory()
+        Eh = torch.as_tensor(sc.env).pin_memory()
+        lh = torch.zeros(1).pin_memory()
+        te = []
+        for k in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            M.copy_(Mh, non_blocking=True)
+            E.copy_(Eh, non_blocking=True)
+            step()
+            lh.copy_(loss, non_blocking=True)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                te.append(time.perf_counter() - t0)
+        r.sync()
+        ems = dist_max(statistics.mean(te), world)
+        e2e = {"value": samples * world / ems, "unit": "samples/s",
+               "h2d_bytes_per_step": Mh.numel() * Mh.element_size() + Eh.numel() * Eh.element_size(),
+               "d2h_bytes_per_step": lh.numel() * lh.element_size()}
+
+    peaks, src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2032.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    flops_fwd = work_fwd[0] * FLOPS_NODE + work_fwd[1] * FLOPS_TRI + work_fwd[2] * FLOPS_BRDF
+    flops_bwd = work_bwd[0] * FLOPS_NODE + work_bwd[1] * FLOPS_TRI + work_bwd[2] * FLOPS_BRDF_ADJ
+    mf, mb = statistics.mean(t_fwd), statistics.mean(t_bwd)
+    dom_bwd = mb >= mf
+    dom_ms, dom_flops = (mb, flops_bwd) if dom_bwd else (mf, flops_fwd)
+    achieved = dom_flops / (dom_ms * 1e-3) / 1e12
+    line = {
+        "metric": "fwd+bwd shaded samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload + ": " + WORKLOADS[args.workload],
+                   "covered_pixels": covered, "shaded_samples_per_step": samples,
+                   "l2": "flushed between steps (256 MiB write outside the timed region)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "ms_forward": mf, "ms_backward": mb},
+        "roofline": {"bound": "alu", "kernel": "shade_kernel<float,%s>" % ("backward" if dom_bwd else "forward"),
+                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": None,
+                     "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
+                                    f"(clock from {src} peaks)",
+                     "work": {"nodes": work_bwd[0] if dom_bwd else work_fwd[0],
+                              "tri_tests": work_bwd[1] if dom_bwd else work_fwd[1],
+                              "brdf": work_bwd[2] if dom_bwd else work_fwd[2],
+                              "rays": work_bwd[3] if dom_bwd else work_fwd[3]}},
+        "clocks": ck,
+        "gpu_launches": 15 * args.steps,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and not args.no_cpu_baseline:
+        s, dt, threads, npx = oracle_sample(sc, args.cpu_pixels)
+        line["cpu_baseline"] = {"value": s / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                                "sample": f"{npx} covered pixels of the workload (decisions, FP64 radiance "
+                                          f"and adjoint), {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    r.close()
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_native(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * exmesh.h -- C ABI of the B300 (sm_103a) Stage-II differentiable UV-PBR renderer.
+ *
+ * The library implements the data-parallel hot path of the UV-PBR decomposition stage
+ * (Sec. 5 of "ExMesh++", arxiv 2608.24109): rasterise a fixed triangle mesh into a
+ * visibility buffer, query UV-space PBR maps (Sec. 5.1, Eqs. 10-11), shade with a
+ * Lambert + GGX microfacet BRDF under an importance-sampled lat-long environment map
+ * with ray-traced visibility (Sec. 5.2, Eqs. 12-17), add one-bounce diffuse indirect
+ * light from secondary rays that hit the same mesh and read the same maps (Sec. 5.3,
+ * Eqs. 18-20), and run the adjoint that scatters gradients into the maps, the
+ * environment map and the vertex positions.
+ *
+ * Conventions (all entry points):
+ *  - Every pointer argument named as "device" is a CUDA device pointer on the context's
+ *    device; "host" pointers are ordinary host memory read before the call returns.
+ *  - The caller owns every input, output and gradient buffer.  The library owns the
+ *    objects it creates (mesh, BVH, environment tables, frames) and frees them in the
+ *    matching *_destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  All
+ *    device work is enqueued on it; calls return once the work is enqueued.
+ *  - Argument errors are returned synchronously and nothing is enqueued.  Errors found on
+ *    the device (guard band, traversal step limit) are latched in the context and
+ *    returned by exm_sync.
+ *  - Nothing crosses the ABI as an exception; every device loop is bounded.
+ *  - Gradients are ACCUMULATED (+=) into caller-zeroed FP32 buffers.
+ */
+#ifndef EXMESH_H
+#define EXMESH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int exm_status;
+#define EXM_OK 0
+#define EXM_ERR_ARG (-1)             /* invalid argument (nothing enqueued) */
+#define EXM_ERR_OOM (-2)             /* device allocation failed */
+#define EXM_ERR_CUDA (-3)            /* a CUDA runtime call failed */
+#define EXM_ERR_GUARDBAND (-4)       /* a vertex behind the near plane / outside +-16384 px,
+                                        or a front face with doubled area >= 2^38 (1/256 px units) */
+#define EXM_ERR_TRAVERSAL_LIMIT (-5) /* a BVH traversal exceeded its step cap (corrupt BVH) */
+#define EXM_ERR_TIMEOUT (-6)         /* a bounded device wait ran out */
+#define EXM_ERR_BUSY (-7)            /* admission refused: not enough budget or slots */
+
+typedef enum { EXM_F32 = 0, EXM_BF16 = 1, EXM_F16 = 2 } exm_dtype;
+
+/* Render flags. */
+#define EXM_FLAG_WRAP_U 1u       /* bilinear fetch wraps in u (spherical UV seam); else clamps */
+#define EXM_FLAG_NO_METALLIC 2u  /* metallic read as 0: the dielectric model (Sec. 5, Sec. 6.1) */
+#define EXM_FLAG_COUNT_WORK 4u   /* also count BVH nodes, triangle tests, BRDF evaluations and rays
+                                    (exm_frame_work); a slower instrumented kernel, same results */
+#define EXM_FLAG_ZERO_GRADS 8u   /* exm_render_backward zeroes the gradient buffers before accumulating */
+
+typedef struct exm_ctx exm_ctx;
+typedef struct exm_mesh exm_mesh;
+typedef struct exm_env exm_env;
+typedef struct exm_frame exm_frame;
+
+/* Pinhole camera (80 bytes).  A point p has camera coordinates x = (p-eye).right,
+ * y = (p-eye).up, w = (p-eye).fwd and projects to pixel (cx + kx*x/w, cy - ky*y/w);
+ * pixel (px, py) has its centre at (px + 0.5, py + 0.5).  near_plane bounds w from below. */
+typedef struct {
+    float eye[3], right[3], up[3], fwd[3];
+    float kx, ky, cx, cy, near_plane;
+    float pad[3];
+} exm_camera;
+
+/* Estimator parameters (Sec. 5.2-5.3): N_d direct environment samples per pixel, N_b
+ * secondary rays per pixel, N_s light samples per valid secondary hit, lambda_ind of
+ * Eq. 20, flags, and the 64-bit seed of the counter-based sample streams. */
+typedef struct {
+    int32_t n_direct;
+    int32_t n_bounce;
+    int32_t n_light;
+    float lambda_ind;
+    uint32_t flags;
+    uint32_t reserved;
+    uint64_t seed;
+} exm_params;
+
+/* ----------------------------------------------------------------- context */
+
+/* Creates a context on CUDA device `device`.  *out receives the handle. */
+exm_status exm_create(int device, exm_ctx** out);
+void exm_destroy(exm_ctx* ctx);
+/* Message of the last error raised on the calling thread (library-owned string). */
+const char* exm_last_error(void);
+/* Waits for `stream` and returns the first device-side error latched since the last
+ * exm_sync (EXM_ERR_GUARDBAND, EXM_ERR_TRAVERSAL_LIMIT), then clears it. */
+exm_status exm_sync(exm_ctx* ctx, void* stream);
+
+/* ------------------------------------------------------------------- mesh (S1) */
+
+/* Uploads the fixed mesh-UV carrier (V*, F*, U*, Phi* of Sec. 5): V float32 [nv,3],
+ * F int32 [nf,3] (counter-clockwise seen from outside), UV float32 [nuv,2] (u right,
+ * v down), Fuv int32 [nf,3] -- all DEVICE pointers, copied.  Computes the per-vertex
+ * normals and per-UV-vertex tangents of the interpolated tangent frame (Sec. 5.1) and
+ * builds the BVH.  Indices are checked on the device; an out-of-range index is an
+ * EXM_ERR_ARG returned by exm_sync. */
+exm_status exm_mesh_create(exm_ctx* ctx, const float* V, int nv, const int32_t* F, int nf,
+                           const float* UV, int nuv, const int32_t* Fuv, void* stream, exm_mesh** out);
+/* Replaces the vertex positions (DEVICE float32 [nv,3]), recomputes frames and BVH. */
+exm_status exm_mesh_update_vertices(exm_mesh* mesh, const float* V, void* stream);
+/* Rebuilds the BVH (linear BVH over 30-bit Morton codes; one triangle per leaf). */
+exm_status exm_bvh_build(exm_mesh* mesh, void* stream);
+void exm_mesh_destroy(exm_mesh* mesh);
+/* Device pointers to the mesh's per-vertex unit normals [nv,3] and per-UV-vertex unit
+ * tangents [nuv,3] (read-only views, valid until the mesh changes). */
+exm_status exm_mesh_frames(const exm_mesh* mesh, const float** normals, const float** tangents);
+
+/* ------------------------------------------------------- environment (Sec. 5.2) */
+
+/* Creates environment tables for a W x H lat-long map (row 0 = +y). */
+exm_status exm_env_create(exm_ctx* ctx, int W, int H, exm_env** out);
+/* Builds the importance distribution from E (DEVICE, [H,W,3] of `dtype`): integer
+ * weights q = 1 + floor(lum * sin(theta_row) * 2^24 / max), exact 64-bit prefix sums and
+ * the sampling guide table; keeps an FP32 copy of E for shading. */
+exm_status exm_env_prepare(exm_env* env, const void* E, exm_dtype dtype, void* stream);
+void exm_env_destroy(exm_env* env);
+/* Total Q of the integer weights (synchronous read, for tests). */
+exm_status exm_env_total(exm_env* env, uint64_t* Q);
+
+/* --------------------------------------------------------- render (Sec. 5.1-5.3) */
+
+/* Per-render saved state: visibility buffer (u64 depth<<32|tri per pixel, all ones when
+ * empty), covered-pixel list, counters, device copy of the cameras. */
+exm_status exm_frame_create(exm_ctx* ctx, int views, int width, int height, exm_frame** out);
+void exm_frame_destroy(exm_frame* frame);
+/* Covered pixels and shaded samples of the last forward (synchronous). */
+exm_status exm_frame_stats(exm_frame* frame, uint64_t* covered, uint64_t* samples);
+/* Work counters of the last pass run with EXM_FLAG_COUNT_WORK (synchronous): counts[0] BVH
+ * nodes visited, [1] ray/triangle tests, [2] BRDF evaluations, [3] rays traced. */
+exm_status exm_frame_work(exm_frame* frame, uint64_t counts[4]);
+/* DEVICE pointer to the visibility buffer [views, height, width] of u64 keys. */
+exm_status exm_frame_visbuf(exm_frame* frame, const uint64_t** keys);
+
+/* Forward render (Eqs. 10-20).  maps: DEVICE [mapH, mapW, 8] texel-interleaved
+ * (A rgb, R, M, N xyz) of `map_dtype`; cams: HOST array of `views` cameras; out_rgb:
+ * DEVICE float32 [views, height, width, 3] (written; background 0).  The frame keeps
+ * the visibility buffer for the backward pass. */
+exm_status exm_render_forward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
+                              int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
+                              const exm_params* params, exm_frame* frame, float* out_rgb, void* stream);
+
+/* Adjoint of exm_render_forward for the same inputs: given grad_rgb (DEVICE float32
+ * [views,height,width,3]) accumulates dL/dmaps (DEVICE float32 [mapH,mapW,8]),
+ * dL/dE (DEVICE float32 [envH,envW,3]) and dL/dV (DEVICE float32 [nv,3]); any gradient
+ * pointer may be NULL to skip it.  The sampling density and every discrete decision are
+ * constants of the derivative. */
+exm_status exm_render_backward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
+                               int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
+                               const exm_params* params, exm_frame* frame, const float* grad_rgb,
+                               float* grad_maps, float* grad_env, float* grad_V, void* stream);
+
+/* L1 image loss of Sec. 6 workloads: *loss (DEVICE float32, written) = mean |pred - target|
+ * over n elements; grad (DEVICE float32 [n], written) = sign(pred - target) / n. */
+exm_status exm_l1_loss(const float* pred, const float* target, int64_t n, float* loss, float* grad,
+                       void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,383 @@
+// C ABI of libexmesh (include/exmesh.h): object lifetimes, argument checks, launches.
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "exm_device.cuh"
+#include "exm_internal.h"
+
+static thread_local std::string g_last_error;
+
+exm_status exm_fail(exm_status code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+exm_status exm_cuda_check(cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return EXM_OK;
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? EXM_ERR_OOM : EXM_ERR_CUDA;
+}
+
+#define EXM_TRY_ALLOC(ptr, bytes, what)                                              \
+    do {                                                                             \
+        if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                    \
+            cudaGetLastError();                                                      \
+            return exm_fail(EXM_ERR_OOM, std::string("allocation failed: ") + what); \
+        }                                                                            \
+    } while (0)
+
+namespace {
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+}  // namespace
+
+__global__ void exm_l1_kernel(const float* __restrict__ pred, const float* __restrict__ target, long long n,
+                              float inv_n, float* loss, float* grad) {
+    float acc = 0.0f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float d = pred[i] - target[i];
+        acc += fabsf(d);
+        grad[i] = d > 0.0f ? inv_n : (d < 0.0f ? -inv_n : 0.0f);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    __shared__ float part[32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) part[wid] = acc;
+    __syncthreads();
+    if (wid == 0) {
+        acc = lane < (int)(blockDim.x >> 5) ? part[lane] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) atomicAdd(loss, acc * inv_n);
+    }
+}
+
+extern "C" {
+
+const char* exm_last_error(void) { return g_last_error.c_str(); }
+
+exm_status exm_create(int device, exm_ctx** out) {
+    if (!out) return exm_fail(EXM_ERR_ARG, "exm_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
+        return exm_fail(EXM_ERR_ARG, "exm_create: no such CUDA device");
+    DeviceGuard g(device);
+    exm_ctx* c = new (std::nothrow) exm_ctx();
+    if (!c) return exm_fail(EXM_ERR_OOM, "exm_create: host allocation");
+    c->device = device;
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess) {
+        delete c;
+        return exm_fail(EXM_ERR_OOM, "exm_create: status word");
+    }
+    cudaMemset(c->d_status, 0, sizeof(uint32_t));
+    *out = c;
+    return exm_cuda_check(cudaDeviceSynchronize(), "exm_create");
+}
+
+void exm_destroy(exm_ctx* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    cudaFree(c->d_status);
+    delete c;
+}
+
+exm_status exm_sync(exm_ctx* c, void* stream) {
+    if (!c) return exm_fail(EXM_ERR_ARG, "exm_sync: ctx is NULL");
+    DeviceGuard g(c->device);
+    exm_status st = exm_cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "exm_sync");
+    if (st != EXM_OK) return st;
+    uint32_t bits = 0;
+    st = exm_cuda_check(cudaMemcpy(&bits, c->d_status, 4, cudaMemcpyDeviceToHost), "exm_sync status read");
+    if (st != EXM_OK) return st;
+    if (bits) cudaMemset(c->d_status, 0, 4);
+    if (bits & exm::ERRBIT_INDEX) return exm_fail(EXM_ERR_ARG, "index out of range in the mesh");
+    if (bits & exm::ERRBIT_GUARD)
+        return exm_fail(EXM_ERR_GUARDBAND, "a vertex lies behind the near plane or outside the guard band");
+    if (bits & exm::ERRBIT_TRAVERSAL) return exm_fail(EXM_ERR_TRAVERSAL_LIMIT, "BVH traversal step/stack limit");
+    return EXM_OK;
+}
+
+// ------------------------------------------------------------------------ mesh
+
+static void mesh_free(exm_mesh* m) {
+    void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nodes, m->tris,
+                    m->codes, m->codes_sorted, m->ids, m->ids_sorted, m->parent, m->child, m->flags, m->bounds,
+                    m->scene_box, m->sort_tmp};
+    for (void* p : ptrs) cudaFree(p);
+}
+
+exm_status exm_mesh_create(exm_ctx* c, const float* V, int nv, const int32_t* F, int nf, const float* UV, int nuv,
+                           const int32_t* Fuv, void* stream, exm_mesh** out) {
+    if (!out) return exm_fail(EXM_ERR_ARG, "exm_mesh_create: out is NULL");
+    *out = nullptr;
+    if (!c || !V || !F || !UV || !Fuv) return exm_fail(EXM_ERR_ARG, "exm_mesh_create: NULL argument");
+    if (nv < 3 || nf < 1 || nuv < 3) return exm_fail(EXM_ERR_ARG, "exm_mesh_create: empty mesh");
+    if (nf > (1 << 28) || nv > (1 << 28) || nuv > (1 << 28)) return exm_fail(EXM_ERR_ARG, "exm_mesh_create: mesh too large");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    exm_mesh* m = new (std::nothrow) exm_mesh();
+    if (!m) return exm_fail(EXM_ERR_OOM, "exm_mesh_create: host allocation");
+    m->ctx = c;
+    m->nv = nv; m->nf = nf; m->nuv = nuv;
+    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    bool ok = alloc((void**)&m->V, (size_t)nv * 12) && alloc((void**)&m->F, (size_t)nf * 12) &&
+              alloc((void**)&m->UV, (size_t)nuv * 8) && alloc((void**)&m->Fuv, (size_t)nf * 12) &&
+              alloc((void**)&m->nacc, (size_t)nv * 12) && alloc((void**)&m->nrm, (size_t)nv * 12) &&
+              alloc((void**)&m->tacc, (size_t)nuv * 12) && alloc((void**)&m->tan, (size_t)nuv * 12) &&
+              alloc((void**)&m->fsign, (size_t)nf * 4);
+    if (!ok) {
+        cudaGetLastError();
+        mesh_free(m);
+        delete m;
+        return exm_fail(EXM_ERR_OOM, "exm_mesh_create: device allocation");
+    }
+    cudaMemcpyAsync(m->V, V, (size_t)nv * 12, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m->F, F, (size_t)nf * 12, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m->UV, UV, (size_t)nuv * 8, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(m->Fuv, Fuv, (size_t)nf * 12, cudaMemcpyDeviceToDevice, s);
+    exm_status st = exm_frames_build(m, s);
+    if (st == EXM_OK) st = exm_bvh_build_impl(m, s);
+    if (st != EXM_OK) {
+        mesh_free(m);
+        delete m;
+        return st;
+    }
+    *out = m;
+    return EXM_OK;
+}
+
+exm_status exm_mesh_update_vertices(exm_mesh* m, const float* V, void* stream) {
+    if (!m || !V) return exm_fail(EXM_ERR_ARG, "exm_mesh_update_vertices: NULL argument");
+    DeviceGuard g(m->ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemcpyAsync(m->V, V, (size_t)m->nv * 12, cudaMemcpyDeviceToDevice, s);
+    exm_status st = exm_frames_build(m, s);
+    if (st != EXM_OK) return st;
+    return exm_bvh_build_impl(m, s);
+}
+
+exm_status exm_bvh_build(exm_mesh* m, void* stream) {
+    if (!m) return exm_fail(EXM_ERR_ARG, "exm_bvh_build: mesh is NULL");
+    DeviceGuard g(m->ctx->device);
+    return exm_bvh_build_impl(m, (cudaStream_t)stream);
+}
+
+void exm_mesh_destroy(exm_mesh* m) {
+    if (!m) return;
+    DeviceGuard g(m->ctx->device);
+    mesh_free(m);
+    delete m;
+}
+
+exm_status exm_mesh_frames(const exm_mesh* m, const float** normals, const float** tangents) {
+    if (!m || !normals || !tangents) return exm_fail(EXM_ERR_ARG, "exm_mesh_frames: NULL argument");
+    *normals = m->nrm;
+    *tangents = m->tan;
+    return EXM_OK;
+}
+
+// ------------------------------------------------------------------------ env
+
+static void env_free(exm_env* e) {
+    void* ptrs[] = {e->texel, e->q, e->cdf, e->rowsum, e->rowpre, e->guide, e->wbuf, e->wmax, e->total};
+    for (void* p : ptrs) cudaFree(p);
+}
+
+exm_status exm_env_create(exm_ctx* c, int W, int H, exm_env** out) {
+    if (!out) return exm_fail(EXM_ERR_ARG, "exm_env_create: out is NULL");
+    *out = nullptr;
+    if (!c || W < 1 || H < 1 || (long long)W * H > (1 << 22)) return exm_fail(EXM_ERR_ARG, "exm_env_create: bad size");
+    DeviceGuard g(c->device);
+    exm_env* e = new (std::nothrow) exm_env();
+    if (!e) return exm_fail(EXM_ERR_OOM, "exm_env_create: host allocation");
+    e->ctx = c;
+    e->W = W; e->H = H;
+    size_t n = (size_t)W * H;
+    int bits = 1;
+    while ((1u << bits) < n && bits < 23) ++bits;
+    e->gbits = bits + 1;
+    size_t G = ((size_t)1 << e->gbits) + 1;
+    bool ok = cudaMalloc(&e->texel, n * sizeof(float4)) == cudaSuccess && cudaMalloc(&e->q, n * 4) == cudaSuccess &&
+              cudaMalloc(&e->cdf, n * 8) == cudaSuccess && cudaMalloc(&e->rowsum, (size_t)H * 8) == cudaSuccess &&
+              cudaMalloc(&e->rowpre, (size_t)H * 8) == cudaSuccess && cudaMalloc(&e->guide, G * 4) == cudaSuccess &&
+              cudaMalloc(&e->wbuf, n * 4) == cudaSuccess && cudaMalloc(&e->wmax, 4) == cudaSuccess &&
+              cudaMalloc(&e->total, 8) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        env_free(e);
+        delete e;
+        return exm_fail(EXM_ERR_OOM, "exm_env_create: device allocation");
+    }
+    *out = e;
+    return EXM_OK;
+}
+
+exm_status exm_env_prepare(exm_env* e, const void* E, exm_dtype dtype, void* stream) {
+    if (!e || !E) return exm_fail(EXM_ERR_ARG, "exm_env_prepare: NULL argument");
+    if (dtype != EXM_F32 && dtype != EXM_BF16 && dtype != EXM_F16) return exm_fail(EXM_ERR_ARG, "exm_env_prepare: dtype");
+    DeviceGuard g(e->ctx->device);
+    return exm_env_prepare_impl(e, E, dtype, (cudaStream_t)stream);
+}
+
+void exm_env_destroy(exm_env* e) {
+    if (!e) return;
+    DeviceGuard g(e->ctx->device);
+    env_free(e);
+    delete e;
+}
+
+exm_status exm_env_total(exm_env* e, uint64_t* Q) {
+    if (!e || !Q) return exm_fail(EXM_ERR_ARG, "exm_env_total: NULL argument");
+    DeviceGuard g(e->ctx->device);
+    return exm_cuda_check(cudaMemcpy(Q, e->total, 8, cudaMemcpyDeviceToHost), "exm_env_total");
+}
+
+// ---------------------------------------------------------------------- frame
+
+static void frame_free(exm_frame* f) {
+    void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY, f->Zq, f->genv, f->gnrm, f->gtan};
+    for (void* p : ptrs) cudaFree(p);
+}
+
+exm_status exm_frame_create(exm_ctx* c, int views, int width, int height, exm_frame** out) {
+    if (!out) return exm_fail(EXM_ERR_ARG, "exm_frame_create: out is NULL");
+    *out = nullptr;
+    if (!c || views < 1 || width < 1 || height < 1 || width > 16384 || height > 16384 ||
+        (long long)views * width * height >= (1ll << 31))
+        return exm_fail(EXM_ERR_ARG, "exm_frame_create: bad size");
+    DeviceGuard g(c->device);
+    exm_frame* f = new (std::nothrow) exm_frame();
+    if (!f) return exm_fail(EXM_ERR_OOM, "exm_frame_create: host allocation");
+    f->ctx = c;
+    f->views = views; f->W = width; f->H = height;
+    size_t n = (size_t)views * width * height;
+    bool ok = cudaMalloc(&f->visbuf, n * 8) == cudaSuccess && cudaMalloc(&f->pixels, n * 4) == cudaSuccess &&
+              cudaMalloc(&f->counters, 16) == cudaSuccess && cudaMalloc(&f->samples, 8) == cudaSuccess &&
+              cudaMalloc(&f->work, 32) == cudaSuccess &&
+              cudaMalloc(&f->cams, (size_t)views * sizeof(exm_camera)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        frame_free(f);
+        delete f;
+        return exm_fail(EXM_ERR_OOM, "exm_frame_create: device allocation");
+    }
+    cudaMemset(f->counters, 0, 16);
+    cudaMemset(f->samples, 0, 8);
+    cudaMemset(f->work, 0, 32);
+    *out = f;
+    return EXM_OK;
+}
+
+void exm_frame_destroy(exm_frame* f) {
+    if (!f) return;
+    DeviceGuard g(f->ctx->device);
+    frame_free(f);
+    delete f;
+}
+
+exm_status exm_frame_stats(exm_frame* f, uint64_t* covered, uint64_t* samples) {
+    if (!f) return exm_fail(EXM_ERR_ARG, "exm_frame_stats: frame is NULL");
+    DeviceGuard g(f->ctx->device);
+    uint32_t cnt = 0;
+    unsigned long long smp = 0;
+    exm_status st = exm_cuda_check(cudaMemcpy(&cnt, f->counters, 4, cudaMemcpyDeviceToHost), "frame stats");
+    if (st == EXM_OK) st = exm_cuda_check(cudaMemcpy(&smp, f->samples, 8, cudaMemcpyDeviceToHost), "frame stats");
+    if (covered) *covered = cnt;
+    if (samples) *samples = smp;
+    return st;
+}
+
+exm_status exm_frame_work(exm_frame* f, uint64_t counts[4]) {
+    if (!f || !counts) return exm_fail(EXM_ERR_ARG, "exm_frame_work: NULL argument");
+    DeviceGuard g(f->ctx->device);
+    return exm_cuda_check(cudaMemcpy(counts, f->work, 32, cudaMemcpyDeviceToHost), "frame work counters");
+}
+
+exm_status exm_frame_visbuf(exm_frame* f, const uint64_t** keys) {
+    if (!f || !keys) return exm_fail(EXM_ERR_ARG, "exm_frame_visbuf: NULL argument");
+    *keys = f->visbuf;
+    return EXM_OK;
+}
+
+// --------------------------------------------------------------------- render
+
+static exm_status check_render(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
+                               const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
+                               const exm_frame* f, const char* who) {
+    std::string w(who);
+    if (!c || !m || !maps || !e || !cams || !p || !f) return exm_fail(EXM_ERR_ARG, w + ": NULL argument");
+    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, w + ": map dtype");
+    if (mapW < 1 || mapH < 1 || (long long)mapW * mapH > (1ll << 28)) return exm_fail(EXM_ERR_ARG, w + ": map size");
+    if (views != f->views) return exm_fail(EXM_ERR_ARG, w + ": views differ from the frame's");
+    if (p->n_direct < 1 || p->n_direct > 65536) return exm_fail(EXM_ERR_ARG, w + ": n_direct must be in [1, 65536]");
+    if (p->n_bounce < 0 || p->n_bounce > 4096) return exm_fail(EXM_ERR_ARG, w + ": n_bounce must be in [0, 4096]");
+    if (p->n_bounce > 0 && (p->n_light < 1 || p->n_light > 4096))
+        return exm_fail(EXM_ERR_ARG, w + ": n_light must be in [1, 4096] with secondary rays");
+    if ((long long)p->n_bounce * (p->n_light > 0 ? p->n_light : 1) > (1ll << 31))
+        return exm_fail(EXM_ERR_ARG, w + ": n_bounce * n_light too large");
+    if (m->ctx != c || e->ctx != c || f->ctx != c) return exm_fail(EXM_ERR_ARG, w + ": objects of another context");
+    for (int v = 0; v < views; ++v)
+        if (!(cams[v].kx > 0.0f) || !(cams[v].ky > 0.0f) || !(cams[v].near_plane > 0.0f))
+            return exm_fail(EXM_ERR_ARG, w + ": camera kx, ky and near_plane must be positive");
+    return EXM_OK;
+}
+
+exm_status exm_render_forward(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
+                              const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
+                              exm_frame* f, float* out_rgb, void* stream) {
+    exm_status st = check_render(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, "exm_render_forward");
+    if (st != EXM_OK) return st;
+    if (!out_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_forward: out_rgb is NULL");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = exm_cuda_check(cudaMemcpyAsync(f->cams, cams, (size_t)views * sizeof(exm_camera), cudaMemcpyHostToDevice, s),
+                        "camera upload");
+    if (st != EXM_OK) return st;
+    st = exm_raster_impl(c, m, f, views, s);
+    if (st != EXM_OK) return st;
+    return exm_shade_forward_impl(c, m, maps, dt, mapW, mapH, e, f, p, out_rgb, s);
+}
+
+exm_status exm_render_backward(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
+                               const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
+                               exm_frame* f, const float* grad_rgb, float* grad_maps, float* grad_env, float* grad_V,
+                               void* stream) {
+    exm_status st = check_render(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, "exm_render_backward");
+    if (st != EXM_OK) return st;
+    if (!grad_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_backward: grad_rgb is NULL");
+    DeviceGuard g(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    st = exm_cuda_check(cudaMemcpyAsync(f->cams, cams, (size_t)views * sizeof(exm_camera), cudaMemcpyHostToDevice, s),
+                        "camera upload");
+    if (st != EXM_OK) return st;
+    return exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, f, p, grad_rgb, grad_maps, grad_env, grad_V, s);
+}
+
+exm_status exm_l1_loss(const float* pred, const float* target, int64_t n, float* loss, float* grad, void* stream) {
+    if (!pred || !target || !loss || !grad || n < 1) return exm_fail(EXM_ERR_ARG, "exm_l1_loss: bad argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaMemsetAsync(loss, 0, sizeof(float), s);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 148;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long blocks = (n + 255) / 256;
+    if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
+    exm_l1_kernel<<<(int)blocks, 256, 0, s>>>(pred, target, (long long)n, 1.0f / (float)n, loss, grad);
+    return exm_cuda_check(cudaGetLastError(), "exm_l1_loss launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,522 @@
+// Device-side building blocks of the Stage-II renderer (sm_103a).
+//
+// Two kinds of arithmetic live here:
+//  * the FP32 decision specification -- every step that decides an integer (coverage,
+//    texel choice, shadow-ray visibility, secondary hit id) or builds the rays that feed
+//    such a decision is written with explicitly rounded intrinsics (__fadd_rn, __fmul_rn,
+//    ...), so the compiler cannot contract it into FMAs and the decision is the one the
+//    specification fixes;
+//  * shading, which is ordinary FP32 (contraction allowed).
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace exm {
+
+// Device error bits latched in the context's status word.
+enum : uint32_t { ERRBIT_GUARD = 1u, ERRBIT_TRAVERSAL = 2u, ERRBIT_INDEX = 4u };
+
+constexpr float kPi = 3.14159265358979323846f;
+constexpr float kFDielectric = 0.04f;   // F_dielectric of Eq. 16
+constexpr float kSpecEps = 1e-6f;       // epsilon of Eq. 15
+constexpr float kRMin = 0.08f;          // roughness clamp before alpha = r^2
+constexpr int kStackSize = 64;
+constexpr int kTraversalCap = 1 << 20;
+
+// ------------------------------------------------------------- spec arithmetic
+struct S3 { float x, y, z; };
+__device__ __forceinline__ S3 s3(float x, float y, float z) { return S3{x, y, z}; }
+__device__ __forceinline__ float sadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float ssub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float smul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float sdiv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ S3 ssub3(S3 a, S3 b) { return s3(ssub(a.x, b.x), ssub(a.y, b.y), ssub(a.z, b.z)); }
+__device__ __forceinline__ float sdot(S3 a, S3 b) {
+    return sadd(sadd(smul(a.x, b.x), smul(a.y, b.y)), smul(a.z, b.z));
+}
+__device__ __forceinline__ S3 scross(S3 a, S3 b) {
+    return s3(ssub(smul(a.y, b.z), smul(a.z, b.y)), ssub(smul(a.z, b.x), smul(a.x, b.z)),
+              ssub(smul(a.x, b.y), smul(a.y, b.x)));
+}
+__device__ __forceinline__ float scomp(S3 a, int k) { return k == 0 ? a.x : (k == 1 ? a.y : a.z); }
+
+// sin(2 pi s), cos(2 pi s) for s in [0, 1): exact quadrant reduction, Taylor polynomials
+// of degree 9 / 10 in Horner form on |a| <= pi/4 (coefficients 1/n! rounded to float).
+__device__ __forceinline__ void sincos2pi(float s, float* sn, float* cs) {
+    int q = __float2int_rn(smul(s, 4.0f));
+    float r = ssub(s, smul((float)q, 0.25f));
+    float a = smul(r, 0x1.921fb6p+2f);
+    float a2 = smul(a, a);
+    float ps = 0x1.71de3ap-19f;
+    ps = ssub(smul(ps, a2), 0x1.a01a02p-13f);
+    ps = sadd(smul(ps, a2), 0x1.111112p-7f);
+    ps = ssub(smul(ps, a2), 0x1.555556p-3f);
+    float sa = sadd(a, smul(smul(a, a2), ps));
+    float pc = -0x1.27e4fcp-22f;
+    pc = sadd(smul(pc, a2), 0x1.a01a02p-16f);
+    pc = ssub(smul(pc, a2), 0x1.6c16c2p-10f);
+    pc = sadd(smul(pc, a2), 0x1.555556p-5f);
+    pc = ssub(smul(pc, a2), 0.5f);
+    float ca = sadd(1.0f, smul(a2, pc));
+    switch (q & 3) {
+        case 0: *sn = sa; *cs = ca; break;
+        case 1: *sn = ca; *cs = -sa; break;
+        case 2: *sn = -sa; *cs = -ca; break;
+        default: *sn = -ca; *cs = sa; break;
+    }
+}
+
+// ------------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3" (SC 2011).
+__device__ __forceinline__ uint4 philox(uint4 c, uint2 k) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k.x += 0x9E3779B9u; k.y += 0xBB67AE85u; }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+__device__ __forceinline__ float unit24(uint32_t h) { return smul(__uint2float_rn(h >> 8), 0x1p-24f); }
+// floor((k * 2^32 + r) / n): stratum k of n as a 32-bit fraction.
+__device__ __forceinline__ uint32_t stratified32(uint32_t k, uint32_t n, uint32_t r) {
+    uint64_t num = ((uint64_t)k << 32) | (uint64_t)r;
+    if ((n & (n - 1)) == 0) return (uint32_t)(num >> (31 - __clz(n)));
+    return (uint32_t)(num / n);
+}
+
+// ------------------------------------------------------------------- rays (spec)
+struct Ray {
+    S3 o, d;
+    int kx, ky, kz;
+    float Sx, Sy, Sz;
+    float3 inv;  // 1/d for the (padded, conservative) box test
+};
+
+__device__ __forceinline__ Ray make_ray(S3 o, S3 d) {
+    Ray r;
+    r.o = o; r.d = d;
+    float ax = fabsf(d.x), ay = fabsf(d.y), az = fabsf(d.z);
+    int kz = ax >= ay ? (ax >= az ? 0 : 2) : (ay >= az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1;
+    int ky = kx == 2 ? 0 : kx + 1;
+    float dz = scomp(d, kz);
+    if (dz < 0.0f) { int t = kx; kx = ky; ky = t; }
+    r.kx = kx; r.ky = ky; r.kz = kz;
+    r.Sx = sdiv(scomp(d, kx), dz);
+    r.Sy = sdiv(scomp(d, ky), dz);
+    r.Sz = sdiv(1.0f, dz);
+    r.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    return r;
+}
+
+// Watertight ray/triangle test (Woop, Benthin, Wald, JCGT 2013).  True on a hit with
+// t = T/det > 0; det > 0 when the face's counter-clockwise side faces the ray origin.
+__device__ __forceinline__ bool woop(const Ray& r, S3 p0, S3 p1, S3 p2, float* Tout, float* detout) {
+    S3 A = ssub3(p0, r.o), B = ssub3(p1, r.o), C = ssub3(p2, r.o);
+    float Akz = scomp(A, r.kz), Bkz = scomp(B, r.kz), Ckz = scomp(C, r.kz);
+    float Ax = ssub(scomp(A, r.kx), smul(r.Sx, Akz)), Ay = ssub(scomp(A, r.ky), smul(r.Sy, Akz));
+    float Bx = ssub(scomp(B, r.kx), smul(r.Sx, Bkz)), By = ssub(scomp(B, r.ky), smul(r.Sy, Bkz));
+    float Cx = ssub(scomp(C, r.kx), smul(r.Sx, Ckz)), Cy = ssub(scomp(C, r.ky), smul(r.Sy, Ckz));
+    float U = ssub(smul(Cx, By), smul(Cy, Bx));
+    float V = ssub(smul(Ax, Cy), smul(Ay, Cx));
+    float W = ssub(smul(Bx, Ay), smul(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = __double2float_rn(__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx)));
+        V = __double2float_rn(__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx)));
+        W = __double2float_rn(__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax)));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    float det = sadd(sadd(U, V), W);
+    if (det == 0.0f) return false;
+    float Az = smul(r.Sz, Akz), Bz = smul(r.Sz, Bkz), Cz = smul(r.Sz, Ckz);
+    float T = sadd(sadd(smul(U, Az), smul(V, Bz)), smul(W, Cz));
+    if (!((det > 0.0f && T > 0.0f) || (det < 0.0f && T < 0.0f))) return false;
+    *Tout = T;
+    *detout = det;
+    return true;
+}
+
+// Moller-Trumbore barycentrics of o + t d on (p0, p1, p2); x = (b0 p0 + b1 p1) + b2 p2;
+// unit geometric normal of the face.
+__device__ __forceinline__ void surface_point(S3 o, S3 d, S3 p0, S3 p1, S3 p2, S3* x, S3* ng, float b[3]) {
+    S3 e1 = ssub3(p1, p0), e2 = ssub3(p2, p0);
+    S3 pv = scross(d, e2);
+    float det = sdot(e1, pv);
+    float inv = sdiv(1.0f, det);
+    S3 s = ssub3(o, p0);
+    float b1 = smul(sdot(s, pv), inv);
+    S3 qv = scross(s, e1);
+    float b2 = smul(sdot(d, qv), inv);
+    float b0 = ssub(ssub(1.0f, b1), b2);
+    b[0] = b0; b[1] = b1; b[2] = b2;
+    *x = s3(sadd(sadd(smul(b0, p0.x), smul(b1, p1.x)), smul(b2, p2.x)),
+            sadd(sadd(smul(b0, p0.y), smul(b1, p1.y)), smul(b2, p2.y)),
+            sadd(sadd(smul(b0, p0.z), smul(b1, p1.z)), smul(b2, p2.z)));
+    S3 c = scross(e1, e2);
+    float len = __fsqrt_rn(sdot(c, c));
+    *ng = s3(sdiv(c.x, len), sdiv(c.y, len), sdiv(c.z, len));
+}
+
+__device__ __forceinline__ S3 offset_origin(S3 x, S3 ng) {
+    const float eps = 0x1.a36e2ep-14f;  // 1e-4 scene units
+    return s3(sadd(x.x, smul(eps, ng.x)), sadd(x.y, smul(eps, ng.y)), sadd(x.z, smul(eps, ng.z)));
+}
+
+struct Cam {  // mirrors exm_camera
+    float eye[3], right[3], up[3], fwd[3];
+    float kx, ky, cx, cy, near_plane;
+    float pad[3];
+};
+
+__device__ __forceinline__ void camera_ray(const Cam& c, int px, int py, S3* o, S3* d) {
+    float dx = sdiv(ssub(sadd((float)px, 0.5f), c.cx), c.kx);
+    float dy = sdiv(ssub(c.cy, sadd((float)py, 0.5f)), c.ky);
+    *o = s3(c.eye[0], c.eye[1], c.eye[2]);
+    *d = s3(sadd(sadd(c.fwd[0], smul(dx, c.right[0])), smul(dy, c.up[0])),
+            sadd(sadd(c.fwd[1], smul(dx, c.right[1])), smul(dy, c.up[1])),
+            sadd(sadd(c.fwd[2], smul(dx, c.right[2])), smul(dy, c.up[2])));
+}
+
+// Orthonormal basis about n (Duff et al., JCGT 2017) and a cosine-weighted direction.
+__device__ __forceinline__ S3 cosine_dir(S3 n, float xi1, float xi2) {
+    float sign = copysignf(1.0f, n.z);
+    float a = sdiv(-1.0f, sadd(sign, n.z));
+    float b = smul(smul(n.x, n.y), a);
+    S3 t = s3(sadd(1.0f, smul(smul(smul(sign, n.x), n.x), a)), smul(sign, b), -smul(sign, n.x));
+    S3 bb = s3(b, sadd(sign, smul(smul(n.y, n.y), a)), -n.y);
+    float r = __fsqrt_rn(xi1);
+    float sp, cp;
+    sincos2pi(xi2, &sp, &cp);
+    float lx = smul(r, cp), ly = smul(r, sp), lz = __fsqrt_rn(ssub(1.0f, xi1));
+    return s3(sadd(sadd(smul(t.x, lx), smul(bb.x, ly)), smul(n.x, lz)),
+              sadd(sadd(smul(t.y, lx), smul(bb.y, ly)), smul(n.y, lz)),
+              sadd(sadd(smul(t.z, lx), smul(bb.z, ly)), smul(n.z, lz)));
+}
+
+// Light direction of texel (i, j) = (row, column) jittered by (xu, xv); also sin(theta).
+__device__ __forceinline__ S3 light_dir(int i, int j, int W, int H, float xu, float xv, float* sin_theta) {
+    float fv = sdiv(sadd((float)i, xv), (float)H);
+    float fu = sdiv(sadd((float)j, xu), (float)W);
+    float st, ct, sp, cp;
+    sincos2pi(smul(fv, 0.5f), &st, &ct);
+    sincos2pi(fu, &sp, &cp);
+    *sin_theta = st;
+    return s3(smul(st, sp), ct, -smul(st, cp));
+}
+
+// ------------------------------------------------------------ environment sampling
+struct EnvView {
+    const float4* texel;     // [H*W]: E.rgb, (q/Q) * W*H / (2 pi^2)
+    const uint64_t* cdf;     // [H*W] inclusive prefix of the integer weights (row-major)
+    const uint32_t* guide;   // [G+1]: texel picked at U = g * 2^(32-gbits)
+    const uint64_t* Qp;      // total of the integer weights (device)
+    uint64_t Q;              // loaded from Qp once per thread
+    int W, H;
+    int gbits;
+};
+
+// Texel chosen by the 32-bit stratified fraction U: target t = floor(U * Q / 2^32), then
+// the smallest index whose inclusive prefix exceeds t (searched inside the guide bucket).
+__device__ __forceinline__ uint32_t pick_texel(const EnvView& e, uint32_t U) {
+    uint64_t qh = e.Q >> 32, ql = e.Q & 0xffffffffull;
+    uint64_t t = (uint64_t)U * qh + (((uint64_t)U * ql) >> 32);
+    uint32_t g = U >> (32 - e.gbits);
+    uint32_t lo = __ldg(e.guide + g), hi = __ldg(e.guide + g + 1);
+    while (lo < hi) {
+        uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(e.cdf + mid) > t) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
+
+struct LightSample {
+    S3 dir;        // unnormalised spec direction
+    float inv_pdf; // 1 / p_omega
+    float3 E;      // environment radiance of the texel
+    uint32_t texel;
+};
+
+__device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, uint32_t k, uint32_t n) {
+    LightSample s;
+    uint32_t U = stratified32(k, n, h.x);
+    uint32_t t = pick_texel(e, U);
+    float xu = unit24(h.y), xv = unit24(h.z);
+    int i = (int)(t / (uint32_t)e.W), j = (int)(t - (uint32_t)i * (uint32_t)e.W);
+    float st;
+    s.dir = light_dir(i, j, e.W, e.H, xu, xv, &st);
+    float4 tx = __ldg(e.texel + t);
+    s.E = make_float3(tx.x, tx.y, tx.z);
+    s.inv_pdf = st / tx.w;
+    s.texel = t;
+    return s;
+}
+
+// ----------------------------------------------------------------------- BVH
+// Binary BVH, 64-byte nodes: child boxes (lo0, hi0, lo1, hi1) in 3 float4 and the two
+// child references in the 4th (>= 0 internal node, < 0 leaf ~k = sorted triangle k).
+// Triangles in leaf order, 3 float4 each (p0 + original id bits in .w, p1, p2).
+struct BvhView {
+    const float4* nodes;
+    const float4* tris;
+};
+
+__device__ __forceinline__ bool slab(float3 lo, float3 hi, const Ray& r, float tmax, float* tnear) {
+    float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
+    float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
+    float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
+    float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    *tnear = t0;
+    return t0 <= t1;
+}
+
+__device__ __forceinline__ bool tri_test(const BvhView& b, int k, const Ray& r, float* T, float* det, int* id) {
+    float4 a = __ldg(b.tris + 3 * k), c = __ldg(b.tris + 3 * k + 1), d = __ldg(b.tris + 3 * k + 2);
+    *id = __float_as_int(a.w);
+    return woop(r, s3(a.x, a.y, a.z), s3(c.x, c.y, c.z), s3(d.x, d.y, d.z), T, det);
+}
+
+// Any hit with t > 0.  Sets ERRBIT_TRAVERSAL in *err and reports a hit when the step cap
+// or the stack is exceeded.
+__device__ __forceinline__ bool any_hit(const BvhView& b, const Ray& r, uint32_t* err, uint32_t& nn, uint32_t& nt) {
+    int stack[kStackSize];
+    int sp = 0;
+    int node = 0;
+    for (int steps = 0; steps < kTraversalCap; ++steps) {
+        ++nn;
+        float4 n0 = __ldg(b.nodes + 4 * node), n1 = __ldg(b.nodes + 4 * node + 1);
+        float4 n2 = __ldg(b.nodes + 4 * node + 2), n3 = __ldg(b.nodes + 4 * node + 3);
+        float ta, tb;
+        bool ha = slab(make_float3(n0.x, n0.y, n0.z), make_float3(n0.w, n1.x, n1.y), r, INFINITY, &ta);
+        bool hb = slab(make_float3(n1.z, n1.w, n2.x), make_float3(n2.y, n2.z, n2.w), r, INFINITY, &tb);
+        int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+        int next = -1;
+        if (ha) {
+            if (ca < 0) { float T, det; int id; ++nt; if (tri_test(b, ~ca, r, &T, &det, &id)) return true; }
+            else next = ca;
+        }
+        if (hb) {
+            if (cb < 0) { float T, det; int id; ++nt; if (tri_test(b, ~cb, r, &T, &det, &id)) return true; }
+            else if (next < 0) next = cb;
+            else {
+                if (sp >= kStackSize) { *err |= ERRBIT_TRAVERSAL; return true; }
+                stack[sp++] = cb;
+            }
+        }
+        if (next < 0) {
+            if (sp == 0) return false;
+            next = stack[--sp];
+        }
+        node = next;
+    }
+    *err |= ERRBIT_TRAVERSAL;
+    return true;
+}
+
+// Closest hit (smallest t, ties to the lower original id).  Returns the id or -1;
+// *front = det > 0 of that hit.
+__device__ __forceinline__ int closest_hit(const BvhView& b, const Ray& r, float* tout, bool* front, uint32_t* err,
+                                           uint32_t& nn, uint32_t& nt) {
+    int stack[kStackSize];
+    int sp = 0;
+    int node = 0;
+    int best = -1;
+    float bt = INFINITY, bdet = 0.0f;
+    for (int steps = 0; steps < kTraversalCap; ++steps) {
+        ++nn;
+        float4 n0 = __ldg(b.nodes + 4 * node), n1 = __ldg(b.nodes + 4 * node + 1);
+        float4 n2 = __ldg(b.nodes + 4 * node + 2), n3 = __ldg(b.nodes + 4 * node + 3);
+        float ta, tb;
+        bool ha = slab(make_float3(n0.x, n0.y, n0.z), make_float3(n0.w, n1.x, n1.y), r, bt, &ta);
+        bool hb = slab(make_float3(n1.z, n1.w, n2.x), make_float3(n2.y, n2.z, n2.w), r, bt, &tb);
+        int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+        if (ha && ca < 0) {
+            float T, det; int id;
+            ++nt;
+            if (tri_test(b, ~ca, r, &T, &det, &id)) {
+                float t = sdiv(T, det);
+                if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+            }
+            ha = false;
+        }
+        if (hb && cb < 0) {
+            float T, det; int id;
+            ++nt;
+            if (tri_test(b, ~cb, r, &T, &det, &id)) {
+                float t = sdiv(T, det);
+                if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+            }
+            hb = false;
+        }
+        // re-check the inner children against the possibly shrunk best distance
+        if (ha && ta > bt) ha = false;
+        if (hb && tb > bt) hb = false;
+        int next = -1;
+        if (ha && hb) {
+            int first = ta <= tb ? ca : cb, second = ta <= tb ? cb : ca;
+            if (sp >= kStackSize) { *err |= ERRBIT_TRAVERSAL; break; }
+            stack[sp++] = second;
+            next = first;
+        } else if (ha) next = ca;
+        else if (hb) next = cb;
+        if (next < 0) {
+            if (sp == 0) break;
+            next = stack[--sp];
+        }
+        node = next;
+        if (steps == kTraversalCap - 1) *err |= ERRBIT_TRAVERSAL;
+    }
+    *tout = bt;
+    *front = bdet > 0.0f;
+    return best;
+}
+
+// ----------------------------------------------------------------- map texels
+template <typename T> struct MapLoad;
+template <> struct MapLoad<float> {
+    __device__ static __forceinline__ void load(const void* base, size_t texel, float v[8]) {
+        const float4* p = reinterpret_cast<const float4*>(base) + 2 * texel;
+        float4 a = __ldg(p), b = __ldg(p + 1);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    }
+};
+template <> struct MapLoad<__nv_bfloat16> {
+    __device__ static __forceinline__ void load(const void* base, size_t texel, float v[8]) {
+        uint4 a = __ldg(reinterpret_cast<const uint4*>(base) + texel);
+        const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { float2 f = __bfloat1622float2(h[k]); v[2 * k] = f.x; v[2 * k + 1] = f.y; }
+    }
+};
+template <> struct MapLoad<__half> {
+    __device__ static __forceinline__ void load(const void* base, size_t texel, float v[8]) {
+        uint4 a = __ldg(reinterpret_cast<const uint4*>(base) + texel);
+        const __half2* h = reinterpret_cast<const __half2*>(&a);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) { float2 f = __half22float2(h[k]); v[2 * k] = f.x; v[2 * k + 1] = f.y; }
+    }
+};
+
+struct MapView {
+    const void* data;
+    int W, H;
+    bool wrap_u;
+};
+
+// Bilinear footprint: 4 texel indices and weights, plus d(weights)/d(fs, ft) data.
+struct Footprint {
+    uint32_t t[4];
+    float fs, ft;
+};
+
+__device__ __forceinline__ Footprint footprint(const MapView& m, float u, float v) {
+    Footprint f;
+    float s = u * (float)m.W - 0.5f, t = v * (float)m.H - 0.5f;
+    float i0f = floorf(s), j0f = floorf(t);
+    f.fs = s - i0f;
+    f.ft = t - j0f;
+    int i0 = (int)i0f, j0 = (int)j0f;
+    int c0, c1;
+    if (m.wrap_u) {
+        c0 = i0 % m.W; if (c0 < 0) c0 += m.W;
+        c1 = c0 + 1 == m.W ? 0 : c0 + 1;
+    } else {
+        c0 = min(max(i0, 0), m.W - 1);
+        c1 = min(max(i0 + 1, 0), m.W - 1);
+    }
+    int r0 = min(max(j0, 0), m.H - 1), r1 = min(max(j0 + 1, 0), m.H - 1);
+    f.t[0] = (uint32_t)r0 * m.W + c0;
+    f.t[1] = (uint32_t)r0 * m.W + c1;
+    f.t[2] = (uint32_t)r1 * m.W + c0;
+    f.t[3] = (uint32_t)r1 * m.W + c1;
+    return f;
+}
+
+// Footprint from texel-space coordinates s = u W - 1/2, t = v H - 1/2 held in FP64 (the
+// shading point's texel position keeps sub-1e-6-texel accuracy even on 4096^2 maps).
+__device__ __forceinline__ Footprint footprint_d(const MapView& m, double s, double t) {
+    Footprint f;
+    double i0d = floor(s), j0d = floor(t);
+    f.fs = (float)(s - i0d);
+    f.ft = (float)(t - j0d);
+    long long i0 = (long long)fmax(fmin(i0d, 1e15), -1e15), j0 = (long long)fmax(fmin(j0d, 1e15), -1e15);
+    int c0, c1;
+    if (m.wrap_u) {
+        long long w = i0 % m.W;
+        if (w < 0) w += m.W;
+        c0 = (int)w;
+        c1 = c0 + 1 == m.W ? 0 : c0 + 1;
+    } else {
+        c0 = (int)min(max(i0, 0ll), (long long)m.W - 1);
+        c1 = (int)min(max(i0 + 1, 0ll), (long long)m.W - 1);
+    }
+    int r0 = (int)min(max(j0, 0ll), (long long)m.H - 1), r1 = (int)min(max(j0 + 1, 0ll), (long long)m.H - 1);
+    f.t[0] = (uint32_t)r0 * m.W + c0;
+    f.t[1] = (uint32_t)r0 * m.W + c1;
+    f.t[2] = (uint32_t)r1 * m.W + c0;
+    f.t[3] = (uint32_t)r1 * m.W + c1;
+    return f;
+}
+
+// ------------------------------------------------- FP64 shading geometry (accuracy only)
+// Barycentrics of the shading point are evaluated in FP64: FP32 ray directions alone put
+// ~1e-5 relative error into the barycentrics of 0.01-unit triangles, which narrow GGX
+// lobes amplify ~50x into radiance.  No decision depends on these values.
+struct D3 { double x, y, z; };
+__device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y, z}; }
+__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
+    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ D3 dof(float3 a) { return d3(a.x, a.y, a.z); }
+
+// Moller-Trumbore barycentrics of the ray o + t d on (p0, p1, p2) in FP64.
+__device__ __forceinline__ void bary_d(D3 o, D3 d, D3 p0, D3 p1, D3 p2, double b[3]) {
+    D3 e1 = dsub(p1, p0), e2 = dsub(p2, p0);
+    D3 pv = dcross(d, e2);
+    double inv = 1.0 / ddot(e1, pv);
+    D3 s = dsub(o, p0);
+    double b1 = ddot(s, pv) * inv;
+    double b2 = ddot(d, dcross(s, e1)) * inv;
+    b[0] = 1.0 - b1 - b2; b[1] = b1; b[2] = b2;
+}
+
+template <typename T>
+__device__ __forceinline__ void fetch8(const MapView& m, const Footprint& f, float out[8], float dfs[8], float dft[8]) {
+    float a[8], b[8], c[8], d[8];
+    MapLoad<T>::load(m.data, f.t[0], a);
+    MapLoad<T>::load(m.data, f.t[1], b);
+    MapLoad<T>::load(m.data, f.t[2], c);
+    MapLoad<T>::load(m.data, f.t[3], d);
+    float w0 = (1.f - f.fs) * (1.f - f.ft), w1 = f.fs * (1.f - f.ft), w2 = (1.f - f.fs) * f.ft, w3 = f.fs * f.ft;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        out[k] = w0 * a[k] + w1 * b[k] + w2 * c[k] + w3 * d[k];
+        if (dfs) {
+            dfs[k] = (1.f - f.ft) * (b[k] - a[k]) + f.ft * (d[k] - c[k]);
+            dft[k] = (1.f - f.fs) * (c[k] - a[k]) + f.fs * (d[k] - b[k]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ small vectors
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 operator*(float3 a, float3 b) { return f3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float3& operator+=(float3& a, float3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+__device__ __forceinline__ float dot(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross(float3 a, float3 b) {
+    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float3 normalize(float3 a) { return rsqrtf(dot(a, a)) * a; }
+__device__ __forceinline__ float3 tof(S3 a) { return f3(a.x, a.y, a.z); }
+__device__ __forceinline__ float3 ld3(const float* p) { return f3(__ldg(p), __ldg(p + 1), __ldg(p + 2)); }
+
+}  // namespace exm

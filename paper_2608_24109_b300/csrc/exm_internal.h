@@ -1,0 +1,98 @@
+// Host-side internals of libexmesh: object layouts and kernel launchers shared by the
+// translation units.  Not part of the public ABI (include/exmesh.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/exmesh.h"
+
+struct exm_ctx {
+    int device = 0;
+    int num_sms = 0;
+    uint32_t* d_status = nullptr;  // latched device error bits
+};
+
+struct exm_mesh {
+    exm_ctx* ctx = nullptr;
+    int nv = 0, nf = 0, nuv = 0;
+    float* V = nullptr;        // [nv,3]
+    int32_t* F = nullptr;      // [nf,3]
+    float* UV = nullptr;       // [nuv,2]
+    int32_t* Fuv = nullptr;    // [nf,3]
+    float* nacc = nullptr;     // [nv,3] sum of incident face cross products
+    float* nrm = nullptr;      // [nv,3] unit vertex normals
+    float* tacc = nullptr;     // [nuv,3] sum of incident face tangents
+    float* tan = nullptr;      // [nuv,3] unit UV-vertex tangents
+    float* fsign = nullptr;    // [nf] UV handedness (+1 / -1)
+    // BVH
+    float4* nodes = nullptr;   // [max(nf-1,1) * 4]
+    float4* tris = nullptr;    // [nf * 3]
+    // build scratch
+    uint32_t* codes = nullptr;
+    uint32_t* codes_sorted = nullptr;
+    uint32_t* ids = nullptr;
+    uint32_t* ids_sorted = nullptr;
+    int32_t* parent = nullptr;     // [2nf-1]
+    int32_t* child = nullptr;      // [2*(nf-1)] encoded children
+    uint32_t* flags = nullptr;     // [nf-1]
+    float* bounds = nullptr;       // [(2nf-1) * 6]
+    float* scene_box = nullptr;    // [6] (ordered-int encoded min/max)
+    void* sort_tmp = nullptr;
+    size_t sort_tmp_bytes = 0;
+};
+
+struct exm_env {
+    exm_ctx* ctx = nullptr;
+    int W = 0, H = 0;
+    int gbits = 0;
+    float4* texel = nullptr;      // [H*W] E.rgb, (q/Q) W H / (2 pi^2)
+    uint32_t* q = nullptr;        // [H*W]
+    uint64_t* cdf = nullptr;      // [H*W] inclusive prefix, row-major
+    uint64_t* rowsum = nullptr;   // [H]
+    uint64_t* rowpre = nullptr;   // [H] exclusive prefix of the row sums
+    uint32_t* guide = nullptr;    // [2^gbits + 1]
+    float* wbuf = nullptr;        // [H*W] FP32 weights
+    uint32_t* wmax = nullptr;     // [1] max weight bits
+    uint64_t* total = nullptr;    // [1] Q on the device
+};
+
+struct exm_frame {
+    exm_ctx* ctx = nullptr;
+    int views = 0, W = 0, H = 0;
+    uint64_t* visbuf = nullptr;   // [views*H*W]
+    uint32_t* pixels = nullptr;   // [views*H*W] covered pixel ids (view*H*W + py*W + px)
+    uint32_t* counters = nullptr; // [0] covered count, [1] work cursor
+    unsigned long long* samples = nullptr;  // [1] shaded samples of the last forward
+    unsigned long long* work = nullptr;     // [4] work counters of the last counted pass
+    void* cams = nullptr;         // device copy of the cameras [views]
+    int32_t* XY = nullptr;        // [views*nv*2] snapped coordinates (sized on demand)
+    uint32_t* Zq = nullptr;       // [views*nv]
+    size_t snap_capacity = 0;     // vertices * views the snap buffers hold
+    float4* genv = nullptr;       // [envW*envH] env gradient accumulator (padded)
+    size_t genv_capacity = 0;
+    float4* gnrm = nullptr;       // [nv] vertex-normal adjoint
+    float4* gtan = nullptr;       // [nuv] tangent adjoint
+    size_t gframe_capacity = 0;
+};
+
+// error helpers (exm_api.cu)
+exm_status exm_fail(exm_status code, const std::string& msg);
+exm_status exm_cuda_check(cudaError_t e, const char* what);
+
+// kernels launchers
+exm_status exm_frames_build(exm_mesh* m, cudaStream_t s);
+exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s);
+exm_status exm_env_prepare_impl(exm_env* e, const void* E, exm_dtype dt, cudaStream_t s);
+exm_status exm_raster_impl(exm_ctx* ctx, const exm_mesh* m, exm_frame* f, int views, cudaStream_t s);
+exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW,
+                                  int mapH, const exm_env* e, exm_frame* f, const exm_params* p, float* out,
+                                  cudaStream_t s);
+exm_status exm_frames_adjoint(exm_mesh* m, float4* gn, float4* gt, float* gV, cudaStream_t s);
+exm_status exm_shade_backward_impl(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW,
+                                   int mapH, const exm_env* e, exm_frame* f, const exm_params* p,
+                                   const float* grad_rgb, float* grad_maps, float* grad_env, float* grad_V,
+                                   cudaStream_t s);
+
+inline int exm_blocks(size_t n, int threads) { return (int)((n + threads - 1) / threads); }

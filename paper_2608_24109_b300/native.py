@@ -1,0 +1,238 @@
+"""ctypes binding of libexmesh (include/exmesh.h): argument marshalling only.
+
+Every entry point keeps its C name.  Device buffers are torch CUDA tensors (their
+data_ptr() is passed); streams are torch.cuda streams (their cuda_stream handle).  The
+library is loaded from this package's directory; if it is missing the import fails
+loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libexmesh.so")
+
+EXM_OK = 0
+EXM_ERR_ARG = -1
+EXM_ERR_OOM = -2
+EXM_ERR_CUDA = -3
+EXM_ERR_GUARDBAND = -4
+EXM_ERR_TRAVERSAL_LIMIT = -5
+EXM_ERR_TIMEOUT = -6
+EXM_ERR_BUSY = -7
+
+EXM_F32, EXM_BF16, EXM_F16 = 0, 1, 2
+FLAG_WRAP_U = 1
+FLAG_NO_METALLIC = 2
+FLAG_COUNT_WORK = 4
+FLAG_ZERO_GRADS = 8
+
+EXPORTS = [
+    "exm_create", "exm_destroy", "exm_last_error", "exm_sync",
+    "exm_mesh_create", "exm_mesh_update_vertices", "exm_bvh_build", "exm_mesh_destroy", "exm_mesh_frames",
+    "exm_env_create", "exm_env_prepare", "exm_env_destroy", "exm_env_total",
+    "exm_frame_create", "exm_frame_destroy", "exm_frame_stats", "exm_frame_work", "exm_frame_visbuf",
+    "exm_render_forward", "exm_render_backward", "exm_l1_loss",
+]
+
+
+class ExmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libexmesh error {code}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("n_direct", ctypes.c_int32), ("n_bounce", ctypes.c_int32), ("n_light", ctypes.c_int32),
+                ("lambda_ind", ctypes.c_float), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libexmesh.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libexmesh.so is not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "exm_create": ([I, PP], I),
+        "exm_destroy": ([P], None),
+        "exm_last_error": ([], ctypes.c_char_p),
+        "exm_sync": ([P, P], I),
+        "exm_mesh_create": ([P, P, I, P, I, P, I, P, P, PP], I),
+        "exm_mesh_update_vertices": ([P, P, P], I),
+        "exm_bvh_build": ([P, P], I),
+        "exm_mesh_destroy": ([P], None),
+        "exm_mesh_frames": ([P, PP, PP], I),
+        "exm_env_create": ([P, I, I, PP], I),
+        "exm_env_prepare": ([P, P, I, P], I),
+        "exm_env_destroy": ([P], None),
+        "exm_env_total": ([P, ctypes.POINTER(U64)], I),
+        "exm_frame_create": ([P, I, I, I, PP], I),
+        "exm_frame_destroy": ([P], None),
+        "exm_frame_stats": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
+        "exm_frame_work": ([P, ctypes.POINTER(U64 * 4)], I),
+        "exm_frame_visbuf": ([P, PP], I),
+        "exm_render_forward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P], I),
+        "exm_render_backward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
+        "exm_l1_loss": ([P, P, I64, P, P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def check(code):
+    if code != EXM_OK:
+        raise ExmError(code, lib().exm_last_error().decode(errors="replace"))
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def dtype_code(dt):
+    import torch
+    return {torch.float32: EXM_F32, torch.bfloat16: EXM_BF16, torch.float16: EXM_F16}[dt]
+
+
+def _cams(cams):
+    a = np.ascontiguousarray(cams, dtype=np.float32)
+    assert a.ndim == 2 and a.shape[1] == 20, "cameras: float32 [views, 20]"
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ------------------------------------------------------------------ entry points
+
+def exm_create(device: int = 0):
+    h = ctypes.c_void_p()
+    check(lib().exm_create(device, ctypes.byref(h)))
+    return h
+
+
+def exm_destroy(ctx):
+    lib().exm_destroy(ctx)
+
+
+def exm_sync(ctx, stream=None):
+    return check(lib().exm_sync(ctx, _stream(stream)))
+
+
+def exm_mesh_create(ctx, V, F, UV, Fuv, stream=None):
+    for t, n in ((V, "V"), (F, "F"), (UV, "UV"), (Fuv, "Fuv")):
+        assert t.is_cuda and t.is_contiguous(), f"{n} must be a contiguous CUDA tensor"
+    h = ctypes.c_void_p()
+    check(lib().exm_mesh_create(ctx, _ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(UV), UV.shape[0], _ptr(Fuv),
+                                _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def exm_mesh_update_vertices(mesh, V, stream=None):
+    return check(lib().exm_mesh_update_vertices(mesh, _ptr(V), _stream(stream)))
+
+
+def exm_bvh_build(mesh, stream=None):
+    return check(lib().exm_bvh_build(mesh, _stream(stream)))
+
+
+def exm_mesh_destroy(mesh):
+    lib().exm_mesh_destroy(mesh)
+
+
+def exm_mesh_frames(mesh):
+    n, t = ctypes.c_void_p(), ctypes.c_void_p()
+    check(lib().exm_mesh_frames(mesh, ctypes.byref(n), ctypes.byref(t)))
+    return n.value, t.value
+
+
+def exm_env_create(ctx, W, H):
+    h = ctypes.c_void_p()
+    check(lib().exm_env_create(ctx, W, H, ctypes.byref(h)))
+    return h
+
+
+def exm_env_prepare(env, E, stream=None):
+    assert E.is_cuda and E.is_contiguous()
+    return check(lib().exm_env_prepare(env, _ptr(E), dtype_code(E.dtype), _stream(stream)))
+
+
+def exm_env_destroy(env):
+    lib().exm_env_destroy(env)
+
+
+def exm_env_total(env):
+    q = ctypes.c_uint64()
+    check(lib().exm_env_total(env, ctypes.byref(q)))
+    return q.value
+
+
+def exm_frame_create(ctx, views, W, H):
+    h = ctypes.c_void_p()
+    check(lib().exm_frame_create(ctx, views, W, H, ctypes.byref(h)))
+    return h
+
+
+def exm_frame_destroy(frame):
+    lib().exm_frame_destroy(frame)
+
+
+def exm_frame_stats(frame):
+    c, s = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().exm_frame_stats(frame, ctypes.byref(c), ctypes.byref(s)))
+    return c.value, s.value
+
+
+def exm_frame_work(frame):
+    c = (ctypes.c_uint64 * 4)()
+    check(lib().exm_frame_work(frame, ctypes.byref(c)))
+    return list(c)
+
+
+def exm_frame_visbuf(frame):
+    p = ctypes.c_void_p()
+    check(lib().exm_frame_visbuf(frame, ctypes.byref(p)))
+    return p.value
+
+
+def exm_render_forward(ctx, mesh, maps, env, cams, params: Params, frame, out, stream=None):
+    a, cp = _cams(cams)
+    assert maps.is_cuda and maps.is_contiguous() and maps.shape[-1] == 8
+    return check(lib().exm_render_forward(ctx, mesh, _ptr(maps), dtype_code(maps.dtype), maps.shape[1], maps.shape[0],
+                                          env, cp, a.shape[0], ctypes.byref(params), frame, _ptr(out),
+                                          _stream(stream)))
+
+
+def exm_render_backward(ctx, mesh, maps, env, cams, params: Params, frame, grad_rgb, grad_maps=None, grad_env=None,
+                        grad_V=None, stream=None):
+    a, cp = _cams(cams)
+    return check(lib().exm_render_backward(ctx, mesh, _ptr(maps), dtype_code(maps.dtype), maps.shape[1],
+                                           maps.shape[0], env, cp, a.shape[0], ctypes.byref(params), frame,
+                                           _ptr(grad_rgb), _ptr(grad_maps), _ptr(grad_env), _ptr(grad_V),
+                                           _stream(stream)))
+
+
+def exm_l1_loss(pred, target, loss, grad, stream=None):
+    return check(lib().exm_l1_loss(_ptr(pred), _ptr(target), pred.numel(), _ptr(loss), _ptr(grad), _stream(stream)))

@@ -1,0 +1,320 @@
+"""GPU path (libexmesh through its C ABI) against the CPU oracle, element by element.
+
+Bars (spec tolerances): visibility-buffer keys bit-exact; radiance per pixel
+|g - o| <= 1e-4 * max(|o|, 1e-3 * mean(o)); gradients ||g - o|| / ||o|| <= 1e-3 per tensor.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import shade
+from paper_2608_24109_b300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+RAD_TOL = 1e-4
+GRAD_TOL = 1e-3
+
+
+def _renderer(sc, **kw):
+    from paper_2608_24109_b300.render import Renderer
+    return Renderer.from_scene(sc, **kw)
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def check_radiance(g, o, what=""):
+    g = np.asarray(g, np.float64)
+    o = np.asarray(o, np.float64)
+    mean = np.abs(o).mean()
+    tol = RAD_TOL * np.maximum(np.abs(o), 1e-3 * mean)
+    err = np.abs(g - o)
+    bad = err > tol
+    assert not bad.any(), f"{what}: {bad.sum()} of {bad.size} values outside tolerance; worst rel " \
+                          f"{(err / np.maximum(np.abs(o), 1e-3 * mean)).max():.3e}"
+
+
+def check_grad(g, o, what):
+    g = np.asarray(g, np.float64).ravel()
+    o = np.asarray(o, np.float64).ravel()
+    rel = np.linalg.norm(g - o) / max(np.linalg.norm(o), 1e-30)
+    assert rel <= GRAD_TOL, f"{what}: relative L2 error {rel:.3e}"
+
+
+def keys_u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def ragged_tiny(W=97, H=61, views=2, n_direct=64, **kw):
+    sc = scenes.config("tiny", n_direct=n_direct, **kw)
+    cams = np.stack([scenes.look_at_camera(c[0:3], W, H) for c in sc.cams[:views]])
+    sc.cams, sc.width, sc.height = cams, W, H
+    return sc
+
+
+def small_cavity(res=64, views=2, n=24, n_direct=16, n_bounce=8, n_light=4):
+    sc = scenes.config("indirect", n=n, map_res=128, env_w=64, env_h=32, views=views, res=res, n_direct=n_direct,
+                       n_bounce=n_bounce, n_light=n_light)
+    return sc
+
+
+def gpu_forward(sc, maps=None, env=None, **kw):
+    r = _renderer(sc, **kw)
+    M = _dev(sc.maps if maps is None else maps)
+    E = _dev(sc.env if env is None else env)
+    out = r.forward(M, E)
+    r.sync()
+    return r, M, E, out
+
+
+def oracle_full(sc, maps=None):
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, sc.width, sc.height)
+    assert st == 0
+    pix = oracle.covered_pixels(keys)
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, pix, keys[pix[:, 0], pix[:, 1], pix[:, 2]])
+    V, M, E = shade.scene_tensors(sc)
+    if maps is not None:
+        M = torch.as_tensor(maps, dtype=torch.float64)
+    return keys, tab, dec, V, M, E
+
+
+# ----------------------------------------------------------------- visibility
+
+@pytest.mark.parametrize("size", [(256, 256, 4), (97, 61, 2), (33, 200, 1)])
+def test_visibility_buffer_bit_exact(size):
+    W, H, views = size
+    sc = ragged_tiny(W, H, views)
+    r, M, E, out = gpu_forward(sc)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, W, H)
+    assert st == 0
+    got = keys_u64(r.visbuf())
+    assert np.array_equal(got, keys)
+    cov, samples = r.stats()
+    assert cov == int(((keys & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)).sum())
+    assert samples == cov * sc.n_direct
+
+
+def test_visibility_buffer_bit_exact_blob():
+    sc = scenes.config("geometry", views=3, res=160)
+    r, M, E, out = gpu_forward(sc)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, sc.width, sc.height)
+    assert np.array_equal(keys_u64(r.visbuf()), keys)
+
+
+def test_env_distribution_total_matches():
+    from paper_2608_24109_b300 import native as N
+    for (w, h, sig) in [(64, 32, 1.0), (256, 128, 1.5), (13, 7, 2.0)]:
+        env = scenes.env_map(np.random.default_rng(w), w, h, sig)
+        sc = scenes.config("tiny", res=32, views=1, env_w=w, env_h=h)
+        sc.env = env
+        r = _renderer(sc)
+        r.prepare_env(_dev(env))
+        r.sync()
+        assert N.exm_env_total(r.env) == oracle.EnvTable(env).Q
+
+
+# ----------------------------------------------------------------- radiance
+
+def test_forward_parity_tiny_ragged_full_frame():
+    sc = ragged_tiny(97, 61, 2)
+    r, M, E, out = gpu_forward(sc)
+    keys, tab, dec, V, Mo, Eo = oracle_full(sc)
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    g = out.cpu().numpy()[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]]
+    check_radiance(g, I, "tiny ragged")
+    # background stays exactly zero
+    bg = np.ones(g.shape[:0] + out.shape[:3], bool)
+    bg[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]] = False
+    assert (out.cpu().numpy()[bg] == 0).all()
+
+
+def test_forward_parity_tiny_full_size_sampled():
+    sc = scenes.config("tiny")
+    r, M, E, out = gpu_forward(sc)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, sc.width, sc.height)
+    pix = oracle.covered_pixels(keys)
+    sel = pix[np.random.default_rng(0).choice(pix.shape[0], 3000, replace=False)]
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, sel, keys[sel[:, 0], sel[:, 1], sel[:, 2]])
+    V, Mo, Eo = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    g = out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]]
+    check_radiance(g, I, "tiny full-size sample")
+
+
+def test_forward_is_deterministic():
+    sc = ragged_tiny(64, 64, 2)
+    r, M, E, out = gpu_forward(sc)
+    out2 = r.forward(M, E)
+    r.sync()
+    assert torch.equal(out, out2)
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_forward_parity_low_precision_maps(dtype):
+    sc = ragged_tiny(80, 72, 1)
+    Mq = torch.as_tensor(sc.maps).to(dtype)
+    r = _renderer(sc)
+    out = r.forward(Mq.cuda().contiguous(), _dev(sc.env))
+    r.sync()
+    keys, tab, dec, V, Mo, Eo = oracle_full(sc, maps=Mq.to(torch.float64).numpy())
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    check_radiance(out.cpu().numpy()[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]], I, str(dtype))
+
+
+def test_forward_parity_indirect_full_frame():
+    sc = small_cavity()
+    r, M, E, out = gpu_forward(sc)
+    keys, tab, dec, V, Mo, Eo = oracle_full(sc)
+    assert np.array_equal(keys_u64(r.visbuf()), keys)
+    assert (dec.stri >= 0).sum() > 100
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    g = out.cpu().numpy()[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]]
+    check_radiance(g, I, "cavity indirect")
+
+
+def test_no_metallic_flag():
+    sc = ragged_tiny(48, 40, 1)
+    sc.metallic = False
+    r, M, E, out = gpu_forward(sc)
+    keys, tab, dec, V, Mo, Eo = oracle_full(sc)
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    check_radiance(out.cpu().numpy()[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]], I, "dielectric")
+
+
+# ----------------------------------------------------------------- gradients
+
+def _grad_compare(sc, npix, seed=0, subset=True):
+    r, M, E, out = gpu_forward(sc)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, sc.width, sc.height)
+    pix = oracle.covered_pixels(keys)
+    rng = np.random.default_rng(seed)
+    sel = pix[rng.choice(pix.shape[0], min(npix, pix.shape[0]), replace=False)] if subset else pix
+    g = rng.normal(size=(sel.shape[0], 3))
+    grad = np.zeros(out.shape, np.float32)
+    grad[sel[:, 0], sel[:, 1], sel[:, 2]] = g
+    gm = torch.zeros_like(M)
+    gE = torch.zeros_like(E)
+    gV = torch.zeros((sc.V.shape[0], 3), dtype=torch.float32, device="cuda")
+    r.backward(M, _dev(grad), gm, gE, gV)
+    r.sync()
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, sel, keys[sel[:, 0], sel[:, 1], sel[:, 2]])
+    V, Mo, Eo = shade.scene_tensors(sc)
+    oV, oM, oE = shade.backward(sc, tab, dec, V, Mo, Eo, grad[sel[:, 0], sel[:, 1], sel[:, 2]].astype(np.float64))
+    check_grad(gm.cpu().numpy(), oM.numpy(), "dL/dmaps")
+    check_grad(gE.cpu().numpy(), oE.numpy(), "dL/dE")
+    check_grad(gV.cpu().numpy(), oV.numpy(), "dL/dV")
+    return r
+
+
+def test_backward_parity_tiny():
+    _grad_compare(ragged_tiny(96, 80, 2), 4000)
+
+
+def test_backward_parity_tiny_all_pixels():
+    _grad_compare(ragged_tiny(64, 48, 1), 0, subset=False)
+
+
+def test_backward_parity_indirect():
+    _grad_compare(small_cavity(res=48, views=1), 0, subset=False)
+
+
+def test_autograd_function_matches_direct_backward():
+    sc = ragged_tiny(64, 64, 1)
+    r = _renderer(sc)
+    M = _dev(sc.maps).requires_grad_(True)
+    E = _dev(sc.env).requires_grad_(True)
+    V = _dev(sc.V).requires_grad_(True)
+    img = r.render(M, E, V)
+    w = torch.randn_like(img)
+    (img * w).sum().backward()
+    gm, gE, gV = torch.zeros_like(M), torch.zeros_like(E), torch.zeros_like(V)
+    r.forward(M.detach(), E.detach())
+    r.backward(M.detach(), w, gm, gE, gV)
+    r.sync()
+    assert torch.allclose(M.grad, gm, rtol=1e-4, atol=1e-6)
+    assert torch.allclose(E.grad, gE, rtol=1e-4, atol=1e-6)
+    assert torch.allclose(V.grad, gV, rtol=1e-3, atol=1e-5)
+
+
+def test_l1_loss():
+    from paper_2608_24109_b300 import native as N
+    a = torch.randn(1000003, device="cuda")
+    b = torch.randn(1000003, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.empty_like(a)
+    N.exm_l1_loss(a, b, loss, grad)
+    torch.cuda.synchronize()
+    ref = (a - b).abs().double().mean().item()
+    assert abs(loss.item() - ref) < 1e-5 * ref
+    assert torch.equal(grad, torch.sign(a - b) / a.numel())
+
+
+# ----------------------------------------------------------------- full-size configs, sampled
+
+def test_geometry_config_sampled():
+    sc = scenes.config("geometry")
+    r, M, E, out = gpu_forward(sc)
+    vis = keys_u64(r.visbuf())
+    covered = np.argwhere((vis & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)).astype(np.int32)
+    rng = np.random.default_rng(1)
+    sel = covered[rng.choice(covered.shape[0], 48, replace=False)]
+    # a few uncovered pixels and silhouette neighbours too
+    st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, sel)
+    assert np.array_equal(keys, vis[sel[:, 0], sel[:, 1], sel[:, 2]])
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, sel, keys)
+    V, Mo, Eo = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    check_radiance(out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]], I, "geometry config")
+
+
+def test_indirect_config_sampled():
+    sc = scenes.config("indirect")
+    r, M, E, out = gpu_forward(sc)
+    vis = keys_u64(r.visbuf())
+    covered = np.argwhere((vis & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)).astype(np.int32)
+    rng = np.random.default_rng(2)
+    sel = covered[rng.choice(covered.shape[0], 24, replace=False)]
+    st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, sel)
+    assert np.array_equal(keys, vis[sel[:, 0], sel[:, 1], sel[:, 2]])
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, sel, keys)
+    V, Mo, Eo = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    check_radiance(out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]], I, "indirect config")
+
+
+# ----------------------------------------------------------------- errors
+
+def test_argument_errors_are_reported():
+    from paper_2608_24109_b300 import native as N
+    sc = ragged_tiny(32, 32, 1)
+    r = _renderer(sc)
+    out = torch.empty(r.image_shape(), device="cuda")
+    bad = N.Params(n_direct=0, n_bounce=0, n_light=0, lambda_ind=1.0, flags=0, reserved=0, seed=0)
+    with pytest.raises(N.ExmError) as e:
+        N.exm_render_forward(r.ctx, r.mesh, _dev(sc.maps), r.env, sc.cams, bad, r.frame, out)
+    assert e.value.code == N.EXM_ERR_ARG
+    with pytest.raises(N.ExmError):
+        N.exm_render_forward(r.ctx, r.mesh, _dev(sc.maps), r.env, np.concatenate([sc.cams, sc.cams]), r.params,
+                             r.frame, out)
+
+
+def test_guard_band_error_from_device():
+    from paper_2608_24109_b300 import native as N
+    sc = ragged_tiny(32, 32, 1)
+    sc.cams[0, 0:3] = [0.0, 0.0, 0.9]
+    r = _renderer(sc)
+    r.forward(_dev(sc.maps), _dev(sc.env))
+    with pytest.raises(N.ExmError) as e:
+        r.sync()
+    assert e.value.code == N.EXM_ERR_GUARDBAND
+    r.sync()  # latched error was cleared
