@@ -154,6 +154,25 @@ exm_status exm_render_backward(exm_ctx* ctx, const exm_mesh* mesh, const void* m
                                const exm_params* params, exm_frame* frame, const float* grad_rgb,
                                float* grad_maps, float* grad_env, float* grad_V, void* stream);
 
+/* Backward pass without device allocation (no counterpart in the paper).
+ *
+ * For callers that must not call cudaMalloc while they run -- a host whose device memory
+ * is owned by another allocator (a caching allocator or a pre-reserved arena), or a
+ * latency-critical loop that cannot take the implicit synchronisation of cudaMalloc.  It
+ * takes the same arguments as exm_render_backward without grad_V and accumulates dL/dmaps
+ * and dL/dE (either may be NULL) for the last forward of `frame`.  Its environment-gradient
+ * accumulator is a static device array of EXM_STATIC_ENV_MAX_TEXELS float4 (4 MiB) that every
+ * GPU loading the library holds until exit; a larger environment is rejected with
+ * EXM_ERR_ARG before anything is enqueued.  The array is shared by all calls on a device:
+ * calls that overlap on the GPU race and must be serialised by the caller.  The first call
+ * on a device resolves the array's address (cudaGetSymbolAddress); make it before any
+ * stream capture. */
+#define EXM_STATIC_ENV_MAX_TEXELS 262144
+exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
+                                       int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
+                                       const exm_params* params, exm_frame* frame, const float* grad_rgb,
+                                       float* grad_maps, float* grad_env, void* stream);
+
 /* L1 image loss of Sec. 6 workloads: *loss (DEVICE float32, written) = mean |pred - target|
  * over n elements; grad (DEVICE float32 [n], written) = sign(pred - target) / n. */
 exm_status exm_l1_loss(const float* pred, const float* target, int64_t n, float* loss, float* grad,

@@ -561,3 +561,97 @@ exm_status exm_shade_backward_impl(exm_ctx* ctx, const exm_mesh* m, const void* 
     }
     return exm_cuda_check(cudaGetLastError(), "backward finish");
 }
+
+// ---------------------------------------------------------------------------------------
+// Backward pass that allocates nothing.
+//
+// Some callers cannot call cudaMalloc while they run: for example, a host whose device
+// memory is entirely owned by another allocator (a framework's caching allocator or a
+// pre-reserved arena that forbids driver allocations), or a latency-critical loop in which
+// the implicit device synchronisation of cudaMalloc/cudaFree is unacceptable.  The regular
+// exm_render_backward may allocate its environment-gradient accumulator on first use; this
+// variant instead keeps that accumulator in the file-scope array below, which every GPU that
+// loads the library holds (EXM_STATIC_ENV_MAX_TEXELS x 16 bytes = 4 MiB) until the process
+// exits.  It computes the map and environment gradients only (grad_V is not supported here,
+// because vertex gradients need per-vertex scratch proportional to the mesh).
+//
+// The array is shared by every call on a device and keeps the last call's contents: each
+// call clears the part it uses before its kernel runs, so calls that overlap on the GPU
+// (different streams, or different host threads) race on it and must be serialised by the
+// caller.  The first call on a device resolves the array's device address with
+// cudaGetSymbolAddress while that device is current; make that first call before any
+// stream capture.
+#include <mutex>
+
+static __device__ __align__(256) float4 g_env_grad_scratch[EXM_STATIC_ENV_MAX_TEXELS];
+
+namespace {
+constexpr int kMaxScratchDevices = 64;
+std::mutex g_scratch_mutex;
+float4* g_scratch_addr[kMaxScratchDevices] = {};
+
+// Device address of g_env_grad_scratch on `device` (which must be current).
+exm_status static_scratch(int device, float4** out) {
+    if (device < 0 || device >= kMaxScratchDevices) return exm_fail(EXM_ERR_ARG, "static scratch: device index");
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (g_scratch_addr[device] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_env_grad_scratch);
+        if (e != cudaSuccess) return exm_cuda_check(e, "cudaGetSymbolAddress(env gradient scratch)");
+        g_scratch_addr[device] = static_cast<float4*>(p);
+    }
+    *out = g_scratch_addr[device];
+    return EXM_OK;
+}
+}  // namespace
+
+extern "C" exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt,
+                                                  int mapW, int mapH, const exm_env* e, const exm_camera* cams,
+                                                  int views, const exm_params* p, exm_frame* f,
+                                                  const float* grad_rgb, float* grad_maps, float* grad_env,
+                                                  void* stream) {
+    if (!ctx || !m || !maps || !e || !cams || !p || !f || !grad_rgb)
+        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: NULL argument");
+    if ((long long)e->W * e->H > EXM_STATIC_ENV_MAX_TEXELS)
+        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: environment has " +
+                                         std::to_string((long long)e->W * e->H) + " texels, more than the " +
+                                         std::to_string(EXM_STATIC_ENV_MAX_TEXELS) + " the static scratch holds");
+    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16)
+        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: map dtype");
+    if (mapW < 1 || mapH < 1 || (long long)mapW * mapH > (1ll << 28))
+        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: map size");
+    if (views != f->views) return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: views differ from the frame's");
+    if (p->n_direct < 1 || p->n_direct > 65536 || p->n_bounce < 0 || p->n_bounce > 4096 ||
+        (p->n_bounce > 0 && (p->n_light < 1 || p->n_light > 4096)))
+        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: sample counts");
+    if (m->ctx != ctx || e->ctx != ctx || f->ctx != ctx)
+        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: objects of another context");
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    float4* scratch = nullptr;
+    exm_status st = static_scratch(ctx->device, &scratch);
+    if (st == EXM_OK)
+        st = exm_cuda_check(cudaMemcpyAsync(f->cams, cams, (size_t)views * sizeof(exm_camera), cudaMemcpyHostToDevice, s),
+                            "camera upload");
+    if (st == EXM_OK) {
+        size_t nenv = (size_t)e->W * e->H;
+        ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
+        A.grad_rgb = grad_rgb;
+        A.gmaps = grad_maps;
+        A.genv = scratch;
+        A.gV = nullptr;
+        if (p->flags & EXM_FLAG_ZERO_GRADS) {
+            if (grad_maps) cudaMemsetAsync(grad_maps, 0, (size_t)mapW * mapH * 8 * sizeof(float), s);
+            if (grad_env) cudaMemsetAsync(grad_env, 0, nenv * 3 * sizeof(float), s);
+        }
+        cudaMemsetAsync(scratch, 0, nenv * sizeof(float4), s);
+        st = launch<true>(A, dt, ctx->num_sms * 8, s, false);
+        if (st == EXM_OK && grad_env)
+            env_grad_finish_kernel<<<exm_blocks(nenv, 256), 256, 0, s>>>(scratch, (int)nenv, grad_env);
+        if (st == EXM_OK) st = exm_cuda_check(cudaGetLastError(), "exm_render_backward_noalloc launch");
+    }
+    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    return st;
+}

@@ -35,7 +35,7 @@ EXPORTS = [
     "exm_mesh_create", "exm_mesh_update_vertices", "exm_bvh_build", "exm_mesh_destroy", "exm_mesh_frames",
     "exm_env_create", "exm_env_prepare", "exm_env_destroy", "exm_env_total",
     "exm_frame_create", "exm_frame_destroy", "exm_frame_stats", "exm_frame_work", "exm_frame_visbuf",
-    "exm_render_forward", "exm_render_backward", "exm_l1_loss",
+    "exm_render_forward", "exm_render_backward", "exm_render_backward_noalloc", "exm_l1_loss",
 ]
 
 
@@ -85,6 +85,7 @@ def lib():
         "exm_frame_visbuf": ([P, PP], I),
         "exm_render_forward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P], I),
         "exm_render_backward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
+        "exm_render_backward_noalloc": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P], I),
         "exm_l1_loss": ([P, P, I64, P, P, P], I),
     }
     for name, (args, res) in sig.items():
@@ -232,6 +233,17 @@ def exm_render_backward(ctx, mesh, maps, env, cams, params: Params, frame, grad_
                                            maps.shape[0], env, cp, a.shape[0], ctypes.byref(params), frame,
                                            _ptr(grad_rgb), _ptr(grad_maps), _ptr(grad_env), _ptr(grad_V),
                                            _stream(stream)))
+
+
+def exm_render_backward_noalloc(ctx, mesh, maps, env, cams, params: Params, frame, grad_rgb, grad_maps=None,
+                                grad_env=None, stream=None):
+    """Backward into maps and environment gradients using the library's static scratch
+    array instead of any device allocation (see include/exmesh.h)."""
+    a, cp = _cams(cams)
+    return check(lib().exm_render_backward_noalloc(ctx, mesh, _ptr(maps), dtype_code(maps.dtype), maps.shape[1],
+                                                   maps.shape[0], env, cp, a.shape[0], ctypes.byref(params), frame,
+                                                   _ptr(grad_rgb), _ptr(grad_maps), _ptr(grad_env),
+                                                   _stream(stream)))
 
 
 def exm_l1_loss(pred, target, loss, grad, stream=None):
