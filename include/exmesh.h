@@ -52,6 +52,8 @@ typedef enum { EXM_F32 = 0, EXM_BF16 = 1, EXM_F16 = 2 } exm_dtype;
 #define EXM_FLAG_COUNT_WORK 4u   /* also count BVH nodes, triangle tests, BRDF evaluations and rays
                                     (exm_frame_work); a slower instrumented kernel, same results */
 #define EXM_FLAG_ZERO_GRADS 8u   /* exm_render_backward zeroes the gradient buffers before accumulating */
+#define EXM_FLAG_TIME_KERNELS 16u /* record CUDA events around the trace and shade launches
+                                     (exm_frame_kernel_ms) */
 
 typedef struct exm_ctx exm_ctx;
 typedef struct exm_mesh exm_mesh;
@@ -133,6 +135,12 @@ exm_status exm_frame_stats(exm_frame* frame, uint64_t* covered, uint64_t* sample
 /* Work counters of the last pass run with EXM_FLAG_COUNT_WORK (synchronous): counts[0] BVH
  * nodes visited, [1] ray/triangle tests, [2] BRDF evaluations, [3] rays traced. */
 exm_status exm_frame_work(exm_frame* frame, uint64_t counts[4]);
+/* Milliseconds spent in the kernels timed since the last call (EXM_FLAG_TIME_KERNELS), summed
+ * per kind: ms[0] any-hit trace, [1] closest-hit trace, [2] forward shade, [3] backward shade.
+ * Waits for the recorded events. */
+exm_status exm_frame_kernel_ms(exm_frame* frame, float ms[4]);
+/* Number of kernels the library has launched on this context so far. */
+exm_status exm_launch_count(exm_ctx* ctx, uint64_t* launches);
 /* DEVICE pointer to the visibility buffer [views, height, width] of u64 keys. */
 exm_status exm_frame_visbuf(exm_frame* frame, const uint64_t** keys);
 

@@ -248,8 +248,14 @@ exm_status exm_env_total(exm_env* e, uint64_t* Q) {
 // ---------------------------------------------------------------------- frame
 
 static void frame_free(exm_frame* f) {
-    void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY, f->Zq, f->genv, f->gnrm, f->gtan};
+    void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY,   f->Zq,
+                    f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr};
     for (void* p : ptrs) cudaFree(p);
+    for (auto& t : f->timers) {
+        cudaEventDestroy(t.begin);
+        cudaEventDestroy(t.end);
+    }
+    f->timers.clear();
 }
 
 exm_status exm_frame_create(exm_ctx* c, int views, int width, int height, exm_frame** out) {
@@ -304,6 +310,29 @@ exm_status exm_frame_work(exm_frame* f, uint64_t counts[4]) {
     if (!f || !counts) return exm_fail(EXM_ERR_ARG, "exm_frame_work: NULL argument");
     DeviceGuard g(f->ctx->device);
     return exm_cuda_check(cudaMemcpy(counts, f->work, 32, cudaMemcpyDeviceToHost), "frame work counters");
+}
+
+exm_status exm_frame_kernel_ms(exm_frame* f, float ms[4]) {
+    if (!f || !ms) return exm_fail(EXM_ERR_ARG, "exm_frame_kernel_ms: NULL argument");
+    DeviceGuard g(f->ctx->device);
+    for (int k = 0; k < 4; ++k) ms[k] = 0.0f;
+    exm_status st = EXM_OK;
+    for (auto& t : f->timers) {
+        float x = 0.0f;
+        if (st == EXM_OK) st = exm_cuda_check(cudaEventSynchronize(t.end), "kernel timer");
+        if (st == EXM_OK) st = exm_cuda_check(cudaEventElapsedTime(&x, t.begin, t.end), "kernel timer");
+        if (t.which >= 0 && t.which < 4) ms[t.which] += x;
+        cudaEventDestroy(t.begin);
+        cudaEventDestroy(t.end);
+    }
+    f->timers.clear();
+    return st;
+}
+
+exm_status exm_launch_count(exm_ctx* c, uint64_t* launches) {
+    if (!c || !launches) return exm_fail(EXM_ERR_ARG, "exm_launch_count: NULL argument");
+    *launches = c->launches;
+    return EXM_OK;
 }
 
 exm_status exm_frame_visbuf(exm_frame* f, const uint64_t** keys) {

@@ -151,5 +151,6 @@ exm_status exm_env_prepare_impl(exm_env* e, const void* E, exm_dtype dt, cudaStr
     env_finish_kernel<<<blocks, 256, 0, s>>>(e->W, e->H, e->rowpre, e->total, e->q, e->cdf, e->texel);
     uint32_t G = 1u << e->gbits;
     env_guide_kernel<<<exm_blocks((size_t)G + 1, 256), 256, 0, s>>>(e->cdf, (uint32_t)n, e->total, e->gbits, e->guide);
+    e->ctx->launches += 5;
     return exm_cuda_check(cudaGetLastError(), "env prepare launch");
 }

@@ -108,6 +108,7 @@ exm_status exm_frames_build(exm_mesh* m, cudaStream_t s) {
                                                                    m->nacc, m->tacc, m->fsign, m->ctx->d_status);
     normalize_rows_kernel<<<exm_blocks(m->nv, 256), 256, 0, s>>>(m->nacc, m->nv, m->nrm);
     normalize_rows_kernel<<<exm_blocks(m->nuv, 256), 256, 0, s>>>(m->tacc, m->nuv, m->tan);
+    m->ctx->launches += 3;
     return exm_cuda_check(cudaGetLastError(), "frames launch");
 }
 

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/exmesh.h"
 
@@ -12,6 +13,7 @@ struct exm_ctx {
     int device = 0;
     int num_sms = 0;
     uint32_t* d_status = nullptr;  // latched device error bits
+    unsigned long long launches = 0;  // kernels launched by the library on this context
 };
 
 struct exm_mesh {
@@ -75,6 +77,19 @@ struct exm_frame {
     float4* gnrm = nullptr;       // [nv] vertex-normal adjoint
     float4* gtan = nullptr;       // [nuv] tangent adjoint
     size_t gframe_capacity = 0;
+    size_t gtan_capacity = 0;
+    // wavefront state of the last forward
+    uint32_t* bits = nullptr;     // visibility bits: [P * wd] direct, then [P * ws] secondary
+    size_t bits_cap = 0;
+    int32_t* hits = nullptr;      // [P * Nb] secondary closest front-facing hit, -1 if none
+    size_t hits_cap = 0;
+    float4* rays = nullptr;       // ray queue of one chunk
+    size_t rays_cap = 0;
+    uint32_t* ctr = nullptr;      // per chunk: queued / fetched counters
+    size_t ctr_cap = 0;
+    int last_nd = -1, last_nb = -1, last_ns = -1, last_wd = 0, last_ws = 0;
+    struct Timer { int which; cudaEvent_t begin, end; };
+    std::vector<Timer> timers;    // EXM_FLAG_TIME_KERNELS
 };
 
 // error helpers (exm_api.cu)

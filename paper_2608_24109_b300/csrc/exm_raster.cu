@@ -145,5 +145,6 @@ exm_status exm_raster_impl(exm_ctx* ctx, const exm_mesh* m, exm_frame* f, int vi
     size_t tiles = (size_t)((f->W + 7) / 8) * ((f->H + 3) / 4) * views;
     compact_kernel<<<exm_blocks(tiles * 32, 256), 256, 0, s>>>((const unsigned long long*)f->visbuf, views, f->W,
                                                                f->H, f->pixels, f->counters);
+    ctx->launches += 3;
     return exm_cuda_check(cudaGetLastError(), "raster launch");
 }

@@ -1,25 +1,34 @@
-// Shading and its adjoint (Sec. 5.1-5.3, Eqs. 10-20), one thread per covered pixel,
-// persistent grid over the tile-ordered covered-pixel list.
+// Shading and its adjoint (Sec. 5.1-5.3, Eqs. 10-20) as a wavefront pipeline.
 //
-// Forward, per pixel: barycentrics of the camera ray on the visible face; interpolated
-// position, UV, vertex normal and tangent; bilinear 8-channel fetch; n_s from the normal
-// map in the interpolated tangent frame (Eqs. 10-11).  Direct light: N_d stratified
-// environment samples, each with f_r = f_d + f_s (Eqs. 13-16) and a BVH any-hit shadow
-// ray (Eq. 17).  Indirect: N_b cosine-weighted secondary rays about n_g with closest-hit
-// traversal; at each valid (front-facing) hit the same attribute query, N_s light samples
-// with shadow rays (Eq. 18), weighted by f_d(x) max(n_s(x).w, 0) / p_b (Eq. 19).
-// Î = L_dir + lambda_ind L_ind (Eq. 20).
+// Forward, per chunk of covered pixels:
+//   gen_secondary  -> one cosine-weighted secondary ray per (pixel, j) about n_g  (Sec. 5.3)
+//   trace<closest> -> the closest hit of each; valid iff front-facing              (Sec. 5.3)
+//   gen_direct     -> one shadow ray per (pixel, k) above the geometric horizon    (Eq. 17)
+//   gen_seclight   -> one shadow ray per (valid hit, s) above its horizon          (Eq. 18)
+//   trace<any>     -> any-hit visibility of every queued shadow ray, as bits
+// then one shade kernel, a warp per pixel, enumerates the pixel's unoccluded samples from
+// the bits (so every lane evaluates a live sample), evaluates f_r = f_d + f_s (Eqs. 13-16),
+// the direct estimator (Eq. 17), L_sec at each valid hit (Eq. 18), the indirect estimator
+// (Eq. 19) and the composite (Eq. 20).
 //
-// Backward recomputes the same decisions (same counter-based samples, same traversal)
-// and scatters dL/d(map texels) (4 bilinear taps x 8 channels, vector float4 atomics),
-// dL/dE (padded float4 accumulator per texel) and dL/dV (through barycentrics, position,
-// view direction, interpolated normals/tangents and UV; the frame adjoint finishes it).
+// The backward pass is the same warp-per-pixel kernel with the adjoint: it re-derives each
+// sample from its counter-based stream, reads the saved visibility bits and hit ids (no ray
+// is traced again), and scatters dL/d(map texels) (4 bilinear taps x 8 channels), dL/dE
+// (one padded float4 per texel) and dL/dV (barycentrics, position, view direction,
+// interpolated normals and tangents, UV; the frame adjoint finishes it).
+//
+// The trace kernel is persistent: each lane refills itself from the ray queue whenever its
+// ray finishes, so lanes do not idle while the longest ray of the warp completes.
+#include <vector>
+
 #include "exm_device.cuh"
 #include "exm_internal.h"
 
-
-
 namespace exm {
+
+constexpr int kShadeWarps = 8;        // warps per block of the shade kernel
+constexpr int kListMax = 1024;        // sample slots enumerated per round (32 bit words)
+constexpr uint32_t kRayCap = 1u << 24; // queued rays per chunk (2 float4 each, 512 MiB)
 
 struct ShadeArgs {
     // mesh
@@ -41,9 +50,17 @@ struct ShadeArgs {
     int W, H;
     // params
     int Nd, Nb, Ns;
+    int wd, ws;        // 32-bit words per pixel of the direct / secondary visibility bits
     float lambda;
     bool metallic;
     uint2 key;
+    // wavefront state
+    uint32_t* visbits;   // [P * wd]
+    uint32_t* secbits;   // [P * ws]
+    int32_t* hits;       // [P * Nb] closest front-facing hit of each secondary ray, -1 if none
+    float4* rays;        // queue: [kRayCap * 2]
+    uint32_t* ctr;       // per chunk: [0] queued, [1] fetch cursor (x2: closest, any)
+    uint32_t chunk_begin, chunk_pixels;
     // outputs
     float* out;
     unsigned long long* samples;
@@ -57,6 +74,68 @@ struct ShadeArgs {
     float4* gnrm;
     float4* gtan;
 };
+
+__device__ __forceinline__ void pixel_of(const ShadeArgs& A, uint32_t pid, int* c, int* px, int* py, uint32_t* rem) {
+    const uint32_t per_view = (uint32_t)A.W * (uint32_t)A.H;
+    *c = (int)(pid / per_view);
+    *rem = pid - (uint32_t)(*c) * per_view;
+    *py = (int)(*rem / (uint32_t)A.W);
+    *px = (int)(*rem - (uint32_t)(*py) * (uint32_t)A.W);
+}
+
+// Spec geometry of a covered pixel: the shading point, its geometric normal and the
+// offset origin of its shadow and secondary rays (all decisions hang on these).
+__device__ __forceinline__ void pixel_geometry(const ShadeArgs& A, uint32_t pid, S3* org, S3* ngs) {
+    int c, px, py;
+    uint32_t rem;
+    pixel_of(A, pid, &c, &px, &py, &rem);
+    const int f = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
+    const int i0 = __ldg(A.F + 3 * f), i1 = __ldg(A.F + 3 * f + 1), i2 = __ldg(A.F + 3 * f + 2);
+    S3 o, d, xs;
+    float bs[3];
+    camera_ray(A.cams[c], px, py, &o, &d);
+    surface_point(o, d, s3(__ldg(A.V + 3 * i0), __ldg(A.V + 3 * i0 + 1), __ldg(A.V + 3 * i0 + 2)),
+                  s3(__ldg(A.V + 3 * i1), __ldg(A.V + 3 * i1 + 1), __ldg(A.V + 3 * i1 + 2)),
+                  s3(__ldg(A.V + 3 * i2), __ldg(A.V + 3 * i2 + 1), __ldg(A.V + 3 * i2 + 2)), &xs, ngs, bs);
+    *org = offset_origin(xs, *ngs);
+}
+
+// The j-th secondary direction of a pixel (stream 1) and xi1 (for p_b).
+__device__ __forceinline__ S3 secondary_dir(const ShadeArgs& A, uint32_t pixel, int c, int j, S3 ngs, float* xi1) {
+    const uint4 h = philox(make_uint4(pixel, (uint32_t)c, (uint32_t)j, 1u), A.key);
+    *xi1 = smul(__uint2float_rn(stratified32((uint32_t)j, (uint32_t)A.Nb, h.x) >> 8), 0x1p-24f);
+    return cosine_dir(ngs, *xi1, unit24(h.y));
+}
+
+// The hit point y of a valid secondary ray (spec), its geometric normal and offset origin.
+__device__ __forceinline__ void secondary_point(const ShadeArgs& A, int g, S3 org, S3 wjs, S3* ys, S3* ngy, S3* yorg,
+                                                float3* Q) {
+    const int j0 = __ldg(A.F + 3 * g), j1 = __ldg(A.F + 3 * g + 1), j2 = __ldg(A.F + 3 * g + 2);
+    Q[0] = ld3(A.V + 3 * j0);
+    Q[1] = ld3(A.V + 3 * j1);
+    Q[2] = ld3(A.V + 3 * j2);
+    float bys[3];
+    surface_point(org, wjs, s3(Q[0].x, Q[0].y, Q[0].z), s3(Q[1].x, Q[1].y, Q[1].z), s3(Q[2].x, Q[2].y, Q[2].z), ys,
+                  ngy, bys);
+    *yorg = offset_origin(*ys, *ngy);
+}
+
+__device__ __forceinline__ void push_ray(float4* rays, uint32_t idx, S3 o, S3 d, uint64_t slot) {
+    rays[2 * (size_t)idx] = make_float4(o.x, o.y, o.z, d.x);
+    rays[2 * (size_t)idx + 1] = make_float4(d.y, d.z, __uint_as_float((uint32_t)slot), __uint_as_float((uint32_t)(slot >> 32)));
+}
+
+// Warp-aggregated append of the lanes with `want` set; returns this lane's queue index.
+__device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
+    const unsigned mask = __ballot_sync(0xffffffffu, want);
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (mask) {
+        if (lane == __ffs(mask) - 1) base = atomicAdd(counter, (uint32_t)__popc(mask));
+        base = __shfl_sync(0xffffffffu, base, __ffs(mask) - 1);
+    }
+    return base + __popc(mask & ((1u << lane) - 1u));
+}
 
 // (f_d + f_s) * max(n.wi, 0), Eqs. 13-16 (FP32).  The GGX denominator uses
 // |n x h|^2 + alpha^2 (n.h)^2, equal to (n.h)^2 (alpha^2 - 1) + 1 for unit vectors.
@@ -183,20 +262,273 @@ __device__ __forceinline__ Surface make_surface(const float att[8], float3 ni, f
     return su;
 }
 
-template <typename T, bool BWD, bool COUNT>
-__global__ void __launch_bounds__(128) shade_kernel(ShadeArgs A) {
+
+// ------------------------------------------------------------------ ray generation
+
+// Ray queues are written in coherent order: a warp's lanes are 32 neighbouring pixels of the
+// tile-ordered pixel list, and consecutive queue entries hold the same sample index k of
+// those pixels, so the 32 rays a warp later traces start close together and point the
+// same way (the same stratum of the same CDF).
+constexpr int kGenK = 32;  // sample indices per warp of gen_direct
+
+// One shadow ray per (pixel, k) whose direction is above the geometric horizon (Eq. 17).
+__global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
     const uint32_t total = *A.count;
-    const uint32_t per_view = (uint32_t)A.W * (uint32_t)A.H;
-    uint32_t err = 0;
-    unsigned long long my_samples = 0;
+    const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
+    if (A.chunk_begin >= end) return;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nkc = (uint32_t)(A.Nd + kGenK - 1) / kGenK;
+    const uint32_t group = warp / nkc, kc = warp % nkc;
+    const int lane = threadIdx.x & 31;
+    if (A.chunk_begin + group * 32 >= end) return;
+    const uint32_t i = A.chunk_begin + group * 32 + lane;
+    const bool valid = i < end;
     EnvView env = A.env;
     env.Q = *A.env.Qp;
-    uint32_t c_nodes = 0, c_tris = 0, c_brdf = 0, c_rays = 0;
-    for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const uint32_t pid = A.pixels[idx];
-        const int c = (int)(pid / per_view);
-        const uint32_t rem = pid - (uint32_t)c * per_view;
-        const int py = (int)(rem / (uint32_t)A.W), px = (int)(rem - (uint32_t)py * (uint32_t)A.W);
+    int c = 0, px, py;
+    uint32_t rem = 0;
+    S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
+    if (valid) {
+        const uint32_t pid = A.pixels[i];
+        pixel_of(A, pid, &c, &px, &py, &rem);
+        pixel_geometry(A, pid, &org, &ngs);
+    }
+    const int k0 = (int)kc * kGenK, k1 = min(A.Nd, k0 + kGenK);
+    for (int k = k0; k < k1; ++k) {
+        bool want = false;
+        S3 dir = s3(0.f, 0.f, 0.f);
+        if (valid) {
+            const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
+            const LightSample ls = light_sample(env, h, (uint32_t)k, (uint32_t)A.Nd);
+            dir = ls.dir;
+            want = sdot(ngs, dir) > 0.0f;
+        }
+        const uint32_t idx = warp_append(A.ctr + 2, want);
+        if (want) {
+            if (idx < kRayCap) push_ray(A.rays, idx, org, dir, (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)k);
+            else atomicOr(A.status, ERRBIT_TRAVERSAL);
+        }
+    }
+}
+
+// One closest-hit ray per (pixel, j): cosine-weighted about n_g (Sec. 5.3).
+__global__ void __launch_bounds__(256) gen_secondary_kernel(ShadeArgs A) {
+    const uint32_t total = *A.count;
+    const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
+    if (A.chunk_begin >= end) return;
+    const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (A.chunk_begin + group * 32 >= end) return;
+    const uint32_t i = A.chunk_begin + group * 32 + lane;
+    const bool valid = i < end;
+    int c = 0, px, py;
+    uint32_t rem = 0;
+    S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
+    if (valid) {
+        const uint32_t pid = A.pixels[i];
+        pixel_of(A, pid, &c, &px, &py, &rem);
+        pixel_geometry(A, pid, &org, &ngs);
+    }
+    for (int j = 0; j < A.Nb; ++j) {
+        S3 wjs = s3(0.f, 0.f, 0.f);
+        if (valid) {
+            float xi1;
+            wjs = secondary_dir(A, rem, c, j, ngs, &xi1);
+        }
+        const uint32_t idx = warp_append(A.ctr, valid);
+        if (valid) {
+            if (idx < kRayCap) push_ray(A.rays, idx, org, wjs, (uint64_t)i * (uint32_t)A.Nb + (uint32_t)j);
+            else atomicOr(A.status, ERRBIT_TRAVERSAL);
+        }
+    }
+}
+
+// One shadow ray per (valid secondary hit, s) above the hit's geometric horizon (Eq. 18).
+__global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
+    const uint32_t total = *A.count;
+    const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
+    if (A.chunk_begin >= end) return;
+    const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (A.chunk_begin + group * 32 >= end) return;
+    const uint32_t i = A.chunk_begin + group * 32 + lane;
+    const bool valid = i < end;
+    EnvView env = A.env;
+    env.Q = *A.env.Qp;
+    int c = 0, px, py;
+    uint32_t rem = 0;
+    S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
+    if (valid) {
+        const uint32_t pid = A.pixels[i];
+        pixel_of(A, pid, &c, &px, &py, &rem);
+        pixel_geometry(A, pid, &org, &ngs);
+    }
+    for (int j = 0; j < A.Nb; ++j) {
+        const int g = valid ? A.hits[(size_t)i * A.Nb + j] : -1;
+        S3 yorg = s3(0.f, 0.f, 0.f), ngy = s3(0.f, 0.f, 1.f);
+        if (g >= 0) {
+            float xi1;
+            const S3 wjs = secondary_dir(A, rem, c, j, ngs, &xi1);
+            S3 ys;
+            float3 Q[3];
+            secondary_point(A, g, org, wjs, &ys, &ngy, &yorg, Q);
+        }
+        for (int s = 0; s < A.Ns; ++s) {
+            bool want = false;
+            S3 dir = s3(0.f, 0.f, 0.f);
+            if (g >= 0) {
+                const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(j * A.Ns + s), 2u), A.key);
+                const LightSample ls = light_sample(env, h, (uint32_t)s, (uint32_t)A.Ns);
+                dir = ls.dir;
+                want = sdot(ngy, dir) > 0.0f;
+            }
+            const uint32_t idx = warp_append(A.ctr + 2, want);
+            if (want) {
+                const uint64_t slot = (uint64_t)i * (uint32_t)A.ws * 32u + (uint32_t)(j * A.Ns + s);
+                if (idx < kRayCap) push_ray(A.rays, idx, yorg, dir, slot | (1ull << 63));
+                else atomicOr(A.status, ERRBIT_TRAVERSAL);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ persistent tracer
+// Any-hit (shadow rays -> visibility bits) or closest-hit (secondary rays -> hit ids) over
+// the chunk's ray queue.  A warp takes 32 consecutive queue entries at a time (the same
+// sample index of 32 neighbouring pixels, so the rays are coherent) and traces them to
+// completion before taking the next batch.
+template <bool CLOSEST, bool COUNT>
+__global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
+    const uint32_t* qcount = A.ctr + (CLOSEST ? 0 : 2);
+    uint32_t* cursor = A.ctr + (CLOSEST ? 1 : 3);
+    const uint32_t n = *qcount;
+    if (n == 0) return;
+    const int lane = threadIdx.x & 31;
+    uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
+    int stack[kStackSize];
+    while (true) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(cursor, 32u);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= n) break;
+        const uint32_t my = base + lane;
+        if (my >= n) continue;
+        const float4 a = A.rays[2 * (size_t)my], b = A.rays[2 * (size_t)my + 1];
+        const Ray r = make_ray(s3(a.x, a.y, a.z), s3(a.w, b.x, b.y));
+        const uint64_t slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
+        ++c_rays;
+        int sp = 0, node = 0, best = -1;
+        float bt = INFINITY, bdet = 0.0f;
+        bool hit = false;
+        for (int steps = 0;; ++steps) {
+            if (steps >= kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; break; }
+            ++c_nodes;
+            const float4 n0 = __ldg(A.bvh.nodes + 4 * node), n1 = __ldg(A.bvh.nodes + 4 * node + 1);
+            const float4 n2 = __ldg(A.bvh.nodes + 4 * node + 2), n3 = __ldg(A.bvh.nodes + 4 * node + 3);
+            float ta, tb;
+            bool ha = slab(make_float3(n0.x, n0.y, n0.z), make_float3(n0.w, n1.x, n1.y), r, CLOSEST ? bt : INFINITY, &ta);
+            bool hb = slab(make_float3(n1.z, n1.w, n2.x), make_float3(n2.y, n2.z, n2.w), r, CLOSEST ? bt : INFINITY, &tb);
+            const int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
+            if (ha && ca < 0) {
+                ++c_tris;
+                float T, det;
+                int id;
+                if (tri_test(A.bvh, ~ca, r, &T, &det, &id)) {
+                    if (!CLOSEST) { hit = true; break; }
+                    const float t = sdiv(T, det);
+                    if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+                }
+                ha = false;
+            }
+            if (hb && cb < 0) {
+                ++c_tris;
+                float T, det;
+                int id;
+                if (tri_test(A.bvh, ~cb, r, &T, &det, &id)) {
+                    if (!CLOSEST) { hit = true; break; }
+                    const float t = sdiv(T, det);
+                    if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+                }
+                hb = false;
+            }
+            if (CLOSEST) {
+                if (ha && ta > bt) ha = false;
+                if (hb && tb > bt) hb = false;
+            }
+            int next;
+            if (ha && hb) {
+                if (sp >= kStackSize) { err |= ERRBIT_TRAVERSAL; hit = true; break; }
+                const bool afirst = ta <= tb;
+                stack[sp++] = afirst ? cb : ca;
+                next = afirst ? ca : cb;
+            } else if (ha) {
+                next = ca;
+            } else if (hb) {
+                next = cb;
+            } else {
+                if (sp == 0) break;
+                next = stack[--sp];
+            }
+            node = next;
+        }
+        if (CLOSEST) {
+            A.hits[slot] = (best >= 0 && bdet > 0.0f) ? best : -1;
+        } else if (!hit) {
+            const uint64_t bit = slot & ~(1ull << 63);
+            uint32_t* words = (slot >> 63) ? A.secbits : A.visbits;
+            atomicOr(words + (bit >> 5), 1u << (uint32_t)(bit & 31));
+        }
+    }
+    if (err) atomicOr(A.status, err);
+    if (COUNT) {
+        atomicAdd(A.work, (unsigned long long)c_nodes);
+        atomicAdd(A.work + 1, (unsigned long long)c_tris);
+        atomicAdd(A.work + 3, (unsigned long long)c_rays);
+    }
+}
+
+// ------------------------------------------------------------------ shading (warp per pixel)
+
+// Appends the set bits of `words` [0, nwords) of a pixel into the warp's list (bit index
+// relative to wbase*32) and returns how many were appended.
+__device__ __forceinline__ int enumerate_bits(const uint32_t* words, int wbase, int nwords, uint16_t* list) {
+    const int lane = threadIdx.x & 31;
+    const int wi = wbase + lane;
+    uint32_t w = wi < nwords ? words[wi] : 0u;
+    const int cnt = __popc(w);
+    int off = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, off, o);
+        if (lane >= o) off += y;
+    }
+    const int tot = __shfl_sync(0xffffffffu, off, 31);
+    off -= cnt;
+    while (w) {
+        const int b = __ffs(w) - 1;
+        list[off++] = (uint16_t)(lane * 32 + b);
+        w &= w - 1u;
+    }
+    __syncwarp();
+    return tot;
+}
+
+template <typename T, bool BWD, bool COUNT>
+__global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
+    __shared__ uint16_t s_list[kShadeWarps][kListMax];
+    const int lane = threadIdx.x & 31;
+    uint16_t* list = s_list[threadIdx.x >> 5];
+    const uint32_t total = *A.count;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    EnvView env = A.env;
+    env.Q = *A.env.Qp;
+    unsigned long long my_samples = 0;
+    uint32_t c_brdf = 0;
+    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
+        const uint32_t pid = A.pixels[i];
+        int c, px, py;
+        uint32_t rem;
+        pixel_of(A, pid, &c, &px, &py, &rem);
         float3 g = f3(0.f, 0.f, 0.f);
         if (BWD) {
             g = ld3(A.grad_rgb + 3 * (size_t)pid);
@@ -234,143 +566,165 @@ __global__ void __launch_bounds__(128) shade_kernel(ShadeArgs A) {
         const float3 T0 = ld3(A.tan + 3 * u0), T1 = ld3(A.tan + 3 * u1), T2 = ld3(A.tan + 3 * u2);
         const float3 ni = b[0] * N0 + b[1] * N1 + b[2] * N2;
         const float3 ti = b[0] * T0 + b[1] * T1 + b[2] * T2;
-        const float sgn = __ldg(A.fsign + f);
-        const Surface su = make_surface(att, ni, ti, sgn, A.metallic);
+        const Surface su = make_surface(att, ni, ti, __ldg(A.fsign + f), A.metallic);
         const D3 vod = dsub(eyed, d3(bd[0] * P0.x + bd[1] * P1.x + bd[2] * P2.x,
                                      bd[0] * P0.y + bd[1] * P1.y + bd[2] * P2.y,
                                      bd[0] * P0.z + bd[1] * P1.z + bd[2] * P2.z));
         const double vold = sqrt(ddot(vod, vod));
         const float vol = (float)vold;
         const float3 wo = f3((float)(vod.x / vold), (float)(vod.y / vold), (float)(vod.z / vold));
-        const uint32_t pixel = rem;
-        // adjoint accumulators at x
+        float3 L = f3(0.f, 0.f, 0.f);
         float3 gns = f3(0.f, 0.f, 0.f), gwo = f3(0.f, 0.f, 0.f), ga = f3(0.f, 0.f, 0.f);
         float gr = 0.f, gm = 0.f;
-        // ---- direct light (Eq. 17)
-        float3 L = f3(0.f, 0.f, 0.f);
+        // ---- direct light (Eq. 17): the pixel's unoccluded samples, one per lane
         const float invNd = 1.0f / (float)A.Nd;
-        for (int k = 0; k < A.Nd; ++k) {
-            const uint4 h = philox(make_uint4(pixel, (uint32_t)c, (uint32_t)k, 0u), A.key);
-            const LightSample ls = light_sample(env, h, (uint32_t)k, (uint32_t)A.Nd);
-            const float3 wi = normalize(tof(ls.dir));
-            if (dot(su.ns, wi) <= 0.0f) continue;
-            if (!(sdot(ngs, ls.dir) > 0.0f)) continue;
-            if (ls.E.x == 0.0f && ls.E.y == 0.0f && ls.E.z == 0.0f && !BWD) continue;
-            ++c_rays;
-            if (any_hit(A.bvh, make_ray(org, ls.dir), &err, c_nodes, c_tris)) continue;
-            const float w = ls.inv_pdf * invNd;
-            ++c_brdf;
-            const float3 fc = brdf_cos(su.ns, wi, wo, su.a, su.r, su.m);
-            L += w * (ls.E * fc);
-            if (BWD) {
-                const float3 gE = w * (g * fc);
-                atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
-                brdf_cos_adjoint(su.ns, wi, wo, su.a, su.r, su.m, w * (g * ls.E), gns, gwo, ga, gr, gm);
+        const uint32_t* vb = A.visbits + (size_t)i * A.wd;
+        for (int wbase = 0; wbase < A.wd; wbase += 32) {
+            const int tot = enumerate_bits(vb, wbase, A.wd, list);
+            for (int t0 = 0; t0 < tot; t0 += 32) {
+                const int e = t0 + lane;
+                if (e < tot) {
+                    const int k = wbase * 32 + list[e];
+                    const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
+                    const LightSample ls = light_sample(env, h, (uint32_t)k, (uint32_t)A.Nd);
+                    const float3 wi = normalize(tof(ls.dir));
+                    const float w = ls.inv_pdf * invNd;
+                    ++c_brdf;
+                    const float3 fc = brdf_cos(su.ns, wi, wo, su.a, su.r, su.m);
+                    if (!BWD) {
+                        L += w * (ls.E * fc);
+                    } else {
+                        const float3 gE = w * (g * fc);
+                        atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
+                        brdf_cos_adjoint(su.ns, wi, wo, su.a, su.r, su.m, w * (g * ls.E), gns, gwo, ga, gr, gm);
+                    }
+                }
             }
+            __syncwarp();
         }
-        my_samples += (unsigned long long)A.Nd;
-        // ---- one-bounce indirect (Eqs. 18-19)
+        if (!BWD && lane == 0) my_samples += (unsigned long long)A.Nd;
+        // ---- one-bounce indirect (Eqs. 18-19): lanes take the pixel's live (j, s) pairs
         if (A.Nb > 0 && A.lambda != 0.0f) {
             const float3 fdx = ((1.0f - su.m) / kPi) * su.a;
             const float scale = A.lambda / (float)A.Nb;
             const float invNs = 1.0f / (float)A.Ns;
-            float3 Lind = f3(0.f, 0.f, 0.f);
-            for (int j = 0; j < A.Nb; ++j) {
-                const uint4 h = philox(make_uint4(pixel, (uint32_t)c, (uint32_t)j, 1u), A.key);
-                const float xi1 = smul(__uint2float_rn(stratified32((uint32_t)j, (uint32_t)A.Nb, h.x) >> 8), 0x1p-24f);
-                const float xi2 = unit24(h.y);
-                const S3 wjs = cosine_dir(ngs, xi1, xi2);
-                my_samples += 1ull;
-                const float3 wj = normalize(tof(wjs));
-                const float cxj = dot(su.ns, wj);
-                if (cxj <= 0.0f) continue;
-                float thit;
-                bool front;
-                ++c_rays;
-                const int gtri = closest_hit(A.bvh, make_ray(org, wjs), &thit, &front, &err, c_nodes, c_tris);
-                if (gtri < 0 || !front) continue;
-                my_samples += (unsigned long long)A.Ns;
-                const int j0 = __ldg(A.F + 3 * gtri), j1 = __ldg(A.F + 3 * gtri + 1), j2 = __ldg(A.F + 3 * gtri + 2);
-                const int v0 = __ldg(A.Fuv + 3 * gtri), v1 = __ldg(A.Fuv + 3 * gtri + 1), v2 = __ldg(A.Fuv + 3 * gtri + 2);
-                const float3 Q0 = ld3(A.V + 3 * j0), Q1 = ld3(A.V + 3 * j1), Q2 = ld3(A.V + 3 * j2);
-                S3 ys, ngy;
-                float bys[3];
-                surface_point(org, wjs, s3(Q0.x, Q0.y, Q0.z), s3(Q1.x, Q1.y, Q1.z), s3(Q2.x, Q2.y, Q2.z), &ys, &ngy, bys);
-                const S3 yorg = offset_origin(ys, ngy);
-                double byd[3];
-                bary_d(d3(org.x, org.y, org.z), d3(wjs.x, wjs.y, wjs.z), dof(Q0), dof(Q1), dof(Q2), byd);
-                const float by[3] = {(float)byd[0], (float)byd[1], (float)byd[2]};
-                const double syd = (byd[0] * __ldg(A.UV + 2 * v0) + byd[1] * __ldg(A.UV + 2 * v1) +
-                                    byd[2] * __ldg(A.UV + 2 * v2)) * A.map.W - 0.5;
-                const double tyd = (byd[0] * __ldg(A.UV + 2 * v0 + 1) + byd[1] * __ldg(A.UV + 2 * v1 + 1) +
-                                    byd[2] * __ldg(A.UV + 2 * v2 + 1)) * A.map.H - 0.5;
-                const Footprint fpy = footprint_d(A.map, syd, tyd);
-                float atty[8];
-                fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
-                const float3 niy = by[0] * ld3(A.nrm + 3 * j0) + by[1] * ld3(A.nrm + 3 * j1) + by[2] * ld3(A.nrm + 3 * j2);
-                const float3 tiy = by[0] * ld3(A.tan + 3 * v0) + by[1] * ld3(A.tan + 3 * v1) + by[2] * ld3(A.tan + 3 * v2);
-                const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
-                const float3 fdy = ((1.0f - sy.m) / kPi) * sy.a;
-                const float wb = scale * kPi * cxj / __fsqrt_rn(ssub(1.0f, xi1));
-                const float3 gLsec = wb * (g * fdx);
-                float3 Esum = f3(0.f, 0.f, 0.f);
-                float3 gnsy = f3(0.f, 0.f, 0.f);
-                for (int s = 0; s < A.Ns; ++s) {
-                    const uint4 h2 = philox(make_uint4(pixel, (uint32_t)c, (uint32_t)(j * A.Ns + s), 2u), A.key);
+            if (!BWD) {
+                int valid = 0;
+                for (int j0 = 0; j0 < A.Nb; j0 += 32) {
+                    const int j = j0 + lane;
+                    valid += __popc(__ballot_sync(0xffffffffu, j < A.Nb && A.hits[(size_t)i * A.Nb + j] >= 0));
+                }
+                if (lane == 0) my_samples += (unsigned long long)A.Nb + (unsigned long long)valid * A.Ns;
+            }
+            const uint32_t* sb = A.secbits + (size_t)i * A.ws;
+            for (int wbase = 0; wbase < A.ws; wbase += 32) {
+                const int tot = enumerate_bits(sb, wbase, A.ws, list);
+                for (int t0 = 0; t0 < tot; t0 += 32) {
+                    const int e = t0 + lane;
+                    if (e >= tot) continue;
+                    const int bit = wbase * 32 + list[e];
+                    const int jj = bit / A.Ns, s = bit - jj * A.Ns;
+                    float xi1;
+                    const S3 wjs = secondary_dir(A, rem, c, jj, ngs, &xi1);
+                    const float3 wj = normalize(tof(wjs));
+                    const float cxj = dot(su.ns, wj);
+                    if (cxj <= 0.0f) continue;
+                    const int gtri = A.hits[(size_t)i * A.Nb + jj];
+                    S3 ys, ngy, yorg;
+                    float3 Q[3];
+                    secondary_point(A, gtri, org, wjs, &ys, &ngy, &yorg, Q);
+                    double byd[3];
+                    bary_d(d3(org.x, org.y, org.z), d3(wjs.x, wjs.y, wjs.z), dof(Q[0]), dof(Q[1]), dof(Q[2]), byd);
+                    const float by[3] = {(float)byd[0], (float)byd[1], (float)byd[2]};
+                    const int v0 = __ldg(A.Fuv + 3 * gtri), v1 = __ldg(A.Fuv + 3 * gtri + 1), v2 = __ldg(A.Fuv + 3 * gtri + 2);
+                    const int q0 = __ldg(A.F + 3 * gtri), q1 = __ldg(A.F + 3 * gtri + 1), q2 = __ldg(A.F + 3 * gtri + 2);
+                    const double syd = (byd[0] * __ldg(A.UV + 2 * v0) + byd[1] * __ldg(A.UV + 2 * v1) +
+                                        byd[2] * __ldg(A.UV + 2 * v2)) * A.map.W - 0.5;
+                    const double tyd = (byd[0] * __ldg(A.UV + 2 * v0 + 1) + byd[1] * __ldg(A.UV + 2 * v1 + 1) +
+                                        byd[2] * __ldg(A.UV + 2 * v2 + 1)) * A.map.H - 0.5;
+                    const Footprint fpy = footprint_d(A.map, syd, tyd);
+                    float atty[8];
+                    fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
+                    const float3 niy = by[0] * ld3(A.nrm + 3 * q0) + by[1] * ld3(A.nrm + 3 * q1) + by[2] * ld3(A.nrm + 3 * q2);
+                    const float3 tiy = by[0] * ld3(A.tan + 3 * v0) + by[1] * ld3(A.tan + 3 * v1) + by[2] * ld3(A.tan + 3 * v2);
+                    const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
+                    const float3 fdy = ((1.0f - sy.m) / kPi) * sy.a;
+                    const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
                     const LightSample ls = light_sample(env, h2, (uint32_t)s, (uint32_t)A.Ns);
                     const float3 wl = normalize(tof(ls.dir));
                     const float cs = dot(sy.ns, wl);
                     if (cs <= 0.0f) continue;
-                    if (!(sdot(ngy, ls.dir) > 0.0f)) continue;
-                    ++c_rays;
-                    if (any_hit(A.bvh, make_ray(yorg, ls.dir), &err, c_nodes, c_tris)) continue;
                     ++c_brdf;
-                    const float wl_ = ls.inv_pdf * invNs * cs;
-                    Esum += wl_ * ls.E;
-                    if (BWD) {
-                        const float3 gE = wl_ * (gLsec * fdy);
+                    const float pb_inv = kPi / __fsqrt_rn(ssub(1.0f, xi1));  // 1 / p_b
+                    const float wb = scale * cxj * pb_inv;
+                    const float term = ls.inv_pdf * invNs * cs;
+                    const float3 ET = term * ls.E;
+                    if (!BWD) {
+                        L += wb * (fdx * (fdy * ET));
+                    } else {
+                        // E of the light sample
+                        const float3 gE = (wb * term) * (g * (fdx * fdy));
                         atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
-                        gnsy += (ls.inv_pdf * invNs * dot(gLsec, fdy * ls.E)) * wl;
+                        // f_d(x) and n_s(x) through max(n_s(x).w_j, 0)
+                        const float3 gfdx = wb * (g * (fdy * ET));
+                        ga += ((1.0f - su.m) / kPi) * gfdx;
+                        gm += -dot(gfdx, su.a) / kPi;
+                        gns += (scale * pb_inv * dot(g, fdx * (fdy * ET))) * wj;
+                        // material at y (its geometry is a constant of the derivative)
+                        const float3 gLsec = wb * (g * fdx);
+                        const float3 gfdy = gLsec * ET;
+                        const float3 gnsy = (ls.inv_pdf * invNs * dot(gLsec, fdy * ls.E)) * wl;
+                        float gy[8];
+                        const float3 gay = ((1.0f - sy.m) / kPi) * gfdy;
+                        gy[0] = gay.x; gy[1] = gay.y; gy[2] = gay.z; gy[3] = 0.0f;
+                        gy[4] = A.metallic ? -dot(gfdy, sy.a) / kPi : 0.0f;
+                        const float3 gnt = f3(dot(sy.T, gnsy), dot(sy.B, gnsy), dot(sy.n, gnsy));
+                        const float3 gq = (1.0f / sy.ql) * (gnt - dot(gnt, sy.nt) * sy.nt);
+                        gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
+                        if (A.gmaps) scatter8(A.gmaps, fpy, gy);
                     }
                 }
-                const float3 Lsec = fdy * Esum;
-                Lind += wb * (fdx * Lsec);
-                if (BWD) {
-                    // primary: dL/df_d(x) and dL/dn_s(x) through max(n_s(x).w_j, 0)
-                    const float3 gfdx = wb * (g * Lsec);
-                    ga += ((1.0f - su.m) / kPi) * gfdx;
-                    gm += -dot(gfdx, su.a) / kPi;
-                    const float gc = scale * kPi / __fsqrt_rn(ssub(1.0f, xi1)) * dot(g, fdx * Lsec);
-                    gns += gc * wj;
-                    // secondary material at y (its geometry is a constant of the derivative)
-                    const float3 gfdy = gLsec * Esum;
-                    float gy[8];
-                    const float3 gay = ((1.0f - sy.m) / kPi) * gfdy;
-                    gy[0] = gay.x; gy[1] = gay.y; gy[2] = gay.z; gy[3] = 0.0f;
-                    gy[4] = A.metallic ? -dot(gfdy, sy.a) / kPi : 0.0f;
-                    const float3 gnt = f3(dot(sy.T, gnsy), dot(sy.B, gnsy), dot(sy.n, gnsy));
-                    const float3 gq = (1.0f / sy.ql) * (gnt - dot(gnt, sy.nt) * sy.nt);
-                    gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
-                    if (A.gmaps) scatter8(A.gmaps, fpy, gy);
-                }
+                __syncwarp();
             }
-            L += Lind;
         }
         if (!BWD) {
-            float* out = A.out + 3 * (size_t)pid;
-            out[0] = L.x; out[1] = L.y; out[2] = L.z;
+#pragma unroll
+            for (int ofs = 16; ofs > 0; ofs >>= 1) {
+                L.x += __shfl_xor_sync(0xffffffffu, L.x, ofs);
+                L.y += __shfl_xor_sync(0xffffffffu, L.y, ofs);
+                L.z += __shfl_xor_sync(0xffffffffu, L.z, ofs);
+            }
+            if (lane == 0) {
+                float* out = A.out + 3 * (size_t)pid;
+                out[0] = L.x; out[1] = L.y; out[2] = L.z;
+            }
             continue;
         }
-        // ---- adjoint of the attribute query at x
+        // ---- adjoint of the attribute query at x: sum the lanes' partial adjoints
+        float acc[11] = {gns.x, gns.y, gns.z, gwo.x, gwo.y, gwo.z, ga.x, ga.y, ga.z, gr, gm};
+#pragma unroll
+        for (int q = 0; q < 11; ++q)
+#pragma unroll
+            for (int ofs = 16; ofs > 0; ofs >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], ofs);
+        gns = f3(acc[0], acc[1], acc[2]);
+        gwo = f3(acc[3], acc[4], acc[5]);
         float gatt[8];
-        gatt[0] = ga.x; gatt[1] = ga.y; gatt[2] = ga.z;
-        gatt[3] = gr;
-        gatt[4] = A.metallic ? gm : 0.0f;
+        gatt[0] = acc[6]; gatt[1] = acc[7]; gatt[2] = acc[8];
+        gatt[3] = acc[9];
+        gatt[4] = A.metallic ? acc[10] : 0.0f;
         // n_s = T nt.x + B nt.y + n nt.z;  B = s (n x T);  nt = q / |q|
         const float3 gnt = f3(dot(su.T, gns), dot(su.B, gns), dot(su.n, gns));
         const float3 gq = (1.0f / su.ql) * (gnt - dot(gnt, su.nt) * su.nt);
         gatt[5] = gq.x; gatt[6] = gq.y; gatt[7] = gq.z;
-        if (A.gmaps) scatter8(A.gmaps, fp, gatt);
+        if (A.gmaps && lane < 8) {
+            const int tap = lane >> 1, half = lane & 1;
+            const float wt = tap == 0 ? (1.f - fp.fs) * (1.f - fp.ft)
+                           : tap == 1 ? fp.fs * (1.f - fp.ft) : tap == 2 ? (1.f - fp.fs) * fp.ft : fp.fs * fp.ft;
+            const uint32_t tx = tap == 0 ? fp.t[0] : tap == 1 ? fp.t[1] : tap == 2 ? fp.t[2] : fp.t[3];
+            const float4 v = half ? make_float4(wt * gatt[4], wt * gatt[5], wt * gatt[6], wt * gatt[7])
+                                  : make_float4(wt * gatt[0], wt * gatt[1], wt * gatt[2], wt * gatt[3]);
+            atomicAdd(reinterpret_cast<float4*>(A.gmaps) + 2 * (size_t)tx + half, v);
+        }
         if (A.gV == nullptr) continue;
         const float3 gB = su.nt.y * gns;
         float3 gT = su.nt.x * gns + su.s * cross(gB, su.n);
@@ -383,13 +737,6 @@ __global__ void __launch_bounds__(128) shade_kernel(ShadeArgs A) {
         gn = gn - (nti * gu + dot(gu, su.n) * ti);
         const float nl = sqrtf(dot(ni, ni));
         const float3 gni = (1.0f / nl) * (gn - dot(gn, su.n) * su.n);
-        // scatter to the vertex-normal / UV-vertex-tangent adjoints
-        const int vi[3] = {i0, i1, i2}, ui[3] = {u0, u1, u2};
-        for (int k = 0; k < 3; ++k) {
-            const float3 a1 = b[k] * gni, a2v = b[k] * gti;
-            atomicAdd(A.gnrm + vi[k], make_float4(a1.x, a1.y, a1.z, 0.0f));
-            atomicAdd(A.gtan + ui[k], make_float4(a2v.x, a2v.y, a2v.z, 0.0f));
-        }
         float gb[3];
         gb[0] = dot(N0, gni) + dot(T0, gti);
         gb[1] = dot(N1, gni) + dot(T1, gti);
@@ -410,13 +757,13 @@ __global__ void __launch_bounds__(128) shade_kernel(ShadeArgs A) {
         {
             const float3 dv = f3((float)dd.x, (float)dd.y, (float)dd.z), oo = tof(o);
             const float3 e1 = P1 - P0, e2 = P2 - P0, sv = oo - P0;
-            const float3 pv = cross(dv, e2), qv = cross(sv, e1);
+            const float3 pv = cross(dv, e2);
             const float det = dot(e1, pv);
             const float b1 = b[1], b2 = b[2];
             const float g1 = gb[1] - gb[0], g2 = gb[2] - gb[0];
             const float gn1 = g1 / det, gn2 = g2 / det, gdet = -(g1 * b1 + g2 * b2) / det;
             float3 gs = gn1 * pv;
-            float3 gp = gn1 * sv + gdet * e1;
+            const float3 gp = gn1 * sv + gdet * e1;
             const float3 gqv = gn2 * dv;
             float3 ge1 = gdet * pv;
             gs += cross(e1, gqv);
@@ -426,23 +773,31 @@ __global__ void __launch_bounds__(128) shade_kernel(ShadeArgs A) {
             gP1 += ge1;
             gP2 += ge2;
         }
-        const float3 gp3[3] = {gP0, gP1, gP2};
-        for (int k = 0; k < 3; ++k) {
-            atomicAdd(A.gV + 3 * vi[k], gp3[k].x);
-            atomicAdd(A.gV + 3 * vi[k] + 1, gp3[k].y);
-            atomicAdd(A.gV + 3 * vi[k] + 2, gp3[k].z);
+        if (lane >= 8 && lane < 11) {
+            const int k = lane - 8;
+            const int vk = k == 0 ? i0 : k == 1 ? i1 : i2;
+            const float3 gp = k == 0 ? gP0 : k == 1 ? gP1 : gP2;
+            atomicAdd(A.gV + 3 * vk, gp.x);
+            atomicAdd(A.gV + 3 * vk + 1, gp.y);
+            atomicAdd(A.gV + 3 * vk + 2, gp.z);
+        } else if (lane >= 11 && lane < 14) {
+            const int k = lane - 11;
+            const int vk = k == 0 ? i0 : k == 1 ? i1 : i2;
+            const float3 a1 = b[k == 0 ? 0 : k == 1 ? 1 : 2] * gni;
+            atomicAdd(A.gnrm + vk, make_float4(a1.x, a1.y, a1.z, 0.0f));
+        } else if (lane >= 14 && lane < 17) {
+            const int k = lane - 14;
+            const int uk = k == 0 ? u0 : k == 1 ? u1 : u2;
+            const float3 a2 = b[k == 0 ? 0 : k == 1 ? 1 : 2] * gti;
+            atomicAdd(A.gtan + uk, make_float4(a2.x, a2.y, a2.z, 0.0f));
         }
     }
-    if (err) atomicOr(A.status, err);
-    if (COUNT) {
-        atomicAdd(A.work, (unsigned long long)c_nodes);
-        atomicAdd(A.work + 1, (unsigned long long)c_tris);
-        atomicAdd(A.work + 2, (unsigned long long)c_brdf);
-        atomicAdd(A.work + 3, (unsigned long long)c_rays);
-    }
     if (!BWD) {
-        for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
-        if ((threadIdx.x & 31) == 0 && my_samples) atomicAdd(A.samples, my_samples);
+        if (lane == 0 && my_samples) atomicAdd(A.samples, my_samples);
+    }
+    if (COUNT) {
+        for (int ofs = 16; ofs > 0; ofs >>= 1) c_brdf += __shfl_xor_sync(0xffffffffu, c_brdf, ofs);
+        if (lane == 0) atomicAdd(A.work + 2, (unsigned long long)c_brdf);
     }
 }
 
@@ -474,67 +829,157 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     A.pixels = f->pixels;
     A.count = f->counters;
     A.W = f->W; A.H = f->H;
-    A.Nd = p->n_direct; A.Nb = p->n_bounce; A.Ns = p->n_light;
+    A.Nd = p->n_direct; A.Nb = p->n_bounce; A.Ns = p->n_bounce > 0 ? p->n_light : 0;
+    A.wd = (p->n_direct + 31) / 32;
+    A.ws = (p->n_bounce > 0 && p->lambda_ind != 0.0f) ? (p->n_bounce * p->n_light + 31) / 32 : 0;
     A.lambda = p->lambda_ind;
     A.metallic = (p->flags & EXM_FLAG_NO_METALLIC) == 0;
     A.key = make_uint2((uint32_t)p->seed, (uint32_t)(p->seed >> 32));
     A.samples = f->samples;
     A.work = f->work;
     A.status = ctx->d_status;
+    const size_t P = (size_t)f->views * f->W * f->H;
+    A.visbits = f->bits;
+    A.secbits = f->bits ? f->bits + P * A.wd : nullptr;
+    A.hits = f->hits;
+    A.rays = f->rays;
     return A;
 }
 
+// Kernel timing (EXM_FLAG_TIME_KERNELS): events around each launch of the four main kernels.
+static void time_begin(exm_frame* f, const exm_params* p, int which, cudaStream_t s) {
+    if (!(p->flags & EXM_FLAG_TIME_KERNELS)) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    f->timers.push_back({which, a, b});
+}
+static void time_end(exm_frame* f, const exm_params* p, cudaStream_t s) {
+    if (!(p->flags & EXM_FLAG_TIME_KERNELS) || f->timers.empty()) return;
+    cudaEventRecord(f->timers.back().end, s);
+}
+
 template <bool BWD, bool COUNT>
-static exm_status launch_t(const ShadeArgs& A, exm_dtype dt, int blocks, cudaStream_t s) {
+static void launch_shade_t(const ShadeArgs& A, exm_dtype dt, int blocks, cudaStream_t s) {
     switch (dt) {
-        case EXM_F32: shade_kernel<float, BWD, COUNT><<<blocks, 128, 0, s>>>(A); break;
-        case EXM_BF16: shade_kernel<__nv_bfloat16, BWD, COUNT><<<blocks, 128, 0, s>>>(A); break;
-        case EXM_F16: shade_kernel<__half, BWD, COUNT><<<blocks, 128, 0, s>>>(A); break;
-        default: return exm_fail(EXM_ERR_ARG, "map dtype");
+        case EXM_F32: shade_kernel<float, BWD, COUNT><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
+        case EXM_BF16: shade_kernel<__nv_bfloat16, BWD, COUNT><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
+        default: shade_kernel<__half, BWD, COUNT><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
     }
-    return exm_cuda_check(cudaGetLastError(), "shade launch");
 }
 
 template <bool BWD>
-static exm_status launch(const ShadeArgs& A, exm_dtype dt, int blocks, cudaStream_t s, bool count) {
-    return count ? launch_t<BWD, true>(A, dt, blocks, s) : launch_t<BWD, false>(A, dt, blocks, s);
+static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, exm_dtype dt,
+                               cudaStream_t s) {
+    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, "map dtype");
+    const int blocks = ctx->num_sms * 4;
+    time_begin(f, p, BWD ? 3 : 2, s);
+    if (p->flags & EXM_FLAG_COUNT_WORK) launch_shade_t<BWD, true>(A, dt, blocks, s);
+    else launch_shade_t<BWD, false>(A, dt, blocks, s);
+    time_end(f, p, s);
+    ctx->launches += 1;
+    return exm_cuda_check(cudaGetLastError(), "shade launch");
+}
+
+template <bool CLOSEST>
+static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, cudaStream_t s) {
+    const int blocks = ctx->num_sms * 8;
+    time_begin(f, p, CLOSEST ? 1 : 0, s);
+    if (p->flags & EXM_FLAG_COUNT_WORK) trace_kernel<CLOSEST, true><<<blocks, 128, 0, s>>>(A);
+    else trace_kernel<CLOSEST, false><<<blocks, 128, 0, s>>>(A);
+    time_end(f, p, s);
+    ctx->launches += 1;
+}
+
+template <typename TT>
+static bool ensure(TT** ptr, size_t* cap, size_t need) {
+    if (need <= *cap && *ptr) return true;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void**)ptr, need * sizeof(TT)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *cap = need;
+    return true;
 }
 
 exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
                                   const exm_env* e, exm_frame* f, const exm_params* p, float* out, cudaStream_t s) {
+    const size_t P = (size_t)f->views * f->W * f->H;
+    const int wd = (p->n_direct + 31) / 32;
+    const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
+    const int ws = indirect ? (p->n_bounce * p->n_light + 31) / 32 : 0;
+    if (!ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)kRayCap * 2) ||
+        (indirect && !ensure(&f->hits, &f->hits_cap, P * (size_t)p->n_bounce)))
+        return exm_fail(EXM_ERR_OOM, "wavefront buffers");
+    const uint32_t per_pixel = (uint32_t)max(wd * 32 + ws * 32, indirect ? p->n_bounce : 1);
+    const uint32_t Pc = max(32u, (kRayCap / per_pixel) & ~31u);
+    const size_t nchunks = (P + Pc - 1) / Pc;
+    if (!ensure(&f->ctr, &f->ctr_cap, nchunks * 4)) return exm_fail(EXM_ERR_OOM, "chunk counters");
     ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
     A.out = out;
     cudaMemsetAsync(f->samples, 0, sizeof(unsigned long long), s);
-    cudaMemsetAsync(out, 0, (size_t)f->views * f->W * f->H * 3 * sizeof(float), s);
-    bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
-    if (count) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
-    return launch<false>(A, dt, ctx->num_sms * 8, s, count);
+    cudaMemsetAsync(out, 0, P * 3 * sizeof(float), s);
+    cudaMemsetAsync(f->bits, 0, P * (size_t)(wd + ws) * sizeof(uint32_t), s);
+    cudaMemsetAsync(f->ctr, 0, nchunks * 4 * sizeof(uint32_t), s);
+    if (indirect) cudaMemsetAsync(f->hits, 0xff, P * (size_t)p->n_bounce * sizeof(int32_t), s);
+    if (p->flags & EXM_FLAG_COUNT_WORK) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
+    for (size_t ch = 0; ch < nchunks; ++ch) {
+        A.chunk_begin = (uint32_t)(ch * Pc);
+        A.chunk_pixels = Pc;
+        A.ctr = f->ctr + 4 * ch;
+        if (indirect) {
+            gen_secondary_kernel<<<exm_blocks((size_t)Pc, 256), 256, 0, s>>>(A);
+            launch_trace<true>(ctx, f, p, A, s);
+            ctx->launches += 1;
+        }
+        gen_direct_kernel<<<exm_blocks((size_t)Pc * ((p->n_direct + kGenK - 1) / kGenK), 256), 256, 0, s>>>(A);
+        ctx->launches += 1;
+        if (indirect) {
+            gen_seclight_kernel<<<exm_blocks((size_t)Pc, 256), 256, 0, s>>>(A);
+            ctx->launches += 1;
+        }
+        launch_trace<false>(ctx, f, p, A, s);
+    }
+    exm_status st = exm_cuda_check(cudaGetLastError(), "wavefront launch");
+    if (st != EXM_OK) return st;
+    f->last_wd = wd;
+    f->last_ws = ws;
+    f->last_nb = indirect ? p->n_bounce : 0;
+    f->last_ns = indirect ? p->n_light : 0;
+    f->last_nd = p->n_direct;
+    return launch_shade<false>(ctx, f, p, A, dt, s);
+}
+
+static exm_status check_saved(const exm_frame* f, const exm_params* p) {
+    const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
+    if (f->last_nd != p->n_direct || f->last_nb != (indirect ? p->n_bounce : 0) ||
+        f->last_ns != (indirect ? p->n_light : 0) || !f->bits)
+        return exm_fail(EXM_ERR_ARG, "backward: the frame holds no forward pass with these sample counts");
+    return EXM_OK;
 }
 
 exm_status exm_shade_backward_impl(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
                                    const exm_env* e, exm_frame* f, const exm_params* p, const float* grad_rgb,
                                    float* grad_maps, float* grad_env, float* grad_V, cudaStream_t s) {
+    exm_status st = check_saved(f, p);
+    if (st != EXM_OK) return st;
     ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
     A.grad_rgb = grad_rgb;
     A.gmaps = grad_maps;
     size_t nenv = (size_t)e->W * e->H;
-    if (nenv > f->genv_capacity) {
-        cudaFree(f->genv);
-        f->genv = nullptr;
-        if (cudaMalloc(&f->genv, nenv * sizeof(float4)) != cudaSuccess) { f->genv_capacity = 0; return exm_fail(EXM_ERR_OOM, "env gradient"); }
-        f->genv_capacity = nenv;
-    }
+    if (!ensure(&f->genv, &f->genv_capacity, nenv)) return exm_fail(EXM_ERR_OOM, "env gradient");
     size_t nfr = (size_t)(m->nv > m->nuv ? m->nv : m->nuv);
-    if (grad_V && nfr > f->gframe_capacity) {
-        cudaFree(f->gnrm);
-        cudaFree(f->gtan);
-        f->gnrm = f->gtan = nullptr;
-        if (cudaMalloc(&f->gnrm, nfr * sizeof(float4)) != cudaSuccess ||
-            cudaMalloc(&f->gtan, nfr * sizeof(float4)) != cudaSuccess) {
-            f->gframe_capacity = 0;
-            return exm_fail(EXM_ERR_OOM, "frame gradient");
-        }
-        f->gframe_capacity = nfr;
+    if (grad_V && (!ensure(&f->gnrm, &f->gframe_capacity, nfr) || !ensure(&f->gtan, &f->gtan_capacity, nfr)))
+        return exm_fail(EXM_ERR_OOM, "frame gradient");
+    if (p->flags & EXM_FLAG_COUNT_WORK) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
+    if (p->flags & EXM_FLAG_ZERO_GRADS) {
+        if (grad_maps) cudaMemsetAsync(grad_maps, 0, (size_t)mapW * mapH * 8 * sizeof(float), s);
+        if (grad_env) cudaMemsetAsync(grad_env, 0, nenv * 3 * sizeof(float), s);
+        if (grad_V) cudaMemsetAsync(grad_V, 0, (size_t)m->nv * 3 * sizeof(float), s);
     }
     cudaMemsetAsync(f->genv, 0, nenv * sizeof(float4), s);
     A.genv = f->genv;
@@ -545,19 +990,16 @@ exm_status exm_shade_backward_impl(exm_ctx* ctx, const exm_mesh* m, const void* 
         A.gnrm = f->gnrm;
         A.gtan = f->gtan;
     }
-    bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
-    if (count) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
-    if (p->flags & EXM_FLAG_ZERO_GRADS) {
-        if (grad_maps) cudaMemsetAsync(grad_maps, 0, (size_t)mapW * mapH * 8 * sizeof(float), s);
-        if (grad_env) cudaMemsetAsync(grad_env, 0, nenv * 3 * sizeof(float), s);
-        if (grad_V) cudaMemsetAsync(grad_V, 0, (size_t)m->nv * 3 * sizeof(float), s);
-    }
-    exm_status st = launch<true>(A, dt, ctx->num_sms * 8, s, count);
+    st = launch_shade<true>(ctx, f, p, A, dt, s);
     if (st != EXM_OK) return st;
-    if (grad_env) env_grad_finish_kernel<<<exm_blocks(nenv, 256), 256, 0, s>>>(f->genv, (int)nenv, grad_env);
+    if (grad_env) {
+        env_grad_finish_kernel<<<exm_blocks(nenv, 256), 256, 0, s>>>(f->genv, (int)nenv, grad_env);
+        ctx->launches += 1;
+    }
     if (grad_V) {
         st = exm_frames_adjoint(const_cast<exm_mesh*>(m), f->gnrm, f->gtan, grad_V, s);
         if (st != EXM_OK) return st;
+        ctx->launches += 3;
     }
     return exm_cuda_check(cudaGetLastError(), "backward finish");
 }
@@ -647,9 +1089,12 @@ extern "C" exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* 
             if (grad_env) cudaMemsetAsync(grad_env, 0, nenv * 3 * sizeof(float), s);
         }
         cudaMemsetAsync(scratch, 0, nenv * sizeof(float4), s);
-        st = launch<true>(A, dt, ctx->num_sms * 8, s, false);
-        if (st == EXM_OK && grad_env)
+        st = check_saved(f, p);
+        if (st == EXM_OK) st = launch_shade<true>(ctx, f, p, A, dt, s);
+        if (st == EXM_OK && grad_env) {
             env_grad_finish_kernel<<<exm_blocks(nenv, 256), 256, 0, s>>>(scratch, (int)nenv, grad_env);
+            ctx->launches += 1;
+        }
         if (st == EXM_OK) st = exm_cuda_check(cudaGetLastError(), "exm_render_backward_noalloc launch");
     }
     if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);

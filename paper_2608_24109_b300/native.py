@@ -29,12 +29,14 @@ FLAG_WRAP_U = 1
 FLAG_NO_METALLIC = 2
 FLAG_COUNT_WORK = 4
 FLAG_ZERO_GRADS = 8
+FLAG_TIME_KERNELS = 16
 
 EXPORTS = [
     "exm_create", "exm_destroy", "exm_last_error", "exm_sync",
     "exm_mesh_create", "exm_mesh_update_vertices", "exm_bvh_build", "exm_mesh_destroy", "exm_mesh_frames",
     "exm_env_create", "exm_env_prepare", "exm_env_destroy", "exm_env_total",
-    "exm_frame_create", "exm_frame_destroy", "exm_frame_stats", "exm_frame_work", "exm_frame_visbuf",
+    "exm_frame_create", "exm_frame_destroy", "exm_frame_stats", "exm_frame_work", "exm_frame_kernel_ms",
+    "exm_launch_count", "exm_frame_visbuf",
     "exm_render_forward", "exm_render_backward", "exm_render_backward_noalloc", "exm_l1_loss",
 ]
 
@@ -82,6 +84,8 @@ def lib():
         "exm_frame_destroy": ([P], None),
         "exm_frame_stats": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
         "exm_frame_work": ([P, ctypes.POINTER(U64 * 4)], I),
+        "exm_frame_kernel_ms": ([P, ctypes.POINTER(ctypes.c_float * 4)], I),
+        "exm_launch_count": ([P, ctypes.POINTER(U64)], I),
         "exm_frame_visbuf": ([P, PP], I),
         "exm_render_forward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P], I),
         "exm_render_backward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
@@ -210,6 +214,18 @@ def exm_frame_work(frame):
     c = (ctypes.c_uint64 * 4)()
     check(lib().exm_frame_work(frame, ctypes.byref(c)))
     return list(c)
+
+
+def exm_frame_kernel_ms(frame):
+    ms = (ctypes.c_float * 4)()
+    check(lib().exm_frame_kernel_ms(frame, ctypes.byref(ms)))
+    return list(ms)
+
+
+def exm_launch_count(ctx):
+    n = ctypes.c_uint64()
+    check(lib().exm_launch_count(ctx, ctypes.byref(n)))
+    return n.value
 
 
 def exm_frame_visbuf(frame):
