@@ -394,9 +394,13 @@ __global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
 
 // ------------------------------------------------------------------ persistent tracer
 // Any-hit (shadow rays -> visibility bits) or closest-hit (secondary rays -> hit ids) over
-// the chunk's ray queue.  A warp takes 32 consecutive queue entries at a time (the same
-// sample index of 32 neighbouring pixels, so the rays are coherent) and traces them to
-// completion before taking the next batch.
+// the chunk's ray queue.  A warp claims a pool of kPool consecutive queue entries (the same
+// few sample indices of 32 neighbouring pixels) and its lanes refill themselves from that
+// pool whenever their ray is done, so no lane idles while the longest ray of the warp
+// finishes, and the rays a warp holds stay local to one group of pixels.
+constexpr uint32_t kPool = 256;
+constexpr int kRound = 16;  // node visits between refills
+
 template <bool CLOSEST, bool COUNT>
 __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
     const uint32_t* qcount = A.ctr + (CLOSEST ? 0 : 2);
@@ -404,24 +408,47 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
     const uint32_t n = *qcount;
     if (n == 0) return;
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
     int stack[kStackSize];
+    int sp = 0, node = 0, best = -1, steps = 0;
+    float bt = INFINITY, bdet = 0.0f;
+    bool active = false;
+    Ray r;
+    r.o = s3(0.f, 0.f, 0.f); r.d = s3(0.f, 0.f, 1.f);
+    r.kx = 0; r.ky = 1; r.kz = 2; r.Sx = r.Sy = 0.f; r.Sz = 1.f; r.inv = make_float3(0.f, 0.f, 1.f);
+    uint64_t slot = 0;
+    uint32_t pnext = 0, pend = 0;  // warp-uniform pool [pnext, pend)
+    bool drained = false;          // warp-uniform: the queue has no more pools
     while (true) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(cursor, 32u);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n) break;
-        const uint32_t my = base + lane;
-        if (my >= n) continue;
-        const float4 a = A.rays[2 * (size_t)my], b = A.rays[2 * (size_t)my + 1];
-        const Ray r = make_ray(s3(a.x, a.y, a.z), s3(a.w, b.x, b.y));
-        const uint64_t slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
-        ++c_rays;
-        int sp = 0, node = 0, best = -1;
-        float bt = INFINITY, bdet = 0.0f;
-        bool hit = false;
-        for (int steps = 0;; ++steps) {
-            if (steps >= kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; break; }
+        const unsigned need = __ballot_sync(0xffffffffu, !active);
+        if (need && pnext >= pend && !drained) {
+            uint32_t b = 0;
+            if (lane == 0) b = atomicAdd(cursor, kPool);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (b >= n) drained = true;
+            else { pnext = b; pend = min(b + kPool, n); }
+        }
+        if (need && pnext < pend) {
+            const uint32_t my = pnext + (uint32_t)__popc(need & lt);
+            if (!active && my < pend) {
+                const float4 a = A.rays[2 * (size_t)my], b = A.rays[2 * (size_t)my + 1];
+                r = make_ray(s3(a.x, a.y, a.z), s3(a.w, b.x, b.y));
+                slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
+                sp = 0; node = 0; best = -1; steps = 0; bt = INFINITY; bdet = 0.0f;
+                active = true;
+                ++c_rays;
+            }
+            pnext = min(pnext + (uint32_t)__popc(need), pend);
+        }
+        if (!__any_sync(0xffffffffu, active)) {
+            if (drained) break;
+            continue;
+        }
+        if (!active) continue;
+        bool done = false, hit = false;
+        for (int it = 0; it < kRound; ++it) {
+            if (++steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
             ++c_nodes;
             const float4 n0 = __ldg(A.bvh.nodes + 4 * node), n1 = __ldg(A.bvh.nodes + 4 * node + 1);
             const float4 n2 = __ldg(A.bvh.nodes + 4 * node + 2), n3 = __ldg(A.bvh.nodes + 4 * node + 3);
@@ -434,7 +461,7 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
                 float T, det;
                 int id;
                 if (tri_test(A.bvh, ~ca, r, &T, &det, &id)) {
-                    if (!CLOSEST) { hit = true; break; }
+                    if (!CLOSEST) { hit = true; done = true; break; }
                     const float t = sdiv(T, det);
                     if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
                 }
@@ -445,7 +472,7 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
                 float T, det;
                 int id;
                 if (tri_test(A.bvh, ~cb, r, &T, &det, &id)) {
-                    if (!CLOSEST) { hit = true; break; }
+                    if (!CLOSEST) { hit = true; done = true; break; }
                     const float t = sdiv(T, det);
                     if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
                 }
@@ -457,7 +484,7 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
             }
             int next;
             if (ha && hb) {
-                if (sp >= kStackSize) { err |= ERRBIT_TRAVERSAL; hit = true; break; }
+                if (sp >= kStackSize) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
                 const bool afirst = ta <= tb;
                 stack[sp++] = afirst ? cb : ca;
                 next = afirst ? ca : cb;
@@ -466,17 +493,20 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
             } else if (hb) {
                 next = cb;
             } else {
-                if (sp == 0) break;
+                if (sp == 0) { done = true; break; }
                 next = stack[--sp];
             }
             node = next;
         }
-        if (CLOSEST) {
-            A.hits[slot] = (best >= 0 && bdet > 0.0f) ? best : -1;
-        } else if (!hit) {
-            const uint64_t bit = slot & ~(1ull << 63);
-            uint32_t* words = (slot >> 63) ? A.secbits : A.visbits;
-            atomicOr(words + (bit >> 5), 1u << (uint32_t)(bit & 31));
+        if (done) {
+            if (CLOSEST) {
+                A.hits[slot] = (best >= 0 && bdet > 0.0f) ? best : -1;
+            } else if (!hit) {
+                const uint64_t bit = slot & ~(1ull << 63);
+                uint32_t* words = (slot >> 63) ? A.secbits : A.visbits;
+                atomicOr(words + (bit >> 5), 1u << (uint32_t)(bit & 31));
+            }
+            active = false;
         }
     }
     if (err) atomicOr(A.status, err);
@@ -884,7 +914,7 @@ static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, 
 
 template <bool CLOSEST>
 static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, cudaStream_t s) {
-    const int blocks = ctx->num_sms * 8;
+    const int blocks = ctx->num_sms * 10;
     time_begin(f, p, CLOSEST ? 1 : 0, s);
     if (p->flags & EXM_FLAG_COUNT_WORK) trace_kernel<CLOSEST, true><<<blocks, 128, 0, s>>>(A);
     else trace_kernel<CLOSEST, false><<<blocks, 128, 0, s>>>(A);
