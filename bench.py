@@ -49,6 +49,12 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=384, help="pixels of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--relight", action="store_true", help="relight-serving benchmark (Poisson arrivals)")
+    ap.add_argument("--assets", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=400)
+    ap.add_argument("--rate", type=float, default=200.0, help="offered requests per second")
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--budget-gb", type=int, default=24)
     return ap.parse_args()
 
 
@@ -341,10 +347,91 @@ def run_native(args, world, rank, local):
     r.close()
 
 
+def run_relight(args, world, rank, local):
+    """Relight serving: Poisson arrivals of relight renders over resident assets."""
+    import math
+
+    import numpy as np
+    import torch
+
+    from paper_2608_24109_b300 import build as libbuild
+    from paper_2608_24109_b300 import scenes
+    from paper_2608_24109_b300.serve import RelightServer
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    rng = np.random.default_rng(5)
+    srv = RelightServer(hbm_budget_bytes=args.budget_gb << 30, max_slots=args.slots, device=local)
+    ids, tris = [], []
+    for a in range(args.assets):
+        t = math.exp(rng.uniform(math.log(1e4), math.log(2e6)))
+        n = max(8, int(round(math.sqrt(t / 12.0))))
+        res = int(rng.choice([512, 1024, 2048, 4096]))
+        ra = np.random.default_rng(1000 + a)
+        V, F, UV, Fuv = scenes.cube_sphere(n, res, ra, dents=int(ra.integers(0, 4)))
+        maps = torch.as_tensor(scenes.material_maps(ra, res)).to(torch.bfloat16)
+        ids.append(srv.add_asset(V, F, UV, Fuv, maps))
+        tris.append(F.shape[0])
+    envs = [torch.as_tensor(scenes.env_map(np.random.default_rng(w + v), w, h, 1.5), device=dev)
+            for (w, h) in [(256, 128), (512, 256), (1024, 512)] for v in range(2)]
+
+    def make(k):
+        r2 = np.random.default_rng(10_000 + k)
+        res = int(r2.choice([256, 512, 1024]))
+        d = r2.normal(size=3)
+        d = 3.0 * d / np.linalg.norm(d)
+        cams = np.stack([scenes.look_at_camera(d, res, res)])
+        return srv.request(ids[int(r2.integers(0, len(ids)))], envs[int(r2.integers(0, len(envs)))], cams, res, res,
+                           n_direct=64, n_bounce=4, n_light=4, seed=k)
+
+    total = args.warmup * 8 + args.requests
+    gaps = np.random.default_rng(6).exponential(1.0 / args.rate, total)
+    arrivals = np.cumsum(gaps)
+    reqs = [make(k) for k in range(total)]
+    clocks = Clocks(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    inflight, lat, done_at = {}, {}, {}
+    nxt = 0
+    while len(lat) < total:
+        now = time.perf_counter() - t0
+        while nxt < total and arrivals[nxt] <= now:
+            inflight[srv.submit(reqs[nxt])] = nxt
+            nxt += 1
+        for tk in list(inflight):
+            d, _, _ = srv.poll(tk)
+            if d:
+                k = inflight.pop(tk)
+                tnow = time.perf_counter() - t0
+                lat[k] = 1e3 * (tnow - arrivals[k])
+                done_at[k] = tnow
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    meas = list(range(args.warmup * 8, total))
+    L = np.array([lat[k] for k in meas])
+    span = max(done_at[k] for k in meas) - arrivals[meas[0]]
+    line = {"metric": "relight latency p99 (p50 beside) at offered rate", "value": float(np.percentile(L, 99)),
+            "unit": "ms", "higher_is_better": False, "p50_ms": float(np.percentile(L, 50)),
+            "p99_ms": float(np.percentile(L, 99)), "mean_ms": float(L.mean()), "frames_per_s": len(meas) / span,
+            "offered_req_per_s": args.rate, "requests": len(meas), "warmup_requests": args.warmup * 8,
+            "n_gpus": 1, "dtype": "bf16 maps, f32 shading", "data": "synthetic",
+            "config": {"workload": f"relight serving: {args.assets} resident assets, 10K-2M tris (log-uniform, "
+                                   f"{min(tris)}-{max(tris)}), maps 512^2-4096^2 BF16, env 256x128-1024x512, "
+                                   f"outputs 256^2-1024^2, 64 direct + 4 secondary x 4 light samples/px, Poisson "
+                                   f"arrivals", "slots": args.slots, "hbm_budget_gb": args.budget_gb},
+            "clocks": ck}
+    print(json.dumps(line), flush=True)
+    srv.close()
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
-    if args.impl == "reference":
+    if args.relight:
+        if rank == 0:
+            run_relight(args, world, rank, local)
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_native(args, world, rank, local)

@@ -162,6 +162,51 @@ exm_status exm_render_backward(exm_ctx* ctx, const exm_mesh* mesh, const void* m
                                const exm_params* params, exm_frame* frame, const float* grad_rgb,
                                float* grad_maps, float* grad_env, float* grad_V, void* stream);
 
+/* ------------------------------------------------- relight serving (Sec. 6.6 relighting) */
+
+typedef struct exm_server exm_server;
+
+/* One relight request: a resident asset rendered under a new environment map (forward only,
+ * Eqs. 10-20).  env: DEVICE [env_h, env_w, 3] of env_dtype and out_rgb: DEVICE float32
+ * [views, height, width, 3], both owned by the caller and kept alive until the request
+ * completes; cams: HOST array of `views` cameras, copied at submission. */
+typedef struct {
+    int32_t asset;
+    int32_t views, width, height;
+    const void* env;
+    exm_dtype env_dtype;
+    int32_t env_w, env_h;
+    const exm_camera* cams;
+    exm_params params;
+    float* out_rgb;
+} exm_relight_req;
+
+/* A relight server on `ctx`: `max_slots` request slots, each with its own CUDA stream, and an
+ * HBM budget (bytes) bounding the device footprint of the requests in flight.  Requests are
+ * admitted in arrival order whenever a slot is free and the head request fits the budget,
+ * so requests that arrive while others run start as soon as resources free up, and the work
+ * of all in-flight requests overlaps on the device. */
+exm_status exm_server_create(exm_ctx* ctx, uint64_t hbm_budget_bytes, int max_slots, exm_server** out);
+void exm_server_destroy(exm_server* server);
+/* Registers a resident asset (mesh with BVH and DEVICE maps [mapH, mapW, 8]); the caller
+ * keeps both alive for the server's lifetime.  *asset_id receives its index. */
+exm_status exm_server_add_asset(exm_server* server, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
+                                int mapW, int mapH, int32_t* asset_id);
+/* Queues a request and runs the scheduler; *ticket identifies it.  EXM_ERR_BUSY when the
+ * request alone exceeds the budget. */
+exm_status exm_relight_submit(exm_server* server, const exm_relight_req* req, uint64_t* ticket);
+/* Non-blocking: runs the scheduler, then reports whether `ticket` is done and its latency
+ * (submission to observed completion, milliseconds).  A done ticket is forgotten after the
+ * call that reports it; that call returns the request's status. */
+exm_status exm_relight_poll(exm_server* server, uint64_t ticket, int* done, double* latency_ms);
+/* Runs the scheduler once (retire finished requests, admit queued ones). */
+exm_status exm_server_progress(exm_server* server);
+/* Queue length, requests in flight, budgeted bytes in use, requests completed. */
+exm_status exm_server_stats(exm_server* server, uint64_t* queued, uint64_t* in_flight, uint64_t* bytes_in_use,
+                            uint64_t* completed);
+/* Device footprint the server budgets for `req`. */
+exm_status exm_relight_footprint(exm_server* server, const exm_relight_req* req, uint64_t* bytes);
+
 /* Backward pass without device allocation (no counterpart in the paper).
  *
  * For callers that must not call cudaMalloc while they run -- a host whose device memory

@@ -63,6 +63,15 @@ __global__ void exm_l1_kernel(const float* __restrict__ pred, const float* __res
     }
 }
 
+// Uploads the cameras unless they equal the frame's last upload (a copy from pageable host
+// memory waits for the stream to drain, so repeated renders of the same views skip it).
+exm_status upload_cameras(exm_frame* f, const exm_camera* cams, int views, cudaStream_t s) {
+    const size_t bytes = (size_t)views * sizeof(exm_camera);
+    if (f->cams_host.size() == bytes && memcmp(f->cams_host.data(), cams, bytes) == 0) return EXM_OK;
+    f->cams_host.assign((const unsigned char*)cams, (const unsigned char*)cams + bytes);
+    return exm_cuda_check(cudaMemcpyAsync(f->cams, cams, bytes, cudaMemcpyHostToDevice, s), "camera upload");
+}
+
 extern "C" {
 
 const char* exm_last_error(void) { return g_last_error.c_str(); }
@@ -113,7 +122,8 @@ exm_status exm_sync(exm_ctx* c, void* stream) {
 // ------------------------------------------------------------------------ mesh
 
 static void mesh_free(exm_mesh* m) {
-    void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nodes, m->tris,
+    void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nfix, m->tfix,
+                    m->nodes, m->tris,
                     m->codes, m->codes_sorted, m->ids, m->ids_sorted, m->parent, m->child, m->flags, m->bounds,
                     m->scene_box, m->sort_tmp};
     for (void* p : ptrs) cudaFree(p);
@@ -137,7 +147,8 @@ exm_status exm_mesh_create(exm_ctx* c, const float* V, int nv, const int32_t* F,
               alloc((void**)&m->UV, (size_t)nuv * 8) && alloc((void**)&m->Fuv, (size_t)nf * 12) &&
               alloc((void**)&m->nacc, (size_t)nv * 12) && alloc((void**)&m->nrm, (size_t)nv * 12) &&
               alloc((void**)&m->tacc, (size_t)nuv * 12) && alloc((void**)&m->tan, (size_t)nuv * 12) &&
-              alloc((void**)&m->fsign, (size_t)nf * 4);
+              alloc((void**)&m->fsign, (size_t)nf * 4) && alloc((void**)&m->nfix, (size_t)nv * 24) &&
+              alloc((void**)&m->tfix, (size_t)nuv * 24);
     if (!ok) {
         cudaGetLastError();
         mesh_free(m);
@@ -372,8 +383,7 @@ exm_status exm_render_forward(exm_ctx* c, const exm_mesh* m, const void* maps, e
     if (!out_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_forward: out_rgb is NULL");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    st = exm_cuda_check(cudaMemcpyAsync(f->cams, cams, (size_t)views * sizeof(exm_camera), cudaMemcpyHostToDevice, s),
-                        "camera upload");
+    st = upload_cameras(f, cams, views, s);
     if (st != EXM_OK) return st;
     st = exm_raster_impl(c, m, f, views, s);
     if (st != EXM_OK) return st;
@@ -389,8 +399,7 @@ exm_status exm_render_backward(exm_ctx* c, const exm_mesh* m, const void* maps, 
     if (!grad_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_backward: grad_rgb is NULL");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    st = exm_cuda_check(cudaMemcpyAsync(f->cams, cams, (size_t)views * sizeof(exm_camera), cudaMemcpyHostToDevice, s),
-                        "camera upload");
+    st = upload_cameras(f, cams, views, s);
     if (st != EXM_OK) return st;
     return exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, f, p, grad_rgb, grad_maps, grad_env, grad_V, s);
 }

@@ -93,7 +93,8 @@ struct Ray {
     S3 o, d;
     int kx, ky, kz;
     float Sx, Sy, Sz;
-    float3 inv;  // 1/d for the (padded, conservative) box test
+    float3 inv;   // 1/d for the (padded, conservative) box test
+    float3 oinv;  // -o/d
 };
 
 __device__ __forceinline__ Ray make_ray(S3 o, S3 d) {
@@ -110,6 +111,7 @@ __device__ __forceinline__ Ray make_ray(S3 o, S3 d) {
     r.Sy = sdiv(scomp(d, ky), dz);
     r.Sz = sdiv(1.0f, dz);
     r.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
+    r.oinv = make_float3(-o.x * r.inv.x, -o.y * r.inv.y, -o.z * r.inv.z);
     return r;
 }
 
@@ -265,11 +267,12 @@ struct BvhView {
 };
 
 __device__ __forceinline__ bool slab(float3 lo, float3 hi, const Ray& r, float tmax, float* tnear) {
-    float tx0 = (lo.x - r.o.x) * r.inv.x, tx1 = (hi.x - r.o.x) * r.inv.x;
-    float ty0 = (lo.y - r.o.y) * r.inv.y, ty1 = (hi.y - r.o.y) * r.inv.y;
-    float tz0 = (lo.z - r.o.z) * r.inv.z, tz1 = (hi.z - r.o.z) * r.inv.z;
-    float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    // (lo - o) / d as lo * (1/d) + (-o/d): one FFMA per plane
+    const float tx0 = fmaf(lo.x, r.inv.x, r.oinv.x), tx1 = fmaf(hi.x, r.inv.x, r.oinv.x);
+    const float ty0 = fmaf(lo.y, r.inv.y, r.oinv.y), ty1 = fmaf(hi.y, r.inv.y, r.oinv.y);
+    const float tz0 = fmaf(lo.z, r.inv.z, r.oinv.z), tz1 = fmaf(hi.z, r.inv.z, r.oinv.z);
+    const float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
     *tnear = t0;
     return t0 <= t1;
 }

@@ -15,9 +15,19 @@ __device__ __forceinline__ float uv_sign(const float* UV, int a, int b, int c) {
     return det < 0.0f ? -1.0f : 1.0f;
 }
 
+// The sums are accumulated in 64-bit fixed point (2^-40 units): integer addition is
+// associative, so the frames do not depend on the order in which faces are summed and
+// every upload of the same mesh yields bit-identical normals and tangents.
+constexpr double kFix = 1099511627776.0;  // 2^40
+
+__device__ __forceinline__ void fix_add(unsigned long long* p, float v) {
+    atomicAdd(p, (unsigned long long)(long long)llrint((double)v * kFix));
+}
+
 __global__ void frames_accumulate_kernel(const float* __restrict__ V, const int32_t* __restrict__ F,
                                          const float* __restrict__ UV, const int32_t* __restrict__ Fuv, int nf,
-                                         int nv, int nuv, float* nacc, float* tacc, float* fsign, uint32_t* status) {
+                                         int nv, int nuv, unsigned long long* nacc, unsigned long long* tacc,
+                                         float* fsign, uint32_t* status) {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= nf) return;
     int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
@@ -33,9 +43,9 @@ __global__ void frames_accumulate_kernel(const float* __restrict__ V, const int3
     float3 fn = cross(e1, e2);
     int idx[3] = {i0, i1, i2};
     for (int k = 0; k < 3; ++k) {
-        atomicAdd(nacc + 3 * idx[k], fn.x);
-        atomicAdd(nacc + 3 * idx[k] + 1, fn.y);
-        atomicAdd(nacc + 3 * idx[k] + 2, fn.z);
+        fix_add(nacc + 3 * idx[k], fn.x);
+        fix_add(nacc + 3 * idx[k] + 1, fn.y);
+        fix_add(nacc + 3 * idx[k] + 2, fn.z);
     }
     float s = uv_sign(UV, u0, u1, u2);
     fsign[f] = s;
@@ -43,16 +53,19 @@ __global__ void frames_accumulate_kernel(const float* __restrict__ V, const int3
     float3 tf = s * (dv2 * e1 - dv1 * e2);
     int uidx[3] = {u0, u1, u2};
     for (int k = 0; k < 3; ++k) {
-        atomicAdd(tacc + 3 * uidx[k], tf.x);
-        atomicAdd(tacc + 3 * uidx[k] + 1, tf.y);
-        atomicAdd(tacc + 3 * uidx[k] + 2, tf.z);
+        fix_add(tacc + 3 * uidx[k], tf.x);
+        fix_add(tacc + 3 * uidx[k] + 1, tf.y);
+        fix_add(tacc + 3 * uidx[k] + 2, tf.z);
     }
 }
 
-__global__ void normalize_rows_kernel(const float* __restrict__ acc, int n, float* out) {
+// Fixed-point sums -> float sums (kept for the adjoint) and unit vectors.
+__global__ void normalize_rows_kernel(const unsigned long long* __restrict__ fix, int n, float* acc, float* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float3 a = ld3(acc + 3 * i);
+    float3 a = f3((float)((double)(long long)fix[3 * i] / kFix), (float)((double)(long long)fix[3 * i + 1] / kFix),
+                  (float)((double)(long long)fix[3 * i + 2] / kFix));
+    acc[3 * i] = a.x; acc[3 * i + 1] = a.y; acc[3 * i + 2] = a.z;
     float l2 = dot(a, a);
     float3 u = l2 > 0.0f ? rsqrtf(l2) * a : f3(0.0f, 0.0f, 1.0f);
     out[3 * i] = u.x; out[3 * i + 1] = u.y; out[3 * i + 2] = u.z;
@@ -102,12 +115,12 @@ __global__ void frames_adjoint_kernel(const float* __restrict__ V, const int32_t
 using namespace exm;
 
 exm_status exm_frames_build(exm_mesh* m, cudaStream_t s) {
-    cudaMemsetAsync(m->nacc, 0, (size_t)m->nv * 3 * 4, s);
-    cudaMemsetAsync(m->tacc, 0, (size_t)m->nuv * 3 * 4, s);
+    cudaMemsetAsync(m->nfix, 0, (size_t)m->nv * 3 * 8, s);
+    cudaMemsetAsync(m->tfix, 0, (size_t)m->nuv * 3 * 8, s);
     frames_accumulate_kernel<<<exm_blocks(m->nf, 256), 256, 0, s>>>(m->V, m->F, m->UV, m->Fuv, m->nf, m->nv, m->nuv,
-                                                                   m->nacc, m->tacc, m->fsign, m->ctx->d_status);
-    normalize_rows_kernel<<<exm_blocks(m->nv, 256), 256, 0, s>>>(m->nacc, m->nv, m->nrm);
-    normalize_rows_kernel<<<exm_blocks(m->nuv, 256), 256, 0, s>>>(m->tacc, m->nuv, m->tan);
+                                                                   m->nfix, m->tfix, m->fsign, m->ctx->d_status);
+    normalize_rows_kernel<<<exm_blocks(m->nv, 256), 256, 0, s>>>(m->nfix, m->nv, m->nacc, m->nrm);
+    normalize_rows_kernel<<<exm_blocks(m->nuv, 256), 256, 0, s>>>(m->tfix, m->nuv, m->tacc, m->tan);
     m->ctx->launches += 3;
     return exm_cuda_check(cudaGetLastError(), "frames launch");
 }

@@ -28,6 +28,8 @@ struct exm_mesh {
     float* tacc = nullptr;     // [nuv,3] sum of incident face tangents
     float* tan = nullptr;      // [nuv,3] unit UV-vertex tangents
     float* fsign = nullptr;    // [nf] UV handedness (+1 / -1)
+    unsigned long long* nfix = nullptr;  // [nv,3] fixed-point normal sums
+    unsigned long long* tfix = nullptr;  // [nuv,3] fixed-point tangent sums
     // BVH
     float4* nodes = nullptr;   // [max(nf-1,1) * 4]
     float4* tris = nullptr;    // [nf * 3]
@@ -69,6 +71,7 @@ struct exm_frame {
     unsigned long long* samples = nullptr;  // [1] shaded samples of the last forward
     unsigned long long* work = nullptr;     // [4] work counters of the last counted pass
     void* cams = nullptr;         // device copy of the cameras [views]
+    std::vector<unsigned char> cams_host;  // host copy of the last uploaded cameras
     int32_t* XY = nullptr;        // [views*nv*2] snapped coordinates (sized on demand)
     uint32_t* Zq = nullptr;       // [views*nv]
     size_t snap_capacity = 0;     // vertices * views the snap buffers hold
@@ -85,6 +88,7 @@ struct exm_frame {
     size_t hits_cap = 0;
     float4* rays = nullptr;       // ray queue of one chunk
     size_t rays_cap = 0;
+    uint32_t ray_cap = 0;         // rays per chunk (0: the default of 2^24)
     uint32_t* ctr = nullptr;      // per chunk: queued / fetched counters
     size_t ctr_cap = 0;
     int last_nd = -1, last_nb = -1, last_ns = -1, last_wd = 0, last_ws = 0;
@@ -95,6 +99,8 @@ struct exm_frame {
 // error helpers (exm_api.cu)
 exm_status exm_fail(exm_status code, const std::string& msg);
 exm_status exm_cuda_check(cudaError_t e, const char* what);
+
+exm_status upload_cameras(exm_frame* f, const exm_camera* cams, int views, cudaStream_t s);
 
 // kernels launchers
 exm_status exm_frames_build(exm_mesh* m, cudaStream_t s);

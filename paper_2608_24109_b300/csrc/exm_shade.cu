@@ -28,7 +28,7 @@ namespace exm {
 
 constexpr int kShadeWarps = 8;        // warps per block of the shade kernel
 constexpr int kListMax = 1024;        // sample slots enumerated per round (32 bit words)
-constexpr uint32_t kRayCap = 1u << 24; // queued rays per chunk (2 float4 each, 512 MiB)
+constexpr uint32_t kRayCapDefault = 1u << 24; // queued rays per chunk (2 float4 each, 512 MiB)
 
 struct ShadeArgs {
     // mesh
@@ -58,7 +58,8 @@ struct ShadeArgs {
     uint32_t* visbits;   // [P * wd]
     uint32_t* secbits;   // [P * ws]
     int32_t* hits;       // [P * Nb] closest front-facing hit of each secondary ray, -1 if none
-    float4* rays;        // queue: [kRayCap * 2]
+    float4* rays;        // queue: [ray_cap * 2]
+    uint32_t ray_cap;
     uint32_t* ctr;       // per chunk: [0] queued, [1] fetch cursor (x2: closest, any)
     uint32_t chunk_begin, chunk_pixels;
     // outputs
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
         }
         const uint32_t idx = warp_append(A.ctr + 2, want);
         if (want) {
-            if (idx < kRayCap) push_ray(A.rays, idx, org, dir, (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)k);
+            if (idx < A.ray_cap) push_ray(A.rays, idx, org, dir, (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)k);
             else atomicOr(A.status, ERRBIT_TRAVERSAL);
         }
     }
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(256) gen_secondary_kernel(ShadeArgs A) {
         }
         const uint32_t idx = warp_append(A.ctr, valid);
         if (valid) {
-            if (idx < kRayCap) push_ray(A.rays, idx, org, wjs, (uint64_t)i * (uint32_t)A.Nb + (uint32_t)j);
+            if (idx < A.ray_cap) push_ray(A.rays, idx, org, wjs, (uint64_t)i * (uint32_t)A.Nb + (uint32_t)j);
             else atomicOr(A.status, ERRBIT_TRAVERSAL);
         }
     }
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
             const uint32_t idx = warp_append(A.ctr + 2, want);
             if (want) {
                 const uint64_t slot = (uint64_t)i * (uint32_t)A.ws * 32u + (uint32_t)(j * A.Ns + s);
-                if (idx < kRayCap) push_ray(A.rays, idx, yorg, dir, slot | (1ull << 63));
+                if (idx < A.ray_cap) push_ray(A.rays, idx, yorg, dir, slot | (1ull << 63));
                 else atomicOr(A.status, ERRBIT_TRAVERSAL);
             }
         }
@@ -417,6 +418,7 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
     Ray r;
     r.o = s3(0.f, 0.f, 0.f); r.d = s3(0.f, 0.f, 1.f);
     r.kx = 0; r.ky = 1; r.kz = 2; r.Sx = r.Sy = 0.f; r.Sz = 1.f; r.inv = make_float3(0.f, 0.f, 1.f);
+    r.oinv = make_float3(0.f, 0.f, 0.f);
     uint64_t slot = 0;
     uint32_t pnext = 0, pend = 0;  // warp-uniform pool [pnext, pend)
     bool drained = false;          // warp-uniform: the queue has no more pools
@@ -942,14 +944,16 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     const int wd = (p->n_direct + 31) / 32;
     const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
     const int ws = indirect ? (p->n_bounce * p->n_light + 31) / 32 : 0;
-    if (!ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)kRayCap * 2) ||
+    const uint32_t ray_cap = f->ray_cap ? f->ray_cap : kRayCapDefault;
+    if (!ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)ray_cap * 2) ||
         (indirect && !ensure(&f->hits, &f->hits_cap, P * (size_t)p->n_bounce)))
         return exm_fail(EXM_ERR_OOM, "wavefront buffers");
     const uint32_t per_pixel = (uint32_t)max(wd * 32 + ws * 32, indirect ? p->n_bounce : 1);
-    const uint32_t Pc = max(32u, (kRayCap / per_pixel) & ~31u);
+    const uint32_t Pc = max(32u, (ray_cap / per_pixel) & ~31u);
     const size_t nchunks = (P + Pc - 1) / Pc;
     if (!ensure(&f->ctr, &f->ctr_cap, nchunks * 4)) return exm_fail(EXM_ERR_OOM, "chunk counters");
     ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
+    A.ray_cap = ray_cap;
     A.out = out;
     cudaMemsetAsync(f->samples, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(out, 0, P * 3 * sizeof(float), s);
@@ -1105,8 +1109,7 @@ extern "C" exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* 
     float4* scratch = nullptr;
     exm_status st = static_scratch(ctx->device, &scratch);
     if (st == EXM_OK)
-        st = exm_cuda_check(cudaMemcpyAsync(f->cams, cams, (size_t)views * sizeof(exm_camera), cudaMemcpyHostToDevice, s),
-                            "camera upload");
+        st = upload_cameras(f, cams, views, s);
     if (st == EXM_OK) {
         size_t nenv = (size_t)e->W * e->H;
         ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);

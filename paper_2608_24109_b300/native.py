@@ -38,6 +38,8 @@ EXPORTS = [
     "exm_frame_create", "exm_frame_destroy", "exm_frame_stats", "exm_frame_work", "exm_frame_kernel_ms",
     "exm_launch_count", "exm_frame_visbuf",
     "exm_render_forward", "exm_render_backward", "exm_render_backward_noalloc", "exm_l1_loss",
+    "exm_server_create", "exm_server_destroy", "exm_server_add_asset", "exm_relight_submit", "exm_relight_poll",
+    "exm_server_progress", "exm_server_stats", "exm_relight_footprint",
 ]
 
 
@@ -51,6 +53,13 @@ class Params(ctypes.Structure):
     _fields_ = [("n_direct", ctypes.c_int32), ("n_bounce", ctypes.c_int32), ("n_light", ctypes.c_int32),
                 ("lambda_ind", ctypes.c_float), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64)]
+
+
+class RelightReq(ctypes.Structure):
+    _fields_ = [("asset", ctypes.c_int32), ("views", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("env", ctypes.c_void_p), ("env_dtype", ctypes.c_int),
+                ("env_w", ctypes.c_int32), ("env_h", ctypes.c_int32), ("cams", ctypes.c_void_p), ("params", Params),
+                ("out_rgb", ctypes.c_void_p)]
 
 
 _lib = None
@@ -91,6 +100,15 @@ def lib():
         "exm_render_backward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
         "exm_render_backward_noalloc": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P], I),
         "exm_l1_loss": ([P, P, I64, P, P, P], I),
+        "exm_server_create": ([P, U64, I, PP], I),
+        "exm_server_destroy": ([P], None),
+        "exm_server_add_asset": ([P, P, P, I, I, I, ctypes.POINTER(ctypes.c_int32)], I),
+        "exm_relight_submit": ([P, ctypes.POINTER(RelightReq), ctypes.POINTER(U64)], I),
+        "exm_relight_poll": ([P, U64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], I),
+        "exm_server_progress": ([P], I),
+        "exm_server_stats": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64),
+                              ctypes.POINTER(U64)], I),
+        "exm_relight_footprint": ([P, ctypes.POINTER(RelightReq), ctypes.POINTER(U64)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -264,3 +282,49 @@ def exm_render_backward_noalloc(ctx, mesh, maps, env, cams, params: Params, fram
 
 def exm_l1_loss(pred, target, loss, grad, stream=None):
     return check(lib().exm_l1_loss(_ptr(pred), _ptr(target), pred.numel(), _ptr(loss), _ptr(grad), _stream(stream)))
+
+
+def exm_server_create(ctx, hbm_budget_bytes, max_slots):
+    h = ctypes.c_void_p()
+    check(lib().exm_server_create(ctx, int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)))
+    return h
+
+
+def exm_server_destroy(server):
+    lib().exm_server_destroy(server)
+
+
+def exm_server_add_asset(server, mesh, maps):
+    aid = ctypes.c_int32()
+    check(lib().exm_server_add_asset(server, mesh, _ptr(maps), dtype_code(maps.dtype), maps.shape[1], maps.shape[0],
+                                     ctypes.byref(aid)))
+    return aid.value
+
+
+def exm_relight_submit(server, req: RelightReq):
+    t = ctypes.c_uint64()
+    check(lib().exm_relight_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def exm_relight_poll(server, ticket):
+    done = ctypes.c_int()
+    lat = ctypes.c_double()
+    check(lib().exm_relight_poll(server, ticket, ctypes.byref(done), ctypes.byref(lat)))
+    return bool(done.value), lat.value
+
+
+def exm_server_progress(server):
+    return check(lib().exm_server_progress(server))
+
+
+def exm_server_stats(server):
+    v = [ctypes.c_uint64() for _ in range(4)]
+    check(lib().exm_server_stats(server, *[ctypes.byref(x) for x in v]))
+    return {"queued": v[0].value, "in_flight": v[1].value, "bytes_in_use": v[2].value, "completed": v[3].value}
+
+
+def exm_relight_footprint(server, req: RelightReq):
+    b = ctypes.c_uint64()
+    check(lib().exm_relight_footprint(server, ctypes.byref(req), ctypes.byref(b)))
+    return b.value
