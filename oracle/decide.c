@@ -339,14 +339,38 @@ static uint64_t scaled_target(uint32_t U, uint64_t Q) {
     return (uint64_t)(((unsigned __int128)U * Q) >> 32);
 }
 
-/* Texel choice and in-texel jitter for one light sample.  Returns the texel index. */
-static uint32_t light_sample(const uint64_t* cdf, uint32_t ntex, uint64_t Q, uint32_t k, uint32_t n,
+/* 2D strata of n samples: ny = the largest divisor of n not above sqrt(n), nx = n / ny. */
+void orc_strata2(uint32_t n, uint32_t* nx, uint32_t* ny) {
+    uint32_t best = 1;
+    for (uint32_t d = 1; (uint64_t)d * d <= n; ++d)
+        if (n % d == 0) best = d;
+    *ny = best;
+    *nx = n / best;
+}
+
+/* Texel choice and in-texel jitter for light sample k of n (2D-stratified inversion of the
+ * marginal row distribution, then of the chosen row's conditional column distribution).
+ * Sample k lies in row stratum k / nx and column stratum k % nx.  cdf is the row-major
+ * inclusive prefix; row i ends at cdf[i*W + W - 1].  Returns the texel index. */
+static uint32_t light_sample(const uint64_t* cdf, int W, int H, uint64_t Q, uint32_t k, uint32_t n,
                              const uint32_t h[4], float* xu, float* xv) {
-    uint32_t U = stratified32(k, n, h[0]);
-    uint32_t t = pick_texel(cdf, ntex, scaled_target(U, Q));
+    uint32_t nx, ny;
+    orc_strata2(n, &nx, &ny);
+    uint32_t kx = k % nx, ky = k / nx;
+    uint64_t tr = scaled_target(stratified32(ky, ny, h[0]), Q);
+    int lo = 0, hi = H - 1;
+    while (lo < hi) {
+        int mid = lo + (hi - lo) / 2;
+        if (cdf[(size_t)mid * W + W - 1] > tr) hi = mid; else lo = mid + 1;
+    }
+    int row = lo;
+    uint64_t pre = row ? cdf[(size_t)row * W - 1] : 0;
+    uint64_t rsum = cdf[(size_t)row * W + W - 1] - pre;
+    uint64_t tc = pre + scaled_target(stratified32(kx, nx, h[3]), rsum);
+    uint32_t col = pick_texel(cdf + (size_t)row * W, (uint32_t)W, tc);
     *xu = unit24(h[1]);
     *xv = unit24(h[2]);
-    return t;
+    return (uint32_t)row * (uint32_t)W + col;
 }
 
 /* Direction of a light sample: theta = pi (i + xv) / H from +y, phi = 2 pi (j + xu) / W
@@ -565,7 +589,7 @@ int orc_decide(const float* V, const int32_t* F, int nf, const float* cams, int 
             uint32_t ctr[4] = {pixel, (uint32_t)c, (uint32_t)k, 0u}, h[4];
             orc_philox(ctr, key, h);
             float xu, xv;
-            uint32_t t = light_sample(cdf, ntex, Q, (uint32_t)k, (uint32_t)Nd, h, &xu, &xv);
+            uint32_t t = light_sample(cdf, envW, envH, Q, (uint32_t)k, (uint32_t)Nd, h, &xu, &xv);
             f3 wi = light_dir(t, envW, envH, xu, xv);
             int vis = dot3(ng, wi) > 0.0f && !any_hit(V, F, nf, org, wi);
             dtex[(size_t)p * Nd + k] = (int32_t)t;
@@ -611,7 +635,7 @@ int orc_decide(const float* V, const int32_t* F, int nf, const float* cams, int 
                 uint32_t ctr2[4] = {pixel, (uint32_t)c, (uint32_t)(j * Ns + s), 2u}, h2[4];
                 orc_philox(ctr2, key, h2);
                 float xu, xv;
-                uint32_t tt = light_sample(cdf, ntex, Q, (uint32_t)s, (uint32_t)Ns, h2, &xu, &xv);
+                uint32_t tt = light_sample(cdf, envW, envH, Q, (uint32_t)s, (uint32_t)Ns, h2, &xu, &xv);
                 f3 wl = light_dir(tt, envW, envH, xu, xv);
                 int vis = dot3(ngy, wl) > 0.0f && !any_hit(V, F, nf, yorg, wl);
                 ltex[pjs] = (int32_t)tt;

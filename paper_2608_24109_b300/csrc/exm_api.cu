@@ -125,7 +125,7 @@ static void mesh_free(exm_mesh* m) {
     void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nfix, m->tfix,
                     m->nodes, m->tris,
                     m->codes, m->codes_sorted, m->ids, m->ids_sorted, m->parent, m->child, m->flags, m->bounds,
-                    m->scene_box, m->sort_tmp};
+                    m->scene_box, m->sort_tmp, m->nodes4, m->frontier, m->frontier_cnt};
     for (void* p : ptrs) cudaFree(p);
 }
 
@@ -203,7 +203,7 @@ exm_status exm_mesh_frames(const exm_mesh* m, const float** normals, const float
 // ------------------------------------------------------------------------ env
 
 static void env_free(exm_env* e) {
-    void* ptrs[] = {e->texel, e->q, e->cdf, e->rowsum, e->rowpre, e->guide, e->wbuf, e->wmax, e->total};
+    void* ptrs[] = {e->texel, e->q, e->cdf, e->rowsum, e->rowpre, e->rguide, e->cguide, e->wbuf, e->wmax, e->total};
     for (void* p : ptrs) cudaFree(p);
 }
 
@@ -217,15 +217,17 @@ exm_status exm_env_create(exm_ctx* c, int W, int H, exm_env** out) {
     e->ctx = c;
     e->W = W; e->H = H;
     size_t n = (size_t)W * H;
-    int bits = 1;
-    while ((1u << bits) < n && bits < 23) ++bits;
-    e->gbits = bits + 1;
-    size_t G = ((size_t)1 << e->gbits) + 1;
+    int rb = 1, cb = 1;
+    while ((1 << rb) < H && rb < 20) ++rb;
+    while ((1 << cb) < W && cb < 20) ++cb;
+    e->rbits = rb + 1;
+    e->cbits = cb + 1;
+    size_t Gr = ((size_t)1 << e->rbits) + 1, Gc = (size_t)H * (((size_t)1 << e->cbits) + 1);
     bool ok = cudaMalloc(&e->texel, n * sizeof(float4)) == cudaSuccess && cudaMalloc(&e->q, n * 4) == cudaSuccess &&
               cudaMalloc(&e->cdf, n * 8) == cudaSuccess && cudaMalloc(&e->rowsum, (size_t)H * 8) == cudaSuccess &&
-              cudaMalloc(&e->rowpre, (size_t)H * 8) == cudaSuccess && cudaMalloc(&e->guide, G * 4) == cudaSuccess &&
-              cudaMalloc(&e->wbuf, n * 4) == cudaSuccess && cudaMalloc(&e->wmax, 4) == cudaSuccess &&
-              cudaMalloc(&e->total, 8) == cudaSuccess;
+              cudaMalloc(&e->rowpre, (size_t)H * 8) == cudaSuccess && cudaMalloc(&e->rguide, Gr * 4) == cudaSuccess &&
+              cudaMalloc(&e->cguide, Gc * 4) == cudaSuccess && cudaMalloc(&e->wbuf, n * 4) == cudaSuccess &&
+              cudaMalloc(&e->wmax, 4) == cudaSuccess && cudaMalloc(&e->total, 8) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         env_free(e);

@@ -193,6 +193,65 @@ __global__ void init_box_kernel(uint32_t* box) {
     else if (k < 6) box[k] = 0u;
 }
 
+
+// ---- 4-wide collapse.  A 4-wide node takes the grandchildren of a binary node (a leaf child
+// stays a leaf).  128-byte node: child boxes as lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4],
+// then the four child references (>= 0: node, < 0: leaf ~k, kEmpty: unused slot).
+constexpr int kEmpty4 = 0x7fffffff;
+
+__device__ __forceinline__ int bounds_index(int n, int c) { return c < 0 ? n - 1 + ~c : c; }
+
+__global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
+                                 const int2* __restrict__ in, const uint32_t* __restrict__ n_in, int2* out,
+                                 uint32_t* n_out, uint32_t* n_nodes, float4* nodes4) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *n_in) return;
+    const int b = in[t].x, q = in[t].y;
+    int slots[4];
+    int ns = 0;
+    for (int h = 0; h < 2; ++h) {
+        const int c = child[2 * b + h];
+        if (c < 0) slots[ns++] = c;
+        else { slots[ns++] = child[2 * c]; slots[ns++] = child[2 * c + 1]; }
+    }
+    float v[6][4];
+    int refs[4];
+    for (int k = 0; k < 4; ++k) {
+        if (k < ns) {
+            const float* bb = bounds + 6 * (size_t)bounds_index(n, slots[k]);
+            for (int a = 0; a < 6; ++a) v[a][k] = bb[a];
+            if (slots[k] < 0) refs[k] = slots[k];
+            else {
+                const uint32_t idx = atomicAdd(n_nodes, 1u);
+                refs[k] = (int)idx;
+                const uint32_t o = atomicAdd(n_out, 1u);
+                out[o] = make_int2(slots[k], (int)idx);
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) { v[a][k] = 0.0f; v[3 + a][k] = 0.0f; }
+            refs[k] = kEmpty4;
+        }
+    }
+    float4* N = nodes4 + 8 * (size_t)q;
+    for (int a = 0; a < 6; ++a) N[a] = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+    N[6] = make_float4(__int_as_float(refs[0]), __int_as_float(refs[1]), __int_as_float(refs[2]), __int_as_float(refs[3]));
+    N[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// A one-triangle mesh: a single 4-wide node holding leaf 0.
+__global__ void single4_kernel(const float* __restrict__ bounds, float4* nodes4) {
+    float4* N = nodes4;
+    for (int a = 0; a < 6; ++a) N[a] = make_float4(bounds[a], 0.f, 0.f, 0.f);
+    N[6] = make_float4(__int_as_float(~0), __int_as_float(kEmpty4), __int_as_float(kEmpty4), __int_as_float(kEmpty4));
+    N[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void seed4_kernel(int2* in, uint32_t* n_in, uint32_t* n_nodes) {
+    in[0] = make_int2(0, 0);
+    *n_in = 1;
+    *n_nodes = 1;
+}
+
 }  // namespace exm
 
 using namespace exm;
@@ -210,7 +269,10 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
                   cudaMalloc(&m->bounds, (2 * nn) * 6 * 4) == cudaSuccess &&
                   cudaMalloc(&m->scene_box, 6 * 4) == cudaSuccess &&
                   cudaMalloc(&m->nodes, internal * 4 * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&m->tris, nn * 3 * sizeof(float4)) == cudaSuccess;
+                  cudaMalloc(&m->tris, nn * 3 * sizeof(float4)) == cudaSuccess &&
+                  cudaMalloc(&m->nodes4, internal * 8 * sizeof(float4)) == cudaSuccess &&
+                  cudaMalloc(&m->frontier, 2 * nn * sizeof(int2)) == cudaSuccess &&
+                  cudaMalloc(&m->frontier_cnt, 4 * sizeof(uint32_t)) == cudaSuccess;
         if (!ok) return exm_fail(EXM_ERR_OOM, "BVH buffers");
         size_t bytes = 0;
         cub::DeviceRadixSort::SortPairs(nullptr, bytes, m->codes, m->codes_sorted, m->ids, m->ids_sorted, n, 0, 30, s);
@@ -234,5 +296,27 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
         write_nodes_kernel<<<exm_blocks(n - 1, 256), 256, 0, s>>>(n, m->child, m->bounds, m->nodes);
     else
         single_node_kernel<<<1, 1, 0, s>>>(m->bounds, m->nodes);
+    // collapse to 4-wide nodes, level by level (the frontier size is read back per level)
+    if (n == 1) {
+        single4_kernel<<<1, 1, 0, s>>>(m->bounds, m->nodes4);
+    } else {
+        int2* fin = m->frontier;
+        int2* fout = m->frontier + n;
+        uint32_t* cnt = m->frontier_cnt;  // [0] in, [1] out, [2] nodes
+        seed4_kernel<<<1, 1, 0, s>>>(fin, cnt, cnt + 2);
+        uint32_t n_in = 1;
+        for (int level = 0; level < 64 && n_in > 0; ++level) {
+            cudaMemsetAsync(cnt + 1, 0, 4, s);
+            collapse4_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, fin, cnt, fout, cnt + 1,
+                                                                  cnt + 2, m->nodes4);
+            cudaMemcpyAsync(cnt, cnt + 1, 4, cudaMemcpyDeviceToDevice, s);
+            if (cudaMemcpyAsync(&n_in, cnt + 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return exm_cuda_check(cudaGetLastError(), "BVH collapse");
+            int2* tmp = fin;
+            fin = fout;
+            fout = tmp;
+        }
+    }
     return exm_cuda_check(cudaGetLastError(), "BVH build launch");
 }

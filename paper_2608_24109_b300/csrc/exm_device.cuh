@@ -23,6 +23,8 @@ constexpr float kFDielectric = 0.04f;   // F_dielectric of Eq. 16
 constexpr float kSpecEps = 1e-6f;       // epsilon of Eq. 15
 constexpr float kRMin = 0.08f;          // roughness clamp before alpha = r^2
 constexpr int kStackSize = 64;
+constexpr int kStackSize4 = 96;
+constexpr int kEmptyChild = 0x7fffffff;
 constexpr int kTraversalCap = 1 << 20;
 
 // ------------------------------------------------------------- spec arithmetic
@@ -214,25 +216,51 @@ __device__ __forceinline__ S3 light_dir(int i, int j, int W, int H, float xu, fl
 struct EnvView {
     const float4* texel;     // [H*W]: E.rgb, (q/Q) * W*H / (2 pi^2)
     const uint64_t* cdf;     // [H*W] inclusive prefix of the integer weights (row-major)
-    const uint32_t* guide;   // [G+1]: texel picked at U = g * 2^(32-gbits)
+    const uint32_t* rguide;  // [Gr+1]: row picked at U1 = g * 2^(32-rbits)
+    const uint32_t* cguide;  // [H*(Gc+1)]: column picked in row i at U2 = g * 2^(32-cbits)
     const uint64_t* Qp;      // total of the integer weights (device)
     uint64_t Q;              // loaded from Qp once per thread
     int W, H;
-    int gbits;
+    int rbits, cbits;
 };
 
-// Texel chosen by the 32-bit stratified fraction U: target t = floor(U * Q / 2^32), then
-// the smallest index whose inclusive prefix exceeds t (searched inside the guide bucket).
-__device__ __forceinline__ uint32_t pick_texel(const EnvView& e, uint32_t U) {
-    uint64_t qh = e.Q >> 32, ql = e.Q & 0xffffffffull;
-    uint64_t t = (uint64_t)U * qh + (((uint64_t)U * ql) >> 32);
-    uint32_t g = U >> (32 - e.gbits);
-    uint32_t lo = __ldg(e.guide + g), hi = __ldg(e.guide + g + 1);
+__device__ __forceinline__ uint64_t scaled_target(uint32_t U, uint64_t X) {
+    return (uint64_t)U * (X >> 32) + (((uint64_t)U * (X & 0xffffffffull)) >> 32);
+}
+
+// 2D strata of n samples: ny = the largest divisor of n not above sqrt(n), nx = n / ny.
+__host__ __device__ __forceinline__ void strata2(uint32_t n, uint32_t* nx, uint32_t* ny) {
+    uint32_t best = 1;
+    for (uint32_t d = 1; d * d <= n; ++d)
+        if (n % d == 0) best = d;
+    *ny = best;
+    *nx = n / best;
+}
+
+// Texel chosen by the row fraction U1 and column fraction U2: the row is the smallest i
+// whose inclusive row prefix exceeds floor(U1 Q / 2^32); the column the smallest j of row i
+// whose in-row prefix exceeds floor(U2 rowsum_i / 2^32) (guide tables bound both searches).
+__device__ __forceinline__ uint32_t pick_texel(const EnvView& e, uint32_t U1, uint32_t U2) {
+    const uint64_t tr = scaled_target(U1, e.Q);
+    const uint32_t g = U1 >> (32 - e.rbits);
+    uint32_t lo = __ldg(e.rguide + g), hi = __ldg(e.rguide + g + 1);
     while (lo < hi) {
-        uint32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(e.cdf + mid) > t) hi = mid; else lo = mid + 1;
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(e.cdf + (size_t)mid * e.W + e.W - 1) > tr) hi = mid; else lo = mid + 1;
     }
-    return lo;
+    const uint32_t row = lo;
+    const uint64_t* rc = e.cdf + (size_t)row * e.W;
+    const uint64_t pre = row ? __ldg(rc - 1) : 0ull;
+    const uint64_t tc = pre + scaled_target(U2, __ldg(rc + e.W - 1) - pre);
+    const uint32_t* cg = e.cguide + (size_t)row * ((1u << e.cbits) + 1);
+    const uint32_t g2 = U2 >> (32 - e.cbits);
+    lo = __ldg(cg + g2);
+    hi = __ldg(cg + g2 + 1);
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(rc + mid) > tc) hi = mid; else lo = mid + 1;
+    }
+    return row * (uint32_t)e.W + lo;
 }
 
 struct LightSample {
@@ -242,10 +270,12 @@ struct LightSample {
     uint32_t texel;
 };
 
-__device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, uint32_t k, uint32_t n) {
+// Light sample k of n = nx * ny (strata2): 2D-stratified, row stratum k / nx and column
+// stratum k % nx.
+__device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, uint32_t k, uint32_t nx, uint32_t ny) {
     LightSample s;
-    uint32_t U = stratified32(k, n, h.x);
-    uint32_t t = pick_texel(e, U);
+    const uint32_t kx = k % nx, ky = k / nx;
+    uint32_t t = pick_texel(e, stratified32(ky, ny, h.x), stratified32(kx, nx, h.w));
     float xu = unit24(h.y), xv = unit24(h.z);
     int i = (int)(t / (uint32_t)e.W), j = (int)(t - (uint32_t)i * (uint32_t)e.W);
     float st;
@@ -264,6 +294,7 @@ __device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, u
 struct BvhView {
     const float4* nodes;
     const float4* tris;
+    const float4* nodes4;  // 4-wide nodes (8 float4 each)
 };
 
 __device__ __forceinline__ bool slab(float3 lo, float3 hi, const Ray& r, float tmax, float* tnear) {

@@ -106,21 +106,38 @@ __global__ void env_finish_kernel(int W, int H, const uint64_t* __restrict__ row
     texel[t].w = p;
 }
 
-__global__ void env_guide_kernel(const uint64_t* __restrict__ cdf, uint32_t n, const uint64_t* __restrict__ total,
-                                 int gbits, uint32_t* guide) {
-    uint32_t G = 1u << gbits;
-    uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+// Row guide: the row picked at each U1 = g * 2^(32-rbits); entry Gr is H - 1.
+__global__ void env_row_guide_kernel(const uint64_t* __restrict__ cdf, int W, int H, const uint64_t* __restrict__ total,
+                                     int rbits, uint32_t* rguide) {
+    const uint32_t G = 1u << rbits;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g > G) return;
-    if (g == G) { guide[g] = n - 1; return; }
-    uint32_t U = g << (32 - gbits);
-    uint64_t Q = *total;
-    uint64_t t = (uint64_t)U * (Q >> 32) + (((uint64_t)U * (Q & 0xffffffffull)) >> 32);
-    uint32_t lo = 0, hi = n - 1;
+    if (g == G) { rguide[g] = (uint32_t)H - 1; return; }
+    const uint64_t t = scaled_target(g << (32 - rbits), *total);
+    uint32_t lo = 0, hi = (uint32_t)H - 1;
     while (lo < hi) {
-        uint32_t mid = lo + ((hi - lo) >> 1);
-        if (cdf[mid] > t) hi = mid; else lo = mid + 1;
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (cdf[(size_t)mid * W + W - 1] > t) hi = mid; else lo = mid + 1;
     }
-    guide[g] = lo;
+    rguide[g] = lo;
+}
+
+// Column guides: for each row, the column picked at each U2 = g * 2^(32-cbits).
+__global__ void env_col_guide_kernel(const uint64_t* __restrict__ cdf, int W, int H, int cbits, uint32_t* cguide) {
+    const uint32_t G = 1u << cbits;
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= (size_t)H * (G + 1)) return;
+    const uint32_t row = (uint32_t)(t / (G + 1)), g = (uint32_t)(t % (G + 1));
+    if (g == G) { cguide[t] = (uint32_t)W - 1; return; }
+    const uint64_t* rc = cdf + (size_t)row * W;
+    const uint64_t pre = row ? rc[-1] : 0ull;
+    const uint64_t tc = pre + scaled_target(g << (32 - cbits), rc[W - 1] - pre);
+    uint32_t lo = 0, hi = (uint32_t)W - 1;
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if (rc[mid] > tc) hi = mid; else lo = mid + 1;
+    }
+    cguide[t] = lo;
 }
 
 }  // namespace exm
@@ -149,8 +166,10 @@ exm_status exm_env_prepare_impl(exm_env* e, const void* E, exm_dtype dt, cudaStr
     env_row_kernel<<<e->H, rt, 0, s>>>(e->wbuf, e->W, e->wmax, e->q, e->cdf, e->rowsum);
     env_rows_prefix_kernel<<<1, 32, 0, s>>>(e->rowsum, e->H, e->rowpre, e->total);
     env_finish_kernel<<<blocks, 256, 0, s>>>(e->W, e->H, e->rowpre, e->total, e->q, e->cdf, e->texel);
-    uint32_t G = 1u << e->gbits;
-    env_guide_kernel<<<exm_blocks((size_t)G + 1, 256), 256, 0, s>>>(e->cdf, (uint32_t)n, e->total, e->gbits, e->guide);
-    e->ctx->launches += 5;
+    env_row_guide_kernel<<<exm_blocks(((size_t)1 << e->rbits) + 1, 256), 256, 0, s>>>(e->cdf, e->W, e->H, e->total,
+                                                                                    e->rbits, e->rguide);
+    env_col_guide_kernel<<<exm_blocks((size_t)e->H * (((size_t)1 << e->cbits) + 1), 256), 256, 0, s>>>(
+        e->cdf, e->W, e->H, e->cbits, e->cguide);
+    e->ctx->launches += 6;
     return exm_cuda_check(cudaGetLastError(), "env prepare launch");
 }

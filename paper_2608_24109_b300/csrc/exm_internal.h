@@ -33,6 +33,9 @@ struct exm_mesh {
     // BVH
     float4* nodes = nullptr;   // [max(nf-1,1) * 4]
     float4* tris = nullptr;    // [nf * 3]
+    float4* nodes4 = nullptr;  // [max(nf-1,1) * 8] 4-wide nodes
+    int2* frontier = nullptr;  // [2 * nf] collapse frontier (binary node, 4-wide node)
+    uint32_t* frontier_cnt = nullptr;
     // build scratch
     uint32_t* codes = nullptr;
     uint32_t* codes_sorted = nullptr;
@@ -50,13 +53,14 @@ struct exm_mesh {
 struct exm_env {
     exm_ctx* ctx = nullptr;
     int W = 0, H = 0;
-    int gbits = 0;
+    int rbits = 0, cbits = 0;
     float4* texel = nullptr;      // [H*W] E.rgb, (q/Q) W H / (2 pi^2)
     uint32_t* q = nullptr;        // [H*W]
     uint64_t* cdf = nullptr;      // [H*W] inclusive prefix, row-major
     uint64_t* rowsum = nullptr;   // [H]
     uint64_t* rowpre = nullptr;   // [H] exclusive prefix of the row sums
-    uint32_t* guide = nullptr;    // [2^gbits + 1]
+    uint32_t* rguide = nullptr;   // [2^rbits + 1] row guide
+    uint32_t* cguide = nullptr;   // [H * (2^cbits + 1)] per-row column guides
     float* wbuf = nullptr;        // [H*W] FP32 weights
     uint32_t* wmax = nullptr;     // [1] max weight bits
     uint64_t* total = nullptr;    // [1] Q on the device

@@ -86,9 +86,11 @@ static size_t request_footprint(const exm_server* s, const exm_relight_req& r) {
     size_t frame = P * (8 + 4) + (size_t)r.views * nv * 12 + P * (size_t)(wd + ws) * 4 +
                    (ind ? P * (size_t)r.params.n_bounce * 4 : 0) + (size_t)s->ray_cap * 32 + (size_t)r.views * 80 + 64;
     const size_t n = (size_t)r.env_w * r.env_h;
-    int gb = 1;
-    while (((size_t)1 << gb) < n && gb < 23) ++gb;
-    size_t env = n * (16 + 4 + 8 + 4) + (size_t)r.env_h * 16 + (((size_t)1 << (gb + 1)) + 1) * 4 + 16;
+    int rb = 1, cb = 1;
+    while ((1 << rb) < r.env_h && rb < 20) ++rb;
+    while ((1 << cb) < r.env_w && cb < 20) ++cb;
+    size_t env = n * (16 + 4 + 8 + 4) + (size_t)r.env_h * 16 + (((size_t)1 << (rb + 1)) + 1) * 4 +
+                 (size_t)r.env_h * (((size_t)1 << (cb + 1)) + 1) * 4 + 16;
     return frame + env;
 }
 

@@ -51,6 +51,7 @@ struct ShadeArgs {
     // params
     int Nd, Nb, Ns;
     int wd, ws;        // 32-bit words per pixel of the direct / secondary visibility bits
+    uint32_t nxd, nyd, nxs, nys;  // 2D strata of the direct and secondary light samples
     float lambda;
     bool metallic;
     uint2 key;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
         S3 dir = s3(0.f, 0.f, 0.f);
         if (valid) {
             const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
-            const LightSample ls = light_sample(env, h, (uint32_t)k, (uint32_t)A.Nd);
+            const LightSample ls = light_sample(env, h, (uint32_t)k, A.nxd, A.nyd);
             dir = ls.dir;
             want = sdot(ngs, dir) > 0.0f;
         }
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
             S3 dir = s3(0.f, 0.f, 0.f);
             if (g >= 0) {
                 const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(j * A.Ns + s), 2u), A.key);
-                const LightSample ls = light_sample(env, h, (uint32_t)s, (uint32_t)A.Ns);
+                const LightSample ls = light_sample(env, h, (uint32_t)s, A.nxs, A.nys);
                 dir = ls.dir;
                 want = sdot(ngy, dir) > 0.0f;
             }
@@ -411,7 +412,7 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
-    int stack[kStackSize];
+    int stack[kStackSize4];
     int sp = 0, node = 0, best = -1, steps = 0;
     float bt = INFINITY, bdet = 0.0f;
     bool active = false;
@@ -452,53 +453,58 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
         for (int it = 0; it < kRound; ++it) {
             if (++steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
             ++c_nodes;
-            const float4 n0 = __ldg(A.bvh.nodes + 4 * node), n1 = __ldg(A.bvh.nodes + 4 * node + 1);
-            const float4 n2 = __ldg(A.bvh.nodes + 4 * node + 2), n3 = __ldg(A.bvh.nodes + 4 * node + 3);
-            float ta, tb;
-            bool ha = slab(make_float3(n0.x, n0.y, n0.z), make_float3(n0.w, n1.x, n1.y), r, CLOSEST ? bt : INFINITY, &ta);
-            bool hb = slab(make_float3(n1.z, n1.w, n2.x), make_float3(n2.y, n2.z, n2.w), r, CLOSEST ? bt : INFINITY, &tb);
-            const int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
-            if (ha && ca < 0) {
-                ++c_tris;
-                float T, det;
-                int id;
-                if (tri_test(A.bvh, ~ca, r, &T, &det, &id)) {
-                    if (!CLOSEST) { hit = true; done = true; break; }
-                    const float t = sdiv(T, det);
-                    if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+            const float4* N = A.bvh.nodes4 + 8 * (size_t)node;
+            const float4 lx = __ldg(N), ly = __ldg(N + 1), lz = __ldg(N + 2);
+            const float4 hx = __ldg(N + 3), hy = __ldg(N + 4), hz = __ldg(N + 5), rf = __ldg(N + 6);
+            const float tmax = CLOSEST ? bt : INFINITY;
+            float tc[4];
+            int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
+            bool hc[4];
+            hc[0] = slab(make_float3(lx.x, ly.x, lz.x), make_float3(hx.x, hy.x, hz.x), r, tmax, &tc[0]);
+            hc[1] = slab(make_float3(lx.y, ly.y, lz.y), make_float3(hx.y, hy.y, hz.y), r, tmax, &tc[1]);
+            hc[2] = slab(make_float3(lx.z, ly.z, lz.z), make_float3(hx.z, hy.z, hz.z), r, tmax, &tc[2]);
+            hc[3] = slab(make_float3(lx.w, ly.w, lz.w), make_float3(hx.w, hy.w, hz.w), r, tmax, &tc[3]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (ref[c] == kEmptyChild) hc[c] = false;
+                if (hc[c] && ref[c] < 0) {
+                    ++c_tris;
+                    float T, det;
+                    int id;
+                    if (tri_test(A.bvh, ~ref[c], r, &T, &det, &id)) {
+                        if (!CLOSEST) { hit = true; done = true; }
+                        else {
+                            const float t = sdiv(T, det);
+                            if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+                        }
+                    }
+                    hc[c] = false;
                 }
-                ha = false;
             }
-            if (hb && cb < 0) {
-                ++c_tris;
-                float T, det;
-                int id;
-                if (tri_test(A.bvh, ~cb, r, &T, &det, &id)) {
-                    if (!CLOSEST) { hit = true; done = true; break; }
-                    const float t = sdiv(T, det);
-                    if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+            if (done) break;
+            // internal children: continue with the nearest, push the others (farthest first)
+            int next = -1;
+            float tn = INFINITY;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (CLOSEST && hc[c] && tc[c] > bt) hc[c] = false;
+                if (hc[c] && tc[c] < tn) { tn = tc[c]; next = c; }
+            }
+            bool overflow = false;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (hc[c] && c != next) {
+                    if (sp >= kStackSize4) overflow = true;
+                    else stack[sp++] = ref[c];
                 }
-                hb = false;
             }
-            if (CLOSEST) {
-                if (ha && ta > bt) ha = false;
-                if (hb && tb > bt) hb = false;
-            }
-            int next;
-            if (ha && hb) {
-                if (sp >= kStackSize) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
-                const bool afirst = ta <= tb;
-                stack[sp++] = afirst ? cb : ca;
-                next = afirst ? ca : cb;
-            } else if (ha) {
-                next = ca;
-            } else if (hb) {
-                next = cb;
+            if (overflow) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
+            if (next >= 0) {
+                node = next == 0 ? ref[0] : next == 1 ? ref[1] : next == 2 ? ref[2] : ref[3];
             } else {
                 if (sp == 0) { done = true; break; }
-                next = stack[--sp];
+                node = stack[--sp];
             }
-            node = next;
         }
         if (done) {
             if (CLOSEST) {
@@ -618,7 +624,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
                 if (e < tot) {
                     const int k = wbase * 32 + list[e];
                     const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
-                    const LightSample ls = light_sample(env, h, (uint32_t)k, (uint32_t)A.Nd);
+                    const LightSample ls = light_sample(env, h, (uint32_t)k, A.nxd, A.nyd);
                     const float3 wi = normalize(tof(ls.dir));
                     const float w = ls.inv_pdf * invNd;
                     ++c_brdf;
@@ -682,7 +688,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
                     const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
                     const float3 fdy = ((1.0f - sy.m) / kPi) * sy.a;
                     const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
-                    const LightSample ls = light_sample(env, h2, (uint32_t)s, (uint32_t)A.Ns);
+                    const LightSample ls = light_sample(env, h2, (uint32_t)s, A.nxs, A.nys);
                     const float3 wl = normalize(tof(ls.dir));
                     const float cs = dot(sy.ns, wl);
                     if (cs <= 0.0f) continue;
@@ -851,10 +857,11 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     ShadeArgs A{};
     A.V = m->V; A.F = m->F; A.UV = m->UV; A.Fuv = m->Fuv;
     A.nrm = m->nrm; A.tan = m->tan; A.fsign = m->fsign;
-    A.bvh.nodes = m->nodes; A.bvh.tris = m->tris;
+    A.bvh.nodes = m->nodes; A.bvh.tris = m->tris; A.bvh.nodes4 = m->nodes4;
     A.map.data = maps; A.map.W = mapW; A.map.H = mapH; A.map.wrap_u = (p->flags & EXM_FLAG_WRAP_U) != 0;
-    A.env.texel = e->texel; A.env.cdf = e->cdf; A.env.guide = e->guide; A.env.W = e->W; A.env.H = e->H;
-    A.env.gbits = e->gbits;
+    A.env.texel = e->texel; A.env.cdf = e->cdf; A.env.rguide = e->rguide; A.env.cguide = e->cguide;
+    A.env.W = e->W; A.env.H = e->H;
+    A.env.rbits = e->rbits; A.env.cbits = e->cbits;
     A.env.Qp = e->total;
     A.cams = (const Cam*)f->cams;
     A.visbuf = (const unsigned long long*)f->visbuf;
@@ -864,6 +871,8 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     A.Nd = p->n_direct; A.Nb = p->n_bounce; A.Ns = p->n_bounce > 0 ? p->n_light : 0;
     A.wd = (p->n_direct + 31) / 32;
     A.ws = (p->n_bounce > 0 && p->lambda_ind != 0.0f) ? (p->n_bounce * p->n_light + 31) / 32 : 0;
+    strata2((uint32_t)A.Nd, &A.nxd, &A.nyd);
+    strata2((uint32_t)(A.Ns > 0 ? A.Ns : 1), &A.nxs, &A.nys);
     A.lambda = p->lambda_ind;
     A.metallic = (p->flags & EXM_FLAG_NO_METALLIC) == 0;
     A.key = make_uint2((uint32_t)p->seed, (uint32_t)(p->seed >> 32));
