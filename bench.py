@@ -36,6 +36,8 @@ WORKLOADS = {
                 "256 env samples/px, fwd+bwd to maps, env and vertex positions",
     "indirect": "blob with 3 cavities 499,392 tris, maps 2048^2 FP32, env 512x256, 8 views 800^2, "
                 "128 direct + 8 secondary rays x 4 light samples/px, fwd+bwd",
+    "precision": "blob with 3 cavities 1,997,568 tris, maps 4096^2, env 1024x512, 8 views 1024^2, "
+                 "64 direct + 4 secondary rays x 4 light samples/px, fwd+bwd",
 }
 
 
@@ -49,6 +51,9 @@ def parse():
     ap.add_argument("--cpu-pixels", type=int, default=384, help="pixels of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling cases)")
+    ap.add_argument("--maps", default="fp32", choices=["fp32", "bf16", "fp16"], help="storage type of the UV maps")
+    ap.add_argument("--env-dtype", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--relight", action="store_true", help="relight-serving benchmark (Poisson arrivals)")
     ap.add_argument("--assets", type=int, default=16)
     ap.add_argument("--requests", type=int, default=400)
@@ -204,17 +209,19 @@ def run_native(args, world, rank, local):
     libbuild.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    sc = scenes.config(args.workload)
+    sc = scenes.config(args.workload, **({"views": args.views} if args.views else {}))
     r = Renderer.from_scene(sc, device=local)
-    M = torch.as_tensor(sc.maps, device=dev)
-    Mt = torch.as_tensor(sc.maps_target, device=dev)
-    E = torch.as_tensor(sc.env, device=dev)
+    mdt = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[args.maps]
+    edt = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[args.env_dtype]
+    M = torch.as_tensor(sc.maps).to(mdt).to(dev)
+    Mt = torch.as_tensor(sc.maps_target).to(mdt).to(dev)
+    E = torch.as_tensor(sc.env).to(edt).to(dev)
     target = r.forward(Mt, E).clone()
     img = torch.empty_like(target)
     grad = torch.empty_like(target)
     loss = torch.zeros(1, device=dev)
-    gm = torch.zeros_like(M)
-    gE = torch.zeros_like(E)
+    gm = torch.zeros(M.shape, dtype=torch.float32, device=dev)
+    gE = torch.zeros(E.shape, dtype=torch.float32, device=dev)
     gV = torch.zeros((sc.V.shape[0], 3), device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     base_flags = r.params.flags
@@ -280,8 +287,8 @@ def run_native(args, world, rank, local):
     # end to end through the public API: host inputs in, loss out, every step
     e2e = None
     if not args.no_e2e:
-        Mh = torch.as_tensor(sc.maps).pin_memory()
-        Eh = torch.as_tensor(sc.env).pin_memory()
+        Mh = M.cpu().pin_memory()
+        Eh = E.cpu().pin_memory()
         lh = torch.zeros(1).pin_memory()
         te = []
         for k in range(args.warmup + args.steps):
@@ -321,7 +328,7 @@ def run_native(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload + ": " + WORKLOADS[args.workload],
-                   "covered_pixels": covered, "shaded_samples_per_step": samples,
+                   "map_storage": args.maps, "env_storage": args.env_dtype, "covered_pixels": covered, "shaded_samples_per_step": samples,
                    "l2": "flushed between steps (256 MiB write outside the timed region)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "ms_forward": mf, "ms_backward": mb,

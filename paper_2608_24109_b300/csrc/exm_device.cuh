@@ -97,7 +97,21 @@ struct Ray {
     float Sx, Sy, Sz;
     float3 inv;   // 1/d for the (padded, conservative) box test
     float3 oinv;  // -o/d
+    int nx, ny, nz;  // 0 when the near plane of that axis is the box's lo, 3 when it is hi
 };
+
+// 3-input minimum / maximum (PTX min.f32 / max.f32 with three operands; a NaN operand is
+// ignored, which keeps the box test conservative for axis-parallel rays).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
 
 __device__ __forceinline__ Ray make_ray(S3 o, S3 d) {
     Ray r;
@@ -114,6 +128,9 @@ __device__ __forceinline__ Ray make_ray(S3 o, S3 d) {
     r.Sz = sdiv(1.0f, dz);
     r.inv = make_float3(1.0f / d.x, 1.0f / d.y, 1.0f / d.z);
     r.oinv = make_float3(-o.x * r.inv.x, -o.y * r.inv.y, -o.z * r.inv.z);
+    r.nx = r.inv.x >= 0.0f ? 0 : 3;
+    r.ny = r.inv.y >= 0.0f ? 0 : 3;
+    r.nz = r.inv.z >= 0.0f ? 0 : 3;
     return r;
 }
 

@@ -403,8 +403,11 @@ __global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
 constexpr uint32_t kPool = 256;
 constexpr int kRound = 16;  // node visits between refills
 
+constexpr int kTraceThreads = 128;
+
 template <bool CLOSEST, bool COUNT>
-__global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
+__global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
+    int stack[kStackSize4];
     const uint32_t* qcount = A.ctr + (CLOSEST ? 0 : 2);
     uint32_t* cursor = A.ctr + (CLOSEST ? 1 : 3);
     const uint32_t n = *qcount;
@@ -412,7 +415,6 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
-    int stack[kStackSize4];
     int sp = 0, node = 0, best = -1, steps = 0;
     float bt = INFINITY, bdet = 0.0f;
     bool active = false;
@@ -454,16 +456,28 @@ __global__ void __launch_bounds__(128) trace_kernel(ShadeArgs A) {
             if (++steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
             ++c_nodes;
             const float4* N = A.bvh.nodes4 + 8 * (size_t)node;
-            const float4 lx = __ldg(N), ly = __ldg(N + 1), lz = __ldg(N + 2);
-            const float4 hx = __ldg(N + 3), hy = __ldg(N + 4), hz = __ldg(N + 5), rf = __ldg(N + 6);
+            // near / far planes of each axis chosen by the ray's direction signs
+            const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
+            const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
+            const float4 rf = __ldg(N + 6);
             const float tmax = CLOSEST ? bt : INFINITY;
             float tc[4];
             int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
             bool hc[4];
-            hc[0] = slab(make_float3(lx.x, ly.x, lz.x), make_float3(hx.x, hy.x, hz.x), r, tmax, &tc[0]);
-            hc[1] = slab(make_float3(lx.y, ly.y, lz.y), make_float3(hx.y, hy.y, hz.y), r, tmax, &tc[1]);
-            hc[2] = slab(make_float3(lx.z, ly.z, lz.z), make_float3(hx.z, hy.z, hz.z), r, tmax, &tc[2]);
-            hc[3] = slab(make_float3(lx.w, ly.w, lz.w), make_float3(hx.w, hy.w, hz.w), r, tmax, &tc[3]);
+#define EXM_BOX(C, c)                                                                                          \
+    {                                                                                                          \
+        const float t0 = fmaxf(fmax3(fmaf(qx.c, r.inv.x, r.oinv.x), fmaf(qy.c, r.inv.y, r.oinv.y),                \
+                                     fmaf(qz.c, r.inv.z, r.oinv.z)), 0.0f);                                    \
+        const float t1 = fminf(fmin3(fmaf(fx.c, r.inv.x, r.oinv.x), fmaf(fy.c, r.inv.y, r.oinv.y),                \
+                                     fmaf(fz.c, r.inv.z, r.oinv.z)), tmax);                                    \
+        tc[C] = t0;                                                                                            \
+        hc[C] = t0 <= t1;                                                                                      \
+    }
+            EXM_BOX(0, x)
+            EXM_BOX(1, y)
+            EXM_BOX(2, z)
+            EXM_BOX(3, w)
+#undef EXM_BOX
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 if (ref[c] == kEmptyChild) hc[c] = false;
@@ -925,10 +939,10 @@ static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, 
 
 template <bool CLOSEST>
 static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, cudaStream_t s) {
-    const int blocks = ctx->num_sms * 10;
+    const int blocks = ctx->num_sms * 8;
     time_begin(f, p, CLOSEST ? 1 : 0, s);
-    if (p->flags & EXM_FLAG_COUNT_WORK) trace_kernel<CLOSEST, true><<<blocks, 128, 0, s>>>(A);
-    else trace_kernel<CLOSEST, false><<<blocks, 128, 0, s>>>(A);
+    if (p->flags & EXM_FLAG_COUNT_WORK) trace_kernel<CLOSEST, true><<<blocks, kTraceThreads, 0, s>>>(A);
+    else trace_kernel<CLOSEST, false><<<blocks, kTraceThreads, 0, s>>>(A);
     time_end(f, p, s);
     ctx->launches += 1;
 }

@@ -341,6 +341,8 @@ def config(name: str, **overrides) -> Scene:
     * ``geometry``  blob 99,372 tris, maps 1024^2, env 256x128, 16 x 512^2, 256 spp, direct only
     * ``indirect``  blob 499,392 tris with 3 cavities, maps 2048^2, env 512x256, 8 x 800^2,
                     128 direct + 8 secondary rays x 4 light samples
+    * ``precision`` blob 1,997,568 tris with 3 cavities, maps 4096^2 (stored BF16/FP16 by the
+                    caller), env 1024x512, 8 x 1024^2, 64 direct + 4 secondary rays x 4 light samples
     """
     if name == "tiny":
         kw = dict()
@@ -354,6 +356,11 @@ def config(name: str, **overrides) -> Scene:
     if name == "indirect":
         kw = dict(n=204, map_res=2048, env_w=512, env_h=256, env_sigma=1.5, views=8, res=800,
                   n_direct=128, n_bounce=8, n_light=4, dents=3, seed=3)
+        kw.update(overrides)
+        return blob_scene(**kw)
+    if name == "precision":
+        kw = dict(n=408, map_res=4096, env_w=1024, env_h=512, env_sigma=1.5, views=8, res=1024,
+                  n_direct=64, n_bounce=4, n_light=4, dents=3, seed=4)
         kw.update(overrides)
         return blob_scene(**kw)
     raise KeyError(name)

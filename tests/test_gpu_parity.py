@@ -318,3 +318,31 @@ def test_guard_band_error_from_device():
         r.sync()
     assert e.value.code == N.EXM_ERR_GUARDBAND
     r.sync()  # latched error was cleared
+
+
+@pytest.mark.parametrize("mdt", [torch.bfloat16, torch.float16])
+def test_precision_form_sampled(mdt):
+    """2M-triangle precision workload with maps stored in BF16/FP16 and the environment in
+    FP16 (shading, accumulation and gradients in FP32): radiance on pixels sampled from the
+    256^2 centre crop of view 0 against the FP64 oracle fed the same rounded values."""
+    sc = scenes.config("precision", views=1)
+    Mq = torch.as_tensor(sc.maps).to(mdt)
+    Eq = torch.as_tensor(sc.env).to(torch.float16)
+    sc.env = Eq.float().numpy()
+    r = _renderer(sc)
+    out = r.forward(Mq.cuda().contiguous(), Eq.cuda().contiguous())
+    r.sync()
+    vis = keys_u64(r.visbuf())
+    c0 = (sc.width - 256) // 2
+    crop = vis[0, c0:c0 + 256, c0:c0 + 256]
+    cov = np.argwhere((crop & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF))
+    rng = np.random.default_rng(4)
+    pick = cov[rng.choice(cov.shape[0], 24, replace=False)]
+    sel = np.concatenate([np.zeros((24, 1), np.int64), pick + c0], 1).astype(np.int32)
+    st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, sel)
+    assert np.array_equal(keys, vis[sel[:, 0], sel[:, 1], sel[:, 2]])
+    tab = oracle.EnvTable(sc.env)
+    dec = oracle.Decisions(sc, tab, sel, keys)
+    V, _, Eo = shade.scene_tensors(sc)
+    I = shade.render_image(sc, tab, dec, V, Mq.to(torch.float64), Eo).numpy()
+    check_radiance(out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]], I, f"precision form {mdt}")
