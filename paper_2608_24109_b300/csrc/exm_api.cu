@@ -262,7 +262,7 @@ exm_status exm_env_total(exm_env* e, uint64_t* Q) {
 
 static void frame_free(exm_frame* f) {
     void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY,   f->Zq,
-                    f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr};
+                    f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr, f->prec};
     for (void* p : ptrs) cudaFree(p);
     for (auto& t : f->timers) {
         cudaEventDestroy(t.begin);

@@ -86,6 +86,8 @@ struct exm_frame {
     size_t gframe_capacity = 0;
     size_t gtan_capacity = 0;
     // wavefront state of the last forward
+    float4* prec = nullptr;       // [P * 5] per-pixel shading records
+    size_t prec_cap = 0;
     uint32_t* bits = nullptr;     // visibility bits: [P * wd] direct, then [P * ws] secondary
     size_t bits_cap = 0;
     int32_t* hits = nullptr;      // [P * Nb] secondary closest front-facing hit, -1 if none

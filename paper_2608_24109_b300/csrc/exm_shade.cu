@@ -26,7 +26,8 @@
 
 namespace exm {
 
-constexpr int kShadeWarps = 8;        // warps per block of the shade kernel
+constexpr int kShadeWarps = 4;        // warps per block of the shade kernel
+constexpr int kPrec = 5;              // float4 per pixel record (pixel_prep_kernel)
 constexpr int kListMax = 1024;        // sample slots enumerated per round (32 bit words)
 constexpr uint32_t kRayCapDefault = 1u << 24; // queued rays per chunk (2 float4 each, 512 MiB)
 
@@ -59,6 +60,7 @@ struct ShadeArgs {
     uint32_t* visbits;   // [P * wd]
     uint32_t* secbits;   // [P * ws]
     int32_t* hits;       // [P * Nb] closest front-facing hit of each secondary ray, -1 if none
+    float4* prec;        // [P * 5] per-pixel shading record (pixel_prep_kernel)
     float4* rays;        // queue: [ray_cap * 2]
     uint32_t ray_cap;
     uint32_t* ctr;       // per chunk: [0] queued, [1] fetch cursor (x2: closest, any)
@@ -293,7 +295,9 @@ __global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
     if (valid) {
         const uint32_t pid = A.pixels[i];
         pixel_of(A, pid, &c, &px, &py, &rem);
-        pixel_geometry(A, pid, &org, &ngs);
+        const float4 r3 = A.prec[kPrec * (size_t)i + 3], r4 = A.prec[kPrec * (size_t)i + 4];
+        org = s3(r3.x, r3.y, r3.z);
+        ngs = s3(r3.w, r4.x, r4.y);
     }
     const int k0 = (int)kc * kGenK, k1 = min(A.Nd, k0 + kGenK);
     for (int k = k0; k < k1; ++k) {
@@ -329,7 +333,9 @@ __global__ void __launch_bounds__(256) gen_secondary_kernel(ShadeArgs A) {
     if (valid) {
         const uint32_t pid = A.pixels[i];
         pixel_of(A, pid, &c, &px, &py, &rem);
-        pixel_geometry(A, pid, &org, &ngs);
+        const float4 r3 = A.prec[kPrec * (size_t)i + 3], r4 = A.prec[kPrec * (size_t)i + 4];
+        org = s3(r3.x, r3.y, r3.z);
+        ngs = s3(r3.w, r4.x, r4.y);
     }
     for (int j = 0; j < A.Nb; ++j) {
         S3 wjs = s3(0.f, 0.f, 0.f);
@@ -363,7 +369,9 @@ __global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
     if (valid) {
         const uint32_t pid = A.pixels[i];
         pixel_of(A, pid, &c, &px, &py, &rem);
-        pixel_geometry(A, pid, &org, &ngs);
+        const float4 r3 = A.prec[kPrec * (size_t)i + 3], r4 = A.prec[kPrec * (size_t)i + 4];
+        org = s3(r3.x, r3.y, r3.z);
+        ngs = s3(r3.w, r4.x, r4.y);
     }
     for (int j = 0; j < A.Nb; ++j) {
         const int g = valid ? A.hits[(size_t)i * A.Nb + j] : -1;
@@ -565,7 +573,113 @@ __device__ __forceinline__ int enumerate_bits(const uint32_t* words, int wbase, 
     return tot;
 }
 
-template <typename T, bool BWD, bool COUNT>
+// Per-pixel record, computed once per covered pixel (one thread each) so that the FP64
+// shading geometry is not repeated by every lane of the warp-per-pixel kernels:
+//   [0] b0 b1 b2 |eye-x|   [1] w_o.xyz fs   [2] ft i0 j0 -   [3] org.xyz ng.x   [4] ng.y ng.z - -
+// (b: FP64 barycentrics of the camera ray; (i0 + fs, j0 + ft): texel-space position of the
+// shading point; org / ng: the spec ray origin and geometric normal).
+__global__ void __launch_bounds__(256) pixel_prep_kernel(ShadeArgs A) {
+    const uint32_t total = *A.count;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t pid = A.pixels[i];
+        int c, px, py;
+        uint32_t rem;
+        pixel_of(A, pid, &c, &px, &py, &rem);
+        const int f = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
+        const Cam& cam = A.cams[c];
+        S3 org, ngs;
+        pixel_geometry(A, pid, &org, &ngs);
+        const int i0 = __ldg(A.F + 3 * f), i1 = __ldg(A.F + 3 * f + 1), i2 = __ldg(A.F + 3 * f + 2);
+        const int u0 = __ldg(A.Fuv + 3 * f), u1 = __ldg(A.Fuv + 3 * f + 1), u2 = __ldg(A.Fuv + 3 * f + 2);
+        const float3 P0 = ld3(A.V + 3 * i0), P1 = ld3(A.V + 3 * i1), P2 = ld3(A.V + 3 * i2);
+        const D3 eyed = d3(cam.eye[0], cam.eye[1], cam.eye[2]);
+        const double dxd = ((double)px + 0.5 - (double)cam.cx) / (double)cam.kx;
+        const double dyd = ((double)cam.cy - ((double)py + 0.5)) / (double)cam.ky;
+        const D3 dd = d3(cam.fwd[0] + dxd * cam.right[0] + dyd * cam.up[0], cam.fwd[1] + dxd * cam.right[1] + dyd * cam.up[1],
+                         cam.fwd[2] + dxd * cam.right[2] + dyd * cam.up[2]);
+        double bd[3];
+        bary_d(eyed, dd, dof(P0), dof(P1), dof(P2), bd);
+        const double sd = (bd[0] * __ldg(A.UV + 2 * u0) + bd[1] * __ldg(A.UV + 2 * u1) + bd[2] * __ldg(A.UV + 2 * u2)) *
+                              A.map.W - 0.5;
+        const double td = (bd[0] * __ldg(A.UV + 2 * u0 + 1) + bd[1] * __ldg(A.UV + 2 * u1 + 1) +
+                           bd[2] * __ldg(A.UV + 2 * u2 + 1)) * A.map.H - 0.5;
+        const double si = floor(sd), tj = floor(td);
+        const D3 vod = dsub(eyed, d3(bd[0] * P0.x + bd[1] * P1.x + bd[2] * P2.x, bd[0] * P0.y + bd[1] * P1.y + bd[2] * P2.y,
+                                     bd[0] * P0.z + bd[1] * P1.z + bd[2] * P2.z));
+        const double vold = sqrt(ddot(vod, vod));
+        const int ii = (int)fmax(fmin(si, 1e9), -1e9), jj = (int)fmax(fmin(tj, 1e9), -1e9);
+        float4* R = A.prec + kPrec * (size_t)i;
+        R[0] = make_float4((float)bd[0], (float)bd[1], (float)bd[2], (float)vold);
+        R[1] = make_float4((float)(vod.x / vold), (float)(vod.y / vold), (float)(vod.z / vold), (float)(sd - si));
+        R[2] = make_float4((float)(td - tj), __int_as_float(ii), __int_as_float(jj), 0.0f);
+        R[3] = make_float4(org.x, org.y, org.z, ngs.x);
+        R[4] = make_float4(ngs.y, ngs.z, 0.0f, 0.0f);
+    }
+}
+
+// Bilinear footprint from an integer texel position and its fractions (wrap / clamp rules of
+// footprint_d).
+__device__ __forceinline__ Footprint footprint_i(const MapView& m, int i0, int j0, float fs, float ft) {
+    Footprint f;
+    f.fs = fs;
+    f.ft = ft;
+    int c0, c1;
+    if (m.wrap_u) {
+        c0 = i0 % m.W;
+        if (c0 < 0) c0 += m.W;
+        c1 = c0 + 1 == m.W ? 0 : c0 + 1;
+    } else {
+        c0 = min(max(i0, 0), m.W - 1);
+        c1 = min(max(i0 + 1, 0), m.W - 1);
+    }
+    const int r0 = min(max(j0, 0), m.H - 1), r1 = min(max(j0 + 1, 0), m.H - 1);
+    f.t[0] = (uint32_t)r0 * m.W + c0;
+    f.t[1] = (uint32_t)r0 * m.W + c1;
+    f.t[2] = (uint32_t)r1 * m.W + c0;
+    f.t[3] = (uint32_t)r1 * m.W + c1;
+    return f;
+}
+
+// Shading state of a covered pixel (Eqs. 10-11) from its record: fetched channels (and their
+// texel-space derivatives when `deriv`), the interpolated frame, the material and n_s.
+struct PixelShade {
+    int i0, i1, i2, u0, u1, u2;
+    float3 P0, P1, P2;
+    float b[3];
+    float2 uv0, uv1, uv2;
+    Footprint fp;
+    float att[8], dfs[8], dft[8];
+    float3 N0, N1, N2, T0, T1, T2, ni, ti;
+    Surface su;
+    float vol;
+    float3 wo;
+};
+
+template <typename T>
+__device__ __forceinline__ void pixel_shade(const ShadeArgs& A, uint32_t i, int f, bool deriv, PixelShade& S) {
+    const float4* R = A.prec + kPrec * (size_t)i;
+    const float4 r0 = R[0], r1 = R[1], r2 = R[2];
+    S.i0 = __ldg(A.F + 3 * f); S.i1 = __ldg(A.F + 3 * f + 1); S.i2 = __ldg(A.F + 3 * f + 2);
+    S.u0 = __ldg(A.Fuv + 3 * f); S.u1 = __ldg(A.Fuv + 3 * f + 1); S.u2 = __ldg(A.Fuv + 3 * f + 2);
+    S.b[0] = r0.x; S.b[1] = r0.y; S.b[2] = r0.z;
+    S.vol = r0.w;
+    S.wo = f3(r1.x, r1.y, r1.z);
+    S.fp = footprint_i(A.map, __float_as_int(r2.y), __float_as_int(r2.z), r1.w, r2.x);
+    fetch8<T>(A.map, S.fp, S.att, deriv ? S.dfs : nullptr, S.dft);
+    S.N0 = ld3(A.nrm + 3 * S.i0); S.N1 = ld3(A.nrm + 3 * S.i1); S.N2 = ld3(A.nrm + 3 * S.i2);
+    S.T0 = ld3(A.tan + 3 * S.u0); S.T1 = ld3(A.tan + 3 * S.u1); S.T2 = ld3(A.tan + 3 * S.u2);
+    S.ni = S.b[0] * S.N0 + S.b[1] * S.N1 + S.b[2] * S.N2;
+    S.ti = S.b[0] * S.T0 + S.b[1] * S.T1 + S.b[2] * S.T2;
+    S.su = make_surface(S.att, S.ni, S.ti, __ldg(A.fsign + f), A.metallic);
+    if (deriv) {
+        S.P0 = ld3(A.V + 3 * S.i0); S.P1 = ld3(A.V + 3 * S.i1); S.P2 = ld3(A.V + 3 * S.i2);
+        S.uv0 = make_float2(__ldg(A.UV + 2 * S.u0), __ldg(A.UV + 2 * S.u0 + 1));
+        S.uv1 = make_float2(__ldg(A.UV + 2 * S.u1), __ldg(A.UV + 2 * S.u1 + 1));
+        S.uv2 = make_float2(__ldg(A.UV + 2 * S.u2), __ldg(A.UV + 2 * S.u2 + 1));
+    }
+}
+
+template <typename T, bool BWD, bool COUNT, bool IND>
 __global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
     __shared__ uint16_t s_list[kShadeWarps][kListMax];
     const int lane = threadIdx.x & 31;
@@ -588,43 +702,18 @@ __global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
         }
         const int f = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
         const Cam& cam = A.cams[c];
-        const int i0 = __ldg(A.F + 3 * f), i1 = __ldg(A.F + 3 * f + 1), i2 = __ldg(A.F + 3 * f + 2);
-        const int u0 = __ldg(A.Fuv + 3 * f), u1 = __ldg(A.Fuv + 3 * f + 1), u2 = __ldg(A.Fuv + 3 * f + 2);
-        const float3 P0 = ld3(A.V + 3 * i0), P1 = ld3(A.V + 3 * i1), P2 = ld3(A.V + 3 * i2);
-        S3 o, d, xs, ngs;
-        float bs[3];
-        camera_ray(cam, px, py, &o, &d);
-        surface_point(o, d, s3(P0.x, P0.y, P0.z), s3(P1.x, P1.y, P1.z), s3(P2.x, P2.y, P2.z), &xs, &ngs, bs);
-        const S3 org = offset_origin(xs, ngs);
-        // ---- attribute query at x (Eqs. 10-11); shading geometry in FP64
-        const D3 eyed = d3(cam.eye[0], cam.eye[1], cam.eye[2]);
-        const double dxd = ((double)px + 0.5 - (double)cam.cx) / (double)cam.kx;
-        const double dyd = ((double)cam.cy - ((double)py + 0.5)) / (double)cam.ky;
-        const D3 dd = d3(cam.fwd[0] + dxd * cam.right[0] + dyd * cam.up[0],
-                         cam.fwd[1] + dxd * cam.right[1] + dyd * cam.up[1],
-                         cam.fwd[2] + dxd * cam.right[2] + dyd * cam.up[2]);
-        double bd[3];
-        bary_d(eyed, dd, dof(P0), dof(P1), dof(P2), bd);
-        const float b[3] = {(float)bd[0], (float)bd[1], (float)bd[2]};
-        const float2 uv0 = make_float2(__ldg(A.UV + 2 * u0), __ldg(A.UV + 2 * u0 + 1));
-        const float2 uv1 = make_float2(__ldg(A.UV + 2 * u1), __ldg(A.UV + 2 * u1 + 1));
-        const float2 uv2 = make_float2(__ldg(A.UV + 2 * u2), __ldg(A.UV + 2 * u2 + 1));
-        const double sd = (bd[0] * uv0.x + bd[1] * uv1.x + bd[2] * uv2.x) * A.map.W - 0.5;
-        const double td = (bd[0] * uv0.y + bd[1] * uv1.y + bd[2] * uv2.y) * A.map.H - 0.5;
-        const Footprint fp = footprint_d(A.map, sd, td);
-        float att[8], dfs[8], dft[8];
-        fetch8<T>(A.map, fp, att, BWD ? dfs : nullptr, dft);
-        const float3 N0 = ld3(A.nrm + 3 * i0), N1 = ld3(A.nrm + 3 * i1), N2 = ld3(A.nrm + 3 * i2);
-        const float3 T0 = ld3(A.tan + 3 * u0), T1 = ld3(A.tan + 3 * u1), T2 = ld3(A.tan + 3 * u2);
-        const float3 ni = b[0] * N0 + b[1] * N1 + b[2] * N2;
-        const float3 ti = b[0] * T0 + b[1] * T1 + b[2] * T2;
-        const Surface su = make_surface(att, ni, ti, __ldg(A.fsign + f), A.metallic);
-        const D3 vod = dsub(eyed, d3(bd[0] * P0.x + bd[1] * P1.x + bd[2] * P2.x,
-                                     bd[0] * P0.y + bd[1] * P1.y + bd[2] * P2.y,
-                                     bd[0] * P0.z + bd[1] * P1.z + bd[2] * P2.z));
-        const double vold = sqrt(ddot(vod, vod));
-        const float vol = (float)vold;
-        const float3 wo = f3((float)(vod.x / vold), (float)(vod.y / vold), (float)(vod.z / vold));
+        S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
+        if (IND) {
+            const float4 r3 = A.prec[kPrec * (size_t)i + 3], r4 = A.prec[kPrec * (size_t)i + 4];
+            org = s3(r3.x, r3.y, r3.z);
+            ngs = s3(r3.w, r4.x, r4.y);
+        }
+        // ---- attribute query at x (Eqs. 10-11); only n_s, the material and w_o stay live
+        // through the sample loops, the backward epilogue recomputes the rest
+        PixelShade S;
+        pixel_shade<T>(A, i, f, false, S);
+        const Surface su = S.su;
+        const float3 wo = S.wo;
         float3 L = f3(0.f, 0.f, 0.f);
         float3 gns = f3(0.f, 0.f, 0.f), gwo = f3(0.f, 0.f, 0.f), ga = f3(0.f, 0.f, 0.f);
         float gr = 0.f, gm = 0.f;
@@ -656,7 +745,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
         }
         if (!BWD && lane == 0) my_samples += (unsigned long long)A.Nd;
         // ---- one-bounce indirect (Eqs. 18-19): lanes take the pixel's live (j, s) pairs
-        if (A.Nb > 0 && A.lambda != 0.0f) {
+        if (IND && A.Nb > 0 && A.lambda != 0.0f) {
             const float3 fdx = ((1.0f - su.m) / kPi) * su.a;
             const float scale = A.lambda / (float)A.Nb;
             const float invNs = 1.0f / (float)A.Ns;
@@ -760,6 +849,29 @@ __global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
             for (int ofs = 16; ofs > 0; ofs >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], ofs);
         gns = f3(acc[0], acc[1], acc[2]);
         gwo = f3(acc[3], acc[4], acc[5]);
+        // recompute the shading state (a fresh read of the visibility key keeps the compiler
+        // from holding the first evaluation live across the sample loops)
+        const int f2 = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
+        PixelShade E;
+        pixel_shade<T>(A, i, f2, true, E);
+        const int i0 = E.i0, i1 = E.i1, i2 = E.i2, u0 = E.u0, u1 = E.u1, u2 = E.u2;
+        const float3 P0 = E.P0, P1 = E.P1, P2 = E.P2;
+        const float3 N0 = E.N0, N1 = E.N1, N2 = E.N2, T0 = E.T0, T1 = E.T1, T2 = E.T2;
+        const float3 ni = E.ni, ti = E.ti;
+        const float2 uv0 = E.uv0, uv1 = E.uv1, uv2 = E.uv2;
+        const Footprint fp = E.fp;
+        const float b[3] = {E.b[0], E.b[1], E.b[2]};
+        float dfs[8], dft[8];
+#pragma unroll
+        for (int ch = 0; ch < 8; ++ch) { dfs[ch] = E.dfs[ch]; dft[ch] = E.dft[ch]; }
+        const float vol = E.vol;
+        const float3 wo2 = E.wo;
+        // camera-ray direction (FP32 suffices for the barycentric adjoint)
+        const float dxf = ((float)px + 0.5f - cam.cx) / cam.kx, dyf = (cam.cy - ((float)py + 0.5f)) / cam.ky;
+        const float3 dvv = f3(cam.fwd[0] + dxf * cam.right[0] + dyf * cam.up[0],
+                              cam.fwd[1] + dxf * cam.right[1] + dyf * cam.up[1],
+                              cam.fwd[2] + dxf * cam.right[2] + dyf * cam.up[2]);
+        S3 o = s3(cam.eye[0], cam.eye[1], cam.eye[2]);
         float gatt[8];
         gatt[0] = acc[6]; gatt[1] = acc[7]; gatt[2] = acc[8];
         gatt[3] = acc[9];
@@ -802,12 +914,12 @@ __global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
         gb[1] += uv1.x * gu_ + uv1.y * gv_;
         gb[2] += uv2.x * gu_ + uv2.y * gv_;
         // x through w_o = (eye - x) / |eye - x|
-        const float3 gx = (-1.0f / vol) * (gwo - dot(gwo, wo) * wo);
+        const float3 gx = (-1.0f / vol) * (gwo - dot(gwo, wo2) * wo2);
         gb[0] += dot(P0, gx); gb[1] += dot(P1, gx); gb[2] += dot(P2, gx);
         float3 gP0 = b[0] * gx, gP1 = b[1] * gx, gP2 = b[2] * gx;
         // barycentrics of the camera ray (Moller-Trumbore) w.r.t. the vertices
         {
-            const float3 dv = f3((float)dd.x, (float)dd.y, (float)dd.z), oo = tof(o);
+            const float3 dv = dvv, oo = tof(o);
             const float3 e1 = P1 - P0, e2 = P2 - P0, sv = oo - P0;
             const float3 pv = cross(dv, e2);
             const float det = dot(e1, pv);
@@ -894,6 +1006,7 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     A.work = f->work;
     A.status = ctx->d_status;
     const size_t P = (size_t)f->views * f->W * f->H;
+    A.prec = f->prec;
     A.visbits = f->bits;
     A.secbits = f->bits ? f->bits + P * A.wd : nullptr;
     A.hits = f->hits;
@@ -915,12 +1028,12 @@ static void time_end(exm_frame* f, const exm_params* p, cudaStream_t s) {
     cudaEventRecord(f->timers.back().end, s);
 }
 
-template <bool BWD, bool COUNT>
+template <bool BWD, bool COUNT, bool IND>
 static void launch_shade_t(const ShadeArgs& A, exm_dtype dt, int blocks, cudaStream_t s) {
     switch (dt) {
-        case EXM_F32: shade_kernel<float, BWD, COUNT><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
-        case EXM_BF16: shade_kernel<__nv_bfloat16, BWD, COUNT><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
-        default: shade_kernel<__half, BWD, COUNT><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
+        case EXM_F32: shade_kernel<float, BWD, COUNT, IND><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
+        case EXM_BF16: shade_kernel<__nv_bfloat16, BWD, COUNT, IND><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
+        default: shade_kernel<__half, BWD, COUNT, IND><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
     }
 }
 
@@ -928,10 +1041,17 @@ template <bool BWD>
 static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, exm_dtype dt,
                                cudaStream_t s) {
     if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, "map dtype");
-    const int blocks = ctx->num_sms * 4;
+    const int blocks = ctx->num_sms * 8;
     time_begin(f, p, BWD ? 3 : 2, s);
-    if (p->flags & EXM_FLAG_COUNT_WORK) launch_shade_t<BWD, true>(A, dt, blocks, s);
-    else launch_shade_t<BWD, false>(A, dt, blocks, s);
+    const bool ind = A.Nb > 0 && A.lambda != 0.0f;
+    const bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
+    if (ind) {
+        if (count) launch_shade_t<BWD, true, true>(A, dt, blocks, s);
+        else launch_shade_t<BWD, false, true>(A, dt, blocks, s);
+    } else {
+        if (count) launch_shade_t<BWD, true, false>(A, dt, blocks, s);
+        else launch_shade_t<BWD, false, false>(A, dt, blocks, s);
+    }
     time_end(f, p, s);
     ctx->launches += 1;
     return exm_cuda_check(cudaGetLastError(), "shade launch");
@@ -968,7 +1088,8 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
     const int ws = indirect ? (p->n_bounce * p->n_light + 31) / 32 : 0;
     const uint32_t ray_cap = f->ray_cap ? f->ray_cap : kRayCapDefault;
-    if (!ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)ray_cap * 2) ||
+    if (!ensure(&f->prec, &f->prec_cap, P * (size_t)kPrec) ||
+        !ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)ray_cap * 2) ||
         (indirect && !ensure(&f->hits, &f->hits_cap, P * (size_t)p->n_bounce)))
         return exm_fail(EXM_ERR_OOM, "wavefront buffers");
     const uint32_t per_pixel = (uint32_t)max(wd * 32 + ws * 32, indirect ? p->n_bounce : 1);
@@ -978,6 +1099,8 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
     A.ray_cap = ray_cap;
     A.out = out;
+    pixel_prep_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(A);
+    ctx->launches += 1;
     cudaMemsetAsync(f->samples, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(out, 0, P * 3 * sizeof(float), s);
     cudaMemsetAsync(f->bits, 0, P * (size_t)(wd + ws) * sizeof(uint32_t), s);
