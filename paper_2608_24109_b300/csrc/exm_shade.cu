@@ -460,18 +460,32 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
         }
         if (!active) continue;
         bool done = false, hit = false;
+        // one item per iteration: a 4-wide node (node >= 0) or one triangle (node < 0, ~k);
+        // hit leaves are pushed like inner nodes, so a warp runs at most one triangle test
+        // per iteration whatever its lanes found in their last node
         for (int it = 0; it < kRound; ++it) {
             if (++steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
-            ++c_nodes;
-            const float4* N = A.bvh.nodes4 + 8 * (size_t)node;
-            // near / far planes of each axis chosen by the ray's direction signs
-            const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
-            const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
-            const float4 rf = __ldg(N + 6);
-            const float tmax = CLOSEST ? bt : INFINITY;
-            float tc[4];
-            int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
-            bool hc[4];
+            int next = INT_MIN;  // none: pop (leaf ~k is negative, ~0 == -1)
+            if (node < 0) {
+                ++c_tris;
+                float T, det;
+                int id;
+                if (tri_test(A.bvh, ~node, r, &T, &det, &id)) {
+                    if (!CLOSEST) { hit = true; done = true; break; }
+                    const float t = sdiv(T, det);
+                    if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+                }
+            } else {
+                ++c_nodes;
+                const float4* N = A.bvh.nodes4 + 8 * (size_t)node;
+                // near / far planes of each axis chosen by the ray's direction signs
+                const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
+                const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
+                const float4 rf = __ldg(N + 6);
+                const float tmax = CLOSEST ? bt : INFINITY;
+                float tc[4];
+                const int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
+                bool hc[4];
 #define EXM_BOX(C, c)                                                                                          \
     {                                                                                                          \
         const float t0 = fmaxf(fmax3(fmaf(qx.c, r.inv.x, r.oinv.x), fmaf(qy.c, r.inv.y, r.oinv.y),                \
@@ -479,54 +493,35 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
         const float t1 = fminf(fmin3(fmaf(fx.c, r.inv.x, r.oinv.x), fmaf(fy.c, r.inv.y, r.oinv.y),                \
                                      fmaf(fz.c, r.inv.z, r.oinv.z)), tmax);                                    \
         tc[C] = t0;                                                                                            \
-        hc[C] = t0 <= t1;                                                                                      \
+        hc[C] = t0 <= t1 && ref[C] != kEmptyChild;                                                             \
     }
-            EXM_BOX(0, x)
-            EXM_BOX(1, y)
-            EXM_BOX(2, z)
-            EXM_BOX(3, w)
+                EXM_BOX(0, x)
+                EXM_BOX(1, y)
+                EXM_BOX(2, z)
+                EXM_BOX(3, w)
 #undef EXM_BOX
+                // continue with the nearest hit child; push the others
+                float tn = INFINITY;
+                int nc = -1;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (ref[c] == kEmptyChild) hc[c] = false;
-                if (hc[c] && ref[c] < 0) {
-                    ++c_tris;
-                    float T, det;
-                    int id;
-                    if (tri_test(A.bvh, ~ref[c], r, &T, &det, &id)) {
-                        if (!CLOSEST) { hit = true; done = true; }
-                        else {
-                            const float t = sdiv(T, det);
-                            if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
-                        }
+                for (int c = 0; c < 4; ++c)
+                    if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
+                bool overflow = false;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    if (hc[c] && c != nc) {
+                        if (sp >= kStackSize4) overflow = true;
+                        else stack[sp++] = ref[c];
                     }
-                    hc[c] = false;
                 }
+                if (overflow) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
+                if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
             }
-            if (done) break;
-            // internal children: continue with the nearest, push the others (farthest first)
-            int next = -1;
-            float tn = INFINITY;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (CLOSEST && hc[c] && tc[c] > bt) hc[c] = false;
-                if (hc[c] && tc[c] < tn) { tn = tc[c]; next = c; }
-            }
-            bool overflow = false;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (hc[c] && c != next) {
-                    if (sp >= kStackSize4) overflow = true;
-                    else stack[sp++] = ref[c];
-                }
-            }
-            if (overflow) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
-            if (next >= 0) {
-                node = next == 0 ? ref[0] : next == 1 ? ref[1] : next == 2 ? ref[2] : ref[3];
-            } else {
+            if (next == INT_MIN) {
                 if (sp == 0) { done = true; break; }
-                node = stack[--sp];
+                next = stack[--sp];
             }
+            node = next;
         }
         if (done) {
             if (CLOSEST) {
