@@ -467,3 +467,108 @@ def test_autograd_matches_central_differences():
         num = fd(which, idx, h)
         ana = G[idx].item()
         assert abs(num - ana) <= 1e-5 * max(abs(ana), 1e-3 * G.abs().max().item()), (which, idx, num, ana)
+
+
+def _l_scene(n_bounce, n_light, seed, lambda_ind=1.0):
+    """Floor quad (y = 0, x in [-1, 0.5], z in [-1, 1], facing +y) and a wall quad (x = 0.5,
+    y in [0, 1], z in [-1, 1], facing -x); constant grey Lambertian maps, flat normals."""
+    V = np.array([[-1, 0, -1], [-1, 0, 1], [0.5, 0, 1], [0.5, 0, -1],
+                  [0.5, 0, -1], [0.5, 0, 1], [0.5, 1, 1], [0.5, 1, -1]], np.float64)
+    F = np.array([[0, 1, 2], [0, 2, 3], [4, 5, 6], [4, 6, 7]])
+    n = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    assert n[0, 1] > 0 and n[2, 0] < 0
+    UV = np.array([[0.1, 0.1], [0.1, 0.9], [0.9, 0.9], [0.9, 0.1]] * 2)
+    Fuv = F.copy()
+    maps = np.zeros((8, 8, 8), np.float32)
+    maps[..., 0:3] = 0.5
+    maps[..., 3] = 0.5
+    maps[..., 7] = 1.0
+    env = scenes.env_map(np.random.default_rng(3), 16, 8, 0.5)
+    W = 64
+    cam = scenes.look_at_camera((-1.2, 1.4, 0.4), W, W, target=(0.0, 0.0, 0.0))
+    sc = scenes._finish("L", V, F, UV, Fuv, maps, maps, env, cam[None], W, W, n_direct=16, n_bounce=n_bounce,
+                        n_light=n_light, seed=seed, lambda_ind=lambda_ind)
+    sc.metallic = False
+    return sc
+
+
+def _floor_pixel(sc):
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, sc.width, sc.height)
+    pix = oracle.covered_pixels(keys)
+    o, d = shade.camera_rays(sc.cams, pix)
+    t = -o[:, 1] / d[:, 1]
+    x = (o + t[:, None] * d).numpy()
+    tri = (keys[pix[:, 0], pix[:, 1], pix[:, 2]] & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    on_floor = tri < 2
+    k = np.argmin(np.where(on_floor, np.abs(x[:, 0] - 0.1) + np.abs(x[:, 2]), np.inf))
+    return pix[k:k + 1], keys[pix[k, 0], pix[k, 1], pix[k, 2]:pix[k, 2] + 1].copy(), x[k]
+
+
+def _indirect_by_quadrature(sc, x):
+    """L_ind(x) = int f_d(x) L_sec(y(w)) cos(w) dw over the floor's upper hemisphere (Eq. 19 in
+    the limit), L_sec(y) = int E Vis f_d(y) max(n.w', 0) dw' (Eq. 18), by midpoint quadrature
+    with analytic ray/plane visibility; the environment is piecewise constant per texel."""
+    fd = 0.5 / math.pi
+    env = sc.env.astype(np.float64)
+    He, We = env.shape[:2]
+    sub = 6
+    th = math.pi * (np.arange(He * sub) + 0.5) / (He * sub)
+    ph = 2 * math.pi * (np.arange(We * sub) + 0.5) / (We * sub)
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    dl = np.stack([np.sin(T) * np.sin(P), np.cos(T), -np.sin(T) * np.cos(P)], -1).reshape(-1, 3)
+    dw_l = (np.sin(T) * (math.pi / (He * sub)) * (2 * math.pi / (We * sub))).ravel()
+    El = env[(np.arange(He * sub) // sub)[:, None].repeat(We * sub, 1).ravel(),
+             (np.arange(We * sub) // sub)[None, :].repeat(He * sub, 0).ravel()]
+    nw = np.array([-1.0, 0.0, 0.0])
+
+    def l_sec(y):
+        cos = dl @ nw
+        ok = cos > 0
+        # blocked when the ray y + t w' meets the floor rectangle
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t = -y[1] / dl[:, 1]
+            px, pz = y[0] + t * dl[:, 0], y[2] + t * dl[:, 2]
+        blocked = (dl[:, 1] < 0) & (t > 0) & (px >= -1) & (px <= 0.5) & (pz >= -1) & (pz <= 1)
+        w = np.where(ok & ~blocked, cos * dw_l, 0.0)
+        return fd * (El * w[:, None]).sum(0)
+
+    nt, npp = 96, 192
+    u = (np.arange(nt) + 0.5) / nt
+    tt = (math.pi / 2) * u
+    pp = 2 * math.pi * (np.arange(npp) + 0.5) / npp
+    TT, PP = np.meshgrid(tt, pp, indexing="ij")
+    dirs = np.stack([np.sin(TT) * np.cos(PP), np.cos(TT), np.sin(TT) * np.sin(PP)], -1).reshape(-1, 3)
+    dw = (np.sin(TT) * (math.pi / 2 / nt) * (2 * math.pi / npp)).ravel()
+    total = np.zeros(3)
+    for w, a in zip(dirs, dw):
+        if w[0] <= 0:
+            continue
+        t = (0.5 - x[0]) / w[0]
+        y = x + t * w
+        if not (0 <= y[1] <= 1 and -1 <= y[2] <= 1):
+            continue
+        total += fd * l_sec(y) * w[1] * a
+    return total
+
+
+def test_indirect_estimator_converges_to_quadrature():
+    """Eq. 19 with Eq. 18: the one-bounce estimator on a floor point in front of a wall
+    converges to the double integral (independent FP64 quadrature with analytic visibility)."""
+    ests = []
+    for seed in range(4):
+        sc = _l_scene(1024, 64, seed)
+        pix, keys, x = _floor_pixel(sc)
+        tab = oracle.EnvTable(sc.env)
+        dec = oracle.Decisions(sc, tab, pix, keys)
+        assert (dec.stri >= 0).sum() > 100
+        V, M, E = shade.scene_tensors(sc)
+        full = shade.render_image(sc, tab, dec, V, M, E).numpy()[0]
+        sc0 = _l_scene(1024, 64, seed, lambda_ind=0.0)
+        dec0 = oracle.Decisions(sc0, tab, pix, keys)
+        direct = shade.render_image(sc0, tab, dec0, V, M, E).numpy()[0]
+        ests.append(full - direct)
+    ests = np.array(ests)
+    est, se = ests.mean(0), ests.std(0, ddof=1) / math.sqrt(len(ests))
+    ref = _indirect_by_quadrature(sc, x)
+    assert np.all(ref > 0)
+    assert np.all(np.abs(est - ref) <= 4 * se + 0.02 * ref), (est, se, ref)
