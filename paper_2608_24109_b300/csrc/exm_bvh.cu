@@ -1,10 +1,12 @@
-// Shadow-ray / secondary-ray acceleration structure (ray tracing of Sec. 5.2-5.3): a linear
-// BVH built on the device.  Triangle centroids -> 30-bit Morton codes -> radix sort ->
-// binary hierarchy from the sorted codes (Karras, "Maximizing parallelism in the
-// construction of BVHs, octrees and k-d trees", HPG 2012) -> bottom-up box refit ->
-// 64-byte traversal nodes holding both child boxes, padded so that the box test is
-// conservative with respect to the watertight triangle test.
+// Shadow-ray / secondary-ray acceleration structure (ray tracing of Sec. 5.2-5.3), built on
+// the device: triangle centroids -> 30-bit Morton codes -> radix sort -> padded leaf boxes
+// (so that the box test is conservative with respect to the watertight triangle test) ->
+// binary hierarchy by locally-ordered clustering -> 4-wide nodes by a surface-area-greedy
+// collapse.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
+#include <cfloat>
+#include <utility>
 
 #include "exm_device.cuh"
 #include "exm_internal.h"
@@ -79,112 +81,8 @@ __global__ void morton_kernel(const float* __restrict__ V, const int32_t* __rest
     ids[f] = (uint32_t)f;
 }
 
-__device__ __forceinline__ int delta(const uint32_t* codes, int n, int i, int j) {
-    if (j < 0 || j >= n) return -1;
-    uint32_t a = codes[i], b = codes[j];
-    if (a == b) return 32 + __clz((uint32_t)i ^ (uint32_t)j);
-    return __clz(a ^ b);
-}
-
-// Internal node i of n-1: its key range and split (Karras 2012).  Children: >= 0 internal,
-// < 0 leaf ~k (k = sorted position).
-__global__ void hierarchy_kernel(const uint32_t* __restrict__ codes, int n, int32_t* child, int32_t* parent) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    int d = (delta(codes, n, i, i + 1) - delta(codes, n, i, i - 1)) >= 0 ? 1 : -1;
-    int dmin = delta(codes, n, i, i - d);
-    int lmax = 2;
-    while (delta(codes, n, i, i + lmax * d) > dmin) lmax <<= 1;
-    int l = 0;
-    for (int t = lmax >> 1; t >= 1; t >>= 1)
-        if (delta(codes, n, i, i + (l + t) * d) > dmin) l += t;
-    int j = i + l * d;
-    int dnode = delta(codes, n, i, j);
-    int s = 0;
-    int div = 2;
-    int t;
-    do {
-        t = (l + div - 1) / div;
-        if (delta(codes, n, i, i + (s + t) * d) > dnode) s += t;
-        div <<= 1;
-    } while (t > 1);
-    int gamma = i + s * d + min(d, 0);
-    int left = (min(i, j) == gamma) ? ~gamma : gamma;
-    int right = (max(i, j) == gamma + 1) ? ~(gamma + 1) : gamma + 1;
-    child[2 * i] = left;
-    child[2 * i + 1] = right;
-    // parent array: internal nodes 0..n-2, leaves at n-1+k
-    parent[left < 0 ? (n - 1 + ~left) : left] = i;
-    parent[right < 0 ? (n - 1 + ~right) : right] = i;
-}
-
 __device__ __forceinline__ float pad_of(float lo, float hi) {
     return 2e-5f * (1.0f + fmaxf(fabsf(lo), fabsf(hi)));
-}
-
-// Leaf boxes, triangle records in leaf order, then the bottom-up refit: the second thread
-// to reach an internal node merges its children's boxes and continues upwards.
-__global__ void refit_kernel(const float* __restrict__ V, const int32_t* __restrict__ F, int n, int nv,
-                             const uint32_t* __restrict__ ids_sorted, const int32_t* __restrict__ child,
-                             const int32_t* __restrict__ parent, uint32_t* flags, float* bounds, float4* tris,
-                             uint32_t* status) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    uint32_t f = ids_sorted[k];
-    int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
-    i0 = min(max(i0, 0), nv - 1); i1 = min(max(i1, 0), nv - 1); i2 = min(max(i2, 0), nv - 1);
-    float p[3][3];
-    for (int c = 0; c < 3; ++c) { p[0][c] = V[3 * i0 + c]; p[1][c] = V[3 * i1 + c]; p[2][c] = V[3 * i2 + c]; }
-    tris[3 * k] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float((int)f));
-    tris[3 * k + 1] = make_float4(p[1][0], p[1][1], p[1][2], 0.0f);
-    tris[3 * k + 2] = make_float4(p[2][0], p[2][1], p[2][2], 0.0f);
-    int leaf = n - 1 + k;
-    float* b = bounds + 6 * (size_t)leaf;
-    for (int c = 0; c < 3; ++c) {
-        float lo = fminf(p[0][c], fminf(p[1][c], p[2][c])), hi = fmaxf(p[0][c], fmaxf(p[1][c], p[2][c]));
-        float pd = pad_of(lo, hi);
-        b[c] = lo - pd;
-        b[3 + c] = hi + pd;
-    }
-    if (n == 1) return;
-    int node = parent[leaf];
-    for (int guard = 0; node >= 0; ++guard) {
-        if (guard > 256) { atomicOr(status, ERRBIT_TRAVERSAL); return; }
-        __threadfence();
-        if (atomicAdd(flags + node, 1u) == 0) return;
-        __threadfence();
-        int l = child[2 * node], r = child[2 * node + 1];
-        const volatile float* bl = bounds + 6 * (size_t)(l < 0 ? n - 1 + ~l : l);
-        const volatile float* br = bounds + 6 * (size_t)(r < 0 ? n - 1 + ~r : r);
-        volatile float* bn = bounds + 6 * (size_t)node;
-        for (int c = 0; c < 3; ++c) {
-            bn[c] = fminf(bl[c], br[c]);
-            bn[3 + c] = fmaxf(bl[3 + c], br[3 + c]);
-        }
-        node = node == 0 ? -1 : parent[node];
-    }
-}
-
-__global__ void write_nodes_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
-                                   float4* nodes) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n - 1) return;
-    int l = child[2 * i], r = child[2 * i + 1];
-    const float* bl = bounds + 6 * (size_t)(l < 0 ? n - 1 + ~l : l);
-    const float* br = bounds + 6 * (size_t)(r < 0 ? n - 1 + ~r : r);
-    nodes[4 * i] = make_float4(bl[0], bl[1], bl[2], bl[3]);
-    nodes[4 * i + 1] = make_float4(bl[4], bl[5], br[0], br[1]);
-    nodes[4 * i + 2] = make_float4(br[2], br[3], br[4], br[5]);
-    nodes[4 * i + 3] = make_float4(__int_as_float(l), __int_as_float(r), 0.0f, 0.0f);
-}
-
-// A one-triangle mesh: a single node whose two children are both leaf 0.
-__global__ void single_node_kernel(const float* __restrict__ bounds, float4* nodes) {
-    const float* b = bounds;
-    nodes[0] = make_float4(b[0], b[1], b[2], b[3]);
-    nodes[1] = make_float4(b[4], b[5], b[0], b[1]);
-    nodes[2] = make_float4(b[2], b[3], b[4], b[5]);
-    nodes[3] = make_float4(__int_as_float(~0), __int_as_float(~0), 0.0f, 0.0f);
 }
 
 __global__ void init_box_kernel(uint32_t* box) {
@@ -194,8 +92,117 @@ __global__ void init_box_kernel(uint32_t* box) {
 }
 
 
-// ---- 4-wide collapse.  A 4-wide node takes the grandchildren of a binary node (a leaf child
-// stays a leaf).  128-byte node: child boxes as lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4],
+// ---- Binary hierarchy by locally-ordered clustering (PLOC: Meister and Bittner, "Parallel
+// locally-ordered clustering for bounding volume hierarchy construction", TVCG 2018).
+// Clusters start as the leaves in Morton order.  Each round every cluster finds, among the
+// kPlocR clusters on either side, the one whose merged box has the smallest surface
+// (ties: the lower index); mutual nearest neighbours merge into a new internal node at
+// the lower position and the cluster array is compacted.  Node ids are handed out from
+// n-2 downwards in scan order, so the last merge, the root, is node 0.
+constexpr int kPlocR = 16;
+constexpr int kPlocBlock = 256;
+constexpr int kPlocMaxRounds = 4096;
+
+__device__ __forceinline__ float merged_half_area(const float* a, const float* b) {
+    const float dx = fmaxf(a[3], b[3]) - fminf(a[0], b[0]);
+    const float dy = fmaxf(a[4], b[4]) - fminf(a[1], b[1]);
+    const float dz = fmaxf(a[5], b[5]) - fminf(a[2], b[2]);
+    return dx * dy + dy * dz + dz * dx;
+}
+
+// Padded leaf boxes and triangle records in Morton order; the initial clusters (leaf ~k).
+__global__ void leaf_kernel(const float* __restrict__ V, const int32_t* __restrict__ F, int n, int nv,
+                            const uint32_t* __restrict__ ids_sorted, float* bounds, float4* tris, int32_t* clusters) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t f = ids_sorted[k];
+    int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+    i0 = min(max(i0, 0), nv - 1); i1 = min(max(i1, 0), nv - 1); i2 = min(max(i2, 0), nv - 1);
+    float p[3][3];
+    for (int c = 0; c < 3; ++c) { p[0][c] = V[3 * i0 + c]; p[1][c] = V[3 * i1 + c]; p[2][c] = V[3 * i2 + c]; }
+    tris[3 * k] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float((int)f));
+    tris[3 * k + 1] = make_float4(p[1][0], p[1][1], p[1][2], 0.0f);
+    tris[3 * k + 2] = make_float4(p[2][0], p[2][1], p[2][2], 0.0f);
+    float* b = bounds + 6 * (size_t)(n - 1 + k);
+    for (int c = 0; c < 3; ++c) {
+        const float lo = fminf(p[0][c], fminf(p[1][c], p[2][c])), hi = fmaxf(p[0][c], fmaxf(p[1][c], p[2][c]));
+        const float pd = pad_of(lo, hi);
+        b[c] = lo - pd;
+        b[3 + c] = hi + pd;
+    }
+    clusters[k] = ~k;
+}
+
+__global__ void __launch_bounds__(kPlocBlock) ploc_nearest_kernel(int n, int m, const int32_t* __restrict__ C,
+                                                                  const float* __restrict__ bounds, int32_t* nn) {
+    __shared__ float box[(kPlocBlock + 2 * kPlocR) * 6];
+    const int base = blockIdx.x * kPlocBlock - kPlocR;
+    for (int t = threadIdx.x; t < kPlocBlock + 2 * kPlocR; t += blockDim.x) {
+        const int g = base + t;
+        if (g >= 0 && g < m) {
+            const int c = C[g];
+            const float* b = bounds + 6 * (size_t)(c < 0 ? n - 1 + ~c : c);
+            for (int a = 0; a < 6; ++a) box[6 * t + a] = b[a];
+        }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * kPlocBlock + threadIdx.x;
+    if (i >= m) return;
+    const float* bi = box + 6 * (threadIdx.x + kPlocR);
+    float best = INFINITY;
+    int bj = -1;
+    for (int o = -kPlocR; o <= kPlocR; ++o) {
+        const int j = i + o;
+        if (o == 0 || j < 0 || j >= m) continue;
+        const float a = fminf(merged_half_area(bi, box + 6 * (threadIdx.x + kPlocR + o)), FLT_MAX);  // NaN, inf -> FLT_MAX
+        if (a < best) { best = a; bj = j; }  // ascending j: a tie keeps the lower index
+    }
+    nn[i] = bj;
+}
+
+// flag = merges << 32 | keeps: the lower cluster of a mutual pair merges, the upper one goes.
+__global__ void ploc_flag_kernel(int m, const int32_t* __restrict__ nn, unsigned long long* flag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const int j = nn[i];
+    const bool mutual = j >= 0 && nn[j] == i;
+    flag[i] = ((unsigned long long)(mutual && i < j) << 32) | (unsigned long long)!(mutual && i > j);
+}
+
+__global__ void ploc_merge_kernel(int n, int m, int id_top, const int32_t* __restrict__ C,
+                                  const int32_t* __restrict__ nn, const unsigned long long* __restrict__ flag,
+                                  const unsigned long long* __restrict__ scan, int32_t* Cout, int32_t* child,
+                                  float* bounds, uint32_t* totals) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    const unsigned long long f = flag[i], s = scan[i];
+    if (i == m - 1) {
+        totals[0] = (uint32_t)(s + f);
+        totals[1] = (uint32_t)((s + f) >> 32);
+    }
+    if (!(f & 1ull)) return;
+    int cl = C[i];
+    if (f >> 32) {
+        const int a = cl, b = C[nn[i]];
+        const int id = id_top - (int)(s >> 32);
+        child[2 * id] = a;
+        child[2 * id + 1] = b;
+        const int ia = a < 0 ? n - 1 + ~a : a, ib = b < 0 ? n - 1 + ~b : b;
+        const float* ba = bounds + 6 * (size_t)ia;
+        const float* bb = bounds + 6 * (size_t)ib;
+        float* bn = bounds + 6 * (size_t)id;
+        for (int c = 0; c < 3; ++c) {
+            bn[c] = fminf(ba[c], bb[c]);
+            bn[3 + c] = fmaxf(ba[3 + c], bb[3 + c]);
+        }
+        cl = id;
+    }
+    Cout[(uint32_t)s] = cl;
+}
+
+// ---- 4-wide collapse.  A 4-wide node starts from the two children of a binary node and
+// opens the internal candidate with the largest box surface until it holds four (a node
+// whose candidates are all leaves keeps fewer).  128-byte node: child boxes as lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4],
 // then the four child references (>= 0: node, < 0: leaf ~k, kEmpty: unused slot).
 constexpr int kEmpty4 = 0x7fffffff;
 
@@ -208,11 +215,23 @@ __global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const
     if (t >= *n_in) return;
     const int b = in[t].x, q = in[t].y;
     int slots[4];
-    int ns = 0;
-    for (int h = 0; h < 2; ++h) {
-        const int c = child[2 * b + h];
-        if (c < 0) slots[ns++] = c;
-        else { slots[ns++] = child[2 * c]; slots[ns++] = child[2 * c + 1]; }
+    int ns = 2;
+    slots[0] = child[2 * b];
+    slots[1] = child[2 * b + 1];
+    while (ns < 4) {
+        int pick = -1;
+        float best = -1.0f;
+        for (int k = 0; k < ns; ++k) {
+            if (slots[k] < 0) continue;
+            const float* bb = bounds + 6 * (size_t)slots[k];
+            const float dx = bb[3] - bb[0], dy = bb[4] - bb[1], dz = bb[5] - bb[2];
+            const float a = dx * dy + dy * dz + dz * dx;
+            if (a > best) { best = a; pick = k; }
+        }
+        if (pick < 0) break;
+        const int c = slots[pick];
+        slots[pick] = child[2 * c];
+        slots[ns++] = child[2 * c + 1];
     }
     float v[6][4];
     int refs[4];
@@ -263,21 +282,24 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
         size_t internal = (size_t)(n > 1 ? n - 1 : 1);
         bool ok = cudaMalloc(&m->codes, nn * 4) == cudaSuccess && cudaMalloc(&m->codes_sorted, nn * 4) == cudaSuccess &&
                   cudaMalloc(&m->ids, nn * 4) == cudaSuccess && cudaMalloc(&m->ids_sorted, nn * 4) == cudaSuccess &&
-                  cudaMalloc(&m->parent, (2 * nn) * 4) == cudaSuccess &&
                   cudaMalloc(&m->child, 2 * internal * 4) == cudaSuccess &&
-                  cudaMalloc(&m->flags, internal * 4) == cudaSuccess &&
                   cudaMalloc(&m->bounds, (2 * nn) * 6 * 4) == cudaSuccess &&
                   cudaMalloc(&m->scene_box, 6 * 4) == cudaSuccess &&
-                  cudaMalloc(&m->nodes, internal * 4 * sizeof(float4)) == cudaSuccess &&
                   cudaMalloc(&m->tris, nn * 3 * sizeof(float4)) == cudaSuccess &&
                   cudaMalloc(&m->nodes4, internal * 8 * sizeof(float4)) == cudaSuccess &&
                   cudaMalloc(&m->frontier, 2 * nn * sizeof(int2)) == cudaSuccess &&
-                  cudaMalloc(&m->frontier_cnt, 4 * sizeof(uint32_t)) == cudaSuccess;
+                  cudaMalloc(&m->frontier_cnt, 4 * sizeof(uint32_t)) == cudaSuccess &&
+                  cudaMalloc(&m->ploc_c, 2 * nn * 4) == cudaSuccess && cudaMalloc(&m->ploc_nn, nn * 4) == cudaSuccess &&
+                  cudaMalloc(&m->ploc_flag, nn * 8) == cudaSuccess && cudaMalloc(&m->ploc_scan, nn * 8) == cudaSuccess;
         if (!ok) return exm_fail(EXM_ERR_OOM, "BVH buffers");
         size_t bytes = 0;
         cub::DeviceRadixSort::SortPairs(nullptr, bytes, m->codes, m->codes_sorted, m->ids, m->ids_sorted, n, 0, 30, s);
         if (cudaMalloc(&m->sort_tmp, bytes) != cudaSuccess) return exm_fail(EXM_ERR_OOM, "BVH sort scratch");
         m->sort_tmp_bytes = bytes;
+        bytes = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, bytes, m->ploc_flag, m->ploc_scan, n, s);
+        if (cudaMalloc(&m->scan_tmp, bytes) != cudaSuccess) return exm_fail(EXM_ERR_OOM, "BVH scan scratch");
+        m->scan_tmp_bytes = bytes;
     }
     uint32_t* box = (uint32_t*)m->scene_box;
     init_box_kernel<<<1, 32, 0, s>>>(box);
@@ -285,17 +307,31 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
     morton_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->V, m->F, n, m->nv, box, m->codes, m->ids);
     size_t bytes = m->sort_tmp_bytes;
     cub::DeviceRadixSort::SortPairs(m->sort_tmp, bytes, m->codes, m->codes_sorted, m->ids, m->ids_sorted, n, 0, 30, s);
-    cudaMemsetAsync(m->parent, 0xff, (size_t)2 * n * 4, s);
+    leaf_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->V, m->F, n, m->nv, m->ids_sorted, m->bounds, m->tris, m->ploc_c);
     if (n > 1) {
-        cudaMemsetAsync(m->flags, 0, (size_t)(n - 1) * 4, s);
-        hierarchy_kernel<<<exm_blocks(n - 1, 256), 256, 0, s>>>(m->codes_sorted, n, m->child, m->parent);
+        int32_t* cin = m->ploc_c;
+        int32_t* cout = m->ploc_c + n;
+        uint32_t* tot = m->frontier_cnt;
+        int mcl = n, merged = 0;
+        for (int round = 0; mcl > 1; ++round) {
+            if (round >= kPlocMaxRounds) return exm_fail(EXM_ERR_ARG, "BVH clustering did not converge");
+            ploc_nearest_kernel<<<(mcl + kPlocBlock - 1) / kPlocBlock, kPlocBlock, 0, s>>>(n, mcl, cin, m->bounds,
+                                                                                         m->ploc_nn);
+            ploc_flag_kernel<<<exm_blocks(mcl, 256), 256, 0, s>>>(mcl, m->ploc_nn, m->ploc_flag);
+            size_t sb = m->scan_tmp_bytes;
+            cub::DeviceScan::ExclusiveSum(m->scan_tmp, sb, m->ploc_flag, m->ploc_scan, mcl, s);
+            ploc_merge_kernel<<<exm_blocks(mcl, 256), 256, 0, s>>>(n, mcl, n - 2 - merged, cin, m->ploc_nn, m->ploc_flag,
+                                                                   m->ploc_scan, cout, m->child, m->bounds, tot);
+            uint32_t h[2] = {0u, 0u};
+            if (cudaMemcpyAsync(h, tot, 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return exm_cuda_check(cudaGetLastError(), "BVH clustering");
+            if (h[1] == 0 || (int)h[1] > mcl / 2) return exm_fail(EXM_ERR_CUDA, "BVH clustering made no progress");
+            merged += (int)h[1];
+            mcl = (int)h[0];
+            std::swap(cin, cout);
+        }
     }
-    refit_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->V, m->F, n, m->nv, m->ids_sorted, m->child, m->parent,
-                                                   m->flags, m->bounds, m->tris, m->ctx->d_status);
-    if (n > 1)
-        write_nodes_kernel<<<exm_blocks(n - 1, 256), 256, 0, s>>>(n, m->child, m->bounds, m->nodes);
-    else
-        single_node_kernel<<<1, 1, 0, s>>>(m->bounds, m->nodes);
     // collapse to 4-wide nodes, level by level (the frontier size is read back per level)
     if (n == 1) {
         single4_kernel<<<1, 1, 0, s>>>(m->bounds, m->nodes4);
@@ -305,7 +341,11 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
         uint32_t* cnt = m->frontier_cnt;  // [0] in, [1] out, [2] nodes
         seed4_kernel<<<1, 1, 0, s>>>(fin, cnt, cnt + 2);
         uint32_t n_in = 1;
-        for (int level = 0; level < 64 && n_in > 0; ++level) {
+        int level = 0;
+        for (; n_in > 0; ++level) {
+            // the traversal stack holds at most 3 entries per level of the current path
+            if (3 * (level + 1) > kStackSize4)
+                return exm_fail(EXM_ERR_TRAVERSAL_LIMIT, "BVH deeper than the traversal stack allows");
             cudaMemsetAsync(cnt + 1, 0, 4, s);
             collapse4_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, fin, cnt, fout, cnt + 1,
                                                                   cnt + 2, m->nodes4);

@@ -22,8 +22,7 @@ constexpr float kPi = 3.14159265358979323846f;
 constexpr float kFDielectric = 0.04f;   // F_dielectric of Eq. 16
 constexpr float kSpecEps = 1e-6f;       // epsilon of Eq. 15
 constexpr float kRMin = 0.08f;          // roughness clamp before alpha = r^2
-constexpr int kStackSize = 64;
-constexpr int kStackSize4 = 96;
+constexpr int kStackSize4 = 192;  // 3 pushes per level of a tree at most 62 levels deep
 constexpr int kEmptyChild = 0x7fffffff;
 constexpr int kTraversalCap = 1 << 20;
 
@@ -305,125 +304,19 @@ __device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, u
 }
 
 // ----------------------------------------------------------------------- BVH
-// Binary BVH, 64-byte nodes: child boxes (lo0, hi0, lo1, hi1) in 3 float4 and the two
-// child references in the 4th (>= 0 internal node, < 0 leaf ~k = sorted triangle k).
-// Triangles in leaf order, 3 float4 each (p0 + original id bits in .w, p1, p2).
+// 4-wide BVH, 128-byte nodes (8 float4): the four child boxes as lo.x[4] lo.y[4] lo.z[4]
+// hi.x[4] hi.y[4] hi.z[4], then the four child references (>= 0: node, < 0: leaf ~k =
+// triangle k in leaf order, kEmptyChild: unused slot).  Triangles in leaf order, 3 float4
+// each (p0 + original id bits in .w, p1, p2).
 struct BvhView {
-    const float4* nodes;
     const float4* tris;
-    const float4* nodes4;  // 4-wide nodes (8 float4 each)
+    const float4* nodes4;
 };
-
-__device__ __forceinline__ bool slab(float3 lo, float3 hi, const Ray& r, float tmax, float* tnear) {
-    // (lo - o) / d as lo * (1/d) + (-o/d): one FFMA per plane
-    const float tx0 = fmaf(lo.x, r.inv.x, r.oinv.x), tx1 = fmaf(hi.x, r.inv.x, r.oinv.x);
-    const float ty0 = fmaf(lo.y, r.inv.y, r.oinv.y), ty1 = fmaf(hi.y, r.inv.y, r.oinv.y);
-    const float tz0 = fmaf(lo.z, r.inv.z, r.oinv.z), tz1 = fmaf(hi.z, r.inv.z, r.oinv.z);
-    const float t0 = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float t1 = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
-    *tnear = t0;
-    return t0 <= t1;
-}
 
 __device__ __forceinline__ bool tri_test(const BvhView& b, int k, const Ray& r, float* T, float* det, int* id) {
     float4 a = __ldg(b.tris + 3 * k), c = __ldg(b.tris + 3 * k + 1), d = __ldg(b.tris + 3 * k + 2);
     *id = __float_as_int(a.w);
     return woop(r, s3(a.x, a.y, a.z), s3(c.x, c.y, c.z), s3(d.x, d.y, d.z), T, det);
-}
-
-// Any hit with t > 0.  Sets ERRBIT_TRAVERSAL in *err and reports a hit when the step cap
-// or the stack is exceeded.
-__device__ __forceinline__ bool any_hit(const BvhView& b, const Ray& r, uint32_t* err, uint32_t& nn, uint32_t& nt) {
-    int stack[kStackSize];
-    int sp = 0;
-    int node = 0;
-    for (int steps = 0; steps < kTraversalCap; ++steps) {
-        ++nn;
-        float4 n0 = __ldg(b.nodes + 4 * node), n1 = __ldg(b.nodes + 4 * node + 1);
-        float4 n2 = __ldg(b.nodes + 4 * node + 2), n3 = __ldg(b.nodes + 4 * node + 3);
-        float ta, tb;
-        bool ha = slab(make_float3(n0.x, n0.y, n0.z), make_float3(n0.w, n1.x, n1.y), r, INFINITY, &ta);
-        bool hb = slab(make_float3(n1.z, n1.w, n2.x), make_float3(n2.y, n2.z, n2.w), r, INFINITY, &tb);
-        int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
-        int next = -1;
-        if (ha) {
-            if (ca < 0) { float T, det; int id; ++nt; if (tri_test(b, ~ca, r, &T, &det, &id)) return true; }
-            else next = ca;
-        }
-        if (hb) {
-            if (cb < 0) { float T, det; int id; ++nt; if (tri_test(b, ~cb, r, &T, &det, &id)) return true; }
-            else if (next < 0) next = cb;
-            else {
-                if (sp >= kStackSize) { *err |= ERRBIT_TRAVERSAL; return true; }
-                stack[sp++] = cb;
-            }
-        }
-        if (next < 0) {
-            if (sp == 0) return false;
-            next = stack[--sp];
-        }
-        node = next;
-    }
-    *err |= ERRBIT_TRAVERSAL;
-    return true;
-}
-
-// Closest hit (smallest t, ties to the lower original id).  Returns the id or -1;
-// *front = det > 0 of that hit.
-__device__ __forceinline__ int closest_hit(const BvhView& b, const Ray& r, float* tout, bool* front, uint32_t* err,
-                                           uint32_t& nn, uint32_t& nt) {
-    int stack[kStackSize];
-    int sp = 0;
-    int node = 0;
-    int best = -1;
-    float bt = INFINITY, bdet = 0.0f;
-    for (int steps = 0; steps < kTraversalCap; ++steps) {
-        ++nn;
-        float4 n0 = __ldg(b.nodes + 4 * node), n1 = __ldg(b.nodes + 4 * node + 1);
-        float4 n2 = __ldg(b.nodes + 4 * node + 2), n3 = __ldg(b.nodes + 4 * node + 3);
-        float ta, tb;
-        bool ha = slab(make_float3(n0.x, n0.y, n0.z), make_float3(n0.w, n1.x, n1.y), r, bt, &ta);
-        bool hb = slab(make_float3(n1.z, n1.w, n2.x), make_float3(n2.y, n2.z, n2.w), r, bt, &tb);
-        int ca = __float_as_int(n3.x), cb = __float_as_int(n3.y);
-        if (ha && ca < 0) {
-            float T, det; int id;
-            ++nt;
-            if (tri_test(b, ~ca, r, &T, &det, &id)) {
-                float t = sdiv(T, det);
-                if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
-            }
-            ha = false;
-        }
-        if (hb && cb < 0) {
-            float T, det; int id;
-            ++nt;
-            if (tri_test(b, ~cb, r, &T, &det, &id)) {
-                float t = sdiv(T, det);
-                if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
-            }
-            hb = false;
-        }
-        // re-check the inner children against the possibly shrunk best distance
-        if (ha && ta > bt) ha = false;
-        if (hb && tb > bt) hb = false;
-        int next = -1;
-        if (ha && hb) {
-            int first = ta <= tb ? ca : cb, second = ta <= tb ? cb : ca;
-            if (sp >= kStackSize) { *err |= ERRBIT_TRAVERSAL; break; }
-            stack[sp++] = second;
-            next = first;
-        } else if (ha) next = ca;
-        else if (hb) next = cb;
-        if (next < 0) {
-            if (sp == 0) break;
-            next = stack[--sp];
-        }
-        node = next;
-        if (steps == kTraversalCap - 1) *err |= ERRBIT_TRAVERSAL;
-    }
-    *tout = bt;
-    *front = bdet > 0.0f;
-    return best;
 }
 
 // ----------------------------------------------------------------- map texels

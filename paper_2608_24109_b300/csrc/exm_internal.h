@@ -31,7 +31,6 @@ struct exm_mesh {
     unsigned long long* nfix = nullptr;  // [nv,3] fixed-point normal sums
     unsigned long long* tfix = nullptr;  // [nuv,3] fixed-point tangent sums
     // BVH
-    float4* nodes = nullptr;   // [max(nf-1,1) * 4]
     float4* tris = nullptr;    // [nf * 3]
     float4* nodes4 = nullptr;  // [max(nf-1,1) * 8] 4-wide nodes
     int2* frontier = nullptr;  // [2 * nf] collapse frontier (binary node, 4-wide node)
@@ -41,11 +40,15 @@ struct exm_mesh {
     uint32_t* codes_sorted = nullptr;
     uint32_t* ids = nullptr;
     uint32_t* ids_sorted = nullptr;
-    int32_t* parent = nullptr;     // [2nf-1]
     int32_t* child = nullptr;      // [2*(nf-1)] encoded children
-    uint32_t* flags = nullptr;     // [nf-1]
     float* bounds = nullptr;       // [(2nf-1) * 6]
     float* scene_box = nullptr;    // [6] (ordered-int encoded min/max)
+    int32_t* ploc_c = nullptr;     // [2nf] cluster arrays (ping-pong)
+    int32_t* ploc_nn = nullptr;    // [nf] nearest neighbour of each cluster
+    unsigned long long* ploc_flag = nullptr;  // [nf] merges << 32 | keeps
+    unsigned long long* ploc_scan = nullptr;  // [nf] exclusive scan of ploc_flag
+    void* scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
     void* sort_tmp = nullptr;
     size_t sort_tmp_bytes = 0;
 };

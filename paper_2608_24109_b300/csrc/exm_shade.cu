@@ -674,8 +674,12 @@ __device__ __forceinline__ void pixel_shade(const ShadeArgs& A, uint32_t i, int 
     }
 }
 
+// Resident blocks per SM the register allocation must allow (no spills at these caps:
+// 128 / 170 registers backward, 64 / 102 forward, direct-only / with indirect).
+constexpr int shade_min_blocks(bool bwd, bool ind) { return bwd ? (ind ? 3 : 4) : (ind ? 5 : 8); }
+
 template <typename T, bool BWD, bool COUNT, bool IND>
-__global__ void __launch_bounds__(kShadeWarps * 32) shade_kernel(ShadeArgs A) {
+__global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) shade_kernel(ShadeArgs A) {
     __shared__ uint16_t s_list[kShadeWarps][kListMax];
     const int lane = threadIdx.x & 31;
     uint16_t* list = s_list[threadIdx.x >> 5];
@@ -978,7 +982,7 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     ShadeArgs A{};
     A.V = m->V; A.F = m->F; A.UV = m->UV; A.Fuv = m->Fuv;
     A.nrm = m->nrm; A.tan = m->tan; A.fsign = m->fsign;
-    A.bvh.nodes = m->nodes; A.bvh.tris = m->tris; A.bvh.nodes4 = m->nodes4;
+    A.bvh.tris = m->tris; A.bvh.nodes4 = m->nodes4;
     A.map.data = maps; A.map.W = mapW; A.map.H = mapH; A.map.wrap_u = (p->flags & EXM_FLAG_WRAP_U) != 0;
     A.env.texel = e->texel; A.env.cdf = e->cdf; A.env.rguide = e->rguide; A.env.cguide = e->cguide;
     A.env.W = e->W; A.env.H = e->H;
@@ -1023,12 +1027,27 @@ static void time_end(exm_frame* f, const exm_params* p, cudaStream_t s) {
     cudaEventRecord(f->timers.back().end, s);
 }
 
+// One resident wave: the grid-stride loop then gives every warp the same share of pixels
+// and no block waits for a second wave.
+template <typename T, bool BWD, bool COUNT, bool IND>
+static void launch_shade_one(const ShadeArgs& A, int num_sms, cudaStream_t s) {
+    static int per_sm = 0;
+    if (per_sm == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, shade_kernel<T, BWD, COUNT, IND>, kShadeWarps * 32, 0) !=
+                cudaSuccess || n < 1)
+            n = 1;
+        per_sm = n;
+    }
+    shade_kernel<T, BWD, COUNT, IND><<<num_sms * per_sm, kShadeWarps * 32, 0, s>>>(A);
+}
+
 template <bool BWD, bool COUNT, bool IND>
-static void launch_shade_t(const ShadeArgs& A, exm_dtype dt, int blocks, cudaStream_t s) {
+static void launch_shade_t(const ShadeArgs& A, exm_dtype dt, int num_sms, cudaStream_t s) {
     switch (dt) {
-        case EXM_F32: shade_kernel<float, BWD, COUNT, IND><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
-        case EXM_BF16: shade_kernel<__nv_bfloat16, BWD, COUNT, IND><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
-        default: shade_kernel<__half, BWD, COUNT, IND><<<blocks, kShadeWarps * 32, 0, s>>>(A); break;
+        case EXM_F32: launch_shade_one<float, BWD, COUNT, IND>(A, num_sms, s); break;
+        case EXM_BF16: launch_shade_one<__nv_bfloat16, BWD, COUNT, IND>(A, num_sms, s); break;
+        default: launch_shade_one<__half, BWD, COUNT, IND>(A, num_sms, s); break;
     }
 }
 
@@ -1036,16 +1055,16 @@ template <bool BWD>
 static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, exm_dtype dt,
                                cudaStream_t s) {
     if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, "map dtype");
-    const int blocks = ctx->num_sms * 8;
+    const int sms = ctx->num_sms;
     time_begin(f, p, BWD ? 3 : 2, s);
     const bool ind = A.Nb > 0 && A.lambda != 0.0f;
     const bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
     if (ind) {
-        if (count) launch_shade_t<BWD, true, true>(A, dt, blocks, s);
-        else launch_shade_t<BWD, false, true>(A, dt, blocks, s);
+        if (count) launch_shade_t<BWD, true, true>(A, dt, sms, s);
+        else launch_shade_t<BWD, false, true>(A, dt, sms, s);
     } else {
-        if (count) launch_shade_t<BWD, true, false>(A, dt, blocks, s);
-        else launch_shade_t<BWD, false, false>(A, dt, blocks, s);
+        if (count) launch_shade_t<BWD, true, false>(A, dt, sms, s);
+        else launch_shade_t<BWD, false, false>(A, dt, sms, s);
     }
     time_end(f, p, s);
     ctx->launches += 1;
