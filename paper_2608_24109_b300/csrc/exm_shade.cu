@@ -500,12 +500,20 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
                 EXM_BOX(2, z)
                 EXM_BOX(3, w)
 #undef EXM_BOX
-                // continue with the nearest hit child; push the others
-                float tn = INFINITY;
+                // closest hit: continue with the nearest hit child; any hit: with the first in slot
+                // order (an unoccluded shadow ray opens every box it crosses whatever the order,
+                // so the sort is skipped); push the others
                 int nc = -1;
+                if (CLOSEST) {
+                    float tn = INFINITY;
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
+                    for (int c = 0; c < 4; ++c)
+                        if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
+                } else {
+#pragma unroll
+                    for (int c = 3; c >= 0; --c)
+                        if (hc[c]) nc = c;
+                }
                 bool overflow = false;
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
