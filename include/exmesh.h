@@ -54,6 +54,10 @@ typedef enum { EXM_F32 = 0, EXM_BF16 = 1, EXM_F16 = 2 } exm_dtype;
 #define EXM_FLAG_ZERO_GRADS 8u   /* exm_render_backward zeroes the gradient buffers before accumulating */
 #define EXM_FLAG_TIME_KERNELS 16u /* record CUDA events around the trace and shade launches
                                      (exm_frame_kernel_ms) */
+#define EXM_FLAG_NO_SECONDARY_MATERIAL 32u /* the "No Secondary Material" ablation (Sec. 6.4): secondary
+                                     hits read no map and take a constant diffuse material (albedo 0.5,
+                                     roughness 0.5, metallic 0, flat normal map, so n_s(y) is the
+                                     interpolated vertex normal); no map gradient flows from y */
 
 typedef struct exm_ctx exm_ctx;
 typedef struct exm_mesh exm_mesh;

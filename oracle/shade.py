@@ -15,6 +15,8 @@ jitters, shadow-ray visibility, secondary hits), this module evaluates, per pixe
 * Sec. 5.3, Eq. 18-19: at each valid secondary hit y, L_sec = (1/N_s) sum_s E Vis f_d(y)
   max(n_s(y).w,0) / p; L_ind = (1/N_b) sum_j 1_hit f_d(x) L_sec(y_j) max(n_s(x).w_j,0) / p_b.
 * Eq. 20: I = L_dir + lambda_ind L_ind.  Background pixels are 0.
+* The No Secondary Material ablation (Sec. 6.4, scene.secondary_material False): no map is
+  read at y; y takes albedo 0.5, roughness 0.5, metallic 0 and a flat tangent-space normal.
 
 Readings where the paper is silent (each documented with the design): alpha = r^2 with r
 clamped to [0.08, 1]; F_dielectric = 0.04; eps = 1e-6; f_s = 0 unless n_s.wi > 0 and
@@ -237,7 +239,12 @@ def shade(scene, table, dec, V, maps, env, rows=None, specular=True, metallic=No
             by = _t(dec.sb[sl][idx][pj])
             gv, guv = F[g], Fuv[g]
             uvy = (by[:, :, None] * UV[guv]).sum(1)
-            atty = bilinear(maps, uvy, scene.wrap_u)
+            if scene.secondary_material:
+                atty = bilinear(maps, uvy, scene.wrap_u)
+            else:
+                # No Secondary Material ablation (Sec. 6.4): no map read at y; a constant grey
+                # diffuse material with a flat tangent-space normal
+                atty = torch.tensor([0.5, 0.5, 0.5, 0.5, 0.0, 0.0, 0.0, 1.0], dtype=DT).expand(uvy.shape[0], 8)
             nsy, ay, _, my = _material(atty, by, nv.detach()[gv], tuv.detach()[guv], sg[g], metallic)
             fdy = (1 - my)[:, None] * ay / math.pi
             ltex = dec.ltex[sl][idx][pj]

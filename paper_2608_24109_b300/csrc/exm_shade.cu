@@ -55,6 +55,7 @@ struct ShadeArgs {
     uint32_t nxd, nyd, nxs, nys;  // 2D strata of the direct and secondary light samples
     float lambda;
     bool metallic;
+    bool sec_material;  // false: secondary hits take the constant default material
     uint2 key;
     // wavefront state
     uint32_t* visbits;   // [P * wd]
@@ -792,7 +793,16 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                                         byd[2] * __ldg(A.UV + 2 * v2 + 1)) * A.map.H - 0.5;
                     const Footprint fpy = footprint_d(A.map, syd, tyd);
                     float atty[8];
-                    fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
+                    if (A.sec_material) {
+                        fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
+                    } else {
+                        // constant default material: grey diffuse, flat tangent-space normal
+                        atty[0] = atty[1] = atty[2] = 0.5f;
+                        atty[3] = 0.5f;
+                        atty[4] = 0.0f;
+                        atty[5] = atty[6] = 0.0f;
+                        atty[7] = 1.0f;
+                    }
                     const float3 niy = by[0] * ld3(A.nrm + 3 * q0) + by[1] * ld3(A.nrm + 3 * q1) + by[2] * ld3(A.nrm + 3 * q2);
                     const float3 tiy = by[0] * ld3(A.tan + 3 * v0) + by[1] * ld3(A.tan + 3 * v1) + by[2] * ld3(A.tan + 3 * v2);
                     const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
@@ -829,7 +839,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                         const float3 gnt = f3(dot(sy.T, gnsy), dot(sy.B, gnsy), dot(sy.n, gnsy));
                         const float3 gq = (1.0f / sy.ql) * (gnt - dot(gnt, sy.nt) * sy.nt);
                         gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
-                        if (A.gmaps) scatter8(A.gmaps, fpy, gy);
+                        if (A.gmaps && A.sec_material) scatter8(A.gmaps, fpy, gy);
                     }
                 }
                 __syncwarp();
@@ -1008,6 +1018,7 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     strata2((uint32_t)(A.Ns > 0 ? A.Ns : 1), &A.nxs, &A.nys);
     A.lambda = p->lambda_ind;
     A.metallic = (p->flags & EXM_FLAG_NO_METALLIC) == 0;
+    A.sec_material = (p->flags & EXM_FLAG_NO_SECONDARY_MATERIAL) == 0;
     A.key = make_uint2((uint32_t)p->seed, (uint32_t)(p->seed >> 32));
     A.samples = f->samples;
     A.work = f->work;

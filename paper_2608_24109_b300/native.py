@@ -30,6 +30,7 @@ FLAG_NO_METALLIC = 2
 FLAG_COUNT_WORK = 4
 FLAG_ZERO_GRADS = 8
 FLAG_TIME_KERNELS = 16
+FLAG_NO_SECONDARY_MATERIAL = 32
 
 EXPORTS = [
     "exm_create", "exm_destroy", "exm_last_error", "exm_sync",

@@ -292,6 +292,7 @@ class Scene:
     seed: int = 0
     wrap_u: bool = False
     metallic: bool = True
+    secondary_material: bool = True  # False: the No Secondary Material ablation
 
     @property
     def views(self):

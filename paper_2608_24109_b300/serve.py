@@ -37,13 +37,14 @@ class RelightServer:
         return aid
 
     def request(self, asset, env, cams, width, height, n_direct, n_bounce=0, n_light=0, lambda_ind=1.0, seed=0,
-                wrap_u=False, metallic=True, out=None):
+                wrap_u=False, metallic=True, secondary_material=True, out=None):
         cams = np.ascontiguousarray(cams, dtype=np.float32)
         if out is None:
             out = torch.empty((cams.shape[0], height, width, 3), dtype=torch.float32, device=self.device)
         env = env.contiguous()
         p = N.Params(n_direct=n_direct, n_bounce=n_bounce, n_light=n_light if n_bounce else 0, lambda_ind=lambda_ind,
-                     flags=(N.FLAG_WRAP_U if wrap_u else 0) | (0 if metallic else N.FLAG_NO_METALLIC), reserved=0,
+                     flags=(N.FLAG_WRAP_U if wrap_u else 0) | (0 if metallic else N.FLAG_NO_METALLIC) |
+                     (0 if secondary_material else N.FLAG_NO_SECONDARY_MATERIAL), reserved=0,
                      seed=seed)
         req = N.RelightReq(asset=asset, views=cams.shape[0], width=width, height=height, env=env.data_ptr(),
                            env_dtype=N.dtype_code(env.dtype), env_w=env.shape[1], env_h=env.shape[0],

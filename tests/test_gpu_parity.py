@@ -179,6 +179,17 @@ def test_forward_parity_indirect_full_frame():
     check_radiance(g, I, "cavity indirect")
 
 
+def test_no_secondary_material_flag():
+    sc = small_cavity()
+    sc.secondary_material = False
+    r, M, E, out = gpu_forward(sc)
+    keys, tab, dec, V, Mo, Eo = oracle_full(sc)
+    assert (dec.stri >= 0).sum() > 100
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    g = out.cpu().numpy()[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]]
+    check_radiance(g, I, "no secondary material")
+
+
 def test_no_metallic_flag():
     sc = ragged_tiny(48, 40, 1)
     sc.metallic = False
@@ -224,6 +235,12 @@ def test_backward_parity_tiny_all_pixels():
 
 def test_backward_parity_indirect():
     _grad_compare(small_cavity(res=48, views=1), 0, subset=False)
+
+
+def test_backward_parity_no_secondary_material():
+    sc = small_cavity(res=48, views=1)
+    sc.secondary_material = False
+    _grad_compare(sc, 0, subset=False)
 
 
 def test_autograd_function_matches_direct_backward():

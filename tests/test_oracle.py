@@ -429,6 +429,44 @@ def test_indirect_sees_cavity():
     assert np.isfinite(dec.sgap[valid]).any()
 
 
+def test_no_secondary_material_is_the_default_material():
+    """The No Secondary Material ablation (Sec. 6.4) equals the full estimator on maps that
+    already hold the default material everywhere, and differs from it on textured maps."""
+    sc = scenes.config("indirect", n=24, map_res=64, env_w=32, env_h=16, views=2, res=48, n_direct=16,
+                       n_bounce=8, n_light=4)
+    keys, tab, dec = full_decisions(sc)
+    assert (dec.stri >= 0).sum() > 20
+    flat = np.zeros_like(sc.maps)
+    flat[..., 0:4] = 0.5
+    flat[..., 7] = 1.0
+    sc.metallic = True
+    for maps, same in ((flat, True), (sc.maps, False)):
+        sc.maps = maps
+        Vt, Mt, Et = shade.scene_tensors(sc)
+        sc.secondary_material = True
+        I_full = shade.render_image(sc, tab, dec, Vt, Mt, Et)
+        sc.secondary_material = False
+        I_abl = shade.render_image(sc, tab, dec, Vt, Mt, Et)
+        if same:
+            assert torch.equal(I_full, I_abl)
+        else:
+            d = (I_full - I_abl).abs().max().item()
+            assert d > 1e-3 * I_full.abs().max().item()
+    # no map gradient flows from the secondary hits: the ablation's map gradient lives on the
+    # texels of the primary footprints (the support of the direct-only gradient), while the
+    # full estimator also reaches texels seen only through secondary hits
+    g = np.random.default_rng(2).normal(size=(dec.pix.shape[0], 3))
+    Vt, Mt, Et = shade.scene_tensors(sc)
+    grads = {}
+    for name, lam, mat in (("direct", 0.0, True), ("ablation", 1.0, False), ("full", 1.0, True)):
+        sc.lambda_ind, sc.secondary_material = lam, mat
+        grads[name] = shade.backward(sc, tab, dec, Vt, Mt, Et, g)[1].abs().sum(-1)
+    primary = grads["direct"] > 0
+    assert primary.any()
+    assert (grads["ablation"][~primary] == 0).all()
+    assert (grads["full"][~primary] > 0).any()
+
+
 # ----------------------------------------------------------------- gradients
 
 def test_autograd_matches_central_differences():
