@@ -109,7 +109,7 @@ exm_status exm_mesh_create(exm_ctx* ctx, const float* V, int nv, const int32_t* 
                            const float* UV, int nuv, const int32_t* Fuv, void* stream, exm_mesh** out);
 /* Replaces the vertex positions (DEVICE float32 [nv,3]), recomputes frames and BVH. */
 exm_status exm_mesh_update_vertices(exm_mesh* mesh, const float* V, void* stream);
-/* Rebuilds the BVH (linear BVH over 30-bit Morton codes; one triangle per leaf). */
+/* Rebuilds the BVH (Morton order, locally-ordered clustering, 4-wide nodes; one triangle per leaf). */
 exm_status exm_bvh_build(exm_mesh* mesh, void* stream);
 void exm_mesh_destroy(exm_mesh* mesh);
 /* Device pointers to the mesh's per-vertex unit normals [nv,3] and per-UV-vertex unit
@@ -234,6 +234,46 @@ exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* mesh, const
  * over n elements; grad (DEVICE float32 [n], written) = sign(pred - target) / n. */
 exm_status exm_l1_loss(const float* pred, const float* target, int64_t n, float* loss, float* grad,
                        void* stream);
+
+/* ------------------------------------------------- Stage-II objective (Sec. 5.4, Eqs. 21-24)
+ *
+ * The objective calls of one context share its FP64 accumulators and scratch: issue them on
+ * one stream (or serialise them).  Loss outputs are DEVICE float32 arrays, written; gradient
+ * outputs follow each call's rule (written or accumulated). */
+
+/* Image term of Eq. 21 on pred, target (DEVICE float32 [views,height,width,3], linear RGB):
+ * (1 - lambda_ssim) * mean|log(1 + pred) - log(1 + target)| + lambda_ssim * (1 - SSIM) with
+ * SSIM on the sRGB-encoded images, per channel, 11 x 11 Gaussian window (sigma 1.5), zero
+ * padding, C1 = 0.01^2, C2 = 0.03^2, averaged over views, pixels and channels.
+ * loss[3] = {total, log-L1, D-SSIM}; grad_rgb (DEVICE [views,height,width,3]) is WRITTEN with
+ * d(total)/d(pred). */
+exm_status exm_image_loss(exm_ctx* ctx, const float* pred, const float* target, int views, int width, int height,
+                          float lambda_ssim, float* loss, float* grad_rgb, void* stream);
+
+/* L_mat of Eq. 23 for the last exm_render_forward held by `frame`: the total variation of the
+ * screen-projected material maps (the bilinear fetch at each pixel's primary hit) of base
+ * colour, roughness and normal, plus metallic unless flags has EXM_FLAG_NO_METALLIC; each TV
+ * is the mean |difference| over horizontal neighbour pairs (both pixels covered) plus the
+ * same over vertical pairs, averaged over the map's channels.  flags' EXM_FLAG_WRAP_U selects
+ * the fetch's u rule, as in the render.  loss[1] = L_mat (unweighted); grad_maps (DEVICE
+ * float32 [mapH,mapW,8], may be NULL) is ACCUMULATED with lambda_mat * dL_mat/dmaps. */
+exm_status exm_material_tv(exm_ctx* ctx, const void* maps, exm_dtype map_dtype, int mapW, int mapH, exm_frame* frame,
+                           uint32_t flags, float lambda_mat, float* loss, float* grad_maps, void* stream);
+
+/* L_env (Eq. 23) and L_chroma (Eq. 24) of E (DEVICE float32 [envH,envW,3]): TV with
+ * longitude wrap-around; chroma = |mean(E) - mu_E 1|^2, mean over texels.  loss[2] = {TV,
+ * chroma} (unweighted); grad_env (DEVICE float32 [envH,envW,3]) is ACCUMULATED with
+ * lambda_env dTV/dE + lambda_chroma dchroma/dE (lambda_chroma is the weight at this step,
+ * lambda_chroma0 (1 - t/T) in the paper). */
+exm_status exm_env_regularizers(exm_ctx* ctx, const float* E, int envW, int envH, float lambda_env, float lambda_chroma,
+                                float* loss, float* grad_env, void* stream);
+
+/* One bias-corrected Adam step (step >= 1) on rows x channels FP32 values (DEVICE param,
+ * grad, m, v; m and v zero before the first step), then a clamp of channel c to
+ * [lo[c], hi[c]] (HOST arrays of `channels` <= 8 entries; NULL for no bound). */
+exm_status exm_adam_step(exm_ctx* ctx, float* param, const float* grad, float* m, float* v, int64_t rows, int channels,
+                         float lr, float beta1, float beta2, float eps, int step, const float* lo, const float* hi,
+                         void* stream);
 
 #ifdef __cplusplus
 }

@@ -100,6 +100,8 @@ void exm_destroy(exm_ctx* c) {
     if (!c) return;
     DeviceGuard g(c->device);
     cudaFree(c->d_status);
+    cudaFree(c->d_acc);
+    cudaFree(c->scratch);
     delete c;
 }
 
@@ -262,7 +264,8 @@ exm_status exm_env_total(exm_env* e, uint64_t* Q) {
 
 static void frame_free(exm_frame* f) {
     void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY,   f->Zq,
-                    f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr, f->prec};
+                    f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr, f->prec,
+                    f->tv_gbuf, f->tv_inv};
     for (void* p : ptrs) cudaFree(p);
     for (auto& t : f->timers) {
         cudaEventDestroy(t.begin);
@@ -418,6 +421,51 @@ exm_status exm_l1_loss(const float* pred, const float* target, int64_t n, float*
     if (blocks > (long long)sms * 8) blocks = (long long)sms * 8;
     exm_l1_kernel<<<(int)blocks, 256, 0, s>>>(pred, target, (long long)n, 1.0f / (float)n, loss, grad);
     return exm_cuda_check(cudaGetLastError(), "exm_l1_loss launch");
+}
+
+// ------------------------------------------------------ Stage-II objective (Sec. 5.4)
+
+exm_status exm_image_loss(exm_ctx* c, const float* pred, const float* target, int views, int width, int height,
+                          float lambda_ssim, float* loss, float* grad_rgb, void* stream) {
+    if (!c || !pred || !target || !loss || !grad_rgb || views < 1 || width < 1 || height < 1)
+        return exm_fail(EXM_ERR_ARG, "exm_image_loss: bad argument");
+    if ((size_t)views * 3 > 65535) return exm_fail(EXM_ERR_ARG, "exm_image_loss: more than 21845 views");
+    if (!(lambda_ssim >= 0.0f && lambda_ssim <= 1.0f)) return exm_fail(EXM_ERR_ARG, "exm_image_loss: lambda_ssim");
+    DeviceGuard g(c->device);
+    return exm_image_loss_impl(c, pred, target, views, width, height, lambda_ssim, loss, grad_rgb,
+                               (cudaStream_t)stream);
+}
+
+exm_status exm_material_tv(exm_ctx* c, const void* maps, exm_dtype map_dtype, int mapW, int mapH, exm_frame* frame,
+                           uint32_t flags, float lambda_mat, float* loss, float* grad_maps, void* stream) {
+    if (!c || !maps || !frame || !loss || mapW < 1 || mapH < 1) return exm_fail(EXM_ERR_ARG, "exm_material_tv: bad argument");
+    if (map_dtype != EXM_F32 && map_dtype != EXM_BF16 && map_dtype != EXM_F16)
+        return exm_fail(EXM_ERR_ARG, "exm_material_tv: map dtype");
+    if (frame->ctx != c) return exm_fail(EXM_ERR_ARG, "exm_material_tv: frame of another context");
+    DeviceGuard g(c->device);
+    return exm_material_tv_impl(c, maps, map_dtype, mapW, mapH, frame, flags, lambda_mat, loss, grad_maps,
+                                (cudaStream_t)stream);
+}
+
+exm_status exm_env_regularizers(exm_ctx* c, const float* E, int envW, int envH, float lambda_env, float lambda_chroma,
+                                float* loss, float* grad_env, void* stream) {
+    if (!c || !E || !loss || !grad_env || envW < 1 || envH < 1)
+        return exm_fail(EXM_ERR_ARG, "exm_env_regularizers: bad argument");
+    DeviceGuard g(c->device);
+    return exm_env_regularizers_impl(c, E, envW, envH, lambda_env, lambda_chroma, loss, grad_env, (cudaStream_t)stream);
+}
+
+exm_status exm_adam_step(exm_ctx* c, float* param, const float* grad, float* m, float* v, int64_t rows, int channels,
+                         float lr, float beta1, float beta2, float eps, int step, const float* lo, const float* hi,
+                         void* stream) {
+    if (!c || !param || !grad || !m || !v || rows < 0 || channels < 1 || channels > 8 || step < 1)
+        return exm_fail(EXM_ERR_ARG, "exm_adam_step: bad argument");
+    if (!(beta1 >= 0.0f && beta1 < 1.0f && beta2 >= 0.0f && beta2 < 1.0f))
+        return exm_fail(EXM_ERR_ARG, "exm_adam_step: beta outside [0, 1)");
+    if (rows == 0) return EXM_OK;
+    DeviceGuard g(c->device);
+    return exm_adam_step_impl(c, param, grad, m, v, (size_t)rows, channels, lr, beta1, beta2, eps, step, lo, hi,
+                              (cudaStream_t)stream);
 }
 
 }  // extern "C"

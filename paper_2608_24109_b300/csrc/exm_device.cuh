@@ -448,6 +448,40 @@ __device__ __forceinline__ void fetch8(const MapView& m, const Footprint& f, flo
     }
 }
 
+// Bilinear footprint from an integer texel position and its fractions (wrap / clamp rules of
+// footprint_d).
+__device__ __forceinline__ Footprint footprint_i(const MapView& m, int i0, int j0, float fs, float ft) {
+    Footprint f;
+    f.fs = fs;
+    f.ft = ft;
+    int c0, c1;
+    if (m.wrap_u) {
+        c0 = i0 % m.W;
+        if (c0 < 0) c0 += m.W;
+        c1 = c0 + 1 == m.W ? 0 : c0 + 1;
+    } else {
+        c0 = min(max(i0, 0), m.W - 1);
+        c1 = min(max(i0 + 1, 0), m.W - 1);
+    }
+    const int r0 = min(max(j0, 0), m.H - 1), r1 = min(max(j0 + 1, 0), m.H - 1);
+    f.t[0] = (uint32_t)r0 * m.W + c0;
+    f.t[1] = (uint32_t)r0 * m.W + c1;
+    f.t[2] = (uint32_t)r1 * m.W + c0;
+    f.t[3] = (uint32_t)r1 * m.W + c1;
+    return f;
+}
+
+// Adds the 8-channel gradient g to the four texels of a footprint, bilinearly weighted.
+__device__ __forceinline__ void scatter8(float* gmaps, const Footprint& fp, const float g[8]) {
+    float w[4] = {(1.f - fp.fs) * (1.f - fp.ft), fp.fs * (1.f - fp.ft), (1.f - fp.fs) * fp.ft, fp.fs * fp.ft};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4* p = reinterpret_cast<float4*>(gmaps) + 2 * (size_t)fp.t[k];
+        atomicAdd(p, make_float4(w[k] * g[0], w[k] * g[1], w[k] * g[2], w[k] * g[3]));
+        atomicAdd(p + 1, make_float4(w[k] * g[4], w[k] * g[5], w[k] * g[6], w[k] * g[7]));
+    }
+}
+
 // ------------------------------------------------------------------ small vectors
 __device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
 __device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }

@@ -14,6 +14,9 @@ struct exm_ctx {
     int num_sms = 0;
     uint32_t* d_status = nullptr;  // latched device error bits
     unsigned long long launches = 0;  // kernels launched by the library on this context
+    double* d_acc = nullptr;          // FP64 accumulators of the objective calls
+    float* scratch = nullptr;         // objective scratch (SSIM coefficients)
+    size_t scratch_cap = 0;
 };
 
 struct exm_mesh {
@@ -101,15 +104,45 @@ struct exm_frame {
     uint32_t* ctr = nullptr;      // per chunk: queued / fetched counters
     size_t ctr_cap = 0;
     int last_nd = -1, last_nb = -1, last_ns = -1, last_wd = 0, last_ws = 0;
+    float* tv_gbuf = nullptr;     // [P * 8] projected material of the material TV
+    size_t tv_gbuf_cap = 0;
+    int32_t* tv_inv = nullptr;    // [views*H*W] covered index of each screen pixel
+    size_t tv_inv_cap = 0;
     struct Timer { int which; cudaEvent_t begin, end; };
     std::vector<Timer> timers;    // EXM_FLAG_TIME_KERNELS
 };
+
+// Grows a device buffer to hold `need` elements (contents are not kept); false on OOM.
+template <typename TT>
+inline bool ensure(TT** ptr, size_t* cap, size_t need) {
+    if (need <= *cap && *ptr) return true;
+    cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    if (cudaMalloc((void**)ptr, need * sizeof(TT)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    *cap = need;
+    return true;
+}
 
 // error helpers (exm_api.cu)
 exm_status exm_fail(exm_status code, const std::string& msg);
 exm_status exm_cuda_check(cudaError_t e, const char* what);
 
 exm_status upload_cameras(exm_frame* f, const exm_camera* cams, int views, cudaStream_t s);
+
+// Stage-II objective (exm_objective.cu)
+exm_status exm_image_loss_impl(exm_ctx* ctx, const float* pred, const float* target, int views, int W, int H,
+                               float lambda_ssim, float* loss, float* grad, cudaStream_t s);
+exm_status exm_material_tv_impl(exm_ctx* ctx, const void* maps, exm_dtype dt, int mapW, int mapH, exm_frame* f,
+                                uint32_t flags, float lambda_mat, float* loss, float* grad_maps, cudaStream_t s);
+exm_status exm_env_regularizers_impl(exm_ctx* ctx, const float* E, int W, int H, float lambda_env,
+                                     float lambda_chroma, float* loss, float* grad_env, cudaStream_t s);
+exm_status exm_adam_step_impl(exm_ctx* ctx, float* param, const float* grad, float* m, float* v, size_t rows,
+                              int channels, float lr, float beta1, float beta2, float eps, int step, const float* lo,
+                              const float* hi, cudaStream_t s);
 
 // kernels launchers
 exm_status exm_frames_build(exm_mesh* m, cudaStream_t s);

@@ -229,16 +229,6 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 ns, float3 wi, float3 wo
     gns += gci * wi;
 }
 
-__device__ __forceinline__ void scatter8(float* gmaps, const Footprint& fp, const float g[8]) {
-    float w[4] = {(1.f - fp.fs) * (1.f - fp.ft), fp.fs * (1.f - fp.ft), (1.f - fp.fs) * fp.ft, fp.fs * fp.ft};
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        float4* p = reinterpret_cast<float4*>(gmaps) + 2 * (size_t)fp.t[k];
-        atomicAdd(p, make_float4(w[k] * g[0], w[k] * g[1], w[k] * g[2], w[k] * g[3]));
-        atomicAdd(p + 1, make_float4(w[k] * g[4], w[k] * g[5], w[k] * g[6], w[k] * g[7]));
-    }
-}
-
 // Material and shading normal from 8 fetched channels and the interpolated frame.
 struct Surface {
     float3 a;
@@ -619,29 +609,6 @@ __global__ void __launch_bounds__(256) pixel_prep_kernel(ShadeArgs A) {
         R[3] = make_float4(org.x, org.y, org.z, ngs.x);
         R[4] = make_float4(ngs.y, ngs.z, 0.0f, 0.0f);
     }
-}
-
-// Bilinear footprint from an integer texel position and its fractions (wrap / clamp rules of
-// footprint_d).
-__device__ __forceinline__ Footprint footprint_i(const MapView& m, int i0, int j0, float fs, float ft) {
-    Footprint f;
-    f.fs = fs;
-    f.ft = ft;
-    int c0, c1;
-    if (m.wrap_u) {
-        c0 = i0 % m.W;
-        if (c0 < 0) c0 += m.W;
-        c1 = c0 + 1 == m.W ? 0 : c0 + 1;
-    } else {
-        c0 = min(max(i0, 0), m.W - 1);
-        c1 = min(max(i0 + 1, 0), m.W - 1);
-    }
-    const int r0 = min(max(j0, 0), m.H - 1), r1 = min(max(j0 + 1, 0), m.H - 1);
-    f.t[0] = (uint32_t)r0 * m.W + c0;
-    f.t[1] = (uint32_t)r0 * m.W + c1;
-    f.t[2] = (uint32_t)r1 * m.W + c0;
-    f.t[3] = (uint32_t)r1 * m.W + c1;
-    return f;
 }
 
 // Shading state of a covered pixel (Eqs. 10-11) from its record: fetched channels (and their
@@ -1098,20 +1065,6 @@ static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const 
     else trace_kernel<CLOSEST, false><<<blocks, kTraceThreads, 0, s>>>(A);
     time_end(f, p, s);
     ctx->launches += 1;
-}
-
-template <typename TT>
-static bool ensure(TT** ptr, size_t* cap, size_t need) {
-    if (need <= *cap && *ptr) return true;
-    cudaFree(*ptr);
-    *ptr = nullptr;
-    *cap = 0;
-    if (cudaMalloc((void**)ptr, need * sizeof(TT)) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    *cap = need;
-    return true;
 }
 
 exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,

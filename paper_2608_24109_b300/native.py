@@ -41,6 +41,7 @@ EXPORTS = [
     "exm_render_forward", "exm_render_backward", "exm_render_backward_noalloc", "exm_l1_loss",
     "exm_server_create", "exm_server_destroy", "exm_server_add_asset", "exm_relight_submit", "exm_relight_poll",
     "exm_server_progress", "exm_server_stats", "exm_relight_footprint",
+    "exm_image_loss", "exm_material_tv", "exm_env_regularizers", "exm_adam_step",
 ]
 
 
@@ -74,7 +75,7 @@ def lib():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libexmesh.so is not built ({LIB_PATH}); run __graft_entry__.build()")
     L = ctypes.CDLL(LIB_PATH)
-    P, I, I64, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64
+    P, I, I64, U64, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_float
     PP = ctypes.POINTER(ctypes.c_void_p)
     sig = {
         "exm_create": ([I, PP], I),
@@ -110,6 +111,10 @@ def lib():
         "exm_server_stats": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64),
                               ctypes.POINTER(U64)], I),
         "exm_relight_footprint": ([P, ctypes.POINTER(RelightReq), ctypes.POINTER(U64)], I),
+        "exm_image_loss": ([P, P, P, I, I, I, F, P, P, P], I),
+        "exm_material_tv": ([P, P, I, I, I, P, ctypes.c_uint32, F, P, P, P], I),
+        "exm_env_regularizers": ([P, P, I, I, F, F, P, P, P], I),
+        "exm_adam_step": ([P, P, P, P, P, I64, I, F, F, F, F, I, ctypes.POINTER(F), ctypes.POINTER(F), P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -329,3 +334,35 @@ def exm_relight_footprint(server, req: RelightReq):
     b = ctypes.c_uint64()
     check(lib().exm_relight_footprint(server, ctypes.byref(req), ctypes.byref(b)))
     return b.value
+
+
+# ------------------------------------------------------------------ Stage-II objective
+
+def exm_image_loss(ctx, pred, target, lambda_ssim, loss, grad_rgb, stream=None):
+    V, H, W, C = pred.shape
+    assert C == 3 and target.shape == pred.shape and loss.numel() >= 3 and grad_rgb.shape == pred.shape
+    return check(lib().exm_image_loss(ctx, _ptr(pred), _ptr(target), V, W, H, float(lambda_ssim), _ptr(loss),
+                                      _ptr(grad_rgb), _stream(stream)))
+
+
+def exm_material_tv(ctx, maps, frame, flags, lambda_mat, loss, grad_maps=None, stream=None):
+    assert maps.shape[-1] == 8 and loss.numel() >= 1
+    return check(lib().exm_material_tv(ctx, _ptr(maps), dtype_code(maps.dtype), maps.shape[1], maps.shape[0], frame,
+                                       int(flags), float(lambda_mat), _ptr(loss), _ptr(grad_maps), _stream(stream)))
+
+
+def exm_env_regularizers(ctx, E, lambda_env, lambda_chroma, loss, grad_env, stream=None):
+    assert E.shape[-1] == 3 and loss.numel() >= 2 and grad_env.shape == E.shape
+    return check(lib().exm_env_regularizers(ctx, _ptr(E), E.shape[1], E.shape[0], float(lambda_env),
+                                            float(lambda_chroma), _ptr(loss), _ptr(grad_env), _stream(stream)))
+
+
+def exm_adam_step(ctx, param, grad, m, v, lr, step, lo=None, hi=None, beta1=0.9, beta2=0.999, eps=1e-8,
+                  stream=None):
+    channels = param.shape[-1]
+    rows = param.numel() // channels
+    F = ctypes.c_float * channels
+    lo_a = F(*lo) if lo is not None else None
+    hi_a = F(*hi) if hi is not None else None
+    return check(lib().exm_adam_step(ctx, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), rows, channels, float(lr),
+                                     float(beta1), float(beta2), float(eps), int(step), lo_a, hi_a, _stream(stream)))
