@@ -224,7 +224,8 @@ def shade(scene, table, dec, V, maps, env, rows=None, specular=True, metallic=No
     fcos = brdf_cos(ns[:, None, :].expand(-1, Nd, -1), wi, wo[:, None, :].expand(-1, Nd, -1),
                     a[:, None, :].expand(-1, Nd, -1), r[:, None].expand(-1, Nd), m[:, None].expand(-1, Nd),
                     specular=specular)
-    Ldir = (vis[..., None] * E * fcos / pdf[..., None]).sum(1) / Nd
+    # an empty sample set (the indirect-only half-resolution pass) has no direct term
+    Ldir = (vis[..., None] * E * fcos / pdf[..., None]).sum(1) / Nd if Nd > 0 else torch.zeros((idx.size, 3), dtype=DT)
     total = Ldir
     # --- one-bounce indirect (Sec. 5.3, Eqs. 18-19)
     Nb = dec.stri.shape[1]
