@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="offered requests per second")
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--budget-gb", type=int, default=24)
+    ap.add_argument("--half-res-indirect", action="store_true",
+                    help="indirect light at half resolution, upsampled (the paper's speed variant)")
     ap.add_argument("--stage2", action="store_true",
                     help="time whole Stage-II iterations: render, objective, adjoint, Adam")
     return ap.parse_args()
@@ -212,6 +214,7 @@ def run_native(args, world, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     sc = scenes.config(args.workload, **({"views": args.views} if args.views else {}))
+    sc.half_res_indirect = args.half_res_indirect
     r = Renderer.from_scene(sc, device=local)
     mdt = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[args.maps]
     edt = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[args.env_dtype]
@@ -331,6 +334,7 @@ def run_native(args, world, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload + ": " + WORKLOADS[args.workload],
                    "map_storage": args.maps, "env_storage": args.env_dtype, "covered_pixels": covered, "shaded_samples_per_step": samples,
+                   "indirect_resolution": "half, upsampled" if args.half_res_indirect else "full",
                    "l2": "flushed between steps (256 MiB write outside the timed region)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "ms_forward": mf, "ms_backward": mb,

@@ -58,6 +58,13 @@ typedef enum { EXM_F32 = 0, EXM_BF16 = 1, EXM_F16 = 2 } exm_dtype;
                                      hits read no map and take a constant diffuse material (albedo 0.5,
                                      roughness 0.5, metallic 0, flat normal map, so n_s(y) is the
                                      interpolated vertex normal); no map gradient flows from y */
+#define EXM_FLAG_HALF_RES_INDIRECT 64u /* indirect light at half resolution (Sec. 6.1 implementation
+                                     details): the frame renders direct light; a child frame of
+                                     ceil(W/2) x ceil(H/2) pixels renders the same cameras with halved
+                                     intrinsics (pixel (i, j) centred on full-resolution (2i+1, 2j+1))
+                                     and the indirect term only; each covered pixel adds its bilinear
+                                     interpolation at ((x + 1/2)/2 - 1/2, (y + 1/2)/2 - 1/2), taps
+                                     clamped to the image.  Not offered by exm_render_backward_noalloc */
 
 typedef struct exm_ctx exm_ctx;
 typedef struct exm_mesh exm_mesh;

@@ -24,7 +24,7 @@ import numpy as np
 import torch
 
 from . import Decisions, EnvTable, covered_pixels, raster_full
-from .shade import DT, render_image
+from .shade import DT, shade
 
 
 def half_scene(scene):
@@ -69,7 +69,9 @@ def _image(scene, table, V, maps, env):
     st, keys = raster_full(scene.V, scene.F, scene.cams, scene.width, scene.height)
     pix = covered_pixels(keys)
     dec = Decisions(scene, table, pix, keys[pix[:, 0], pix[:, 1], pix[:, 2]])
-    rad = render_image(scene, table, dec, V, maps, env)
+    # chunked like render_image, but keeping the autograd graph when the inputs require grad
+    rad = torch.cat([shade(scene, table, dec, V, maps, env, rows=slice(s, s + 4096))
+                     for s in range(0, dec.pix.shape[0], 4096)])
     img = torch.zeros((scene.views, scene.height, scene.width, 3), dtype=DT)
     p = torch.as_tensor(pix, dtype=torch.long)
     img = img.index_put((p[:, 0], p[:, 1], p[:, 2]), rad)

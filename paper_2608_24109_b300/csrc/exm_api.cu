@@ -265,8 +265,13 @@ exm_status exm_env_total(exm_env* e, uint64_t* Q) {
 static void frame_free(exm_frame* f) {
     void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY,   f->Zq,
                     f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr, f->prec,
-                    f->tv_gbuf, f->tv_inv};
+                    f->tv_gbuf, f->tv_inv, f->half_img, f->half_grad};
     for (void* p : ptrs) cudaFree(p);
+    if (f->half) {
+        frame_free(f->half);
+        delete f->half;
+        f->half = nullptr;
+    }
     for (auto& t : f->timers) {
         cudaEventDestroy(t.begin);
         cudaEventDestroy(t.end);
@@ -317,6 +322,11 @@ exm_status exm_frame_stats(exm_frame* f, uint64_t* covered, uint64_t* samples) {
     unsigned long long smp = 0;
     exm_status st = exm_cuda_check(cudaMemcpy(&cnt, f->counters, 4, cudaMemcpyDeviceToHost), "frame stats");
     if (st == EXM_OK) st = exm_cuda_check(cudaMemcpy(&smp, f->samples, 8, cudaMemcpyDeviceToHost), "frame stats");
+    if (st == EXM_OK && f->half) {  // samples of the half-resolution indirect pass
+        unsigned long long hs = 0;
+        st = exm_cuda_check(cudaMemcpy(&hs, f->half->samples, 8, cudaMemcpyDeviceToHost), "frame stats");
+        smp += hs;
+    }
     if (covered) *covered = cnt;
     if (samples) *samples = smp;
     return st;
@@ -325,7 +335,13 @@ exm_status exm_frame_stats(exm_frame* f, uint64_t* covered, uint64_t* samples) {
 exm_status exm_frame_work(exm_frame* f, uint64_t counts[4]) {
     if (!f || !counts) return exm_fail(EXM_ERR_ARG, "exm_frame_work: NULL argument");
     DeviceGuard g(f->ctx->device);
-    return exm_cuda_check(cudaMemcpy(counts, f->work, 32, cudaMemcpyDeviceToHost), "frame work counters");
+    exm_status st = exm_cuda_check(cudaMemcpy(counts, f->work, 32, cudaMemcpyDeviceToHost), "frame work counters");
+    if (st == EXM_OK && f->half) {
+        uint64_t h[4];
+        st = exm_cuda_check(cudaMemcpy(h, f->half->work, 32, cudaMemcpyDeviceToHost), "frame work counters");
+        for (int k = 0; k < 4; ++k) counts[k] += h[k];
+    }
+    return st;
 }
 
 exm_status exm_frame_kernel_ms(exm_frame* f, float ms[4]) {
@@ -342,6 +358,11 @@ exm_status exm_frame_kernel_ms(exm_frame* f, float ms[4]) {
         cudaEventDestroy(t.end);
     }
     f->timers.clear();
+    if (st == EXM_OK && f->half) {
+        float h[4];
+        st = exm_frame_kernel_ms(f->half, h);
+        for (int k = 0; k < 4; ++k) ms[k] += h[k];
+    }
     return st;
 }
 
@@ -388,6 +409,8 @@ exm_status exm_render_forward(exm_ctx* c, const exm_mesh* m, const void* maps, e
     if (!out_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_forward: out_rgb is NULL");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if ((p->flags & EXM_FLAG_HALF_RES_INDIRECT) && p->n_bounce > 0 && p->lambda_ind != 0.0f)
+        return exm_render_forward_halfres(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, out_rgb, s);
     st = upload_cameras(f, cams, views, s);
     if (st != EXM_OK) return st;
     st = exm_raster_impl(c, m, f, views, s);
@@ -404,6 +427,9 @@ exm_status exm_render_backward(exm_ctx* c, const exm_mesh* m, const void* maps, 
     if (!grad_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_backward: grad_rgb is NULL");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
+    if ((p->flags & EXM_FLAG_HALF_RES_INDIRECT) && p->n_bounce > 0 && p->lambda_ind != 0.0f)
+        return exm_render_backward_halfres(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, grad_rgb, grad_maps,
+                                           grad_env, grad_V, s);
     st = upload_cameras(f, cams, views, s);
     if (st != EXM_OK) return st;
     return exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, f, p, grad_rgb, grad_maps, grad_env, grad_V, s);

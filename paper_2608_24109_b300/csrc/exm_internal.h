@@ -104,6 +104,11 @@ struct exm_frame {
     uint32_t* ctr = nullptr;      // per chunk: queued / fetched counters
     size_t ctr_cap = 0;
     int last_nd = -1, last_nb = -1, last_ns = -1, last_wd = 0, last_ws = 0;
+    exm_frame* half = nullptr;    // half-resolution indirect pass (EXM_FLAG_HALF_RES_INDIRECT)
+    float* half_img = nullptr;    // [views*H'*W'*3] its lambda_ind L_ind image
+    size_t half_img_cap = 0;
+    float* half_grad = nullptr;   // [views*H'*W'*3] adjoint of the upsampling
+    size_t half_grad_cap = 0;
     float* tv_gbuf = nullptr;     // [P * 8] projected material of the material TV
     size_t tv_gbuf_cap = 0;
     int32_t* tv_inv = nullptr;    // [views*H*W] covered index of each screen pixel
@@ -132,6 +137,15 @@ exm_status exm_fail(exm_status code, const std::string& msg);
 exm_status exm_cuda_check(cudaError_t e, const char* what);
 
 exm_status upload_cameras(exm_frame* f, const exm_camera* cams, int views, cudaStream_t s);
+
+// the half-resolution indirect pass (exm_halfres.cu)
+exm_status exm_render_forward_halfres(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW,
+                                      int mapH, const exm_env* e, const exm_camera* cams, int views,
+                                      const exm_params* p, exm_frame* f, float* out, cudaStream_t s);
+exm_status exm_render_backward_halfres(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW,
+                                       int mapH, const exm_env* e, const exm_camera* cams, int views,
+                                       const exm_params* p, exm_frame* f, const float* grad_rgb, float* grad_maps,
+                                       float* grad_env, float* grad_V, cudaStream_t s);
 
 // Stage-II objective (exm_objective.cu)
 exm_status exm_image_loss_impl(exm_ctx* ctx, const float* pred, const float* target, int views, int W, int H,

@@ -77,14 +77,28 @@ struct exm_server {
 
 // Device bytes a request needs while it runs: the frame (visibility buffer, pixel list,
 // snapped vertices, visibility bits, secondary hits, ray queue) and the environment tables.
+// Device bytes of one frame: visibility keys and pixel list, 80-byte pixel records, snapped
+// vertices, visibility bits, secondary hit ids, the ray queue of a chunk, cameras, counters.
+static size_t frame_bytes(size_t P, size_t views, size_t nv, int wd, int ws, int nb, size_t ray_cap) {
+    return P * (8 + 4 + 80) + views * nv * 12 + P * (size_t)(wd + ws) * 4 + P * (size_t)nb * 4 + ray_cap * 32 +
+           views * 80 + 64;
+}
+
 static size_t request_footprint(const exm_server* s, const exm_relight_req& r) {
     const size_t P = (size_t)r.views * r.width * r.height;
     const size_t nv = (size_t)s->assets[r.asset].mesh->nv;
     const int wd = (r.params.n_direct + 31) / 32;
     const bool ind = r.params.n_bounce > 0 && r.params.lambda_ind != 0.0f;
     const int ws = ind ? (r.params.n_bounce * r.params.n_light + 31) / 32 : 0;
-    size_t frame = P * (8 + 4) + (size_t)r.views * nv * 12 + P * (size_t)(wd + ws) * 4 +
-                   (ind ? P * (size_t)r.params.n_bounce * 4 : 0) + (size_t)s->ray_cap * 32 + (size_t)r.views * 80 + 64;
+    size_t frame;
+    if (ind && (r.params.flags & EXM_FLAG_HALF_RES_INDIRECT)) {
+        // direct-only frame, plus the half-resolution child frame and its image
+        const size_t Ph = (size_t)r.views * ((r.width + 1) / 2) * ((r.height + 1) / 2);
+        frame = frame_bytes(P, r.views, nv, wd, 0, 0, s->ray_cap) +
+                frame_bytes(Ph, r.views, nv, 0, ws, r.params.n_bounce, s->ray_cap) + Ph * 12;
+    } else {
+        frame = frame_bytes(P, r.views, nv, wd, ws, ind ? r.params.n_bounce : 0, s->ray_cap);
+    }
     const size_t n = (size_t)r.env_w * r.env_h;
     int rb = 1, cb = 1;
     while ((1 << rb) < r.env_h && rb < 20) ++rb;

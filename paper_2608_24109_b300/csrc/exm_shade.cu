@@ -1102,8 +1102,10 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
             launch_trace<true>(ctx, f, p, A, s);
             ctx->launches += 1;
         }
-        gen_direct_kernel<<<exm_blocks((size_t)Pc * ((p->n_direct + kGenK - 1) / kGenK), 256), 256, 0, s>>>(A);
-        ctx->launches += 1;
+        if (p->n_direct > 0) {  // 0 in the indirect-only half-resolution pass
+            gen_direct_kernel<<<exm_blocks((size_t)Pc * ((p->n_direct + kGenK - 1) / kGenK), 256), 256, 0, s>>>(A);
+            ctx->launches += 1;
+        }
         if (indirect) {
             gen_seclight_kernel<<<exm_blocks((size_t)Pc, 256), 256, 0, s>>>(A);
             ctx->launches += 1;
@@ -1234,6 +1236,8 @@ extern "C" exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* 
         return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: sample counts");
     if (m->ctx != ctx || e->ctx != ctx || f->ctx != ctx)
         return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: objects of another context");
+    if (p->flags & EXM_FLAG_HALF_RES_INDIRECT)
+        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: half-resolution indirect light is not offered");
     int prev = -1;
     cudaGetDevice(&prev);
     if (prev != ctx->device) cudaSetDevice(ctx->device);

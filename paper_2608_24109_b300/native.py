@@ -31,6 +31,7 @@ FLAG_COUNT_WORK = 4
 FLAG_ZERO_GRADS = 8
 FLAG_TIME_KERNELS = 16
 FLAG_NO_SECONDARY_MATERIAL = 32
+FLAG_HALF_RES_INDIRECT = 64
 
 EXPORTS = [
     "exm_create", "exm_destroy", "exm_last_error", "exm_sync",

@@ -15,7 +15,8 @@ class Renderer:
     (visibility buffer) for `views` cameras at width x height, on one CUDA device."""
 
     def __init__(self, V, F, UV, Fuv, env_w, env_h, cams, width, height, n_direct, n_bounce=0, n_light=0,
-                 lambda_ind=1.0, seed=0, wrap_u=False, metallic=True, secondary_material=True, device=0):
+                 lambda_ind=1.0, seed=0, wrap_u=False, metallic=True, secondary_material=True,
+                 half_res_indirect=False, device=0):
         self.device = torch.device("cuda", device)
         dev = self.device
         self.V = torch.as_tensor(np.asarray(V), dtype=torch.float32, device=dev).contiguous()
@@ -28,7 +29,8 @@ class Renderer:
         self.params = N.Params(n_direct=n_direct, n_bounce=n_bounce, n_light=max(n_light, 1 if n_bounce else 0),
                                lambda_ind=lambda_ind, flags=(N.FLAG_WRAP_U if wrap_u else 0) |
                                (0 if metallic else N.FLAG_NO_METALLIC) |
-                               (0 if secondary_material else N.FLAG_NO_SECONDARY_MATERIAL), reserved=0, seed=seed)
+                               (0 if secondary_material else N.FLAG_NO_SECONDARY_MATERIAL) |
+                               (N.FLAG_HALF_RES_INDIRECT if half_res_indirect else 0), reserved=0, seed=seed)
         self.ctx = N.exm_create(device)
         self.mesh = N.exm_mesh_create(self.ctx, self.V, self.F, self.UV, self.Fuv)
         self.env = N.exm_env_create(self.ctx, env_w, env_h)
@@ -40,7 +42,7 @@ class Renderer:
     def from_scene(cls, sc, device=0, **kw):
         args = dict(n_direct=sc.n_direct, n_bounce=sc.n_bounce, n_light=sc.n_light, lambda_ind=sc.lambda_ind,
                     seed=sc.seed, wrap_u=sc.wrap_u, metallic=sc.metallic,
-                    secondary_material=sc.secondary_material)
+                    secondary_material=sc.secondary_material, half_res_indirect=sc.half_res_indirect)
         args.update(kw)
         return cls(sc.V, sc.F, sc.UV, sc.Fuv, sc.env.shape[1], sc.env.shape[0], sc.cams, sc.width, sc.height,
                    device=device, **args)

@@ -293,6 +293,7 @@ class Scene:
     wrap_u: bool = False
     metallic: bool = True
     secondary_material: bool = True  # False: the No Secondary Material ablation
+    half_res_indirect: bool = False  # indirect light at half resolution, then upsampled
 
     @property
     def views(self):
