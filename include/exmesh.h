@@ -282,6 +282,44 @@ exm_status exm_adam_step(exm_ctx* ctx, float* param, const float* grad, float* m
                          float lr, float beta1, float beta2, float eps, int step, const float* lo, const float* hi,
                          void* stream);
 
+/* ------------------------------------------- Stage-I topology round (Sec. 4.1-4.3, Eqs. 1-6) */
+
+typedef struct {
+    float beta_g;          /* EMA coefficient of Eq. 1 (0.95) */
+    float w_g, w_k;        /* split-score weights of Eq. 3 (0.6, 0.4) */
+    float tau_degen;       /* degeneracy threshold of Eq. 4 (0.05) */
+    float tau_uv;          /* UV seam distance of Eqs. 5-6 (1e-4) */
+    int32_t split_percent; /* faces tried for splitting per round, percent of the face count (5) */
+    int32_t max_faces;     /* face budget (200000) */
+    int32_t reserved;
+} exm_topology_params;
+
+typedef struct exm_topology exm_topology;
+exm_status exm_topology_create(exm_ctx* ctx, exm_topology** out);
+void exm_topology_destroy(exm_topology* topo);
+
+/* Per-face count of covered pixels in the frame's last raster (C_rend of Sec. 4.2), ADDED to
+ * counts (DEVICE uint32 [nf]). */
+exm_status exm_face_render_counts(exm_frame* frame, int nf, uint32_t* counts, void* stream);
+
+/* One topology round on the mesh V [nv,3], F [nf,3], UV [nuv,2], Fuv [nf,3] (DEVICE, read
+ * only) with the vertex EMA state ema [nv], this iteration's position gradients grad_V [nv,3]
+ * and the render counts [nf] (DEVICE).  Updates the EMA (Eq. 1); scores faces (Eqs. 2-3);
+ * splits the best-scoring large faces on their best edge, greedily in rank order with no face
+ * modified twice, keeping separate UVs across seams (Eqs. 5-6); then collapses small
+ * degenerate or never-rendered faces (Eq. 4) on the split mesh, greedily in rank order; deletes
+ * the faces that lose a vertex and compacts vertices, faces and UVs.  Every floating-point
+ * decision is taken in FP32 in a fixed operation order (arccos by Abramowitz and Stegun
+ * 4.4.46), so the result is deterministic.  Synchronous (it reads sizes back); the result is
+ * held by `topo` until its next round. */
+exm_status exm_topology_round(exm_topology* topo, const float* V, int nv, const int32_t* F, int nf, const float* UV,
+                              int nuv, const int32_t* Fuv, const float* ema, const float* grad_V,
+                              const uint32_t* render_counts, const exm_topology_params* params, void* stream);
+/* Sizes and DEVICE pointers of the last round's mesh and EMA (valid until the next round or
+ * destroy); stats = {splits, merges, faces deleted}.  Any output pointer may be NULL. */
+exm_status exm_topology_result(exm_topology* topo, int* nv, int* nf, int* nuv, const float** V, const int32_t** F,
+                               const float** UV, const int32_t** Fuv, const float** ema, int stats[3]);
+
 #ifdef __cplusplus
 }
 #endif

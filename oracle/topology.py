@@ -18,9 +18,10 @@ with the design):
    split edge maximises l_e / mean degree (ties: edge order (0,1), (1,2), (2,0)); the new
    vertex is the mean of the projections of the two opposite vertices onto the edge line
    (the midpoint on a boundary edge); mu = |v_s - v_a| / |v_b - v_a| outside [0.25, 0.75]
-   discards the split.  A split is skipped when one of its faces was already modified in the
-   round, or when it would exceed the face budget.  Edge choice, v_s and mu use the mesh at
-   the start of the round.
+   discards the split.  A split is skipped when one of its faces was already claimed by an
+   accepted split (greedy in rank order).  The accepted splits are then applied in rank order
+   while the face count stays within the face budget; the rest are dropped.  Edge choice, v_s
+   and mu use the mesh at the start of the round.
 6. UV maintenance (Eqs. 5-6): u_s interpolated at mu in the UV space of each old face; two
    candidates closer than tau_uv share one averaged UV, else each side keeps its own.
 7. Merging, on the mesh after the splits: unmodified faces with C_rend = 0 or D_f < tau_degen
@@ -201,27 +202,38 @@ def topology_round(V, F, UV, Fuv, G, grad_V, render_counts, prm: TopoParams = To
     cand = [f for f in range(nf) if area[f] >= amed]
     cand.sort(key=lambda f: (-float(S[f]), f))
     cand = cand[:(nf * prm.split_percent + 99) // 100]
-    touched = np.zeros(nf, bool)
-    F0, Fuv0 = F.copy(), Fuv.copy()  # the mesh at the start of the round (F is rewritten below)
-    new_V, new_G, new_F, new_Fuv, new_UV = [], [], [], [], []
-    faces_now = nf
-    n_split = 0
+    # greedy selection in rank order on the mesh at the start of the round
+    claimed = np.zeros(nf, bool)
+    accepted = []
     for f in cand:
-        score = [f32(elen[f, k] / f32(f32(deg[F0[f, k]] + deg[F0[f, (k + 1) % 3]]) * f32(0.5))) for k in range(3)]
+        score = [f32(elen[f, k] / f32(f32(deg[F[f, k]] + deg[F[f, (k + 1) % 3]]) * f32(0.5))) for k in range(3)]
         k = 0
         for c in (1, 2):
             if score[c] > score[k]:
                 k = c
-        g, kg = _neighbour(faces_of, F0, f, k)
-        vs, mu = split_vertex(V, F0, f, k, g, kg)
+        g, kg = _neighbour(faces_of, F, f, k)
+        vs, mu = split_vertex(V, F, f, k, g, kg)
         if not (f32(0.25) <= mu <= f32(0.75)):
             continue
-        if touched[f] or (g >= 0 and touched[g]):
+        if claimed[f] or (g >= 0 and claimed[g]):
             continue
-        add = 2 if g >= 0 else 1
+        claimed[f] = True
+        if g >= 0:
+            claimed[g] = True
+        accepted.append((f, k, g, kg, vs, mu))
+    # the face budget keeps a prefix of the accepted splits
+    applied, faces_now = [], nf
+    for sp in accepted:
+        add = 2 if sp[2] >= 0 else 1
         if faces_now + add > prm.max_faces:
-            continue
+            break
         faces_now += add
+        applied.append(sp)
+    touched = np.zeros(nf, bool)
+    F0, Fuv0 = F.copy(), Fuv.copy()  # the mesh at the start of the round (F is rewritten below)
+    new_V, new_G, new_F, new_Fuv, new_UV = [], [], [], [], []
+    n_split = 0
+    for (f, k, g, kg, vs, mu) in applied:
         touched[f] = True
         if g >= 0:
             touched[g] = True

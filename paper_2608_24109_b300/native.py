@@ -43,6 +43,8 @@ EXPORTS = [
     "exm_server_create", "exm_server_destroy", "exm_server_add_asset", "exm_relight_submit", "exm_relight_poll",
     "exm_server_progress", "exm_server_stats", "exm_relight_footprint",
     "exm_image_loss", "exm_material_tv", "exm_env_regularizers", "exm_adam_step",
+    "exm_topology_create", "exm_topology_destroy", "exm_face_render_counts", "exm_topology_round",
+    "exm_topology_result",
 ]
 
 
@@ -56,6 +58,12 @@ class Params(ctypes.Structure):
     _fields_ = [("n_direct", ctypes.c_int32), ("n_bounce", ctypes.c_int32), ("n_light", ctypes.c_int32),
                 ("lambda_ind", ctypes.c_float), ("flags", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
                 ("seed", ctypes.c_uint64)]
+
+
+class TopologyParams(ctypes.Structure):
+    _fields_ = [("beta_g", ctypes.c_float), ("w_g", ctypes.c_float), ("w_k", ctypes.c_float),
+                ("tau_degen", ctypes.c_float), ("tau_uv", ctypes.c_float), ("split_percent", ctypes.c_int32),
+                ("max_faces", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class RelightReq(ctypes.Structure):
@@ -116,6 +124,12 @@ def lib():
         "exm_material_tv": ([P, P, I, I, I, P, ctypes.c_uint32, F, P, P, P], I),
         "exm_env_regularizers": ([P, P, I, I, F, F, P, P, P], I),
         "exm_adam_step": ([P, P, P, P, P, I64, I, F, F, F, F, I, ctypes.POINTER(F), ctypes.POINTER(F), P], I),
+        "exm_topology_create": ([P, PP], I),
+        "exm_topology_destroy": ([P], None),
+        "exm_face_render_counts": ([P, I, P, P], I),
+        "exm_topology_round": ([P, P, I, P, I, P, I, P, P, P, P, ctypes.POINTER(TopologyParams), P], I),
+        "exm_topology_result": ([P, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), PP, PP, PP, PP, PP,
+                                 ctypes.POINTER(I * 3)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -367,3 +381,35 @@ def exm_adam_step(ctx, param, grad, m, v, lr, step, lo=None, hi=None, beta1=0.9,
     hi_a = F(*hi) if hi is not None else None
     return check(lib().exm_adam_step(ctx, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), rows, channels, float(lr),
                                      float(beta1), float(beta2), float(eps), int(step), lo_a, hi_a, _stream(stream)))
+
+
+# ------------------------------------------------------------------ Stage-I topology round
+
+def exm_topology_create(ctx):
+    out = ctypes.c_void_p()
+    check(lib().exm_topology_create(ctx, ctypes.byref(out)))
+    return out
+
+
+def exm_topology_destroy(topo):
+    lib().exm_topology_destroy(topo)
+
+
+def exm_face_render_counts(frame, nf, counts, stream=None):
+    return check(lib().exm_face_render_counts(frame, int(nf), _ptr(counts), _stream(stream)))
+
+
+def exm_topology_round(topo, V, F, UV, Fuv, ema, grad_V, render_counts, params: TopologyParams, stream=None):
+    return check(lib().exm_topology_round(topo, _ptr(V), V.shape[0], _ptr(F), F.shape[0], _ptr(UV), UV.shape[0],
+                                          _ptr(Fuv), _ptr(ema), _ptr(grad_V), _ptr(render_counts),
+                                          ctypes.byref(params), _stream(stream)))
+
+
+def exm_topology_result(topo):
+    """(nv, nf, nuv, pointers (V, F, UV, Fuv, ema), stats)."""
+    nv, nf, nuv = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ptrs = [ctypes.c_void_p() for _ in range(5)]
+    stats = (ctypes.c_int * 3)()
+    check(lib().exm_topology_result(topo, ctypes.byref(nv), ctypes.byref(nf), ctypes.byref(nuv),
+                                    *[ctypes.byref(p) for p in ptrs], ctypes.byref(stats)))
+    return nv.value, nf.value, nuv.value, [p.value for p in ptrs], list(stats)
