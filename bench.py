@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--budget-gb", type=int, default=24)
     ap.add_argument("--half-res-indirect", action="store_true",
                     help="indirect light at half resolution, upsampled (the paper's speed variant)")
+    ap.add_argument("--topology", action="store_true",
+                    help="time Stage-I topology rounds on the workload's mesh (Sec. 4.1-4.3)")
     ap.add_argument("--stage2", action="store_true",
                     help="time whole Stage-II iterations: render, objective, adjoint, Adam")
     return ap.parse_args()
@@ -463,6 +465,70 @@ def run_stage2(args, world, rank, local):
     r.close()
 
 
+def run_topology(args, world, rank, local):
+    """Stage-I topology rounds (EMA, scores, greedy splits and collapses, UV maintenance,
+    compaction) on the workload's mesh; render counts from a raster of its views."""
+    import numpy as np
+    import torch
+
+    from paper_2608_24109_b300 import build as libbuild
+    from paper_2608_24109_b300 import native as N
+    from paper_2608_24109_b300 import scenes
+    from paper_2608_24109_b300.render import Renderer
+    from paper_2608_24109_b300.topology import TopologyRound
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = scenes.config(args.workload, **({"views": args.views} if args.views else {}))
+    r = Renderer.from_scene(sc, device=local)
+    r.forward(torch.as_tensor(sc.maps).to(dev), torch.as_tensor(sc.env).to(dev))
+    nf = sc.F.shape[0]
+    counts = torch.zeros(nf, dtype=torch.int32, device=dev)
+    N.exm_face_render_counts(r.frame, nf, counts)
+    rng = np.random.default_rng(0)
+    V = torch.as_tensor(sc.V, device=dev)
+    F = torch.as_tensor(sc.F, device=dev)
+    UV = torch.as_tensor(sc.UV, device=dev)
+    Fuv = torch.as_tensor(sc.Fuv, device=dev)
+    G = torch.as_tensor(rng.uniform(0, 1, sc.V.shape[0]).astype(np.float32), device=dev)
+    grad = torch.as_tensor(rng.normal(size=sc.V.shape).astype(np.float32), device=dev)
+    tr = TopologyRound(r.ctx)
+    for _ in range(max(args.warmup, 1)):
+        out, stats = tr(V, F, UV, Fuv, G, grad, counts)
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    launches0 = N.exm_launch_count(r.ctx)
+    clocks.start()
+    times = []
+    stream = torch.cuda.current_stream()
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out, stats = tr(V, F, UV, Fuv, G, grad, counts)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ck = clocks.stop()
+    launches = (N.exm_launch_count(r.ctx) - launches0) // max(args.steps, 1)
+    ms = dist_max(statistics.mean(times), world)
+    line = {"metric": "Stage-I topology round, input faces/s", "value": world * nf / (ms * 1e-3), "unit": "faces/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{args.workload} mesh: {nf} faces, {sc.V.shape[0]} vertices, {sc.UV.shape[0]} UVs; "
+                                   "one round: EMA, curvature and split scores, splits of 5% of the faces, collapses "
+                                   "of small degenerate or never-rendered faces, UV maintenance, compaction",
+                       "render_counts": f"from a raster of the workload's {sc.views} views",
+                       "faces_out": int(out[1].shape[0]), **stats, "kernel_launches_per_round": int(launches),
+                       "note": "synchronous: the host reads sizes and selection state back between rounds of the "
+                               "greedy selection"},
+            "clocks": ck}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    tr.close()
+    r.close()
+
+
 def run_relight(args, world, rank, local):
     """Relight serving: Poisson arrivals of relight renders over resident assets."""
     import math
@@ -551,6 +617,8 @@ def main():
         run_reference(args, world, rank)
     elif args.stage2:
         run_stage2(args, world, rank, local)
+    elif args.topology:
+        run_topology(args, world, rank, local)
     else:
         run_native(args, world, rank, local)
     if world > 1:
