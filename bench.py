@@ -24,11 +24,16 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # algorithmic FP32 operation counts (per unit of work) used for the ALU roofline
-FLOPS_NODE = 50.0       # one 64-byte node: two slab tests (~25 flops each)
+FLOPS_NODE = 50.0       # one 4-wide node: four slab tests (6 FMA + 6 min/max each) and the clamps
 FLOPS_TRI = 30.0        # one watertight ray/triangle test
 FLOPS_BRDF = 80.0       # one Lambert + GGX evaluation with its cosine and estimator weight
 FLOPS_BRDF_ADJ = 240.0  # evaluation + adjoint in the backward pass
 FP32_LANES_PER_SM = 128
+# DRAM bytes (read + write) per traced shadow ray of the any-hit tracer on the geometry workload,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the first chunk launch of
+# the 2-view case: 281.4 MB for 8.6 M rays).  The ray record (32 B) is read once; nodes and
+# triangles stay in L2.
+TRACE_DRAM_BYTES_PER_RAY = {"geometry": 32.7}
 
 WORKLOADS = {
     "tiny": "icosphere 1280 tris, maps 256^2 FP32, env 64x32, 4 views 256^2, 64 env samples/px, fwd+bwd",
@@ -329,6 +334,14 @@ def run_native(args, world, rank, local):
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_flops, dom_work = kinds[dom]
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+    # DRAM traffic of one any-hit launch (the ray queue chunks of the forward pass)
+    traffic = None
+    if dom.startswith("trace_kernel") and args.workload in TRACE_DRAM_BYTES_PER_RAY and sc.n_bounce == 0:
+        nd_words = (sc.n_direct + 31) // 32
+        per_pixel = nd_words * 32
+        chunk_pixels = max(32, ((1 << 24) // per_pixel) & ~31)
+        launches_any = -(-(sc.views * sc.width * sc.height) // chunk_pixels)
+        traffic = TRACE_DRAM_BYTES_PER_RAY[args.workload] * work_fwd[3] / launches_any
     mf, mb = statistics.mean(t_fwd), statistics.mean(t_bwd)
     line = {
         "metric": "fwd+bwd shaded samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
@@ -343,7 +356,8 @@ def run_native(args, world, rank, local):
                    "kernel_ms_per_step": {"trace_any": kms[0], "trace_closest": kms[1], "shade_forward": kms[2],
                                           "shade_backward": kms[3]}},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "traffic_unit": "bytes per launch (ncu DRAM read + write per traced ray x rays per launch)",
                      "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
                                     f"(clock from {src} peaks)",
                      "work_per_step": dom_work},

@@ -29,18 +29,6 @@ exm_status exm_cuda_check(cudaError_t e, const char* what) {
     } while (0)
 
 namespace {
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
 }  // namespace
 
 __global__ void exm_l1_kernel(const float* __restrict__ pred, const float* __restrict__ target, long long n,

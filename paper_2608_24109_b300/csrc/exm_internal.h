@@ -117,6 +117,20 @@ struct exm_frame {
     std::vector<Timer> timers;    // EXM_FLAG_TIME_KERNELS
 };
 
+// Makes `dev` current for a scope and restores the caller's device on exit.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // Grows a device buffer to hold `need` elements (contents are not kept); false on OOM.
 template <typename TT>
 inline bool ensure(TT** ptr, size_t* cap, size_t need) {

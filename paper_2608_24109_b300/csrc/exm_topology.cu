@@ -665,18 +665,18 @@ exm_status exm_topology_create(exm_ctx* c, exm_topology** out) {
 
 void exm_topology_destroy(exm_topology* t) {
     if (!t) return;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != t->ctx->device) cudaSetDevice(t->ctx->device);
-    for (auto& b : t->bufs) cudaFree(b.first);
-    cudaFree(t->tmp);
-    cudaFree(t->V); cudaFree(t->F); cudaFree(t->UV); cudaFree(t->Fuv); cudaFree(t->G);
-    if (prev >= 0 && prev != t->ctx->device) cudaSetDevice(prev);
+    {
+        DeviceGuard guard(t->ctx->device);
+        for (auto& b : t->bufs) cudaFree(b.first);
+        cudaFree(t->tmp);
+        cudaFree(t->V); cudaFree(t->F); cudaFree(t->UV); cudaFree(t->Fuv); cudaFree(t->G);
+    }
     delete t;
 }
 
 exm_status exm_face_render_counts(exm_frame* f, int nf, uint32_t* counts, void* stream) {
     if (!f || !counts || nf < 1) return exm_fail(EXM_ERR_ARG, "exm_face_render_counts: bad argument");
+    DeviceGuard guard(f->ctx->device);
     const size_t P = (size_t)f->views * f->W * f->H;
     render_count_kernel<<<grid(f->ctx, P), 256, 0, (cudaStream_t)stream>>>(P, (const unsigned long long*)f->visbuf,
                                                                           nf, counts);
@@ -692,9 +692,7 @@ exm_status exm_topology_round(exm_topology* t, const float* V, int nv, const int
     if (p->split_percent < 0 || p->split_percent > 100 || p->max_faces < 1 || (long long)nf * 3 >= INT_MAX / 2)
         return exm_fail(EXM_ERR_ARG, "exm_topology_round: parameters");
     exm_ctx* c = t->ctx;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != c->device) cudaSetDevice(c->device);
+    DeviceGuard guard(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     exm_status st = EXM_OK;
     uint32_t* cnt = scratch<uint32_t>(t, 0, 8);
@@ -913,7 +911,6 @@ exm_status exm_topology_round(exm_topology* t, const float* V, int nv, const int
     t->stats[0] = applied;
     t->stats[1] = (int)merges;
     t->stats[2] = nf1 - nf2;
-    if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
     return EXM_OK;
 }
 

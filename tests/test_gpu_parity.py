@@ -363,3 +363,34 @@ def test_precision_form_sampled(mdt):
     V, _, Eo = shade.scene_tensors(sc)
     I = shade.render_image(sc, tab, dec, V, Mq.to(torch.float64), Eo).numpy()
     check_radiance(out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]], I, f"precision form {mdt}")
+
+
+def test_empty_frame_everywhere():
+    """A camera that sees no surface: zero image, zero gradients, zero render counts and a zero
+    material TV, with no error latched -- also through the half-resolution indirect pass."""
+    from paper_2608_24109_b300 import native as N
+    from paper_2608_24109_b300.render import Renderer
+    sc = scenes.config("indirect", n=12, map_res=64, env_w=32, env_h=16, views=2, res=40, n_direct=16,
+                       n_bounce=4, n_light=2)
+    # the mesh is in front of the camera (no guard-band error) but outside its 10-degree view
+    sc.cams = np.stack([scenes.look_at_camera((0.0, 0.0, 5.0), 40, 40, fovy_deg=10.0, target=(2.5, 0.0, 0.0))] * 2)
+    for half in (False, True):
+        sc.half_res_indirect = half
+        r = Renderer.from_scene(sc)
+        M, E = _dev(sc.maps), _dev(sc.env)
+        out = r.forward(M, E)
+        r.sync()
+        covered, samples = r.stats()
+        assert covered == 0 and samples == 0 and float(out.abs().sum()) == 0.0
+        gm, gE = torch.zeros_like(M), torch.zeros_like(E)
+        gV = torch.zeros((sc.V.shape[0], 3), device="cuda")
+        r.backward(M, torch.ones_like(out), gm, gE, gV)
+        r.sync()
+        assert float(gm.abs().sum() + gE.abs().sum() + gV.abs().sum()) == 0.0
+        loss = torch.full((1,), 7.0, device="cuda")
+        N.exm_material_tv(r.ctx, M, r.frame, r.params.flags, 0.1, loss, gm)
+        counts = torch.zeros(sc.F.shape[0], dtype=torch.int32, device="cuda")
+        N.exm_face_render_counts(r.frame, sc.F.shape[0], counts)
+        r.sync()
+        assert loss.item() == 0.0 and float(gm.abs().sum()) == 0.0 and int(counts.sum()) == 0
+        r.close()
