@@ -19,6 +19,7 @@ namespace exm {
 enum : uint32_t { ERRBIT_GUARD = 1u, ERRBIT_TRAVERSAL = 2u, ERRBIT_INDEX = 4u };
 
 constexpr float kPi = 3.14159265358979323846f;
+constexpr float kInvPi = 0.318309886183790671538f;
 constexpr float kFDielectric = 0.04f;   // F_dielectric of Eq. 16
 constexpr float kSpecEps = 1e-6f;       // epsilon of Eq. 15
 constexpr float kRMin = 0.08f;          // roughness clamp before alpha = r^2
@@ -256,7 +257,8 @@ __host__ __device__ __forceinline__ void strata2(uint32_t n, uint32_t* nx, uint3
 // Texel chosen by the row fraction U1 and column fraction U2: the row is the smallest i
 // whose inclusive row prefix exceeds floor(U1 Q / 2^32); the column the smallest j of row i
 // whose in-row prefix exceeds floor(U2 rowsum_i / 2^32) (guide tables bound both searches).
-__device__ __forceinline__ uint32_t pick_texel(const EnvView& e, uint32_t U1, uint32_t U2) {
+__device__ __forceinline__ void pick_texel(const EnvView& e, uint32_t U1, uint32_t U2, uint32_t* row_out,
+                                           uint32_t* col_out) {
     const uint64_t tr = scaled_target(U1, e.Q);
     const uint32_t g = U1 >> (32 - e.rbits);
     uint32_t lo = __ldg(e.rguide + g), hi = __ldg(e.rguide + g + 1);
@@ -276,7 +278,8 @@ __device__ __forceinline__ uint32_t pick_texel(const EnvView& e, uint32_t U1, ui
         const uint32_t mid = lo + ((hi - lo) >> 1);
         if (__ldg(rc + mid) > tc) hi = mid; else lo = mid + 1;
     }
-    return row * (uint32_t)e.W + lo;
+    *row_out = row;
+    *col_out = lo;
 }
 
 struct LightSample {
@@ -290,15 +293,23 @@ struct LightSample {
 // stratum k % nx.
 __device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, uint32_t k, uint32_t nx, uint32_t ny) {
     LightSample s;
-    const uint32_t kx = k % nx, ky = k / nx;
-    uint32_t t = pick_texel(e, stratified32(ky, ny, h.x), stratified32(kx, nx, h.w));
+    uint32_t kx, ky;
+    if ((nx & (nx - 1)) == 0) {  // the strata of power-of-two sample counts: no integer division
+        kx = k & (nx - 1);
+        ky = k >> (31 - __clz(nx));
+    } else {
+        kx = k % nx;
+        ky = k / nx;
+    }
+    uint32_t i, j;
+    pick_texel(e, stratified32(ky, ny, h.x), stratified32(kx, nx, h.w), &i, &j);
+    const uint32_t t = i * (uint32_t)e.W + j;
     float xu = unit24(h.y), xv = unit24(h.z);
-    int i = (int)(t / (uint32_t)e.W), j = (int)(t - (uint32_t)i * (uint32_t)e.W);
     float st;
-    s.dir = light_dir(i, j, e.W, e.H, xu, xv, &st);
+    s.dir = light_dir((int)i, (int)j, e.W, e.H, xu, xv, &st);
     float4 tx = __ldg(e.texel + t);
     s.E = make_float3(tx.x, tx.y, tx.z);
-    s.inv_pdf = st / tx.w;
+    s.inv_pdf = __fdividef(st, tx.w);  // an estimator weight, not a decision
     s.texel = t;
     return s;
 }

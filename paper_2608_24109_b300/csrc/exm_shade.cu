@@ -29,7 +29,9 @@ namespace exm {
 constexpr int kShadeWarps = 4;        // warps per block of the shade kernel
 constexpr int kPrec = 5;              // float4 per pixel record (pixel_prep_kernel)
 constexpr int kListMax = 1024;        // sample slots enumerated per round (32 bit words)
-constexpr uint32_t kRayCapDefault = 1u << 24; // queued rays per chunk (2 float4 each, 512 MiB)
+// Queued rays per chunk at most (2 float4 each: 4 GiB).  Few, large chunks keep the persistent
+// tracer's launch tails small: the geometry workload's forward takes 8 chunks (64 at 2^24 rays).
+constexpr uint32_t kRayCapDefault = 1u << 27;
 
 struct ShadeArgs {
     // mesh
@@ -142,13 +144,17 @@ __device__ __forceinline__ uint32_t warp_append(uint32_t* counter, bool want) {
     return base + __popc(mask & ((1u << lane) - 1u));
 }
 
+// sqrt of a positive shading quantity (the BRDF weights are estimator values, not decisions:
+// approximate reciprocals and square roots are within a few ulp)
+__device__ __forceinline__ float fsqrt_pos(float q) { return q * rsqrtf(q); }
+
 // (f_d + f_s) * max(n.wi, 0), Eqs. 13-16 (FP32).  The GGX denominator uses
 // |n x h|^2 + alpha^2 (n.h)^2, equal to (n.h)^2 (alpha^2 - 1) + 1 for unit vectors.
 __device__ __forceinline__ float3 brdf_cos(float3 ns, float3 wi, float3 wo, float3 a, float r, float m) {
     float ci = dot(ns, wi), co = dot(ns, wo);
     if (ci <= 0.0f) return f3(0.f, 0.f, 0.f);
     float om = 1.0f - m;
-    float3 res = (om / kPi) * a;
+    float3 res = (om * kInvPi) * a;
     if (co > 0.0f) {
         float rc = fminf(fmaxf(r, kRMin), 1.0f);
         float al = rc * rc, a2 = al * al;
@@ -157,13 +163,13 @@ __device__ __forceinline__ float3 brdf_cos(float3 ns, float3 wi, float3 wo, floa
         float nh = dot(ns, h), vh = dot(wi, h);
         float3 cx = cross(ns, h);
         float k = dot(cx, cx) + a2 * nh * nh;
-        float D = a2 / (kPi * k * k);
-        float sqi = sqrtf(a2 + (1.0f - a2) * ci * ci), sqo = sqrtf(a2 + (1.0f - a2) * co * co);
-        float G = (2.0f * ci / (ci + sqi)) * (2.0f * co / (co + sqo));
+        float D = __fdividef(a2, kPi * k * k);
+        float sqi = fsqrt_pos(a2 + (1.0f - a2) * ci * ci), sqo = fsqrt_pos(a2 + (1.0f - a2) * co * co);
+        float G = __fdividef(2.0f * ci, ci + sqi) * __fdividef(2.0f * co, co + sqo);
         float om5 = 1.0f - vh, w2 = om5 * om5, w5 = w2 * w2 * om5;
         float3 F0 = f3(om * kFDielectric + m * a.x, om * kFDielectric + m * a.y, om * kFDielectric + m * a.z);
         float3 Fr = f3(F0.x + (1.f - F0.x) * w5, F0.y + (1.f - F0.y) * w5, F0.z + (1.f - F0.z) * w5);
-        float P = D * G / (4.0f * ci * co + kSpecEps);
+        float P = __fdividef(D * G, 4.0f * ci * co + kSpecEps);
         res += P * Fr;
     }
     return ci * res;
@@ -175,12 +181,12 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 ns, float3 wi, float3 wo
     float ci = dot(ns, wi), co = dot(ns, wo);
     if (ci <= 0.0f) return;
     float om = 1.0f - m;
-    float3 fd = (om / kPi) * a;
+    float3 fd = (om * kInvPi) * a;
     float3 res = fd;
     float gci = 0.0f, gco = 0.0f;
     float3 gres = ci * G3;
-    ga += (om / kPi) * gres;
-    gm += -dot(gres, a) / kPi;
+    ga += (om * kInvPi) * gres;
+    gm += -dot(gres, a) * kInvPi;
     if (co > 0.0f) {
         float rc = fminf(fmaxf(r, kRMin), 1.0f);
         float al = rc * rc, a2 = al * al;
@@ -190,19 +196,22 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 ns, float3 wi, float3 wo
         float nh = dot(ns, h), vh = dot(wi, h);
         float3 cx = cross(ns, h);
         float k = dot(cx, cx) + a2 * nh * nh;
-        float D = a2 / (kPi * k * k);
-        float sqi = sqrtf(a2 + (1.0f - a2) * ci * ci), sqo = sqrtf(a2 + (1.0f - a2) * co * co);
-        float G1i = 2.0f * ci / (ci + sqi), G1o = 2.0f * co / (co + sqo);
+        const float ipk2 = __fdividef(1.0f, kPi * k * k);
+        float D = a2 * ipk2;
+        float sqi = fsqrt_pos(a2 + (1.0f - a2) * ci * ci), sqo = fsqrt_pos(a2 + (1.0f - a2) * co * co);
+        const float ici2 = __fdividef(1.0f, ci + sqi), ico2 = __fdividef(1.0f, co + sqo);
+        float G1i = 2.0f * ci * ici2, G1o = 2.0f * co * ico2;
         float G = G1i * G1o;
         float om5 = 1.0f - vh, w2 = om5 * om5, w4 = w2 * w2, w5 = w4 * om5;
         float3 F0 = f3(om * kFDielectric + m * a.x, om * kFDielectric + m * a.y, om * kFDielectric + m * a.z);
         float3 Fr = f3(F0.x + (1.f - F0.x) * w5, F0.y + (1.f - F0.y) * w5, F0.z + (1.f - F0.z) * w5);
         float den = 4.0f * ci * co + kSpecEps;
-        float P = D * G / den;
+        const float iden = __fdividef(1.0f, den);
+        float P = D * G * iden;
         res += P * Fr;
         float S = dot(gres, Fr);
         float3 gF = P * gres;
-        float gD = S * G / den, gG = S * D / den, gden = -S * P / den;
+        float gD = S * G * iden, gG = S * D * iden, gden = -S * P * iden;
         gci += gden * 4.0f * co;
         gco += gden * 4.0f * ci;
         float3 gF0 = f3(gF.x * (1.f - w5), gF.y * (1.f - w5), gF.z * (1.f - w5));
@@ -210,14 +219,14 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 ns, float3 wi, float3 wo
         float gvh = -5.0f * w4 * gw5;
         gm += gF0.x * (a.x - kFDielectric) + gF0.y * (a.y - kFDielectric) + gF0.z * (a.z - kFDielectric);
         ga += m * gF0;
-        float gk = -2.0f * gD * D / k;
-        float ga2 = gD / (kPi * k * k) + gk * nh * nh;
+        float gk = -2.0f * gD * D * __fdividef(1.0f, k);
+        float ga2 = gD * ipk2 + gk * nh * nh;
         float gnh = gk * 2.0f * nh * (a2 - 1.0f);
-        float ci2 = ci + sqi, co2 = co + sqo;
-        gci += gG * G1o * (2.0f * a2 / (sqi * ci2 * ci2));
-        gco += gG * G1i * (2.0f * a2 / (sqo * co2 * co2));
-        ga2 += gG * G1o * (-ci * (1.0f - ci * ci) / (sqi * ci2 * ci2));
-        ga2 += gG * G1i * (-co * (1.0f - co * co) / (sqo * co2 * co2));
+        const float di = __fdividef(ici2 * ici2, sqi), dq = __fdividef(ico2 * ico2, sqo);  // 1/(sq (c+sq)^2)
+        gci += gG * G1o * (2.0f * a2 * di);
+        gco += gG * G1i * (2.0f * a2 * dq);
+        ga2 += gG * G1o * (-ci * (1.0f - ci * ci) * di);
+        ga2 += gG * G1i * (-co * (1.0f - co * co) * dq);
         if (r >= kRMin && r <= 1.0f) gr += ga2 * 4.0f * rc * rc * rc;
         gns += gnh * h;
         float3 gh = gnh * ns + gvh * wi;
@@ -721,7 +730,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
         if (!BWD && lane == 0) my_samples += (unsigned long long)A.Nd;
         // ---- one-bounce indirect (Eqs. 18-19): lanes take the pixel's live (j, s) pairs
         if (IND && A.Nb > 0 && A.lambda != 0.0f) {
-            const float3 fdx = ((1.0f - su.m) / kPi) * su.a;
+            const float3 fdx = ((1.0f - su.m) * kInvPi) * su.a;
             const float scale = A.lambda / (float)A.Nb;
             const float invNs = 1.0f / (float)A.Ns;
             if (!BWD) {
@@ -773,7 +782,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                     const float3 niy = by[0] * ld3(A.nrm + 3 * q0) + by[1] * ld3(A.nrm + 3 * q1) + by[2] * ld3(A.nrm + 3 * q2);
                     const float3 tiy = by[0] * ld3(A.tan + 3 * v0) + by[1] * ld3(A.tan + 3 * v1) + by[2] * ld3(A.tan + 3 * v2);
                     const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
-                    const float3 fdy = ((1.0f - sy.m) / kPi) * sy.a;
+                    const float3 fdy = ((1.0f - sy.m) * kInvPi) * sy.a;
                     const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
                     const LightSample ls = light_sample(env, h2, (uint32_t)s, A.nxs, A.nys);
                     const float3 wl = normalize(tof(ls.dir));
@@ -792,17 +801,17 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                         atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
                         // f_d(x) and n_s(x) through max(n_s(x).w_j, 0)
                         const float3 gfdx = wb * (g * (fdy * ET));
-                        ga += ((1.0f - su.m) / kPi) * gfdx;
-                        gm += -dot(gfdx, su.a) / kPi;
+                        ga += ((1.0f - su.m) * kInvPi) * gfdx;
+                        gm += -dot(gfdx, su.a) * kInvPi;
                         gns += (scale * pb_inv * dot(g, fdx * (fdy * ET))) * wj;
                         // material at y (its geometry is a constant of the derivative)
                         const float3 gLsec = wb * (g * fdx);
                         const float3 gfdy = gLsec * ET;
                         const float3 gnsy = (ls.inv_pdf * invNs * dot(gLsec, fdy * ls.E)) * wl;
                         float gy[8];
-                        const float3 gay = ((1.0f - sy.m) / kPi) * gfdy;
+                        const float3 gay = ((1.0f - sy.m) * kInvPi) * gfdy;
                         gy[0] = gay.x; gy[1] = gay.y; gy[2] = gay.z; gy[3] = 0.0f;
-                        gy[4] = A.metallic ? -dot(gfdy, sy.a) / kPi : 0.0f;
+                        gy[4] = A.metallic ? -dot(gfdy, sy.a) * kInvPi : 0.0f;
                         const float3 gnt = f3(dot(sy.T, gnsy), dot(sy.B, gnsy), dot(sy.n, gnsy));
                         const float3 gq = (1.0f / sy.ql) * (gnt - dot(gnt, sy.nt) * sy.nt);
                         gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
@@ -1073,13 +1082,17 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     const int wd = (p->n_direct + 31) / 32;
     const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
     const int ws = indirect ? (p->n_bounce * p->n_light + 31) / 32 : 0;
-    const uint32_t ray_cap = f->ray_cap ? f->ray_cap : kRayCapDefault;
+    const uint32_t cap_max = f->ray_cap ? f->ray_cap : kRayCapDefault;
+    const uint32_t per_pixel = (uint32_t)max(wd * 32 + ws * 32, indirect ? p->n_bounce : 1);
+    // a chunk of Pc pixels queues at most Pc * per_pixel rays; the queue holds one chunk and no
+    // more than the frame can use
+    const size_t P32 = (P + 31) & ~(size_t)31;
+    const uint32_t Pc = (uint32_t)max((size_t)32, min(P32, (size_t)((cap_max / per_pixel) & ~31u)));
+    const uint32_t ray_cap = (uint32_t)min((size_t)cap_max, (size_t)Pc * per_pixel);
     if (!ensure(&f->prec, &f->prec_cap, P * (size_t)kPrec) ||
         !ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)ray_cap * 2) ||
         (indirect && !ensure(&f->hits, &f->hits_cap, P * (size_t)p->n_bounce)))
         return exm_fail(EXM_ERR_OOM, "wavefront buffers");
-    const uint32_t per_pixel = (uint32_t)max(wd * 32 + ws * 32, indirect ? p->n_bounce : 1);
-    const uint32_t Pc = max(32u, (ray_cap / per_pixel) & ~31u);
     const size_t nchunks = (P + Pc - 1) / Pc;
     if (!ensure(&f->ctr, &f->ctr_cap, nchunks * 4)) return exm_fail(EXM_ERR_OOM, "chunk counters");
     ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
