@@ -30,10 +30,11 @@ FLOPS_BRDF = 80.0       # one Lambert + GGX evaluation with its cosine and estim
 FLOPS_BRDF_ADJ = 240.0  # evaluation + adjoint in the backward pass
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per traced shadow ray of the any-hit tracer on the geometry workload,
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the first chunk launch of
-# the 2-view case: 281.4 MB for 8.6 M rays).  The ray record (32 B) is read once; nodes and
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the single chunk launch of
+# the 2-view case: 1.288 GB for 39 M rays).  The ray record (32 B) is read once; nodes and
 # triangles stay in L2.
-TRACE_DRAM_BYTES_PER_RAY = {"geometry": 32.7}
+TRACE_DRAM_BYTES_PER_RAY = {"geometry": 33.0}
+RAY_QUEUE_MAX = 1 << 27  # rays per chunk at most (the library's default queue)
 
 WORKLOADS = {
     "tiny": "icosphere 1280 tris, maps 256^2 FP32, env 64x32, 4 views 256^2, 64 env samples/px, fwd+bwd",
@@ -337,10 +338,10 @@ def run_native(args, world, rank, local):
     # DRAM traffic of one any-hit launch (the ray queue chunks of the forward pass)
     traffic = None
     if dom.startswith("trace_kernel") and args.workload in TRACE_DRAM_BYTES_PER_RAY and sc.n_bounce == 0:
-        nd_words = (sc.n_direct + 31) // 32
-        per_pixel = nd_words * 32
-        chunk_pixels = max(32, ((1 << 24) // per_pixel) & ~31)
-        launches_any = -(-(sc.views * sc.width * sc.height) // chunk_pixels)
+        per_pixel = ((sc.n_direct + 31) // 32) * 32
+        pixels = sc.views * sc.width * sc.height
+        chunk_pixels = max(32, min((pixels + 31) & ~31, (RAY_QUEUE_MAX // per_pixel) & ~31))
+        launches_any = -(-pixels // chunk_pixels)
         traffic = TRACE_DRAM_BYTES_PER_RAY[args.workload] * work_fwd[3] / launches_any
     mf, mb = statistics.mean(t_fwd), statistics.mean(t_bwd)
     line = {

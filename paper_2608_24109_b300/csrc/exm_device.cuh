@@ -282,6 +282,45 @@ __device__ __forceinline__ void pick_texel(const EnvView& e, uint32_t U1, uint32
     *col_out = lo;
 }
 
+// Two texel picks in lockstep: the same arithmetic as pick_texel for each, with the loads of
+// both searches issued together so that their latencies overlap.
+__device__ __forceinline__ void pick_texel2(const EnvView& e, uint32_t U1a, uint32_t U2a, uint32_t U1b,
+                                            uint32_t U2b, uint32_t* ra, uint32_t* ca, uint32_t* rb,
+                                            uint32_t* cb) {
+    const uint64_t tra = scaled_target(U1a, e.Q), trb = scaled_target(U1b, e.Q);
+    const uint32_t ga = U1a >> (32 - e.rbits), gb = U1b >> (32 - e.rbits);
+    uint32_t loa = __ldg(e.rguide + ga), hia = __ldg(e.rguide + ga + 1);
+    uint32_t lob = __ldg(e.rguide + gb), hib = __ldg(e.rguide + gb + 1);
+    while (loa < hia || lob < hib) {
+        const bool aa = loa < hia, ab = lob < hib;
+        const uint32_t ma = loa + ((hia - loa) >> 1), mb = lob + ((hib - lob) >> 1);
+        const uint64_t va = aa ? __ldg(e.cdf + (size_t)ma * e.W + e.W - 1) : 0ull;
+        const uint64_t vb = ab ? __ldg(e.cdf + (size_t)mb * e.W + e.W - 1) : 0ull;
+        if (aa) { if (va > tra) hia = ma; else loa = ma + 1; }
+        if (ab) { if (vb > trb) hib = mb; else lob = mb + 1; }
+    }
+    const uint32_t rowa = loa, rowb = lob;
+    const uint64_t* rca = e.cdf + (size_t)rowa * e.W;
+    const uint64_t* rcb = e.cdf + (size_t)rowb * e.W;
+    const uint64_t prea = rowa ? __ldg(rca - 1) : 0ull, preb = rowb ? __ldg(rcb - 1) : 0ull;
+    const uint64_t enda = __ldg(rca + e.W - 1), endb = __ldg(rcb + e.W - 1);
+    const uint64_t tca = prea + scaled_target(U2a, enda - prea), tcb = preb + scaled_target(U2b, endb - preb);
+    const uint32_t stride = (1u << e.cbits) + 1;
+    const uint32_t g2a = U2a >> (32 - e.cbits), g2b = U2b >> (32 - e.cbits);
+    loa = __ldg(e.cguide + (size_t)rowa * stride + g2a);
+    hia = __ldg(e.cguide + (size_t)rowa * stride + g2a + 1);
+    lob = __ldg(e.cguide + (size_t)rowb * stride + g2b);
+    hib = __ldg(e.cguide + (size_t)rowb * stride + g2b + 1);
+    while (loa < hia || lob < hib) {
+        const bool aa = loa < hia, ab = lob < hib;
+        const uint32_t ma = loa + ((hia - loa) >> 1), mb = lob + ((hib - lob) >> 1);
+        const uint64_t va = aa ? __ldg(rca + ma) : 0ull, vb = ab ? __ldg(rcb + mb) : 0ull;
+        if (aa) { if (va > tca) hia = ma; else loa = ma + 1; }
+        if (ab) { if (vb > tcb) hib = mb; else lob = mb + 1; }
+    }
+    *ra = rowa; *ca = loa; *rb = rowb; *cb = lob;
+}
+
 struct LightSample {
     S3 dir;        // unnormalised spec direction
     float inv_pdf; // 1 / p_omega
@@ -291,27 +330,45 @@ struct LightSample {
 
 // Light sample k of n = nx * ny (strata2): 2D-stratified, row stratum k / nx and column
 // stratum k % nx.
+__device__ __forceinline__ void strata_of(uint32_t k, uint32_t nx, uint32_t* kx, uint32_t* ky) {
+    if ((nx & (nx - 1)) == 0) {  // the strata of power-of-two sample counts: no integer division
+        *kx = k & (nx - 1);
+        *ky = k >> (31 - __clz(nx));
+    } else {
+        *kx = k % nx;
+        *ky = k / nx;
+    }
+}
+
+__device__ __forceinline__ void finish_sample(const EnvView& e, uint4 h, uint32_t i, uint32_t j, LightSample* s) {
+    const uint32_t t = i * (uint32_t)e.W + j;
+    float st;
+    s->dir = light_dir((int)i, (int)j, e.W, e.H, unit24(h.y), unit24(h.z), &st);
+    const float4 tx = __ldg(e.texel + t);
+    s->E = make_float3(tx.x, tx.y, tx.z);
+    s->inv_pdf = __fdividef(st, tx.w);  // an estimator weight, not a decision
+    s->texel = t;
+}
+
 __device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, uint32_t k, uint32_t nx, uint32_t ny) {
     LightSample s;
-    uint32_t kx, ky;
-    if ((nx & (nx - 1)) == 0) {  // the strata of power-of-two sample counts: no integer division
-        kx = k & (nx - 1);
-        ky = k >> (31 - __clz(nx));
-    } else {
-        kx = k % nx;
-        ky = k / nx;
-    }
-    uint32_t i, j;
+    uint32_t kx, ky, i, j;
+    strata_of(k, nx, &kx, &ky);
     pick_texel(e, stratified32(ky, ny, h.x), stratified32(kx, nx, h.w), &i, &j);
-    const uint32_t t = i * (uint32_t)e.W + j;
-    float xu = unit24(h.y), xv = unit24(h.z);
-    float st;
-    s.dir = light_dir((int)i, (int)j, e.W, e.H, xu, xv, &st);
-    float4 tx = __ldg(e.texel + t);
-    s.E = make_float3(tx.x, tx.y, tx.z);
-    s.inv_pdf = __fdividef(st, tx.w);  // an estimator weight, not a decision
-    s.texel = t;
+    finish_sample(e, h, i, j, &s);
     return s;
+}
+
+// Light samples ka and kb together (pick_texel2): each equal to light_sample's.
+__device__ __forceinline__ void light_sample2(const EnvView& e, uint4 ha, uint32_t ka, uint4 hb, uint32_t kb,
+                                              uint32_t nx, uint32_t ny, LightSample* sa, LightSample* sb) {
+    uint32_t kxa, kya, kxb, kyb, ia, ja, ib, jb;
+    strata_of(ka, nx, &kxa, &kya);
+    strata_of(kb, nx, &kxb, &kyb);
+    pick_texel2(e, stratified32(kya, ny, ha.x), stratified32(kxa, nx, ha.w), stratified32(kyb, ny, hb.x),
+                stratified32(kxb, nx, hb.w), &ia, &ja, &ib, &jb);
+    finish_sample(e, ha, ia, ja, sa);
+    finish_sample(e, hb, ib, jb, sb);
 }
 
 // ----------------------------------------------------------------------- BVH

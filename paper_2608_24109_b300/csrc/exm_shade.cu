@@ -300,19 +300,29 @@ __global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
         ngs = s3(r3.w, r4.x, r4.y);
     }
     const int k0 = (int)kc * kGenK, k1 = min(A.Nd, k0 + kGenK);
-    for (int k = k0; k < k1; ++k) {
-        bool want = false;
-        S3 dir = s3(0.f, 0.f, 0.f);
+    // samples k and k + 1 together (their texel searches overlap), appended in order
+    for (int k = k0; k < k1; k += 2) {
+        const bool two = k + 1 < k1;  // warp-uniform
+        bool want[2] = {false, false};
+        S3 dir[2] = {s3(0.f, 0.f, 0.f), s3(0.f, 0.f, 0.f)};
         if (valid) {
-            const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
-            const LightSample ls = light_sample(env, h, (uint32_t)k, A.nxd, A.nyd);
-            dir = ls.dir;
-            want = sdot(ngs, dir) > 0.0f;
+            const int kb = two ? k + 1 : k;
+            const uint4 ha = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
+            const uint4 hb = philox(make_uint4(rem, (uint32_t)c, (uint32_t)kb, 0u), A.key);
+            LightSample sa, sb;
+            light_sample2(env, ha, (uint32_t)k, hb, (uint32_t)kb, A.nxd, A.nyd, &sa, &sb);
+            dir[0] = sa.dir;
+            dir[1] = sb.dir;
+            want[0] = sdot(ngs, dir[0]) > 0.0f;
+            want[1] = two && sdot(ngs, dir[1]) > 0.0f;
         }
-        const uint32_t idx = warp_append(A.ctr + 2, want);
-        if (want) {
-            if (idx < A.ray_cap) push_ray(A.rays, idx, org, dir, (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)k);
-            else atomicOr(A.status, ERRBIT_TRAVERSAL);
+        for (int u = 0; u < (two ? 2 : 1); ++u) {
+            const uint32_t idx = warp_append(A.ctr + 2, want[u]);
+            if (want[u]) {
+                if (idx < A.ray_cap)
+                    push_ray(A.rays, idx, org, dir[u], (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)(k + u));
+                else atomicOr(A.status, ERRBIT_TRAVERSAL);
+            }
         }
     }
 }
