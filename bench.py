@@ -23,9 +23,10 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic FP32 operation counts (per unit of work) used for the ALU roofline
-FLOPS_NODE = 50.0       # one 4-wide node: four slab tests (6 FMA + 6 min/max each) and the clamps
-FLOPS_TRI = 30.0        # one watertight ray/triangle test
+# algorithmic FP32 operation counts (per unit of work) used for the ALU roofline; an FMA counts
+# 2, as in the peak, and a min, max or comparison 1
+FLOPS_NODE = 72.0       # one 4-wide node: per child 6 FMA, a 3-way max and a max with 0, a 3-way min, one compare
+FLOPS_TRI = 50.0        # one watertight test: 40 adds and multiplies (no FMA: decision arithmetic), ~10 compares
 FLOPS_BRDF = 80.0       # one Lambert + GGX evaluation with its cosine and estimator weight
 FLOPS_BRDF_ADJ = 240.0  # evaluation + adjoint in the backward pass
 FP32_LANES_PER_SM = 128

@@ -72,6 +72,10 @@ struct exm_env {
     uint64_t* total = nullptr;    // [1] Q on the device
 };
 
+// float4 per pixel record: [0..4] the camera-ray geometry (pixel_prep_kernel), [5..6] the
+// material and shading normal (pixel_surface_kernel)
+constexpr int kPrec = 7;
+
 struct exm_frame {
     exm_ctx* ctx = nullptr;
     int views = 0, W = 0, H = 0;
@@ -92,8 +96,10 @@ struct exm_frame {
     size_t gframe_capacity = 0;
     size_t gtan_capacity = 0;
     // wavefront state of the last forward
-    float4* prec = nullptr;       // [P * 5] per-pixel shading records
+    float4* prec = nullptr;       // [P * kPrec] per-pixel shading records
     size_t prec_cap = 0;
+    float* pacc = nullptr;        // [P * 12] per-pixel sums of the backward's sample adjoints
+    size_t pacc_cap = 0;
     uint32_t* bits = nullptr;     // visibility bits: [P * wd] direct, then [P * ws] secondary
     size_t bits_cap = 0;
     int32_t* hits = nullptr;      // [P * Nb] secondary closest front-facing hit, -1 if none

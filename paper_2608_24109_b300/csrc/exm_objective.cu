@@ -216,7 +216,7 @@ template <typename T>
 __global__ void tv_gbuf_kernel(TvArgs a) {
     const uint32_t n = *a.count;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float4 r1 = a.prec[5 * (size_t)i + 1], r2 = a.prec[5 * (size_t)i + 2];
+        const float4 r1 = a.prec[kPrec * (size_t)i + 1], r2 = a.prec[kPrec * (size_t)i + 2];
         const Footprint fp = footprint_i(a.map, __float_as_int(r2.y), __float_as_int(r2.z), r1.w, r2.x);
         float att[8];
         fetch8<T>(a.map, fp, att, nullptr, nullptr);
@@ -276,7 +276,7 @@ __global__ void tv_grad_kernel(TvArgs a) {
             g[ch] = a.lambda * s * inv_c;
         }
         if (a.gmaps) {
-            const float4 r1 = a.prec[5 * (size_t)i + 1], r2 = a.prec[5 * (size_t)i + 2];
+            const float4 r1 = a.prec[kPrec * (size_t)i + 1], r2 = a.prec[kPrec * (size_t)i + 2];
             const Footprint fp = footprint_i(a.map, __float_as_int(r2.y), __float_as_int(r2.z), r1.w, r2.x);
             scatter8(a.gmaps, fp, g);
         }

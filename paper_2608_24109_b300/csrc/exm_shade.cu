@@ -27,7 +27,6 @@
 namespace exm {
 
 constexpr int kShadeWarps = 4;        // warps per block of the shade kernel
-constexpr int kPrec = 5;              // float4 per pixel record (pixel_prep_kernel)
 constexpr int kListMax = 1024;        // sample slots enumerated per round (32 bit words)
 // Queued rays per chunk at most (2 float4 each: 4 GiB).  Few, large chunks keep the persistent
 // tracer's launch tails small: the geometry workload's forward takes 8 chunks (64 at 2^24 rays).
@@ -63,7 +62,8 @@ struct ShadeArgs {
     uint32_t* visbits;   // [P * wd]
     uint32_t* secbits;   // [P * ws]
     int32_t* hits;       // [P * Nb] closest front-facing hit of each secondary ray, -1 if none
-    float4* prec;        // [P * 5] per-pixel shading record (pixel_prep_kernel)
+    float4* prec;        // [P * kPrec] per-pixel shading record
+    float* pacc;         // [P * 12] backward: per-pixel sums of the sample adjoints
     float4* rays;        // queue: [ray_cap * 2]
     uint32_t ray_cap;
     uint32_t* ctr;       // per chunk: [0] queued, [1] fetch cursor (x2: closest, any)
@@ -562,28 +562,48 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
 
 // ------------------------------------------------------------------ shading (warp per pixel)
 
-// Appends the set bits of `words` [0, nwords) of a pixel into the warp's list (bit index
-// relative to wbase*32) and returns how many were appended.
+// Appends the set bits of `words` [wbase, min(wbase + 32, nwords)) of a pixel to the warp's
+// list (bit index relative to wbase*32) and returns how many were appended.  Word k goes to
+// all lanes at once: lane l writes bit l of it, if set, at the count of the set bits below.
 __device__ __forceinline__ int enumerate_bits(const uint32_t* words, int wbase, int nwords, uint16_t* list) {
     const int lane = threadIdx.x & 31;
-    const int wi = wbase + lane;
-    uint32_t w = wi < nwords ? words[wi] : 0u;
-    const int cnt = __popc(w);
-    int off = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, off, o);
-        if (lane >= o) off += y;
-    }
-    const int tot = __shfl_sync(0xffffffffu, off, 31);
-    off -= cnt;
-    while (w) {
-        const int b = __ffs(w) - 1;
-        list[off++] = (uint16_t)(lane * 32 + b);
-        w &= w - 1u;
+    const unsigned lt = (1u << lane) - 1u;
+    const int n = min(32, nwords - wbase);
+    const uint32_t mine = lane < n ? words[wbase + lane] : 0u;
+    int tot = 0;
+    for (int k = 0; k < n; ++k) {
+        const uint32_t w = __shfl_sync(0xffffffffu, mine, k);
+        if ((w >> lane) & 1u) list[tot + __popc(w & lt)] = (uint16_t)(k * 32 + lane);
+        tot += __popc(w);
     }
     __syncwarp();
     return tot;
+}
+
+// Warp sum of N values (N a power of two, at most 32).  Each step halves the values a lane
+// holds: the lanes with bit `ofs` set keep the upper half and add their partner's, the others
+// the lower half; once one value is left the remaining steps are a plain butterfly.  Lane l
+// returns the total of v[l >> (5 - log2 N)].  N - 1 + 5 - log2 N shuffles instead of 5 N.
+template <int N>
+__device__ __forceinline__ float warp_sum_spread(float (&v)[N]) {
+    static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "N: a power of two up to 32");
+    const int lane = threadIdx.x & 31;
+    int ofs = 16;
+#pragma unroll
+    for (int h = N / 2; h >= 1; h /= 2) {
+        const bool up = (lane & ofs) != 0;
+#pragma unroll
+        for (int k = 0; k < h; ++k) {
+            const float send = up ? v[k] : v[k + h];
+            const float keep = up ? v[k + h] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, ofs);
+        }
+        ofs >>= 1;
+    }
+    float t = v[0];
+#pragma unroll
+    for (; ofs > 0; ofs >>= 1) t += __shfl_xor_sync(0xffffffffu, t, ofs);
+    return t;
 }
 
 // Per-pixel record, computed once per covered pixel (one thread each) so that the FP64
@@ -670,9 +690,29 @@ __device__ __forceinline__ void pixel_shade(const ShadeArgs& A, uint32_t i, int 
 }
 
 // Resident blocks per SM the register allocation must allow (no spills at these caps:
-// 128 / 170 registers backward, 64 / 102 forward, direct-only / with indirect).
-constexpr int shade_min_blocks(bool bwd, bool ind) { return bwd ? (ind ? 3 : 4) : (ind ? 5 : 8); }
+// 96 / 128 registers backward, 64 / 102 forward, direct-only / with indirect).
+constexpr int shade_min_blocks(bool bwd, bool ind) { return bwd ? (ind ? 4 : 5) : (ind ? 5 : 8); }
 
+// Material and shading normal of each covered pixel from the maps of the pass that runs it,
+// one thread per pixel, into its record: [5] a.xyz r, [6] m n_s.xyz.  The warp-per-pixel
+// sample loops below read them instead of evaluating Eqs. 10-11 once per warp.
+template <typename T>
+__global__ void __launch_bounds__(256) pixel_surface_kernel(ShadeArgs A) {
+    const uint32_t total = *A.count;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t pid = A.pixels[i];
+        const int f = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
+        PixelShade S;
+        pixel_shade<T>(A, i, f, false, S);
+        float4* R = A.prec + kPrec * (size_t)i;
+        R[5] = make_float4(S.su.a.x, S.su.a.y, S.su.a.z, S.su.r);
+        R[6] = make_float4(S.su.m, S.su.ns.x, S.su.ns.y, S.su.ns.z);
+    }
+}
+
+// Sample loops, one warp per pixel: the forward sums the pixel's estimator (Eqs. 17-20); the
+// backward sums, over the pixel's samples, the adjoints of E (scattered per sample) and of
+// n_s, w_o, a, r and m, which shade_epilogue_kernel carries back to the maps and vertices.
 template <typename T, bool BWD, bool COUNT, bool IND>
 __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) shade_kernel(ShadeArgs A) {
     __shared__ uint16_t s_list[kShadeWarps][kListMax];
@@ -694,20 +734,18 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
             g = ld3(A.grad_rgb + 3 * (size_t)pid);
             if (g.x == 0.0f && g.y == 0.0f && g.z == 0.0f) continue;
         }
-        const int f = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
-        const Cam& cam = A.cams[c];
+        const float4* R = A.prec + kPrec * (size_t)i;
         S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
         if (IND) {
-            const float4 r3 = A.prec[kPrec * (size_t)i + 3], r4 = A.prec[kPrec * (size_t)i + 4];
+            const float4 r3 = R[3], r4 = R[4];
             org = s3(r3.x, r3.y, r3.z);
             ngs = s3(r3.w, r4.x, r4.y);
         }
-        // ---- attribute query at x (Eqs. 10-11); only n_s, the material and w_o stay live
-        // through the sample loops, the backward epilogue recomputes the rest
-        PixelShade S;
-        pixel_shade<T>(A, i, f, false, S);
-        const Surface su = S.su;
-        const float3 wo = S.wo;
+        // shading state at x (Eqs. 10-11) from the pixel's record
+        const float4 r1 = R[1], r5 = R[5], r6 = R[6];
+        const float3 wo = f3(r1.x, r1.y, r1.z);
+        const float3 sa = f3(r5.x, r5.y, r5.z), sns = f3(r6.y, r6.z, r6.w);
+        const float sr = r5.w, sm = r6.x;
         float3 L = f3(0.f, 0.f, 0.f);
         float3 gns = f3(0.f, 0.f, 0.f), gwo = f3(0.f, 0.f, 0.f), ga = f3(0.f, 0.f, 0.f);
         float gr = 0.f, gm = 0.f;
@@ -725,13 +763,13 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                     const float3 wi = normalize(tof(ls.dir));
                     const float w = ls.inv_pdf * invNd;
                     ++c_brdf;
-                    const float3 fc = brdf_cos(su.ns, wi, wo, su.a, su.r, su.m);
+                    const float3 fc = brdf_cos(sns, wi, wo, sa, sr, sm);
                     if (!BWD) {
                         L += w * (ls.E * fc);
                     } else {
                         const float3 gE = w * (g * fc);
                         atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
-                        brdf_cos_adjoint(su.ns, wi, wo, su.a, su.r, su.m, w * (g * ls.E), gns, gwo, ga, gr, gm);
+                        brdf_cos_adjoint(sns, wi, wo, sa, sr, sm, w * (g * ls.E), gns, gwo, ga, gr, gm);
                     }
                 }
             }
@@ -740,7 +778,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
         if (!BWD && lane == 0) my_samples += (unsigned long long)A.Nd;
         // ---- one-bounce indirect (Eqs. 18-19): lanes take the pixel's live (j, s) pairs
         if (IND && A.Nb > 0 && A.lambda != 0.0f) {
-            const float3 fdx = ((1.0f - su.m) * kInvPi) * su.a;
+            const float3 fdx = ((1.0f - sm) * kInvPi) * sa;
             const float scale = A.lambda / (float)A.Nb;
             const float invNs = 1.0f / (float)A.Ns;
             if (!BWD) {
@@ -762,7 +800,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                     float xi1;
                     const S3 wjs = secondary_dir(A, rem, c, jj, ngs, &xi1);
                     const float3 wj = normalize(tof(wjs));
-                    const float cxj = dot(su.ns, wj);
+                    const float cxj = dot(sns, wj);
                     if (cxj <= 0.0f) continue;
                     const int gtri = A.hits[(size_t)i * A.Nb + jj];
                     S3 ys, ngy, yorg;
@@ -811,8 +849,8 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                         atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
                         // f_d(x) and n_s(x) through max(n_s(x).w_j, 0)
                         const float3 gfdx = wb * (g * (fdy * ET));
-                        ga += ((1.0f - su.m) * kInvPi) * gfdx;
-                        gm += -dot(gfdx, su.a) * kInvPi;
+                        ga += ((1.0f - sm) * kInvPi) * gfdx;
+                        gm += -dot(gfdx, sa) * kInvPi;
                         gns += (scale * pb_inv * dot(g, fdx * (fdy * ET))) * wj;
                         // material at y (its geometry is a constant of the derivative)
                         const float3 gLsec = wb * (g * fdx);
@@ -832,41 +870,58 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
             }
         }
         if (!BWD) {
-#pragma unroll
-            for (int ofs = 16; ofs > 0; ofs >>= 1) {
-                L.x += __shfl_xor_sync(0xffffffffu, L.x, ofs);
-                L.y += __shfl_xor_sync(0xffffffffu, L.y, ofs);
-                L.z += __shfl_xor_sync(0xffffffffu, L.z, ofs);
-            }
-            if (lane == 0) {
-                float* out = A.out + 3 * (size_t)pid;
-                out[0] = L.x; out[1] = L.y; out[2] = L.z;
-            }
+            float v[4] = {L.x, L.y, L.z, 0.0f};
+            const float t = warp_sum_spread<4>(v);  // lanes 0, 8, 16: L.x, L.y, L.z
+            if ((lane & 7) == 0 && lane < 24) A.out[3 * (size_t)pid + (lane >> 3)] = t;
             continue;
         }
-        // ---- adjoint of the attribute query at x: sum the lanes' partial adjoints
-        float acc[11] = {gns.x, gns.y, gns.z, gwo.x, gwo.y, gwo.z, ga.x, ga.y, ga.z, gr, gm};
-#pragma unroll
-        for (int q = 0; q < 11; ++q)
-#pragma unroll
-            for (int ofs = 16; ofs > 0; ofs >>= 1) acc[q] += __shfl_xor_sync(0xffffffffu, acc[q], ofs);
-        gns = f3(acc[0], acc[1], acc[2]);
-        gwo = f3(acc[3], acc[4], acc[5]);
-        // recompute the shading state (a fresh read of the visibility key keeps the compiler
-        // from holding the first evaluation live across the sample loops)
-        const int f2 = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
+        // ---- the pixel's sums of the sample adjoints, for the epilogue
+        float v[16] = {gns.x, gns.y, gns.z, gwo.x, gwo.y, gwo.z, ga.x, ga.y, ga.z, gr, gm, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float t = warp_sum_spread<16>(v);  // lanes 2q and 2q + 1: value q
+        if ((lane & 1) == 0 && lane < 22) A.pacc[12 * (size_t)i + (lane >> 1)] = t;
+    }
+    if (!BWD) {
+        if (lane == 0 && my_samples) atomicAdd(A.samples, my_samples);
+    }
+    if (COUNT) {
+        for (int ofs = 16; ofs > 0; ofs >>= 1) c_brdf += __shfl_xor_sync(0xffffffffu, c_brdf, ofs);
+        if (lane == 0) atomicAdd(A.work + 2, (unsigned long long)c_brdf);
+    }
+}
+
+// Adjoint of the attribute query at x (Eqs. 10-11), one thread per pixel: from the sums of
+// the sample adjoints of n_s, w_o, a, r and m to the map texels of the bilinear footprint
+// and, when vertex gradients are asked for, through the tangent frame, the UV and the
+// camera-ray barycentrics to the vertices, their normals and the UV-vertex tangents.
+template <typename T>
+__global__ void __launch_bounds__(256) shade_epilogue_kernel(ShadeArgs A) {
+    const uint32_t total = *A.count;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+        const uint32_t pid = A.pixels[i];
+        const float3 g = ld3(A.grad_rgb + 3 * (size_t)pid);
+        if (g.x == 0.0f && g.y == 0.0f && g.z == 0.0f) continue;  // the sample kernel skipped it
+        int c, px, py;
+        uint32_t rem;
+        pixel_of(A, pid, &c, &px, &py, &rem);
+        const Cam& cam = A.cams[c];
+        const float4* q = reinterpret_cast<const float4*>(A.pacc + 12 * (size_t)i);
+        const float4 q0 = q[0], q1 = q[1], q2 = q[2];
+        const float acc[11] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w, q2.x, q2.y, q2.z};
+        const float3 gns = f3(acc[0], acc[1], acc[2]);
+        const float3 gwo = f3(acc[3], acc[4], acc[5]);
+        const int f = (int)(uint32_t)(A.visbuf[pid] & 0xffffffffull);
         PixelShade E;
-        pixel_shade<T>(A, i, f2, true, E);
+        pixel_shade<T>(A, i, f, true, E);
+        const Surface& su = E.su;
         const int i0 = E.i0, i1 = E.i1, i2 = E.i2, u0 = E.u0, u1 = E.u1, u2 = E.u2;
         const float3 P0 = E.P0, P1 = E.P1, P2 = E.P2;
         const float3 N0 = E.N0, N1 = E.N1, N2 = E.N2, T0 = E.T0, T1 = E.T1, T2 = E.T2;
         const float3 ni = E.ni, ti = E.ti;
         const float2 uv0 = E.uv0, uv1 = E.uv1, uv2 = E.uv2;
         const Footprint fp = E.fp;
-        const float b[3] = {E.b[0], E.b[1], E.b[2]};
-        float dfs[8], dft[8];
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch) { dfs[ch] = E.dfs[ch]; dft[ch] = E.dft[ch]; }
+        const float* b = E.b;
+        const float* dfs = E.dfs;
+        const float* dft = E.dft;
         const float vol = E.vol;
         const float3 wo2 = E.wo;
         // camera-ray direction (FP32 suffices for the barycentric adjoint)
@@ -883,14 +938,15 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
         const float3 gnt = f3(dot(su.T, gns), dot(su.B, gns), dot(su.n, gns));
         const float3 gq = (1.0f / su.ql) * (gnt - dot(gnt, su.nt) * su.nt);
         gatt[5] = gq.x; gatt[6] = gq.y; gatt[7] = gq.z;
-        if (A.gmaps && lane < 8) {
-            const int tap = lane >> 1, half = lane & 1;
-            const float wt = tap == 0 ? (1.f - fp.fs) * (1.f - fp.ft)
-                           : tap == 1 ? fp.fs * (1.f - fp.ft) : tap == 2 ? (1.f - fp.fs) * fp.ft : fp.fs * fp.ft;
-            const uint32_t tx = tap == 0 ? fp.t[0] : tap == 1 ? fp.t[1] : tap == 2 ? fp.t[2] : fp.t[3];
-            const float4 v = half ? make_float4(wt * gatt[4], wt * gatt[5], wt * gatt[6], wt * gatt[7])
-                                  : make_float4(wt * gatt[0], wt * gatt[1], wt * gatt[2], wt * gatt[3]);
-            atomicAdd(reinterpret_cast<float4*>(A.gmaps) + 2 * (size_t)tx + half, v);
+        if (A.gmaps) {
+            const float wt[4] = {(1.f - fp.fs) * (1.f - fp.ft), fp.fs * (1.f - fp.ft), (1.f - fp.fs) * fp.ft, fp.fs * fp.ft};
+            float4* gm = reinterpret_cast<float4*>(A.gmaps);
+#pragma unroll
+            for (int tap = 0; tap < 4; ++tap) {
+                const float w = wt[tap];
+                atomicAdd(gm + 2 * (size_t)fp.t[tap], make_float4(w * gatt[0], w * gatt[1], w * gatt[2], w * gatt[3]));
+                atomicAdd(gm + 2 * (size_t)fp.t[tap] + 1, make_float4(w * gatt[4], w * gatt[5], w * gatt[6], w * gatt[7]));
+            }
         }
         if (A.gV == nullptr) continue;
         const float3 gB = su.nt.y * gns;
@@ -940,31 +996,17 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
             gP1 += ge1;
             gP2 += ge2;
         }
-        if (lane >= 8 && lane < 11) {
-            const int k = lane - 8;
-            const int vk = k == 0 ? i0 : k == 1 ? i1 : i2;
-            const float3 gp = k == 0 ? gP0 : k == 1 ? gP1 : gP2;
-            atomicAdd(A.gV + 3 * vk, gp.x);
-            atomicAdd(A.gV + 3 * vk + 1, gp.y);
-            atomicAdd(A.gV + 3 * vk + 2, gp.z);
-        } else if (lane >= 11 && lane < 14) {
-            const int k = lane - 11;
-            const int vk = k == 0 ? i0 : k == 1 ? i1 : i2;
-            const float3 a1 = b[k == 0 ? 0 : k == 1 ? 1 : 2] * gni;
-            atomicAdd(A.gnrm + vk, make_float4(a1.x, a1.y, a1.z, 0.0f));
-        } else if (lane >= 14 && lane < 17) {
-            const int k = lane - 14;
-            const int uk = k == 0 ? u0 : k == 1 ? u1 : u2;
-            const float3 a2 = b[k == 0 ? 0 : k == 1 ? 1 : 2] * gti;
-            atomicAdd(A.gtan + uk, make_float4(a2.x, a2.y, a2.z, 0.0f));
+        const int vi[3] = {i0, i1, i2}, ui[3] = {u0, u1, u2};
+        const float3 gP[3] = {gP0, gP1, gP2};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            atomicAdd(A.gV + 3 * vi[k], gP[k].x);
+            atomicAdd(A.gV + 3 * vi[k] + 1, gP[k].y);
+            atomicAdd(A.gV + 3 * vi[k] + 2, gP[k].z);
+            const float3 a1 = b[k] * gni, a2 = b[k] * gti;
+            atomicAdd(A.gnrm + vi[k], make_float4(a1.x, a1.y, a1.z, 0.0f));
+            atomicAdd(A.gtan + ui[k], make_float4(a2.x, a2.y, a2.z, 0.0f));
         }
-    }
-    if (!BWD) {
-        if (lane == 0 && my_samples) atomicAdd(A.samples, my_samples);
-    }
-    if (COUNT) {
-        for (int ofs = 16; ofs > 0; ofs >>= 1) c_brdf += __shfl_xor_sync(0xffffffffu, c_brdf, ofs);
-        if (lane == 0) atomicAdd(A.work + 2, (unsigned long long)c_brdf);
     }
 }
 
@@ -1011,6 +1053,7 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     A.status = ctx->d_status;
     const size_t P = (size_t)f->views * f->W * f->H;
     A.prec = f->prec;
+    A.pacc = f->pacc;
     A.visbits = f->bits;
     A.secbits = f->bits ? f->bits + P * A.wd : nullptr;
     A.hits = f->hits;
@@ -1056,6 +1099,21 @@ static void launch_shade_t(const ShadeArgs& A, exm_dtype dt, int num_sms, cudaSt
     }
 }
 
+// The thread-per-pixel kernels around the sample loops: the surface records before them, and
+// after the backward's, its epilogue.
+template <typename T>
+static void launch_pixel_kernels(const ShadeArgs& A, bool epilogue, int num_sms, cudaStream_t s) {
+    if (epilogue) shade_epilogue_kernel<T><<<num_sms * 8, 256, 0, s>>>(A);
+    else pixel_surface_kernel<T><<<num_sms * 8, 256, 0, s>>>(A);
+}
+static void launch_pixel_kernels(const ShadeArgs& A, exm_dtype dt, bool epilogue, int num_sms, cudaStream_t s) {
+    switch (dt) {
+        case EXM_F32: launch_pixel_kernels<float>(A, epilogue, num_sms, s); break;
+        case EXM_BF16: launch_pixel_kernels<__nv_bfloat16>(A, epilogue, num_sms, s); break;
+        default: launch_pixel_kernels<__half>(A, epilogue, num_sms, s); break;
+    }
+}
+
 template <bool BWD>
 static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, exm_dtype dt,
                                cudaStream_t s) {
@@ -1064,6 +1122,7 @@ static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, 
     time_begin(f, p, BWD ? 3 : 2, s);
     const bool ind = A.Nb > 0 && A.lambda != 0.0f;
     const bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
+    launch_pixel_kernels(A, dt, false, sms, s);
     if (ind) {
         if (count) launch_shade_t<BWD, true, true>(A, dt, sms, s);
         else launch_shade_t<BWD, false, true>(A, dt, sms, s);
@@ -1071,8 +1130,10 @@ static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, 
         if (count) launch_shade_t<BWD, true, false>(A, dt, sms, s);
         else launch_shade_t<BWD, false, false>(A, dt, sms, s);
     }
+    const bool epilogue = BWD && (A.gmaps || A.gV);
+    if (epilogue) launch_pixel_kernels(A, dt, true, sms, s);
     time_end(f, p, s);
-    ctx->launches += 1;
+    ctx->launches += epilogue ? 3 : 2;
     return exm_cuda_check(cudaGetLastError(), "shade launch");
 }
 
@@ -1099,7 +1160,7 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     const size_t P32 = (P + 31) & ~(size_t)31;
     const uint32_t Pc = (uint32_t)max((size_t)32, min(P32, (size_t)((cap_max / per_pixel) & ~31u)));
     const uint32_t ray_cap = (uint32_t)min((size_t)cap_max, (size_t)Pc * per_pixel);
-    if (!ensure(&f->prec, &f->prec_cap, P * (size_t)kPrec) ||
+    if (!ensure(&f->prec, &f->prec_cap, P * (size_t)kPrec) || !ensure(&f->pacc, &f->pacc_cap, P * (size_t)12) ||
         !ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)ray_cap * 2) ||
         (indirect && !ensure(&f->hits, &f->hits_cap, P * (size_t)p->n_bounce)))
         return exm_fail(EXM_ERR_OOM, "wavefront buffers");
@@ -1148,7 +1209,7 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
 static exm_status check_saved(const exm_frame* f, const exm_params* p) {
     const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
     if (f->last_nd != p->n_direct || f->last_nb != (indirect ? p->n_bounce : 0) ||
-        f->last_ns != (indirect ? p->n_light : 0) || !f->bits)
+        f->last_ns != (indirect ? p->n_light : 0) || !f->bits || !f->pacc)
         return exm_fail(EXM_ERR_ARG, "backward: the frame holds no forward pass with these sample counts");
     return EXM_OK;
 }
