@@ -273,10 +273,16 @@ __device__ __forceinline__ Surface make_surface(const float att[8], float3 ni, f
 // tile-ordered pixel list, and consecutive queue entries hold the same sample index k of
 // those pixels, so the 32 rays a warp later traces start close together and point the
 // same way (the same stratum of the same CDF).
-constexpr int kGenK = 32;  // sample indices per warp of gen_direct
+constexpr int kGenK = 32;     // sample indices per warp of gen_direct
+constexpr int kGenBatch = 8;  // sample indices per queue append of a warp
+constexpr int kGenThreads = 256;
 
 // One shadow ray per (pixel, k) whose direction is above the geometric horizon (Eq. 17).
-__global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
+// A warp appends the rays of kGenBatch sample indices at once: their directions wait in
+// shared memory (each lane its own column) while one atomic on the chunk's queue counter
+// reserves their slots, so the counter sees one request per batch instead of one per sample.
+__global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
+    __shared__ float s_dir[kGenThreads / 32][kGenBatch][3][32];
     const uint32_t total = *A.count;
     const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
     if (A.chunk_begin >= end) return;
@@ -284,7 +290,9 @@ __global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
     const uint32_t nkc = (uint32_t)(A.Nd + kGenK - 1) / kGenK;
     const uint32_t group = warp / nkc, kc = warp % nkc;
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     if (A.chunk_begin + group * 32 >= end) return;
+    float (*sd)[3][32] = s_dir[threadIdx.x >> 5];
     const uint32_t i = A.chunk_begin + group * 32 + lane;
     const bool valid = i < end;
     EnvView env = A.env;
@@ -300,29 +308,47 @@ __global__ void __launch_bounds__(256) gen_direct_kernel(ShadeArgs A) {
         ngs = s3(r3.w, r4.x, r4.y);
     }
     const int k0 = (int)kc * kGenK, k1 = min(A.Nd, k0 + kGenK);
-    // samples k and k + 1 together (their texel searches overlap), appended in order
-    for (int k = k0; k < k1; k += 2) {
-        const bool two = k + 1 < k1;  // warp-uniform
-        bool want[2] = {false, false};
-        S3 dir[2] = {s3(0.f, 0.f, 0.f), s3(0.f, 0.f, 0.f)};
-        if (valid) {
-            const int kb = two ? k + 1 : k;
+    for (int kb = k0; kb < k1; kb += kGenBatch) {
+        const int kn = min(kGenBatch, k1 - kb);  // warp-uniform
+        uint32_t want = 0;                       // bit u: the ray of sample kb + u is queued
+        // samples k and k + 1 together (their texel searches overlap)
+        for (int u = 0; u < kn; u += 2) {
+            if (!valid) continue;
+            const int k = kb + u;
+            const bool two = u + 1 < kn;
+            const int k2 = two ? k + 1 : k;
             const uint4 ha = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
-            const uint4 hb = philox(make_uint4(rem, (uint32_t)c, (uint32_t)kb, 0u), A.key);
+            const uint4 hb = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k2, 0u), A.key);
             LightSample sa, sb;
-            light_sample2(env, ha, (uint32_t)k, hb, (uint32_t)kb, A.nxd, A.nyd, &sa, &sb);
-            dir[0] = sa.dir;
-            dir[1] = sb.dir;
-            want[0] = sdot(ngs, dir[0]) > 0.0f;
-            want[1] = two && sdot(ngs, dir[1]) > 0.0f;
+            light_sample2(env, ha, (uint32_t)k, hb, (uint32_t)k2, A.nxd, A.nyd, &sa, &sb);
+            if (sdot(ngs, sa.dir) > 0.0f) {
+                want |= 1u << u;
+                sd[u][0][lane] = sa.dir.x; sd[u][1][lane] = sa.dir.y; sd[u][2][lane] = sa.dir.z;
+            }
+            if (two && sdot(ngs, sb.dir) > 0.0f) {
+                want |= 2u << u;
+                sd[u + 1][0][lane] = sb.dir.x; sd[u + 1][1][lane] = sb.dir.y; sd[u + 1][2][lane] = sb.dir.z;
+            }
         }
-        for (int u = 0; u < (two ? 2 : 1); ++u) {
-            const uint32_t idx = warp_append(A.ctr + 2, want[u]);
-            if (want[u]) {
+        // one reservation for the batch; within it the rays keep the order (k, lane)
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int u = 0; u < kGenBatch; ++u) cnt += (uint32_t)__popc(__ballot_sync(0xffffffffu, (want >> u) & 1u));
+        if (cnt == 0) continue;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(A.ctr + 2, cnt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+        for (int u = 0; u < kGenBatch; ++u) {
+            const unsigned mu = __ballot_sync(0xffffffffu, (want >> u) & 1u);
+            if ((want >> u) & 1u) {
+                const uint32_t idx = base + (uint32_t)__popc(mu & lt);
+                const S3 d = s3(sd[u][0][lane], sd[u][1][lane], sd[u][2][lane]);
                 if (idx < A.ray_cap)
-                    push_ray(A.rays, idx, org, dir[u], (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)(k + u));
+                    push_ray(A.rays, idx, org, d, (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)(kb + u));
                 else atomicOr(A.status, ERRBIT_TRAVERSAL);
             }
+            base += (uint32_t)__popc(mu);
         }
     }
 }
@@ -361,14 +387,18 @@ __global__ void __launch_bounds__(256) gen_secondary_kernel(ShadeArgs A) {
     }
 }
 
-// One shadow ray per (valid secondary hit, s) above the hit's geometric horizon (Eq. 18).
-__global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
+// One shadow ray per (valid secondary hit, s) above the hit's geometric horizon (Eq. 18),
+// appended kGenBatch light samples at a time like gen_direct's.
+__global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) {
+    __shared__ float s_dir[kGenThreads / 32][kGenBatch][3][32];
     const uint32_t total = *A.count;
     const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
     if (A.chunk_begin >= end) return;
     const uint32_t group = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     if (A.chunk_begin + group * 32 >= end) return;
+    float (*sd)[3][32] = s_dir[threadIdx.x >> 5];
     const uint32_t i = A.chunk_begin + group * 32 + lane;
     const bool valid = i < end;
     EnvView env = A.env;
@@ -393,20 +423,38 @@ __global__ void __launch_bounds__(256) gen_seclight_kernel(ShadeArgs A) {
             float3 Q[3];
             secondary_point(A, g, org, wjs, &ys, &ngy, &yorg, Q);
         }
-        for (int s = 0; s < A.Ns; ++s) {
-            bool want = false;
-            S3 dir = s3(0.f, 0.f, 0.f);
+        for (int sb = 0; sb < A.Ns; sb += kGenBatch) {
+            const int sn = min(kGenBatch, A.Ns - sb);  // warp-uniform
+            uint32_t want = 0;
             if (g >= 0) {
-                const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(j * A.Ns + s), 2u), A.key);
-                const LightSample ls = light_sample(env, h, (uint32_t)s, A.nxs, A.nys);
-                dir = ls.dir;
-                want = sdot(ngy, dir) > 0.0f;
+                for (int u = 0; u < sn; ++u) {
+                    const int s = sb + u;
+                    const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(j * A.Ns + s), 2u), A.key);
+                    const LightSample ls = light_sample(env, h, (uint32_t)s, A.nxs, A.nys);
+                    if (sdot(ngy, ls.dir) > 0.0f) {
+                        want |= 1u << u;
+                        sd[u][0][lane] = ls.dir.x; sd[u][1][lane] = ls.dir.y; sd[u][2][lane] = ls.dir.z;
+                    }
+                }
             }
-            const uint32_t idx = warp_append(A.ctr + 2, want);
-            if (want) {
-                const uint64_t slot = (uint64_t)i * (uint32_t)A.ws * 32u + (uint32_t)(j * A.Ns + s);
-                if (idx < A.ray_cap) push_ray(A.rays, idx, yorg, dir, slot | (1ull << 63));
-                else atomicOr(A.status, ERRBIT_TRAVERSAL);
+            uint32_t cnt = 0;
+#pragma unroll
+            for (int u = 0; u < kGenBatch; ++u) cnt += (uint32_t)__popc(__ballot_sync(0xffffffffu, (want >> u) & 1u));
+            if (cnt == 0) continue;
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(A.ctr + 2, cnt);
+            base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+            for (int u = 0; u < kGenBatch; ++u) {
+                const unsigned mu = __ballot_sync(0xffffffffu, (want >> u) & 1u);
+                if ((want >> u) & 1u) {
+                    const uint32_t idx = base + (uint32_t)__popc(mu & lt);
+                    const S3 d = s3(sd[u][0][lane], sd[u][1][lane], sd[u][2][lane]);
+                    const uint64_t slot = (uint64_t)i * (uint32_t)A.ws * 32u + (uint32_t)(j * A.Ns + sb + u);
+                    if (idx < A.ray_cap) push_ray(A.rays, idx, yorg, d, slot | (1ull << 63));
+                    else atomicOr(A.status, ERRBIT_TRAVERSAL);
+                }
+                base += (uint32_t)__popc(mu);
             }
         }
     }
@@ -1187,11 +1235,11 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
             ctx->launches += 1;
         }
         if (p->n_direct > 0) {  // 0 in the indirect-only half-resolution pass
-            gen_direct_kernel<<<exm_blocks((size_t)Pc * ((p->n_direct + kGenK - 1) / kGenK), 256), 256, 0, s>>>(A);
+            gen_direct_kernel<<<exm_blocks((size_t)Pc * ((p->n_direct + kGenK - 1) / kGenK), kGenThreads), kGenThreads, 0, s>>>(A);
             ctx->launches += 1;
         }
         if (indirect) {
-            gen_seclight_kernel<<<exm_blocks((size_t)Pc, 256), 256, 0, s>>>(A);
+            gen_seclight_kernel<<<exm_blocks((size_t)Pc, kGenThreads), kGenThreads, 0, s>>>(A);
             ctx->launches += 1;
         }
         launch_trace<false>(ctx, f, p, A, s);
