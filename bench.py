@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="geometry", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-pixels", type=int, default=384, help="pixels of the CPU-baseline sample")
+    ap.add_argument("--cpu-pixels", type=int, default=1536, help="pixels of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling cases)")
