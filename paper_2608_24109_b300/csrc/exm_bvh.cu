@@ -265,6 +265,41 @@ __global__ void single4_kernel(const float* __restrict__ bounds, float4* nodes4)
     N[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// Bounding sphere of the leaf triangles, for clipping rays: the centre is the middle of the
+// root node's box, the radius the largest distance from it to a triangle vertex.  The stored
+// R^2 is inflated by 2e-4 relative (far above the FP32 rounding of the distances), so that
+// every point of every triangle lies inside the stored sphere.
+__global__ void sphere_centre_kernel(const float4* __restrict__ nodes4, float4* sphere) {
+    const float4* N = nodes4;
+    const float* lo[3] = {&N[0].x, &N[1].x, &N[2].x};
+    const float* hi[3] = {&N[3].x, &N[4].x, &N[5].x};
+    const int* ref = reinterpret_cast<const int*>(&N[6].x);
+    float c[3];
+    for (int a = 0; a < 3; ++a) {
+        float l = INFINITY, h = -INFINITY;
+        for (int k = 0; k < 4; ++k)
+            if (ref[k] != kEmpty4) { l = fminf(l, lo[a][k]); h = fmaxf(h, hi[a][k]); }
+        c[a] = 0.5f * (l + h);
+    }
+    *sphere = make_float4(c[0], c[1], c[2], 0.0f);
+}
+
+__global__ void sphere_radius_kernel(const float4* __restrict__ tris, int nf, float4* sphere) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const float4 c = *sphere;
+    float r2 = 0.0f;
+    if (k < nf) {
+        for (int v = 0; v < 3; ++v) {
+            const float4 p = tris[3 * k + v];
+            const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+            r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
+        }
+        r2 = r2 * 1.0002f + 1e-30f;
+    }
+    for (int o = 16; o > 0; o >>= 1) r2 = fmaxf(r2, __shfl_xor_sync(0xffffffffu, r2, o));
+    if ((threadIdx.x & 31) == 0 && r2 > 0.0f) atomicMax(reinterpret_cast<unsigned int*>(&sphere->w), __float_as_uint(r2));
+}
+
 __global__ void seed4_kernel(int2* in, uint32_t* n_in, uint32_t* n_nodes) {
     in[0] = make_int2(0, 0);
     *n_in = 1;
@@ -287,6 +322,7 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
                   cudaMalloc(&m->scene_box, 6 * 4) == cudaSuccess &&
                   cudaMalloc(&m->tris, nn * 3 * sizeof(float4)) == cudaSuccess &&
                   cudaMalloc(&m->nodes4, internal * 8 * sizeof(float4)) == cudaSuccess &&
+                  cudaMalloc(&m->sphere, sizeof(float4)) == cudaSuccess &&
                   cudaMalloc(&m->frontier, 2 * nn * sizeof(int2)) == cudaSuccess &&
                   cudaMalloc(&m->frontier_cnt, 4 * sizeof(uint32_t)) == cudaSuccess &&
                   cudaMalloc(&m->ploc_c, 2 * nn * 4) == cudaSuccess && cudaMalloc(&m->ploc_nn, nn * 4) == cudaSuccess &&
@@ -358,5 +394,7 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
             fout = tmp;
         }
     }
+    sphere_centre_kernel<<<1, 1, 0, s>>>(m->nodes4, m->sphere);
+    sphere_radius_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->tris, n, m->sphere);
     return exm_cuda_check(cudaGetLastError(), "BVH build launch");
 }

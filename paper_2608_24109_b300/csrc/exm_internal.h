@@ -36,6 +36,7 @@ struct exm_mesh {
     // BVH
     float4* tris = nullptr;    // [nf * 3]
     float4* nodes4 = nullptr;  // [max(nf-1,1) * 8] 4-wide nodes
+    float4* sphere = nullptr;  // [1] bounding sphere of the triangles: centre, inflated R^2
     int2* frontier = nullptr;  // [2 * nf] collapse frontier (binary node, 4-wide node)
     uint32_t* frontier_cnt = nullptr;
     // build scratch

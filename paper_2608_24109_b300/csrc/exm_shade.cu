@@ -472,7 +472,7 @@ constexpr int kRound = 16;  // node visits between refills
 constexpr int kTraceThreads = 128;
 
 template <bool CLOSEST, bool COUNT>
-__global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
+__global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
     int stack[kStackSize4];
     const uint32_t* qcount = A.ctr + (CLOSEST ? 0 : 2);
     uint32_t* cursor = A.ctr + (CLOSEST ? 1 : 3);
@@ -483,6 +483,7 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
     uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
     int sp = 0, node = 0, best = -1, steps = 0;
     float bt = INFINITY, bdet = 0.0f;
+    float tclip = 0.0f;  // where the ray leaves the triangles' bounding sphere
     bool active = false;
     Ray r;
     r.o = s3(0.f, 0.f, 0.f); r.d = s3(0.f, 0.f, 1.f);
@@ -505,6 +506,7 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
             if (!active && my < pend) {
                 const float4 a = A.rays[2 * (size_t)my], b = A.rays[2 * (size_t)my + 1];
                 r = make_ray(s3(a.x, a.y, a.z), s3(a.w, b.x, b.y));
+                tclip = sphere_exit(r.o, r.d, __ldg(A.bvh.sphere));
                 slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
                 sp = 0; node = 0; best = -1; steps = 0; bt = INFINITY; bdet = 0.0f;
                 active = true;
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(kTraceThreads) trace_kernel(ShadeArgs A) {
                 const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
                 const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
                 const float4 rf = __ldg(N + 6);
-                const float tmax = CLOSEST ? bt : INFINITY;
+                const float tmax = CLOSEST ? fminf(bt, tclip) : tclip;
                 float tc[4];
                 const int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
                 bool hc[4];
@@ -1076,7 +1078,7 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     ShadeArgs A{};
     A.V = m->V; A.F = m->F; A.UV = m->UV; A.Fuv = m->Fuv;
     A.nrm = m->nrm; A.tan = m->tan; A.fsign = m->fsign;
-    A.bvh.tris = m->tris; A.bvh.nodes4 = m->nodes4;
+    A.bvh.tris = m->tris; A.bvh.nodes4 = m->nodes4; A.bvh.sphere = m->sphere;
     A.map.data = maps; A.map.W = mapW; A.map.H = mapH; A.map.wrap_u = (p->flags & EXM_FLAG_WRAP_U) != 0;
     A.env.texel = e->texel; A.env.cdf = e->cdf; A.env.rguide = e->rguide; A.env.cguide = e->cguide;
     A.env.W = e->W; A.env.H = e->H;
