@@ -394,3 +394,34 @@ def test_empty_frame_everywhere():
         r.sync()
         assert loss.item() == 0.0 and float(gm.abs().sum()) == 0.0 and int(counts.sum()) == 0
         r.close()
+
+
+# ----------------------------------------------------------------- sample counts off the fast paths
+
+def _forward_and_backward_full(sc, what):
+    r, M, E, out = gpu_forward(sc)
+    keys, tab, dec, V, Mo, Eo = oracle_full(sc)
+    assert np.array_equal(keys_u64(r.visbuf()), keys)
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    check_radiance(out.cpu().numpy()[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]], I, what)
+    _grad_compare(sc, 0, subset=False)
+    return dec
+
+
+def test_parity_sample_counts_without_powers_of_two():
+    """N_d = 37, N_b = 3, N_s = 3.  The light strata are 37 x 1 and 3 x 1 (the general mapping of
+    a sample index to its stratum, not the shift and mask of power-of-two counts); ray
+    generation reserves queue slots 8 sample indices at a time, so the direct batches end in
+    a tail of 5 (an odd pair) and the secondary light batches hold 3; the visibility words per
+    pixel (2 direct, 1 secondary) are partly filled."""
+    sc = small_cavity(res=40, views=2, n_direct=37, n_bounce=3, n_light=3)
+    dec = _forward_and_backward_full(sc, "N_d 37, N_b 3, N_s 3")
+    assert (dec.stri >= 0).sum() > 50
+
+
+def test_parity_more_direct_samples_than_one_list_round():
+    """N_d = 1100 takes 35 visibility words per pixel; the shade kernels list a pixel's live
+    samples 32 words (1024 samples) at a time, so every pixel needs a second, partial round.
+    The strata are 44 x 25."""
+    sc = ragged_tiny(26, 22, 1, n_direct=1100)
+    _forward_and_backward_full(sc, "N_d 1100")
