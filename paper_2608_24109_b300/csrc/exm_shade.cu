@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
 // pool whenever their ray is done, so no lane idles while the longest ray of the warp
 // finishes, and the rays a warp holds stay local to one group of pixels.
 constexpr uint32_t kPool = 256;
-constexpr int kRound = 16;  // node visits between refills
+constexpr int kRound = 24;  // node visits between refills
 
 constexpr int kTraceThreads = 128;
 
@@ -523,8 +523,9 @@ __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
         // one item per iteration: a 4-wide node (node >= 0) or one triangle (node < 0, ~k);
         // hit leaves are pushed like inner nodes, so a warp runs at most one triangle test
         // per iteration whatever its lanes found in their last node
-        for (int it = 0; it < kRound; ++it) {
-            if (++steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
+        steps += kRound;  // the cap is checked once per round: at most kTraversalCap + kRound items
+        if (steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; }
+        for (int it = 0; it < kRound && !done; ++it) {
             int next = INT_MIN;  // none: pop (leaf ~k is negative, ~0 == -1)
             if (node < 0) {
                 ++c_tris;
@@ -574,15 +575,11 @@ __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
                     for (int c = 3; c >= 0; --c)
                         if (hc[c]) nc = c;
                 }
-                bool overflow = false;
+                // a node pushes at most 3 children; the build keeps 3 entries per level within the stack
+                if (sp > kStackSize4 - 3) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (hc[c] && c != nc) {
-                        if (sp >= kStackSize4) overflow = true;
-                        else stack[sp++] = ref[c];
-                    }
-                }
-                if (overflow) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
+                for (int c = 0; c < 4; ++c)
+                    if (hc[c] && c != nc) stack[sp++] = ref[c];
                 if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
             }
             if (next == INT_MIN) {
