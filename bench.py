@@ -32,9 +32,9 @@ FLOPS_BRDF_ADJ = 240.0  # evaluation + adjoint in the backward pass
 FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per traced shadow ray of the any-hit tracer on the geometry workload,
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the single chunk launch of
-# the 2-view case: 1.288 GB for 39 M rays).  The ray record (32 B) is read once; nodes and
+# the 2-view case: 1.289 GB for 38.7 M rays).  The ray record (32 B) is read once; nodes and
 # triangles stay in L2.
-TRACE_DRAM_BYTES_PER_RAY = {"geometry": 33.0}
+TRACE_DRAM_BYTES_PER_RAY = {"geometry": 33.3}
 RAY_QUEUE_MAX = 1 << 27  # rays per chunk at most (the library's default queue)
 
 WORKLOADS = {
