@@ -369,6 +369,34 @@ def test_ggx_lobe_normalisation():
         assert 0.97 < val < 1.0 + 1e-3, val
 
 
+def test_ggx_white_furnace_and_closed_form_at_alpha_one():
+    """Specular lobe with F = 1 (metallic, white base colour) in a white furnace.  Its
+    directional albedo E(mu_o) = int f_s cos_i dw_i, integrated over half vectors with
+    dw_i = 4 (h.w_o) dw_h, never exceeds 1 (the lobe loses energy to Smith shadowing, it does
+    not create any).  At r = 1 (alpha = 1) the GGX distribution is the constant 1/pi and
+    G1(c) = 2c / (1 + c), so E(mu_o) = (1/pi) / (1 + mu_o) * int mu_i / (1 + mu_i) dw_i
+    = 2 (1 - ln 2) / (1 + mu_o) in closed form: a wrong normalisation of D, a wrong G1, a
+    missing 4 in the denominator or a missing cosine each break it."""
+    d, w = _hemisphere_quadrature(nt=1500, npp=128)
+    h = torch.tensor(d)
+    W = torch.tensor(w)
+    n = torch.tensor([0.0, 0.0, 1.0], dtype=torch.float64).expand_as(h)
+    one = torch.ones(h.shape[0], dtype=torch.float64)
+    for deg in (0.0, 30.0, 60.0, 80.0, 89.0):
+        t = math.radians(deg)
+        wo = torch.tensor([math.sin(t), 0.0, math.cos(t)], dtype=torch.float64).expand_as(h)
+        hv = (h * wo).sum(1)
+        wi = 2 * hv[:, None] * h - wo
+        keep = (wi[:, 2] > 0) & (hv > 0)
+        for r in (0.08, 0.2, 0.4, 0.7, 1.0):
+            f = shade.brdf_cos(n, wi, wo, torch.ones_like(h), one * r, one)[:, 0]
+            E = (f * 4 * hv * W)[keep].sum().item()
+            assert E <= 1.0 + 2e-3, (deg, r, E)
+            if r == 1.0:
+                want = 2 * (1 - math.log(2)) / (1 + math.cos(t))
+                assert abs(E - want) <= 2e-3 * want, (deg, E, want)
+
+
 # ----------------------------------------------------------------- estimators
 
 def test_furnace_diffuse_sphere_under_constant_env():
