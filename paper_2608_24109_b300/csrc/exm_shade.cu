@@ -463,9 +463,12 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
 // ------------------------------------------------------------------ persistent tracer
 // Any-hit (shadow rays -> visibility bits) or closest-hit (secondary rays -> hit ids) over
 // the chunk's ray queue.  A warp claims a pool of kPool consecutive queue entries (the same
-// few sample indices of 32 neighbouring pixels) and its lanes refill themselves from that
-// pool whenever their ray is done, so no lane idles while the longest ray of the warp
-// finishes, and the rays a warp holds stay local to one group of pixels.
+// few sample indices of 32 neighbouring pixels), so the rays a warp holds stay local to one
+// group of pixels.  Its lanes run rounds of kRound items (a 4-wide node or a triangle each)
+// and the lanes whose ray ended refill from the pool between rounds: a lane waits at most
+// the rest of a round, never for the longest ray of the warp.  Longer rounds idle more
+// lanes, shorter ones refill more often; 24 measured best.  Each ray is clipped where it
+// leaves the triangles' bounding sphere (sphere_exit).
 constexpr uint32_t kPool = 256;
 constexpr int kRound = 24;  // node visits between refills
 
