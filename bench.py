@@ -35,6 +35,10 @@ FP32_LANES_PER_SM = 128
 # the 2-view case: 1.289 GB for 38.7 M rays).  The ray record (32 B) is read once; nodes and
 # triangles stay in L2.
 TRACE_DRAM_BYTES_PER_RAY = {"geometry": 33.3}
+# The same capture: L2 sectors (lts__t_sectors.sum) were 5.7% of their peak rate over the launch,
+# and the warp schedulers issued on 62.7% of the active cycles.
+TRACE_L2_FRAC_NCU = {"geometry": 0.057}
+TRACE_ISSUE_FRAC_NCU = {"geometry": 0.627}
 RAY_QUEUE_MAX = 1 << 27  # rays per chunk at most (the library's default queue)
 
 WORKLOADS = {
@@ -344,6 +348,14 @@ def run_native(args, world, rank, local):
         chunk_pixels = max(32, min((pixels + 31) & ~31, (RAY_QUEUE_MAX // per_pixel) & ~31))
         launches_any = -(-pixels // chunk_pixels)
         traffic = TRACE_DRAM_BYTES_PER_RAY[args.workload] * work_fwd[3] / launches_any
+    # the three resources side by side for the tracer: HBM (live: measured bytes per ray x rays per
+    # step over the tracer's time), L2 and issue slots (from the capture), FP32 (the frac above)
+    fractions = None
+    if dom.startswith("trace_kernel") and traffic is not None:
+        hbm = float(peaks.get("hbm_gbs", 6400.0))
+        fractions = {"hbm": TRACE_DRAM_BYTES_PER_RAY[args.workload] * work_fwd[3] / (dom_ms * 1e-3) / (hbm * 1e9),
+                     "l2_ncu": TRACE_L2_FRAC_NCU[args.workload], "issue_slots_ncu": TRACE_ISSUE_FRAC_NCU[args.workload],
+                     "fp32": achieved / fp32_peak}
     mf, mb = statistics.mean(t_fwd), statistics.mean(t_bwd)
     line = {
         "metric": "fwd+bwd shaded samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
@@ -362,7 +374,7 @@ def run_native(args, world, rank, local):
                      "traffic_unit": "bytes per launch (ncu DRAM read + write per traced ray x rays per launch)",
                      "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
                                     f"(clock from {src} peaks)",
-                     "work_per_step": dom_work},
+                     "work_per_step": dom_work, "fractions": fractions},
         "clocks": ck,
         "gpu_launches": launches,
     }
