@@ -425,3 +425,61 @@ def test_parity_more_direct_samples_than_one_list_round():
     The strata are 44 x 25."""
     sc = ragged_tiny(26, 22, 1, n_direct=1100)
     _forward_and_backward_full(sc, "N_d 1100")
+
+
+# ----------------------------------------------------------------- small meshes and occlusion
+
+def _custom_scene(V, F, UV, eye, target, W, H, seed, **kw):
+    rng = np.random.default_rng(seed)
+    maps = scenes.material_maps(rng, 32)
+    env = scenes.env_map(rng, 32, 16, 1.0)
+    cam = scenes.look_at_camera(eye, W, H, target=target)
+    return scenes._finish("custom", np.asarray(V), np.asarray(F), np.asarray(UV), np.asarray(F), maps, maps, env,
+                          cam[None], W, H, seed=seed, **kw)
+
+
+def test_parity_single_triangle_mesh():
+    """A mesh of one triangle: the BVH is one 4-wide node with one child, its bounding sphere
+    comes from that child's box, and every shadow ray escapes."""
+    V = [[-1.0, -0.8, 0.0], [1.0, -0.8, 0.0], [0.1, 0.9, 0.0]]
+    sc = _custom_scene(V, [[0, 1, 2]], [[0.05, 0.05], [0.95, 0.1], [0.5, 0.95]], (0.3, 0.2, 2.5), (0.0, 0.0, 0.0),
+                       48, 40, seed=11, n_direct=32)
+    dec = _forward_and_backward_full(sc, "one triangle")
+    assert dec.pix.shape[0] > 300
+
+
+def _floor_and_occluder(with_occluder, **kw):
+    # floor y = 0 facing +y (x, z in [-1, 1]); occluder quad at y = 0.25 over x, z in [-0.5, 0.5]
+    # facing -y, so secondary rays from the floor meet its front face (camera rays from above see
+    # its back face, which is culled)
+    V = [[-1, 0, -1], [-1, 0, 1], [1, 0, 1], [1, 0, -1]]
+    F = [[0, 1, 2], [0, 2, 3]]
+    UV = [[0.02, 0.02], [0.02, 0.98], [0.98, 0.98], [0.98, 0.02]]
+    if with_occluder:
+        V += [[-0.5, 0.25, -0.5], [0.5, 0.25, -0.5], [0.5, 0.25, 0.5], [-0.5, 0.25, 0.5]]
+        F += [[4, 5, 6], [4, 6, 7]]
+        UV += [[0.3, 0.3], [0.7, 0.3], [0.7, 0.7], [0.3, 0.7]]
+    sc = _custom_scene(np.array(V, float), np.array(F), np.array(UV), (-1.3, 1.6, 0.9), (0.0, 0.0, 0.0), 56, 48,
+                       seed=5, **kw)
+    n = np.cross(sc.V[sc.F[:, 1]] - sc.V[sc.F[:, 0]], sc.V[sc.F[:, 2]] - sc.V[sc.F[:, 0]])
+    assert (n[:2, 1] > 0).all() and (not with_occluder or (n[2:, 1] < 0).all())
+    return sc
+
+
+def test_parity_occluder_casts_shadows_direct_and_indirect():
+    """A textured floor under a quad that faces it: many of the floor's shadow rays are occluded
+    (the any-hit tracer's hit path, which the blob workloads rarely take) and its secondary rays
+    find the quad's front face; forward and backward against the oracle."""
+    sc = _floor_and_occluder(True, n_direct=64, n_bounce=4, n_light=2)
+    dec = _forward_and_backward_full(sc, "occluder")
+    bare = _floor_and_occluder(False, n_direct=64)
+    st, keys = oracle.raster_full(bare.V, bare.F, bare.cams, bare.width, bare.height)
+    pix = oracle.covered_pixels(keys)
+    dec_bare = oracle.Decisions(bare, oracle.EnvTable(bare.env), pix, keys[pix[:, 0], pix[:, 1], pix[:, 2]])
+    on_floor = dec.tri < 2
+    seen = {tuple(p) for p in dec.pix[on_floor]}
+    bare_rows = np.array([tuple(p) in seen for p in dec_bare.pix])
+    assert bare_rows.sum() == on_floor.sum()
+    # the floor's visible direct samples drop by a tenth or more under the occluder
+    assert dec.dvis[on_floor].sum() < 0.9 * dec_bare.dvis[bare_rows].sum()
+    assert (dec.stri[on_floor] >= 2).sum() > 100
