@@ -158,7 +158,11 @@ exm_status exm_frame_visbuf(exm_frame* frame, const uint64_t** keys);
 /* Forward render (Eqs. 10-20).  maps: DEVICE [mapH, mapW, 8] texel-interleaved
  * (A rgb, R, M, N xyz) of `map_dtype`; cams: HOST array of `views` cameras; out_rgb:
  * DEVICE float32 [views, height, width, 3] (written; background 0).  The frame keeps
- * the visibility buffer for the backward pass. */
+ * the visibility buffer for the backward pass.  The frame grows its wavefront buffers on the
+ * first forward of a size and sample count and keeps them until destroyed: per frame pixel
+ * 160 bytes (the 112-byte shading record and the backward's 48-byte adjoint sums), one bit per
+ * direct and per secondary light sample, and 4 bytes per secondary ray; plus one ray queue of
+ * at most 2^27 rays x 32 bytes (4 GiB), sized down to the rays the frame can produce. */
 exm_status exm_render_forward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
                               int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
                               const exm_params* params, exm_frame* frame, float* out_rgb, void* stream);
@@ -167,7 +171,9 @@ exm_status exm_render_forward(exm_ctx* ctx, const exm_mesh* mesh, const void* ma
  * [views,height,width,3]) accumulates dL/dmaps (DEVICE float32 [mapH,mapW,8]),
  * dL/dE (DEVICE float32 [envH,envW,3]) and dL/dV (DEVICE float32 [nv,3]); any gradient
  * pointer may be NULL to skip it.  The sampling density and every discrete decision are
- * constants of the derivative. */
+ * constants of the derivative.  It reads the visibility bits, secondary hits and camera-ray
+ * records of the frame's last forward (no ray is traced again) and evaluates the material from
+ * `maps` as passed. */
 exm_status exm_render_backward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
                                int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
                                const exm_params* params, exm_frame* frame, const float* grad_rgb,
