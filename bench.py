@@ -75,6 +75,8 @@ def parse():
                     help="indirect light at half resolution, upsampled (the paper's speed variant)")
     ap.add_argument("--topology", action="store_true",
                     help="time Stage-I topology rounds on the workload's mesh (Sec. 4.1-4.3)")
+    ap.add_argument("--relight-protocol", action="store_true",
+                    help="relight frames/s under the paper's timing protocol (1600^2, N_d = 8, then one bounce)")
     ap.add_argument("--stage2", action="store_true",
                     help="time whole Stage-II iterations: render, objective, adjoint, Adam")
     return ap.parse_args()
@@ -635,6 +637,60 @@ def run_relight(args, world, rank, local):
     srv.close()
 
 
+def run_relight_protocol(args, world, rank, local):
+    """Relight frames under the paper's relighting timing protocol (Sec. 6.6): the first frame
+    is a warm-up; each timed frame includes the environment's transfer from pinned host memory,
+    its sampling distribution, light transport and shading; asset loading is not timed.  The
+    asset is the geometry blob (99,372 tris, ~50K vertices) with BF16 maps 1024^2, one view at
+    1600 x 1600, a new 512 x 256 environment per frame; N_d = 8 direct samples, then the same
+    with one bounce (N_b = 16 secondary rays at half resolution, N_s = 4)."""
+    import numpy as np
+    import torch
+
+    from paper_2608_24109_b300 import build as libbuild
+    from paper_2608_24109_b300 import scenes
+    from paper_2608_24109_b300.render import Renderer
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = scenes.config("geometry")
+    W = H = 1600
+    cams = np.stack([scenes.look_at_camera((0.0, 0.4, 3.0), W, H)])
+    maps = torch.as_tensor(sc.maps).to(torch.bfloat16).to(dev).contiguous()
+    envs = [torch.as_tensor(scenes.env_map(np.random.default_rng(40 + k), 512, 256, 1.5)).pin_memory() for k in range(4)]
+    frames = max(args.steps, 10)
+    results = {}
+    for name, kw in [("direct", dict(n_direct=8)),
+                     ("one_bounce", dict(n_direct=8, n_bounce=16, n_light=4, half_res_indirect=True))]:
+        r = Renderer(sc.V, sc.F, sc.UV, sc.Fuv, 512, 256, cams, W, H, seed=7, device=local, **kw)
+        Ed = torch.empty((256, 512, 3), dtype=torch.float32, device=dev)
+        out = torch.empty(r.image_shape(), dtype=torch.float32, device=dev)
+        times = []
+        for f in range(frames + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            Ed.copy_(envs[f % len(envs)], non_blocking=True)
+            r.forward(maps, Ed, out=out)
+            r.sync()
+            if f > 0:
+                times.append(time.perf_counter() - t0)
+        covered, _ = r.stats()
+        results[name] = {"frames_per_s": 1.0 / statistics.mean(times), "ms_per_frame": 1e3 * statistics.mean(times),
+                         "covered_pixels": int(covered)}
+        r.close()
+    line = {"metric": "relight frames/s (paper's protocol)", "value": results["direct"]["frames_per_s"],
+            "unit": "frames/s", "higher_is_better": True, "n_gpus": 1, "frames": frames, "vs_baseline": None,
+            "dtype": "bf16 maps, f32 shading", "data": "synthetic",
+            "config": {"workload": "geometry blob 99,372 tris, BF16 maps 1024^2, env 512x256 new per frame, "
+                                   "1 view 1600x1600, N_d = 8; one bounce: N_b = 16 at half resolution, N_s = 4",
+                       "timed": "env upload from pinned host memory + env distribution + render, per frame"},
+            "direct": results["direct"], "one_bounce": results["one_bounce"],
+            "context": "paper, RTX A6000, Stanford-ORB 1600^2: 40.47 frames/s direct-only, 15.09 with one bounce "
+                       "(other hardware and assets; not a ratio)"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     world, rank, local = dist_init()
@@ -643,6 +699,9 @@ def main():
             run_relight(args, world, rank, local)
     elif args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.relight_protocol:
+        if rank == 0:
+            run_relight_protocol(args, world, rank, local)
     elif args.stage2:
         run_stage2(args, world, rank, local)
     elif args.topology:
