@@ -382,7 +382,7 @@ def run_native(args, world, rank, local):
     }
     if e2e:
         line["e2e"] = e2e
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the CPU baseline is an N = 1 figure
         s, dt, threads, npx = oracle_sample(sc, args.cpu_pixels)
         line["cpu_baseline"] = {"value": s / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
                                 "sample": f"{npx} covered pixels of the workload (decisions, FP64 radiance "
