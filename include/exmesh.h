@@ -236,7 +236,8 @@ exm_status exm_relight_footprint(exm_server* server, const exm_relight_req* req,
  * EXM_ERR_ARG before anything is enqueued.  The array is shared by all calls on a device:
  * calls that overlap on the GPU race and must be serialised by the caller.  The first call
  * on a device resolves the array's address (cudaGetSymbolAddress); make it before any
- * stream capture. */
+ * stream capture.  The per-pixel buffers it reads and writes belong to `frame` and were
+ * allocated by its forward pass. */
 #define EXM_STATIC_ENV_MAX_TEXELS 262144
 exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
                                        int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
