@@ -65,7 +65,7 @@ struct exm_server {
     exm_ctx* ctx = nullptr;
     size_t budget = 0;
     size_t used = 0;
-    uint32_t ray_cap = 1u << 22;
+    uint32_t ray_cap = 1u << 25;  // rays per chunk of a slot's frame (1 GiB): fewer chunks, fewer tracer tails
     std::vector<Asset> assets;
     std::vector<Slot> slots;
     std::deque<Pending> queue;
