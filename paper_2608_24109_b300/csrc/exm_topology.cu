@@ -538,6 +538,9 @@ struct exm_topology {
     size_t tmp_cap = 0;
 };
 
+// selection rounds launched between two read-backs of the undecided count
+constexpr int kSelectBatch = 4;
+
 namespace {
 
 // named scratch slots of a topology object (grown on demand, contents not kept)
@@ -732,14 +735,18 @@ exm_status exm_topology_round(exm_topology* t, const float* V, int nv, const int
     if (!list || !adds || !pos || !incl) return exm_fail(EXM_ERR_OOM, "topology buffers");
     if (K > 0) {
         split_prep_kernel<<<grid(c, K), 256, 0, s>>>(K, sv1, V, F, A0.elen, A0.deg, A0.nb, cand);
-        for (int it = 0;; ++it) {
+        // kSelectBatch rounds between read-backs of the undecided count: the kernels skip
+        // decided candidates, so rounds after the last decision change nothing
+        for (int it = 0;; it += kSelectBatch) {
             if (it > K + 1) return exm_fail(EXM_ERR_CUDA, "topology split selection did not converge");
-            cudaMemsetAsync(owner, 0x7f, (size_t)nf * sizeof(int32_t), s);
-            split_claim_kernel<<<grid(c, K), 256, 0, s>>>(K, cand, owner);
-            split_accept_kernel<<<grid(c, K), 256, 0, s>>>(K, cand, owner, taken);
-            cudaMemsetAsync(cnt + 1, 0, 4, s);
-            split_reject_kernel<<<grid(c, K), 256, 0, s>>>(K, cand, taken, cnt + 1);
-            c->launches += 3;
+            for (int b = 0; b < kSelectBatch; ++b) {
+                cudaMemsetAsync(owner, 0x7f, (size_t)nf * sizeof(int32_t), s);
+                split_claim_kernel<<<grid(c, K), 256, 0, s>>>(K, cand, owner);
+                split_accept_kernel<<<grid(c, K), 256, 0, s>>>(K, cand, owner, taken);
+                cudaMemsetAsync(cnt + 1, 0, 4, s);
+                split_reject_kernel<<<grid(c, K), 256, 0, s>>>(K, cand, taken, cnt + 1);
+                c->launches += 3;
+            }
             uint32_t und = 0;
             st = read_u32(cnt + 1, &und, s);
             if (st != EXM_OK) return st;
@@ -854,7 +861,9 @@ exm_status exm_topology_round(exm_topology* t, const float* V, int nv, const int
         star_ranges_kernel<<<grid(c, 3 * (size_t)nf1), 256, 0, s>>>(3 * (size_t)nf1, ck1, first, last);
         // faces modified by the splits are taken from the start
         cudaMemcpyAsync(taken1, m1.touched, nf1, cudaMemcpyDeviceToDevice, s);
-        for (int it = 0;; ++it) {
+        // rounds of reject, claim, accept, kSelectBatch at a time, then a reject whose count
+        // of undecided candidates is read back (rounds after the last decision change nothing)
+        for (int it = 0;; it += kSelectBatch) {
             if (it > MC + 1) return exm_fail(EXM_ERR_CUDA, "topology merge selection did not converge");
             cudaMemsetAsync(cnt + 4, 0, 4, s);
             merge_reject_kernel<<<grid(c, MC), 256, 0, s>>>(MC, mc, first, last, star, taken1, cnt + 4);
@@ -862,10 +871,17 @@ exm_status exm_topology_round(exm_topology* t, const float* V, int nv, const int
             st = read_u32(cnt + 4, &und, s);
             if (st != EXM_OK) return st;
             if (und == 0) break;
-            cudaMemsetAsync(owner1, 0x7f, (size_t)nf1 * sizeof(int32_t), s);
-            merge_claim_kernel<<<grid(c, MC), 256, 0, s>>>(MC, mc, first, last, star, owner1);
-            merge_accept_kernel<<<grid(c, MC), 256, 0, s>>>(MC, mc, first, last, star, owner1, taken1);
-            c->launches += 3;
+            for (int b = 0; b < kSelectBatch; ++b) {
+                cudaMemsetAsync(owner1, 0x7f, (size_t)nf1 * sizeof(int32_t), s);
+                merge_claim_kernel<<<grid(c, MC), 256, 0, s>>>(MC, mc, first, last, star, owner1);
+                merge_accept_kernel<<<grid(c, MC), 256, 0, s>>>(MC, mc, first, last, star, owner1, taken1);
+                c->launches += 2;
+                if (b + 1 < kSelectBatch) {
+                    merge_reject_kernel<<<grid(c, MC), 256, 0, s>>>(MC, mc, first, last, star, taken1, cnt + 4);
+                    c->launches += 1;
+                }
+            }
+            c->launches += 1;
         }
         vmap_apply_kernel<<<grid(c, MC), 256, 0, s>>>(MC, mc, vmap, alive, cnt + 5);
         c->launches += 4;
