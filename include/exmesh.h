@@ -160,8 +160,9 @@ exm_status exm_frame_visbuf(exm_frame* frame, const uint64_t** keys);
  * DEVICE float32 [views, height, width, 3] (written; background 0).  The frame keeps
  * the visibility buffer for the backward pass.  The frame grows its wavefront buffers on the
  * first forward of a size and sample count and keeps them until destroyed: per frame pixel
- * 160 bytes (the 112-byte shading record and the backward's 48-byte adjoint sums), one bit per
- * direct and per secondary light sample, and 4 bytes per secondary ray; plus one ray queue of
+ * 160 bytes (the 112-byte shading record and the backward's 48-byte adjoint sums), 4 bytes
+ * per direct sample (the texel it picked), one bit per direct and per secondary light sample,
+ * and 4 bytes per secondary ray; plus one ray queue of
  * at most 2^27 rays x 32 bytes (4 GiB), sized down to the rays the frame can produce. */
 exm_status exm_render_forward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
                               int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,

@@ -78,10 +78,10 @@ struct exm_server {
 // Device bytes a request needs while it runs: the frame (visibility buffer, pixel list,
 // snapped vertices, visibility bits, secondary hits, ray queue) and the environment tables.
 // Device bytes of one frame: visibility keys and pixel list, pixel records (the 112-byte
-// shading record and the 48-byte adjoint sums), snapped vertices, visibility bits, secondary
-// hit ids, the ray queue of a chunk, cameras, counters.
+// shading record and the 48-byte adjoint sums), the texel of each direct sample, snapped
+// vertices, visibility bits, secondary hit ids, the ray queue of a chunk, cameras, counters.
 static size_t frame_bytes(size_t P, size_t views, size_t nv, int wd, int ws, int nb, size_t ray_cap) {
-    return P * (8 + 4 + 16 * kPrec + 48) + views * nv * 12 + P * (size_t)(wd + ws) * 4 + P * (size_t)nb * 4 + ray_cap * 32 +
+    return P * (8 + 4 + 16 * kPrec + 48) + P * (size_t)wd * 32 * 4 + views * nv * 12 + P * (size_t)(wd + ws) * 4 + P * (size_t)nb * 4 + ray_cap * 32 +
            views * 80 + 64;
 }
 

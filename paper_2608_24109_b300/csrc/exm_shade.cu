@@ -6,19 +6,23 @@
 //   gen_direct     -> one shadow ray per (pixel, k) above the geometric horizon    (Eq. 17)
 //   gen_seclight   -> one shadow ray per (valid hit, s) above its horizon          (Eq. 18)
 //   trace<any>     -> any-hit visibility of every queued shadow ray, as bits
-// then one shade kernel, a warp per pixel, enumerates the pixel's unoccluded samples from
-// the bits (so every lane evaluates a live sample), evaluates f_r = f_d + f_s (Eqs. 13-16),
-// the direct estimator (Eq. 17), L_sec at each valid hit (Eq. 18), the indirect estimator
-// (Eq. 19) and the composite (Eq. 20).
+// then pixel_surface (a thread per pixel: material and n_s into the pixel record) and one
+// shade kernel, a warp per pixel, which enumerates the pixel's unoccluded samples from the
+// bits (so every lane evaluates a live sample), evaluates f_r = f_d + f_s (Eqs. 13-16), the
+// direct estimator (Eq. 17), L_sec at each valid hit (Eq. 18), the indirect estimator
+// (Eq. 19) and the composite (Eq. 20).  gen_direct records the texel each queued direct
+// sample picked, so the shade kernels re-derive a sample's direction from its stream and
+// that texel without repeating the search.
 //
 // The backward pass is the same warp-per-pixel kernel with the adjoint: it re-derives each
-// sample from its counter-based stream, reads the saved visibility bits and hit ids (no ray
-// is traced again), and scatters dL/d(map texels) (4 bilinear taps x 8 channels), dL/dE
-// (one padded float4 per texel) and dL/dV (barycentrics, position, view direction,
-// interpolated normals and tangents, UV; the frame adjoint finishes it).
+// sample, reads the saved visibility bits and hit ids (no ray is traced again), scatters
+// dL/dE (one padded float4 per texel) and sums the sample adjoints of n_s, w_o, a, r and m per
+// pixel; shade_epilogue (a thread per pixel) carries them to dL/d(map texels) (4 bilinear
+// taps x 8 channels) and dL/dV (barycentrics, position, view direction, interpolated normals
+// and tangents, UV; the frame adjoint finishes it).
 //
-// The trace kernel is persistent: each lane refills itself from the ray queue whenever its
-// ray finishes, so lanes do not idle while the longest ray of the warp completes.
+// The trace kernel is persistent: a warp claims pools of queued rays and its lanes refill
+// from the pool between rounds of kRound items.
 #include <vector>
 
 #include "exm_device.cuh"
@@ -64,6 +68,7 @@ struct ShadeArgs {
     int32_t* hits;       // [P * Nb] closest front-facing hit of each secondary ray, -1 if none
     float4* prec;        // [P * kPrec] per-pixel shading record
     float* pacc;         // [P * 12] backward: per-pixel sums of the sample adjoints
+    uint32_t* tsel;      // [P * Nd] texel picked by each queued direct sample (gen_direct)
     float4* rays;        // queue: [ray_cap * 2]
     uint32_t ray_cap;
     uint32_t* ctr;       // per chunk: [0] queued, [1] fetch cursor (x2: closest, any)
@@ -323,10 +328,12 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
             light_sample2(env, ha, (uint32_t)k, hb, (uint32_t)k2, A.nxd, A.nyd, &sa, &sb);
             if (sdot(ngs, sa.dir) > 0.0f) {
                 want |= 1u << u;
+                A.tsel[(size_t)i * A.Nd + k] = sa.texel;
                 sd[u][0][lane] = sa.dir.x; sd[u][1][lane] = sa.dir.y; sd[u][2][lane] = sa.dir.z;
             }
             if (two && sdot(ngs, sb.dir) > 0.0f) {
                 want |= 2u << u;
+                A.tsel[(size_t)i * A.Nd + k2] = sb.texel;
                 sd[u + 1][0][lane] = sb.dir.x; sd[u + 1][1][lane] = sb.dir.y; sd[u + 1][2][lane] = sb.dir.z;
             }
         }
@@ -802,6 +809,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
         float gr = 0.f, gm = 0.f;
         // ---- direct light (Eq. 17): the pixel's unoccluded samples, one per lane
         const float invNd = 1.0f / (float)A.Nd;
+        const float invW = 1.0f / (float)env.W;
         const uint32_t* vb = A.visbits + (size_t)i * A.wd;
         for (int wbase = 0; wbase < A.wd; wbase += 32) {
             const int tot = enumerate_bits(vb, wbase, A.wd, list);
@@ -810,7 +818,15 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                 if (e < tot) {
                     const int k = wbase * 32 + list[e];
                     const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
-                    const LightSample ls = light_sample(env, h, (uint32_t)k, A.nxd, A.nyd);
+                    // the texel gen_direct's search picked for this sample (a live sample was
+                    // queued, so it was recorded); t < 2^22 is exact in FP32, and one step
+                    // corrects the rounded quotient
+                    const uint32_t t = A.tsel[(size_t)i * A.Nd + k];
+                    uint32_t row = (uint32_t)((float)t * invW);
+                    if (row * (uint32_t)env.W > t) --row;
+                    else if ((row + 1u) * (uint32_t)env.W <= t) ++row;
+                    LightSample ls;
+                    finish_sample(env, h, row, t - row * (uint32_t)env.W, &ls);
                     const float3 wi = normalize(tof(ls.dir));
                     const float w = ls.inv_pdf * invNd;
                     ++c_brdf;
@@ -1105,6 +1121,7 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     const size_t P = (size_t)f->views * f->W * f->H;
     A.prec = f->prec;
     A.pacc = f->pacc;
+    A.tsel = f->tsel;
     A.visbits = f->bits;
     A.secbits = f->bits ? f->bits + P * A.wd : nullptr;
     A.hits = f->hits;
@@ -1212,6 +1229,7 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     const uint32_t Pc = (uint32_t)max((size_t)32, min(P32, (size_t)((cap_max / per_pixel) & ~31u)));
     const uint32_t ray_cap = (uint32_t)min((size_t)cap_max, (size_t)Pc * per_pixel);
     if (!ensure(&f->prec, &f->prec_cap, P * (size_t)kPrec) || !ensure(&f->pacc, &f->pacc_cap, P * (size_t)12) ||
+        (p->n_direct > 0 && !ensure(&f->tsel, &f->tsel_cap, P * (size_t)p->n_direct)) ||
         !ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)ray_cap * 2) ||
         (indirect && !ensure(&f->hits, &f->hits_cap, P * (size_t)p->n_bounce)))
         return exm_fail(EXM_ERR_OOM, "wavefront buffers");
