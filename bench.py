@@ -6,7 +6,11 @@ build, visibility-buffer raster, direct (+ indirect) shading, L1 loss against a 
 render, and the adjoint into the maps, the environment and the vertex positions.
 Metric: shaded samples per second (fwd+bwd).  One JSON line on rank 0.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload geometry|tiny|indirect]
+The default workload is the largest single-GPU one, the precision blob (2M triangles, 8 views
+of 1024^2, 64 direct + 4 x (1 + 4) indirect samples per pixel): its headline form stores the
+maps and the environment in FP32, and the BF16-map / FP16-environment form is timed beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload precision|geometry|indirect|tiny]
   python bench.py --impl reference ...   # the CPU oracle on a bounded sample (host cores)
 """
 from __future__ import annotations
@@ -25,21 +29,27 @@ sys.path.insert(0, ROOT)
 
 # algorithmic FP32 operation counts (per unit of work) used for the ALU roofline; an FMA counts
 # 2, as in the peak, and a min, max or comparison 1
-FLOPS_NODE = 72.0       # one 4-wide node: per child 6 FMA, a 3-way max and a max with 0, a 3-way min, one compare
+FLOPS_NODE_MODEL = 100.0  # the scope table's op model: 25 per child box slab test of a 4-wide node
+FLOPS_TRI_MODEL = 30.0    # and 30 per watertight triangle test
+FLOPS_NODE = 72.0       # this build's count: per child 6 FMA, a 3-way max and a max with 0, a 3-way min, one compare
 FLOPS_TRI = 50.0        # one watertight test: 40 adds and multiplies (no FMA: decision arithmetic), ~10 compares
 FLOPS_BRDF = 80.0       # one Lambert + GGX evaluation with its cosine and estimator weight
 FLOPS_BRDF_ADJ = 240.0  # evaluation + adjoint in the backward pass
 FP32_LANES_PER_SM = 128
-# DRAM bytes (read + write) per traced shadow ray of the any-hit tracer on the geometry workload,
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum of the single chunk launch of
-# the 2-view case: 1.289 GB for 38.7 M rays).  The ray record (32 B) is read once; nodes and
-# triangles stay in L2.
-TRACE_DRAM_BYTES_PER_RAY = {"geometry": 33.3}
-# The same capture: L2 sectors (lts__t_sectors.sum) were 5.7% of their peak rate over the launch,
-# and the warp schedulers issued on 62.7% of the active cycles.
-TRACE_L2_FRAC_NCU = {"geometry": 0.057}
-TRACE_ISSUE_FRAC_NCU = {"geometry": 0.627}
+# algorithmic bytes of the tracer: a 4-wide node record, a triangle record, a queued ray
+NODE_BYTES = 128.0
+TRI_BYTES = 48.0
+RAY_BYTES = 32.0
+# The tracer's memory traffic from one ncu capture per workload (single any-hit launch of a
+# one- or two-view case of the same scene; profiles/trace_kernel_<workload>.md): DRAM bytes
+# (read + write) per traced ray, L2 sector throughput and issue-slot use as fractions of peak.
+TRACE_NCU = {
+    "geometry": {"dram_bytes_per_ray": 33.3, "l2_frac": 0.057, "issue_frac": 0.627,
+                 "source": "ncu, any-hit launch of the 2-view geometry case"},
+}
 RAY_QUEUE_MAX = 1 << 27  # rays per chunk at most (the library's default queue)
+# covered pixels of the CPU-baseline sample per workload: about 10-30 s of oracle work on 16 cores
+CPU_PIXELS = {"tiny": 2048, "geometry": 1536, "indirect": 384, "precision": 192}
 
 WORKLOADS = {
     "tiny": "icosphere 1280 tris, maps 256^2 FP32, env 64x32, 4 views 256^2, 64 env samples/px, fwd+bwd",
@@ -58,8 +68,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="geometry", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-pixels", type=int, default=1536, help="pixels of the CPU-baseline sample")
+    ap.add_argument("--workload", default="precision", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-pixels", type=int, default=0,
+                    help="pixels of the CPU-baseline sample (0: the workload's default)")
+    ap.add_argument("--single-form", action="store_true",
+                    help="precision workload: time only the --maps/--env-dtype storage form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--views", type=int, default=0, help="override the workload's view count (profiling cases)")
@@ -79,7 +92,10 @@ def parse():
                     help="relight frames/s under the paper's timing protocol (1600^2, N_d = 8, then one bounce)")
     ap.add_argument("--stage2", action="store_true",
                     help="time whole Stage-II iterations: render, objective, adjoint, Adam")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if not args.cpu_pixels:
+        args.cpu_pixels = CPU_PIXELS[args.workload]
+    return args
 
 
 class Clocks:
@@ -216,37 +232,19 @@ def run_reference(args, world, rank):
 
 # --------------------------------------------------------------------------- native
 
-def run_native(args, world, rank, local):
-    import numpy as np
+def timed_steps(args, r, N, M, E, target, stream, flush, world):
+    """W untimed warm-up steps, one instrumented pass (work counters), then K timed steps of the
+    whole path with CUDA events on the launching stream.  Returns the per-step figures."""
     import torch
 
-    from paper_2608_24109_b300 import build as libbuild
-    from paper_2608_24109_b300 import native as N
-    from paper_2608_24109_b300 import scenes
-    from paper_2608_24109_b300.render import Renderer
-
-    libbuild.build()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    sc = scenes.config(args.workload, **({"views": args.views} if args.views else {}))
-    sc.half_res_indirect = args.half_res_indirect
-    r = Renderer.from_scene(sc, device=local)
-    mdt = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[args.maps]
-    edt = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}[args.env_dtype]
-    M = torch.as_tensor(sc.maps).to(mdt).to(dev)
-    Mt = torch.as_tensor(sc.maps_target).to(mdt).to(dev)
-    E = torch.as_tensor(sc.env).to(edt).to(dev)
-    target = r.forward(Mt, E).clone()
     img = torch.empty_like(target)
     grad = torch.empty_like(target)
-    loss = torch.zeros(1, device=dev)
-    gm = torch.zeros(M.shape, dtype=torch.float32, device=dev)
-    gE = torch.zeros(E.shape, dtype=torch.float32, device=dev)
-    gV = torch.zeros((sc.V.shape[0], 3), device=dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    loss = torch.zeros(1, device=M.device)
+    gm = torch.zeros(M.shape, dtype=torch.float32, device=M.device)
+    gE = torch.zeros(E.shape, dtype=torch.float32, device=M.device)
+    gV = torch.zeros((r.V.shape[0], 3), device=M.device)
     base_flags = r.params.flags
     r.params.flags = base_flags | N.FLAG_ZERO_GRADS
-    stream = torch.cuda.current_stream()
 
     def step(ev=None):
         r.prepare_env(E)
@@ -272,14 +270,12 @@ def run_native(args, world, rank, local):
     r.backward(M, grad, gm, gE, gV)
     r.sync()
     work_bwd = N.exm_frame_work(r.frame)
-    r.params.flags = base_flags | N.FLAG_ZERO_GRADS
-
-    clocks = Clocks(local)
     barrier(world)
     torch.cuda.synchronize()
     N.exm_frame_kernel_ms(r.frame)  # drop timers of earlier passes
     launches0 = N.exm_launch_count(r.ctx)
     r.params.flags = base_flags | N.FLAG_ZERO_GRADS | N.FLAG_TIME_KERNELS
+    clocks = Clocks(torch.cuda.current_device())
     clocks.start()
     t_step, t_fwd, t_bwd = [], [], []
     for _ in range(args.steps):
@@ -302,14 +298,16 @@ def run_native(args, world, rank, local):
     r.sync()
     barrier(world)
     ms = dist_max(statistics.mean(t_step), world)
-    value = samples * world / (ms * 1e-3)
 
-    # end to end through the public API: host inputs in, loss out, every step
+    # end to end through the public API: the step's inputs (maps, environment) copied in from
+    # pinned host memory and its results (loss and the gradients into maps, environment and
+    # vertices) copied back, every step
     e2e = None
     if not args.no_e2e:
         Mh = M.cpu().pin_memory()
         Eh = E.cpu().pin_memory()
-        lh = torch.zeros(1).pin_memory()
+        outs = [loss, gm, gE, gV]
+        hosts = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in outs]
         te = []
         for k in range(args.warmup + args.steps):
             flush.zero_()
@@ -318,7 +316,8 @@ def run_native(args, world, rank, local):
             M.copy_(Mh, non_blocking=True)
             E.copy_(Eh, non_blocking=True)
             step()
-            lh.copy_(loss, non_blocking=True)
+            for h, t in zip(hosts, outs):
+                h.copy_(t, non_blocking=True)
             torch.cuda.synchronize()
             if k >= args.warmup:
                 te.append(time.perf_counter() - t0)
@@ -326,70 +325,210 @@ def run_native(args, world, rank, local):
         ems = dist_max(statistics.mean(te), world)
         e2e = {"value": samples * world / ems, "unit": "samples/s",
                "h2d_bytes_per_step": Mh.numel() * Mh.element_size() + Eh.numel() * Eh.element_size(),
-               "d2h_bytes_per_step": lh.numel() * lh.element_size()}
+               "d2h_bytes_per_step": sum(h.numel() * h.element_size() for h in hosts),
+               "ms_per_step": 1e3 * ems}
+    r.params.flags = base_flags
+    return {"ms": ms, "covered": covered, "samples": samples, "work_fwd": work_fwd, "work_bwd": work_bwd,
+            "kms": kms, "clocks": ck, "launches": launches, "ms_forward": statistics.mean(t_fwd),
+            "ms_backward": statistics.mean(t_bwd), "e2e": e2e, "value": samples * world / (ms * 1e-3)}
+
+
+def error_table_sample(args, sc, r, M, E, mdt_name):
+    """Per-output error of the GPU path against the FP64 oracle on the CPU-baseline sample:
+    the oracle's decisions, radiance and adjoint on `cpu_pixels` covered pixels (the 256^2 centre
+    crop of view 0 for the precision workload), the GPU's full-frame forward and its backward of
+    a loss masked to those pixels.  Returns (oracle timing, error table)."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from oracle import shade
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    n = args.cpu_pixels
+    if args.workload == "precision":
+        c0 = (sc.width - 256) // 2
+        cand = np.stack([np.zeros(8 * n, int), rng.integers(c0, c0 + 256, 8 * n),
+                         rng.integers(c0, c0 + 256, 8 * n)], 1).astype(np.int32)
+    else:
+        cand = np.stack([rng.integers(0, sc.views, 8 * n), rng.integers(0, sc.height, 8 * n),
+                         rng.integers(0, sc.width, 8 * n)], 1).astype(np.int32)
+    cand = np.unique(cand, axis=0)
+    rng.shuffle(cand)
+    st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, cand)
+    cov = (keys & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)
+    pix, keys = cand[cov][:n], keys[cov][:n]
+    import dataclasses
+    sco = dataclasses.replace(sc, env=E.float().cpu().numpy())  # the environment as stored
+    tab = oracle.EnvTable(sco.env)
+    dec = oracle.Decisions(sco, tab, pix, keys)
+    V, _, Eo = shade.scene_tensors(sco)
+    Mo = M.cpu().to(torch.float64)
+    I = shade.render_image(sco, tab, dec, V, Mo, Eo)
+    gs = rng.normal(size=(pix.shape[0], 3))
+    oV, oM, oE = shade.backward(sco, tab, dec, V, Mo, Eo, gs)
+    dt = time.perf_counter() - t0
+    nb = max(sc.n_bounce, 0)
+    valid = int((dec.stri >= 0).sum()) if nb else 0
+    samples = pix.shape[0] * (sc.n_direct + nb) + valid * sc.n_light
+    threads = torch.get_num_threads()
+    # the GPU on the same pixels
+    img = r.forward(M, E)
+    grad = torch.zeros_like(img)
+    idx = tuple(torch.as_tensor(pix[:, k]).long() for k in range(3))
+    grad[idx] = torch.as_tensor(gs, dtype=torch.float32, device=img.device)
+    gm = torch.zeros(M.shape, dtype=torch.float32, device=M.device)
+    gE = torch.zeros(E.shape, dtype=torch.float32, device=M.device)
+    gV = torch.zeros((sc.V.shape[0], 3), device=M.device)
+    r.backward(M, grad, gm, gE, gV)
+    r.sync()
+
+    def err(g, o):
+        g = np.asarray(g, np.float64).ravel()
+        o = np.asarray(o, np.float64).ravel()
+        return {"max_rel": float(np.abs(g - o).max() / max(np.abs(o).max(), 1e-30)),
+                "l2_rel": float(np.linalg.norm(g - o) / max(np.linalg.norm(o), 1e-30))}
+
+    gmc = gm.cpu()
+    nz = (gmc != 0).any(-1) | (oM != 0).any(-1)
+    table = {"maps": mdt_name, "pixels": int(pix.shape[0]),
+             "radiance": err(img[idx].cpu().numpy(), I.numpy()), "dL/dmaps": err(gmc[nz].numpy(), oM[nz].numpy()),
+             "dL/dE": err(gE.cpu().numpy(), oE.numpy()), "dL/dV": err(gV.cpu().numpy(), oV.numpy())}
+    return (samples, dt, threads, int(pix.shape[0])), table
+
+
+def run_native(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_2608_24109_b300 import build as libbuild
+    from paper_2608_24109_b300 import native as N
+    from paper_2608_24109_b300 import scenes
+    from paper_2608_24109_b300.render import Renderer
+
+    libbuild.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sc = scenes.config(args.workload, **({"views": args.views} if args.views else {}))
+    sc.half_res_indirect = args.half_res_indirect
+    r = Renderer.from_scene(sc, device=local)
+    dts = {"fp32": torch.float32, "bf16": torch.bfloat16, "fp16": torch.float16}
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    # the headline form, then (precision workload) the low-precision storage form beside it
+    forms = [(args.maps, args.env_dtype)]
+    if args.workload == "precision" and not args.single_form:
+        forms.append(("bf16", "fp16") if args.maps == "fp32" else ("fp32", "fp32"))
+    res = {}
+    for mname, ename in forms:
+        M = torch.as_tensor(sc.maps).to(dts[mname]).to(dev).contiguous()
+        E = torch.as_tensor(sc.env).to(dts[ename]).to(dev).contiguous()
+        target = r.forward(torch.as_tensor(sc.maps_target).to(dts[mname]).to(dev).contiguous(), E).clone()
+        res[(mname, ename)] = timed_steps(args, r, N, M, E, target, stream, flush, world)
+        res[(mname, ename)]["tensors"] = (M, E)
+        del target
+    head = res[forms[0]]
+    ms, samples, covered = head["ms"], head["samples"], head["covered"]
+    value = head["value"]
+    work_fwd, work_bwd, kms = head["work_fwd"], head["work_bwd"], head["kms"]
 
     peaks, src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2032.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    # per-step algorithmic work of each kernel kind, from the instrumented pass
+    trace_ms = kms[0] + kms[1]
+    # the tracer's FP32 work by the op model of the scope table (25 flops per child box test of a
+    # 4-wide node, 30 per watertight triangle test) and by this build's own count
+    flops_model = work_fwd[0] * FLOPS_NODE_MODEL + work_fwd[1] * FLOPS_TRI_MODEL
+    flops_own = work_fwd[0] * FLOPS_NODE + work_fwd[1] * FLOPS_TRI
     kinds = {
-        "trace_kernel (any-hit + closest-hit)": (kms[0] + kms[1], work_fwd[0] * FLOPS_NODE + work_fwd[1] * FLOPS_TRI,
-                                                 {"nodes": work_fwd[0], "tri_tests": work_fwd[1], "rays": work_fwd[3]}),
-        "shade_kernel<forward>": (kms[2], work_fwd[2] * FLOPS_BRDF, {"brdf": work_fwd[2]}),
-        "shade_kernel<backward>": (kms[3], work_bwd[2] * FLOPS_BRDF_ADJ, {"brdf": work_bwd[2]}),
+        "trace_kernel (any-hit + closest-hit)": (trace_ms, flops_model),
+        "shade_kernel<forward>": (kms[2], work_fwd[2] * FLOPS_BRDF),
+        "shade_kernel<backward>": (kms[3], work_bwd[2] * FLOPS_BRDF_ADJ),
     }
     dom = max(kinds, key=lambda k: kinds[k][0])
-    dom_ms, dom_flops, dom_work = kinds[dom]
+    dom_ms, dom_flops = kinds[dom]
     achieved = dom_flops / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
-    # DRAM traffic of one any-hit launch (the ray queue chunks of the forward pass)
-    traffic = None
-    if dom.startswith("trace_kernel") and args.workload in TRACE_DRAM_BYTES_PER_RAY and sc.n_bounce == 0:
-        per_pixel = ((sc.n_direct + 31) // 32) * 32
-        pixels = sc.views * sc.width * sc.height
-        chunk_pixels = max(32, min((pixels + 31) & ~31, (RAY_QUEUE_MAX // per_pixel) & ~31))
-        launches_any = -(-pixels // chunk_pixels)
-        traffic = TRACE_DRAM_BYTES_PER_RAY[args.workload] * work_fwd[3] / launches_any
-    # the three resources side by side for the tracer: HBM (live: measured bytes per ray x rays per
-    # step over the tracer's time), L2 and issue slots (from the capture), FP32 (the frac above)
-    fractions = None
-    if dom.startswith("trace_kernel") and traffic is not None:
-        hbm = float(peaks.get("hbm_gbs", 6400.0))
-        fractions = {"hbm": TRACE_DRAM_BYTES_PER_RAY[args.workload] * work_fwd[3] / (dom_ms * 1e-3) / (hbm * 1e9),
-                     "l2_ncu": TRACE_L2_FRAC_NCU[args.workload], "issue_slots_ncu": TRACE_ISSUE_FRAC_NCU[args.workload],
-                     "fp32": achieved / fp32_peak}
-    mf, mb = statistics.mean(t_fwd), statistics.mean(t_bwd)
+    # the tracer's memory side: algorithmic bytes (node and triangle records fetched, the ray queue
+    # read), DRAM and L2 traffic per traced ray from the ncu capture of this workload's tracer
+    rays = work_fwd[3]
+    algo_bytes = work_fwd[0] * NODE_BYTES + work_fwd[1] * TRI_BYTES + rays * RAY_BYTES
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    ncu = TRACE_NCU.get(args.workload)
+    traffic = fractions = None
+    if ncu is not None and not args.views and not args.half_res_indirect:
+        fractions = {"hbm_measured": ncu["dram_bytes_per_ray"] * rays / (trace_ms * 1e-3) / (hbm * 1e9),
+                     "l2_ncu": ncu["l2_frac"], "issue_slots_ncu": ncu["issue_frac"],
+                     "fp32_scope_model": flops_model / (trace_ms * 1e-3) / 1e12 / fp32_peak,
+                     "fp32_own_model": flops_own / (trace_ms * 1e-3) / 1e12 / fp32_peak,
+                     "algorithmic_bytes_gbs": algo_bytes / (trace_ms * 1e-3) / 1e9,
+                     "source": ncu["source"]}
+        if dom.startswith("trace_kernel"):
+            traffic = ncu["dram_bytes_per_ray"] * rays / trace_launches(sc, args)
+    config = {"workload": args.workload + ": " + WORKLOADS[args.workload],
+              "map_storage": forms[0][0], "env_storage": forms[0][1], "covered_pixels": covered,
+              "shaded_samples_per_step": samples,
+              "indirect_resolution": "half, upsampled" if args.half_res_indirect else "full",
+              "l2": "flushed between steps (256 MiB write outside the timed region)",
+              "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+              "ms_forward": head["ms_forward"], "ms_backward": head["ms_backward"],
+              "kernel_ms_per_step": {"trace_any": kms[0], "trace_closest": kms[1], "shade_forward": kms[2],
+                                     "shade_backward": kms[3]},
+              "work_per_step": {"nodes": work_fwd[0], "tri_tests": work_fwd[1], "rays": work_fwd[3],
+                                "brdf_fwd": work_fwd[2], "brdf_bwd": work_bwd[2]}}
+    for key, rr in res.items():
+        if key == forms[0]:
+            continue
+        config["other_storage_form"] = {
+            "map_storage": key[0], "env_storage": key[1], "value": rr["value"], "ms_per_step": rr["ms"],
+            "ratio_to_headline": rr["value"] / value,
+            "kernel_ms_per_step": {"trace_any": rr["kms"][0], "trace_closest": rr["kms"][1],
+                                   "shade_forward": rr["kms"][2], "shade_backward": rr["kms"][3]},
+            "e2e": rr["e2e"], "clocks": rr["clocks"]}
     line = {
         "metric": "fwd+bwd shaded samples/s", "value": value, "unit": "samples/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload + ": " + WORKLOADS[args.workload],
-                   "map_storage": args.maps, "env_storage": args.env_dtype, "covered_pixels": covered, "shaded_samples_per_step": samples,
-                   "indirect_resolution": "half, upsampled" if args.half_res_indirect else "full",
-                   "l2": "flushed between steps (256 MiB write outside the timed region)",
-                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "ms_forward": mf, "ms_backward": mb,
-                   "kernel_ms_per_step": {"trace_any": kms[0], "trace_closest": kms[1], "shade_forward": kms[2],
-                                          "shade_backward": kms[3]}},
+        "config": config,
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": traffic,
-                     "traffic_unit": "bytes per launch (ncu DRAM read + write per traced ray x rays per launch)",
+                     "traffic_unit": "bytes per any-hit launch (ncu DRAM read + write per traced ray x rays per launch)",
                      "peak_source": f"FP32 FMA: {n_sm} SMs x {FP32_LANES_PER_SM} lanes x 2 x {sm_max:.0f} MHz "
                                     f"(clock from {src} peaks)",
-                     "work_per_step": dom_work, "fractions": fractions},
-        "clocks": ck,
-        "gpu_launches": launches,
+                     "op_model": f"{FLOPS_NODE_MODEL:.0f} flops per 4-wide node visit, {FLOPS_TRI_MODEL:.0f} per "
+                                 "triangle test (scope table); own count "
+                                 f"{FLOPS_NODE:.0f} / {FLOPS_TRI:.0f}",
+                     "fractions": fractions},
+        "clocks": head["clocks"],
+        "gpu_launches": head["launches"],
     }
-    if e2e:
-        line["e2e"] = e2e
+    if head["e2e"]:
+        line["e2e"] = head["e2e"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the CPU baseline is an N = 1 figure
-        s, dt, threads, npx = oracle_sample(sc, args.cpu_pixels)
-        line["cpu_baseline"] = {"value": s / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{npx} covered pixels of the workload (decisions, FP64 radiance "
-                                          f"and adjoint), {dt:.1f} s"}
+        tables = []
+        for key in forms:
+            M, E = res[key]["tensors"]
+            (s, dt, threads, npx), table = error_table_sample(args, sc, r, M, E, key[0])
+            tables.append(table)
+            if key == forms[0]:
+                line["cpu_baseline"] = {"value": s / dt, "unit": "samples/s", "cores": threads, "kind": "oracle",
+                                        "sample": f"{npx} covered pixels of the workload"
+                                                  f"{' (256^2 centre crop of view 0)' if args.workload == 'precision' else ''}: "
+                                                  f"decisions, FP64 radiance and adjoint, {dt:.1f} s"}
+        line["error_vs_oracle"] = tables
     if rank == 0:
         print(json.dumps(line), flush=True)
     r.close()
+
+
+def trace_launches(sc, args):
+    """Any-hit tracer launches per forward pass: one per ray-queue chunk."""
+    per_pixel = ((sc.n_direct + 31) // 32) * 32
+    if sc.n_bounce > 0:
+        per_pixel += ((sc.n_bounce * sc.n_light + 31) // 32) * 32
+    pixels = sc.views * sc.width * sc.height
+    chunk = max(32, min((pixels + 31) & ~31, (RAY_QUEUE_MAX // per_pixel) & ~31))
+    return -(-pixels // chunk)
 
 
 def run_stage2(args, world, rank, local):

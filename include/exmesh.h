@@ -43,6 +43,8 @@ typedef int exm_status;
 #define EXM_ERR_TRAVERSAL_LIMIT (-5) /* a BVH traversal exceeded its step cap (corrupt BVH) */
 #define EXM_ERR_TIMEOUT (-6)         /* a bounded device wait ran out */
 #define EXM_ERR_BUSY (-7)            /* admission refused: not enough budget or slots */
+#define EXM_ERR_QUEUE_OVERFLOW (-8)  /* a ray-queue chunk overflowed (exm_frame_set_limits' ray_cap below one
+                                        chunk's rays); the rays beyond it were not traced */
 
 typedef enum { EXM_F32 = 0, EXM_BF16 = 1, EXM_F16 = 2 } exm_dtype;
 
@@ -65,6 +67,14 @@ typedef enum { EXM_F32 = 0, EXM_BF16 = 1, EXM_F16 = 2 } exm_dtype;
                                      and the indirect term only; each covered pixel adds its bilinear
                                      interpolation at ((x + 1/2)/2 - 1/2, (y + 1/2)/2 - 1/2), taps
                                      clamped to the image.  Not offered by exm_render_backward_noalloc */
+#define EXM_FLAG_RECOMPUTE 128u /* keep the per-sample state (recorded texels, visibility bits, secondary
+                                     hit ids) one chunk of pixels at a time instead of for the whole frame:
+                                     the forward pass shades each chunk right after tracing it, and the
+                                     backward pass generates and traces each chunk's rays again before its
+                                     adjoint (the same decisions: the sample streams are counter-based and
+                                     the traversal deterministic).  A frame also switches to it by itself
+                                     when the whole-frame state would exceed its budget
+                                     (exm_frame_set_limits) */
 
 typedef struct exm_ctx exm_ctx;
 typedef struct exm_mesh exm_mesh;
@@ -141,6 +151,15 @@ exm_status exm_env_total(exm_env* env, uint64_t* Q);
  * empty), covered-pixel list, counters, device copy of the cameras. */
 exm_status exm_frame_create(exm_ctx* ctx, int views, int width, int height, exm_frame** out);
 void exm_frame_destroy(exm_frame* frame);
+/* Memory limits of a frame's wavefront state.  ray_cap: queued rays per chunk at most (0: the
+ * default of 2^27 = 4 GiB of 32-byte rays; at most 2^27); a chunk is the pixels whose worst-case
+ * ray count fits it, at least 32 pixels, so a cap below 32 pixels' rays overflows
+ * (EXM_ERR_QUEUE_OVERFLOW from exm_sync).  saved_budget_bytes: bytes of per-sample state (4 per
+ * direct sample, 4 per visibility word, 4 per secondary ray, per frame pixel) the frame keeps for
+ * the whole frame (0: the default of 16 GiB); above it the frame works as with
+ * EXM_FLAG_RECOMPUTE, with chunks whose state fits the budget.  Takes effect at the next forward
+ * pass; a backward pass follows the split of its forward pass. */
+exm_status exm_frame_set_limits(exm_frame* frame, uint32_t ray_cap, uint64_t saved_budget_bytes);
 /* Covered pixels and shaded samples of the last forward (synchronous). */
 exm_status exm_frame_stats(exm_frame* frame, uint64_t* covered, uint64_t* samples);
 /* Work counters of the last pass run with EXM_FLAG_COUNT_WORK (synchronous): counts[0] BVH
@@ -155,15 +174,29 @@ exm_status exm_launch_count(exm_ctx* ctx, uint64_t* launches);
 /* DEVICE pointer to the visibility buffer [views, height, width] of u64 keys. */
 exm_status exm_frame_visbuf(exm_frame* frame, const uint64_t** keys);
 
+/* Read-only DEVICE views of the per-sample decisions of the frame's last forward pass (for
+ * inspection and tests; valid until the frame's next pass).  pixels: the covered-pixel list in
+ * shading order (view*H*W + py*W + px; exm_frame_stats gives its length n).  visbits: row i
+ * (covered pixel i) of [rows, dims[0]] u32 words holds the direct samples, bit k of word k/32
+ * set iff sample k's direction lies above the geometric horizon and its shadow ray escapes
+ * (Eq. 17's Vis); then, from visbits + rows*dims[0], [rows, dims[1]] words hold the light samples
+ * of the secondary hits, bit j*N_s + s for light sample s of secondary ray j (Eq. 18's Vis).
+ * hits: [rows, dims[2]] i32, the closest front-facing triangle of each secondary ray, -1 if none
+ * (NULL without an indirect term).  dims = {direct words, secondary words, N_b, rows}.
+ * EXM_ERR_ARG when the forward kept its state one chunk at a time (EXM_FLAG_RECOMPUTE). */
+exm_status exm_frame_saved_state(exm_frame* frame, const uint32_t** pixels, const uint32_t** visbits,
+                                 const int32_t** hits, int dims[4]);
+
 /* Forward render (Eqs. 10-20).  maps: DEVICE [mapH, mapW, 8] texel-interleaved
  * (A rgb, R, M, N xyz) of `map_dtype`; cams: HOST array of `views` cameras; out_rgb:
  * DEVICE float32 [views, height, width, 3] (written; background 0).  The frame keeps
  * the visibility buffer for the backward pass.  The frame grows its wavefront buffers on the
  * first forward of a size and sample count and keeps them until destroyed: per frame pixel
- * 160 bytes (the 112-byte shading record and the backward's 48-byte adjoint sums), 4 bytes
- * per direct sample (the texel it picked), one bit per direct and per secondary light sample,
- * and 4 bytes per secondary ray; plus one ray queue of
- * at most 2^27 rays x 32 bytes (4 GiB), sized down to the rays the frame can produce. */
+ * 160 bytes (the 112-byte shading record and the backward's 48-byte adjoint sums); the
+ * per-sample state -- 4 bytes per direct sample (the texel it picked), one bit per direct and
+ * per secondary light sample, and 4 bytes per secondary ray -- per frame pixel, or per pixel of
+ * one chunk when it is recomputed (EXM_FLAG_RECOMPUTE, exm_frame_set_limits); plus one ray
+ * queue of at most 2^27 rays x 32 bytes (4 GiB), sized down to the rays a chunk can produce. */
 exm_status exm_render_forward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
                               int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
                               const exm_params* params, exm_frame* frame, float* out_rgb, void* stream);
@@ -172,9 +205,13 @@ exm_status exm_render_forward(exm_ctx* ctx, const exm_mesh* mesh, const void* ma
  * [views,height,width,3]) accumulates dL/dmaps (DEVICE float32 [mapH,mapW,8]),
  * dL/dE (DEVICE float32 [envH,envW,3]) and dL/dV (DEVICE float32 [nv,3]); any gradient
  * pointer may be NULL to skip it.  The sampling density and every discrete decision are
- * constants of the derivative.  It reads the visibility bits, secondary hits and camera-ray
- * records of the frame's last forward (no ray is traced again) and evaluates the material from
- * `maps` as passed. */
+ * constants of the derivative.  It reads the camera-ray records, recorded texels, visibility
+ * bits and secondary hits of the frame's last forward (no ray is traced again, unless that
+ * forward kept them per chunk: then each chunk is generated and traced again) and evaluates the
+ * material from `maps` as passed.  The cameras, sample counts and seed must be the forward's,
+ * and the mesh, the environment and the map size the ones it used, unchanged since (no
+ * exm_mesh_update_vertices, exm_bvh_build or exm_env_prepare in between): otherwise EXM_ERR_ARG
+ * before anything is enqueued. */
 exm_status exm_render_backward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
                                int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,
                                const exm_params* params, exm_frame* frame, const float* grad_rgb,
@@ -230,15 +267,18 @@ exm_status exm_relight_footprint(exm_server* server, const exm_relight_req* req,
  * For callers that must not call cudaMalloc while they run -- a host whose device memory
  * is owned by another allocator (a caching allocator or a pre-reserved arena), or a
  * latency-critical loop that cannot take the implicit synchronisation of cudaMalloc.  It
- * takes the same arguments as exm_render_backward without grad_V and accumulates dL/dmaps
- * and dL/dE (either may be NULL) for the last forward of `frame`.  Its environment-gradient
+ * takes the same arguments as exm_render_backward without grad_V, makes the same checks
+ * (EXM_ERR_ARG before anything is enqueued, outputs untouched) and accumulates dL/dmaps and
+ * dL/dE (either may be NULL) for the last forward of `frame`.  Its environment-gradient
  * accumulator is a static device array of EXM_STATIC_ENV_MAX_TEXELS float4 (4 MiB) that every
  * GPU loading the library holds until exit; a larger environment is rejected with
- * EXM_ERR_ARG before anything is enqueued.  The array is shared by all calls on a device:
- * calls that overlap on the GPU race and must be serialised by the caller.  The first call
- * on a device resolves the array's address (cudaGetSymbolAddress); make it before any
- * stream capture.  The per-pixel buffers it reads and writes belong to `frame` and were
- * allocated by its forward pass. */
+ * EXM_ERR_ARG.  The array is shared by all calls on a device and keeps the last call's
+ * contents (each call clears the part it uses): calls that overlap on the GPU race and must be
+ * serialised by the caller.  The first call on a device resolves the array's address
+ * (cudaGetSymbolAddress); make it before any stream capture.  The per-pixel and per-chunk
+ * buffers it reads and writes belong to `frame` and were allocated by its forward pass.
+ * Half-resolution indirect light (EXM_FLAG_HALF_RES_INDIRECT with an active indirect term) is
+ * not offered. */
 #define EXM_STATIC_ENV_MAX_TEXELS 262144
 exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,
                                        int mapW, int mapH, const exm_env* env, const exm_camera* cams, int views,

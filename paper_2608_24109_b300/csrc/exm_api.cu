@@ -7,7 +7,12 @@
 #include "exm_device.cuh"
 #include "exm_internal.h"
 
+#include <atomic>
+
 static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_stamp{0};
+
+uint64_t exm_next_stamp() { return ++g_stamp; }
 
 exm_status exm_fail(exm_status code, const std::string& msg) {
     g_last_error = msg;
@@ -105,7 +110,10 @@ exm_status exm_sync(exm_ctx* c, void* stream) {
     if (bits & exm::ERRBIT_INDEX) return exm_fail(EXM_ERR_ARG, "index out of range in the mesh");
     if (bits & exm::ERRBIT_GUARD)
         return exm_fail(EXM_ERR_GUARDBAND, "a vertex lies behind the near plane or outside the guard band");
+    if (bits & exm::ERRBIT_QUEUE)
+        return exm_fail(EXM_ERR_QUEUE_OVERFLOW, "a ray queue chunk overflowed; the rays beyond it were not traced");
     if (bits & exm::ERRBIT_TRAVERSAL) return exm_fail(EXM_ERR_TRAVERSAL_LIMIT, "BVH traversal step/stack limit");
+    if (bits & exm::ERRBIT_TIMEOUT) return exm_fail(EXM_ERR_TIMEOUT, "a bounded device wait ran out");
     return EXM_OK;
 }
 
@@ -149,6 +157,7 @@ exm_status exm_mesh_create(exm_ctx* c, const float* V, int nv, const int32_t* F,
     cudaMemcpyAsync(m->F, F, (size_t)nf * 12, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(m->UV, UV, (size_t)nuv * 8, cudaMemcpyDeviceToDevice, s);
     cudaMemcpyAsync(m->Fuv, Fuv, (size_t)nf * 12, cudaMemcpyDeviceToDevice, s);
+    m->stamp = exm_next_stamp();
     exm_status st = exm_frames_build(m, s);
     if (st == EXM_OK) st = exm_bvh_build_impl(m, s);
     if (st != EXM_OK) {
@@ -165,6 +174,7 @@ exm_status exm_mesh_update_vertices(exm_mesh* m, const float* V, void* stream) {
     DeviceGuard g(m->ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     cudaMemcpyAsync(m->V, V, (size_t)m->nv * 12, cudaMemcpyDeviceToDevice, s);
+    m->stamp = exm_next_stamp();
     exm_status st = exm_frames_build(m, s);
     if (st != EXM_OK) return st;
     return exm_bvh_build_impl(m, s);
@@ -173,6 +183,7 @@ exm_status exm_mesh_update_vertices(exm_mesh* m, const float* V, void* stream) {
 exm_status exm_bvh_build(exm_mesh* m, void* stream) {
     if (!m) return exm_fail(EXM_ERR_ARG, "exm_bvh_build: mesh is NULL");
     DeviceGuard g(m->ctx->device);
+    m->stamp = exm_next_stamp();
     return exm_bvh_build_impl(m, (cudaStream_t)stream);
 }
 
@@ -232,6 +243,7 @@ exm_status exm_env_prepare(exm_env* e, const void* E, exm_dtype dtype, void* str
     if (!e || !E) return exm_fail(EXM_ERR_ARG, "exm_env_prepare: NULL argument");
     if (dtype != EXM_F32 && dtype != EXM_BF16 && dtype != EXM_F16) return exm_fail(EXM_ERR_ARG, "exm_env_prepare: dtype");
     DeviceGuard g(e->ctx->device);
+    e->stamp = exm_next_stamp();
     return exm_env_prepare_impl(e, E, dtype, (cudaStream_t)stream);
 }
 
@@ -303,6 +315,14 @@ void exm_frame_destroy(exm_frame* f) {
     delete f;
 }
 
+exm_status exm_frame_set_limits(exm_frame* f, uint32_t ray_cap, uint64_t saved_budget_bytes) {
+    if (!f) return exm_fail(EXM_ERR_ARG, "exm_frame_set_limits: frame is NULL");
+    if (ray_cap > (1u << 27)) return exm_fail(EXM_ERR_ARG, "exm_frame_set_limits: ray_cap above 2^27");
+    f->ray_cap = ray_cap;
+    f->saved_budget = saved_budget_bytes;
+    return EXM_OK;
+}
+
 exm_status exm_frame_stats(exm_frame* f, uint64_t* covered, uint64_t* samples) {
     if (!f) return exm_fail(EXM_ERR_ARG, "exm_frame_stats: frame is NULL");
     DeviceGuard g(f->ctx->device);
@@ -368,9 +388,11 @@ exm_status exm_frame_visbuf(exm_frame* f, const uint64_t** keys) {
 
 // --------------------------------------------------------------------- render
 
-static exm_status check_render(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
-                               const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
-                               const exm_frame* f, const char* who) {
+}  // extern "C"
+
+exm_status check_render(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
+                        const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
+                        const exm_frame* f, const char* who) {
     std::string w(who);
     if (!c || !m || !maps || !e || !cams || !p || !f) return exm_fail(EXM_ERR_ARG, w + ": NULL argument");
     if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, w + ": map dtype");
@@ -388,6 +410,8 @@ static exm_status check_render(exm_ctx* c, const exm_mesh* m, const void* maps, 
             return exm_fail(EXM_ERR_ARG, w + ": camera kx, ky and near_plane must be positive");
     return EXM_OK;
 }
+
+extern "C" {
 
 exm_status exm_render_forward(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
                               const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
@@ -418,7 +442,7 @@ exm_status exm_render_backward(exm_ctx* c, const exm_mesh* m, const void* maps, 
     if ((p->flags & EXM_FLAG_HALF_RES_INDIRECT) && p->n_bounce > 0 && p->lambda_ind != 0.0f)
         return exm_render_backward_halfres(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, grad_rgb, grad_maps,
                                            grad_env, grad_V, s);
-    st = upload_cameras(f, cams, views, s);
+    st = exm_check_backward(f, m, e, mapW, mapH, cams, views, p);
     if (st != EXM_OK) return st;
     return exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, f, p, grad_rgb, grad_maps, grad_env, grad_V, s);
 }

@@ -92,6 +92,7 @@ static exm_status half_frame(exm_ctx* c, exm_frame* f, exm_frame** out) {
         if (st != EXM_OK) return st;
     }
     f->half->ray_cap = f->ray_cap;
+    f->half->saved_budget = f->saved_budget;
     *out = f->half;
     return EXM_OK;
 }
@@ -151,23 +152,22 @@ exm_status exm_render_backward_halfres(exm_ctx* c, const exm_mesh* m, const void
     exm_params pd = *p;
     pd.n_bounce = 0;
     pd.n_light = 0;
-    exm_status st = upload_cameras(f, cams, views, s);
-    if (st == EXM_OK)
-        st = exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, f, &pd, grad_rgb, grad_maps, grad_env, grad_V, s);
+    exm_params ph = *p;
+    ph.n_direct = 0;
+    ph.flags &= ~EXM_FLAG_ZERO_GRADS;  // the direct adjoint below zeroes them if asked
+    const std::vector<exm_camera> hc = half_cameras(cams, views);
+    // both passes' saved state is checked before anything is enqueued
+    exm_status st = exm_check_backward(f, m, e, mapW, mapH, cams, views, &pd);
+    if (st == EXM_OK) st = exm_check_backward(h, m, e, mapW, mapH, hc.data(), views, &ph);
     if (st != EXM_OK) return st;
     const size_t nh = (size_t)views * h->W * h->H * 3;
     if (!ensure(&f->half_grad, &f->half_grad_cap, nh)) return exm_fail(EXM_ERR_OOM, "half-resolution gradient");
+    st = exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, f, &pd, grad_rgb, grad_maps, grad_env, grad_V, s);
+    if (st != EXM_OK) return st;
     cudaMemsetAsync(f->half_grad, 0, nh * sizeof(float), s);
     upsample_adjoint_kernel<<<grid_pixels(c, f), 256, 0, s>>>(grad_rgb, f->pixels, f->counters, f->W, f->H, h->W,
                                                              h->H, f->half_grad);
     c->launches += 1;
-    exm_params ph = *p;
-    ph.n_direct = 0;
-    ph.flags &= ~EXM_FLAG_ZERO_GRADS;  // the direct adjoint above already zeroed them if asked
-    const std::vector<exm_camera> hc = half_cameras(cams, views);
-    st = upload_cameras(h, hc.data(), views, s);
-    if (st == EXM_OK)
-        st = exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, h, &ph, f->half_grad, grad_maps, grad_env, grad_V,
-                                     s);
-    return st;
+    return exm_shade_backward_impl(c, m, maps, dt, mapW, mapH, e, h, &ph, f->half_grad, grad_maps, grad_env, grad_V,
+                                   s);
 }

@@ -19,8 +19,14 @@ struct exm_ctx {
     size_t scratch_cap = 0;
 };
 
+// Stamps of object contents: every mesh upload or vertex update, BVH build and environment
+// preparation takes a new process-wide stamp, so a frame can tell whether the objects handed to a
+// backward pass are the ones its forward pass used, unchanged (exm_api.cu).
+uint64_t exm_next_stamp();
+
 struct exm_mesh {
     exm_ctx* ctx = nullptr;
+    uint64_t stamp = 0;        // contents stamp (upload, vertex update, BVH build)
     int nv = 0, nf = 0, nuv = 0;
     float* V = nullptr;        // [nv,3]
     int32_t* F = nullptr;      // [nf,3]
@@ -59,6 +65,7 @@ struct exm_mesh {
 
 struct exm_env {
     exm_ctx* ctx = nullptr;
+    uint64_t stamp = 0;           // contents stamp (exm_env_prepare)
     int W = 0, H = 0;
     int rbits = 0, cbits = 0;
     float4* texel = nullptr;      // [H*W] E.rgb, (q/Q) W H / (2 pi^2)
@@ -109,10 +116,23 @@ struct exm_frame {
     size_t hits_cap = 0;
     float4* rays = nullptr;       // ray queue of one chunk
     size_t rays_cap = 0;
-    uint32_t ray_cap = 0;         // rays per chunk (0: the default of 2^24)
+    uint32_t ray_cap = 0;         // rays per chunk at most (0: the library's default of 2^27)
     uint32_t* ctr = nullptr;      // per chunk: queued / fetched counters
     size_t ctr_cap = 0;
     int last_nd = -1, last_nb = -1, last_ns = -1, last_wd = 0, last_ws = 0;
+    // what the last forward pass used: the backward pass must be given the same objects,
+    // unchanged, because the recorded texels, visibility bits, hit ids and pixel records
+    // index into them
+    uint64_t fwd_mesh_stamp = 0, fwd_env_stamp = 0;
+    int fwd_env_W = 0, fwd_env_H = 0, fwd_mapW = 0, fwd_mapH = 0;
+    uint32_t fwd_flags = 0;
+    // per-sample saved state: whole frame (stored) or one chunk at a time (recomputed by the
+    // backward pass, exm_frame_set_limits / EXM_FLAG_RECOMPUTE)
+    bool fwd_recompute = false;
+    uint32_t fwd_chunk = 0;        // pixels per chunk of the last forward
+    uint32_t fwd_ray_cap = 0;      // queue entries per chunk of the last forward
+    uint64_t fwd_seed = 0;
+    uint64_t saved_budget = 0;     // bytes of per-sample state kept for the whole frame (0: default)
     exm_frame* half = nullptr;    // half-resolution indirect pass (EXM_FLAG_HALF_RES_INDIRECT)
     float* half_img = nullptr;    // [views*H'*W'*3] its lambda_ind L_ind image
     size_t half_img_cap = 0;
@@ -154,6 +174,16 @@ inline bool ensure(TT** ptr, size_t* cap, size_t need) {
     *cap = need;
     return true;
 }
+
+// argument checks shared by the render entry points (exm_api.cu)
+exm_status check_render(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
+                        const exm_env* e, const exm_camera* cams, int views, const exm_params* p, const exm_frame* f,
+                        const char* who);
+
+// The backward pass's checks of the frame's saved forward state against its arguments
+// (exm_shade.cu): cameras, mesh, environment, map size, seed and sample counts.
+exm_status exm_check_backward(const exm_frame* f, const exm_mesh* m, const exm_env* e, int mapW, int mapH,
+                              const exm_camera* cams, int views, const exm_params* p);
 
 // error helpers (exm_api.cu)
 exm_status exm_fail(exm_status code, const std::string& msg);

@@ -23,6 +23,9 @@
 //
 // The trace kernel is persistent: a warp claims pools of queued rays and its lanes refill
 // from the pool between rounds of kRound items.
+#include <algorithm>
+#include <cstring>
+#include <string>
 #include <vector>
 
 #include "exm_device.cuh"
@@ -73,6 +76,10 @@ struct ShadeArgs {
     uint32_t ray_cap;
     uint32_t* ctr;       // per chunk: [0] queued, [1] fetch cursor (x2: closest, any)
     uint32_t chunk_begin, chunk_pixels;
+    // per-sample state (tsel, visibility bits, hits) holds pixels [state_base, ...): the whole
+    // frame (state_base 0) or, when it is recomputed chunk by chunk, the current chunk
+    uint32_t state_base;
+    uint32_t shade_begin, shade_end;  // covered-pixel range of a shade launch
     // outputs
     float* out;
     unsigned long long* samples;
@@ -328,12 +335,12 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
             light_sample2(env, ha, (uint32_t)k, hb, (uint32_t)k2, A.nxd, A.nyd, &sa, &sb);
             if (sdot(ngs, sa.dir) > 0.0f) {
                 want |= 1u << u;
-                A.tsel[(size_t)i * A.Nd + k] = sa.texel;
+                A.tsel[(size_t)(i - A.state_base) * A.Nd + k] = sa.texel;
                 sd[u][0][lane] = sa.dir.x; sd[u][1][lane] = sa.dir.y; sd[u][2][lane] = sa.dir.z;
             }
             if (two && sdot(ngs, sb.dir) > 0.0f) {
                 want |= 2u << u;
-                A.tsel[(size_t)i * A.Nd + k2] = sb.texel;
+                A.tsel[(size_t)(i - A.state_base) * A.Nd + k2] = sb.texel;
                 sd[u + 1][0][lane] = sb.dir.x; sd[u + 1][1][lane] = sb.dir.y; sd[u + 1][2][lane] = sb.dir.z;
             }
         }
@@ -352,8 +359,9 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
                 const uint32_t idx = base + (uint32_t)__popc(mu & lt);
                 const S3 d = s3(sd[u][0][lane], sd[u][1][lane], sd[u][2][lane]);
                 if (idx < A.ray_cap)
-                    push_ray(A.rays, idx, org, d, (uint64_t)i * (uint32_t)A.wd * 32u + (uint32_t)(kb + u));
-                else atomicOr(A.status, ERRBIT_TRAVERSAL);
+                    push_ray(A.rays, idx, org, d,
+                             (uint64_t)(i - A.state_base) * (uint32_t)A.wd * 32u + (uint32_t)(kb + u));
+                else atomicOr(A.status, ERRBIT_QUEUE);
             }
             base += (uint32_t)__popc(mu);
         }
@@ -388,8 +396,9 @@ __global__ void __launch_bounds__(256) gen_secondary_kernel(ShadeArgs A) {
         }
         const uint32_t idx = warp_append(A.ctr, valid);
         if (valid) {
-            if (idx < A.ray_cap) push_ray(A.rays, idx, org, wjs, (uint64_t)i * (uint32_t)A.Nb + (uint32_t)j);
-            else atomicOr(A.status, ERRBIT_TRAVERSAL);
+            if (idx < A.ray_cap)
+                push_ray(A.rays, idx, org, wjs, (uint64_t)(i - A.state_base) * (uint32_t)A.Nb + (uint32_t)j);
+            else atomicOr(A.status, ERRBIT_QUEUE);
         }
     }
 }
@@ -421,7 +430,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
         ngs = s3(r3.w, r4.x, r4.y);
     }
     for (int j = 0; j < A.Nb; ++j) {
-        const int g = valid ? A.hits[(size_t)i * A.Nb + j] : -1;
+        const int g = valid ? A.hits[(size_t)(i - A.state_base) * A.Nb + j] : -1;
         S3 yorg = s3(0.f, 0.f, 0.f), ngy = s3(0.f, 0.f, 1.f);
         if (g >= 0) {
             float xi1;
@@ -457,9 +466,10 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
                 if ((want >> u) & 1u) {
                     const uint32_t idx = base + (uint32_t)__popc(mu & lt);
                     const S3 d = s3(sd[u][0][lane], sd[u][1][lane], sd[u][2][lane]);
-                    const uint64_t slot = (uint64_t)i * (uint32_t)A.ws * 32u + (uint32_t)(j * A.Ns + sb + u);
+                    const uint64_t slot =
+                        (uint64_t)(i - A.state_base) * (uint32_t)A.ws * 32u + (uint32_t)(j * A.Ns + sb + u);
                     if (idx < A.ray_cap) push_ray(A.rays, idx, yorg, d, slot | (1ull << 63));
-                    else atomicOr(A.status, ERRBIT_TRAVERSAL);
+                    else atomicOr(A.status, ERRBIT_QUEUE);
                 }
                 base += (uint32_t)__popc(mu);
             }
@@ -486,7 +496,7 @@ __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
     int stack[kStackSize4];
     const uint32_t* qcount = A.ctr + (CLOSEST ? 0 : 2);
     uint32_t* cursor = A.ctr + (CLOSEST ? 1 : 3);
-    const uint32_t n = *qcount;
+    const uint32_t n = min(*qcount, A.ray_cap);  // an overflowed queue holds ray_cap rays (ERRBIT_QUEUE)
     if (n == 0) return;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -782,8 +792,10 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
     env.Q = *A.env.Qp;
     unsigned long long my_samples = 0;
     uint32_t c_brdf = 0;
-    for (uint32_t i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < total; i += nwarps) {
+    const uint32_t end = min(A.shade_end, total);
+    for (uint32_t i = A.shade_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < end; i += nwarps) {
         const uint32_t pid = A.pixels[i];
+        const size_t si = (size_t)(i - A.state_base);  // the pixel's row of the per-sample state
         int c, px, py;
         uint32_t rem;
         pixel_of(A, pid, &c, &px, &py, &rem);
@@ -810,7 +822,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
         // ---- direct light (Eq. 17): the pixel's unoccluded samples, one per lane
         const float invNd = 1.0f / (float)A.Nd;
         const float invW = 1.0f / (float)env.W;
-        const uint32_t* vb = A.visbits + (size_t)i * A.wd;
+        const uint32_t* vb = A.visbits + si * A.wd;
         for (int wbase = 0; wbase < A.wd; wbase += 32) {
             const int tot = enumerate_bits(vb, wbase, A.wd, list);
             for (int t0 = 0; t0 < tot; t0 += 32) {
@@ -821,7 +833,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                     // the texel gen_direct's search picked for this sample (a live sample was
                     // queued, so it was recorded); t < 2^22 is exact in FP32, and one step
                     // corrects the rounded quotient
-                    const uint32_t t = A.tsel[(size_t)i * A.Nd + k];
+                    const uint32_t t = A.tsel[si * A.Nd + k];
                     uint32_t row = (uint32_t)((float)t * invW);
                     if (row * (uint32_t)env.W > t) --row;
                     else if ((row + 1u) * (uint32_t)env.W <= t) ++row;
@@ -852,11 +864,11 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                 int valid = 0;
                 for (int j0 = 0; j0 < A.Nb; j0 += 32) {
                     const int j = j0 + lane;
-                    valid += __popc(__ballot_sync(0xffffffffu, j < A.Nb && A.hits[(size_t)i * A.Nb + j] >= 0));
+                    valid += __popc(__ballot_sync(0xffffffffu, j < A.Nb && A.hits[si * A.Nb + j] >= 0));
                 }
                 if (lane == 0) my_samples += (unsigned long long)A.Nb + (unsigned long long)valid * A.Ns;
             }
-            const uint32_t* sb = A.secbits + (size_t)i * A.ws;
+            const uint32_t* sb = A.secbits + si * A.ws;
             for (int wbase = 0; wbase < A.ws; wbase += 32) {
                 const int tot = enumerate_bits(sb, wbase, A.ws, list);
                 for (int t0 = 0; t0 < tot; t0 += 32) {
@@ -869,7 +881,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                     const float3 wj = normalize(tof(wjs));
                     const float cxj = dot(sns, wj);
                     if (cxj <= 0.0f) continue;
-                    const int gtri = A.hits[(size_t)i * A.Nb + jj];
+                    const int gtri = A.hits[si * A.Nb + jj];
                     S3 ys, ngy, yorg;
                     float3 Q[3];
                     secondary_point(A, gtri, org, wjs, &ys, &ngy, &yorg, Q);
@@ -1182,15 +1194,23 @@ static void launch_pixel_kernels(const ShadeArgs& A, exm_dtype dt, bool epilogue
     }
 }
 
+// The thread-per-pixel surface records (material and n_s) from the maps of the pass.
+static void launch_surface(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, exm_dtype dt,
+                           bool bwd, cudaStream_t s) {
+    time_begin(f, p, bwd ? 3 : 2, s);
+    launch_pixel_kernels(A, dt, false, ctx->num_sms, s);
+    time_end(f, p, s);
+    ctx->launches += 1;
+}
+
+// The warp-per-pixel sample loops over covered pixels [A.shade_begin, A.shade_end).
 template <bool BWD>
-static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, exm_dtype dt,
-                               cudaStream_t s) {
-    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, "map dtype");
+static void launch_samples(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, exm_dtype dt,
+                           cudaStream_t s) {
     const int sms = ctx->num_sms;
     time_begin(f, p, BWD ? 3 : 2, s);
     const bool ind = A.Nb > 0 && A.lambda != 0.0f;
     const bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
-    launch_pixel_kernels(A, dt, false, sms, s);
     if (ind) {
         if (count) launch_shade_t<BWD, true, true>(A, dt, sms, s);
         else launch_shade_t<BWD, false, true>(A, dt, sms, s);
@@ -1198,11 +1218,8 @@ static exm_status launch_shade(exm_ctx* ctx, exm_frame* f, const exm_params* p, 
         if (count) launch_shade_t<BWD, true, false>(A, dt, sms, s);
         else launch_shade_t<BWD, false, false>(A, dt, sms, s);
     }
-    const bool epilogue = BWD && (A.gmaps || A.gV);
-    if (epilogue) launch_pixel_kernels(A, dt, true, sms, s);
     time_end(f, p, s);
-    ctx->launches += epilogue ? 3 : 2;
-    return exm_cuda_check(cudaGetLastError(), "shade launch");
+    ctx->launches += 1;
 }
 
 template <bool CLOSEST>
@@ -1215,78 +1232,218 @@ static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const 
     ctx->launches += 1;
 }
 
+// Per-sample state a frame keeps for the whole frame at most (the texel each direct sample
+// picked, the visibility bits and the secondary hit ids); above it the state lives one chunk
+// at a time and the backward pass recomputes it chunk by chunk.
+constexpr uint64_t kSavedBudgetDefault = 16ull << 30;
+
+// How a pass splits the frame's pixels into chunks: the rays of a chunk fit one queue and,
+// when the per-sample state is recomputed, the chunk's state fits the budget.
+struct ChunkPlan {
+    size_t P = 0;            // frame pixels (views * W * H): the covered ones are a prefix of the list
+    int wd = 0, ws = 0;      // visibility words per pixel: direct, secondary light samples
+    int nb = 0;              // secondary rays per pixel with an active indirect term, else 0
+    bool indirect = false;
+    uint32_t Pc = 0;         // pixels per chunk (a multiple of 32)
+    uint32_t ray_cap = 0;    // queue entries per chunk
+    size_t nchunks = 0;
+    bool recompute = false;  // per-sample state per chunk, recomputed by the backward pass
+    size_t Ps = 0;           // pixels whose per-sample state is resident at once
+    size_t state_per_px = 0; // bytes of per-sample state per pixel
+};
+
+static ChunkPlan plan_chunks(const exm_frame* f, const exm_params* p) {
+    ChunkPlan c;
+    c.P = (size_t)f->views * f->W * f->H;
+    c.wd = (p->n_direct + 31) / 32;
+    c.indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
+    c.ws = c.indirect ? (int)(((int64_t)p->n_bounce * p->n_light + 31) / 32) : 0;
+    c.nb = c.indirect ? p->n_bounce : 0;
+    const size_t cap_max = f->ray_cap ? f->ray_cap : kRayCapDefault;
+    // rays a pixel queues at most: one per direct sample, secondary ray and secondary light sample
+    const size_t per_pixel = std::max((size_t)c.wd * 32 + (size_t)c.ws * 32, (size_t)std::max(c.nb, 1));
+    const size_t P32 = (c.P + 31) & ~(size_t)31;
+    size_t Pc = std::max((size_t)32, std::min(P32, (cap_max / per_pixel) & ~(size_t)31));
+    c.state_per_px = std::max((size_t)1, 4 * (size_t)p->n_direct + 4 * (size_t)(c.wd + c.ws) + 4 * (size_t)c.nb);
+    const uint64_t budget = f->saved_budget ? f->saved_budget : kSavedBudgetDefault;
+    c.recompute = (p->flags & EXM_FLAG_RECOMPUTE) != 0 || (uint64_t)c.P * c.state_per_px > budget;
+    if (c.recompute) Pc = std::max((size_t)32, std::min(Pc, (size_t)(budget / c.state_per_px) & ~(size_t)31));
+    c.Pc = (uint32_t)Pc;
+    c.ray_cap = (uint32_t)std::min(cap_max, Pc * per_pixel);
+    c.nchunks = (c.P + Pc - 1) / Pc;
+    c.Ps = c.recompute ? Pc : c.P;
+    return c;
+}
+
+// Ray generation and tracing of chunk `ch`: secondary rays and their closest hits, then the
+// shadow rays of the direct samples and of the secondary hits' light samples, as bits.
+static void trace_chunk(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ChunkPlan& c, ShadeArgs& A,
+                        size_t ch, cudaStream_t s) {
+    A.chunk_begin = (uint32_t)(ch * c.Pc);
+    A.chunk_pixels = c.Pc;
+    A.ctr = f->ctr + 4 * ch;
+    A.state_base = c.recompute ? A.chunk_begin : 0;
+    if (c.recompute) {  // this chunk's state starts empty
+        cudaMemsetAsync(f->bits, 0, c.Ps * (size_t)(c.wd + c.ws) * sizeof(uint32_t), s);
+        if (c.indirect) cudaMemsetAsync(f->hits, 0xff, c.Ps * (size_t)c.nb * sizeof(int32_t), s);
+    }
+    if (c.indirect) {
+        gen_secondary_kernel<<<exm_blocks((size_t)c.Pc, 256), 256, 0, s>>>(A);
+        ctx->launches += 1;
+        launch_trace<true>(ctx, f, p, A, s);
+    }
+    if (p->n_direct > 0) {  // 0 in the indirect-only half-resolution pass
+        gen_direct_kernel<<<exm_blocks((size_t)c.Pc * ((p->n_direct + kGenK - 1) / kGenK), kGenThreads), kGenThreads,
+                            0, s>>>(A);
+        ctx->launches += 1;
+    }
+    if (c.indirect) {
+        gen_seclight_kernel<<<exm_blocks((size_t)c.Pc, kGenThreads), kGenThreads, 0, s>>>(A);
+        ctx->launches += 1;
+    }
+    launch_trace<false>(ctx, f, p, A, s);
+}
+
 exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
                                   const exm_env* e, exm_frame* f, const exm_params* p, float* out, cudaStream_t s) {
-    const size_t P = (size_t)f->views * f->W * f->H;
-    const int wd = (p->n_direct + 31) / 32;
-    const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
-    const int ws = indirect ? (p->n_bounce * p->n_light + 31) / 32 : 0;
-    const uint32_t cap_max = f->ray_cap ? f->ray_cap : kRayCapDefault;
-    const uint32_t per_pixel = (uint32_t)max(wd * 32 + ws * 32, indirect ? p->n_bounce : 1);
-    // a chunk of Pc pixels queues at most Pc * per_pixel rays; the queue holds one chunk and no
-    // more than the frame can use
-    const size_t P32 = (P + 31) & ~(size_t)31;
-    const uint32_t Pc = (uint32_t)max((size_t)32, min(P32, (size_t)((cap_max / per_pixel) & ~31u)));
-    const uint32_t ray_cap = (uint32_t)min((size_t)cap_max, (size_t)Pc * per_pixel);
+    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, "map dtype");
+    const ChunkPlan c = plan_chunks(f, p);
+    const size_t P = c.P;
+    f->last_nd = -1;  // no valid saved state until this pass is enqueued
     if (!ensure(&f->prec, &f->prec_cap, P * (size_t)kPrec) || !ensure(&f->pacc, &f->pacc_cap, P * (size_t)12) ||
-        (p->n_direct > 0 && !ensure(&f->tsel, &f->tsel_cap, P * (size_t)p->n_direct)) ||
-        !ensure(&f->bits, &f->bits_cap, P * (size_t)(wd + ws)) || !ensure(&f->rays, &f->rays_cap, (size_t)ray_cap * 2) ||
-        (indirect && !ensure(&f->hits, &f->hits_cap, P * (size_t)p->n_bounce)))
+        (p->n_direct > 0 && !ensure(&f->tsel, &f->tsel_cap, c.Ps * (size_t)p->n_direct)) ||
+        !ensure(&f->bits, &f->bits_cap, c.Ps * (size_t)(c.wd + c.ws)) ||
+        !ensure(&f->rays, &f->rays_cap, (size_t)c.ray_cap * 2) ||
+        (c.indirect && !ensure(&f->hits, &f->hits_cap, c.Ps * (size_t)c.nb)))
         return exm_fail(EXM_ERR_OOM, "wavefront buffers");
-    const size_t nchunks = (P + Pc - 1) / Pc;
-    if (!ensure(&f->ctr, &f->ctr_cap, nchunks * 4)) return exm_fail(EXM_ERR_OOM, "chunk counters");
+    if (!ensure(&f->ctr, &f->ctr_cap, c.nchunks * 4)) return exm_fail(EXM_ERR_OOM, "chunk counters");
     ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
-    A.ray_cap = ray_cap;
+    A.secbits = f->bits + c.Ps * (size_t)c.wd;
+    A.ray_cap = c.ray_cap;
     A.out = out;
     pixel_prep_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(A);
     ctx->launches += 1;
     cudaMemsetAsync(f->samples, 0, sizeof(unsigned long long), s);
     cudaMemsetAsync(out, 0, P * 3 * sizeof(float), s);
-    cudaMemsetAsync(f->bits, 0, P * (size_t)(wd + ws) * sizeof(uint32_t), s);
-    cudaMemsetAsync(f->ctr, 0, nchunks * 4 * sizeof(uint32_t), s);
-    if (indirect) cudaMemsetAsync(f->hits, 0xff, P * (size_t)p->n_bounce * sizeof(int32_t), s);
-    if (p->flags & EXM_FLAG_COUNT_WORK) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
-    for (size_t ch = 0; ch < nchunks; ++ch) {
-        A.chunk_begin = (uint32_t)(ch * Pc);
-        A.chunk_pixels = Pc;
-        A.ctr = f->ctr + 4 * ch;
-        if (indirect) {
-            gen_secondary_kernel<<<exm_blocks((size_t)Pc, 256), 256, 0, s>>>(A);
-            launch_trace<true>(ctx, f, p, A, s);
-            ctx->launches += 1;
-        }
-        if (p->n_direct > 0) {  // 0 in the indirect-only half-resolution pass
-            gen_direct_kernel<<<exm_blocks((size_t)Pc * ((p->n_direct + kGenK - 1) / kGenK), kGenThreads), kGenThreads, 0, s>>>(A);
-            ctx->launches += 1;
-        }
-        if (indirect) {
-            gen_seclight_kernel<<<exm_blocks((size_t)Pc, kGenThreads), kGenThreads, 0, s>>>(A);
-            ctx->launches += 1;
-        }
-        launch_trace<false>(ctx, f, p, A, s);
+    cudaMemsetAsync(f->ctr, 0, c.nchunks * 4 * sizeof(uint32_t), s);
+    if (!c.recompute) {
+        cudaMemsetAsync(f->bits, 0, P * (size_t)(c.wd + c.ws) * sizeof(uint32_t), s);
+        if (c.indirect) cudaMemsetAsync(f->hits, 0xff, P * (size_t)c.nb * sizeof(int32_t), s);
     }
-    exm_status st = exm_cuda_check(cudaGetLastError(), "wavefront launch");
+    if (p->flags & EXM_FLAG_COUNT_WORK) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
+    launch_surface(ctx, f, p, A, dt, false, s);
+    for (size_t ch = 0; ch < c.nchunks; ++ch) {
+        trace_chunk(ctx, f, p, c, A, ch, s);
+        if (c.recompute) {  // shade the chunk while its state is resident
+            A.shade_begin = A.chunk_begin;
+            A.shade_end = A.chunk_begin + c.Pc;
+            launch_samples<false>(ctx, f, p, A, dt, s);
+        }
+    }
+    if (!c.recompute) {
+        A.state_base = 0;
+        A.shade_begin = 0;
+        A.shade_end = 0xffffffffu;
+        launch_samples<false>(ctx, f, p, A, dt, s);
+    }
+    exm_status st = exm_cuda_check(cudaGetLastError(), "forward launch");
     if (st != EXM_OK) return st;
-    f->last_wd = wd;
-    f->last_ws = ws;
-    f->last_nb = indirect ? p->n_bounce : 0;
-    f->last_ns = indirect ? p->n_light : 0;
+    f->last_wd = c.wd;
+    f->last_ws = c.ws;
+    f->last_nb = c.nb;
+    f->last_ns = c.indirect ? p->n_light : 0;
     f->last_nd = p->n_direct;
-    return launch_shade<false>(ctx, f, p, A, dt, s);
+    f->fwd_mesh_stamp = m->stamp;
+    f->fwd_env_stamp = e->stamp;
+    f->fwd_env_W = e->W;
+    f->fwd_env_H = e->H;
+    f->fwd_mapW = mapW;
+    f->fwd_mapH = mapH;
+    f->fwd_seed = p->seed;
+    f->fwd_recompute = c.recompute;
+    f->fwd_chunk = c.Pc;
+    f->fwd_ray_cap = c.ray_cap;
+    return EXM_OK;
 }
 
-static exm_status check_saved(const exm_frame* f, const exm_params* p) {
+// The backward pass reads what the forward pass left in the frame: the pixel records, and the
+// recorded texels, visibility bits and hit ids (or, recomputed, their chunks).  They index the
+// forward's mesh, environment and maps, so the backward must get the same objects, unchanged.
+static exm_status check_saved(const exm_frame* f, const exm_mesh* m, const exm_env* e, int mapW, int mapH,
+                              const exm_params* p) {
     const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
     if (f->last_nd != p->n_direct || f->last_nb != (indirect ? p->n_bounce : 0) ||
         f->last_ns != (indirect ? p->n_light : 0) || !f->bits || !f->pacc)
         return exm_fail(EXM_ERR_ARG, "backward: the frame holds no forward pass with these sample counts");
+    if (f->fwd_mesh_stamp != m->stamp)
+        return exm_fail(EXM_ERR_ARG, "backward: the mesh, its vertices or its BVH differ from the forward pass's");
+    if (f->fwd_env_stamp != e->stamp || f->fwd_env_W != e->W || f->fwd_env_H != e->H)
+        return exm_fail(EXM_ERR_ARG, "backward: the environment differs from the one the forward pass sampled (" +
+                                         std::to_string(f->fwd_env_W) + "x" + std::to_string(f->fwd_env_H) +
+                                         " prepared before it)");
+    if (f->fwd_mapW != mapW || f->fwd_mapH != mapH)
+        return exm_fail(EXM_ERR_ARG, "backward: the map size differs from the forward pass's");
+    if (f->fwd_seed != p->seed) return exm_fail(EXM_ERR_ARG, "backward: the sample seed differs from the forward pass's");
     return EXM_OK;
+}
+
+// True when `cams` are the cameras the frame's last pass uploaded.
+static bool cameras_match(const exm_frame* f, const exm_camera* cams, int views) {
+    const size_t bytes = (size_t)views * sizeof(exm_camera);
+    return f->cams_host.size() == bytes && memcmp(f->cams_host.data(), cams, bytes) == 0;
+}
+
+exm_status exm_check_backward(const exm_frame* f, const exm_mesh* m, const exm_env* e, int mapW, int mapH,
+                              const exm_camera* cams, int views, const exm_params* p) {
+    if (!cameras_match(f, cams, views))
+        return exm_fail(EXM_ERR_ARG, "backward: the cameras differ from the forward pass's");
+    return check_saved(f, m, e, mapW, mapH, p);
+}
+
+// The sample loops and epilogue of the backward pass, with A's gradient outputs set.  With a
+// recomputed state, each chunk's rays are generated and traced again (the same decisions: the
+// streams are counter-based and the traversal deterministic) before its sample loops.  Uses
+// only buffers the frame's forward pass allocated.
+static exm_status backward_core(exm_ctx* ctx, exm_frame* f, const exm_params* p, ShadeArgs& A, exm_dtype dt,
+                                cudaStream_t s) {
+    ChunkPlan c = plan_chunks(f, p);
+    c.recompute = f->fwd_recompute;  // the forward's split, whatever the limits are now
+    c.Pc = f->fwd_chunk;
+    c.ray_cap = f->fwd_ray_cap;
+    c.nchunks = (c.P + c.Pc - 1) / c.Pc;
+    c.Ps = c.recompute ? c.Pc : c.P;
+    A.secbits = f->bits + c.Ps * (size_t)c.wd;
+    A.ray_cap = c.ray_cap;
+    if (p->flags & EXM_FLAG_COUNT_WORK) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
+    launch_surface(ctx, f, p, A, dt, true, s);
+    if (!c.recompute) {
+        A.state_base = 0;
+        A.shade_begin = 0;
+        A.shade_end = 0xffffffffu;
+        launch_samples<true>(ctx, f, p, A, dt, s);
+    } else {
+        cudaMemsetAsync(f->ctr, 0, c.nchunks * 4 * sizeof(uint32_t), s);
+        for (size_t ch = 0; ch < c.nchunks; ++ch) {
+            trace_chunk(ctx, f, p, c, A, ch, s);
+            A.shade_begin = A.chunk_begin;
+            A.shade_end = A.chunk_begin + c.Pc;
+            launch_samples<true>(ctx, f, p, A, dt, s);
+        }
+    }
+    if (A.gmaps || A.gV) {
+        time_begin(f, p, 3, s);
+        launch_pixel_kernels(A, dt, true, ctx->num_sms, s);
+        time_end(f, p, s);
+        ctx->launches += 1;
+    }
+    return exm_cuda_check(cudaGetLastError(), "backward launch");
 }
 
 exm_status exm_shade_backward_impl(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
                                    const exm_env* e, exm_frame* f, const exm_params* p, const float* grad_rgb,
                                    float* grad_maps, float* grad_env, float* grad_V, cudaStream_t s) {
-    exm_status st = check_saved(f, p);
+    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, "map dtype");
+    exm_status st = check_saved(f, m, e, mapW, mapH, p);
     if (st != EXM_OK) return st;
     ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
     A.grad_rgb = grad_rgb;
@@ -1296,7 +1453,6 @@ exm_status exm_shade_backward_impl(exm_ctx* ctx, const exm_mesh* m, const void* 
     size_t nfr = (size_t)(m->nv > m->nuv ? m->nv : m->nuv);
     if (grad_V && (!ensure(&f->gnrm, &f->gframe_capacity, nfr) || !ensure(&f->gtan, &f->gtan_capacity, nfr)))
         return exm_fail(EXM_ERR_OOM, "frame gradient");
-    if (p->flags & EXM_FLAG_COUNT_WORK) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
     if (p->flags & EXM_FLAG_ZERO_GRADS) {
         if (grad_maps) cudaMemsetAsync(grad_maps, 0, (size_t)mapW * mapH * 8 * sizeof(float), s);
         if (grad_env) cudaMemsetAsync(grad_env, 0, nenv * 3 * sizeof(float), s);
@@ -1311,7 +1467,7 @@ exm_status exm_shade_backward_impl(exm_ctx* ctx, const exm_mesh* m, const void* 
         A.gnrm = f->gnrm;
         A.gtan = f->gtan;
     }
-    st = launch_shade<true>(ctx, f, p, A, dt, s);
+    st = backward_core(ctx, f, p, A, dt, s);
     if (st != EXM_OK) return st;
     if (grad_env) {
         env_grad_finish_kernel<<<exm_blocks(nenv, 256), 256, 0, s>>>(f->genv, (int)nenv, grad_env);
@@ -1373,52 +1529,55 @@ extern "C" exm_status exm_render_backward_noalloc(exm_ctx* ctx, const exm_mesh* 
                                                   int views, const exm_params* p, exm_frame* f,
                                                   const float* grad_rgb, float* grad_maps, float* grad_env,
                                                   void* stream) {
-    if (!ctx || !m || !maps || !e || !cams || !p || !f || !grad_rgb)
-        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: NULL argument");
+    exm_status st = check_render(ctx, m, maps, dt, mapW, mapH, e, cams, views, p, f, "exm_render_backward_noalloc");
+    if (st != EXM_OK) return st;
+    if (!grad_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: grad_rgb is NULL");
     if ((long long)e->W * e->H > EXM_STATIC_ENV_MAX_TEXELS)
         return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: environment has " +
                                          std::to_string((long long)e->W * e->H) + " texels, more than the " +
                                          std::to_string(EXM_STATIC_ENV_MAX_TEXELS) + " the static scratch holds");
-    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16)
-        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: map dtype");
-    if (mapW < 1 || mapH < 1 || (long long)mapW * mapH > (1ll << 28))
-        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: map size");
-    if (views != f->views) return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: views differ from the frame's");
-    if (p->n_direct < 1 || p->n_direct > 65536 || p->n_bounce < 0 || p->n_bounce > 4096 ||
-        (p->n_bounce > 0 && (p->n_light < 1 || p->n_light > 4096)))
-        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: sample counts");
-    if (m->ctx != ctx || e->ctx != ctx || f->ctx != ctx)
-        return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: objects of another context");
-    if (p->flags & EXM_FLAG_HALF_RES_INDIRECT)
+    if ((p->flags & EXM_FLAG_HALF_RES_INDIRECT) && p->n_bounce > 0 && p->lambda_ind != 0.0f)
         return exm_fail(EXM_ERR_ARG, "exm_render_backward_noalloc: half-resolution indirect light is not offered");
-    int prev = -1;
-    cudaGetDevice(&prev);
-    if (prev != ctx->device) cudaSetDevice(ctx->device);
+    DeviceGuard g(ctx->device);
+    // every check before anything is enqueued: a rejected call leaves the outputs untouched
+    st = exm_check_backward(f, m, e, mapW, mapH, cams, views, p);
+    if (st != EXM_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     float4* scratch = nullptr;
-    exm_status st = static_scratch(ctx->device, &scratch);
-    if (st == EXM_OK)
-        st = upload_cameras(f, cams, views, s);
-    if (st == EXM_OK) {
-        size_t nenv = (size_t)e->W * e->H;
-        ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
-        A.grad_rgb = grad_rgb;
-        A.gmaps = grad_maps;
-        A.genv = scratch;
-        A.gV = nullptr;
-        if (p->flags & EXM_FLAG_ZERO_GRADS) {
-            if (grad_maps) cudaMemsetAsync(grad_maps, 0, (size_t)mapW * mapH * 8 * sizeof(float), s);
-            if (grad_env) cudaMemsetAsync(grad_env, 0, nenv * 3 * sizeof(float), s);
-        }
-        cudaMemsetAsync(scratch, 0, nenv * sizeof(float4), s);
-        st = check_saved(f, p);
-        if (st == EXM_OK) st = launch_shade<true>(ctx, f, p, A, dt, s);
-        if (st == EXM_OK && grad_env) {
-            env_grad_finish_kernel<<<exm_blocks(nenv, 256), 256, 0, s>>>(scratch, (int)nenv, grad_env);
-            ctx->launches += 1;
-        }
-        if (st == EXM_OK) st = exm_cuda_check(cudaGetLastError(), "exm_render_backward_noalloc launch");
+    st = static_scratch(ctx->device, &scratch);
+    if (st != EXM_OK) return st;
+    const size_t nenv = (size_t)e->W * e->H;
+    ShadeArgs A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
+    A.grad_rgb = grad_rgb;
+    A.gmaps = grad_maps;
+    A.genv = scratch;
+    A.gV = nullptr;
+    if (p->flags & EXM_FLAG_ZERO_GRADS) {
+        if (grad_maps) cudaMemsetAsync(grad_maps, 0, (size_t)mapW * mapH * 8 * sizeof(float), s);
+        if (grad_env) cudaMemsetAsync(grad_env, 0, nenv * 3 * sizeof(float), s);
     }
-    if (prev >= 0 && prev != ctx->device) cudaSetDevice(prev);
+    cudaMemsetAsync(scratch, 0, nenv * sizeof(float4), s);
+    st = backward_core(ctx, f, p, A, dt, s);
+    if (st == EXM_OK && grad_env) {
+        env_grad_finish_kernel<<<exm_blocks(nenv, 256), 256, 0, s>>>(scratch, (int)nenv, grad_env);
+        ctx->launches += 1;
+    }
+    if (st == EXM_OK) st = exm_cuda_check(cudaGetLastError(), "exm_render_backward_noalloc launch");
     return st;
+}
+
+extern "C" exm_status exm_frame_saved_state(exm_frame* f, const uint32_t** pixels, const uint32_t** visbits,
+                                            const int32_t** hits, int dims[4]) {
+    if (!f || !pixels || !visbits || !hits || !dims) return exm_fail(EXM_ERR_ARG, "exm_frame_saved_state: NULL argument");
+    if (f->last_nd < 0 || !f->bits) return exm_fail(EXM_ERR_ARG, "exm_frame_saved_state: no forward pass yet");
+    if (f->fwd_recompute)
+        return exm_fail(EXM_ERR_ARG, "exm_frame_saved_state: the last forward kept its state one chunk at a time");
+    *pixels = f->pixels;
+    *visbits = f->bits;
+    *hits = f->last_nb > 0 ? f->hits : nullptr;
+    dims[0] = f->last_wd;
+    dims[1] = f->last_ws;
+    dims[2] = f->last_nb;
+    dims[3] = f->views * f->W * f->H;
+    return EXM_OK;
 }

@@ -23,6 +23,7 @@ EXM_ERR_GUARDBAND = -4
 EXM_ERR_TRAVERSAL_LIMIT = -5
 EXM_ERR_TIMEOUT = -6
 EXM_ERR_BUSY = -7
+EXM_ERR_QUEUE_OVERFLOW = -8
 
 EXM_F32, EXM_BF16, EXM_F16 = 0, 1, 2
 FLAG_WRAP_U = 1
@@ -32,13 +33,14 @@ FLAG_ZERO_GRADS = 8
 FLAG_TIME_KERNELS = 16
 FLAG_NO_SECONDARY_MATERIAL = 32
 FLAG_HALF_RES_INDIRECT = 64
+FLAG_RECOMPUTE = 128
 
 EXPORTS = [
     "exm_create", "exm_destroy", "exm_last_error", "exm_sync",
     "exm_mesh_create", "exm_mesh_update_vertices", "exm_bvh_build", "exm_mesh_destroy", "exm_mesh_frames",
     "exm_env_create", "exm_env_prepare", "exm_env_destroy", "exm_env_total",
-    "exm_frame_create", "exm_frame_destroy", "exm_frame_stats", "exm_frame_work", "exm_frame_kernel_ms",
-    "exm_launch_count", "exm_frame_visbuf",
+    "exm_frame_create", "exm_frame_destroy", "exm_frame_set_limits", "exm_frame_stats", "exm_frame_work", "exm_frame_kernel_ms",
+    "exm_launch_count", "exm_frame_visbuf", "exm_frame_saved_state",
     "exm_render_forward", "exm_render_backward", "exm_render_backward_noalloc", "exm_l1_loss",
     "exm_server_create", "exm_server_destroy", "exm_server_add_asset", "exm_relight_submit", "exm_relight_poll",
     "exm_server_progress", "exm_server_stats", "exm_relight_footprint",
@@ -102,11 +104,13 @@ def lib():
         "exm_env_total": ([P, ctypes.POINTER(U64)], I),
         "exm_frame_create": ([P, I, I, I, PP], I),
         "exm_frame_destroy": ([P], None),
+        "exm_frame_set_limits": ([P, ctypes.c_uint32, U64], I),
         "exm_frame_stats": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
         "exm_frame_work": ([P, ctypes.POINTER(U64 * 4)], I),
         "exm_frame_kernel_ms": ([P, ctypes.POINTER(ctypes.c_float * 4)], I),
         "exm_launch_count": ([P, ctypes.POINTER(U64)], I),
         "exm_frame_visbuf": ([P, PP], I),
+        "exm_frame_saved_state": ([P, PP, PP, PP, ctypes.POINTER(I * 4)], I),
         "exm_render_forward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P], I),
         "exm_render_backward": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P, P], I),
         "exm_render_backward_noalloc": ([P, P, P, I, I, I, P, P, I, ctypes.POINTER(Params), P, P, P, P, P], I),
@@ -243,6 +247,10 @@ def exm_frame_destroy(frame):
     lib().exm_frame_destroy(frame)
 
 
+def exm_frame_set_limits(frame, ray_cap=0, saved_budget_bytes=0):
+    return check(lib().exm_frame_set_limits(frame, int(ray_cap), int(saved_budget_bytes)))
+
+
 def exm_frame_stats(frame):
     c, s = ctypes.c_uint64(), ctypes.c_uint64()
     check(lib().exm_frame_stats(frame, ctypes.byref(c), ctypes.byref(s)))
@@ -271,6 +279,14 @@ def exm_frame_visbuf(frame):
     p = ctypes.c_void_p()
     check(lib().exm_frame_visbuf(frame, ctypes.byref(p)))
     return p.value
+
+
+def exm_frame_saved_state(frame):
+    """(pixels, visbits, hits) DEVICE addresses and dims (direct words, secondary words, N_b, rows)."""
+    ptrs = [ctypes.c_void_p() for _ in range(3)]
+    dims = (ctypes.c_int * 4)()
+    check(lib().exm_frame_saved_state(frame, *[ctypes.byref(p) for p in ptrs], ctypes.byref(dims)))
+    return [p.value for p in ptrs], list(dims)
 
 
 def exm_render_forward(ctx, mesh, maps, env, cams, params: Params, frame, out, stream=None):

@@ -47,6 +47,11 @@ class Renderer:
         return cls(sc.V, sc.F, sc.UV, sc.Fuv, sc.env.shape[1], sc.env.shape[0], sc.cams, sc.width, sc.height,
                    device=device, **args)
 
+    def set_limits(self, ray_cap=0, saved_budget_bytes=0):
+        """Ray-queue entries per chunk and the byte budget of the whole-frame per-sample state
+        (0: the library's defaults); see exm_frame_set_limits."""
+        N.exm_frame_set_limits(self.frame, ray_cap, saved_budget_bytes)
+
     def image_shape(self):
         return (self.views, self.height, self.width, 3)
 
@@ -89,6 +94,26 @@ class Renderer:
                                         "strides": None}
 
         return torch.as_tensor(_View(), device=self.device).clone()
+
+    def saved_state(self):
+        """Copies of the last forward's per-sample decisions: covered-pixel ids [n] (int64),
+        direct visibility words [n, wd], secondary light-sample words [n, ws] (uint32 bit
+        patterns in int64) and secondary hits [n, N_b] (int32); see exm_frame_saved_state."""
+        (pp, pb, ph), (wd, ws, nb, rows) = N.exm_frame_saved_state(self.frame)
+        n, _ = self.stats()
+
+        def grab(ptr, shape, typestr):
+            class _View:
+                __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, True), "version": 3,
+                                            "strides": None}
+            return torch.as_tensor(_View(), device=self.device).clone()
+
+        pixels = grab(pp, (n,), "<i4").long() & 0xFFFFFFFF
+        bits_all = grab(pb, (rows * (wd + ws),), "<i4").long() & 0xFFFFFFFF
+        dbits = bits_all[:rows * wd].view(rows, wd)[:n]
+        sbits = bits_all[rows * wd:].view(rows, ws)[:n] if ws else bits_all[:0].view(0, 0)
+        hits = grab(ph, (rows * nb,), "<i4").view(rows, nb)[:n] if nb else None
+        return pixels, dbits, sbits, hits
 
     def update_vertices(self, V):
         self.V.copy_(V)

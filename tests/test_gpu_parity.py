@@ -276,37 +276,118 @@ def test_l1_loss():
 
 # ----------------------------------------------------------------- full-size configs, sampled
 
-def test_geometry_config_sampled():
-    sc = scenes.config("geometry")
-    r, M, E, out = gpu_forward(sc)
+def error_table(got, ref):
+    """Per-output error: largest absolute error over the largest reference magnitude, and the
+    relative L2 error (the gradient bar)."""
+    g = np.asarray(got, np.float64).ravel()
+    o = np.asarray(ref, np.float64).ravel()
+    scale = max(np.abs(o).max(), 1e-30)
+    return {"max_rel": float(np.abs(g - o).max() / scale), "l2_rel": float(np.linalg.norm(g - o) / max(np.linalg.norm(o), 1e-30))}
+
+
+def sampled_parity(sc, sel, maps, env, seed, what):
+    """Full-size forward and backward on the GPU; the loss gradient is nonzero only on the
+    sampled pixels `sel` (a masked loss), so the oracle's brute-force decisions and FP64
+    adjoint on those pixels give every output exactly: radiance at the sample, and dL/dmaps,
+    dL/dE, dL/dV everywhere.  `maps` / `env` are the stored values (possibly BF16/FP16); the
+    oracle reads them widened exactly to FP64.  Returns the per-output error table."""
+    r = _renderer(sc)
+    Md = maps.cuda().contiguous()
+    Ed = env.cuda().contiguous()
+    out = r.forward(Md, Ed)
+    r.sync()
     vis = keys_u64(r.visbuf())
-    covered = np.argwhere((vis & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)).astype(np.int32)
-    rng = np.random.default_rng(1)
-    sel = covered[rng.choice(covered.shape[0], 48, replace=False)]
-    # a few uncovered pixels and silhouette neighbours too
     st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, sel)
     assert np.array_equal(keys, vis[sel[:, 0], sel[:, 1], sel[:, 2]])
+    rng = np.random.default_rng(seed)
+    gs = rng.normal(size=(sel.shape[0], 3)).astype(np.float32)
+    grad = torch.zeros(out.shape, dtype=torch.float32, device="cuda")
+    grad[torch.as_tensor(sel[:, 0]).long(), torch.as_tensor(sel[:, 1]).long(), torch.as_tensor(sel[:, 2]).long()] = \
+        torch.as_tensor(gs, device="cuda")
+    gm = torch.zeros(Md.shape, dtype=torch.float32, device="cuda")
+    gE = torch.zeros(Ed.shape, dtype=torch.float32, device="cuda")
+    gV = torch.zeros((sc.V.shape[0], 3), dtype=torch.float32, device="cuda")
+    r.backward(Md, grad, gm, gE, gV)
+    r.sync()
+    sc.env = env.float().numpy()  # the environment as stored: its distribution and values
     tab = oracle.EnvTable(sc.env)
     dec = oracle.Decisions(sc, tab, sel, keys)
-    V, Mo, Eo = shade.scene_tensors(sc)
+    V, _, Eo = shade.scene_tensors(sc)
+    Mo = maps.to(torch.float64)
     I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
-    check_radiance(out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]], I, "geometry config")
+    got = out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]]
+    check_radiance(got, I, what)
+    oV, oM, oE = shade.backward(sc, tab, dec, V, Mo, Eo, gs.astype(np.float64))
+    table = {"radiance": error_table(got, I)}
+    # compare the gradients on their support (the other entries are zero on both sides)
+    gm_c = gm.cpu()
+    nz = (gm_c != 0).any(-1) | (oM != 0).any(-1)
+    for got_g, ref_g, name in ((gm_c[nz], oM[nz], "dL/dmaps"), (gE.cpu(), oE, "dL/dE"), (gV.cpu(), oV, "dL/dV")):
+        check_grad(got_g.numpy(), ref_g.numpy(), f"{what} {name}")
+        table[name] = error_table(got_g.numpy(), ref_g.numpy())
+    print(what, table)
+    r.close()
+    return table
+
+
+def _sample_covered(sc, view_pixels, count, seed, crop=None):
+    """`count` covered pixels from the oracle's raster of random candidates (a view and, with
+    `crop`, the centre crop of that size)."""
+    rng = np.random.default_rng(seed)
+    n = 40 * count
+    v = rng.integers(0, sc.views if view_pixels is None else 1, n)
+    if crop:
+        c0 = (sc.width - crop) // 2
+        y, x = rng.integers(c0, c0 + crop, n), rng.integers(c0, c0 + crop, n)
+    else:
+        y, x = rng.integers(0, sc.height, n), rng.integers(0, sc.width, n)
+    cand = np.stack([v, y, x], 1).astype(np.int32)
+    cand = np.unique(cand, axis=0)
+    rng.shuffle(cand)
+    st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, cand)
+    cov = (keys & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)
+    sel = cand[cov][:count]
+    assert sel.shape[0] == count
+    return sel
+
+
+def test_geometry_config_sampled():
+    """99K-triangle blob, 16 views of 512^2, N_d = 256: 48 sampled pixels, forward and masked
+    backward into maps, environment and vertices."""
+    sc = scenes.config("geometry")
+    sel = _sample_covered(sc, None, 48, 1)
+    sampled_parity(sc, sel, torch.as_tensor(sc.maps), torch.as_tensor(sc.env), 11, "geometry")
 
 
 def test_indirect_config_sampled():
+    """499K-triangle blob with cavities, 8 views of 800^2, N_d = 128, N_b = 8, N_s = 4."""
     sc = scenes.config("indirect")
-    r, M, E, out = gpu_forward(sc)
-    vis = keys_u64(r.visbuf())
-    covered = np.argwhere((vis & np.uint64(0xFFFFFFFF)) != np.uint64(0xFFFFFFFF)).astype(np.int32)
-    rng = np.random.default_rng(2)
-    sel = covered[rng.choice(covered.shape[0], 24, replace=False)]
-    st, keys = oracle.raster_pixels(sc.V, sc.F, sc.cams, sc.width, sc.height, sel)
-    assert np.array_equal(keys, vis[sel[:, 0], sel[:, 1], sel[:, 2]])
-    tab = oracle.EnvTable(sc.env)
-    dec = oracle.Decisions(sc, tab, sel, keys)
-    V, Mo, Eo = shade.scene_tensors(sc)
-    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
-    check_radiance(out.cpu().numpy()[sel[:, 0], sel[:, 1], sel[:, 2]], I, "indirect config")
+    sel = _sample_covered(sc, None, 24, 2)
+    sampled_parity(sc, sel, torch.as_tensor(sc.maps), torch.as_tensor(sc.env), 12, "indirect")
+
+
+@pytest.mark.parametrize("mdt", [torch.bfloat16, torch.float16])
+def test_precision_form_sampled(mdt):
+    """2M-triangle precision workload in the benchmark's configuration (8 views of 1024^2,
+    N_d = 64, N_b = 4, N_s = 4), maps stored in BF16 / FP16 and the environment in FP16 with FP32
+    shading, accumulation and gradients: 24 pixels of the 256^2 centre crop of view 0, radiance
+    and gradients against the FP64 oracle fed the same rounded values (the error left is the
+    compute error; the storage rounding is reported separately by the benchmark)."""
+    sc = scenes.config("precision")
+    sel = _sample_covered(sc, 0, 24, 4, crop=256)
+    Mq = torch.as_tensor(sc.maps).to(mdt)
+    Eq = torch.as_tensor(sc.env).to(torch.float16)
+    sampled_parity(sc, sel, Mq, Eq, 14, f"precision {mdt}")
+
+
+def test_low_precision_backward_full_frame():
+    """BF16 maps and FP16 environment on a small ragged frame: every covered pixel, forward and
+    backward, against the oracle fed the same rounded values."""
+    sc = ragged_tiny(72, 56, 1)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, sc.width, sc.height)
+    sel = oracle.covered_pixels(keys)
+    sampled_parity(sc, sel, torch.as_tensor(sc.maps).to(torch.bfloat16),
+                   torch.as_tensor(sc.env).to(torch.float16), 15, "tiny bf16/fp16")
 
 
 # ----------------------------------------------------------------- errors

@@ -296,6 +296,84 @@ def test_vertex_frames_on_sphere():
     assert len(set(sgn.tolist())) == 1
 
 
+# ---- the tangent-space normal of Eq. 11, pinned by geometry on a flat quad
+
+def _quad_chart(flip_u=False, flip_v=False):
+    """A unit square in a tilted plane, P(s, t) = O + s a + t b with a, b orthonormal, two
+    counter-clockwise faces seen from a x b, and UVs u = s, v = t, mirrored in u and/or v.  By
+    construction dP/du = +-a and dP/dv = +-b."""
+    a = np.array([0.6, 0.8, 0.0])
+    b = np.array([-0.48, 0.36, 0.8])
+    O = np.array([0.2, -0.1, 0.3])
+    st = np.array([[0, 0], [1, 0], [1, 1], [0, 1]], float)
+    V = O + st[:, :1] * a + st[:, 1:] * b
+    F = np.array([[0, 1, 2], [0, 2, 3]])
+    UV = st.copy()
+    if flip_u:
+        UV[:, 0] = 1 - UV[:, 0]
+    if flip_v:
+        UV[:, 1] = 1 - UV[:, 1]
+    dPdu = -a if flip_u else a
+    dPdv = -b if flip_v else b
+    return V, F, UV.astype(np.float32), dPdu, dPdv, np.cross(a, b)
+
+
+def _oracle_ns(V, F, UV, q, bary=(0.2, 0.3, 0.5), face=0):
+    """n_s of the oracle at a point of `face` for a constant normal-map value q, through its own
+    chain: UV handedness, vertex frames, bilinear fetch of a constant map, Eq. 11."""
+    sgn = shade.face_uv_sign(UV, F)
+    nv, tuv = shade.vertex_frames(torch.tensor(V, dtype=torch.float64), F, UV, F, UV.shape[0], sgn)
+    att = torch.tensor([[0.5, 0.5, 0.5, 0.5, 0.0, *q]], dtype=torch.float64)
+    b = torch.tensor([bary], dtype=torch.float64)
+    fv = torch.as_tensor(F[face:face + 1], dtype=torch.long)
+    ns, _, _, _ = shade._material(att, b, nv[fv], tuv[fv], torch.tensor(sgn[face:face + 1]), True)
+    return ns[0].numpy()
+
+
+def _normal_map_pins():
+    """The tangent frame's meaning, independent of any formula: the map's x axis follows
+    increasing u, its y axis increasing v, its z axis the surface normal; a tilted value mixes
+    them and is renormalised.  In all four UV orientations (mirrored charts have s_f = -1)."""
+    for flip_u in (False, True):
+        for flip_v in (False, True):
+            V, F, UV, du, dv, n = _quad_chart(flip_u, flip_v)
+            for face in (0, 1):
+                for q, want in (((1, 0, 0), du), ((0, 1, 0), dv), ((0, 0, 1), n), ((0.6, 0, 0.8), 0.6 * du + 0.8 * n),
+                                ((0, -0.6, 0.8), -0.6 * dv + 0.8 * n), ((3, 4, 0), (3 * du + 4 * dv) / 5)):
+                    got = _oracle_ns(V, F, UV, q, face=face)
+                    assert np.abs(got - want).max() < 1e-12, (flip_u, flip_v, face, q, got, want)
+
+
+def test_normal_map_axes_follow_u_v_and_the_normal():
+    _normal_map_pins()
+
+
+def _planted(kind):
+    def material(att, b, nvert, tvert, sgn_f, metallic):
+        a, r = att[..., 0:3], att[..., 3]
+        m = att[..., 4] if metallic else torch.zeros_like(att[..., 4])
+        n = shade._normalize((b[..., None] * nvert).sum(-2))
+        ti = (b[..., None] * tvert).sum(-2)
+        T = shade._normalize(ti - shade._dot(n, ti)[..., None] * n)
+        s = sgn_f[..., None]
+        B = {"swap": s * torch.linalg.cross(n, T), "flip": -s * torch.linalg.cross(n, T),
+             "no_sign": torch.linalg.cross(n, T)}[kind]
+        nt = shade._normalize(att[..., 5:8])
+        if kind == "swap":
+            T, B = B, T
+        return T * nt[..., 0:1] + B * nt[..., 1:2] + n * nt[..., 2:3], a, r, m
+    return material
+
+
+@pytest.mark.parametrize("kind", ["swap", "flip", "no_sign"])
+def test_normal_map_pins_catch_planted_mistakes(kind, monkeypatch):
+    """A T/B swap, a flipped B or a dropped handedness sign planted in the oracle's Eq. 11 each
+    fails the pins above."""
+    monkeypatch.setattr(shade, "_material", _planted(kind))
+    with pytest.raises(AssertionError):
+        _normal_map_pins()
+
+
 def _frame(n):
     n = n / np.linalg.norm(n)
     return torch.tensor(n)

@@ -99,3 +99,25 @@ def test_face_render_counts_match_the_raster():
     ref = np.bincount((k & np.uint64(0xFFFFFFFF)).astype(np.int64), minlength=sc.F.shape[0])
     assert np.array_equal(counts.cpu().numpy(), ref)
     assert (ref == 0).any() and (ref > 0).any()
+
+
+@pytest.mark.parametrize("max_faces", [4, 5, 6])
+def test_topology_face_budget_hand_worked(max_faces):
+    """The hand-worked budget case of the oracle's pins (a +2 split ranked before a +1 split):
+    the GPU keeps the same prefix of the accepted splits."""
+    from paper_2608_24109_b300 import native as N
+    V = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [3, 0, 0], [4, 0, 0], [3, 1, 0]], f32)
+    F = np.array([[0, 1, 2], [0, 2, 3], [4, 5, 6]], np.int32)
+    grad = np.zeros((7, 3), f32)
+    grad[0:3] = [1, 0, 0]
+    grad[4:7] = [0.5, 0, 0]
+    mesh = (V, F, V[:, :2].copy(), F.copy())
+    G = np.zeros(7, f32)
+    counts = np.ones(3, np.int64)
+    prm = T.TopoParams(split_percent=100, max_faces=max_faces)
+    ctx = N.exm_create(0)
+    (Vg, Fg, UVg, Fuvg, Gg), st = _run_gpu(ctx, mesh, G, grad, counts, prm)
+    N.exm_destroy(ctx)
+    Vo, Fo, UVo, Fuvo, Go, sto = T.topology_round(*mesh, G, grad, counts, prm)
+    assert st == sto and st["splits"] == {4: 0, 5: 1, 6: 2}[max_faces]
+    assert np.array_equal(Fg, Fo) and np.array_equal(Vg.view(np.uint32), Vo.view(np.uint32))

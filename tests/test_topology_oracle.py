@@ -138,3 +138,32 @@ def test_round_invariants_on_a_closed_mesh():
     nf2 = sc.F.shape[0] + 2 * st["splits"] - st["faces_deleted"]
     assert F2.shape[0] == nf2
     assert V2.shape[0] == sc.V.shape[0] + st["splits"] - st["merges"]
+
+
+def _budget_case():
+    # a quad (faces 0, 1) and a lone triangle (face 2).  Rank order: face 0 (its diagonal, shared
+    # with face 1: +2 faces), face 1 (claimed by face 0's split), face 2 (its hypotenuse, a
+    # boundary edge: +1 face).  So the accepted splits are [face 0 (+2), face 2 (+1)]
+    V = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0], [3, 0, 0], [4, 0, 0], [3, 1, 0]], f32)
+    F = np.array([[0, 1, 2], [0, 2, 3], [4, 5, 6]])
+    grad = np.zeros((7, 3), f32)
+    grad[0:3] = [1, 0, 0]
+    grad[4:7] = [0.5, 0, 0]
+    return V, F, V[:, :2].copy(), F.copy(), grad
+
+
+def test_face_budget_keeps_the_prefix_of_the_accepted_splits():
+    """R40's budget rule, hand-worked where the two readings of "max 200K faces" differ: with
+    room for one more face, skipping the +2 split and taking the later +1 split would give one
+    split; keeping the prefix of the accepted splits that fits gives none.  With room for two
+    faces the first split fits and the second does not; with room for three both fit."""
+    V, F, UV, Fuv, grad = _budget_case()
+    expect = {4: (0, 3), 5: (1, 5), 6: (2, 6)}
+    for max_faces, (splits, faces) in expect.items():
+        prm = T.TopoParams(split_percent=100, max_faces=max_faces)
+        V2, F2, UV2, Fuv2, G2, st = T.topology_round(V, F, UV, Fuv, np.zeros(7, f32), grad, np.ones(3), prm)
+        assert (st["splits"], F2.shape[0]) == (splits, faces), max_faces
+    # with room for two faces the applied split is face 0's diagonal (new vertex at the centre)
+    prm = T.TopoParams(split_percent=100, max_faces=5)
+    V2, F2, *_ = T.topology_round(V, F, UV, Fuv, np.zeros(7, f32), grad, np.ones(3), prm)
+    assert np.array_equal(V2[7], f32([0.5, 0.5, 0]))
