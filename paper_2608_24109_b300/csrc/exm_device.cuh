@@ -464,54 +464,102 @@ __device__ __forceinline__ Footprint footprint(const MapView& m, float u, float 
     return f;
 }
 
-// Footprint from texel-space coordinates s = u W - 1/2, t = v H - 1/2 held in FP64 (the
-// shading point's texel position keeps sub-1e-6-texel accuracy even on 4096^2 maps).
-__device__ __forceinline__ Footprint footprint_d(const MapView& m, double s, double t) {
-    Footprint f;
-    double i0d = floor(s), j0d = floor(t);
-    f.fs = (float)(s - i0d);
-    f.ft = (float)(t - j0d);
-    long long i0 = (long long)fmax(fmin(i0d, 1e15), -1e15), j0 = (long long)fmax(fmin(j0d, 1e15), -1e15);
-    int c0, c1;
-    if (m.wrap_u) {
-        long long w = i0 % m.W;
-        if (w < 0) w += m.W;
-        c0 = (int)w;
-        c1 = c0 + 1 == m.W ? 0 : c0 + 1;
-    } else {
-        c0 = (int)min(max(i0, 0ll), (long long)m.W - 1);
-        c1 = (int)min(max(i0 + 1, 0ll), (long long)m.W - 1);
+// ------------------------------------------- float-float shading geometry (accuracy only)
+// The barycentrics of a shading point must be accurate to ~1e-7 relative: narrow GGX lobes
+// amplify their error ~50x into radiance.  In plain FP32 they are not -- the ray origin lies
+// |o - p0| ~ 3 units from a triangle whose edges are ~0.004 units, and the triple products of
+// Moller-Trumbore cancel ~1000-fold -- so they are evaluated in float-float ("double-word")
+// arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2, and the operations are the
+// error-free transformations TwoSum (Knuth) and TwoProd (one FMA) composed as in Joldes,
+// Muller and Popescu, "Tight and rigorous error bounds for basic building blocks of
+// double-word arithmetic" (ACM TOMS 2017): relative errors of a few 2^-48.  No decision
+// depends on these values.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff(float a) { return FF{a, 0.0f}; }
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return FF{s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b) {  // exponent of a >= exponent of b
+    const float s = __fadd_rn(a, b);
+    return FF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return FF{p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+// sum of two double-words (the accurate algorithm, relative error <= 3 u^2)
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+    const FF s = ff_two_sum(a.hi, b.hi);
+    const FF t = ff_two_sum(a.lo, b.lo);
+    const FF v = ff_fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+    return ff_fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, ff_neg(b)); }
+// product of two double-words (relative error <= 5 u^2)
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const FF c = ff_two_prod(a.hi, b.hi);
+    const float t = __fmaf_rn(a.lo, b.hi, __fmul_rn(a.hi, b.lo));
+    return ff_fast_two_sum(c.hi, __fadd_rn(c.lo, t));
+}
+// double-word times float (relative error <= 2 u^2)
+__device__ __forceinline__ FF ff_mul_f(FF a, float b) {
+    const FF c = ff_two_prod(a.hi, b);
+    return ff_fast_two_sum(c.hi, __fmaf_rn(a.lo, b, c.lo));
+}
+// quotient of two double-words (one correction of the float quotient)
+__device__ __forceinline__ FF ff_div(FF a, FF b) {
+    const float th = __fdiv_rn(a.hi, b.hi);
+    const FF r = ff_mul_f(b, th);
+    const float d = __fadd_rn(__fsub_rn(a.hi, r.hi), __fsub_rn(a.lo, r.lo));
+    return ff_fast_two_sum(th, __fdiv_rn(d, b.hi));
+}
+__device__ __forceinline__ float ff_f(FF a) { return __fadd_rn(a.hi, a.lo); }
+
+struct FF3 { FF x, y, z; };
+__device__ __forceinline__ FF3 ff3_sub(float3 a, float3 b) {  // exact
+    return FF3{ff_two_sum(a.x, -b.x), ff_two_sum(a.y, -b.y), ff_two_sum(a.z, -b.z)};
+}
+__device__ __forceinline__ FF3 ff3_cross(FF3 a, FF3 b) {
+    return FF3{ff_sub(ff_mul(a.y, b.z), ff_mul(a.z, b.y)), ff_sub(ff_mul(a.z, b.x), ff_mul(a.x, b.z)),
+               ff_sub(ff_mul(a.x, b.y), ff_mul(a.y, b.x))};
+}
+__device__ __forceinline__ FF ff3_dot(FF3 a, FF3 b) {
+    return ff_add(ff_add(ff_mul(a.x, b.x), ff_mul(a.y, b.y)), ff_mul(a.z, b.z));
+}
+
+// Moller-Trumbore barycentrics of the ray o + t d on (p0, p1, p2): b1 = (s . (d x e2)) / det,
+// b2 = (d . (s x e1)) / det with s = o - p0, e1 = p1 - p0, e2 = p2 - p0, det = e1 . (d x e2);
+// b0 = 1 - b1 - b2.  The differences of float inputs are exact double-words.
+__device__ __forceinline__ void bary_ff(FF3 s, FF3 d, float3 p0, float3 p1, float3 p2, FF b[3]) {
+    const FF3 e1 = ff3_sub(p1, p0), e2 = ff3_sub(p2, p0);
+    const FF3 pv = ff3_cross(d, e2);
+    const FF det = ff3_dot(e1, pv);
+    b[1] = ff_div(ff3_dot(s, pv), det);
+    b[2] = ff_div(ff3_dot(d, ff3_cross(s, e1)), det);
+    b[0] = ff_sub(ff_sub(ff(1.0f), b[1]), b[2]);
+}
+
+// Texel-space coordinate (b0 c0 + b1 c1 + b2 c2) * n - 1/2 of a UV component c at double-word
+// barycentrics, split into floor and fraction (the fraction to ~1e-7 of a texel on 4096^2
+// maps, where a float coordinate would keep only 5e-4).
+__device__ __forceinline__ void texel_coord(const FF b[3], float c0, float c1, float c2, int n, int* i0, float* frac) {
+    FF x = ff_add(ff_add(ff_mul_f(b[0], c0), ff_mul_f(b[1], c1)), ff_mul_f(b[2], c2));
+    x = ff_add(ff_mul_f(x, (float)n), ff(-0.5f));
+    float fl = floorf(x.hi);
+    float fr = __fadd_rn(__fsub_rn(x.hi, fl), x.lo);  // x.hi - fl is exact
+    if (fr < 0.0f) {  // x.hi an integer and x.lo < 0
+        fl = __fsub_rn(fl, 1.0f);
+        fr = __fadd_rn(fr, 1.0f);
     }
-    int r0 = (int)min(max(j0, 0ll), (long long)m.H - 1), r1 = (int)min(max(j0 + 1, 0ll), (long long)m.H - 1);
-    f.t[0] = (uint32_t)r0 * m.W + c0;
-    f.t[1] = (uint32_t)r0 * m.W + c1;
-    f.t[2] = (uint32_t)r1 * m.W + c0;
-    f.t[3] = (uint32_t)r1 * m.W + c1;
-    return f;
-}
-
-// ------------------------------------------------- FP64 shading geometry (accuracy only)
-// Barycentrics of the shading point are evaluated in FP64: FP32 ray directions alone put
-// ~1e-5 relative error into the barycentrics of 0.01-unit triangles, which narrow GGX
-// lobes amplify ~50x into radiance.  No decision depends on these values.
-struct D3 { double x, y, z; };
-__device__ __forceinline__ D3 d3(double x, double y, double z) { return D3{x, y, z}; }
-__device__ __forceinline__ D3 dsub(D3 a, D3 b) { return d3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ double ddot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ D3 dcross(D3 a, D3 b) {
-    return d3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ D3 dof(float3 a) { return d3(a.x, a.y, a.z); }
-
-// Moller-Trumbore barycentrics of the ray o + t d on (p0, p1, p2) in FP64.
-__device__ __forceinline__ void bary_d(D3 o, D3 d, D3 p0, D3 p1, D3 p2, double b[3]) {
-    D3 e1 = dsub(p1, p0), e2 = dsub(p2, p0);
-    D3 pv = dcross(d, e2);
-    double inv = 1.0 / ddot(e1, pv);
-    D3 s = dsub(o, p0);
-    double b1 = ddot(s, pv) * inv;
-    double b2 = ddot(d, dcross(s, e1)) * inv;
-    b[0] = 1.0 - b1 - b2; b[1] = b1; b[2] = b2;
+    if (fr >= 1.0f) {
+        fl = __fadd_rn(fl, 1.0f);
+        fr = 0.0f;
+    }
+    *i0 = (int)fmaxf(fminf(fl, 1e9f), -1e9f);
+    *frac = fr;
 }
 
 template <typename T>

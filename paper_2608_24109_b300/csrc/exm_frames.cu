@@ -18,10 +18,16 @@ __device__ __forceinline__ float uv_sign(const float* UV, int a, int b, int c) {
 // The sums are accumulated in 64-bit fixed point (2^-40 units): integer addition is
 // associative, so the frames do not depend on the order in which faces are summed and
 // every upload of the same mesh yields bit-identical normals and tangents.
-constexpr double kFix = 1099511627776.0;  // 2^40
+// Scaling by the power of two 2^40 is exact in FP32 (no overflow for |v| < 2^87), and the
+// conversions round once, to nearest even: the same integers as rounding the exact products.
+constexpr float kFix = 0x1p40f;
+constexpr float kInvFix = 0x1p-40f;
 
 __device__ __forceinline__ void fix_add(unsigned long long* p, float v) {
-    atomicAdd(p, (unsigned long long)(long long)llrint((double)v * kFix));
+    atomicAdd(p, (unsigned long long)__float2ll_rn(__fmul_rn(v, kFix)));
+}
+__device__ __forceinline__ float fix_value(unsigned long long x) {
+    return __fmul_rn(__ll2float_rn((long long)x), kInvFix);
 }
 
 __global__ void frames_accumulate_kernel(const float* __restrict__ V, const int32_t* __restrict__ F,
@@ -63,8 +69,7 @@ __global__ void frames_accumulate_kernel(const float* __restrict__ V, const int3
 __global__ void normalize_rows_kernel(const unsigned long long* __restrict__ fix, int n, float* acc, float* out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float3 a = f3((float)((double)(long long)fix[3 * i] / kFix), (float)((double)(long long)fix[3 * i + 1] / kFix),
-                  (float)((double)(long long)fix[3 * i + 2] / kFix));
+    float3 a = f3(fix_value(fix[3 * i]), fix_value(fix[3 * i + 1]), fix_value(fix[3 * i + 2]));
     acc[3 * i] = a.x; acc[3 * i + 1] = a.y; acc[3 * i + 2] = a.z;
     float l2 = dot(a, a);
     float3 u = l2 > 0.0f ? rsqrtf(l2) * a : f3(0.0f, 0.0f, 1.0f);

@@ -647,6 +647,30 @@ __device__ __forceinline__ int enumerate_bits(const uint32_t* words, int wbase, 
     return tot;
 }
 
+// As enumerate_bits, over words [wbase, min(wbase + 32, wend)) and keeping only the bits whose
+// index lies in [lo, hi).
+__device__ __forceinline__ int enumerate_bits_in(const uint32_t* words, int wbase, int wend, int lo, int hi,
+                                                 uint16_t* list) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int n = min(32, wend - wbase);
+    uint32_t mine = 0u;
+    if (lane < n) {
+        const int b0 = (wbase + lane) * 32;  // index of the word's bit 0
+        mine = words[wbase + lane];
+        if (lo > b0) mine = lo - b0 >= 32 ? 0u : mine & (0xffffffffu << (lo - b0));
+        if (hi < b0 + 32) mine = hi <= b0 ? 0u : mine & (0xffffffffu >> (b0 + 32 - hi));
+    }
+    int tot = 0;
+    for (int k = 0; k < n; ++k) {
+        const uint32_t w = __shfl_sync(0xffffffffu, mine, k);
+        if ((w >> lane) & 1u) list[tot + __popc(w & lt)] = (uint16_t)(k * 32 + lane);
+        tot += __popc(w);
+    }
+    __syncwarp();
+    return tot;
+}
+
 // Warp sum of N values (N a power of two, at most 32).  Each step halves the values a lane
 // holds: the lanes with bit `ofs` set keep the upper half and add their partner's, the others
 // the lower half; once one value is left the remaining steps are a plain butterfly.  Lane l
@@ -673,11 +697,11 @@ __device__ __forceinline__ float warp_sum_spread(float (&v)[N]) {
     return t;
 }
 
-// Per-pixel record, computed once per covered pixel (one thread each) so that the FP64
-// shading geometry is not repeated by every lane of the warp-per-pixel kernels:
+// Per-pixel record, computed once per covered pixel (one thread each) so that the
+// double-word shading geometry is not repeated by every lane of the warp-per-pixel kernels:
 //   [0] b0 b1 b2 |eye-x|   [1] w_o.xyz fs   [2] ft i0 j0 -   [3] org.xyz ng.x   [4] ng.y ng.z - -
-// (b: FP64 barycentrics of the camera ray; (i0 + fs, j0 + ft): texel-space position of the
-// shading point; org / ng: the spec ray origin and geometric normal).
+// (b: barycentrics of the camera ray; (i0 + fs, j0 + ft): texel-space position of the shading
+// point; org / ng: the spec ray origin and geometric normal).
 __global__ void __launch_bounds__(256) pixel_prep_kernel(ShadeArgs A) {
     const uint32_t total = *A.count;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
@@ -692,26 +716,36 @@ __global__ void __launch_bounds__(256) pixel_prep_kernel(ShadeArgs A) {
         const int i0 = __ldg(A.F + 3 * f), i1 = __ldg(A.F + 3 * f + 1), i2 = __ldg(A.F + 3 * f + 2);
         const int u0 = __ldg(A.Fuv + 3 * f), u1 = __ldg(A.Fuv + 3 * f + 1), u2 = __ldg(A.Fuv + 3 * f + 2);
         const float3 P0 = ld3(A.V + 3 * i0), P1 = ld3(A.V + 3 * i1), P2 = ld3(A.V + 3 * i2);
-        const D3 eyed = d3(cam.eye[0], cam.eye[1], cam.eye[2]);
-        const double dxd = ((double)px + 0.5 - (double)cam.cx) / (double)cam.kx;
-        const double dyd = ((double)cam.cy - ((double)py + 0.5)) / (double)cam.ky;
-        const D3 dd = d3(cam.fwd[0] + dxd * cam.right[0] + dyd * cam.up[0], cam.fwd[1] + dxd * cam.right[1] + dyd * cam.up[1],
-                         cam.fwd[2] + dxd * cam.right[2] + dyd * cam.up[2]);
-        double bd[3];
-        bary_d(eyed, dd, dof(P0), dof(P1), dof(P2), bd);
-        const double sd = (bd[0] * __ldg(A.UV + 2 * u0) + bd[1] * __ldg(A.UV + 2 * u1) + bd[2] * __ldg(A.UV + 2 * u2)) *
-                              A.map.W - 0.5;
-        const double td = (bd[0] * __ldg(A.UV + 2 * u0 + 1) + bd[1] * __ldg(A.UV + 2 * u1 + 1) +
-                           bd[2] * __ldg(A.UV + 2 * u2 + 1)) * A.map.H - 0.5;
-        const double si = floor(sd), tj = floor(td);
-        const D3 vod = dsub(eyed, d3(bd[0] * P0.x + bd[1] * P1.x + bd[2] * P2.x, bd[0] * P0.y + bd[1] * P1.y + bd[2] * P2.y,
-                                     bd[0] * P0.z + bd[1] * P1.z + bd[2] * P2.z));
-        const double vold = sqrt(ddot(vod, vod));
-        const int ii = (int)fmax(fmin(si, 1e9), -1e9), jj = (int)fmax(fmin(tj, 1e9), -1e9);
+        // the camera ray through the pixel centre, d = fwd + dx right + dy up with
+        // dx = (px + 1/2 - cx) / kx and dy = (cy - py - 1/2) / ky, as double-words
+        const FF dx = ff_div(ff_two_sum((float)px + 0.5f, -cam.cx), ff(cam.kx));
+        const FF dy = ff_div(ff_two_sum(cam.cy, -((float)py + 0.5f)), ff(cam.ky));
+        FF3 d;
+        d.x = ff_add(ff_add(ff(cam.fwd[0]), ff_mul_f(dx, cam.right[0])), ff_mul_f(dy, cam.up[0]));
+        d.y = ff_add(ff_add(ff(cam.fwd[1]), ff_mul_f(dx, cam.right[1])), ff_mul_f(dy, cam.up[1]));
+        d.z = ff_add(ff_add(ff(cam.fwd[2]), ff_mul_f(dx, cam.right[2])), ff_mul_f(dy, cam.up[2]));
+        const float3 eye = f3(cam.eye[0], cam.eye[1], cam.eye[2]);
+        const FF3 so = ff3_sub(eye, P0);
+        FF b[3];
+        bary_ff(so, d, P0, P1, P2, b);
+        int ii, jj;
+        float fs, ft;
+        texel_coord(b, __ldg(A.UV + 2 * u0), __ldg(A.UV + 2 * u1), __ldg(A.UV + 2 * u2), A.map.W, &ii, &fs);
+        texel_coord(b, __ldg(A.UV + 2 * u0 + 1), __ldg(A.UV + 2 * u1 + 1), __ldg(A.UV + 2 * u2 + 1), A.map.H, &jj,
+                    &ft);
+        // view vector eye - x = (eye - p0) - b1 e1 - b2 e2 and its length
+        const FF3 e1 = ff3_sub(P1, P0), e2 = ff3_sub(P2, P0);
+        FF3 v;
+        v.x = ff_sub(so.x, ff_add(ff_mul(b[1], e1.x), ff_mul(b[2], e2.x)));
+        v.y = ff_sub(so.y, ff_add(ff_mul(b[1], e1.y), ff_mul(b[2], e2.y)));
+        v.z = ff_sub(so.z, ff_add(ff_mul(b[1], e1.z), ff_mul(b[2], e2.z)));
+        const FF l2 = ff3_dot(v, v);
+        const float r0 = __fsqrt_rn(l2.hi);  // one Newton step: |v| = r0 + (l2 - r0^2) / (2 r0)
+        const FF len = ff_fast_two_sum(r0, __fdiv_rn(ff_f(ff_sub(l2, ff_two_prod(r0, r0))), __fmul_rn(2.0f, r0)));
         float4* R = A.prec + kPrec * (size_t)i;
-        R[0] = make_float4((float)bd[0], (float)bd[1], (float)bd[2], (float)vold);
-        R[1] = make_float4((float)(vod.x / vold), (float)(vod.y / vold), (float)(vod.z / vold), (float)(sd - si));
-        R[2] = make_float4((float)(td - tj), __int_as_float(ii), __int_as_float(jj), 0.0f);
+        R[0] = make_float4(ff_f(b[0]), ff_f(b[1]), ff_f(b[2]), ff_f(len));
+        R[1] = make_float4(ff_f(ff_div(v.x, len)), ff_f(ff_div(v.y, len)), ff_f(ff_div(v.z, len)), fs);
+        R[2] = make_float4(ft, __int_as_float(ii), __int_as_float(jj), 0.0f);
         R[3] = make_float4(org.x, org.y, org.z, ngs.x);
         R[4] = make_float4(ngs.y, ngs.z, 0.0f, 0.0f);
     }
@@ -781,11 +815,21 @@ __global__ void __launch_bounds__(256) pixel_surface_kernel(ShadeArgs A) {
 // Sample loops, one warp per pixel: the forward sums the pixel's estimator (Eqs. 17-20); the
 // backward sums, over the pixel's samples, the adjoints of E (scattered per sample) and of
 // n_s, w_o, a, r and m, which shade_epilogue_kernel carries back to the maps and vertices.
+// Fields of the per-hit records of the indirect loop (one column per secondary ray of a batch of
+// 32): the forward's first seven, then the backward's hit state and its adjoint sums.
+enum : int {
+    HWB, HF_X, HF_Y, HF_Z, HN_X, HN_Y, HN_Z, kHitFwd,
+    HJ_X = kHitFwd, HJ_Y, HJ_Z, HPBS, HA_X, HA_Y, HA_Z, HM, HT_X, HT_Y, HT_Z, HB_X, HB_Y, HB_Z, HN_X2, HN_Y2, HN_Z2,
+    HNT_X, HNT_Y, HNT_Z, HQL, HFP0, HFP1, HFP2, HFP3, HFS, HFT, GFD_X, GFD_Y, GFD_Z, GNS_X, GNS_Y, GNS_Z, kHitBwd
+};
+
 template <typename T, bool BWD, bool COUNT, bool IND>
 __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) shade_kernel(ShadeArgs A) {
     __shared__ uint16_t s_list[kShadeWarps][kListMax];
+    __shared__ float hit[kShadeWarps][IND ? (BWD ? kHitBwd : kHitFwd) : 1][32];
     const int lane = threadIdx.x & 31;
-    uint16_t* list = s_list[threadIdx.x >> 5];
+    const int hw = threadIdx.x >> 5;
+    uint16_t* list = s_list[hw];
     const uint32_t total = *A.count;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     EnvView env = A.env;
@@ -855,7 +899,10 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
             __syncwarp();
         }
         if (!BWD && lane == 0) my_samples += (unsigned long long)A.Nd;
-        // ---- one-bounce indirect (Eqs. 18-19): lanes take the pixel's live (j, s) pairs
+        // ---- one-bounce indirect (Eqs. 18-19), 32 secondary rays at a time: first one lane per
+        // ray j evaluates what depends on j alone -- the direction, the hit point's double-word
+        // barycentrics, the material and frame at y -- into the warp's records; then the lanes
+        // take the live (j, s) pairs of those rays (named by the visibility bits)
         if (IND && A.Nb > 0 && A.lambda != 0.0f) {
             const float3 fdx = ((1.0f - sm) * kInvPi) * sa;
             const float scale = A.lambda / (float)A.Nb;
@@ -869,81 +916,147 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                 if (lane == 0) my_samples += (unsigned long long)A.Nb + (unsigned long long)valid * A.Ns;
             }
             const uint32_t* sb = A.secbits + si * A.ws;
-            for (int wbase = 0; wbase < A.ws; wbase += 32) {
-                const int tot = enumerate_bits(sb, wbase, A.ws, list);
-                for (int t0 = 0; t0 < tot; t0 += 32) {
-                    const int e = t0 + lane;
-                    if (e >= tot) continue;
-                    const int bit = wbase * 32 + list[e];
-                    const int jj = bit / A.Ns, s = bit - jj * A.Ns;
+            for (int jb = 0; jb < A.Nb; jb += 32) {
+                const int j = jb + lane;
+                const int gtri = j < A.Nb ? A.hits[si * A.Nb + j] : -1;
+                float wb = 0.0f;  // 0: no live samples (no valid hit, or n_s(x).w_j <= 0)
+                float3 fdy = f3(0.f, 0.f, 0.f), nsy = f3(0.f, 0.f, 1.f);
+                if (gtri >= 0) {
                     float xi1;
-                    const S3 wjs = secondary_dir(A, rem, c, jj, ngs, &xi1);
+                    const S3 wjs = secondary_dir(A, rem, c, j, ngs, &xi1);
                     const float3 wj = normalize(tof(wjs));
                     const float cxj = dot(sns, wj);
-                    if (cxj <= 0.0f) continue;
-                    const int gtri = A.hits[si * A.Nb + jj];
-                    S3 ys, ngy, yorg;
-                    float3 Q[3];
-                    secondary_point(A, gtri, org, wjs, &ys, &ngy, &yorg, Q);
-                    double byd[3];
-                    bary_d(d3(org.x, org.y, org.z), d3(wjs.x, wjs.y, wjs.z), dof(Q[0]), dof(Q[1]), dof(Q[2]), byd);
-                    const float by[3] = {(float)byd[0], (float)byd[1], (float)byd[2]};
-                    const int v0 = __ldg(A.Fuv + 3 * gtri), v1 = __ldg(A.Fuv + 3 * gtri + 1), v2 = __ldg(A.Fuv + 3 * gtri + 2);
-                    const int q0 = __ldg(A.F + 3 * gtri), q1 = __ldg(A.F + 3 * gtri + 1), q2 = __ldg(A.F + 3 * gtri + 2);
-                    const double syd = (byd[0] * __ldg(A.UV + 2 * v0) + byd[1] * __ldg(A.UV + 2 * v1) +
-                                        byd[2] * __ldg(A.UV + 2 * v2)) * A.map.W - 0.5;
-                    const double tyd = (byd[0] * __ldg(A.UV + 2 * v0 + 1) + byd[1] * __ldg(A.UV + 2 * v1 + 1) +
-                                        byd[2] * __ldg(A.UV + 2 * v2 + 1)) * A.map.H - 0.5;
-                    const Footprint fpy = footprint_d(A.map, syd, tyd);
-                    float atty[8];
-                    if (A.sec_material) {
-                        fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
-                    } else {
-                        // constant default material: grey diffuse, flat tangent-space normal
-                        atty[0] = atty[1] = atty[2] = 0.5f;
-                        atty[3] = 0.5f;
-                        atty[4] = 0.0f;
-                        atty[5] = atty[6] = 0.0f;
-                        atty[7] = 1.0f;
+                    if (cxj > 0.0f) {
+                        const float pbs = scale * (kPi / __fsqrt_rn(ssub(1.0f, xi1)));  // lambda / (N_b p_b)
+                        wb = pbs * cxj;
+                        const int q0 = __ldg(A.F + 3 * gtri), q1 = __ldg(A.F + 3 * gtri + 1), q2 = __ldg(A.F + 3 * gtri + 2);
+                        const int v0 = __ldg(A.Fuv + 3 * gtri), v1 = __ldg(A.Fuv + 3 * gtri + 1), v2 = __ldg(A.Fuv + 3 * gtri + 2);
+                        const float3 Q0 = ld3(A.V + 3 * q0), Q1 = ld3(A.V + 3 * q1), Q2 = ld3(A.V + 3 * q2);
+                        FF by[3];
+                        bary_ff(ff3_sub(f3(org.x, org.y, org.z), Q0), FF3{ff(wjs.x), ff(wjs.y), ff(wjs.z)}, Q0, Q1, Q2, by);
+                        int ti, tj;
+                        float fs, ft;
+                        texel_coord(by, __ldg(A.UV + 2 * v0), __ldg(A.UV + 2 * v1), __ldg(A.UV + 2 * v2), A.map.W, &ti, &fs);
+                        texel_coord(by, __ldg(A.UV + 2 * v0 + 1), __ldg(A.UV + 2 * v1 + 1), __ldg(A.UV + 2 * v2 + 1),
+                                    A.map.H, &tj, &ft);
+                        const Footprint fpy = footprint_i(A.map, ti, tj, fs, ft);
+                        float atty[8];
+                        if (A.sec_material) {
+                            fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
+                        } else {
+                            // constant default material: grey diffuse, flat tangent-space normal
+                            atty[0] = atty[1] = atty[2] = 0.5f;
+                            atty[3] = 0.5f;
+                            atty[4] = 0.0f;
+                            atty[5] = atty[6] = 0.0f;
+                            atty[7] = 1.0f;
+                        }
+                        const float b0 = ff_f(by[0]), b1 = ff_f(by[1]), b2 = ff_f(by[2]);
+                        const float3 niy = b0 * ld3(A.nrm + 3 * q0) + b1 * ld3(A.nrm + 3 * q1) + b2 * ld3(A.nrm + 3 * q2);
+                        const float3 tiy = b0 * ld3(A.tan + 3 * v0) + b1 * ld3(A.tan + 3 * v1) + b2 * ld3(A.tan + 3 * v2);
+                        const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
+                        fdy = ((1.0f - sy.m) * kInvPi) * sy.a;
+                        nsy = sy.ns;
+                        if (BWD) {
+                            float (*hr)[32] = hit[hw];
+                            hr[HJ_X][lane] = wj.x; hr[HJ_Y][lane] = wj.y; hr[HJ_Z][lane] = wj.z;
+                            hr[HPBS][lane] = pbs;
+                            hr[HA_X][lane] = sy.a.x; hr[HA_Y][lane] = sy.a.y; hr[HA_Z][lane] = sy.a.z;
+                            hr[HM][lane] = sy.m;
+                            hr[HT_X][lane] = sy.T.x; hr[HT_Y][lane] = sy.T.y; hr[HT_Z][lane] = sy.T.z;
+                            hr[HB_X][lane] = sy.B.x; hr[HB_Y][lane] = sy.B.y; hr[HB_Z][lane] = sy.B.z;
+                            hr[HN_X2][lane] = sy.n.x; hr[HN_Y2][lane] = sy.n.y; hr[HN_Z2][lane] = sy.n.z;
+                            hr[HNT_X][lane] = sy.nt.x; hr[HNT_Y][lane] = sy.nt.y; hr[HNT_Z][lane] = sy.nt.z;
+                            hr[HQL][lane] = sy.ql;
+                            hr[HFP0][lane] = __uint_as_float(fpy.t[0]); hr[HFP1][lane] = __uint_as_float(fpy.t[1]);
+                            hr[HFP2][lane] = __uint_as_float(fpy.t[2]); hr[HFP3][lane] = __uint_as_float(fpy.t[3]);
+                            hr[HFS][lane] = fpy.fs; hr[HFT][lane] = fpy.ft;
+                            hr[GFD_X][lane] = 0.f; hr[GFD_Y][lane] = 0.f; hr[GFD_Z][lane] = 0.f;
+                            hr[GNS_X][lane] = 0.f; hr[GNS_Y][lane] = 0.f; hr[GNS_Z][lane] = 0.f;
+                        }
                     }
-                    const float3 niy = by[0] * ld3(A.nrm + 3 * q0) + by[1] * ld3(A.nrm + 3 * q1) + by[2] * ld3(A.nrm + 3 * q2);
-                    const float3 tiy = by[0] * ld3(A.tan + 3 * v0) + by[1] * ld3(A.tan + 3 * v1) + by[2] * ld3(A.tan + 3 * v2);
-                    const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
-                    const float3 fdy = ((1.0f - sy.m) * kInvPi) * sy.a;
-                    const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
-                    const LightSample ls = light_sample(env, h2, (uint32_t)s, A.nxs, A.nys);
-                    const float3 wl = normalize(tof(ls.dir));
-                    const float cs = dot(sy.ns, wl);
-                    if (cs <= 0.0f) continue;
-                    ++c_brdf;
-                    const float pb_inv = kPi / __fsqrt_rn(ssub(1.0f, xi1));  // 1 / p_b
-                    const float wb = scale * cxj * pb_inv;
-                    const float term = ls.inv_pdf * invNs * cs;
-                    const float3 ET = term * ls.E;
-                    if (!BWD) {
-                        L += wb * (fdx * (fdy * ET));
-                    } else {
-                        // E of the light sample
-                        const float3 gE = (wb * term) * (g * (fdx * fdy));
-                        atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
-                        // f_d(x) and n_s(x) through max(n_s(x).w_j, 0)
-                        const float3 gfdx = wb * (g * (fdy * ET));
-                        ga += ((1.0f - sm) * kInvPi) * gfdx;
-                        gm += -dot(gfdx, sa) * kInvPi;
-                        gns += (scale * pb_inv * dot(g, fdx * (fdy * ET))) * wj;
-                        // material at y (its geometry is a constant of the derivative)
-                        const float3 gLsec = wb * (g * fdx);
-                        const float3 gfdy = gLsec * ET;
-                        const float3 gnsy = (ls.inv_pdf * invNs * dot(gLsec, fdy * ls.E)) * wl;
-                        float gy[8];
-                        const float3 gay = ((1.0f - sy.m) * kInvPi) * gfdy;
-                        gy[0] = gay.x; gy[1] = gay.y; gy[2] = gay.z; gy[3] = 0.0f;
-                        gy[4] = A.metallic ? -dot(gfdy, sy.a) * kInvPi : 0.0f;
-                        const float3 gnt = f3(dot(sy.T, gnsy), dot(sy.B, gnsy), dot(sy.n, gnsy));
-                        const float3 gq = (1.0f / sy.ql) * (gnt - dot(gnt, sy.nt) * sy.nt);
-                        gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
-                        if (A.gmaps && A.sec_material) scatter8(A.gmaps, fpy, gy);
+                }
+                {
+                    float (*hr)[32] = hit[hw];
+                    hr[HWB][lane] = wb;
+                    hr[HF_X][lane] = fdy.x; hr[HF_Y][lane] = fdy.y; hr[HF_Z][lane] = fdy.z;
+                    hr[HN_X][lane] = nsy.x; hr[HN_Y][lane] = nsy.y; hr[HN_Z][lane] = nsy.z;
+                }
+                __syncwarp();
+                // the live (j, s) of rays jb .. jend - 1: bits [jb N_s, jend N_s)
+                const int jend = min(jb + 32, A.Nb);
+                const int blo = jb * A.Ns, bhi = jend * A.Ns;
+                for (int wbase = blo >> 5; wbase < ((bhi + 31) >> 5); wbase += 32) {
+                    const int tot = enumerate_bits_in(sb, wbase, (bhi + 31) >> 5, blo, bhi, list);
+                    for (int t0 = 0; t0 < tot; t0 += 32) {
+                        const int e = t0 + lane;
+                        if (e >= tot) continue;
+                        const int bit = wbase * 32 + list[e];
+                        const int jj = bit / A.Ns, s = bit - jj * A.Ns;
+                        const float (*hr)[32] = hit[hw];
+                        const int hl = jj - jb;
+                        const float wbj = hr[HWB][hl];
+                        if (wbj == 0.0f) continue;
+                        const float3 fdyj = f3(hr[HF_X][hl], hr[HF_Y][hl], hr[HF_Z][hl]);
+                        const float3 nsyj = f3(hr[HN_X][hl], hr[HN_Y][hl], hr[HN_Z][hl]);
+                        const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
+                        const LightSample ls = light_sample(env, h2, (uint32_t)s, A.nxs, A.nys);
+                        const float3 wl = normalize(tof(ls.dir));
+                        const float cs = dot(nsyj, wl);
+                        if (cs <= 0.0f) continue;
+                        ++c_brdf;
+                        const float term = ls.inv_pdf * invNs * cs;
+                        const float3 ET = term * ls.E;
+                        if (!BWD) {
+                            L += wbj * (fdx * (fdyj * ET));
+                        } else {
+                            // E of the light sample
+                            const float3 gE = (wbj * term) * (g * (fdx * fdyj));
+                            atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
+                            // f_d(x) and n_s(x) through max(n_s(x).w_j, 0)
+                            const float3 gfdx = wbj * (g * (fdyj * ET));
+                            ga += ((1.0f - sm) * kInvPi) * gfdx;
+                            gm += -dot(gfdx, sa) * kInvPi;
+                            gns += (hr[HPBS][hl] * dot(g, fdx * (fdyj * ET))) * f3(hr[HJ_X][hl], hr[HJ_Y][hl], hr[HJ_Z][hl]);
+                            // the material at y (its geometry is a constant of the derivative): the
+                            // adjoints of f_d(y) and n_s(y), summed per hit
+                            const float3 gLsec = wbj * (g * fdx);
+                            const float3 gfdy = gLsec * ET;
+                            const float3 gnsy = (ls.inv_pdf * invNs * dot(gLsec, fdyj * ls.E)) * wl;
+                            float (*hw_acc)[32] = hit[hw];
+                            atomicAdd(&hw_acc[GFD_X][hl], gfdy.x);
+                            atomicAdd(&hw_acc[GFD_Y][hl], gfdy.y);
+                            atomicAdd(&hw_acc[GFD_Z][hl], gfdy.z);
+                            atomicAdd(&hw_acc[GNS_X][hl], gnsy.x);
+                            atomicAdd(&hw_acc[GNS_Y][hl], gnsy.y);
+                            atomicAdd(&hw_acc[GNS_Z][hl], gnsy.z);
+                        }
                     }
+                    __syncwarp();
+                }
+                // backward: each hit's summed material adjoint to its map footprint, once
+                if (BWD && wb != 0.0f && A.gmaps && A.sec_material) {
+                    const float (*hr)[32] = hit[hw];
+                    const float3 gfd = f3(hr[GFD_X][lane], hr[GFD_Y][lane], hr[GFD_Z][lane]);
+                    const float3 gny = f3(hr[GNS_X][lane], hr[GNS_Y][lane], hr[GNS_Z][lane]);
+                    const float my = hr[HM][lane];
+                    const float3 ay = f3(hr[HA_X][lane], hr[HA_Y][lane], hr[HA_Z][lane]);
+                    const float3 nty = f3(hr[HNT_X][lane], hr[HNT_Y][lane], hr[HNT_Z][lane]);
+                    float gy[8];
+                    const float3 gay = ((1.0f - my) * kInvPi) * gfd;
+                    gy[0] = gay.x; gy[1] = gay.y; gy[2] = gay.z; gy[3] = 0.0f;
+                    gy[4] = A.metallic ? -dot(gfd, ay) * kInvPi : 0.0f;
+                    const float3 gnt = f3(dot(f3(hr[HT_X][lane], hr[HT_Y][lane], hr[HT_Z][lane]), gny),
+                                          dot(f3(hr[HB_X][lane], hr[HB_Y][lane], hr[HB_Z][lane]), gny),
+                                          dot(f3(hr[HN_X2][lane], hr[HN_Y2][lane], hr[HN_Z2][lane]), gny));
+                    const float3 gq = (1.0f / hr[HQL][lane]) * (gnt - dot(gnt, nty) * nty);
+                    gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
+                    Footprint fpy;
+                    fpy.t[0] = __float_as_uint(hr[HFP0][lane]); fpy.t[1] = __float_as_uint(hr[HFP1][lane]);
+                    fpy.t[2] = __float_as_uint(hr[HFP2][lane]); fpy.t[3] = __float_as_uint(hr[HFP3][lane]);
+                    fpy.fs = hr[HFS][lane];
+                    fpy.ft = hr[HFT][lane];
+                    scatter8(A.gmaps, fpy, gy);
                 }
                 __syncwarp();
             }

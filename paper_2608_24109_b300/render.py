@@ -104,7 +104,7 @@ class Renderer:
 
         def grab(ptr, shape, typestr):
             class _View:
-                __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, True), "version": 3,
+                __cuda_array_interface__ = {"shape": shape, "typestr": typestr, "data": (ptr, False), "version": 3,
                                             "strides": None}
             return torch.as_tensor(_View(), device=self.device).clone()
 
