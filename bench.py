@@ -46,6 +46,8 @@ RAY_BYTES = 32.0
 TRACE_NCU = {
     "geometry": {"dram_bytes_per_ray": 33.3, "l2_frac": 0.057, "issue_frac": 0.627,
                  "source": "ncu, any-hit launch of the 2-view geometry case"},
+    "precision": {"dram_bytes_per_ray": 40.1, "l2_frac": 0.100, "issue_frac": 0.523, "l1_frac": 0.926,
+                  "source": "ncu, any-hit launch of the 1-view precision case"},
 }
 RAY_QUEUE_MAX = 1 << 27  # rays per chunk at most (the library's default queue)
 # covered pixels of the CPU-baseline sample per workload: about 10-30 s of oracle work on 16 cores
@@ -458,7 +460,7 @@ def run_native(args, world, rank, local):
     traffic = fractions = None
     if ncu is not None and not args.views and not args.half_res_indirect:
         fractions = {"hbm_measured": ncu["dram_bytes_per_ray"] * rays / (trace_ms * 1e-3) / (hbm * 1e9),
-                     "l2_ncu": ncu["l2_frac"], "issue_slots_ncu": ncu["issue_frac"],
+                     "l2_ncu": ncu["l2_frac"], "issue_slots_ncu": ncu["issue_frac"], "l1_ncu": ncu.get("l1_frac"),
                      "fp32_scope_model": flops_model / (trace_ms * 1e-3) / 1e12 / fp32_peak,
                      "fp32_own_model": flops_own / (trace_ms * 1e-3) / 1e12 / fp32_peak,
                      "algorithmic_bytes_gbs": algo_bytes / (trace_ms * 1e-3) / 1e9,
