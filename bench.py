@@ -761,6 +761,7 @@ def run_relight(args, world, rank, local):
                 done_at[k] = tnow
     torch.cuda.synchronize()
     ck = clocks.stop()
+    batches, batched = srv.batches()
     meas = list(range(args.warmup * 8, total))
     L = np.array([lat[k] for k in meas])
     span = max(done_at[k] for k in meas) - arrivals[meas[0]]
@@ -772,7 +773,9 @@ def run_relight(args, world, rank, local):
             "config": {"workload": f"relight serving: {args.assets} resident assets, 10K-2M tris (log-uniform, "
                                    f"{min(tris)}-{max(tris)}), maps 512^2-4096^2 BF16, env 256x128-1024x512, "
                                    f"outputs 256^2-1024^2, 64 direct + 4 secondary x 4 light samples/px, Poisson "
-                                   f"arrivals", "slots": args.slots, "hbm_budget_gb": args.budget_gb},
+                                   f"arrivals", "slots": args.slots, "hbm_budget_gb": args.budget_gb,
+                       "batching": f"{batched} requests in {batches} batches (persistent tracer launches shared "
+                                   "by the requests of a batch)"},
             "clocks": ck}
     print(json.dumps(line), flush=True)
     srv.close()

@@ -41,10 +41,11 @@ typedef int exm_status;
 #define EXM_ERR_GUARDBAND (-4)       /* a vertex behind the near plane / outside +-16384 px,
                                         or a front face with doubled area >= 2^38 (1/256 px units) */
 #define EXM_ERR_TRAVERSAL_LIMIT (-5) /* a BVH traversal exceeded its step cap (corrupt BVH) */
-#define EXM_ERR_TIMEOUT (-6)         /* a bounded device wait ran out */
+#define EXM_ERR_TIMEOUT (-6)         /* a bounded wait ran out (exm_relight_wait) */
 #define EXM_ERR_BUSY (-7)            /* admission refused: not enough budget or slots */
 #define EXM_ERR_QUEUE_OVERFLOW (-8)  /* a ray-queue chunk overflowed (exm_frame_set_limits' ray_cap below one
                                         chunk's rays); the rays beyond it were not traced */
+#define EXM_ERR_CANCELLED (-9)       /* a relight request was cancelled (exm_relight_cancel) */
 
 typedef enum { EXM_F32 = 0, EXM_BF16 = 1, EXM_F16 = 2 } exm_dtype;
 
@@ -132,6 +133,50 @@ void exm_mesh_destroy(exm_mesh* mesh);
 /* Device pointers to the mesh's per-vertex unit normals [nv,3] and per-UV-vertex unit
  * tangents [nuv,3] (read-only views, valid until the mesh changes). */
 exm_status exm_mesh_frames(const exm_mesh* mesh, const float** normals, const float** tangents);
+
+/* Asset export and import (no counterpart in the paper: the serving registry's reload path).
+ * An exported asset is the mesh-UV carrier and its BVH in EXM_ASSET_SECTIONS little-endian
+ * sections: V float32 [nv,3], F int32 [nf,3], UV float32 [nuv,2], Fuv int32 [nf,3], the BVH's
+ * 4-wide nodes (node_bytes each: child boxes lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4],
+ * then four int32 child references: >= 0 a node, < 0 the leaf ~k, 0x7fffffff an empty slot;
+ * node 0 is the root), its triangle records (three float4 per leaf: the vertices, the original
+ * face id in the first .w) and its bounding sphere (float4 centre, R^2). */
+#define EXM_ASSET_VERSION 1
+#define EXM_ASSET_SECTIONS 7
+typedef struct {
+    uint32_t version;    /* EXM_ASSET_VERSION */
+    uint32_t node_bytes; /* bytes of one BVH node (128) */
+    int32_t nv, nf, nuv;
+    uint32_t n_nodes;    /* BVH nodes */
+    uint64_t bytes[EXM_ASSET_SECTIONS];
+} exm_asset_info;
+/* Sizes of `mesh`'s export. */
+exm_status exm_mesh_export_info(const exm_mesh* mesh, exm_asset_info* info);
+/* Copies the sections into caller buffers (HOST or DEVICE, of info.bytes each); synchronous. */
+exm_status exm_mesh_export(const exm_mesh* mesh, void* const sections[EXM_ASSET_SECTIONS], void* stream);
+/* A mesh from exported sections (HOST or DEVICE; copied): the carrier's frames are computed and
+ * the imported BVH is used as it is.  Before it is used every face index and every node
+ * reference is checked to lie in range (EXM_ERR_ARG otherwise, nothing created); a tree with a
+ * cycle is not detected here, and its rays end at the traversal's caps (EXM_ERR_TRAVERSAL_LIMIT
+ * from exm_sync after a render).  Synchronous. */
+exm_status exm_mesh_import(exm_ctx* ctx, const exm_asset_info* info, const void* const sections[EXM_ASSET_SECTIONS],
+                           void* stream, exm_mesh** out);
+
+/* Host-side fault injection for failure tests (no counterpart in the paper; it makes no GPU
+ * fault).  The next `count` events of `kind` fail: EXM_FAULT_ALLOC a device allocation by the
+ * library (EXM_ERR_OOM); EXM_FAULT_ADMIT a relight submission (EXM_ERR_BUSY); EXM_FAULT_CANCEL a
+ * submitted relight request is cancelled right after it is queued (EXM_ERR_CANCELLED);
+ * EXM_FAULT_CORRUPT an imported BVH gets a cycle (the root's first node child points back to the
+ * root).  EXM_FAULT_SLOW holds every relight request `count` milliseconds on the host before
+ * its work is enqueued.  count 0 clears a kind.  The same settings come from the environment
+ * variable EXM_FAULT ("alloc:N,admit:N,slow:MS,cancel:N,corrupt:N"), read by the process's
+ * first exm_create.  Process-wide. */
+#define EXM_FAULT_ALLOC 1
+#define EXM_FAULT_ADMIT 2
+#define EXM_FAULT_SLOW 3
+#define EXM_FAULT_CANCEL 4
+#define EXM_FAULT_CORRUPT 5
+exm_status exm_debug_fault(int kind, uint32_t count);
 
 /* ------------------------------------------------------- environment (Sec. 5.2) */
 
@@ -236,11 +281,17 @@ typedef struct {
     float* out_rgb;
 } exm_relight_req;
 
-/* A relight server on `ctx`: `max_slots` request slots, each with its own CUDA stream, and an
- * HBM budget (bytes) bounding the device footprint of the requests in flight.  Requests are
- * admitted in arrival order whenever a slot is free and the head request fits the budget,
- * so requests that arrive while others run start as soon as resources free up, and the work
- * of all in-flight requests overlaps on the device. */
+/* A relight server on `ctx`: at most `max_slots` requests in flight, an HBM budget (bytes)
+ * bounding their device footprint, and min(max_slots, 3) batch streams.  Requests wait in a
+ * FIFO queue; whenever a batch stream is free, the requests at the head of the queue that find
+ * a free slot and fit the remaining budget are run as one batch on it: each request's own setup
+ * (environment distribution, raster, pixel records), then one persistent closest-hit tracer
+ * launch over all their secondary rays and one persistent any-hit tracer launch over all their
+ * shadow rays -- each ray traced through the BVH of its own asset -- and each request's shading.
+ * A request whose rays exceed one 2^27-ray queue, or that asks for half-resolution indirect
+ * light, runs its own chunked forward pass inside the batch.  Requests that arrive while a batch
+ * runs join the next batch on another stream, so batches overlap on the device.  A request's
+ * footprint counts a ray queue sized to its own rays. */
 exm_status exm_server_create(exm_ctx* ctx, uint64_t hbm_budget_bytes, int max_slots, exm_server** out);
 void exm_server_destroy(exm_server* server);
 /* Registers a resident asset (mesh with BVH and DEVICE maps [mapH, mapW, 8]); the caller
@@ -254,6 +305,15 @@ exm_status exm_relight_submit(exm_server* server, const exm_relight_req* req, ui
  * (submission to observed completion, milliseconds).  A done ticket is forgotten after the
  * call that reports it; that call returns the request's status. */
 exm_status exm_relight_poll(exm_server* server, uint64_t ticket, int* done, double* latency_ms);
+/* Cancels a request: a queued one is dropped; one in flight finishes on the device but its
+ * result is discarded (its output buffer is left undefined).  Either way the ticket reports
+ * EXM_ERR_CANCELLED.  A finished ticket keeps its result; an unknown ticket is EXM_ERR_ARG. */
+exm_status exm_relight_cancel(exm_server* server, uint64_t ticket);
+/* Waits at most timeout_ms for `ticket`, running the scheduler meanwhile: the request's status
+ * once it is done (and then forgets it, like exm_relight_poll), or EXM_ERR_TIMEOUT. */
+exm_status exm_relight_wait(exm_server* server, uint64_t ticket, double timeout_ms, double* latency_ms);
+/* Batches launched so far and the requests they held. */
+exm_status exm_server_batches(exm_server* server, uint64_t* batches, uint64_t* batched_requests);
 /* Runs the scheduler once (retire finished requests, admit queued ones). */
 exm_status exm_server_progress(exm_server* server);
 /* Queue length, requests in flight, budgeted bytes in use, requests completed. */

@@ -1,5 +1,6 @@
 // C ABI of libexmesh (include/exmesh.h): object lifetimes, argument checks, launches.
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -14,6 +15,48 @@ static std::atomic<uint64_t> g_stamp{0};
 
 uint64_t exm_next_stamp() { return ++g_stamp; }
 
+// ------------------------------------------------------------ host-side fault injection
+
+static std::atomic<uint32_t> g_fault[kFaultKinds];
+
+static void parse_fault_env() {
+    static std::atomic<bool> parsed{false};
+    if (parsed.exchange(true)) return;  // once per process
+    const char* v = getenv("EXM_FAULT");
+    if (!v) return;
+    static const char* names[kFaultKinds] = {"alloc", "admit", "slow", "cancel", "corrupt"};
+    std::string s(v);
+    size_t pos = 0;
+    while (pos < s.size()) {
+        size_t end = s.find(',', pos);
+        if (end == std::string::npos) end = s.size();
+        const std::string item = s.substr(pos, end - pos);
+        const size_t colon = item.find(':');
+        const std::string name = item.substr(0, colon);
+        const uint32_t count = colon == std::string::npos ? 1u : (uint32_t)strtoul(item.c_str() + colon + 1, nullptr, 10);
+        for (int k = 0; k < kFaultKinds; ++k)
+            if (name == names[k]) g_fault[k] = count;
+        pos = end + 1;
+    }
+}
+
+bool exm_fault_take(int kind) {
+    uint32_t c = g_fault[kind].load();
+    while (c > 0)
+        if (g_fault[kind].compare_exchange_weak(c, c - 1)) return true;
+    return false;
+}
+
+uint32_t exm_fault_value(int kind) { return g_fault[kind].load(); }
+
+cudaError_t exm_malloc(void** p, size_t bytes) {
+    if (exm_fault_take(kFaultAlloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 exm_status exm_fail(exm_status code, const std::string& msg) {
     g_last_error = msg;
     return code;
@@ -27,7 +70,7 @@ exm_status exm_cuda_check(cudaError_t e, const char* what) {
 
 #define EXM_TRY_ALLOC(ptr, bytes, what)                                              \
     do {                                                                             \
-        if (cudaMalloc((void**)&(ptr), (bytes)) != cudaSuccess) {                    \
+        if (exm_malloc((void**)&(ptr), (bytes)) != cudaSuccess) {                    \
             cudaGetLastError();                                                      \
             return exm_fail(EXM_ERR_OOM, std::string("allocation failed: ") + what); \
         }                                                                            \
@@ -69,8 +112,15 @@ extern "C" {
 
 const char* exm_last_error(void) { return g_last_error.c_str(); }
 
+exm_status exm_debug_fault(int kind, uint32_t count) {
+    if (kind < EXM_FAULT_ALLOC || kind > EXM_FAULT_CORRUPT) return exm_fail(EXM_ERR_ARG, "exm_debug_fault: kind");
+    g_fault[kind - EXM_FAULT_ALLOC] = count;
+    return EXM_OK;
+}
+
 exm_status exm_create(int device, exm_ctx** out) {
     if (!out) return exm_fail(EXM_ERR_ARG, "exm_create: out is NULL");
+    parse_fault_env();
     *out = nullptr;
     int count = 0;
     if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count)
@@ -80,7 +130,7 @@ exm_status exm_create(int device, exm_ctx** out) {
     if (!c) return exm_fail(EXM_ERR_OOM, "exm_create: host allocation");
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (cudaMalloc(&c->d_status, sizeof(uint32_t)) != cudaSuccess) {
+    if (exm_malloc((void**)&c->d_status, sizeof(uint32_t)) != cudaSuccess) {
         delete c;
         return exm_fail(EXM_ERR_OOM, "exm_create: status word");
     }
@@ -113,7 +163,6 @@ exm_status exm_sync(exm_ctx* c, void* stream) {
     if (bits & exm::ERRBIT_QUEUE)
         return exm_fail(EXM_ERR_QUEUE_OVERFLOW, "a ray queue chunk overflowed; the rays beyond it were not traced");
     if (bits & exm::ERRBIT_TRAVERSAL) return exm_fail(EXM_ERR_TRAVERSAL_LIMIT, "BVH traversal step/stack limit");
-    if (bits & exm::ERRBIT_TIMEOUT) return exm_fail(EXM_ERR_TIMEOUT, "a bounded device wait ran out");
     return EXM_OK;
 }
 
@@ -140,7 +189,7 @@ exm_status exm_mesh_create(exm_ctx* c, const float* V, int nv, const int32_t* F,
     if (!m) return exm_fail(EXM_ERR_OOM, "exm_mesh_create: host allocation");
     m->ctx = c;
     m->nv = nv; m->nf = nf; m->nuv = nuv;
-    auto alloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes) == cudaSuccess; };
+    auto alloc = [&](void** p, size_t bytes) { return exm_malloc((void**)p, bytes) == cudaSuccess; };
     bool ok = alloc((void**)&m->V, (size_t)nv * 12) && alloc((void**)&m->F, (size_t)nf * 12) &&
               alloc((void**)&m->UV, (size_t)nuv * 8) && alloc((void**)&m->Fuv, (size_t)nf * 12) &&
               alloc((void**)&m->nacc, (size_t)nv * 12) && alloc((void**)&m->nrm, (size_t)nv * 12) &&
@@ -224,11 +273,11 @@ exm_status exm_env_create(exm_ctx* c, int W, int H, exm_env** out) {
     e->rbits = rb + 1;
     e->cbits = cb + 1;
     size_t Gr = ((size_t)1 << e->rbits) + 1, Gc = (size_t)H * (((size_t)1 << e->cbits) + 1);
-    bool ok = cudaMalloc(&e->texel, n * sizeof(float4)) == cudaSuccess && cudaMalloc(&e->q, n * 4) == cudaSuccess &&
-              cudaMalloc(&e->cdf, n * 8) == cudaSuccess && cudaMalloc(&e->rowsum, (size_t)H * 8) == cudaSuccess &&
-              cudaMalloc(&e->rowpre, (size_t)H * 8) == cudaSuccess && cudaMalloc(&e->rguide, Gr * 4) == cudaSuccess &&
-              cudaMalloc(&e->cguide, Gc * 4) == cudaSuccess && cudaMalloc(&e->wbuf, n * 4) == cudaSuccess &&
-              cudaMalloc(&e->wmax, 4) == cudaSuccess && cudaMalloc(&e->total, 8) == cudaSuccess;
+    bool ok = exm_malloc((void**)&e->texel, n * sizeof(float4)) == cudaSuccess && exm_malloc((void**)&e->q, n * 4) == cudaSuccess &&
+              exm_malloc((void**)&e->cdf, n * 8) == cudaSuccess && exm_malloc((void**)&e->rowsum, (size_t)H * 8) == cudaSuccess &&
+              exm_malloc((void**)&e->rowpre, (size_t)H * 8) == cudaSuccess && exm_malloc((void**)&e->rguide, Gr * 4) == cudaSuccess &&
+              exm_malloc((void**)&e->cguide, Gc * 4) == cudaSuccess && exm_malloc((void**)&e->wbuf, n * 4) == cudaSuccess &&
+              exm_malloc((void**)&e->wmax, 4) == cudaSuccess && exm_malloc((void**)&e->total, 8) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         env_free(e);
@@ -291,10 +340,10 @@ exm_status exm_frame_create(exm_ctx* c, int views, int width, int height, exm_fr
     f->ctx = c;
     f->views = views; f->W = width; f->H = height;
     size_t n = (size_t)views * width * height;
-    bool ok = cudaMalloc(&f->visbuf, n * 8) == cudaSuccess && cudaMalloc(&f->pixels, n * 4) == cudaSuccess &&
-              cudaMalloc(&f->counters, 16) == cudaSuccess && cudaMalloc(&f->samples, 8) == cudaSuccess &&
-              cudaMalloc(&f->work, 32) == cudaSuccess &&
-              cudaMalloc(&f->cams, (size_t)views * sizeof(exm_camera)) == cudaSuccess;
+    bool ok = exm_malloc((void**)&f->visbuf, n * 8) == cudaSuccess && exm_malloc((void**)&f->pixels, n * 4) == cudaSuccess &&
+              exm_malloc((void**)&f->counters, 16) == cudaSuccess && exm_malloc((void**)&f->samples, 8) == cudaSuccess &&
+              exm_malloc((void**)&f->work, 32) == cudaSuccess &&
+              exm_malloc((void**)&f->cams, (size_t)views * sizeof(exm_camera)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         frame_free(f);

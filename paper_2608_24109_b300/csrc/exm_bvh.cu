@@ -315,26 +315,26 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
     if (!m->codes) {
         size_t nn = (size_t)n;
         size_t internal = (size_t)(n > 1 ? n - 1 : 1);
-        bool ok = cudaMalloc(&m->codes, nn * 4) == cudaSuccess && cudaMalloc(&m->codes_sorted, nn * 4) == cudaSuccess &&
-                  cudaMalloc(&m->ids, nn * 4) == cudaSuccess && cudaMalloc(&m->ids_sorted, nn * 4) == cudaSuccess &&
-                  cudaMalloc(&m->child, 2 * internal * 4) == cudaSuccess &&
-                  cudaMalloc(&m->bounds, (2 * nn) * 6 * 4) == cudaSuccess &&
-                  cudaMalloc(&m->scene_box, 6 * 4) == cudaSuccess &&
-                  cudaMalloc(&m->tris, nn * 3 * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&m->nodes4, internal * 8 * sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&m->sphere, sizeof(float4)) == cudaSuccess &&
-                  cudaMalloc(&m->frontier, 2 * nn * sizeof(int2)) == cudaSuccess &&
-                  cudaMalloc(&m->frontier_cnt, 4 * sizeof(uint32_t)) == cudaSuccess &&
-                  cudaMalloc(&m->ploc_c, 2 * nn * 4) == cudaSuccess && cudaMalloc(&m->ploc_nn, nn * 4) == cudaSuccess &&
-                  cudaMalloc(&m->ploc_flag, nn * 8) == cudaSuccess && cudaMalloc(&m->ploc_scan, nn * 8) == cudaSuccess;
+        bool ok = exm_malloc((void**)&m->codes, nn * 4) == cudaSuccess && exm_malloc((void**)&m->codes_sorted, nn * 4) == cudaSuccess &&
+                  exm_malloc((void**)&m->ids, nn * 4) == cudaSuccess && exm_malloc((void**)&m->ids_sorted, nn * 4) == cudaSuccess &&
+                  exm_malloc((void**)&m->child, 2 * internal * 4) == cudaSuccess &&
+                  exm_malloc((void**)&m->bounds, (2 * nn) * 6 * 4) == cudaSuccess &&
+                  exm_malloc((void**)&m->scene_box, 6 * 4) == cudaSuccess &&
+                  exm_malloc((void**)&m->tris, nn * 3 * sizeof(float4)) == cudaSuccess &&
+                  exm_malloc((void**)&m->nodes4, internal * 8 * sizeof(float4)) == cudaSuccess &&
+                  exm_malloc((void**)&m->sphere, sizeof(float4)) == cudaSuccess &&
+                  exm_malloc((void**)&m->frontier, 2 * nn * sizeof(int2)) == cudaSuccess &&
+                  exm_malloc((void**)&m->frontier_cnt, 4 * sizeof(uint32_t)) == cudaSuccess &&
+                  exm_malloc((void**)&m->ploc_c, 2 * nn * 4) == cudaSuccess && exm_malloc((void**)&m->ploc_nn, nn * 4) == cudaSuccess &&
+                  exm_malloc((void**)&m->ploc_flag, nn * 8) == cudaSuccess && exm_malloc((void**)&m->ploc_scan, nn * 8) == cudaSuccess;
         if (!ok) return exm_fail(EXM_ERR_OOM, "BVH buffers");
         size_t bytes = 0;
         cub::DeviceRadixSort::SortPairs(nullptr, bytes, m->codes, m->codes_sorted, m->ids, m->ids_sorted, n, 0, 30, s);
-        if (cudaMalloc(&m->sort_tmp, bytes) != cudaSuccess) return exm_fail(EXM_ERR_OOM, "BVH sort scratch");
+        if (exm_malloc((void**)&m->sort_tmp, bytes) != cudaSuccess) return exm_fail(EXM_ERR_OOM, "BVH sort scratch");
         m->sort_tmp_bytes = bytes;
         bytes = 0;
         cub::DeviceScan::ExclusiveSum(nullptr, bytes, m->ploc_flag, m->ploc_scan, n, s);
-        if (cudaMalloc(&m->scan_tmp, bytes) != cudaSuccess) return exm_fail(EXM_ERR_OOM, "BVH scan scratch");
+        if (exm_malloc((void**)&m->scan_tmp, bytes) != cudaSuccess) return exm_fail(EXM_ERR_OOM, "BVH scan scratch");
         m->scan_tmp_bytes = bytes;
     }
     uint32_t* box = (uint32_t*)m->scene_box;
@@ -393,6 +393,12 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
             fin = fout;
             fout = tmp;
         }
+    }
+    if (n == 1) {
+        m->n_nodes = 1;
+    } else if (cudaMemcpyAsync(&m->n_nodes, m->frontier_cnt + 2, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+               cudaStreamSynchronize(s) != cudaSuccess) {
+        return exm_cuda_check(cudaGetLastError(), "BVH node count");
     }
     sphere_centre_kernel<<<1, 1, 0, s>>>(m->nodes4, m->sphere);
     sphere_radius_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->tris, n, m->sphere);

@@ -16,7 +16,7 @@
 namespace exm {
 
 // Device error bits latched in the context's status word.
-enum : uint32_t { ERRBIT_GUARD = 1u, ERRBIT_TRAVERSAL = 2u, ERRBIT_INDEX = 4u, ERRBIT_QUEUE = 8u, ERRBIT_TIMEOUT = 16u };
+enum : uint32_t { ERRBIT_GUARD = 1u, ERRBIT_TRAVERSAL = 2u, ERRBIT_INDEX = 4u, ERRBIT_QUEUE = 8u };
 
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kInvPi = 0.318309886183790671538f;

@@ -43,6 +43,7 @@ struct exm_mesh {
     float4* tris = nullptr;    // [nf * 3]
     float4* nodes4 = nullptr;  // [max(nf-1,1) * 8] 4-wide nodes
     float4* sphere = nullptr;  // [1] bounding sphere of the triangles: centre, inflated R^2
+    uint32_t n_nodes = 0;      // 4-wide nodes in nodes4
     int2* frontier = nullptr;  // [2 * nf] collapse frontier (binary node, 4-wide node)
     uint32_t* frontier_cnt = nullptr;
     // build scratch
@@ -160,6 +161,19 @@ struct DeviceGuard {
     }
 };
 
+// Host-side fault injection (failure tests; no GPU fault is made).  Set from the environment
+// variable EXM_FAULT ("alloc:N,admit:N,slow:MS,cancel:N,corrupt:N", read by exm_create) or by
+// exm_debug_fault; process-wide counters (exm_api.cu).
+enum ExmFault { kFaultAlloc = 0, kFaultAdmit, kFaultSlow, kFaultCancel, kFaultCorrupt, kFaultKinds };
+// True (and one count used up) when an injected fault of `kind` is due.
+bool exm_fault_take(int kind);
+// The current value of a fault setting (the slow-request delay in milliseconds).
+uint32_t exm_fault_value(int kind);
+
+// cudaMalloc through the allocation-failure injector: cudaErrorMemoryAllocation (nothing
+// allocated) when an injected failure is due.
+cudaError_t exm_malloc(void** p, size_t bytes);
+
 // Grows a device buffer to hold `need` elements (contents are not kept); false on OOM.
 template <typename TT>
 inline bool ensure(TT** ptr, size_t* cap, size_t need) {
@@ -167,13 +181,48 @@ inline bool ensure(TT** ptr, size_t* cap, size_t need) {
     cudaFree(*ptr);
     *ptr = nullptr;
     *cap = 0;
-    if (cudaMalloc((void**)ptr, need * sizeof(TT)) != cudaSuccess) {
+    if (exm_malloc((void**)ptr, need * sizeof(TT)) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
     *cap = need;
     return true;
 }
+
+// Batched relight forward (exm_shade.cu; used by the relight server, exm_serve.cu): one
+// request's forward pass split at its two tracer launches, which the server makes once for a
+// whole batch of requests.  A request's rays must fit one queue chunk (relight_queue_rays at
+// most 2^27).
+struct exm_relight_pass;
+// One ray queue of a batched tracer launch: the queue of one request, the BVH of its asset and
+// the outputs its rays write.
+struct ExmTraceJob {
+    const float4* nodes4;
+    const float4* tris;
+    const float4* sphere;
+    const float4* rays;
+    const uint32_t* qcount;  // rays queued
+    uint32_t ray_cap;
+    uint32_t* visbits;
+    uint32_t* secbits;
+    int32_t* hits;
+};
+constexpr int kMaxBatch = 32;  // queues per batched tracer launch
+// Setup on `s`: pixel records, surface records and (indirect) the secondary rays.
+exm_status relight_pass_begin(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
+                              const exm_env* e, exm_frame* f, const exm_params* p, float* out, cudaStream_t s,
+                              exm_relight_pass** out_pass);
+bool relight_pass_indirect(const exm_relight_pass* rp);
+// Shadow rays of the direct samples and of the secondary hits' light samples.
+void relight_pass_shadow_rays(exm_ctx* ctx, exm_relight_pass* rp, cudaStream_t s);
+// The sample loops (Eqs. 17-20) into the request's image.
+exm_status relight_pass_shade(exm_ctx* ctx, exm_relight_pass* rp, exm_frame* f, cudaStream_t s);
+void relight_pass_free(exm_relight_pass* rp);
+uint64_t relight_queue_rays(int views, int W, int H, const exm_params* p);
+// One persistent tracer launch over the queues of `passes` (closest: secondary rays, else shadow
+// rays); the job table goes through h_jobs (pinned host) to d_jobs (device), kMaxBatch entries.
+exm_status relight_trace_batch(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
+                               ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s);
 
 // argument checks shared by the render entry points (exm_api.cu)
 exm_status check_render(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,

@@ -391,7 +391,7 @@ static int grid_for(exm_ctx* ctx, size_t n, int threads) {
 
 static bool ensure_acc(exm_ctx* ctx) {
     if (ctx->d_acc) return true;
-    if (cudaMalloc(&ctx->d_acc, kAccSlots * sizeof(double)) != cudaSuccess) {
+    if (exm_malloc((void**)&ctx->d_acc, kAccSlots * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }

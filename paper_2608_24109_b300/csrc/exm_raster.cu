@@ -127,8 +127,8 @@ exm_status exm_raster_impl(exm_ctx* ctx, const exm_mesh* m, exm_frame* f, int vi
         cudaFree(f->Zq);
         f->XY = nullptr;
         f->Zq = nullptr;
-        if (cudaMalloc(&f->XY, need * sizeof(int2)) != cudaSuccess ||
-            cudaMalloc(&f->Zq, need * sizeof(uint32_t)) != cudaSuccess) {
+        if (exm_malloc((void**)&f->XY, need * sizeof(int2)) != cudaSuccess ||
+            exm_malloc((void**)&f->Zq, need * sizeof(uint32_t)) != cudaSuccess) {
             f->snap_capacity = 0;
             return exm_fail(EXM_ERR_OOM, "snap buffers");
         }

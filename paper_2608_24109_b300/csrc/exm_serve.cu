@@ -1,20 +1,26 @@
 // Relight serving (the relighting use of the exported asset, Sec. 6.6): resident assets,
-// HBM-budget admission and continuous batching.
+// HBM-budget admission and continuous batching into persistent launches.
 //
 // A request names a resident asset (mesh + BVH + UV maps), an environment map, cameras and
-// an output size.  Requests wait in a FIFO queue; the scheduler admits the head of the
-// queue as soon as a slot is free and the request's device footprint fits the remaining
-// budget, so requests that arrive while others run are admitted as slots and memory free
-// up.  Each slot owns a CUDA stream and its reusable render state (environment tables and a
-// frame); an admitted request's whole forward pass (environment distribution, raster,
-// shading) is enqueued on its slot's stream, so the work of all in-flight requests overlaps
-// on the device.  Completion is observed by polling each slot's event; latency is measured
-// from submission to that observation on the host's steady clock.
+// an output size.  Requests wait in a FIFO queue.  Whenever one of the server's batch streams
+// is free, the scheduler takes requests from the head of the queue as long as a request slot
+// is free and the request's device footprint (computed before any allocation) fits the
+// remaining budget, and runs them as one batch on that stream: each request's own setup
+// (environment distribution, raster, pixel records, secondary rays), then ONE persistent
+// closest-hit tracer launch over the secondary-ray queues of every request in the batch, the
+// shadow rays of each, ONE persistent any-hit tracer launch over all their shadow-ray queues,
+// and each request's shading.  The tracer's warps claim pools of rays from the queues in turn
+// and each lane traces its ray through the BVH of its own asset, so assets of different mesh
+// sizes, map sizes and output resolutions share the launches.  Requests that arrive while a
+// batch runs go into the next batch, on another stream, so the GPU keeps working on several
+// batches at once.  Each request's completion is an event recorded after its shading; latency
+// is measured from submission to the observation of that event on the host's steady clock.
 #include <chrono>
 #include <deque>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -24,6 +30,7 @@
 namespace {
 
 using clk = std::chrono::steady_clock;
+constexpr uint64_t kBatchQueueMax = 1ull << 27;  // rays a batched request's queue holds at most
 
 struct Asset {
     const exm_mesh* mesh;
@@ -38,19 +45,30 @@ struct Pending {
     std::vector<exm_camera> cams;
     size_t footprint;
     clk::time_point arrival;
+    clk::time_point ready;  // not launched before (the slow-request injector)
 };
 
+// The render state of one request in flight: frames and environment tables, one per output
+// size and environment size the slot has served (allocated on first use, so that steady-state
+// requests allocate nothing).
 struct Slot {
-    cudaStream_t stream = nullptr;
-    cudaEvent_t done = nullptr;
-    // reusable render state, one per output size / environment size this slot has served
-    // (allocated on first use, so steady-state requests allocate nothing)
     std::vector<std::pair<uint64_t, exm_frame*>> frames;
     std::vector<std::pair<uint64_t, exm_env*>> envs;
+    cudaEvent_t done = nullptr;
     bool busy = false;
+    bool cancelled = false;
     uint64_t ticket = 0;
     size_t footprint = 0;
     clk::time_point arrival;
+};
+
+// A batch stream with its job tables for the batched tracer launches (closest, any).
+struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    bool busy = false;
+    ExmTraceJob* h_jobs = nullptr;  // pinned host, 2 x kMaxBatch
+    ExmTraceJob* d_jobs = nullptr;  // device, 2 x kMaxBatch
 };
 
 struct Result {
@@ -65,24 +83,29 @@ struct exm_server {
     exm_ctx* ctx = nullptr;
     size_t budget = 0;
     size_t used = 0;
-    uint32_t ray_cap = 1u << 25;  // rays per chunk of a slot's frame (1 GiB): fewer chunks, fewer tracer tails
     std::vector<Asset> assets;
     std::vector<Slot> slots;
+    std::vector<Lane> lanes;
     std::deque<Pending> queue;
     std::unordered_map<uint64_t, Result> results;
     uint64_t next_ticket = 1;
-    uint64_t completed = 0;
+    uint64_t completed = 0, batches = 0, batched_requests = 0;
     std::mutex mu;
 };
 
-// Device bytes a request needs while it runs: the frame (visibility buffer, pixel list,
-// snapped vertices, visibility bits, secondary hits, ray queue) and the environment tables.
 // Device bytes of one frame: visibility keys and pixel list, pixel records (the 112-byte
 // shading record and the 48-byte adjoint sums), the texel of each direct sample, snapped
 // vertices, visibility bits, secondary hit ids, the ray queue of a chunk, cameras, counters.
 static size_t frame_bytes(size_t P, size_t views, size_t nv, int wd, int ws, int nb, size_t ray_cap) {
-    return P * (8 + 4 + 16 * kPrec + 48) + P * (size_t)wd * 32 * 4 + views * nv * 12 + P * (size_t)(wd + ws) * 4 + P * (size_t)nb * 4 + ray_cap * 32 +
-           views * 80 + 64;
+    return P * (8 + 4 + 16 * kPrec + 48) + P * (size_t)wd * 32 * 4 + views * nv * 12 + P * (size_t)(wd + ws) * 4 +
+           P * (size_t)nb * 4 + ray_cap * 32 + views * 80 + 64;
+}
+
+// The queue a request's frame needs: all its rays (one chunk) when they fit a batched queue,
+// else the chunked default.
+static size_t request_queue(const exm_relight_req& r, const exm_params& p) {
+    const uint64_t rays = relight_queue_rays(r.views, r.width, r.height, &p);
+    return rays <= kBatchQueueMax ? (size_t)rays : (size_t)kBatchQueueMax;
 }
 
 static size_t request_footprint(const exm_server* s, const exm_relight_req& r) {
@@ -94,11 +117,14 @@ static size_t request_footprint(const exm_server* s, const exm_relight_req& r) {
     size_t frame;
     if (ind && (r.params.flags & EXM_FLAG_HALF_RES_INDIRECT)) {
         // direct-only frame, plus the half-resolution child frame and its image
+        exm_params pd = r.params, ph = r.params;
+        pd.n_bounce = 0;
+        ph.n_direct = 0;
         const size_t Ph = (size_t)r.views * ((r.width + 1) / 2) * ((r.height + 1) / 2);
-        frame = frame_bytes(P, r.views, nv, wd, 0, 0, s->ray_cap) +
-                frame_bytes(Ph, r.views, nv, 0, ws, r.params.n_bounce, s->ray_cap) + Ph * 12;
+        frame = frame_bytes(P, r.views, nv, wd, 0, 0, request_queue(r, pd)) +
+                frame_bytes(Ph, r.views, nv, 0, ws, r.params.n_bounce, kBatchQueueMax) + Ph * 12;
     } else {
-        frame = frame_bytes(P, r.views, nv, wd, ws, ind ? r.params.n_bounce : 0, s->ray_cap);
+        frame = frame_bytes(P, r.views, nv, wd, ws, ind ? r.params.n_bounce : 0, request_queue(r, r.params));
     }
     const size_t n = (size_t)r.env_w * r.env_h;
     int rb = 1, cb = 1;
@@ -109,74 +135,156 @@ static size_t request_footprint(const exm_server* s, const exm_relight_req& r) {
     return frame + env;
 }
 
-static exm_status launch_request(exm_server* s, Slot& sl, Pending& p) {
-    exm_ctx* ctx = s->ctx;
-    const exm_relight_req& r = p.req;
-    const Asset& a = s->assets[r.asset];
-    exm_status st = EXM_OK;
+// The slot's frame and environment tables for this request (created on first use).
+static exm_status slot_state(exm_server* s, Slot& sl, const exm_relight_req& r, exm_frame** frame, exm_env** env) {
     const uint64_t fkey = ((uint64_t)r.views << 40) | ((uint64_t)r.width << 20) | (uint64_t)r.height;
     const uint64_t ekey = ((uint64_t)r.env_w << 32) | (uint64_t)r.env_h;
-    exm_frame* frame = nullptr;
+    *frame = nullptr;
+    *env = nullptr;
     for (auto& kv : sl.frames)
-        if (kv.first == fkey) frame = kv.second;
-    if (!frame) {
-        st = exm_frame_create(ctx, r.views, r.width, r.height, &frame);
+        if (kv.first == fkey) *frame = kv.second;
+    if (!*frame) {
+        exm_status st = exm_frame_create(s->ctx, r.views, r.width, r.height, frame);
         if (st != EXM_OK) return st;
-        frame->ray_cap = s->ray_cap;
-        sl.frames.push_back({fkey, frame});
+        sl.frames.push_back({fkey, *frame});
     }
-    exm_env* env = nullptr;
     for (auto& kv : sl.envs)
-        if (kv.first == ekey) env = kv.second;
-    if (!env) {
-        st = exm_env_create(ctx, r.env_w, r.env_h, &env);
+        if (kv.first == ekey) *env = kv.second;
+    if (!*env) {
+        exm_status st = exm_env_create(s->ctx, r.env_w, r.env_h, env);
         if (st != EXM_OK) return st;
-        sl.envs.push_back({ekey, env});
+        sl.envs.push_back({ekey, *env});
     }
-    st = exm_env_prepare(env, r.env, r.env_dtype, sl.stream);
-    if (st != EXM_OK) return st;
-    st = exm_render_forward(ctx, a.mesh, a.maps, a.dtype, a.mapW, a.mapH, env, p.cams.data(), r.views, &r.params,
-                            frame, r.out_rgb, sl.stream);
-    if (st != EXM_OK) return st;
-    return exm_cuda_check(cudaEventRecord(sl.done, sl.stream), "relight completion event");
+    return EXM_OK;
 }
 
-// Retires finished slots, then admits queued requests in arrival order while a slot is free
-// and the head request's footprint fits the remaining budget.
+// Enqueues one batch on `lane`: every request's setup, the batched tracer launches, every
+// request's shading and completion event.  A request whose rays exceed one queue, or that
+// asks for half-resolution indirect light, runs its whole (chunked) forward pass in the batch's
+// stream instead.  Returns per request the status of its enqueueing.
+static void launch_batch(exm_server* s, Lane& lane, const std::vector<int>& slot_ids, std::vector<Pending>& reqs,
+                         std::vector<exm_status>& status) {
+    exm_ctx* ctx = s->ctx;
+    cudaStream_t st_ = lane.stream;
+    const size_t n = reqs.size();
+    status.assign(n, EXM_OK);
+    std::vector<exm_relight_pass*> pass(n, nullptr);
+    std::vector<exm_frame*> frames(n, nullptr);
+    for (size_t i = 0; i < n; ++i) {
+        Slot& sl = s->slots[slot_ids[i]];
+        const exm_relight_req& r = reqs[i].req;
+        const Asset& a = s->assets[r.asset];
+        exm_env* env = nullptr;
+        exm_status st = slot_state(s, sl, r, &frames[i], &env);
+        if (st == EXM_OK) st = exm_env_prepare(env, r.env, r.env_dtype, st_);
+        const bool batchable = !((r.params.flags & EXM_FLAG_HALF_RES_INDIRECT) && r.params.n_bounce > 0 &&
+                                 r.params.lambda_ind != 0.0f) &&
+                               relight_queue_rays(r.views, r.width, r.height, &r.params) <= kBatchQueueMax;
+        if (st == EXM_OK && !batchable) {
+            frames[i]->ray_cap = 0;
+            st = exm_render_forward(ctx, a.mesh, a.maps, a.dtype, a.mapW, a.mapH, env, reqs[i].cams.data(), r.views,
+                                    &r.params, frames[i], r.out_rgb, st_);
+        } else if (st == EXM_OK) {
+            frames[i]->ray_cap = (uint32_t)kBatchQueueMax;
+            st = check_render(ctx, a.mesh, a.maps, a.dtype, a.mapW, a.mapH, env, reqs[i].cams.data(), r.views,
+                              &r.params, frames[i], "relight");
+            if (st == EXM_OK) st = upload_cameras(frames[i], reqs[i].cams.data(), r.views, st_);
+            if (st == EXM_OK) st = exm_raster_impl(ctx, a.mesh, frames[i], r.views, st_);
+            if (st == EXM_OK)
+                st = relight_pass_begin(ctx, a.mesh, a.maps, a.dtype, a.mapW, a.mapH, env, frames[i], &r.params,
+                                        r.out_rgb, st_, &pass[i]);
+        }
+        status[i] = st;
+    }
+    std::vector<exm_relight_pass*> live;
+    for (size_t i = 0; i < n; ++i)
+        if (pass[i]) live.push_back(pass[i]);
+    exm_status bst = EXM_OK;
+    if (!live.empty()) {
+        bst = relight_trace_batch(ctx, live.data(), (int)live.size(), true, lane.h_jobs, lane.d_jobs, st_);
+        for (exm_relight_pass* rp : live) relight_pass_shadow_rays(ctx, rp, st_);
+        if (bst == EXM_OK)
+            bst = relight_trace_batch(ctx, live.data(), (int)live.size(), false, lane.h_jobs + kMaxBatch,
+                                      lane.d_jobs + kMaxBatch, st_);
+    }
+    for (size_t i = 0; i < n; ++i) {
+        if (pass[i]) {
+            exm_status st = bst == EXM_OK ? relight_pass_shade(ctx, pass[i], frames[i], st_) : bst;
+            if (status[i] == EXM_OK) status[i] = st;
+            relight_pass_free(pass[i]);
+        }
+        cudaEventRecord(s->slots[slot_ids[i]].done, st_);
+    }
+    cudaEventRecord(lane.done, st_);
+}
+
+static void finish(exm_server* s, uint64_t ticket, exm_status st, clk::time_point arrival) {
+    Result& res = s->results[ticket];
+    res.done = true;
+    res.status = st;
+    res.latency_ms = std::chrono::duration<double, std::milli>(clk::now() - arrival).count();
+}
+
+// Retires finished requests and batches, then forms batches from the head of the queue while a
+// batch stream is free: requests join in arrival order as long as a slot is free and the
+// request's footprint fits the remaining budget.
 static exm_status progress_locked(exm_server* s) {
     for (Slot& sl : s->slots) {
         if (!sl.busy) continue;
         cudaError_t q = cudaEventQuery(sl.done);
         if (q == cudaErrorNotReady) continue;
-        Result& res = s->results[sl.ticket];
-        res.done = true;
-        res.status = q == cudaSuccess ? EXM_OK : exm_cuda_check(q, "relight request");
-        res.latency_ms = std::chrono::duration<double, std::milli>(clk::now() - sl.arrival).count();
+        exm_status st = q == cudaSuccess ? EXM_OK : exm_cuda_check(q, "relight request");
+        if (sl.cancelled) st = exm_fail(EXM_ERR_CANCELLED, "relight request cancelled");
+        finish(s, sl.ticket, st, sl.arrival);
         s->used -= sl.footprint;
         sl.busy = false;
+        sl.cancelled = false;
         ++s->completed;
     }
-    while (!s->queue.empty()) {
-        Pending& p = s->queue.front();
-        if (s->used + p.footprint > s->budget) break;
-        Slot* free_slot = nullptr;
-        for (Slot& sl : s->slots)
-            if (!sl.busy) { free_slot = &sl; break; }
-        if (!free_slot) break;
-        exm_status st = launch_request(s, *free_slot, p);
-        if (st != EXM_OK) {
-            Result& res = s->results[p.ticket];
-            res.done = true;
-            res.status = st;
+    for (Lane& ln : s->lanes) {
+        if (!ln.busy) continue;
+        if (cudaEventQuery(ln.done) != cudaErrorNotReady) ln.busy = false;
+    }
+    const clk::time_point now = clk::now();
+    for (Lane& ln : s->lanes) {
+        if (ln.busy || s->queue.empty()) continue;
+        std::vector<int> ids;
+        std::vector<Pending> batch;
+        size_t used = s->used;
+        while (!s->queue.empty() && (int)batch.size() < kMaxBatch) {
+            Pending& p = s->queue.front();
+            if (p.ready > now || used + p.footprint > s->budget) break;
+            int free_slot = -1;
+            for (size_t k = 0; k < s->slots.size(); ++k) {
+                bool taken = s->slots[k].busy;
+                for (int id : ids) taken = taken || id == (int)k;
+                if (!taken) { free_slot = (int)k; break; }
+            }
+            if (free_slot < 0) break;
+            ids.push_back(free_slot);
+            used += p.footprint;
+            batch.push_back(std::move(p));
             s->queue.pop_front();
-            continue;
         }
-        free_slot->busy = true;
-        free_slot->ticket = p.ticket;
-        free_slot->footprint = p.footprint;
-        free_slot->arrival = p.arrival;
-        s->used += p.footprint;
-        s->queue.pop_front();
+        if (batch.empty()) break;
+        std::vector<exm_status> status;
+        launch_batch(s, ln, ids, batch, status);
+        ln.busy = true;
+        ++s->batches;
+        s->batched_requests += batch.size();
+        for (size_t i = 0; i < batch.size(); ++i) {
+            if (status[i] != EXM_OK) {
+                finish(s, batch[i].ticket, status[i], batch[i].arrival);
+                continue;
+            }
+            Slot& sl = s->slots[ids[i]];
+            sl.busy = true;
+            sl.cancelled = false;
+            sl.ticket = batch[i].ticket;
+            sl.footprint = batch[i].footprint;
+            sl.arrival = batch[i].arrival;
+            s->used += batch[i].footprint;
+        }
     }
     return EXM_OK;
 }
@@ -192,37 +300,43 @@ exm_status exm_server_create(exm_ctx* ctx, uint64_t hbm_budget_bytes, int max_sl
     if (!s) return exm_fail(EXM_ERR_OOM, "exm_server_create: host allocation");
     s->ctx = ctx;
     s->budget = hbm_budget_bytes;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(ctx->device);
+    DeviceGuard g(ctx->device);
     s->slots.resize(max_slots);
-    for (Slot& sl : s->slots) {
-        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            exm_server_destroy(s);
-            if (prev >= 0) cudaSetDevice(prev);
-            return exm_fail(EXM_ERR_CUDA, "exm_server_create: stream/event creation");
-        }
+    s->lanes.resize(max_slots < 3 ? max_slots : 3);
+    bool ok = true;
+    for (Slot& sl : s->slots)
+        ok = ok && cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess;
+    for (Lane& ln : s->lanes)
+        ok = ok && cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) == cudaSuccess &&
+             cudaHostAlloc((void**)&ln.h_jobs, 2 * kMaxBatch * sizeof(ExmTraceJob), cudaHostAllocDefault) ==
+                 cudaSuccess &&
+             exm_malloc((void**)&ln.d_jobs, 2 * kMaxBatch * sizeof(ExmTraceJob)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        exm_server_destroy(s);
+        return exm_fail(EXM_ERR_OOM, "exm_server_create: streams, events or job tables");
     }
-    if (prev >= 0) cudaSetDevice(prev);
     *out = s;
     return EXM_OK;
 }
 
 void exm_server_destroy(exm_server* s) {
     if (!s) return;
-    int prev = -1;
-    cudaGetDevice(&prev);
-    cudaSetDevice(s->ctx->device);
+    DeviceGuard g(s->ctx->device);
+    for (Lane& ln : s->lanes)
+        if (ln.stream) cudaStreamSynchronize(ln.stream);
     for (Slot& sl : s->slots) {
-        if (sl.stream) cudaStreamSynchronize(sl.stream);
         for (auto& kv : sl.frames) exm_frame_destroy(kv.second);
         for (auto& kv : sl.envs) exm_env_destroy(kv.second);
         if (sl.done) cudaEventDestroy(sl.done);
-        if (sl.stream) cudaStreamDestroy(sl.stream);
     }
-    if (prev >= 0) cudaSetDevice(prev);
+    for (Lane& ln : s->lanes) {
+        if (ln.done) cudaEventDestroy(ln.done);
+        if (ln.stream) cudaStreamDestroy(ln.stream);
+        cudaFreeHost(ln.h_jobs);
+        cudaFree(ln.d_jobs);
+    }
     delete s;
 }
 
@@ -252,23 +366,73 @@ exm_status exm_relight_submit(exm_server* s, const exm_relight_req* r, uint64_t*
     p.footprint = request_footprint(s, *r);
     if (p.footprint > s->budget)
         return exm_fail(EXM_ERR_BUSY, "exm_relight_submit: the request alone exceeds the server's HBM budget");
+    if (exm_fault_take(kFaultAdmit)) return exm_fail(EXM_ERR_BUSY, "exm_relight_submit: admission refused (injected)");
+    DeviceGuard g(s->ctx->device);
     p.arrival = clk::now();
+    p.ready = p.arrival + std::chrono::milliseconds(exm_fault_value(kFaultSlow));
     p.ticket = s->next_ticket++;
     s->results[p.ticket] = Result{};
+    *ticket = p.ticket;
+    if (exm_fault_take(kFaultCancel)) {  // a client that cancels right after submitting
+        finish(s, p.ticket, EXM_ERR_CANCELLED, p.arrival);
+        return progress_locked(s);
+    }
     s->queue.push_back(std::move(p));
-    *ticket = s->queue.back().ticket;
     return progress_locked(s);
 }
 
 exm_status exm_server_progress(exm_server* s) {
     if (!s) return exm_fail(EXM_ERR_ARG, "exm_server_progress: NULL server");
     std::lock_guard<std::mutex> lock(s->mu);
+    DeviceGuard g(s->ctx->device);
     return progress_locked(s);
+}
+
+exm_status exm_relight_cancel(exm_server* s, uint64_t ticket) {
+    if (!s) return exm_fail(EXM_ERR_ARG, "exm_relight_cancel: NULL server");
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return exm_fail(EXM_ERR_ARG, "exm_relight_cancel: unknown ticket");
+    if (it->second.done) return EXM_OK;  // finished already: its result stands
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+        if (q->ticket == ticket) {
+            finish(s, ticket, EXM_ERR_CANCELLED, q->arrival);
+            s->queue.erase(q);
+            return EXM_OK;
+        }
+    for (Slot& sl : s->slots)
+        if (sl.busy && sl.ticket == ticket) sl.cancelled = true;  // its kernels finish; the result is dropped
+    return EXM_OK;
+}
+
+exm_status exm_relight_wait(exm_server* s, uint64_t ticket, double timeout_ms, double* latency_ms) {
+    if (!s || !(timeout_ms >= 0.0)) return exm_fail(EXM_ERR_ARG, "exm_relight_wait: bad argument");
+    const clk::time_point deadline =
+        clk::now() + std::chrono::microseconds((long long)(timeout_ms < 1e9 ? timeout_ms * 1000.0 : 1e12));
+    while (true) {
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            DeviceGuard g(s->ctx->device);
+            progress_locked(s);
+            auto it = s->results.find(ticket);
+            if (it == s->results.end()) return exm_fail(EXM_ERR_ARG, "exm_relight_wait: unknown ticket");
+            if (it->second.done) {
+                if (latency_ms) *latency_ms = it->second.latency_ms;
+                const exm_status st = it->second.status;
+                s->results.erase(it);
+                return st == EXM_OK ? EXM_OK : exm_fail(st, st == EXM_ERR_CANCELLED ? "relight request cancelled"
+                                                                                      : "relight request failed");
+            }
+        }
+        if (clk::now() >= deadline) return exm_fail(EXM_ERR_TIMEOUT, "exm_relight_wait: the request is not done");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
 }
 
 exm_status exm_relight_poll(exm_server* s, uint64_t ticket, int* done, double* latency_ms) {
     if (!s || !done) return exm_fail(EXM_ERR_ARG, "exm_relight_poll: NULL argument");
     std::lock_guard<std::mutex> lock(s->mu);
+    DeviceGuard g(s->ctx->device);
     progress_locked(s);
     auto it = s->results.find(ticket);
     if (it == s->results.end()) return exm_fail(EXM_ERR_ARG, "exm_relight_poll: unknown ticket");
@@ -277,8 +441,17 @@ exm_status exm_relight_poll(exm_server* s, uint64_t ticket, int* done, double* l
     if (it->second.done) {
         exm_status st = it->second.status;
         s->results.erase(it);
-        return st;
+        return st == EXM_OK ? EXM_OK : exm_fail(st, st == EXM_ERR_CANCELLED ? "relight request cancelled"
+                                                                              : "relight request failed");
     }
+    return EXM_OK;
+}
+
+exm_status exm_server_batches(exm_server* s, uint64_t* batches, uint64_t* batched_requests) {
+    if (!s) return exm_fail(EXM_ERR_ARG, "exm_server_batches: NULL server");
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (batches) *batches = s->batches;
+    if (batched_requests) *batched_requests = s->batched_requests;
     return EXM_OK;
 }
 

@@ -25,6 +25,7 @@
 // from the pool between rounds of kRound items.
 #include <algorithm>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -491,13 +492,39 @@ constexpr int kRound = 24;  // node visits between refills
 
 constexpr int kTraceThreads = 128;
 
-template <bool CLOSEST, bool COUNT>
-__global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
+using TraceJob = ExmTraceJob;
+
+// The traversal loop.  Single queue (BATCH false): the chunk's queue of A, claimed kPool rays at
+// a time.  Batched: the queues of `jobs`, whose pools are numbered one after another; a warp
+// claims a pool number, finds its queue, and each lane keeps the BVH of the queue its ray came
+// from, so the lanes of a warp may trace rays of different assets.
+template <bool CLOSEST, bool COUNT, bool BATCH>
+__device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* __restrict__ jobs, int njobs,
+                                           uint32_t* batch_cursor) {
     int stack[kStackSize4];
-    const uint32_t* qcount = A.ctr + (CLOSEST ? 0 : 2);
-    uint32_t* cursor = A.ctr + (CLOSEST ? 1 : 3);
-    const uint32_t n = min(*qcount, A.ray_cap);  // an overflowed queue holds ray_cap rays (ERRBIT_QUEUE)
-    if (n == 0) return;
+    __shared__ uint32_t s_pool_end[BATCH ? kMaxBatch : 1];  // BATCH: pools of queues 0..j
+    __shared__ uint32_t s_count[BATCH ? kMaxBatch : 1];     // BATCH: rays of queue j
+    uint32_t n = 0;          // single queue: its rays
+    uint32_t* cursor = nullptr;
+    if (BATCH) {
+        if (threadIdx.x < (unsigned)njobs)
+            s_count[threadIdx.x] = min(__ldg(jobs[threadIdx.x].qcount), jobs[threadIdx.x].ray_cap);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int j = 0; j < njobs; ++j) {
+                acc += (s_count[j] + kPool - 1) / kPool;
+                s_pool_end[j] = acc;
+            }
+        }
+        __syncthreads();
+        if (njobs == 0 || s_pool_end[njobs - 1] == 0) return;
+        cursor = batch_cursor;
+    } else {
+        n = min(*(A.ctr + (CLOSEST ? 0 : 2)), A.ray_cap);  // an overflowed queue holds ray_cap rays (ERRBIT_QUEUE)
+        if (n == 0) return;
+        cursor = A.ctr + (CLOSEST ? 1 : 3);
+    }
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
@@ -511,22 +538,49 @@ __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
     r.oinv = make_float3(0.f, 0.f, 0.f);
     uint64_t slot = 0;
     uint32_t pnext = 0, pend = 0;  // warp-uniform pool [pnext, pend)
+    int pjob = 0;                  // BATCH, warp-uniform: the queue of the pool
+    int job = 0;                   // BATCH: the queue of this lane's ray
+    BvhView bvh = A.bvh;           // BATCH: the BVH of this lane's ray
     bool drained = false;          // warp-uniform: the queue has no more pools
     while (true) {
         const unsigned need = __ballot_sync(0xffffffffu, !active);
         if (need && pnext >= pend && !drained) {
-            uint32_t b = 0;
-            if (lane == 0) b = atomicAdd(cursor, kPool);
-            b = __shfl_sync(0xffffffffu, b, 0);
-            if (b >= n) drained = true;
-            else { pnext = b; pend = min(b + kPool, n); }
+            if (BATCH) {
+                uint32_t g = 0;
+                if (lane == 0) g = atomicAdd(cursor, 1u);
+                g = __shfl_sync(0xffffffffu, g, 0);
+                if (g >= s_pool_end[njobs - 1]) {
+                    drained = true;
+                } else {
+                    int j = 0;
+                    while (s_pool_end[j] <= g) ++j;
+                    const uint32_t first = (g - (j ? s_pool_end[j - 1] : 0u)) * kPool;
+                    pjob = j;
+                    pnext = first;
+                    pend = min(first + kPool, s_count[j]);
+                }
+            } else {
+                uint32_t b = 0;
+                if (lane == 0) b = atomicAdd(cursor, kPool);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (b >= n) drained = true;
+                else { pnext = b; pend = min(b + kPool, n); }
+            }
         }
         if (need && pnext < pend) {
             const uint32_t my = pnext + (uint32_t)__popc(need & lt);
             if (!active && my < pend) {
-                const float4 a = A.rays[2 * (size_t)my], b = A.rays[2 * (size_t)my + 1];
+                const float4* rays = A.rays;
+                if (BATCH) {
+                    job = pjob;
+                    rays = jobs[job].rays;
+                    bvh.nodes4 = jobs[job].nodes4;
+                    bvh.tris = jobs[job].tris;
+                    bvh.sphere = jobs[job].sphere;
+                }
+                const float4 a = rays[2 * (size_t)my], b = rays[2 * (size_t)my + 1];
                 r = make_ray(s3(a.x, a.y, a.z), s3(a.w, b.x, b.y));
-                tclip = sphere_exit(r.o, r.d, __ldg(A.bvh.sphere));
+                tclip = sphere_exit(r.o, r.d, __ldg(bvh.sphere));
                 slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
                 sp = 0; node = 0; best = -1; steps = 0; bt = INFINITY; bdet = 0.0f;
                 active = true;
@@ -551,14 +605,14 @@ __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
                 ++c_tris;
                 float T, det;
                 int id;
-                if (tri_test(A.bvh, ~node, r, &T, &det, &id)) {
+                if (tri_test(bvh, ~node, r, &T, &det, &id)) {
                     if (!CLOSEST) { hit = true; done = true; break; }
                     const float t = sdiv(T, det);
                     if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
                 }
             } else {
                 ++c_nodes;
-                const float4* N = A.bvh.nodes4 + 8 * (size_t)node;
+                const float4* N = bvh.nodes4 + 8 * (size_t)node;
                 // near / far planes of each axis chosen by the ray's direction signs
                 const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
                 const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
@@ -610,10 +664,12 @@ __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
         }
         if (done) {
             if (CLOSEST) {
-                A.hits[slot] = (best >= 0 && bdet > 0.0f) ? best : -1;
+                int32_t* hits = BATCH ? jobs[job].hits : A.hits;
+                hits[slot] = (best >= 0 && bdet > 0.0f) ? best : -1;
             } else if (!hit) {
                 const uint64_t bit = slot & ~(1ull << 63);
-                uint32_t* words = (slot >> 63) ? A.secbits : A.visbits;
+                uint32_t* words = (slot >> 63) ? (BATCH ? jobs[job].secbits : A.secbits)
+                                               : (BATCH ? jobs[job].visbits : A.visbits);
                 atomicOr(words + (bit >> 5), 1u << (uint32_t)(bit & 31));
             }
             active = false;
@@ -625,6 +681,18 @@ __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
         atomicAdd(A.work + 1, (unsigned long long)c_tris);
         atomicAdd(A.work + 3, (unsigned long long)c_rays);
     }
+}
+
+template <bool CLOSEST, bool COUNT>
+__global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
+    trace_body<CLOSEST, COUNT, false>(A, nullptr, 0, nullptr);
+}
+
+// The batched tracer: one persistent launch over the ray queues of several relight requests.
+template <bool CLOSEST>
+__global__ void __launch_bounds__(kTraceThreads, 8) trace_batch_kernel(ShadeArgs A, const TraceJob* __restrict__ jobs,
+                                                                       int njobs, uint32_t* cursor) {
+    trace_body<CLOSEST, false, true>(A, jobs, njobs, cursor);
 }
 
 // ------------------------------------------------------------------ shading (warp per pixel)
@@ -1477,6 +1545,139 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     f->fwd_chunk = c.Pc;
     f->fwd_ray_cap = c.ray_cap;
     return EXM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched relight forward (relight serving, exm_serve.cu): one request's forward pass split at
+// its two tracer launches, which the server makes once for a whole batch of requests
+// (trace_batch_kernel).  A request's rays must fit one queue chunk.
+
+struct exm_relight_pass {
+    ShadeArgs A;
+    ChunkPlan c;
+    exm_params p;
+    exm_dtype dt;
+};
+
+exm_status relight_pass_begin(exm_ctx* ctx, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
+                              const exm_env* e, exm_frame* f, const exm_params* p, float* out, cudaStream_t s,
+                              exm_relight_pass** out_pass) {
+    *out_pass = nullptr;
+    if (dt != EXM_F32 && dt != EXM_BF16 && dt != EXM_F16) return exm_fail(EXM_ERR_ARG, "map dtype");
+    const ChunkPlan c = plan_chunks(f, p);
+    if (c.nchunks != 1 || c.recompute)
+        return exm_fail(EXM_ERR_ARG, "relight batch: the request's rays exceed one queue chunk");
+    f->last_nd = -1;
+    if (!ensure(&f->prec, &f->prec_cap, c.P * (size_t)kPrec) || !ensure(&f->pacc, &f->pacc_cap, c.P * (size_t)12) ||
+        (p->n_direct > 0 && !ensure(&f->tsel, &f->tsel_cap, c.Ps * (size_t)p->n_direct)) ||
+        !ensure(&f->bits, &f->bits_cap, c.Ps * (size_t)(c.wd + c.ws)) ||
+        !ensure(&f->rays, &f->rays_cap, (size_t)c.ray_cap * 2) ||
+        (c.indirect && !ensure(&f->hits, &f->hits_cap, c.Ps * (size_t)c.nb)) || !ensure(&f->ctr, &f->ctr_cap, 4))
+        return exm_fail(EXM_ERR_OOM, "relight batch: wavefront buffers");
+    exm_relight_pass* rp = new (std::nothrow) exm_relight_pass();
+    if (!rp) return exm_fail(EXM_ERR_OOM, "relight batch: host allocation");
+    rp->c = c;
+    rp->p = *p;
+    rp->dt = dt;
+    ShadeArgs& A = rp->A;
+    A = make_args(ctx, m, maps, mapW, mapH, e, f, p);
+    A.secbits = f->bits + c.Ps * (size_t)c.wd;
+    A.ray_cap = c.ray_cap;
+    A.out = out;
+    A.chunk_begin = 0;
+    A.chunk_pixels = c.Pc;
+    A.ctr = f->ctr;
+    A.state_base = 0;
+    A.shade_begin = 0;
+    A.shade_end = 0xffffffffu;
+    pixel_prep_kernel<<<ctx->num_sms * 8, 256, 0, s>>>(A);
+    ctx->launches += 1;
+    cudaMemsetAsync(f->samples, 0, sizeof(unsigned long long), s);
+    cudaMemsetAsync(out, 0, c.P * 3 * sizeof(float), s);
+    cudaMemsetAsync(f->ctr, 0, 4 * sizeof(uint32_t), s);
+    cudaMemsetAsync(f->bits, 0, c.P * (size_t)(c.wd + c.ws) * sizeof(uint32_t), s);
+    launch_surface(ctx, f, p, A, dt, false, s);
+    if (c.indirect) {
+        cudaMemsetAsync(f->hits, 0xff, c.P * (size_t)c.nb * sizeof(int32_t), s);
+        gen_secondary_kernel<<<exm_blocks((size_t)c.Pc, 256), 256, 0, s>>>(A);
+        ctx->launches += 1;
+    }
+    *out_pass = rp;
+    return exm_cuda_check(cudaGetLastError(), "relight batch: setup");
+}
+
+bool relight_pass_indirect(const exm_relight_pass* rp) { return rp->c.indirect; }
+
+void relight_pass_shadow_rays(exm_ctx* ctx, exm_relight_pass* rp, cudaStream_t s) {
+    const ShadeArgs& A = rp->A;
+    if (rp->p.n_direct > 0) {
+        gen_direct_kernel<<<exm_blocks((size_t)rp->c.Pc * ((rp->p.n_direct + kGenK - 1) / kGenK), kGenThreads),
+                            kGenThreads, 0, s>>>(A);
+        ctx->launches += 1;
+    }
+    if (rp->c.indirect) {
+        gen_seclight_kernel<<<exm_blocks((size_t)rp->c.Pc, kGenThreads), kGenThreads, 0, s>>>(A);
+        ctx->launches += 1;
+    }
+}
+
+exm_status relight_pass_shade(exm_ctx* ctx, exm_relight_pass* rp, exm_frame* f, cudaStream_t s) {
+    launch_samples<false>(ctx, f, &rp->p, rp->A, rp->dt, s);
+    const ChunkPlan& c = rp->c;
+    f->last_wd = c.wd;
+    f->last_ws = c.ws;
+    f->last_nb = c.nb;
+    f->last_ns = c.indirect ? rp->p.n_light : 0;
+    f->last_nd = rp->p.n_direct;
+    f->fwd_recompute = false;
+    f->fwd_chunk = c.Pc;
+    f->fwd_ray_cap = c.ray_cap;
+    f->fwd_seed = rp->p.seed;
+    return exm_cuda_check(cudaGetLastError(), "relight batch: shade");
+}
+
+void relight_pass_free(exm_relight_pass* rp) { delete rp; }
+
+// Rays a request of these sizes queues at most (its one chunk).
+uint64_t relight_queue_rays(int views, int W, int H, const exm_params* p) {
+    const bool indirect = p->n_bounce > 0 && p->lambda_ind != 0.0f;
+    const uint64_t wd = (uint64_t)(p->n_direct + 31) / 32;
+    const uint64_t ws = indirect ? ((uint64_t)p->n_bounce * p->n_light + 31) / 32 : 0;
+    const uint64_t per_pixel = std::max(wd * 32 + ws * 32, (uint64_t)(indirect ? p->n_bounce : 1));
+    const uint64_t P32 = ((uint64_t)views * W * H + 31) & ~(uint64_t)31;
+    return P32 * per_pixel;
+}
+
+exm_status relight_trace_batch(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
+                               ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s) {
+    if (n < 1 || n > kMaxBatch) return exm_fail(EXM_ERR_ARG, "relight batch: size");
+    int k = 0;
+    uint32_t* cursor = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const ShadeArgs& A = passes[i]->A;
+        if (closest && !passes[i]->c.indirect) continue;
+        TraceJob& j = h_jobs[k++];
+        j.nodes4 = A.bvh.nodes4;
+        j.tris = A.bvh.tris;
+        j.sphere = A.bvh.sphere;
+        j.rays = A.rays;
+        j.qcount = A.ctr + (closest ? 0 : 2);
+        j.ray_cap = A.ray_cap;
+        j.visbits = A.visbits;
+        j.secbits = A.secbits;
+        j.hits = A.hits;
+        if (!cursor) cursor = A.ctr + (closest ? 1 : 3);  // zeroed with the first pass's counters
+    }
+    if (k == 0) return EXM_OK;
+    exm_status st = exm_cuda_check(cudaMemcpyAsync(d_jobs, h_jobs, (size_t)k * sizeof(ExmTraceJob),
+                                                   cudaMemcpyHostToDevice, s), "relight batch: job table");
+    if (st != EXM_OK) return st;
+    ShadeArgs A = passes[0]->A;
+    const int blocks = ctx->num_sms * 8;
+    if (closest) trace_batch_kernel<true><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+    else trace_batch_kernel<false><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+    ctx->launches += 1;
+    return exm_cuda_check(cudaGetLastError(), "relight batch: trace");
 }
 
 // The backward pass reads what the forward pass left in the frame: the pixel records, and the

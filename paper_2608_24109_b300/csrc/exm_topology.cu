@@ -553,7 +553,7 @@ T* scratch(exm_topology* t, int slot, size_t n) {
         cudaFree(b.first);
         b.first = nullptr;
         b.second = 0;
-        if (cudaMalloc(&b.first, bytes) != cudaSuccess) {
+        if (exm_malloc((void**)&b.first, bytes) != cudaSuccess) {
             cudaGetLastError();
             return nullptr;
         }
@@ -567,7 +567,7 @@ bool ensure_tmp(exm_topology* t, size_t bytes) {
     cudaFree(t->tmp);
     t->tmp = nullptr;
     t->tmp_cap = 0;
-    if (cudaMalloc(&t->tmp, bytes ? bytes : 1) != cudaSuccess) {
+    if (exm_malloc((void**)&t->tmp, bytes ? bytes : 1) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }

@@ -24,6 +24,10 @@ EXM_ERR_TRAVERSAL_LIMIT = -5
 EXM_ERR_TIMEOUT = -6
 EXM_ERR_BUSY = -7
 EXM_ERR_QUEUE_OVERFLOW = -8
+EXM_ERR_CANCELLED = -9
+FAULT_ALLOC, FAULT_ADMIT, FAULT_SLOW, FAULT_CANCEL, FAULT_CORRUPT = 1, 2, 3, 4, 5
+ASSET_VERSION = 1
+ASSET_SECTIONS = 7
 
 EXM_F32, EXM_BF16, EXM_F16 = 0, 1, 2
 FLAG_WRAP_U = 1
@@ -36,14 +40,16 @@ FLAG_HALF_RES_INDIRECT = 64
 FLAG_RECOMPUTE = 128
 
 EXPORTS = [
-    "exm_create", "exm_destroy", "exm_last_error", "exm_sync",
+    "exm_create", "exm_destroy", "exm_last_error", "exm_sync", "exm_debug_fault",
     "exm_mesh_create", "exm_mesh_update_vertices", "exm_bvh_build", "exm_mesh_destroy", "exm_mesh_frames",
+    "exm_mesh_export_info", "exm_mesh_export", "exm_mesh_import",
     "exm_env_create", "exm_env_prepare", "exm_env_destroy", "exm_env_total",
     "exm_frame_create", "exm_frame_destroy", "exm_frame_set_limits", "exm_frame_stats", "exm_frame_work", "exm_frame_kernel_ms",
     "exm_launch_count", "exm_frame_visbuf", "exm_frame_saved_state",
     "exm_render_forward", "exm_render_backward", "exm_render_backward_noalloc", "exm_l1_loss",
     "exm_server_create", "exm_server_destroy", "exm_server_add_asset", "exm_relight_submit", "exm_relight_poll",
-    "exm_server_progress", "exm_server_stats", "exm_relight_footprint",
+    "exm_server_progress", "exm_server_stats", "exm_relight_footprint", "exm_relight_cancel", "exm_relight_wait",
+    "exm_server_batches",
     "exm_image_loss", "exm_material_tv", "exm_env_regularizers", "exm_adam_step",
     "exm_topology_create", "exm_topology_destroy", "exm_face_render_counts", "exm_topology_round",
     "exm_topology_result",
@@ -75,6 +81,12 @@ class RelightReq(ctypes.Structure):
                 ("out_rgb", ctypes.c_void_p)]
 
 
+class AssetInfo(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_uint32), ("node_bytes", ctypes.c_uint32), ("nv", ctypes.c_int32),
+                ("nf", ctypes.c_int32), ("nuv", ctypes.c_int32), ("n_nodes", ctypes.c_uint32),
+                ("bytes", ctypes.c_uint64 * ASSET_SECTIONS)]
+
+
 _lib = None
 
 
@@ -93,6 +105,13 @@ def lib():
         "exm_destroy": ([P], None),
         "exm_last_error": ([], ctypes.c_char_p),
         "exm_sync": ([P, P], I),
+        "exm_debug_fault": ([I, ctypes.c_uint32], I),
+        "exm_mesh_export_info": ([P, ctypes.POINTER(AssetInfo)], I),
+        "exm_mesh_export": ([P, ctypes.POINTER(ctypes.c_void_p * ASSET_SECTIONS), P], I),
+        "exm_mesh_import": ([P, ctypes.POINTER(AssetInfo), ctypes.POINTER(ctypes.c_void_p * ASSET_SECTIONS), P, PP], I),
+        "exm_relight_cancel": ([P, U64], I),
+        "exm_relight_wait": ([P, U64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], I),
+        "exm_server_batches": ([P, ctypes.POINTER(U64), ctypes.POINTER(U64)], I),
         "exm_mesh_create": ([P, P, I, P, I, P, I, P, P, PP], I),
         "exm_mesh_update_vertices": ([P, P, P], I),
         "exm_bvh_build": ([P, P], I),
@@ -187,6 +206,38 @@ def exm_destroy(ctx):
 
 def exm_sync(ctx, stream=None):
     return check(lib().exm_sync(ctx, _stream(stream)))
+
+
+def exm_debug_fault(kind, count):
+    return check(lib().exm_debug_fault(int(kind), int(count)))
+
+
+def exm_mesh_export_info(mesh):
+    info = AssetInfo()
+    check(lib().exm_mesh_export_info(mesh, ctypes.byref(info)))
+    return info
+
+
+def exm_mesh_export(mesh, sections, stream=None):
+    """Copies the asset's sections into `sections` (ASSET_SECTIONS buffers: numpy arrays or
+    torch tensors of info.bytes bytes each)."""
+    ptrs = (ctypes.c_void_p * ASSET_SECTIONS)(*[_addr(x) for x in sections])
+    return check(lib().exm_mesh_export(mesh, ctypes.byref(ptrs), _stream(stream)))
+
+
+def exm_mesh_import(ctx, info: AssetInfo, sections, stream=None):
+    ptrs = (ctypes.c_void_p * ASSET_SECTIONS)(*[_addr(x) for x in sections])
+    h = ctypes.c_void_p()
+    check(lib().exm_mesh_import(ctx, ctypes.byref(info), ctypes.byref(ptrs), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def _addr(x):
+    """Address of a host numpy array or of a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    return x.data_ptr()
 
 
 def exm_mesh_create(ctx, V, F, UV, Fuv, stream=None):
@@ -349,6 +400,22 @@ def exm_relight_poll(server, ticket):
     lat = ctypes.c_double()
     check(lib().exm_relight_poll(server, ticket, ctypes.byref(done), ctypes.byref(lat)))
     return bool(done.value), lat.value
+
+
+def exm_relight_cancel(server, ticket):
+    return check(lib().exm_relight_cancel(server, int(ticket)))
+
+
+def exm_relight_wait(server, ticket, timeout_ms):
+    lat = ctypes.c_double()
+    check(lib().exm_relight_wait(server, int(ticket), float(timeout_ms), ctypes.byref(lat)))
+    return lat.value
+
+
+def exm_server_batches(server):
+    b, r = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().exm_server_batches(server, ctypes.byref(b), ctypes.byref(r)))
+    return b.value, r.value
 
 
 def exm_server_progress(server):

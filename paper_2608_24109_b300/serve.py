@@ -1,9 +1,10 @@
 """Relight serving over resident assets (thin wrapper of libexmesh's native server).
 
 The server (include/exmesh.h, exm_server_*) keeps assets resident on the device, admits
-requests by their device footprint against an HBM budget, and runs every admitted request
-on its own slot stream, so requests that arrive while others run start as soon as a slot
-and memory free up and their work overlaps on the GPU.  This module only marshals
+requests by their device footprint against an HBM budget, and runs the admitted requests in
+batches on a few batch streams: each batch traces all its requests' rays in shared persistent
+tracer launches (every ray through its own asset's BVH), and requests that arrive while a
+batch runs join the next one, so batches overlap on the GPU.  This module only marshals
 arguments and keeps the Python-side buffers of in-flight requests alive.
 """
 from __future__ import annotations
@@ -58,11 +59,40 @@ class RelightServer:
         return ticket
 
     def poll(self, ticket):
-        done, lat = N.exm_relight_poll(self.server, ticket)
+        try:
+            done, lat = N.exm_relight_poll(self.server, ticket)
+        except N.ExmError:
+            self._inflight.pop(ticket, None)  # done with an error (cancelled, failed)
+            raise
         out = None
         if done:
             out = self._inflight.pop(ticket)[1]
         return done, lat, out
+
+    def wait(self, ticket, timeout_ms):
+        """(latency ms, output) once the request is done; raises N.ExmError with EXM_ERR_TIMEOUT
+        if it is not done within timeout_ms (it stays pending), or the request's own error."""
+        try:
+            lat = N.exm_relight_wait(self.server, ticket, timeout_ms)
+        except N.ExmError as e:
+            if e.code != N.EXM_ERR_TIMEOUT:
+                self._inflight.pop(ticket, None)
+            raise
+        return lat, self._inflight.pop(ticket)[1]
+
+    def cancel(self, ticket):
+        N.exm_relight_cancel(self.server, ticket)
+
+    def batches(self):
+        """(batches launched, requests they held)."""
+        return N.exm_server_batches(self.server)
+
+    def add_imported_asset(self, mesh, maps):
+        """Registers a mesh handle from exm_mesh_import with its maps; the server frees it on close."""
+        maps = maps.to(self.device).contiguous()
+        aid = N.exm_server_add_asset(self.server, mesh, maps)
+        self.assets.append((mesh, [], maps))
+        return aid
 
     def footprint(self, req_and_buffers):
         return N.exm_relight_footprint(self.server, req_and_buffers[0])

@@ -58,6 +58,7 @@ def test_same_alone_and_in_the_mix():
         t = srv.submit(srv.request(**r))
         outs, _ = _wait(srv, [t])
         alone.append(outs[t].clone())
+    b0, r0 = srv.batches()
     tickets = [srv.submit(srv.request(**r)) for r in reqs]
     peak = srv.stats()["in_flight"]
     outs, lats = _wait(srv, tickets)
@@ -66,6 +67,40 @@ def test_same_alone_and_in_the_mix():
         assert outs[t].abs().sum() > 0
         assert lats[t] > 0
     assert peak >= 2  # several requests were in flight together
+    b1, r1 = srv.batches()
+    assert r1 - r0 == len(reqs) and b1 - b0 < len(reqs)  # some batch held several requests
+    srv.close()
+
+
+def test_one_batch_of_different_assets_and_sizes():
+    """Eight requests over three assets (1280 to 3072 triangles, maps of 64^2 to 256^2 in BF16,
+    direct-only and one-bounce), three output sizes and two environment sizes, submitted while
+    no batch stream is free, run as one batch: the two persistent tracer launches trace all
+    their rays, each through its own asset's BVH, and every image equals the request rendered
+    alone."""
+    from paper_2608_24109_b300.serve import RelightServer
+    from paper_2608_24109_b300 import native as N
+    scs = _assets()
+    srv = RelightServer(hbm_budget_bytes=8 << 30, max_slots=8)
+    ids = [srv.add_asset(s.V, s.F, s.UV, s.Fuv, torch.as_tensor(s.maps).to(torch.bfloat16)) for s in scs]
+    reqs = _requests(srv, ids, scs, np.random.default_rng(1))
+    alone = []
+    for r in reqs:
+        t = srv.submit(srv.request(**r))
+        outs, _ = _wait(srv, [t])
+        alone.append(outs[t].clone())
+    # hold the first three requests on the host for 200 ms: the queue is first in, first out,
+    # so the other five queue up behind them and all eight are ready when a stream takes them
+    N.exm_debug_fault(N.FAULT_SLOW, 200)
+    held = [srv.submit(srv.request(**r)) for r in reqs[:3]]
+    N.exm_debug_fault(N.FAULT_SLOW, 0)
+    b0, r0 = srv.batches()
+    tickets = held + [srv.submit(srv.request(**r)) for r in reqs[3:]]
+    outs, _ = _wait(srv, tickets)
+    b1, r1 = srv.batches()
+    assert r1 - r0 == 8 and b1 - b0 == 1, (b1 - b0, r1 - r0)
+    for k, t in enumerate(tickets):
+        assert torch.equal(outs[t], alone[k]), f"request {k} differs in the batch"
     srv.close()
 
 
