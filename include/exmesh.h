@@ -117,6 +117,13 @@ exm_status exm_sync(exm_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------------- mesh (S1) */
 
+/* BVH node width of the meshes `ctx` builds from now on (uploads, vertex updates, rebuilds): 4
+ * (4-wide nodes of 128 bytes), 8 (8-wide nodes of 80 bytes with 8-bit quantised child boxes) or 0
+ * (the default: 8-wide once the 4-wide tree of the mesh would exceed 32 MiB, a quarter of the
+ * L2).  The environment variable EXM_BVH_WIDTH sets it at exm_create.  Both widths take the same
+ * decisions (the box tests are conservative; the triangle tests are the same). */
+exm_status exm_ctx_set_bvh_width(exm_ctx* ctx, int width);
+
 /* Uploads the fixed mesh-UV carrier (V*, F*, U*, Phi* of Sec. 5): V float32 [nv,3],
  * F int32 [nf,3] (counter-clockwise seen from outside), UV float32 [nuv,2] (u right,
  * v down), Fuv int32 [nf,3] -- all DEVICE pointers, copied.  Computes the per-vertex
@@ -127,7 +134,8 @@ exm_status exm_mesh_create(exm_ctx* ctx, const float* V, int nv, const int32_t* 
                            const float* UV, int nuv, const int32_t* Fuv, void* stream, exm_mesh** out);
 /* Replaces the vertex positions (DEVICE float32 [nv,3]), recomputes frames and BVH. */
 exm_status exm_mesh_update_vertices(exm_mesh* mesh, const float* V, void* stream);
-/* Rebuilds the BVH (Morton order, locally-ordered clustering, 4-wide nodes; one triangle per leaf). */
+/* Rebuilds the BVH (Morton order, locally-ordered clustering, then 4- or 8-wide nodes
+ * (exm_ctx_set_bvh_width); one triangle per leaf). */
 exm_status exm_bvh_build(exm_mesh* mesh, void* stream);
 void exm_mesh_destroy(exm_mesh* mesh);
 /* Device pointers to the mesh's per-vertex unit normals [nv,3] and per-UV-vertex unit
@@ -137,10 +145,15 @@ exm_status exm_mesh_frames(const exm_mesh* mesh, const float** normals, const fl
 /* Asset export and import (no counterpart in the paper: the serving registry's reload path).
  * An exported asset is the mesh-UV carrier and its BVH in EXM_ASSET_SECTIONS little-endian
  * sections: V float32 [nv,3], F int32 [nf,3], UV float32 [nuv,2], Fuv int32 [nf,3], the BVH's
- * 4-wide nodes (node_bytes each: child boxes lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4],
- * then four int32 child references: >= 0 a node, < 0 the leaf ~k, 0x7fffffff an empty slot;
- * node 0 is the root), its triangle records (three float4 per leaf: the vertices, the original
- * face id in the first .w) and its bounding sphere (float4 centre, R^2). */
+ * nodes (node 0 is the root), its triangle records (three float4 per triangle: the vertices, the
+ * original face id in the first .w) and its bounding sphere (float4 centre, R^2).  A node of
+ * node_bytes 128 is 4-wide: child boxes lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4], then four
+ * int32 child references (>= 0 a node, < 0 the triangle record ~k, 0x7fffffff an empty slot).
+ * A node of node_bytes 80 is 8-wide compressed: float origin p.xyz and the biased exponents e of
+ * the per-axis grid steps 2^(e-127) in bytes 0-2 of word 3; then uint32 child_base, tri_base and
+ * ni | nt << 8; then the child boxes quantised on that grid, qlo.x[8] qlo.y[8] qlo.z[8] qhi.x[8]
+ * qhi.y[8] qhi.z[8] (bytes; plane = p + q 2^(e-127)): slots 0..ni-1 are the nodes child_base + c,
+ * slots ni..ni+nt-1 the triangle records tri_base + c - ni. */
 #define EXM_ASSET_VERSION 1
 #define EXM_ASSET_SECTIONS 7
 typedef struct {

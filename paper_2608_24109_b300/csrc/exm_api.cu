@@ -130,6 +130,7 @@ exm_status exm_create(int device, exm_ctx** out) {
     if (!c) return exm_fail(EXM_ERR_OOM, "exm_create: host allocation");
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (const char* w = getenv("EXM_BVH_WIDTH")) c->bvh_width = atoi(w) == 8 ? 8 : (atoi(w) == 4 ? 4 : 0);
     if (exm_malloc((void**)&c->d_status, sizeof(uint32_t)) != cudaSuccess) {
         delete c;
         return exm_fail(EXM_ERR_OOM, "exm_create: status word");
@@ -146,6 +147,12 @@ void exm_destroy(exm_ctx* c) {
     cudaFree(c->d_acc);
     cudaFree(c->scratch);
     delete c;
+}
+
+exm_status exm_ctx_set_bvh_width(exm_ctx* c, int width) {
+    if (!c || (width != 0 && width != 4 && width != 8)) return exm_fail(EXM_ERR_ARG, "exm_ctx_set_bvh_width");
+    c->bvh_width = width;
+    return EXM_OK;
 }
 
 exm_status exm_sync(exm_ctx* c, void* stream) {
@@ -171,7 +178,8 @@ exm_status exm_sync(exm_ctx* c, void* stream) {
 static void mesh_free(exm_mesh* m) {
     void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nfix, m->tfix,
                     m->tris, m->codes, m->codes_sorted, m->ids, m->ids_sorted, m->child, m->bounds,
-                    m->scene_box, m->sort_tmp, m->nodes4, m->sphere, m->frontier, m->frontier_cnt,
+                    m->scene_box, m->sort_tmp, m->nodes4, m->sphere, m->frontier, m->frontier_cnt, m->nodes8,
+                    m->tris8, m->n_tris8,
                     m->ploc_c, m->ploc_nn, m->ploc_flag, m->ploc_scan, m->scan_tmp};
     for (void* p : ptrs) cudaFree(p);
 }

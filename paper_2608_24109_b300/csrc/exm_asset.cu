@@ -46,10 +46,26 @@ __global__ void asset_check_kernel(const int32_t* __restrict__ F, const int32_t*
     if (b) atomicOr(bad, b);
 }
 
+// The same for 8-wide compressed nodes: a node's node children child_base .. child_base + ni - 1
+// and triangle records tri_base .. tri_base + nt - 1 must exist, with ni + nt <= 8.
+__global__ void asset_check8_kernel(const float4* __restrict__ nodes8, uint32_t n_nodes, int nf, uint32_t* bad) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_nodes) return;
+    const float4 w1 = nodes8[kNode8 * (size_t)t + 1];
+    const uint64_t cb = __float_as_uint(w1.x), tb = __float_as_uint(w1.y);
+    const uint32_t ni = __float_as_uint(w1.z) & 0xffu, nt = (__float_as_uint(w1.z) >> 8) & 0xffu;
+    if (ni + nt > 8 || (ni && cb + ni > n_nodes) || (nt && tb + nt > (uint64_t)nf)) atomicOr(bad, 2u);
+}
+
 // The corrupt-asset injector: the root's first child that is a node is made the root again,
 // a cycle that every index check passes.
-__global__ void asset_corrupt_kernel(float4* nodes4) {
-    int* ref = reinterpret_cast<int*>(&nodes4[6].x);
+__global__ void asset_corrupt_kernel(float4* nodes, int width) {
+    if (width == 8) {  // the root's node children start at the root
+        uint32_t* w1 = reinterpret_cast<uint32_t*>(&nodes[1].x);
+        if (w1[2] & 0xffu) w1[0] = 0u;
+        return;
+    }
+    int* ref = reinterpret_cast<int*>(&nodes[6].x);
     for (int k = 0; k < 4; ++k)
         if (ref[k] >= 0 && ref[k] != kEmptyRef) {
             ref[k] = 0;
@@ -66,7 +82,7 @@ static void asset_sizes(const exm_mesh* m, uint64_t bytes[EXM_ASSET_SECTIONS]) {
     bytes[1] = (uint64_t)m->nf * 12;
     bytes[2] = (uint64_t)m->nuv * 8;
     bytes[3] = (uint64_t)m->nf * 12;
-    bytes[4] = (uint64_t)m->n_nodes * 8 * sizeof(float4);
+    bytes[4] = (uint64_t)m->n_nodes * (m->width == 8 ? kNode8 : 8) * sizeof(float4);
     bytes[5] = (uint64_t)m->nf * 3 * sizeof(float4);
     bytes[6] = sizeof(float4);
 }
@@ -77,7 +93,7 @@ exm_status exm_mesh_export_info(const exm_mesh* m, exm_asset_info* info) {
     if (!m || !info) return exm_fail(EXM_ERR_ARG, "exm_mesh_export_info: NULL argument");
     memset(info, 0, sizeof(*info));
     info->version = EXM_ASSET_VERSION;
-    info->node_bytes = 8 * sizeof(float4);
+    info->node_bytes = (m->width == 8 ? kNode8 : 8) * sizeof(float4);
     info->nv = m->nv;
     info->nf = m->nf;
     info->nuv = m->nuv;
@@ -94,7 +110,8 @@ exm_status exm_mesh_export(const exm_mesh* m, void* const sections[EXM_ASSET_SEC
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t bytes[EXM_ASSET_SECTIONS];
     asset_sizes(m, bytes);
-    const void* src[EXM_ASSET_SECTIONS] = {m->V, m->F, m->UV, m->Fuv, m->nodes4, m->tris, m->sphere};
+    const void* src[EXM_ASSET_SECTIONS] = {m->V, m->F, m->UV, m->Fuv, m->width == 8 ? m->nodes8 : m->nodes4,
+                                           m->width == 8 ? m->tris8 : m->tris, m->sphere};
     for (int k = 0; k < EXM_ASSET_SECTIONS; ++k) {
         exm_status st = exm_cuda_check(cudaMemcpyAsync(sections[k], src[k], bytes[k], cudaMemcpyDefault, s),
                                        "exm_mesh_export copy");
@@ -110,10 +127,12 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
     if (!c || !info || !sections) return exm_fail(EXM_ERR_ARG, "exm_mesh_import: NULL argument");
     for (int k = 0; k < EXM_ASSET_SECTIONS; ++k)
         if (!sections[k]) return exm_fail(EXM_ERR_ARG, "exm_mesh_import: NULL section");
-    if (info->version != EXM_ASSET_VERSION || info->node_bytes != 8 * sizeof(float4))
+    if (info->version != EXM_ASSET_VERSION ||
+        (info->node_bytes != 8 * sizeof(float4) && info->node_bytes != kNode8 * sizeof(float4)))
         return exm_fail(EXM_ERR_ARG, "exm_mesh_import: asset version or node format differs from this library's");
+    const int width = info->node_bytes == kNode8 * sizeof(float4) ? 8 : 4;
     if (info->nv < 3 || info->nf < 1 || info->nuv < 3 || info->nf > (1 << 28) || info->nv > (1 << 28) ||
-        info->nuv > (1 << 28) || info->n_nodes < 1 || info->n_nodes > (uint32_t)(info->nf > 1 ? info->nf - 1 : 1))
+        info->nuv > (1 << 28) || info->n_nodes < 1 || info->n_nodes > (uint32_t)info->nf)
         return exm_fail(EXM_ERR_ARG, "exm_mesh_import: sizes");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -152,11 +171,16 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
     if (st == EXM_OK) {
         uint64_t bytes[EXM_ASSET_SECTIONS];
         m->n_nodes = info->n_nodes;
+        m->width = width;
         asset_sizes(m, bytes);
         for (int k = 4; k < EXM_ASSET_SECTIONS && st == EXM_OK; ++k)
             if (info->bytes[k] != bytes[k]) st = exm_fail(EXM_ERR_ARG, "exm_mesh_import: BVH section size");
+        if (st == EXM_OK && width == 8 && !m->nodes8 &&
+            (exm_malloc((void**)&m->nodes8, (size_t)m->nf * kNode8 * sizeof(float4)) != cudaSuccess ||
+             exm_malloc((void**)&m->tris8, (size_t)m->nf * 3 * sizeof(float4)) != cudaSuccess))
+            st = exm_fail(EXM_ERR_OOM, "exm_mesh_import: BVH buffers");
         if (st == EXM_OK) {
-            void* dst[3] = {m->nodes4, m->tris, m->sphere};
+            void* dst[3] = {width == 8 ? m->nodes8 : m->nodes4, width == 8 ? m->tris8 : m->tris, m->sphere};
             for (int k = 0; k < 3 && st == EXM_OK; ++k)
                 st = exm_cuda_check(cudaMemcpyAsync(dst[k], sections[4 + k], bytes[4 + k], cudaMemcpyDefault, s),
                                     "import BVH copy");
@@ -164,8 +188,11 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
         if (st == EXM_OK) {
             cudaMemsetAsync(bad, 0, 4, s);
             const size_t n = (size_t)std::max((uint32_t)m->nf, m->n_nodes);
-            asset_check_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->F, m->Fuv, m->nf, m->nv, m->nuv, m->nodes4,
-                                                                 m->n_nodes, m->tris, bad);
+            asset_check_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->F, m->Fuv, m->nf, m->nv, m->nuv,
+                                                                 width == 8 ? nullptr : m->nodes4, m->n_nodes,
+                                                                 width == 8 ? m->tris8 : m->tris, bad);
+            if (width == 8)
+                asset_check8_kernel<<<exm_blocks(m->n_nodes, 256), 256, 0, s>>>(m->nodes8, m->n_nodes, m->nf, bad);
             uint32_t h = 0;
             st = exm_cuda_check(cudaMemcpyAsync(&h, bad, 4, cudaMemcpyDeviceToHost, s), "import check");
             if (st == EXM_OK) st = exm_cuda_check(cudaStreamSynchronize(s), "import check");
@@ -174,7 +201,8 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
                                                ((h & 2u) ? "a BVH node reference is out of range"
                                                          : "a BVH triangle record names no face"));
         }
-        if (st == EXM_OK && exm_fault_take(kFaultCorrupt)) asset_corrupt_kernel<<<1, 1, 0, s>>>(m->nodes4);
+        if (st == EXM_OK && exm_fault_take(kFaultCorrupt))
+            asset_corrupt_kernel<<<1, 1, 0, s>>>(width == 8 ? m->nodes8 : m->nodes4, width);
         if (st == EXM_OK) {
             m->stamp = exm_next_stamp();
             st = exm_cuda_check(cudaStreamSynchronize(s), "exm_mesh_import");

@@ -257,6 +257,124 @@ __global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const
     N[7] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
+// ---- 8-wide compressed nodes (the node format of Ylitie, Karras and Laine, "Efficient
+// incoherent ray traversal on GPUs through compressed wide BVHs", HPG 2017).  A node holds up
+// to eight children: its box origin p and per-axis power-of-two steps 2^e, and each child's box
+// quantised to 8 bits per plane on that grid, rounded outwards (lo down, hi up), so a decoded
+// box contains the child's (padded) box.  Internal children come first, in slots 0..ni-1, and
+// are the consecutive nodes child_base + c; the triangle children follow, in slots ni..ni+nt-1,
+// and are the consecutive triangle records tri_base + (c - ni).  80 bytes (5 x 16):
+//   [0] p.x p.y p.z, ex | ey << 8 | ez << 16 (biased exponents of the steps)
+//   [1] child_base, tri_base, ni | nt << 8, 0
+//   [2] qlo.x[8] qlo.y[8]   [3] qlo.z[8] qhi.x[8]   [4] qhi.y[8] qhi.z[8]
+// An empty slot has qlo = 255 and qhi = 0.
+
+// Biased exponent e with 2^(e - 127) * 255 >= ext (ext > 0).
+__device__ __forceinline__ uint32_t step_exponent(float ext) {
+    const float x = __fdiv_ru(ext, 255.0f);
+    const uint32_t b = __float_as_uint(x);
+    uint32_t e = (b >> 23) & 0xffu;
+    if (b & 0x7fffffu) ++e;
+    return max(e, 1u);
+}
+
+__global__ void collapse8_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
+                                 const int2* __restrict__ in, const uint32_t* __restrict__ n_in, int2* out,
+                                 uint32_t* n_out, uint32_t* n_nodes, uint32_t* n_tris, const float4* __restrict__ tris_in,
+                                 float4* tris_out, float4* nodes8) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *n_in) return;
+    const int b = in[t].x, q = in[t].y;
+    int slots[8];
+    int ns = 2;
+    slots[0] = child[2 * b];
+    slots[1] = child[2 * b + 1];
+    while (ns < 8) {
+        int pick = -1;
+        float best = -1.0f;
+        for (int k = 0; k < ns; ++k) {
+            if (slots[k] < 0) continue;
+            const float* bb = bounds + 6 * (size_t)slots[k];
+            const float dx = bb[3] - bb[0], dy = bb[4] - bb[1], dz = bb[5] - bb[2];
+            const float a = dx * dy + dy * dz + dz * dx;
+            if (a > best) { best = a; pick = k; }
+        }
+        if (pick < 0) break;
+        const int c = slots[pick];
+        slots[pick] = child[2 * c];
+        slots[ns++] = child[2 * c + 1];
+    }
+    // internal children first, then the triangles
+    int order[8], ni = 0, nt = 0;
+    for (int k = 0; k < ns; ++k)
+        if (slots[k] >= 0) order[ni++] = slots[k];
+    for (int k = 0; k < ns; ++k)
+        if (slots[k] < 0) order[ni + nt++] = slots[k];
+    const uint32_t cbase = ni ? atomicAdd(n_nodes, (uint32_t)ni) : 0u;
+    const uint32_t tbase = nt ? atomicAdd(n_tris, (uint32_t)nt) : 0u;
+    for (int k = 0; k < ni; ++k) out[atomicAdd(n_out, 1u)] = make_int2(order[k], (int)(cbase + k));
+    for (int k = 0; k < nt; ++k) {
+        const int leaf = ~order[ni + k];
+        for (int v = 0; v < 3; ++v) tris_out[3 * (size_t)(tbase + k) + v] = tris_in[3 * (size_t)leaf + v];
+    }
+    // the node's grid: origin at its box's low corner, steps covering its extent in 255
+    const float* nb = bounds + 6 * (size_t)b;
+    uint32_t e[3];
+    float inv_step[3];
+    for (int a = 0; a < 3; ++a) {
+        e[a] = step_exponent(fmaxf(__fsub_ru(nb[3 + a], nb[a]), 1e-30f));
+        inv_step[a] = __uint_as_float((254u - e[a]) << 23);  // 2^-(e - 127)
+    }
+    uint32_t qlo[3][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}}, qhi[3][2] = {{0u, 0u}, {0u, 0u}, {0u, 0u}};
+    for (int k = 0; k < 8; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            uint32_t lo = 255u, hi = 0u;
+            if (k < ns) {
+                const float* cb = bounds + 6 * (size_t)bounds_index(n, order[k]);
+                const float l = floorf(__fmul_rd(__fsub_rd(cb[a], nb[a]), inv_step[a]));
+                const float h = ceilf(__fmul_ru(__fsub_ru(cb[3 + a], nb[a]), inv_step[a]));
+                lo = (uint32_t)fminf(fmaxf(l, 0.0f), 255.0f);
+                hi = (uint32_t)fminf(fmaxf(h, 0.0f), 255.0f);
+            }
+            qlo[a][k >> 2] |= lo << (8 * (k & 3));
+            qhi[a][k >> 2] |= hi << (8 * (k & 3));
+        }
+    }
+    float4* N = nodes8 + kNode8 * (size_t)q;
+    N[0] = make_float4(nb[0], nb[1], nb[2], __uint_as_float(e[0] | (e[1] << 8) | (e[2] << 16)));
+    N[1] = make_float4(__uint_as_float(cbase), __uint_as_float(tbase), __uint_as_float((uint32_t)ni | ((uint32_t)nt << 8)),
+                       0.0f);
+    N[2] = make_float4(__uint_as_float(qlo[0][0]), __uint_as_float(qlo[0][1]), __uint_as_float(qlo[1][0]),
+                       __uint_as_float(qlo[1][1]));
+    N[3] = make_float4(__uint_as_float(qlo[2][0]), __uint_as_float(qlo[2][1]), __uint_as_float(qhi[0][0]),
+                       __uint_as_float(qhi[0][1]));
+    N[4] = make_float4(__uint_as_float(qhi[1][0]), __uint_as_float(qhi[1][1]), __uint_as_float(qhi[2][0]),
+                       __uint_as_float(qhi[2][1]));
+}
+
+// A one-triangle mesh: a single 8-wide node holding triangle 0.
+__global__ void single8_kernel(const float* __restrict__ bounds, const float4* __restrict__ tris_in, float4* tris_out,
+                               float4* nodes8) {
+    for (int v = 0; v < 3; ++v) tris_out[v] = tris_in[v];
+    uint32_t e[3];
+    for (int a = 0; a < 3; ++a) e[a] = step_exponent(fmaxf(__fsub_ru(bounds[3 + a], bounds[a]), 1e-30f));
+    // the child's box is the node's box: planes 0 and 255 contain it
+    const uint32_t lo = 0x000000u | 0xffffff00u, hi = 0x000000ffu;
+    float4* N = nodes8;
+    N[0] = make_float4(bounds[0], bounds[1], bounds[2], __uint_as_float(e[0] | (e[1] << 8) | (e[2] << 16)));
+    N[1] = make_float4(__uint_as_float(0u), __uint_as_float(0u), __uint_as_float(1u << 8), 0.0f);
+    N[2] = make_float4(__uint_as_float(lo), __uint_as_float(0xffffffffu), __uint_as_float(lo), __uint_as_float(0xffffffffu));
+    N[3] = make_float4(__uint_as_float(lo), __uint_as_float(0xffffffffu), __uint_as_float(hi), 0.0f);
+    N[4] = make_float4(__uint_as_float(hi), 0.0f, __uint_as_float(hi), 0.0f);
+}
+
+__global__ void seed8_kernel(int2* in, uint32_t* n_in, uint32_t* n_nodes, uint32_t* n_tris) {
+    in[0] = make_int2(0, 0);
+    *n_in = 1;
+    *n_nodes = 1;
+    *n_tris = 0;
+}
+
 // A one-triangle mesh: a single 4-wide node holding leaf 0.
 __global__ void single4_kernel(const float* __restrict__ bounds, float4* nodes4) {
     float4* N = nodes4;
@@ -282,6 +400,12 @@ __global__ void sphere_centre_kernel(const float4* __restrict__ nodes4, float4* 
         c[a] = 0.5f * (l + h);
     }
     *sphere = make_float4(c[0], c[1], c[2], 0.0f);
+}
+
+// The same centre from the binary root's box (the 8-wide build).
+__global__ void sphere8_centre_kernel(const float* __restrict__ bounds, int n, float4* sphere) {
+    const float* b = bounds + 6 * (size_t)(n > 1 ? 0 : n - 1);
+    *sphere = make_float4(0.5f * (b[0] + b[3]), 0.5f * (b[1] + b[4]), 0.5f * (b[2] + b[5]), 0.0f);
 }
 
 __global__ void sphere_radius_kernel(const float4* __restrict__ tris, int nf, float4* sphere) {
@@ -367,6 +491,49 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
             mcl = (int)h[0];
             std::swap(cin, cout);
         }
+    }
+    // the node width: 8-wide compressed nodes when asked for, or by default once the 4-wide tree
+    // (128 B per node, 48 B per triangle) would outgrow a quarter of the L2
+    int width = m->ctx->bvh_width;
+    if (width == 0) width = (size_t)n * (128 + 48) > (32u << 20) ? 8 : 4;
+    if (width == 8 && (size_t)n >= (1u << 27)) width = 4;  // the 8-wide stack entries hold 24-bit node indices
+    m->width = width;
+    if (width == 8) {
+        if (!m->nodes8) {
+            const size_t nn = (size_t)n;
+            if (exm_malloc((void**)&m->nodes8, nn * kNode8 * sizeof(float4)) != cudaSuccess ||
+                exm_malloc((void**)&m->tris8, nn * 3 * sizeof(float4)) != cudaSuccess ||
+                exm_malloc((void**)&m->n_tris8, 4) != cudaSuccess)
+                return exm_fail(EXM_ERR_OOM, "BVH buffers (8-wide)");
+        }
+        if (n == 1) {
+            single8_kernel<<<1, 1, 0, s>>>(m->bounds, m->tris, m->tris8, m->nodes8);
+            m->n_nodes = 1;
+        } else {
+            int2* fin = m->frontier;
+            int2* fout = m->frontier + n;
+            uint32_t* cnt = m->frontier_cnt;  // [0] in, [1] out, [2] nodes
+            seed8_kernel<<<1, 1, 0, s>>>(fin, cnt, cnt + 2, m->n_tris8);
+            uint32_t n_in = 1;
+            for (int level = 0; n_in > 0; ++level) {
+                if (level + 1 > kStackSize8)
+                    return exm_fail(EXM_ERR_TRAVERSAL_LIMIT, "BVH deeper than the traversal stack allows");
+                cudaMemsetAsync(cnt + 1, 0, 4, s);
+                collapse8_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, fin, cnt, fout, cnt + 1,
+                                                                      cnt + 2, m->n_tris8, m->tris, m->tris8, m->nodes8);
+                cudaMemcpyAsync(cnt, cnt + 1, 4, cudaMemcpyDeviceToDevice, s);
+                if (cudaMemcpyAsync(&n_in, cnt + 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                    cudaStreamSynchronize(s) != cudaSuccess)
+                    return exm_cuda_check(cudaGetLastError(), "BVH collapse");
+                std::swap(fin, fout);
+            }
+            if (cudaMemcpyAsync(&m->n_nodes, cnt + 2, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess)
+                return exm_cuda_check(cudaGetLastError(), "BVH node count");
+        }
+        sphere8_centre_kernel<<<1, 1, 0, s>>>(m->bounds, n, m->sphere);
+        sphere_radius_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->tris, n, m->sphere);
+        return exm_cuda_check(cudaGetLastError(), "BVH build launch");
     }
     // collapse to 4-wide nodes, level by level (the frontier size is read back per level)
     if (n == 1) {

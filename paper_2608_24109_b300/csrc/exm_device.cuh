@@ -380,7 +380,10 @@ struct BvhView {
     const float4* tris;
     const float4* nodes4;
     const float4* sphere;  // bounding sphere of the triangles: centre, R^2
+    const float4* nodes8;  // 8-wide compressed nodes (exm_bvh.cu), when the mesh uses them
 };
+constexpr int kNode8 = 5;      // float4 per 8-wide compressed node
+constexpr int kStackSize8 = 64;  // node groups on the 8-wide traversal stack: one per level
 
 // Ray parameter beyond which o + t d lies outside the bounding sphere `sp` (centre, R^2), where
 // no triangle can be hit, plus a margin (0.1% relative and 1e-4 R absolute) far above the

@@ -12,6 +12,7 @@
 struct exm_ctx {
     int device = 0;
     int num_sms = 0;
+    int bvh_width = 0;             // BVH node width of new meshes: 4, 8, 0 = by mesh size (EXM_BVH_WIDTH)
     uint32_t* d_status = nullptr;  // latched device error bits
     unsigned long long launches = 0;  // kernels launched by the library on this context
     double* d_acc = nullptr;          // FP64 accumulators of the objective calls
@@ -43,7 +44,11 @@ struct exm_mesh {
     float4* tris = nullptr;    // [nf * 3]
     float4* nodes4 = nullptr;  // [max(nf-1,1) * 8] 4-wide nodes
     float4* sphere = nullptr;  // [1] bounding sphere of the triangles: centre, inflated R^2
-    uint32_t n_nodes = 0;      // 4-wide nodes in nodes4
+    uint32_t n_nodes = 0;      // nodes of the BVH in use (4-wide in nodes4 or 8-wide in nodes8)
+    int width = 4;             // BVH in use: 4-wide (nodes4, tris) or 8-wide compressed (nodes8, tris8)
+    float4* nodes8 = nullptr;  // [n_nodes * 5] 8-wide compressed nodes
+    float4* tris8 = nullptr;   // [nf * 3] triangle records in the 8-wide nodes' order
+    uint32_t* n_tris8 = nullptr;
     int2* frontier = nullptr;  // [2 * nf] collapse frontier (binary node, 4-wide node)
     uint32_t* frontier_cnt = nullptr;
     // build scratch

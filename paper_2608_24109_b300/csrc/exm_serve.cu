@@ -67,8 +67,8 @@ struct Lane {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
-    ExmTraceJob* h_jobs = nullptr;  // pinned host, 2 x kMaxBatch
-    ExmTraceJob* d_jobs = nullptr;  // device, 2 x kMaxBatch
+    ExmTraceJob* h_jobs = nullptr;  // pinned host, 2 x 2 x kMaxBatch (closest / any, 4- / 8-wide)
+    ExmTraceJob* d_jobs = nullptr;  // device, 2 x 2 x kMaxBatch
 };
 
 struct Result {
@@ -204,8 +204,8 @@ static void launch_batch(exm_server* s, Lane& lane, const std::vector<int>& slot
         bst = relight_trace_batch(ctx, live.data(), (int)live.size(), true, lane.h_jobs, lane.d_jobs, st_);
         for (exm_relight_pass* rp : live) relight_pass_shadow_rays(ctx, rp, st_);
         if (bst == EXM_OK)
-            bst = relight_trace_batch(ctx, live.data(), (int)live.size(), false, lane.h_jobs + kMaxBatch,
-                                      lane.d_jobs + kMaxBatch, st_);
+            bst = relight_trace_batch(ctx, live.data(), (int)live.size(), false, lane.h_jobs + 2 * kMaxBatch,
+                                      lane.d_jobs + 2 * kMaxBatch, st_);
     }
     for (size_t i = 0; i < n; ++i) {
         if (pass[i]) {
@@ -309,9 +309,9 @@ exm_status exm_server_create(exm_ctx* ctx, uint64_t hbm_budget_bytes, int max_sl
     for (Lane& ln : s->lanes)
         ok = ok && cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) == cudaSuccess &&
-             cudaHostAlloc((void**)&ln.h_jobs, 2 * kMaxBatch * sizeof(ExmTraceJob), cudaHostAllocDefault) ==
+             cudaHostAlloc((void**)&ln.h_jobs, 4 * kMaxBatch * sizeof(ExmTraceJob), cudaHostAllocDefault) ==
                  cudaSuccess &&
-             exm_malloc((void**)&ln.d_jobs, 2 * kMaxBatch * sizeof(ExmTraceJob)) == cudaSuccess;
+             exm_malloc((void**)&ln.d_jobs, 4 * kMaxBatch * sizeof(ExmTraceJob)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         exm_server_destroy(s);

@@ -50,6 +50,7 @@ struct ShadeArgs {
     const float* tan;
     const float* fsign;
     BvhView bvh;
+    int bvh_width;  // 4: bvh.nodes4, 8: bvh.nodes8 (and bvh.tris in its order)
     // maps, env, frame
     MapView map;
     EnvView env;
@@ -492,16 +493,59 @@ constexpr int kRound = 24;  // node visits between refills
 
 constexpr int kTraceThreads = 128;
 
+// Byte c of a pair of words (children 0-3 in .x, 4-7 in .y) as a float: one byte permutation
+// puts it under the exponent of 2^23, and subtracting 2^23 leaves the byte's value (exact).
+__device__ __forceinline__ float q8(uint2 w, int c) {
+    return __uint_as_float(__byte_perm(c < 4 ? w.x : w.y, 0x4B000000u, 0x7540u + (uint32_t)(c & 3))) - 8388608.0f;
+}
+
+// Box tests of the eight children of an 8-wide compressed node (exm_bvh.cu): a child's plane is
+// p + q 2^e, and its ray parameter fma(q, 2^e / d, (p - o) / d) (the same conservative slab test
+// as the 4-wide nodes': the build's padding of the leaf boxes absorbs its rounding).  Returns the
+// node's child groups: node children gbase + bit, triangle children tbase + bit.
+__device__ __forceinline__ void node8_hits(const float4* N, const Ray& r, float tmax, uint32_t* gbase, uint32_t* tbase,
+                                           uint32_t* gmask, uint32_t* tmask) {
+    const float4 w0 = __ldg(N);
+    const uint4 w1 = __ldg(reinterpret_cast<const uint4*>(N) + 1);
+    const uint4 w2 = __ldg(reinterpret_cast<const uint4*>(N) + 2);
+    const uint4 w3 = __ldg(reinterpret_cast<const uint4*>(N) + 3);
+    const uint4 w4 = __ldg(reinterpret_cast<const uint4*>(N) + 4);
+    const uint32_t eb = __float_as_uint(w0.w);
+    const float sx = r.inv.x * __uint_as_float((eb & 0xffu) << 23);
+    const float sy = r.inv.y * __uint_as_float(((eb >> 8) & 0xffu) << 23);
+    const float sz = r.inv.z * __uint_as_float(((eb >> 16) & 0xffu) << 23);
+    const float bx = fmaf(w0.x, r.inv.x, r.oinv.x), by = fmaf(w0.y, r.inv.y, r.oinv.y), bz = fmaf(w0.z, r.inv.z, r.oinv.z);
+    const uint2 lox = make_uint2(w2.x, w2.y), loy = make_uint2(w2.z, w2.w), loz = make_uint2(w3.x, w3.y);
+    const uint2 hix = make_uint2(w3.z, w3.w), hiy = make_uint2(w4.x, w4.y), hiz = make_uint2(w4.z, w4.w);
+    // near / far planes of each axis chosen by the ray's direction signs
+    const uint2 nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
+    const uint2 ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
+    const uint2 nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
+    uint32_t h = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float t0 = fmaxf(fmax3(fmaf(q8(nx, c), sx, bx), fmaf(q8(ny, c), sy, by), fmaf(q8(nz, c), sz, bz)), 0.0f);
+        const float t1 = fminf(fmin3(fmaf(q8(fx, c), sx, bx), fmaf(q8(fy, c), sy, by), fmaf(q8(fz, c), sz, bz)), tmax);
+        h |= (t0 <= t1 ? 1u : 0u) << c;
+    }
+    const uint32_t ni = w1.z & 0xffu, nt = (w1.z >> 8) & 0xffu;
+    h &= (1u << (ni + nt)) - 1u;
+    *gbase = w1.x;
+    *tbase = w1.y;
+    *gmask = h & ((1u << ni) - 1u);
+    *tmask = h >> ni;
+}
+
 using TraceJob = ExmTraceJob;
 
 // The traversal loop.  Single queue (BATCH false): the chunk's queue of A, claimed kPool rays at
 // a time.  Batched: the queues of `jobs`, whose pools are numbered one after another; a warp
 // claims a pool number, finds its queue, and each lane keeps the BVH of the queue its ray came
 // from, so the lanes of a warp may trace rays of different assets.
-template <bool CLOSEST, bool COUNT, bool BATCH>
+template <bool CLOSEST, bool COUNT, bool BATCH, bool W8>
 __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* __restrict__ jobs, int njobs,
                                            uint32_t* batch_cursor) {
-    int stack[kStackSize4];
+    int stack[W8 ? kStackSize8 : kStackSize4];
     __shared__ uint32_t s_pool_end[BATCH ? kMaxBatch : 1];  // BATCH: pools of queues 0..j
     __shared__ uint32_t s_count[BATCH ? kMaxBatch : 1];     // BATCH: rays of queue j
     uint32_t n = 0;          // single queue: its rays
@@ -529,6 +573,9 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
     const unsigned lt = (1u << lane) - 1u;
     uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
     int sp = 0, node = 0, best = -1, steps = 0;
+    // 8-wide traversal: the current group of node children (base, mask of those left to visit)
+    // and of triangle children (base, mask of those left to test)
+    uint32_t gbase = 0, gmask = 0, tbase = 0, tmask = 0;
     float bt = INFINITY, bdet = 0.0f;
     float tclip = 0.0f;  // where the ray leaves the triangles' bounding sphere
     bool active = false;
@@ -575,6 +622,7 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                     job = pjob;
                     rays = jobs[job].rays;
                     bvh.nodes4 = jobs[job].nodes4;
+                    bvh.nodes8 = jobs[job].nodes4;
                     bvh.tris = jobs[job].tris;
                     bvh.sphere = jobs[job].sphere;
                 }
@@ -583,6 +631,7 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                 tclip = sphere_exit(r.o, r.d, __ldg(bvh.sphere));
                 slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
                 sp = 0; node = 0; best = -1; steps = 0; bt = INFINITY; bdet = 0.0f;
+                gbase = 0; gmask = 1u; tmask = 0u;  // 8-wide: the root alone
                 active = true;
                 ++c_rays;
             }
@@ -599,68 +648,104 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
         // per iteration whatever its lanes found in their last node
         steps += kRound;  // the cap is checked once per round: at most kTraversalCap + kRound items
         if (steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; }
-        for (int it = 0; it < kRound && !done; ++it) {
-            int next = INT_MIN;  // none: pop (leaf ~k is negative, ~0 == -1)
-            if (node < 0) {
-                ++c_tris;
-                float T, det;
-                int id;
-                if (tri_test(bvh, ~node, r, &T, &det, &id)) {
-                    if (!CLOSEST) { hit = true; done = true; break; }
-                    const float t = sdiv(T, det);
-                    if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+        if constexpr (W8) {
+            // one item per iteration: an 8-wide node (the next child of the current node group)
+            // or one triangle of the current triangle group; a visited node's remaining group is
+            // pushed as one stack entry (base << 8 | mask)
+            for (int it = 0; it < kRound && !done; ++it) {
+                if (tmask) {
+                    const int k = __ffs(tmask) - 1;
+                    tmask &= tmask - 1u;
+                    ++c_tris;
+                    float T, det;
+                    int id;
+                    if (tri_test(bvh, (int)(tbase + k), r, &T, &det, &id)) {
+                        if (!CLOSEST) { hit = true; done = true; break; }
+                        const float t = sdiv(T, det);
+                        if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+                    }
+                    continue;
                 }
-            } else {
+                if (!gmask) {
+                    if (sp == 0) { done = true; break; }
+                    const uint32_t e = (uint32_t)stack[--sp];
+                    gbase = e >> 8;
+                    gmask = e & 0xffu;
+                }
+                const uint32_t nd = gbase + (uint32_t)(__ffs(gmask) - 1);
+                gmask &= gmask - 1u;
+                if (gmask) {
+                    if (sp >= kStackSize8) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
+                    stack[sp++] = (int)((gbase << 8) | gmask);
+                }
                 ++c_nodes;
-                const float4* N = bvh.nodes4 + 8 * (size_t)node;
-                // near / far planes of each axis chosen by the ray's direction signs
-                const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
-                const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
-                const float4 rf = __ldg(N + 6);
-                const float tmax = CLOSEST ? fminf(bt, tclip) : tclip;
-                float tc[4];
-                const int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
-                bool hc[4];
-#define EXM_BOX(C, c)                                                                                          \
-    {                                                                                                          \
-        const float t0 = fmaxf(fmax3(fmaf(qx.c, r.inv.x, r.oinv.x), fmaf(qy.c, r.inv.y, r.oinv.y),                \
-                                     fmaf(qz.c, r.inv.z, r.oinv.z)), 0.0f);                                    \
-        const float t1 = fminf(fmin3(fmaf(fx.c, r.inv.x, r.oinv.x), fmaf(fy.c, r.inv.y, r.oinv.y),                \
-                                     fmaf(fz.c, r.inv.z, r.oinv.z)), tmax);                                    \
-        tc[C] = t0;                                                                                            \
-        hc[C] = t0 <= t1 && ref[C] != kEmptyChild;                                                             \
-    }
-                EXM_BOX(0, x)
-                EXM_BOX(1, y)
-                EXM_BOX(2, z)
-                EXM_BOX(3, w)
-#undef EXM_BOX
-                // closest hit: continue with the nearest hit child; any hit: with the first in slot
-                // order (an unoccluded shadow ray opens every box it crosses whatever the order,
-                // so the sort is skipped); push the others
-                int nc = -1;
-                if (CLOSEST) {
-                    float tn = INFINITY;
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
+                node8_hits(bvh.nodes8 + kNode8 * (size_t)nd, r, CLOSEST ? fminf(bt, tclip) : tclip, &gbase, &tbase,
+                           &gmask, &tmask);
+            }
+        } else {
+            for (int it = 0; it < kRound && !done; ++it) {
+                int next = INT_MIN;  // none: pop (leaf ~k is negative, ~0 == -1)
+                if (node < 0) {
+                    ++c_tris;
+                    float T, det;
+                    int id;
+                    if (tri_test(bvh, ~node, r, &T, &det, &id)) {
+                        if (!CLOSEST) { hit = true; done = true; break; }
+                        const float t = sdiv(T, det);
+                        if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
+                    }
                 } else {
-#pragma unroll
-                    for (int c = 3; c >= 0; --c)
-                        if (hc[c]) nc = c;
+                    ++c_nodes;
+                    const float4* N = bvh.nodes4 + 8 * (size_t)node;
+                    // near / far planes of each axis chosen by the ray's direction signs
+                    const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
+                    const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
+                    const float4 rf = __ldg(N + 6);
+                    const float tmax = CLOSEST ? fminf(bt, tclip) : tclip;
+                    float tc[4];
+                    const int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
+                    bool hc[4];
+    #define EXM_BOX(C, c)                                                                                          \
+        {                                                                                                          \
+            const float t0 = fmaxf(fmax3(fmaf(qx.c, r.inv.x, r.oinv.x), fmaf(qy.c, r.inv.y, r.oinv.y),                \
+                                         fmaf(qz.c, r.inv.z, r.oinv.z)), 0.0f);                                    \
+            const float t1 = fminf(fmin3(fmaf(fx.c, r.inv.x, r.oinv.x), fmaf(fy.c, r.inv.y, r.oinv.y),                \
+                                         fmaf(fz.c, r.inv.z, r.oinv.z)), tmax);                                    \
+            tc[C] = t0;                                                                                            \
+            hc[C] = t0 <= t1 && ref[C] != kEmptyChild;                                                             \
+        }
+                    EXM_BOX(0, x)
+                    EXM_BOX(1, y)
+                    EXM_BOX(2, z)
+                    EXM_BOX(3, w)
+    #undef EXM_BOX
+                    // closest hit: continue with the nearest hit child; any hit: with the first in slot
+                    // order (an unoccluded shadow ray opens every box it crosses whatever the order,
+                    // so the sort is skipped); push the others
+                    int nc = -1;
+                    if (CLOSEST) {
+                        float tn = INFINITY;
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
+                    } else {
+    #pragma unroll
+                        for (int c = 3; c >= 0; --c)
+                            if (hc[c]) nc = c;
+                    }
+                    // a node pushes at most 3 children; the build keeps 3 entries per level within the stack
+                    if (sp > kStackSize4 - 3) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
+    #pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (hc[c] && c != nc) stack[sp++] = ref[c];
+                    if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
                 }
-                // a node pushes at most 3 children; the build keeps 3 entries per level within the stack
-                if (sp > kStackSize4 - 3) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (hc[c] && c != nc) stack[sp++] = ref[c];
-                if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
+                if (next == INT_MIN) {
+                    if (sp == 0) { done = true; break; }
+                    next = stack[--sp];
+                }
+                node = next;
             }
-            if (next == INT_MIN) {
-                if (sp == 0) { done = true; break; }
-                next = stack[--sp];
-            }
-            node = next;
         }
         if (done) {
             if (CLOSEST) {
@@ -683,16 +768,17 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
     }
 }
 
-template <bool CLOSEST, bool COUNT>
+template <bool CLOSEST, bool COUNT, bool W8>
 __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
-    trace_body<CLOSEST, COUNT, false>(A, nullptr, 0, nullptr);
+    trace_body<CLOSEST, COUNT, false, W8>(A, nullptr, 0, nullptr);
 }
 
-// The batched tracer: one persistent launch over the ray queues of several relight requests.
-template <bool CLOSEST>
+// The batched tracer: one persistent launch over the ray queues of several relight requests
+// (whose assets all use W8 nodes or all 4-wide ones).
+template <bool CLOSEST, bool W8>
 __global__ void __launch_bounds__(kTraceThreads, 8) trace_batch_kernel(ShadeArgs A, const TraceJob* __restrict__ jobs,
                                                                        int njobs, uint32_t* cursor) {
-    trace_body<CLOSEST, false, true>(A, jobs, njobs, cursor);
+    trace_body<CLOSEST, false, true, W8>(A, jobs, njobs, cursor);
 }
 
 // ------------------------------------------------------------------ shading (warp per pixel)
@@ -1288,7 +1374,11 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     ShadeArgs A{};
     A.V = m->V; A.F = m->F; A.UV = m->UV; A.Fuv = m->Fuv;
     A.nrm = m->nrm; A.tan = m->tan; A.fsign = m->fsign;
-    A.bvh.tris = m->tris; A.bvh.nodes4 = m->nodes4; A.bvh.sphere = m->sphere;
+    A.bvh.tris = m->width == 8 ? m->tris8 : m->tris;
+    A.bvh.nodes4 = m->nodes4;
+    A.bvh.nodes8 = m->nodes8;
+    A.bvh.sphere = m->sphere;
+    A.bvh_width = m->width;
     A.map.data = maps; A.map.W = mapW; A.map.H = mapH; A.map.wrap_u = (p->flags & EXM_FLAG_WRAP_U) != 0;
     A.env.texel = e->texel; A.env.cdf = e->cdf; A.env.rguide = e->rguide; A.env.cguide = e->cguide;
     A.env.W = e->W; A.env.H = e->H;
@@ -1407,8 +1497,14 @@ template <bool CLOSEST>
 static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, cudaStream_t s) {
     const int blocks = ctx->num_sms * 8;
     time_begin(f, p, CLOSEST ? 1 : 0, s);
-    if (p->flags & EXM_FLAG_COUNT_WORK) trace_kernel<CLOSEST, true><<<blocks, kTraceThreads, 0, s>>>(A);
-    else trace_kernel<CLOSEST, false><<<blocks, kTraceThreads, 0, s>>>(A);
+    const bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
+    if (A.bvh_width == 8) {
+        if (count) trace_kernel<CLOSEST, true, true><<<blocks, kTraceThreads, 0, s>>>(A);
+        else trace_kernel<CLOSEST, false, true><<<blocks, kTraceThreads, 0, s>>>(A);
+    } else {
+        if (count) trace_kernel<CLOSEST, true, false><<<blocks, kTraceThreads, 0, s>>>(A);
+        else trace_kernel<CLOSEST, false, false><<<blocks, kTraceThreads, 0, s>>>(A);
+    }
     time_end(f, p, s);
     ctx->launches += 1;
 }
@@ -1648,16 +1744,31 @@ uint64_t relight_queue_rays(int views, int W, int H, const exm_params* p) {
     return P32 * per_pixel;
 }
 
+static exm_status relight_trace_batch_width(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
+                                            int width, ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s);
+
 exm_status relight_trace_batch(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
                                ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s) {
     if (n < 1 || n > kMaxBatch) return exm_fail(EXM_ERR_ARG, "relight batch: size");
+    // one launch for the assets with 4-wide nodes, one for those with 8-wide nodes
+    for (const int width : {4, 8}) {
+        exm_status st = relight_trace_batch_width(ctx, passes, n, closest, width, h_jobs + (width == 8 ? n : 0),
+                                                  d_jobs + (width == 8 ? n : 0), s);
+        if (st != EXM_OK) return st;
+    }
+    return EXM_OK;
+}
+
+static exm_status relight_trace_batch_width(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
+                                            int width, ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s) {
     int k = 0;
     uint32_t* cursor = nullptr;
     for (int i = 0; i < n; ++i) {
         const ShadeArgs& A = passes[i]->A;
         if (closest && !passes[i]->c.indirect) continue;
+        if (A.bvh_width != width) continue;
         TraceJob& j = h_jobs[k++];
-        j.nodes4 = A.bvh.nodes4;
+        j.nodes4 = width == 8 ? A.bvh.nodes8 : A.bvh.nodes4;
         j.tris = A.bvh.tris;
         j.sphere = A.bvh.sphere;
         j.rays = A.rays;
@@ -1674,8 +1785,13 @@ exm_status relight_trace_batch(exm_ctx* ctx, exm_relight_pass* const* passes, in
     if (st != EXM_OK) return st;
     ShadeArgs A = passes[0]->A;
     const int blocks = ctx->num_sms * 8;
-    if (closest) trace_batch_kernel<true><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
-    else trace_batch_kernel<false><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+    if (width == 8) {
+        if (closest) trace_batch_kernel<true, true><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+        else trace_batch_kernel<false, true><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+    } else {
+        if (closest) trace_batch_kernel<true, false><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+        else trace_batch_kernel<false, false><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+    }
     ctx->launches += 1;
     return exm_cuda_check(cudaGetLastError(), "relight batch: trace");
 }

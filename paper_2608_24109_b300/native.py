@@ -40,7 +40,7 @@ FLAG_HALF_RES_INDIRECT = 64
 FLAG_RECOMPUTE = 128
 
 EXPORTS = [
-    "exm_create", "exm_destroy", "exm_last_error", "exm_sync", "exm_debug_fault",
+    "exm_create", "exm_destroy", "exm_last_error", "exm_sync", "exm_debug_fault", "exm_ctx_set_bvh_width",
     "exm_mesh_create", "exm_mesh_update_vertices", "exm_bvh_build", "exm_mesh_destroy", "exm_mesh_frames",
     "exm_mesh_export_info", "exm_mesh_export", "exm_mesh_import",
     "exm_env_create", "exm_env_prepare", "exm_env_destroy", "exm_env_total",
@@ -106,6 +106,7 @@ def lib():
         "exm_last_error": ([], ctypes.c_char_p),
         "exm_sync": ([P, P], I),
         "exm_debug_fault": ([I, ctypes.c_uint32], I),
+        "exm_ctx_set_bvh_width": ([P, I], I),
         "exm_mesh_export_info": ([P, ctypes.POINTER(AssetInfo)], I),
         "exm_mesh_export": ([P, ctypes.POINTER(ctypes.c_void_p * ASSET_SECTIONS), P], I),
         "exm_mesh_import": ([P, ctypes.POINTER(AssetInfo), ctypes.POINTER(ctypes.c_void_p * ASSET_SECTIONS), P, PP], I),
@@ -206,6 +207,10 @@ def exm_destroy(ctx):
 
 def exm_sync(ctx, stream=None):
     return check(lib().exm_sync(ctx, _stream(stream)))
+
+
+def exm_ctx_set_bvh_width(ctx, width):
+    return check(lib().exm_ctx_set_bvh_width(ctx, int(width)))
 
 
 def exm_debug_fault(kind, count):
