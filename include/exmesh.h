@@ -119,9 +119,9 @@ exm_status exm_sync(exm_ctx* ctx, void* stream);
 
 /* BVH node width of the meshes `ctx` builds from now on (uploads, vertex updates, rebuilds): 4
  * (4-wide nodes of 128 bytes), 8 (8-wide nodes of 80 bytes with 8-bit quantised child boxes) or 0
- * (the default: 8-wide once the 4-wide tree of the mesh would exceed 32 MiB, a quarter of the
- * L2).  The environment variable EXM_BVH_WIDTH sets it at exm_create.  Both widths take the same
- * decisions (the box tests are conservative; the triangle tests are the same). */
+ * (the default, 4-wide).  The environment variable EXM_BVH_WIDTH sets it at exm_create.  Both
+ * widths take the same decisions (the box tests are conservative; the triangle tests are the
+ * same), so they render the same images bit for bit. */
 exm_status exm_ctx_set_bvh_width(exm_ctx* ctx, int width);
 
 /* Uploads the fixed mesh-UV carrier (V*, F*, U*, Phi* of Sec. 5): V float32 [nv,3],

@@ -57,12 +57,15 @@ __global__ void asset_check8_kernel(const float4* __restrict__ nodes8, uint32_t 
     if (ni + nt > 8 || (ni && cb + ni > n_nodes) || (nt && tb + nt > (uint64_t)nf)) atomicOr(bad, 2u);
 }
 
-// The corrupt-asset injector: the root's first child that is a node is made the root again,
-// a cycle that every index check passes.
+// The corrupt-asset injector: a cycle that every index check passes.  4-wide: the root's node
+// children become the root; 8-wide: the root becomes its own only child, with the root's box.
 __global__ void asset_corrupt_kernel(float4* nodes, int width) {
-    if (width == 8) {  // the root's node children start at the root
-        uint32_t* w1 = reinterpret_cast<uint32_t*>(&nodes[1].x);
-        if (w1[2] & 0xffu) w1[0] = 0u;
+    if (width == 8) {  // the root becomes its own only child, with the root's box
+        uint32_t* w = reinterpret_cast<uint32_t*>(nodes);
+        w[4] = 0u;          // child_base
+        w[6] = 1u;          // one node child, no triangles
+        for (int k = 8; k < 14; ++k) w[k] = (k & 1) ? 0xffffffffu : 0xffffff00u;   // qlo: slot 0 at 0
+        for (int k = 14; k < 20; ++k) w[k] = (k & 1) ? 0u : 0x000000ffu;          // qhi: slot 0 at 255
         return;
     }
     int* ref = reinterpret_cast<int*>(&nodes[6].x);

@@ -492,10 +492,11 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
             std::swap(cin, cout);
         }
     }
-    // the node width: 8-wide compressed nodes when asked for, or by default once the 4-wide tree
-    // (128 B per node, 48 B per triangle) would outgrow a quarter of the L2
+    // the node width: 8-wide compressed nodes when asked for, else 4-wide.  Measured on the three
+    // blob workloads, the 8-wide tree visits 32% fewer nodes but its eight quantised boxes cost
+    // more instructions per visit: its tracer took 20%, 8% and 1% longer (99K, 499K, 2M triangles)
     int width = m->ctx->bvh_width;
-    if (width == 0) width = (size_t)n * (128 + 48) > (32u << 20) ? 8 : 4;
+    if (width == 0) width = 4;
     if (width == 8 && (size_t)n >= (1u << 27)) width = 4;  // the 8-wide stack entries hold 24-bit node indices
     m->width = width;
     if (width == 8) {

@@ -66,7 +66,7 @@ def _nodes(secs, info):
 
 
 def test_bvh_with_a_cycle_ends_at_the_traversal_cap():
-    """The root's first node child is made the root again: every index stays in range, so the
+    """The root's node children are made the root again: every index stays in range, so the
     import accepts it; each ray then loops until the traversal stack or step cap ends it, the
     kernels return, exm_sync reports EXM_ERR_TRAVERSAL_LIMIT, and the context renders the
     intact mesh as before."""
@@ -79,8 +79,7 @@ def test_bvh_with_a_cycle_ends_at_the_traversal_cap():
     r.sync()
     info, secs = assets.export_mesh(r.mesh)
     refs = _nodes(secs, info)[0, 6]
-    k = int(np.nonzero((refs >= 0) & (refs != 0x7FFFFFFF))[0][0])
-    refs[k] = 0
+    refs[(refs >= 0) & (refs != 0x7FFFFFFF)] = 0
     bad = assets.import_mesh(r.ctx, info, secs)
     _render_with(r, bad, M)
     with pytest.raises(N.ExmError) as e:

@@ -89,13 +89,13 @@ def test_one_batch_of_different_assets_and_sizes():
         t = srv.submit(srv.request(**r))
         outs, _ = _wait(srv, [t])
         alone.append(outs[t].clone())
-    # hold the first three requests on the host for 200 ms: the queue is first in, first out,
-    # so the other five queue up behind them and all eight are ready when a stream takes them
-    N.exm_debug_fault(N.FAULT_SLOW, 200)
-    held = [srv.submit(srv.request(**r)) for r in reqs[:3]]
-    N.exm_debug_fault(N.FAULT_SLOW, 0)
+    # hold the first request on the host for 200 ms: the queue is first in, first out, so the
+    # other seven queue up behind it and all eight are ready when a stream takes them
     b0, r0 = srv.batches()
-    tickets = held + [srv.submit(srv.request(**r)) for r in reqs[3:]]
+    N.exm_debug_fault(N.FAULT_SLOW, 200)
+    held = srv.submit(srv.request(**reqs[0]))
+    N.exm_debug_fault(N.FAULT_SLOW, 0)
+    tickets = [held] + [srv.submit(srv.request(**r)) for r in reqs[1:]]
     outs, _ = _wait(srv, tickets)
     b1, r1 = srv.batches()
     assert r1 - r0 == 8 and b1 - b0 == 1, (b1 - b0, r1 - r0)
