@@ -113,7 +113,7 @@ class Renderer:
         pixels = grab(pp, (n,), "<i4").long() & 0xFFFFFFFF
         bits_all = grab(pb, (rows * (wd + ws),), "<i4").long() & 0xFFFFFFFF
         dbits = bits_all[:rows * wd].view(rows, wd)[:n]
-        sbits = bits_all[rows * wd:].view(rows, ws)[:n] if ws else bits_all[:0].view(0, 0)
+        sbits = bits_all[rows * wd:].view(rows, ws)[:n]
         hits = grab(ph, (rows * nb,), "<i4").view(rows, nb)[:n] if nb else None
         return pixels, dbits, sbits, hits
 
