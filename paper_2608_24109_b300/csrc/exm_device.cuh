@@ -100,6 +100,14 @@ struct Ray {
     int nx, ny, nz;  // 0 when the near plane of that axis is the box's lo, 3 when it is hi
 };
 
+// 32-byte read-only load (a 256-bit vector load, sm_100 and later): two float4 from a 32-byte
+// aligned address in one instruction.
+__device__ __forceinline__ void ldg32(const float4* p, float4& a, float4& b) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // 3-input minimum / maximum (PTX min.f32 / max.f32 with three operands; a NaN operand is
 // ignored, which keeps the box test conservative for axis-parallel rays).
 __device__ __forceinline__ float fmax3(float a, float b, float c) {

@@ -626,7 +626,8 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                     bvh.tris = jobs[job].tris;
                     bvh.sphere = jobs[job].sphere;
                 }
-                const float4 a = rays[2 * (size_t)my], b = rays[2 * (size_t)my + 1];
+                float4 a, b;
+                ldg32(rays + 2 * (size_t)my, a, b);
                 r = make_ray(s3(a.x, a.y, a.z), s3(a.w, b.x, b.y));
                 tclip = sphere_exit(r.o, r.d, __ldg(bvh.sphere));
                 slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
@@ -697,10 +698,15 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                 } else {
                     ++c_nodes;
                     const float4* N = bvh.nodes4 + 8 * (size_t)node;
-                    // near / far planes of each axis chosen by the ray's direction signs
-                    const float4 qx = __ldg(N + r.nx), qy = __ldg(N + 1 + r.ny), qz = __ldg(N + 2 + r.nz);
-                    const float4 fx = __ldg(N + 3 - r.nx), fy = __ldg(N + 4 - r.ny), fz = __ldg(N + 5 - r.nz);
+                    // the six plane vectors in three 32-byte loads, then the near / far planes of
+                    // each axis chosen by the ray's direction signs
+                    float4 lx, ly, lz, hx, hy, hz;
+                    ldg32(N, lx, ly);
+                    ldg32(N + 2, lz, hx);
+                    ldg32(N + 4, hy, hz);
                     const float4 rf = __ldg(N + 6);
+                    const float4 qx = r.nx ? hx : lx, qy = r.ny ? hy : ly, qz = r.nz ? hz : lz;
+                    const float4 fx = r.nx ? lx : hx, fy = r.ny ? ly : hy, fz = r.nz ? lz : hz;
                     const float tmax = CLOSEST ? fminf(bt, tclip) : tclip;
                     float tc[4];
                     const int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
