@@ -30,7 +30,7 @@ __global__ void asset_check_kernel(const int32_t* __restrict__ F, const int32_t*
             if (i < 0 || i >= nv || u < 0 || u >= nuv) b |= 1u;
         }
         if (tris) {
-            const int id = __float_as_int(tris[3 * t].w);
+            const int id = __float_as_int(tris[kTri * (size_t)t].w);
             if (id < 0 || id >= nf) b |= 4u;
         }
     }
@@ -86,7 +86,7 @@ static void asset_sizes(const exm_mesh* m, uint64_t bytes[EXM_ASSET_SECTIONS]) {
     bytes[2] = (uint64_t)m->nuv * 8;
     bytes[3] = (uint64_t)m->nf * 12;
     bytes[4] = (uint64_t)m->n_nodes * (m->width == 8 ? kNode8 : 8) * sizeof(float4);
-    bytes[5] = (uint64_t)m->nf * 3 * sizeof(float4);
+    bytes[5] = (uint64_t)m->nf * kTri * sizeof(float4);
     bytes[6] = sizeof(float4);
 }
 
@@ -180,7 +180,7 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
             if (info->bytes[k] != bytes[k]) st = exm_fail(EXM_ERR_ARG, "exm_mesh_import: BVH section size");
         if (st == EXM_OK && width == 8 && !m->nodes8 &&
             (exm_malloc((void**)&m->nodes8, (size_t)m->nf * kNode8 * sizeof(float4)) != cudaSuccess ||
-             exm_malloc((void**)&m->tris8, (size_t)m->nf * 3 * sizeof(float4)) != cudaSuccess))
+             exm_malloc((void**)&m->tris8, (size_t)m->nf * kTri * sizeof(float4)) != cudaSuccess))
             st = exm_fail(EXM_ERR_OOM, "exm_mesh_import: BVH buffers");
         if (st == EXM_OK) {
             void* dst[3] = {width == 8 ? m->nodes8 : m->nodes4, width == 8 ? m->tris8 : m->tris, m->sphere};

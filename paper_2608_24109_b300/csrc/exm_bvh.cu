@@ -120,9 +120,10 @@ __global__ void leaf_kernel(const float* __restrict__ V, const int32_t* __restri
     i0 = min(max(i0, 0), nv - 1); i1 = min(max(i1, 0), nv - 1); i2 = min(max(i2, 0), nv - 1);
     float p[3][3];
     for (int c = 0; c < 3; ++c) { p[0][c] = V[3 * i0 + c]; p[1][c] = V[3 * i1 + c]; p[2][c] = V[3 * i2 + c]; }
-    tris[3 * k] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float((int)f));
-    tris[3 * k + 1] = make_float4(p[1][0], p[1][1], p[1][2], 0.0f);
-    tris[3 * k + 2] = make_float4(p[2][0], p[2][1], p[2][2], 0.0f);
+    tris[kTri * (size_t)k] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float((int)f));
+    tris[kTri * (size_t)k + 1] = make_float4(p[1][0], p[1][1], p[1][2], 0.0f);
+    tris[kTri * (size_t)k + 2] = make_float4(p[2][0], p[2][1], p[2][2], 0.0f);
+    tris[kTri * (size_t)k + 3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float* b = bounds + 6 * (size_t)(n - 1 + k);
     for (int c = 0; c < 3; ++c) {
         const float lo = fminf(p[0][c], fminf(p[1][c], p[2][c])), hi = fmaxf(p[0][c], fmaxf(p[1][c], p[2][c]));
@@ -315,7 +316,7 @@ __global__ void collapse8_kernel(int n, const int32_t* __restrict__ child, const
     for (int k = 0; k < ni; ++k) out[atomicAdd(n_out, 1u)] = make_int2(order[k], (int)(cbase + k));
     for (int k = 0; k < nt; ++k) {
         const int leaf = ~order[ni + k];
-        for (int v = 0; v < 3; ++v) tris_out[3 * (size_t)(tbase + k) + v] = tris_in[3 * (size_t)leaf + v];
+        for (int v = 0; v < kTri; ++v) tris_out[kTri * (size_t)(tbase + k) + v] = tris_in[kTri * (size_t)leaf + v];
     }
     // the node's grid: origin at its box's low corner, steps covering its extent in 255
     const float* nb = bounds + 6 * (size_t)b;
@@ -355,7 +356,7 @@ __global__ void collapse8_kernel(int n, const int32_t* __restrict__ child, const
 // A one-triangle mesh: a single 8-wide node holding triangle 0.
 __global__ void single8_kernel(const float* __restrict__ bounds, const float4* __restrict__ tris_in, float4* tris_out,
                                float4* nodes8) {
-    for (int v = 0; v < 3; ++v) tris_out[v] = tris_in[v];
+    for (int v = 0; v < kTri; ++v) tris_out[v] = tris_in[v];
     uint32_t e[3];
     for (int a = 0; a < 3; ++a) e[a] = step_exponent(fmaxf(__fsub_ru(bounds[3 + a], bounds[a]), 1e-30f));
     // the child's box is the node's box: planes 0 and 255 contain it
@@ -414,7 +415,7 @@ __global__ void sphere_radius_kernel(const float4* __restrict__ tris, int nf, fl
     float r2 = 0.0f;
     if (k < nf) {
         for (int v = 0; v < 3; ++v) {
-            const float4 p = tris[3 * k + v];
+            const float4 p = tris[kTri * (size_t)k + v];
             const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
             r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
         }
@@ -444,7 +445,7 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
                   exm_malloc((void**)&m->child, 2 * internal * 4) == cudaSuccess &&
                   exm_malloc((void**)&m->bounds, (2 * nn) * 6 * 4) == cudaSuccess &&
                   exm_malloc((void**)&m->scene_box, 6 * 4) == cudaSuccess &&
-                  exm_malloc((void**)&m->tris, nn * 3 * sizeof(float4)) == cudaSuccess &&
+                  exm_malloc((void**)&m->tris, nn * kTri * sizeof(float4)) == cudaSuccess &&
                   exm_malloc((void**)&m->nodes4, internal * 8 * sizeof(float4)) == cudaSuccess &&
                   exm_malloc((void**)&m->sphere, sizeof(float4)) == cudaSuccess &&
                   exm_malloc((void**)&m->frontier, 2 * nn * sizeof(int2)) == cudaSuccess &&
@@ -503,7 +504,7 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
         if (!m->nodes8) {
             const size_t nn = (size_t)n;
             if (exm_malloc((void**)&m->nodes8, nn * kNode8 * sizeof(float4)) != cudaSuccess ||
-                exm_malloc((void**)&m->tris8, nn * 3 * sizeof(float4)) != cudaSuccess ||
+                exm_malloc((void**)&m->tris8, nn * kTri * sizeof(float4)) != cudaSuccess ||
                 exm_malloc((void**)&m->n_tris8, 4) != cudaSuccess)
                 return exm_fail(EXM_ERR_OOM, "BVH buffers (8-wide)");
         }

@@ -391,6 +391,7 @@ struct BvhView {
     const float4* nodes8;  // 8-wide compressed nodes (exm_bvh.cu), when the mesh uses them
 };
 constexpr int kNode8 = 5;      // float4 per 8-wide compressed node
+constexpr int kTri = 4;        // float4 per triangle record: the vertices (original id in the first .w), padding
 constexpr int kStackSize8 = 64;  // node groups on the 8-wide traversal stack: one per level
 
 // Ray parameter beyond which o + t d lies outside the bounding sphere `sp` (centre, R^2), where
@@ -409,7 +410,9 @@ __device__ __forceinline__ float sphere_exit(S3 o, S3 d, float4 sp) {
 }
 
 __device__ __forceinline__ bool tri_test(const BvhView& b, int k, const Ray& r, float* T, float* det, int* id) {
-    float4 a = __ldg(b.tris + 3 * k), c = __ldg(b.tris + 3 * k + 1), d = __ldg(b.tris + 3 * k + 2);
+    float4 a, c, d, pad;
+    ldg32(b.tris + kTri * (size_t)k, a, c);
+    ldg32(b.tris + kTri * (size_t)k + 2, d, pad);
     *id = __float_as_int(a.w);
     return woop(r, s3(a.x, a.y, a.z), s3(c.x, c.y, c.z), s3(d.x, d.y, d.z), T, det);
 }

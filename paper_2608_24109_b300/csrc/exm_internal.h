@@ -41,13 +41,13 @@ struct exm_mesh {
     unsigned long long* nfix = nullptr;  // [nv,3] fixed-point normal sums
     unsigned long long* tfix = nullptr;  // [nuv,3] fixed-point tangent sums
     // BVH
-    float4* tris = nullptr;    // [nf * 3]
+    float4* tris = nullptr;    // [nf * 4] triangle records in leaf order (64 B: three vertices, padding)
     float4* nodes4 = nullptr;  // [max(nf-1,1) * 8] 4-wide nodes
     float4* sphere = nullptr;  // [1] bounding sphere of the triangles: centre, inflated R^2
     uint32_t n_nodes = 0;      // nodes of the BVH in use (4-wide in nodes4 or 8-wide in nodes8)
     int width = 4;             // BVH in use: 4-wide (nodes4, tris) or 8-wide compressed (nodes8, tris8)
     float4* nodes8 = nullptr;  // [n_nodes * 5] 8-wide compressed nodes
-    float4* tris8 = nullptr;   // [nf * 3] triangle records in the 8-wide nodes' order
+    float4* tris8 = nullptr;   // [nf * 4] triangle records in the 8-wide nodes' order
     uint32_t* n_tris8 = nullptr;
     int2* frontier = nullptr;  // [2 * nf] collapse frontier (binary node, 4-wide node)
     uint32_t* frontier_cnt = nullptr;
