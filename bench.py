@@ -149,14 +149,18 @@ def measured_peaks():
     return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "sm_max_mhz": 2032.0}, "fallback"
 
 
-def dist_init():
-    import torch
+def dist_init(timeout_s=None):
+    """Joins the replicas' process group (gloo: only the timing reduction crosses ranks).  Its
+    collectives give up after `timeout_s` seconds (EXM_DIST_TIMEOUT_S, default 600): a rank that
+    dies or never arrives makes the others fail with an error instead of waiting forever."""
+    import datetime
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("gloo")
+        t = timeout_s if timeout_s is not None else float(os.environ.get("EXM_DIST_TIMEOUT_S", "600"))
+        dist.init_process_group("gloo", timeout=datetime.timedelta(seconds=t))
     return world, rank, local
 
 

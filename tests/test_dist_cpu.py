@@ -1,6 +1,7 @@
 """The multi-process timing path of bench.py (barrier + max over ranks) with two gloo ranks
 on the CPU.  The benchmark shards nothing on the data path: each rank renders its own
-replica; only the timing reduction crosses ranks."""
+replica; only the timing reduction crosses ranks.  A rank that leaves before the barrier makes
+the other fail with an error, not wait."""
 import os
 import socket
 import sys
@@ -43,3 +44,36 @@ def test_two_rank_max_and_barrier():
         p.join(timeout=60)
         assert p.exitcode == 0
     assert res == [(0, 2, 11.0), (1, 2, 11.0)]
+
+
+def _worker_leaves(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import time
+
+    import bench
+    w, r, local = bench.dist_init(timeout_s=10)
+    if rank == 1:
+        os._exit(3)  # a rank that dies between steps, before the barrier
+    t0 = time.time()
+    try:
+        bench.barrier(w)
+        bench.dist_max(1.0, w)
+        q.put(("no error", time.time() - t0))
+    except Exception as e:  # noqa: BLE001 -- the failure is the point
+        q.put((type(e).__name__, time.time() - t0))
+
+
+def test_a_rank_that_leaves_fails_the_other_within_the_timeout():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ps = [ctx.Process(target=_worker_leaves, args=(k, 2, port, q)) for k in range(2)]
+    for p in ps:
+        p.start()
+    what, waited = q.get(timeout=120)
+    for p in ps:
+        p.join(timeout=60)
+    assert what != "no error" and waited < 60
+    assert ps[1].exitcode == 3
