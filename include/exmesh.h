@@ -366,7 +366,7 @@ exm_status exm_l1_loss(const float* pred, const float* target, int64_t n, float*
 
 /* ------------------------------------------------- Stage-II objective (Sec. 5.4, Eqs. 21-24)
  *
- * The objective calls of one context share its FP64 accumulators and scratch: issue them on
+ * The objective calls of one context share its fixed-point accumulators and scratch: issue them on
  * one stream (or serialise them).  Loss outputs are DEVICE float32 arrays, written; gradient
  * outputs follow each call's rule (written or accumulated). */
 

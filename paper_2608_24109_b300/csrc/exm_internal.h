@@ -15,7 +15,7 @@ struct exm_ctx {
     int bvh_width = 0;             // BVH node width of new meshes: 4, 8, 0 = by mesh size (EXM_BVH_WIDTH)
     uint32_t* d_status = nullptr;  // latched device error bits
     unsigned long long launches = 0;  // kernels launched by the library on this context
-    double* d_acc = nullptr;          // FP64 accumulators of the objective calls
+    unsigned long long* d_acc = nullptr;  // 64-bit fixed-point accumulators of the objective calls
     float* scratch = nullptr;         // objective scratch (SSIM coefficients)
     size_t scratch_cap = 0;
 };

@@ -29,7 +29,8 @@ struct Gauss {
     float w[kWin];
 };
 
-// accumulator slots (FP64) of one objective call
+// accumulator slots of one objective call: signed 64-bit fixed point (integer addition is
+// exact and order-independent, so the loss values are deterministic)
 enum : int {
     ACC_LOG = 0,
     ACC_SSIM = 1,
@@ -48,25 +49,49 @@ __device__ __forceinline__ float srgb_d(float x) {
 }
 __device__ __forceinline__ float sgnf(float d) { return d > 0.0f ? 1.0f : (d < 0.0f ? -1.0f : 0.0f); }
 
-// Warp sum, one FP64 atomic per warp (every lane of the warp must call it).
-__device__ __forceinline__ void warp_add(double v, double* dst) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(dst, v);
+// Fixed-point scales of the slots: 2^32 for the image and material sums (terms of magnitude at
+// most a few units, at most ~10^8 of them), 1 for the pair counts, 2^16 for the environment
+// sums (HDR texel values).
+constexpr float kFixImg = 0x1p32f, kFixEnv = 0x1p16f;
+
+// A thread's running sum as a double word (hi + lo), one TwoSum per term.
+__device__ __forceinline__ void ff_acc(FF& s, float x) {
+    const FF t = ff_two_sum(s.hi, x);
+    s.hi = t.hi;
+    s.lo = __fadd_rn(s.lo, t.lo);
 }
+
+// Warp sum of the lanes' double words in `scale` fixed point, one 64-bit integer atomic per warp
+// (every lane of the warp must call it).
+__device__ __forceinline__ void warp_add(FF v, float scale, unsigned long long* dst) {
+    long long q = __float2ll_rn(__fmul_rn(v.hi, scale)) + __float2ll_rn(__fmul_rn(v.lo, scale));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+    if ((threadIdx.x & 31) == 0 && q != 0) atomicAdd(dst, (unsigned long long)q);
+}
+
+// A fixed-point sum back as a double word: the integer split into two floats, then unscaled
+// (a power of two: exact).
+__device__ __forceinline__ FF fix_ff(unsigned long long a, float inv_scale) {
+    const long long q = (long long)a;
+    const float hi = __ll2float_rn(q);
+    const float lo = __ll2float_rn(q - __float2ll_rn(hi));
+    return FF{__fmul_rn(hi, inv_scale), __fmul_rn(lo, inv_scale)};
+}
+__device__ __forceinline__ float fix_f(unsigned long long a, float inv_scale) { return ff_f(fix_ff(a, inv_scale)); }
 
 // ------------------------------------------------------------------ image term (Eq. 21)
 
 __global__ void log_l1_kernel(const float* __restrict__ pred, const float* __restrict__ target, size_t n,
-                              float scale, float* grad, double* acc) {
-    double local = 0.0;
+                              float scale, float* grad, unsigned long long* acc) {
+    FF local = ff(0.0f);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const float p = pred[i];
         const float d = log1pf(p) - log1pf(target[i]);
-        local += fabsf(d);
+        ff_acc(local, fabsf(d));
         grad[i] = scale * sgnf(d) / (1.0f + p);
     }
-    warp_add(local, acc + ACC_LOG);
+    warp_add(local, kFixImg, acc + ACC_LOG);
 }
 
 // One (view, channel) plane of the interleaved [views, H, W, 3] images per grid z; the tile and
@@ -74,7 +99,7 @@ __global__ void log_l1_kernel(const float* __restrict__ pred, const float* __res
 __global__ void __launch_bounds__(kTW * kTH) ssim_fwd_kernel(const float* __restrict__ pred,
                                                             const float* __restrict__ target, int H, int W,
                                                             Gauss g, float* coef, size_t plane_total,
-                                                            double* acc) {
+                                                            unsigned long long* acc) {
     __shared__ float sx[kSH][kSW], sy[kSH][kSW];
     __shared__ float hs[5][kSH][kTW];
     const int plane = blockIdx.z, v = plane / 3, ch = plane - 3 * v;
@@ -110,7 +135,7 @@ __global__ void __launch_bounds__(kTW * kTH) ssim_fwd_kernel(const float* __rest
     __syncthreads();
     const int ty = tid / kTW, tx = tid - ty * kTW;
     const int gx = x0 + tx, gy = y0 + ty;
-    double local = 0.0;
+    FF local = ff(0.0f);
     if (gx < W && gy < H) {
         float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
 #pragma unroll
@@ -127,14 +152,14 @@ __global__ void __launch_bounds__(kTW * kTH) ssim_fwd_kernel(const float* __rest
         const float B1 = mx * mx + my * my + kC1, B2 = sxx + syy + kC2;
         const float inv = 1.0f / (B1 * B2);
         const float S = A1 * A2 * inv;
-        local = S;
+        local = ff(S);
         // dS / d(mu_x), 2 dS / d(E[x^2]), dS / d(E[xy]) at this output
         const size_t o = ((size_t)plane * H + gy) * W + gx;
         coef[o] = 2.0f * my * (A2 - A1) * inv - 2.0f * mx * S * (1.0f / B1 - 1.0f / B2);
         coef[plane_total + o] = -2.0f * S / B2;
         coef[2 * plane_total + o] = 2.0f * A1 * inv;
     }
-    warp_add(local, acc + ACC_SSIM);
+    warp_add(local, kFixImg, acc + ACC_SSIM);
 }
 
 __global__ void __launch_bounds__(kTW * kTH) ssim_bwd_kernel(const float* __restrict__ pred,
@@ -189,11 +214,12 @@ __global__ void __launch_bounds__(kTW * kTH) ssim_bwd_kernel(const float* __rest
     grad[idx] += scale * G * srgb_d(p);
 }
 
-__global__ void image_loss_finish_kernel(const double* acc, double n, float lambda_ssim, float* loss) {
-    const double l1 = acc[ACC_LOG] / n, dssim = 1.0 - acc[ACC_SSIM] / n;
-    loss[0] = (float)((1.0 - lambda_ssim) * l1 + lambda_ssim * dssim);
-    loss[1] = (float)l1;
-    loss[2] = (float)dssim;
+__global__ void image_loss_finish_kernel(const unsigned long long* acc, float n, float lambda_ssim, float* loss) {
+    const float l1 = fix_f(acc[ACC_LOG], 0x1p-32f) / n;
+    const float dssim = ff_f(ff_sub(ff(1.0f), ff_div(fix_ff(acc[ACC_SSIM], 0x1p-32f), ff(n))));
+    loss[0] = (1.0f - lambda_ssim) * l1 + lambda_ssim * dssim;
+    loss[1] = l1;
+    loss[2] = dssim;
 }
 
 // ------------------------------------------------------------------ material TV (Eq. 23)
@@ -209,7 +235,7 @@ struct TvArgs {
     float* gmaps;
     float lambda;
     bool metallic;
-    double* acc;
+    unsigned long long* acc;
 };
 
 template <typename T>
@@ -229,16 +255,16 @@ __global__ void tv_gbuf_kernel(TvArgs a) {
 
 __global__ void tv_pairs_kernel(TvArgs a) {
     const uint32_t n = *a.count;
-    double h = 0.0, v = 0.0;
+    FF h = ff(0.0f), v = ff(0.0f);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t pid = a.pixels[i];
         const uint32_t rem = pid % (uint32_t)(a.W * a.H);
         const int y = (int)(rem / a.W), x = (int)(rem - (uint32_t)y * a.W);
-        if (x + 1 < a.W && a.inv[pid + 1] >= 0) h += 1.0;
-        if (y + 1 < a.H && a.inv[pid + a.W] >= 0) v += 1.0;
+        if (x + 1 < a.W && a.inv[pid + 1] >= 0) ff_acc(h, 1.0f);
+        if (y + 1 < a.H && a.inv[pid + a.W] >= 0) ff_acc(v, 1.0f);
     }
-    warp_add(h, a.acc + ACC_PAIRS);
-    warp_add(v, a.acc + ACC_PAIRS + 1);
+    warp_add(h, 1.0f, a.acc + ACC_PAIRS);
+    warp_add(v, 1.0f, a.acc + ACC_PAIRS + 1);
 }
 
 // channel groups of the material map: A (0..2), R (3), N (5..7), M (4)
@@ -248,9 +274,11 @@ __device__ __forceinline__ float tv_group_size(int grp) { return grp == 0 || grp
 template <typename T>
 __global__ void tv_grad_kernel(TvArgs a) {
     const uint32_t n = *a.count;
-    const double ph = a.acc[ACC_PAIRS], pv = a.acc[ACC_PAIRS + 1];
-    const float ih = ph > 0.0 ? (float)(1.0 / ph) : 0.0f, iv = pv > 0.0 ? (float)(1.0 / pv) : 0.0f;
-    double part[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const float ph = fix_f(a.acc[ACC_PAIRS], 1.0f), pv = fix_f(a.acc[ACC_PAIRS + 1], 1.0f);
+    const float ih = ph > 0.0f ? 1.0f / ph : 0.0f, iv = pv > 0.0f ? 1.0f / pv : 0.0f;
+    FF part[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) part[k] = ff(0.0f);
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t pid = a.pixels[i];
         const uint32_t rem = pid % (uint32_t)(a.W * a.H);
@@ -270,8 +298,8 @@ __global__ void tv_grad_kernel(TvArgs a) {
                 if (nb[k] < 0) continue;
                 const float d = p - a.gbuf[8 * (size_t)nb[k] + ch];
                 s += sgnf(d) * (k < 2 ? ih : iv);
-                if (k == 1) part[2 * grp] += fabsf(d);      // pair (x, x + 1), counted once
-                if (k == 3) part[2 * grp + 1] += fabsf(d);  // pair (y, y + 1)
+                if (k == 1) ff_acc(part[2 * grp], fabsf(d));      // pair (x, x + 1), counted once
+                if (k == 3) ff_acc(part[2 * grp + 1], fabsf(d));  // pair (y, y + 1)
             }
             g[ch] = a.lambda * s * inv_c;
         }
@@ -282,71 +310,79 @@ __global__ void tv_grad_kernel(TvArgs a) {
         }
     }
 #pragma unroll
-    for (int k = 0; k < 8; ++k) warp_add(part[k], a.acc + ACC_MAT + k);
+    for (int k = 0; k < 8; ++k) warp_add(part[k], kFixImg, a.acc + ACC_MAT + k);
 }
 
-__global__ void tv_finish_kernel(const double* acc, bool metallic, float* loss) {
-    const double ph = acc[ACC_PAIRS], pv = acc[ACC_PAIRS + 1];
-    const double size[4] = {3.0, 1.0, 3.0, 1.0};
-    double tot = 0.0;
+__global__ void tv_finish_kernel(const unsigned long long* acc, bool metallic, float* loss) {
+    const float ph = fix_f(acc[ACC_PAIRS], 1.0f), pv = fix_f(acc[ACC_PAIRS + 1], 1.0f);
+    const float size[4] = {3.0f, 1.0f, 3.0f, 1.0f};
+    FF tot = ff(0.0f);
     for (int grp = 0; grp < 4; ++grp) {
         if (grp == 3 && !metallic) continue;
-        if (ph > 0.0) tot += acc[ACC_MAT + 2 * grp] / (ph * size[grp]);
-        if (pv > 0.0) tot += acc[ACC_MAT + 2 * grp + 1] / (pv * size[grp]);
+        if (ph > 0.0f) tot = ff_add(tot, ff_div(fix_ff(acc[ACC_MAT + 2 * grp], 0x1p-32f), ff(ph * size[grp])));
+        if (pv > 0.0f) tot = ff_add(tot, ff_div(fix_ff(acc[ACC_MAT + 2 * grp + 1], 0x1p-32f), ff(pv * size[grp])));
     }
-    loss[0] = (float)tot;
+    loss[0] = ff_f(tot);
 }
 
 // ------------------------------------------------------------- env TV and chroma (Eqs. 23-24)
 
-__global__ void env_sum_kernel(const float* __restrict__ E, size_t texels, double* acc) {
-    double s[3] = {0.0, 0.0, 0.0};
+__global__ void env_sum_kernel(const float* __restrict__ E, size_t texels, unsigned long long* acc) {
+    FF s[3] = {ff(0.0f), ff(0.0f), ff(0.0f)};
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < texels; t += (size_t)gridDim.x * blockDim.x) {
-        s[0] += E[3 * t];
-        s[1] += E[3 * t + 1];
-        s[2] += E[3 * t + 2];
+        ff_acc(s[0], E[3 * t]);
+        ff_acc(s[1], E[3 * t + 1]);
+        ff_acc(s[2], E[3 * t + 2]);
     }
-    for (int c = 0; c < 3; ++c) warp_add(s[c], acc + ACC_ESUM + c);
+    for (int c = 0; c < 3; ++c) warp_add(s[c], kFixEnv, acc + ACC_ESUM + c);
 }
 
 __global__ void env_reg_kernel(const float* __restrict__ E, int W, int H, float lambda_env, float lambda_chroma,
-                               float* grad, double* acc) {
+                               float* grad, unsigned long long* acc) {
     const size_t texels = (size_t)W * H;
-    const double inv_t = 1.0 / (double)texels;
-    const float m[3] = {(float)(acc[ACC_ESUM] * inv_t), (float)(acc[ACC_ESUM + 1] * inv_t),
-                        (float)(acc[ACC_ESUM + 2] * inv_t)};
-    const float mu = (m[0] + m[1] + m[2]) * (1.0f / 3.0f);
+    const float inv_t = 1.0f / (float)texels;
+    // channel means as double words, and their differences from the grey mean
+    FF mf[3];
+    for (int c = 0; c < 3; ++c) mf[c] = ff_div(fix_ff(acc[ACC_ESUM + c], 0x1p-16f), ff((float)texels));
+    const FF muf = ff_div(ff_add(ff_add(mf[0], mf[1]), mf[2]), ff(3.0f));
+    const float dm[3] = {ff_f(ff_sub(mf[0], muf)), ff_f(ff_sub(mf[1], muf)), ff_f(ff_sub(mf[2], muf))};
     const float ih = 1.0f / (float)(texels * 3), iv = H > 1 ? 1.0f / (float)((size_t)(H - 1) * W * 3) : 0.0f;
-    double ph = 0.0, pv = 0.0;
+    FF ph = ff(0.0f), pv = ff(0.0f);
     for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < texels; t += (size_t)gridDim.x * blockDim.x) {
         const int i = (int)(t / W), j = (int)(t - (size_t)i * W);
         const size_t l = (size_t)i * W + (j == 0 ? W - 1 : j - 1), r = (size_t)i * W + (j + 1 == W ? 0 : j + 1);
         for (int c = 0; c < 3; ++c) {
             const float e = E[3 * t + c];
             const float dr = E[3 * r + c] - e;
-            ph += fabsf(dr);
+            ff_acc(ph, fabsf(dr));
             float g = (sgnf(e - E[3 * l + c]) - sgnf(dr)) * ih;
             if (i > 0) g += sgnf(e - E[3 * (t - W) + c]) * iv;
             if (i + 1 < H) {
                 const float dd = E[3 * (t + W) + c] - e;
-                pv += fabsf(dd);
+                ff_acc(pv, fabsf(dd));
                 g -= sgnf(dd) * iv;
             }
-            grad[3 * t + c] += lambda_env * g + lambda_chroma * 2.0f * (m[c] - mu) * (float)inv_t;
+            grad[3 * t + c] += lambda_env * g + lambda_chroma * 2.0f * dm[c] * inv_t;
         }
     }
-    warp_add(ph, acc + ACC_ETV);
-    warp_add(pv, acc + ACC_ETV + 1);
+    warp_add(ph, kFixEnv, acc + ACC_ETV);
+    warp_add(pv, kFixEnv, acc + ACC_ETV + 1);
 }
 
-__global__ void env_reg_finish_kernel(const double* acc, int W, int H, float* loss) {
-    const double texels = (double)W * H;
-    double tv = acc[ACC_ETV] / (texels * 3.0);
-    if (H > 1) tv += acc[ACC_ETV + 1] / ((double)(H - 1) * W * 3.0);
-    const double m0 = acc[ACC_ESUM] / texels, m1 = acc[ACC_ESUM + 1] / texels, m2 = acc[ACC_ESUM + 2] / texels;
-    const double mu = (m0 + m1 + m2) / 3.0;
-    loss[0] = (float)tv;
-    loss[1] = (float)((m0 - mu) * (m0 - mu) + (m1 - mu) * (m1 - mu) + (m2 - mu) * (m2 - mu));
+__global__ void env_reg_finish_kernel(const unsigned long long* acc, int W, int H, float* loss) {
+    const float texels = (float)((size_t)W * H);
+    FF tv = ff_div(fix_ff(acc[ACC_ETV], 0x1p-16f), ff(__fmul_rn(texels, 3.0f)));
+    if (H > 1) tv = ff_add(tv, ff_div(fix_ff(acc[ACC_ETV + 1], 0x1p-16f), ff((float)((size_t)(H - 1) * W * 3))));
+    FF m[3];
+    for (int c = 0; c < 3; ++c) m[c] = ff_div(fix_ff(acc[ACC_ESUM + c], 0x1p-16f), ff(texels));
+    const FF mu = ff_div(ff_add(ff_add(m[0], m[1]), m[2]), ff(3.0f));
+    FF ch = ff(0.0f);
+    for (int c = 0; c < 3; ++c) {
+        const FF d = ff_sub(m[c], mu);
+        ch = ff_add(ch, ff_mul(d, d));
+    }
+    loss[0] = ff_f(tv);
+    loss[1] = ff_f(ch);
 }
 
 // ------------------------------------------------------------------ Adam
@@ -391,7 +427,7 @@ static int grid_for(exm_ctx* ctx, size_t n, int threads) {
 
 static bool ensure_acc(exm_ctx* ctx) {
     if (ctx->d_acc) return true;
-    if (exm_malloc((void**)&ctx->d_acc, kAccSlots * sizeof(double)) != cudaSuccess) {
+    if (exm_malloc((void**)&ctx->d_acc, kAccSlots * sizeof(unsigned long long)) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -407,7 +443,7 @@ exm_status exm_image_loss_impl(exm_ctx* ctx, const float* pred, const float* tar
     const size_t n = (size_t)views * W * H * 3, planes = (size_t)views * 3, plane_total = planes * W * H;
     if (!ensure_acc(ctx) || !ensure(&ctx->scratch, &ctx->scratch_cap, 3 * plane_total))
         return exm_fail(EXM_ERR_OOM, "exm_image_loss: scratch");
-    cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(double), s);
+    cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(unsigned long long), s);
     log_l1_kernel<<<grid_for(ctx, n, 256), 256, 0, s>>>(pred, target, n, (1.0f - lambda_ssim) / (float)n, grad,
                                                         ctx->d_acc);
     const dim3 tiles((W + kTW - 1) / kTW, (H + kTH - 1) / kTH, (unsigned)planes);
@@ -415,7 +451,7 @@ exm_status exm_image_loss_impl(exm_ctx* ctx, const float* pred, const float* tar
     ssim_fwd_kernel<<<tiles, kTW * kTH, 0, s>>>(pred, target, H, W, g, ctx->scratch, plane_total, ctx->d_acc);
     ssim_bwd_kernel<<<tiles, kTW * kTH, 0, s>>>(pred, target, H, W, g, ctx->scratch, plane_total,
                                                 -lambda_ssim / (float)n, grad);
-    image_loss_finish_kernel<<<1, 1, 0, s>>>(ctx->d_acc, (double)n, lambda_ssim, loss);
+    image_loss_finish_kernel<<<1, 1, 0, s>>>(ctx->d_acc, (float)n, lambda_ssim, loss);
     ctx->launches += 4;
     return exm_cuda_check(cudaGetLastError(), "exm_image_loss launch");
 }
@@ -426,7 +462,7 @@ exm_status exm_material_tv_impl(exm_ctx* ctx, const void* maps, exm_dtype dt, in
     const size_t P = (size_t)f->views * f->W * f->H;
     if (!ensure_acc(ctx) || !ensure(&f->tv_gbuf, &f->tv_gbuf_cap, 8 * P) || !ensure(&f->tv_inv, &f->tv_inv_cap, P))
         return exm_fail(EXM_ERR_OOM, "exm_material_tv: scratch");
-    cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(double), s);
+    cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(unsigned long long), s);
     cudaMemsetAsync(f->tv_inv, 0xff, P * sizeof(int32_t), s);
     TvArgs a;
     a.prec = f->prec;
@@ -465,7 +501,7 @@ exm_status exm_env_regularizers_impl(exm_ctx* ctx, const float* E, int W, int H,
                                      float lambda_chroma, float* loss, float* grad_env, cudaStream_t s) {
     if (!ensure_acc(ctx)) return exm_fail(EXM_ERR_OOM, "exm_env_regularizers: scratch");
     const size_t texels = (size_t)W * H;
-    cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(double), s);
+    cudaMemsetAsync(ctx->d_acc, 0, kAccSlots * sizeof(unsigned long long), s);
     env_sum_kernel<<<grid_for(ctx, texels, 256), 256, 0, s>>>(E, texels, ctx->d_acc);
     env_reg_kernel<<<grid_for(ctx, texels, 256), 256, 0, s>>>(E, W, H, lambda_env, lambda_chroma, grad_env,
                                                              ctx->d_acc);

@@ -1,6 +1,6 @@
 """Stage-II objective kernels (Eqs. 21-24) and the Adam step against the oracle.
 
-Bars: loss values within 2e-5 relative (FP32 arithmetic, FP64 accumulation); gradients
+Bars: loss values within 2e-5 relative (FP32 arithmetic, 64-bit fixed-point sums); gradients
 ||g - o|| / ||o|| <= 1e-3 per tensor; Adam parameters within 1e-6 relative."""
 import numpy as np
 import pytest
