@@ -950,10 +950,11 @@ __device__ __forceinline__ void pixel_shade(const ShadeArgs& A, uint32_t i, int 
     }
 }
 
-// Resident blocks per SM the register allocation must allow (at these caps the backward keeps
-// 80 / 96 registers and spills 12 / 16 bytes, the forward 64 / 102 without spills; direct-only
-// / with indirect).
-constexpr int shade_min_blocks(bool bwd, bool ind) { return bwd ? (ind ? 5 : 6) : (ind ? 5 : 8); }
+// Resident blocks per SM the register allocation must allow.  The sample loops are latency-bound,
+// so more resident warps pay until spills cost more: measured on the 2M-triangle workload, the
+// indirect forward ran 8.16 / 7.50 / 7.25 ms at 5 / 6 / 7 blocks and the indirect backward
+// 12.31 / 11.92 / 12.46 ms at 5 / 6 / 5 (direct-only / with indirect).
+constexpr int shade_min_blocks(bool bwd, bool ind) { return bwd ? 6 : (ind ? 7 : 8); }
 
 // Material and shading normal of each covered pixel from the maps of the pass that runs it,
 // one thread per pixel, into its record: [5] a.xyz r, [6] m n_s.xyz.  The warp-per-pixel
