@@ -30,12 +30,12 @@ __global__ void asset_check_kernel(const int32_t* __restrict__ F, const int32_t*
             if (i < 0 || i >= nv || u < 0 || u >= nuv) b |= 1u;
         }
         if (tris) {
-            const int id = __float_as_int(tris[kTri * (size_t)t].w);
+            const int id = __float_as_int(tris[tri_at(t, 0)].w);
             if (id < 0 || id >= nf) b |= 4u;
         }
     }
     if (nodes4 && t < n_nodes) {
-        const float4 r = nodes4[8 * (size_t)t + 6];
+        const float4 r = nodes4[node4_at(t, 6)];
         const int ref[4] = {__float_as_int(r.x), __float_as_int(r.y), __float_as_int(r.z), __float_as_int(r.w)};
         for (int k = 0; k < 4; ++k) {
             const int c = ref[k];
@@ -68,7 +68,7 @@ __global__ void asset_corrupt_kernel(float4* nodes, int width) {
         for (int k = 14; k < 20; ++k) w[k] = (k & 1) ? 0u : 0x000000ffu;          // qhi: slot 0 at 255
         return;
     }
-    int* ref = reinterpret_cast<int*>(&nodes[6].x);
+    int* ref = reinterpret_cast<int*>(&nodes[node4_at(0, 6)].x);
     for (int k = 0; k < 4; ++k)
         if (ref[k] >= 0 && ref[k] != kEmptyRef) {
             ref[k] = 0;

@@ -120,10 +120,10 @@ __global__ void leaf_kernel(const float* __restrict__ V, const int32_t* __restri
     i0 = min(max(i0, 0), nv - 1); i1 = min(max(i1, 0), nv - 1); i2 = min(max(i2, 0), nv - 1);
     float p[3][3];
     for (int c = 0; c < 3; ++c) { p[0][c] = V[3 * i0 + c]; p[1][c] = V[3 * i1 + c]; p[2][c] = V[3 * i2 + c]; }
-    tris[kTri * (size_t)k] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float((int)f));
-    tris[kTri * (size_t)k + 1] = make_float4(p[1][0], p[1][1], p[1][2], 0.0f);
-    tris[kTri * (size_t)k + 2] = make_float4(p[2][0], p[2][1], p[2][2], 0.0f);
-    tris[kTri * (size_t)k + 3] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    tris[tri_at(k, 0)] = make_float4(p[0][0], p[0][1], p[0][2], __int_as_float((int)f));
+    tris[tri_at(k, 1)] = make_float4(p[1][0], p[1][1], p[1][2], 0.0f);
+    tris[tri_at(k, 2)] = make_float4(p[2][0], p[2][1], p[2][2], 0.0f);
+    tris[tri_at(k, 3)] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     float* b = bounds + 6 * (size_t)(n - 1 + k);
     for (int c = 0; c < 3; ++c) {
         const float lo = fminf(p[0][c], fminf(p[1][c], p[2][c])), hi = fmaxf(p[0][c], fmaxf(p[1][c], p[2][c]));
@@ -252,10 +252,10 @@ __global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const
             refs[k] = kEmpty4;
         }
     }
-    float4* N = nodes4 + 8 * (size_t)q;
-    for (int a = 0; a < 6; ++a) N[a] = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
-    N[6] = make_float4(__int_as_float(refs[0]), __int_as_float(refs[1]), __int_as_float(refs[2]), __int_as_float(refs[3]));
-    N[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int a = 0; a < 6; ++a) nodes4[node4_at(q, a)] = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+    nodes4[node4_at(q, 6)] = make_float4(__int_as_float(refs[0]), __int_as_float(refs[1]), __int_as_float(refs[2]),
+                                         __int_as_float(refs[3]));
+    nodes4[node4_at(q, 7)] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // ---- 8-wide compressed nodes (the node format of Ylitie, Karras and Laine, "Efficient
@@ -316,7 +316,7 @@ __global__ void collapse8_kernel(int n, const int32_t* __restrict__ child, const
     for (int k = 0; k < ni; ++k) out[atomicAdd(n_out, 1u)] = make_int2(order[k], (int)(cbase + k));
     for (int k = 0; k < nt; ++k) {
         const int leaf = ~order[ni + k];
-        for (int v = 0; v < kTri; ++v) tris_out[kTri * (size_t)(tbase + k) + v] = tris_in[kTri * (size_t)leaf + v];
+        for (int v = 0; v < kTri; ++v) tris_out[tri_at(tbase + k, v)] = tris_in[tri_at(leaf, v)];
     }
     // the node's grid: origin at its box's low corner, steps covering its extent in 255
     const float* nb = bounds + 6 * (size_t)b;
@@ -376,12 +376,12 @@ __global__ void seed8_kernel(int2* in, uint32_t* n_in, uint32_t* n_nodes, uint32
     *n_tris = 0;
 }
 
-// A one-triangle mesh: a single 4-wide node holding leaf 0.
+// A one-triangle mesh: a single 4-wide node holding leaf 0 (node 0: no skew).
 __global__ void single4_kernel(const float* __restrict__ bounds, float4* nodes4) {
-    float4* N = nodes4;
-    for (int a = 0; a < 6; ++a) N[a] = make_float4(bounds[a], 0.f, 0.f, 0.f);
-    N[6] = make_float4(__int_as_float(~0), __int_as_float(kEmpty4), __int_as_float(kEmpty4), __int_as_float(kEmpty4));
-    N[7] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int a = 0; a < 6; ++a) nodes4[node4_at(0, a)] = make_float4(bounds[a], 0.f, 0.f, 0.f);
+    nodes4[node4_at(0, 6)] =
+        make_float4(__int_as_float(~0), __int_as_float(kEmpty4), __int_as_float(kEmpty4), __int_as_float(kEmpty4));
+    nodes4[node4_at(0, 7)] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 // Bounding sphere of the leaf triangles, for clipping rays: the centre is the middle of the
@@ -389,10 +389,10 @@ __global__ void single4_kernel(const float* __restrict__ bounds, float4* nodes4)
 // R^2 is inflated by 2e-4 relative (far above the FP32 rounding of the distances), so that
 // every point of every triangle lies inside the stored sphere.
 __global__ void sphere_centre_kernel(const float4* __restrict__ nodes4, float4* sphere) {
-    const float4* N = nodes4;
-    const float* lo[3] = {&N[0].x, &N[1].x, &N[2].x};
-    const float* hi[3] = {&N[3].x, &N[4].x, &N[5].x};
-    const int* ref = reinterpret_cast<const int*>(&N[6].x);
+    const float4* N = nodes4;  // the root, node 0
+    const float* lo[3] = {&N[node4_at(0, 0)].x, &N[node4_at(0, 1)].x, &N[node4_at(0, 2)].x};
+    const float* hi[3] = {&N[node4_at(0, 3)].x, &N[node4_at(0, 4)].x, &N[node4_at(0, 5)].x};
+    const int* ref = reinterpret_cast<const int*>(&N[node4_at(0, 6)].x);
     float c[3];
     for (int a = 0; a < 3; ++a) {
         float l = INFINITY, h = -INFINITY;
@@ -415,7 +415,7 @@ __global__ void sphere_radius_kernel(const float4* __restrict__ tris, int nf, fl
     float r2 = 0.0f;
     if (k < nf) {
         for (int v = 0; v < 3; ++v) {
-            const float4 p = tris[kTri * (size_t)k + v];
+            const float4 p = tris[tri_at(k, v)];
             const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
             r2 = fmaxf(r2, dx * dx + dy * dy + dz * dz);
         }

@@ -382,8 +382,18 @@ __device__ __forceinline__ void light_sample2(const EnvView& e, uint4 ha, uint32
 // ----------------------------------------------------------------------- BVH
 // 4-wide BVH, 128-byte nodes (8 float4): the four child boxes as lo.x[4] lo.y[4] lo.z[4]
 // hi.x[4] hi.y[4] hi.z[4], then the four child references (>= 0: node, < 0: leaf ~k =
-// triangle k in leaf order, kEmptyChild: unused slot).  Triangles in leaf order, 3 float4
-// each (p0 + original id bits in .w, p1, p2).
+// triangle k in leaf order, kEmptyChild: unused slot).  Triangles in leaf order, 64-byte
+// records (p0 + original id bits in .w, p1, p2, padding).
+//
+// Bank skew.  The lanes of a warp read different nodes with the same load instruction.  Were
+// chunk j (32 bytes) of every node at the same offset of its 128-byte line, every lane would
+// address the same eight of the L1's 32 banks and the lanes would be served one per cycle.  So
+// chunk j of node q is stored at chunk position j xor (q mod 4) of the node, and chunk j of
+// triangle record k at position j xor (k/2 mod 2) of the record (records sit at offset 0 or 64
+// of a line by the parity of k): over the lanes' nodes and records the reads spread across the
+// four bank groups.  node4_at / tri_at give the float4 index of element v of a record; the
+// traversal forms the same addresses by xor-ing the record's (128- or 64-byte aligned) address,
+// one logic operation per chunk (chunk_at).
 struct BvhView {
     const float4* tris;
     const float4* nodes4;
@@ -393,6 +403,18 @@ struct BvhView {
 constexpr int kNode8 = 5;      // float4 per 8-wide compressed node
 constexpr int kTri = 4;        // float4 per triangle record: the vertices (original id in the first .w), padding
 constexpr int kStackSize8 = 64;  // node groups on the 8-wide traversal stack: one per level
+
+__host__ __device__ __forceinline__ size_t node4_at(size_t q, unsigned v) {
+    return 8 * q + 2 * ((v / 2) ^ ((unsigned)q & 3u)) + (v & 1u);
+}
+__host__ __device__ __forceinline__ size_t tri_at(size_t k, unsigned v) {
+    return (size_t)kTri * k + 2 * ((v / 2) ^ ((unsigned)(k >> 1) & 1u)) + (v & 1u);
+}
+// The chunk at byte offset `x` (a multiple of 32 below the record's alignment) of an aligned
+// record: no carry can occur, so the xor stays in the address's low word.
+__device__ __forceinline__ const float4* chunk_at(const float4* rec, unsigned x) {
+    return reinterpret_cast<const float4*>(reinterpret_cast<uintptr_t>(rec) ^ (uintptr_t)x);
+}
 
 // Ray parameter beyond which o + t d lies outside the bounding sphere `sp` (centre, R^2), where
 // no triangle can be hit, plus a margin (0.1% relative and 1e-4 R absolute) far above the
@@ -410,9 +432,11 @@ __device__ __forceinline__ float sphere_exit(S3 o, S3 d, float4 sp) {
 }
 
 __device__ __forceinline__ bool tri_test(const BvhView& b, int k, const Ray& r, float* T, float* det, int* id) {
-    float4 a, c, d, pad;
-    ldg32(b.tris + kTri * (size_t)k, a, c);
-    ldg32(b.tris + kTri * (size_t)k + 2, d, pad);
+    float4 a, c;
+    const float4* rec = b.tris + kTri * (size_t)k;
+    const unsigned x = ((unsigned)k & 2u) << 4;  // 32 when bit 1 of k is set
+    ldg32(chunk_at(rec, x), a, c);
+    const float4 d = __ldg(chunk_at(rec, x ^ 32u));
     *id = __float_as_int(a.w);
     return woop(r, s3(a.x, a.y, a.z), s3(c.x, c.y, c.z), s3(d.x, d.y, d.z), T, det);
 }

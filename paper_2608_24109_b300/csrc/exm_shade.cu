@@ -698,13 +698,15 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                 } else {
                     ++c_nodes;
                     const float4* N = bvh.nodes4 + 8 * (size_t)node;
-                    // the six plane vectors in three 32-byte loads, then the near / far planes of
-                    // each axis chosen by the ray's direction signs
+                    // the six plane vectors in three 32-byte loads (chunks skewed by the node
+                    // index), then the near / far planes of each axis chosen by the ray's
+                    // direction signs
+                    const unsigned sk = ((unsigned)node & 3u) << 5;
                     float4 lx, ly, lz, hx, hy, hz;
-                    ldg32(N, lx, ly);
-                    ldg32(N + 2, lz, hx);
-                    ldg32(N + 4, hy, hz);
-                    const float4 rf = __ldg(N + 6);
+                    ldg32(chunk_at(N, sk), lx, ly);
+                    ldg32(chunk_at(N, sk ^ 32u), lz, hx);
+                    ldg32(chunk_at(N, sk ^ 64u), hy, hz);
+                    const float4 rf = __ldg(chunk_at(N, sk ^ 96u));
                     const float4 qx = r.nx ? hx : lx, qy = r.ny ? hy : ly, qz = r.nz ? hz : lz;
                     const float4 fx = r.nx ? lx : hx, fy = r.ny ? ly : hy, fz = r.nz ? lz : hz;
                     const float tmax = CLOSEST ? fminf(bt, tclip) : tclip;

@@ -26,7 +26,7 @@ EXM_ERR_BUSY = -7
 EXM_ERR_QUEUE_OVERFLOW = -8
 EXM_ERR_CANCELLED = -9
 FAULT_ALLOC, FAULT_ADMIT, FAULT_SLOW, FAULT_CANCEL, FAULT_CORRUPT = 1, 2, 3, 4, 5
-ASSET_VERSION = 2
+ASSET_VERSION = 3
 ASSET_SECTIONS = 7
 
 EXM_F32, EXM_BF16, EXM_F16 = 0, 1, 2
