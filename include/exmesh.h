@@ -117,11 +117,22 @@ exm_status exm_sync(exm_ctx* ctx, void* stream);
 
 /* ------------------------------------------------------------------- mesh (S1) */
 
-/* BVH node width of the meshes `ctx` builds from now on (uploads, vertex updates, rebuilds): 4
- * (4-wide nodes of 128 bytes), 8 (8-wide nodes of 80 bytes with 8-bit quantised child boxes) or 0
- * (the default, 4-wide).  The environment variable EXM_BVH_WIDTH sets it at exm_create.  Both
- * widths take the same decisions (the box tests are conservative; the triangle tests are the
- * same), so they render the same images bit for bit. */
+/* BVH node layout of the meshes `ctx` builds from now on (uploads, vertex updates, rebuilds):
+ *   EXM_BVH_4   4-wide nodes of 128 bytes, FP32 child boxes;
+ *   EXM_BVH_4Q  4-wide nodes of 64 bytes, child boxes quantised to 8 bits per plane on a per-node
+ *               power-of-two grid, rounded outwards by one grid step (the same tree as EXM_BVH_4);
+ *   EXM_BVH_8Q  8-wide nodes of 80 bytes with 8-bit quantised child boxes;
+ *   EXM_BVH_AUTO the library's default (EXM_BVH_4).
+ * The environment variable EXM_BVH_LAYOUT (4, 4q or 8) sets it at exm_create.  All layouts take
+ * the same decisions (the box tests are conservative; the triangle tests are the same), so they
+ * render the same images bit for bit. */
+#define EXM_BVH_AUTO 0
+#define EXM_BVH_4 1
+#define EXM_BVH_4Q 2
+#define EXM_BVH_8Q 3
+exm_status exm_ctx_set_bvh_layout(exm_ctx* ctx, int layout);
+/* The same by node width: 4 (EXM_BVH_4), 8 (EXM_BVH_8Q) or 0 (EXM_BVH_AUTO); EXM_BVH_WIDTH (4 or
+ * 8) in the environment sets it at exm_create. */
 exm_status exm_ctx_set_bvh_width(exm_ctx* ctx, int width);
 
 /* Uploads the fixed mesh-UV carrier (V*, F*, U*, Phi* of Sec. 5): V float32 [nv,3],
@@ -134,8 +145,8 @@ exm_status exm_mesh_create(exm_ctx* ctx, const float* V, int nv, const int32_t* 
                            const float* UV, int nuv, const int32_t* Fuv, void* stream, exm_mesh** out);
 /* Replaces the vertex positions (DEVICE float32 [nv,3]), recomputes frames and BVH. */
 exm_status exm_mesh_update_vertices(exm_mesh* mesh, const float* V, void* stream);
-/* Rebuilds the BVH (Morton order, locally-ordered clustering, then 4- or 8-wide nodes
- * (exm_ctx_set_bvh_width); one triangle per leaf). */
+/* Rebuilds the BVH (Morton order, locally-ordered clustering, then 4- or 8-wide nodes in the
+ * context's layout (exm_ctx_set_bvh_layout); one triangle per leaf). */
 exm_status exm_bvh_build(exm_mesh* mesh, void* stream);
 void exm_mesh_destroy(exm_mesh* mesh);
 /* Device pointers to the mesh's per-vertex unit normals [nv,3] and per-UV-vertex unit

@@ -130,7 +130,11 @@ exm_status exm_create(int device, exm_ctx** out) {
     if (!c) return exm_fail(EXM_ERR_OOM, "exm_create: host allocation");
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
-    if (const char* w = getenv("EXM_BVH_WIDTH")) c->bvh_width = atoi(w) == 8 ? 8 : (atoi(w) == 4 ? 4 : 0);
+    if (const char* w = getenv("EXM_BVH_WIDTH")) c->bvh_layout = atoi(w) == 8 ? EXM_BVH_8Q : (atoi(w) == 4 ? EXM_BVH_4 : 0);
+    if (const char* l = getenv("EXM_BVH_LAYOUT")) {
+        const std::string v(l);
+        c->bvh_layout = v == "4" ? EXM_BVH_4 : v == "4q" ? EXM_BVH_4Q : v == "8" ? EXM_BVH_8Q : c->bvh_layout;
+    }
     if (exm_malloc((void**)&c->d_status, sizeof(uint32_t)) != cudaSuccess) {
         delete c;
         return exm_fail(EXM_ERR_OOM, "exm_create: status word");
@@ -149,9 +153,15 @@ void exm_destroy(exm_ctx* c) {
     delete c;
 }
 
+exm_status exm_ctx_set_bvh_layout(exm_ctx* c, int layout) {
+    if (!c || layout < EXM_BVH_AUTO || layout > EXM_BVH_8Q) return exm_fail(EXM_ERR_ARG, "exm_ctx_set_bvh_layout");
+    c->bvh_layout = layout;
+    return EXM_OK;
+}
+
 exm_status exm_ctx_set_bvh_width(exm_ctx* c, int width) {
     if (!c || (width != 0 && width != 4 && width != 8)) return exm_fail(EXM_ERR_ARG, "exm_ctx_set_bvh_width");
-    c->bvh_width = width;
+    c->bvh_layout = width == 8 ? EXM_BVH_8Q : (width == 4 ? EXM_BVH_4 : EXM_BVH_AUTO);
     return EXM_OK;
 }
 
@@ -179,7 +189,7 @@ static void mesh_free(exm_mesh* m) {
     void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nfix, m->tfix,
                     m->tris, m->codes, m->codes_sorted, m->ids, m->ids_sorted, m->child, m->bounds,
                     m->scene_box, m->sort_tmp, m->nodes4, m->sphere, m->frontier, m->frontier_cnt, m->nodes8,
-                    m->tris8, m->n_tris8,
+                    m->tris8, m->n_tris8, m->nodesq,
                     m->ploc_c, m->ploc_nn, m->ploc_flag, m->ploc_scan, m->scan_tmp};
     for (void* p : ptrs) cudaFree(p);
 }
@@ -322,7 +332,7 @@ exm_status exm_env_total(exm_env* e, uint64_t* Q) {
 static void frame_free(exm_frame* f) {
     void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY,   f->Zq,
                     f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr, f->prec,
-                    f->pacc,   f->tsel, f->tv_gbuf, f->tv_inv, f->half_img, f->half_grad};
+                    f->pacc,   f->tsel, f->tv_gbuf, f->tv_inv, f->half_img, f->half_grad, f->big_tris};
     for (void* p : ptrs) cudaFree(p);
     if (f->half) {
         frame_free(f->half);

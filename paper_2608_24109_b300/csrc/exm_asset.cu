@@ -18,9 +18,10 @@ namespace exm {
 constexpr int kEmptyRef = 0x7fffffff;  // an unused child slot of a 4-wide node
 
 // Range checks of an imported asset; bit 0: a mesh index, bit 1: a node reference, bit 2: a
-// triangle record's original face id.
+// triangle record's original face id.  `nodes4`: 4-wide nodes (FP32 boxes, or quantised ones
+// when `quant`), whose four child references are checked.
 __global__ void asset_check_kernel(const int32_t* __restrict__ F, const int32_t* __restrict__ Fuv, int nf, int nv,
-                                   int nuv, const float4* __restrict__ nodes4, uint32_t n_nodes,
+                                   int nuv, const float4* __restrict__ nodes4, bool quant, uint32_t n_nodes,
                                    const float4* __restrict__ tris, uint32_t* bad) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint32_t b = 0;
@@ -35,7 +36,7 @@ __global__ void asset_check_kernel(const int32_t* __restrict__ F, const int32_t*
         }
     }
     if (nodes4 && t < n_nodes) {
-        const float4 r = nodes4[node4_at(t, 6)];
+        const float4 r = nodes4[quant ? nodeq_at(t, 1) : node4_at(t, 6)];
         const int ref[4] = {__float_as_int(r.x), __float_as_int(r.y), __float_as_int(r.z), __float_as_int(r.w)};
         for (int k = 0; k < 4; ++k) {
             const int c = ref[k];
@@ -57,10 +58,10 @@ __global__ void asset_check8_kernel(const float4* __restrict__ nodes8, uint32_t 
     if (ni + nt > 8 || (ni && cb + ni > n_nodes) || (nt && tb + nt > (uint64_t)nf)) atomicOr(bad, 2u);
 }
 
-// The corrupt-asset injector: a cycle that every index check passes.  4-wide: the root's node
-// children become the root; 8-wide: the root becomes its own only child, with the root's box.
-__global__ void asset_corrupt_kernel(float4* nodes, int width) {
-    if (width == 8) {  // the root becomes its own only child, with the root's box
+// The corrupt-asset injector: a cycle that every index check passes.  4-wide: the root's first
+// node child becomes the root; 8-wide: the root becomes its own only child, with the root's box.
+__global__ void asset_corrupt_kernel(float4* nodes, int layout) {
+    if (layout == EXM_BVH_8Q) {  // the root becomes its own only child, with the root's box
         uint32_t* w = reinterpret_cast<uint32_t*>(nodes);
         w[4] = 0u;          // child_base
         w[6] = 1u;          // one node child, no triangles
@@ -68,7 +69,7 @@ __global__ void asset_corrupt_kernel(float4* nodes, int width) {
         for (int k = 14; k < 20; ++k) w[k] = (k & 1) ? 0u : 0x000000ffu;          // qhi: slot 0 at 255
         return;
     }
-    int* ref = reinterpret_cast<int*>(&nodes[node4_at(0, 6)].x);
+    int* ref = reinterpret_cast<int*>(&nodes[layout == EXM_BVH_4Q ? nodeq_at(0, 1) : node4_at(0, 6)].x);
     for (int k = 0; k < 4; ++k)
         if (ref[k] >= 0 && ref[k] != kEmptyRef) {
             ref[k] = 0;
@@ -80,12 +81,20 @@ __global__ void asset_corrupt_kernel(float4* nodes, int width) {
 
 using namespace exm;
 
+static uint32_t node_bytes_of(int layout) {
+    return (layout == EXM_BVH_8Q ? kNode8 : (layout == EXM_BVH_4Q ? kNodeQ4 : 8)) * (uint32_t)sizeof(float4);
+}
+
+static float4* nodes_of(const exm_mesh* m) {
+    return m->layout == EXM_BVH_8Q ? m->nodes8 : (m->layout == EXM_BVH_4Q ? m->nodesq : m->nodes4);
+}
+
 static void asset_sizes(const exm_mesh* m, uint64_t bytes[EXM_ASSET_SECTIONS]) {
     bytes[0] = (uint64_t)m->nv * 12;
     bytes[1] = (uint64_t)m->nf * 12;
     bytes[2] = (uint64_t)m->nuv * 8;
     bytes[3] = (uint64_t)m->nf * 12;
-    bytes[4] = (uint64_t)m->n_nodes * (m->width == 8 ? kNode8 : 8) * sizeof(float4);
+    bytes[4] = (uint64_t)m->n_nodes * node_bytes_of(m->layout);
     bytes[5] = (uint64_t)m->nf * kTri * sizeof(float4);
     bytes[6] = sizeof(float4);
 }
@@ -96,7 +105,7 @@ exm_status exm_mesh_export_info(const exm_mesh* m, exm_asset_info* info) {
     if (!m || !info) return exm_fail(EXM_ERR_ARG, "exm_mesh_export_info: NULL argument");
     memset(info, 0, sizeof(*info));
     info->version = EXM_ASSET_VERSION;
-    info->node_bytes = (m->width == 8 ? kNode8 : 8) * sizeof(float4);
+    info->node_bytes = node_bytes_of(m->layout);
     info->nv = m->nv;
     info->nf = m->nf;
     info->nuv = m->nuv;
@@ -113,8 +122,8 @@ exm_status exm_mesh_export(const exm_mesh* m, void* const sections[EXM_ASSET_SEC
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t bytes[EXM_ASSET_SECTIONS];
     asset_sizes(m, bytes);
-    const void* src[EXM_ASSET_SECTIONS] = {m->V, m->F, m->UV, m->Fuv, m->width == 8 ? m->nodes8 : m->nodes4,
-                                           m->width == 8 ? m->tris8 : m->tris, m->sphere};
+    const void* src[EXM_ASSET_SECTIONS] = {m->V, m->F, m->UV, m->Fuv, nodes_of(m),
+                                           m->layout == EXM_BVH_8Q ? m->tris8 : m->tris, m->sphere};
     for (int k = 0; k < EXM_ASSET_SECTIONS; ++k) {
         exm_status st = exm_cuda_check(cudaMemcpyAsync(sections[k], src[k], bytes[k], cudaMemcpyDefault, s),
                                        "exm_mesh_export copy");
@@ -130,13 +139,17 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
     if (!c || !info || !sections) return exm_fail(EXM_ERR_ARG, "exm_mesh_import: NULL argument");
     for (int k = 0; k < EXM_ASSET_SECTIONS; ++k)
         if (!sections[k]) return exm_fail(EXM_ERR_ARG, "exm_mesh_import: NULL section");
-    if (info->version != EXM_ASSET_VERSION ||
-        (info->node_bytes != 8 * sizeof(float4) && info->node_bytes != kNode8 * sizeof(float4)))
+    int layout = 0;
+    for (const int l : {EXM_BVH_4, EXM_BVH_4Q, EXM_BVH_8Q})
+        if (info->node_bytes == node_bytes_of(l)) layout = l;
+    if (info->version != EXM_ASSET_VERSION || layout == 0)
         return exm_fail(EXM_ERR_ARG, "exm_mesh_import: asset version or node format differs from this library's");
-    const int width = info->node_bytes == kNode8 * sizeof(float4) ? 8 : 4;
     if (info->nv < 3 || info->nf < 1 || info->nuv < 3 || info->nf > (1 << 28) || info->nv > (1 << 28) ||
         info->nuv > (1 << 28) || info->n_nodes < 1 || info->n_nodes > (uint32_t)info->nf)
         return exm_fail(EXM_ERR_ARG, "exm_mesh_import: sizes");
+    // a 4-wide tree over nf leaves has at most max(nf - 1, 1) nodes (the buffers hold that many)
+    if (layout != EXM_BVH_8Q && info->n_nodes > (uint32_t)std::max(info->nf - 1, 1))
+        return exm_fail(EXM_ERR_ARG, "exm_mesh_import: more 4-wide nodes than a tree over nf leaves has");
     DeviceGuard g(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     // staging copies of the carrier on the device, then the regular upload path (frames, BVH
@@ -162,7 +175,8 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
         // the mesh indices first: the upload path's frame and BVH kernels read through them
         const int n = info->nf;
         asset_check_kernel<<<exm_blocks((size_t)n, 256), 256, 0, s>>>((const int32_t*)dF, (const int32_t*)dFuv, n,
-                                                                      info->nv, info->nuv, nullptr, 0, nullptr, bad);
+                                                                      info->nv, info->nuv, nullptr, false, 0, nullptr,
+                                                                      bad);
         uint32_t h = 0;
         st = exm_cuda_check(cudaMemcpyAsync(&h, bad, 4, cudaMemcpyDeviceToHost, s), "import check");
         if (st == EXM_OK) st = exm_cuda_check(cudaStreamSynchronize(s), "import check");
@@ -174,16 +188,19 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
     if (st == EXM_OK) {
         uint64_t bytes[EXM_ASSET_SECTIONS];
         m->n_nodes = info->n_nodes;
-        m->width = width;
+        m->layout = layout;
         asset_sizes(m, bytes);
         for (int k = 4; k < EXM_ASSET_SECTIONS && st == EXM_OK; ++k)
             if (info->bytes[k] != bytes[k]) st = exm_fail(EXM_ERR_ARG, "exm_mesh_import: BVH section size");
-        if (st == EXM_OK && width == 8 && !m->nodes8 &&
+        if (st == EXM_OK && layout == EXM_BVH_8Q && !m->nodes8 &&
             (exm_malloc((void**)&m->nodes8, (size_t)m->nf * kNode8 * sizeof(float4)) != cudaSuccess ||
              exm_malloc((void**)&m->tris8, (size_t)m->nf * kTri * sizeof(float4)) != cudaSuccess))
             st = exm_fail(EXM_ERR_OOM, "exm_mesh_import: BVH buffers");
+        if (st == EXM_OK && layout == EXM_BVH_4Q && !m->nodesq &&
+            exm_malloc((void**)&m->nodesq, (size_t)std::max(m->nf - 1, 1) * kNodeQ4 * sizeof(float4)) != cudaSuccess)
+            st = exm_fail(EXM_ERR_OOM, "exm_mesh_import: BVH buffers");
         if (st == EXM_OK) {
-            void* dst[3] = {width == 8 ? m->nodes8 : m->nodes4, width == 8 ? m->tris8 : m->tris, m->sphere};
+            void* dst[3] = {nodes_of(m), layout == EXM_BVH_8Q ? m->tris8 : m->tris, m->sphere};
             for (int k = 0; k < 3 && st == EXM_OK; ++k)
                 st = exm_cuda_check(cudaMemcpyAsync(dst[k], sections[4 + k], bytes[4 + k], cudaMemcpyDefault, s),
                                     "import BVH copy");
@@ -191,10 +208,10 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
         if (st == EXM_OK) {
             cudaMemsetAsync(bad, 0, 4, s);
             const size_t n = (size_t)std::max((uint32_t)m->nf, m->n_nodes);
-            asset_check_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->F, m->Fuv, m->nf, m->nv, m->nuv,
-                                                                 width == 8 ? nullptr : m->nodes4, m->n_nodes,
-                                                                 width == 8 ? m->tris8 : m->tris, bad);
-            if (width == 8)
+            asset_check_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(
+                m->F, m->Fuv, m->nf, m->nv, m->nuv, layout == EXM_BVH_8Q ? nullptr : nodes_of(m), layout == EXM_BVH_4Q,
+                m->n_nodes, layout == EXM_BVH_8Q ? m->tris8 : m->tris, bad);
+            if (layout == EXM_BVH_8Q)
                 asset_check8_kernel<<<exm_blocks(m->n_nodes, 256), 256, 0, s>>>(m->nodes8, m->n_nodes, m->nf, bad);
             uint32_t h = 0;
             st = exm_cuda_check(cudaMemcpyAsync(&h, bad, 4, cudaMemcpyDeviceToHost, s), "import check");
@@ -205,7 +222,7 @@ exm_status exm_mesh_import(exm_ctx* c, const exm_asset_info* info, const void* c
                                                          : "a BVH triangle record names no face"));
         }
         if (st == EXM_OK && exm_fault_take(kFaultCorrupt))
-            asset_corrupt_kernel<<<1, 1, 0, s>>>(width == 8 ? m->nodes8 : m->nodes4, width);
+            asset_corrupt_kernel<<<1, 1, 0, s>>>(nodes_of(m), layout);
         if (st == EXM_OK) {
             m->stamp = exm_next_stamp();
             st = exm_cuda_check(cudaStreamSynchronize(s), "exm_mesh_import");

@@ -99,6 +99,7 @@ __global__ void init_box_kernel(uint32_t* box) {
 // (ties: the lower index); mutual nearest neighbours merge into a new internal node at
 // the lower position and the cluster array is compacted.  Node ids are handed out from
 // n-2 downwards in scan order, so the last merge, the root, is node 0.
+constexpr int kDefaultLayout = EXM_BVH_4;  // the BVH layout of EXM_BVH_AUTO
 constexpr int kPlocR = 16;
 constexpr int kPlocBlock = 256;
 constexpr int kPlocMaxRounds = 4096;
@@ -270,13 +271,14 @@ __global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const
 //   [2] qlo.x[8] qlo.y[8]   [3] qlo.z[8] qhi.x[8]   [4] qhi.y[8] qhi.z[8]
 // An empty slot has qlo = 255 and qhi = 0.
 
-// Biased exponent e with 2^(e - 127) * 255 >= ext (ext > 0).
-__device__ __forceinline__ uint32_t step_exponent(float ext) {
-    const float x = __fdiv_ru(ext, 255.0f);
+// Biased exponent e with 2^(e - 127) * div >= ext (ext > 0), within 1..253 (so that 2^-(e-127)
+// is a normal float too).
+__device__ __forceinline__ uint32_t step_exponent(float ext, float div = 255.0f) {
+    const float x = __fdiv_ru(ext, div);
     const uint32_t b = __float_as_uint(x);
     uint32_t e = (b >> 23) & 0xffu;
     if (b & 0x7fffffu) ++e;
-    return max(e, 1u);
+    return min(max(e, 1u), 253u);
 }
 
 __global__ void collapse8_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
@@ -403,6 +405,63 @@ __global__ void sphere_centre_kernel(const float4* __restrict__ nodes4, float4* 
     *sphere = make_float4(c[0], c[1], c[2], 0.0f);
 }
 
+// ---- 4-wide nodes with quantised child boxes (EXM_BVH_4Q): the 4-wide tree above, each node
+// re-encoded in 64 bytes (layout in exm_device.cuh).  Per node and axis the grid step is the
+// smallest power of two with 250 steps covering the node's box (the union of its children's),
+// raised while the box's top lies above 252 steps, and the origin p lies at least one step
+// below the box (p = lo - step rounded down).  Each child plane is quantised outwards and
+// widened by one more step: qlo = floor((lo - p) / step) - 1, qhi = ceil((hi - p) / step) + 1
+// with the subtractions rounded down and up respectively, so that qlo >= 0, qhi <= 254 and the
+// decoded box contains the child's FP32 box with a margin of one step on every side.  The
+// traversal's folded plane evaluation (exm_shade.cu) is exact to half a step, so its box tests
+// are conservative: they keep every box the FP32 node's test keeps.
+__global__ void quant4_kernel(const float4* __restrict__ nodes4, uint32_t n_nodes, float4* __restrict__ nodesq) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_nodes) return;
+    float pl[6][4];
+    for (int a = 0; a < 6; ++a) {
+        const float4 v = nodes4[node4_at(q, a)];
+        pl[a][0] = v.x; pl[a][1] = v.y; pl[a][2] = v.z; pl[a][3] = v.w;
+    }
+    const float4 rv = nodes4[node4_at(q, 6)];
+    const int ref[4] = {__float_as_int(rv.x), __float_as_int(rv.y), __float_as_int(rv.z), __float_as_int(rv.w)};
+    float p[3], step[3];
+    uint32_t qlo[3], qhi[3];
+    for (int a = 0; a < 3; ++a) {
+        float L = INFINITY, H = -INFINITY;
+        for (int c = 0; c < 4; ++c)
+            if (ref[c] != kEmpty4) { L = fminf(L, pl[a][c]); H = fmaxf(H, pl[3 + a][c]); }
+        if (!(L <= H)) L = H = 0.0f;
+        uint32_t e = step_exponent(fmaxf(__fsub_ru(H, L), 1e-30f), 250.0f);
+        float st = __uint_as_float(e << 23), inv = __uint_as_float((254u - e) << 23), o = __fsub_rd(L, st);
+        while (e < 253u && __fmul_ru(__fsub_ru(H, o), inv) > 252.0f) {
+            ++e;
+            st = __uint_as_float(e << 23);
+            inv = __uint_as_float((254u - e) << 23);
+            o = __fsub_rd(L, st);
+        }
+        p[a] = o;
+        step[a] = st;
+        qlo[a] = qhi[a] = 0u;
+        for (int c = 0; c < 4; ++c) {
+            uint32_t bl = 255u, bh = 0u;
+            if (ref[c] != kEmpty4) {
+                const float fl = floorf(__fmul_rd(__fsub_rd(pl[a][c], o), inv)) - 1.0f;
+                const float fh = ceilf(__fmul_ru(__fsub_ru(pl[3 + a][c], o), inv)) + 1.0f;
+                bl = (uint32_t)fminf(fmaxf(fl, 0.0f), 255.0f);
+                bh = (uint32_t)fminf(fmaxf(fh, 0.0f), 255.0f);
+            }
+            qlo[a] |= bl << (8 * c);
+            qhi[a] |= bh << (8 * c);
+        }
+    }
+    nodesq[nodeq_at(q, 0)] = make_float4(p[0], p[1], p[2], step[0]);
+    nodesq[nodeq_at(q, 1)] = rv;
+    nodesq[nodeq_at(q, 2)] = make_float4(__uint_as_float(qlo[0]), __uint_as_float(qlo[1]), __uint_as_float(qlo[2]),
+                                         __uint_as_float(qhi[0]));
+    nodesq[nodeq_at(q, 3)] = make_float4(__uint_as_float(qhi[1]), __uint_as_float(qhi[2]), step[1], step[2]);
+}
+
 // The same centre from the binary root's box (the 8-wide build).
 __global__ void sphere8_centre_kernel(const float* __restrict__ bounds, int n, float4* sphere) {
     const float* b = bounds + 6 * (size_t)(n > 1 ? 0 : n - 1);
@@ -493,14 +552,16 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
             std::swap(cin, cout);
         }
     }
-    // the node width: 8-wide compressed nodes when asked for, else 4-wide.  Measured on the three
-    // blob workloads, the 8-wide tree visits 32% fewer nodes but its eight quantised boxes cost
-    // more instructions per visit: its tracer took 20%, 8% and 1% longer (99K, 499K, 2M triangles)
-    int width = m->ctx->bvh_width;
-    if (width == 0) width = 4;
-    if (width == 8 && (size_t)n >= (1u << 27)) width = 4;  // the 8-wide stack entries hold 24-bit node indices
-    m->width = width;
-    if (width == 8) {
+    // the node layout: 8-wide compressed nodes when asked for, else 4-wide ones (FP32 or quantised
+    // boxes).  Measured on the three blob workloads (99K, 499K, 2M triangles), the 8-wide tree
+    // visits 32% fewer nodes but its eight quantised boxes cost more instructions per visit: its
+    // tracer took 20%, 8% and 1% longer than the FP32 4-wide tree.  The quantised 4-wide nodes
+    // halve the node loads (L1 data-pipe use 74% -> 49% on the 2M-triangle tree) for 17% more
+    // instructions, and the tracer, then issue-bound, took 8%, 6% and 4% longer.
+    int layout = m->ctx->bvh_layout ? m->ctx->bvh_layout : kDefaultLayout;
+    if (layout == EXM_BVH_8Q && (size_t)n >= (1u << 27)) layout = EXM_BVH_4Q;  // 8-wide stack entries: 24-bit node indices
+    m->layout = layout;
+    if (layout == EXM_BVH_8Q) {
         if (!m->nodes8) {
             const size_t nn = (size_t)n;
             if (exm_malloc((void**)&m->nodes8, nn * kNode8 * sizeof(float4)) != cudaSuccess ||
@@ -571,5 +632,13 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
     }
     sphere_centre_kernel<<<1, 1, 0, s>>>(m->nodes4, m->sphere);
     sphere_radius_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->tris, n, m->sphere);
+    if (layout == EXM_BVH_4Q) {
+        if (!m->nodesq && exm_malloc((void**)&m->nodesq, (size_t)(n > 1 ? n - 1 : 1) * kNodeQ4 * sizeof(float4)) !=
+                              cudaSuccess) {
+            m->nodesq = nullptr;
+            return exm_fail(EXM_ERR_OOM, "BVH buffers (quantised 4-wide)");
+        }
+        quant4_kernel<<<exm_blocks(m->n_nodes, 256), 256, 0, s>>>(m->nodes4, m->n_nodes, m->nodesq);
+    }
     return exm_cuda_check(cudaGetLastError(), "BVH build launch");
 }

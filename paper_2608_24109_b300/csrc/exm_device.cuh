@@ -399,7 +399,16 @@ struct BvhView {
     const float4* nodes4;
     const float4* sphere;  // bounding sphere of the triangles: centre, R^2
     const float4* nodes8;  // 8-wide compressed nodes (exm_bvh.cu), when the mesh uses them
+    const float4* nodesq;  // 4-wide nodes with quantised boxes, when the mesh uses them
 };
+// 4-wide node with quantised child boxes (EXM_BVH_4Q), 64 bytes in two 32-byte chunks (skewed
+// like the triangle records: chunk j of node q at position j xor (q/2 mod 2)):
+//   chunk 0: p.x p.y p.z step.x | ref[4]
+//   chunk 1: qlo.x qlo.y qlo.z qhi.x | qhi.y qhi.z step.y step.z
+// The q words hold one byte per child (child c in byte c); child c's box on axis a is
+// [p_a + qlo_c step_a, p_a + qhi_c step_a] with power-of-two steps.  An empty slot has qlo 255,
+// qhi 0 and ref kEmptyChild.
+constexpr int kNodeQ4 = 4;     // float4 per quantised 4-wide node
 constexpr int kNode8 = 5;      // float4 per 8-wide compressed node
 constexpr int kTri = 4;        // float4 per triangle record: the vertices (original id in the first .w), padding
 constexpr int kStackSize8 = 64;  // node groups on the 8-wide traversal stack: one per level
@@ -409,6 +418,10 @@ __host__ __device__ __forceinline__ size_t node4_at(size_t q, unsigned v) {
 }
 __host__ __device__ __forceinline__ size_t tri_at(size_t k, unsigned v) {
     return (size_t)kTri * k + 2 * ((v / 2) ^ ((unsigned)(k >> 1) & 1u)) + (v & 1u);
+}
+// float4 v (0..3) of quantised 4-wide node q (layout below): skewed like a triangle record.
+__host__ __device__ __forceinline__ size_t nodeq_at(size_t q, unsigned v) {
+    return 4 * q + 2 * ((v / 2) ^ ((unsigned)(q >> 1) & 1u)) + (v & 1u);
 }
 // The chunk at byte offset `x` (a multiple of 32 below the record's alignment) of an aligned
 // record: no carry can occur, so the xor stays in the address's low word.

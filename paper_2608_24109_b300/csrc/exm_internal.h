@@ -12,7 +12,7 @@
 struct exm_ctx {
     int device = 0;
     int num_sms = 0;
-    int bvh_width = 0;             // BVH node width of new meshes: 4, 8, 0 = by mesh size (EXM_BVH_WIDTH)
+    int bvh_layout = 0;            // BVH layout of new meshes: EXM_BVH_4 / _4Q / _8Q, 0 = the default
     uint32_t* d_status = nullptr;  // latched device error bits
     unsigned long long launches = 0;  // kernels launched by the library on this context
     unsigned long long* d_acc = nullptr;  // 64-bit fixed-point accumulators of the objective calls
@@ -44,8 +44,9 @@ struct exm_mesh {
     float4* tris = nullptr;    // [nf * 4] triangle records in leaf order (64 B: three vertices, padding)
     float4* nodes4 = nullptr;  // [max(nf-1,1) * 8] 4-wide nodes
     float4* sphere = nullptr;  // [1] bounding sphere of the triangles: centre, inflated R^2
-    uint32_t n_nodes = 0;      // nodes of the BVH in use (4-wide in nodes4 or 8-wide in nodes8)
-    int width = 4;             // BVH in use: 4-wide (nodes4, tris) or 8-wide compressed (nodes8, tris8)
+    uint32_t n_nodes = 0;      // nodes of the BVH in use (in nodes4, nodesq or nodes8)
+    int layout = EXM_BVH_4;    // BVH in use: EXM_BVH_4 (nodes4, tris), _4Q (nodesq, tris), _8Q (nodes8, tris8)
+    float4* nodesq = nullptr;  // [n_nodes * 4] 4-wide nodes with quantised child boxes
     float4* nodes8 = nullptr;  // [n_nodes * 5] 8-wide compressed nodes
     float4* tris8 = nullptr;   // [nf * 4] triangle records in the 8-wide nodes' order
     uint32_t* n_tris8 = nullptr;
@@ -89,13 +90,15 @@ struct exm_env {
 // float4 per pixel record: [0..4] the camera-ray geometry (pixel_prep_kernel), [5..6] the
 // material and shading normal (pixel_surface_kernel)
 constexpr int kPrec = 7;
+constexpr uint32_t kBigTriCap = 1u << 18;  // entries of a frame's large-triangle list (exm_raster.cu)
 
 struct exm_frame {
     exm_ctx* ctx = nullptr;
     int views = 0, W = 0, H = 0;
     uint64_t* visbuf = nullptr;   // [views*H*W]
     uint32_t* pixels = nullptr;   // [views*H*W] covered pixel ids (view*H*W + py*W + px)
-    uint32_t* counters = nullptr; // [0] covered count, [1] work cursor
+    uint32_t* counters = nullptr; // [0] covered count, [1] work cursor, [2] large triangles listed
+    uint2* big_tris = nullptr;    // (view, face) of the triangles with large pixel boxes (exm_raster.cu)
     unsigned long long* samples = nullptr;  // [1] shaded samples of the last forward
     unsigned long long* work = nullptr;     // [4] work counters of the last counted pass
     void* cams = nullptr;         // device copy of the cameras [views]
@@ -201,6 +204,7 @@ inline bool ensure(TT** ptr, size_t* cap, size_t need) {
 struct exm_relight_pass;
 // One ray queue of a batched tracer launch: the queue of one request, the BVH of its asset and
 // the outputs its rays write.
+constexpr int kJobLayouts = 3;  // BVH layouts EXM_BVH_4, _4Q, _8Q: one batched launch each
 struct ExmTraceJob {
     const float4* nodes4;
     const float4* tris;

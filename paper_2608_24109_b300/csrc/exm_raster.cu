@@ -44,50 +44,107 @@ __global__ void snap_kernel(const float* __restrict__ V, int nv, const Cam* __re
 
 __device__ __forceinline__ bool edge_incl(long long dx, long long dy) { return dy > 0 || (dy == 0 && dx < 0); }
 
+// A snapped triangle set up for rasterisation: integer vertices, twice its area, quantised
+// depths, its pixel box (inclusive, clipped to the image) and the fill rule of each edge.
+struct TriSetup {
+    long long X0, Y0, X1, Y1, X2, Y2, A2, Z0, Z1, Z2;
+    int x0, x1, y0, y1;
+    bool in0, in1, in2;
+};
+
+// false: the triangle is culled (a bad vertex, back-facing or degenerate, or outside the
+// guard band, which latches ERRBIT_GUARD) or covers no pixel centre.
+__device__ __forceinline__ bool tri_setup(const int32_t* __restrict__ F, int f, int nv, const int2* __restrict__ xy,
+                                          const uint32_t* __restrict__ zq, int W, int H, uint32_t* status,
+                                          TriSetup* t) {
+    const int ia = __ldg(F + 3 * f), ib = __ldg(F + 3 * f + 1), ic = __ldg(F + 3 * f + 2);
+    if ((unsigned)ia >= (unsigned)nv || (unsigned)ib >= (unsigned)nv || (unsigned)ic >= (unsigned)nv) return false;
+    const int2 a = xy[ia], b = xy[ib], d = xy[ic];
+    if (a.x == kBadSnap || b.x == kBadSnap || d.x == kBadSnap) return false;
+    t->X0 = a.x; t->Y0 = a.y; t->X1 = b.x; t->Y1 = b.y; t->X2 = d.x; t->Y2 = d.y;
+    t->A2 = (t->Y1 - t->Y0) * (t->X2 - t->X0) - (t->X1 - t->X0) * (t->Y2 - t->Y0);
+    if (t->A2 <= 0) return false;
+    if (t->A2 >= (1ll << 38)) { atomicOr(status, ERRBIT_GUARD); return false; }
+    t->Z0 = zq[ia]; t->Z1 = zq[ib]; t->Z2 = zq[ic];
+    const long long mnx = min(t->X0, min(t->X1, t->X2)), mxx = max(t->X0, max(t->X1, t->X2));
+    const long long mny = min(t->Y0, min(t->Y1, t->Y2)), mxy = max(t->Y0, max(t->Y1, t->Y2));
+    const long long x0 = mnx - 128 <= 0 ? 0 : (mnx - 128 + 255) / 256;
+    const long long x1 = min(mxx - 128 < 0 ? -1 : (mxx - 128) / 256, (long long)W - 1);
+    const long long y0 = mny - 128 <= 0 ? 0 : (mny - 128 + 255) / 256;
+    const long long y1 = min(mxy - 128 < 0 ? -1 : (mxy - 128) / 256, (long long)H - 1);
+    if (x0 > x1 || y0 > y1) return false;
+    t->x0 = (int)x0; t->x1 = (int)x1; t->y0 = (int)y0; t->y1 = (int)y1;
+    t->in0 = edge_incl(t->X2 - t->X1, t->Y2 - t->Y1);
+    t->in1 = edge_incl(t->X0 - t->X2, t->Y0 - t->Y2);
+    t->in2 = edge_incl(t->X1 - t->X0, t->Y1 - t->Y0);
+    return true;
+}
+
+// Pixel (px, py): the three edge functions at its centre under the fill rule, then depth =
+// floor(sum E_i Z_i / A2) and a 64-bit atomicMin of (depth << 32 | f).
+__device__ __forceinline__ void raster_pixel(const TriSetup& t, int f, int px, int py, int W,
+                                             unsigned long long* __restrict__ vb) {
+    const long long Px = (long long)px * 256 + 128, Py = (long long)py * 256 + 128;
+    const long long E0 = (t.Y1 - Py) * (t.X2 - Px) - (t.X1 - Px) * (t.Y2 - Py);
+    const long long E1 = (t.Y2 - Py) * (t.X0 - Px) - (t.X2 - Px) * (t.Y0 - Py);
+    const long long E2 = (t.Y0 - Py) * (t.X1 - Px) - (t.X0 - Px) * (t.Y1 - Py);
+    if (!(E0 > 0 || (E0 == 0 && t.in0))) return;
+    if (!(E1 > 0 || (E1 == 0 && t.in1))) return;
+    if (!(E2 > 0 || (E2 == 0 && t.in2))) return;
+    const long long num = E0 * t.Z0 + E1 * t.Z1 + E2 * t.Z2;
+    const unsigned long long z = (unsigned long long)(num / t.A2);
+    atomicMin(vb + (size_t)py * W + px, (z << 32) | (unsigned long long)(uint32_t)f);
+}
+
+// Triangles whose pixel box holds more than kBigTriPixels pixels are handed to
+// raster_big_kernel (a warp per triangle) through the frame's list of kBigTriCap (view, face)
+// entries; when the list is full, the thread rasterises the triangle itself.  Both paths write
+// the same keys by atomicMin, so the visibility buffer does not depend on which path took a
+// triangle.
+constexpr long long kBigTriPixels = 256;
+
 // a2: one thread per (view, triangle).  Integer edge functions, lexicographic (top-left)
 // fill rule, back faces culled, depth = floor(sum E_i Z_i / A2), 64-bit atomicMin.
 __global__ void raster_kernel(const int32_t* __restrict__ F, int nf, int nv, const int2* __restrict__ XY,
                               const uint32_t* __restrict__ Zq, int views, int W, int H,
-                              unsigned long long* __restrict__ visbuf, uint32_t* status) {
-    int f = blockIdx.x * blockDim.x + threadIdx.x;
-    int c = blockIdx.y;
+                              unsigned long long* __restrict__ visbuf, uint2* __restrict__ big,
+                              uint32_t* __restrict__ big_count, uint32_t* status) {
+    const int f = blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
     if (f >= nf || c >= views) return;
-    int ia = __ldg(F + 3 * f), ib = __ldg(F + 3 * f + 1), ic = __ldg(F + 3 * f + 2);
-    if ((unsigned)ia >= (unsigned)nv || (unsigned)ib >= (unsigned)nv || (unsigned)ic >= (unsigned)nv) return;
-    const int2* xy = XY + (size_t)c * nv;
-    const uint32_t* zq = Zq + (size_t)c * nv;
-    int2 a = xy[ia], b = xy[ib], d = xy[ic];
-    if (a.x == kBadSnap || b.x == kBadSnap || d.x == kBadSnap) return;
-    long long X0 = a.x, Y0 = a.y, X1 = b.x, Y1 = b.y, X2 = d.x, Y2 = d.y;
-    long long A2 = (Y1 - Y0) * (X2 - X0) - (X1 - X0) * (Y2 - Y0);
-    if (A2 <= 0) return;
-    if (A2 >= (1ll << 38)) { atomicOr(status, ERRBIT_GUARD); return; }
-    long long Z0 = zq[ia], Z1 = zq[ib], Z2 = zq[ic];
-    long long mnx = min(X0, min(X1, X2)), mxx = max(X0, max(X1, X2));
-    long long mny = min(Y0, min(Y1, Y2)), mxy = max(Y0, max(Y1, Y2));
-    long long x0 = mnx - 128 <= 0 ? 0 : (mnx - 128 + 255) / 256;
-    long long x1 = mxx - 128 < 0 ? -1 : (mxx - 128) / 256;
-    long long y0 = mny - 128 <= 0 ? 0 : (mny - 128 + 255) / 256;
-    long long y1 = mxy - 128 < 0 ? -1 : (mxy - 128) / 256;
-    x1 = min(x1, (long long)W - 1);
-    y1 = min(y1, (long long)H - 1);
-    bool in0 = edge_incl(X2 - X1, Y2 - Y1), in1 = edge_incl(X0 - X2, Y0 - Y2), in2 = edge_incl(X1 - X0, Y1 - Y0);
-    unsigned long long* vb = visbuf + (size_t)c * W * H;
-    for (long long py = y0; py <= y1; ++py) {
-        long long Py = py * 256 + 128;
-        for (long long px = x0; px <= x1; ++px) {
-            long long Px = px * 256 + 128;
-            long long E0 = (Y1 - Py) * (X2 - Px) - (X1 - Px) * (Y2 - Py);
-            long long E1 = (Y2 - Py) * (X0 - Px) - (X2 - Px) * (Y0 - Py);
-            long long E2 = (Y0 - Py) * (X1 - Px) - (X0 - Px) * (Y1 - Py);
-            if (!(E0 > 0 || (E0 == 0 && in0))) continue;
-            if (!(E1 > 0 || (E1 == 0 && in1))) continue;
-            if (!(E2 > 0 || (E2 == 0 && in2))) continue;
-            long long num = E0 * Z0 + E1 * Z1 + E2 * Z2;
-            unsigned long long z = (unsigned long long)(num / A2);
-            unsigned long long key = (z << 32) | (unsigned long long)(uint32_t)f;
-            atomicMin(vb + py * W + px, key);
+    TriSetup t;
+    if (!tri_setup(F, f, nv, XY + (size_t)c * nv, Zq + (size_t)c * nv, W, H, status, &t)) return;
+    if ((long long)(t.x1 - t.x0 + 1) * (t.y1 - t.y0 + 1) > kBigTriPixels && big) {
+        const uint32_t k = atomicAdd(big_count, 1u);
+        if (k < kBigTriCap) {
+            big[k] = make_uint2((uint32_t)c, (uint32_t)f);
+            return;
         }
+    }
+    unsigned long long* vb = visbuf + (size_t)c * W * H;
+    for (int py = t.y0; py <= t.y1; ++py)
+        for (int px = t.x0; px <= t.x1; ++px) raster_pixel(t, f, px, py, W, vb);
+}
+
+// The listed large triangles: persistent warps, a triangle per warp at a time, its pixel box
+// walked 32 pixels at a time (row-major, so a warp's pixels share rows of the buffer).
+__global__ void raster_big_kernel(const int32_t* __restrict__ F, int nv, const int2* __restrict__ XY,
+                                  const uint32_t* __restrict__ Zq, int W, int H,
+                                  unsigned long long* __restrict__ visbuf, const uint2* __restrict__ big,
+                                  const uint32_t* __restrict__ big_count, uint32_t* status) {
+    const uint32_t n = min(*big_count, kBigTriCap);
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < n; k += nwarps) {
+        const uint2 e = big[k];
+        const int c = (int)e.x, f = (int)e.y;
+        TriSetup t;
+        if (!tri_setup(F, f, nv, XY + (size_t)c * nv, Zq + (size_t)c * nv, W, H, status, &t)) continue;
+        unsigned long long* vb = visbuf + (size_t)c * W * H;
+        const uint32_t bw = (uint32_t)(t.x1 - t.x0 + 1);
+        const uint64_t area = (uint64_t)bw * (uint32_t)(t.y1 - t.y0 + 1);
+        for (uint64_t i = lane; i < area; i += 32)
+            raster_pixel(t, f, t.x0 + (int)(i % bw), t.y0 + (int)(i / bw), W, vb);
     }
 }
 
@@ -134,17 +191,24 @@ exm_status exm_raster_impl(exm_ctx* ctx, const exm_mesh* m, exm_frame* f, int vi
         }
         f->snap_capacity = need;
     }
+    if (!f->big_tris && exm_malloc((void**)&f->big_tris, (size_t)kBigTriCap * sizeof(uint2)) != cudaSuccess) {
+        f->big_tris = nullptr;
+        return exm_fail(EXM_ERR_OOM, "large-triangle list");
+    }
     size_t npx = (size_t)views * f->W * f->H;
     cudaMemsetAsync(f->visbuf, 0xff, npx * sizeof(uint64_t), s);
-    cudaMemsetAsync(f->counters, 0, 2 * sizeof(uint32_t), s);
+    cudaMemsetAsync(f->counters, 0, 3 * sizeof(uint32_t), s);  // covered count, work cursor, large triangles
     dim3 g1(exm_blocks(m->nv, 256), views);
     snap_kernel<<<g1, 256, 0, s>>>(m->V, m->nv, (const Cam*)f->cams, views, (int2*)f->XY, f->Zq, ctx->d_status);
     dim3 g2(exm_blocks(m->nf, 128), views);
     raster_kernel<<<g2, 128, 0, s>>>(m->F, m->nf, m->nv, (const int2*)f->XY, f->Zq, views, f->W, f->H,
-                                     (unsigned long long*)f->visbuf, ctx->d_status);
+                                     (unsigned long long*)f->visbuf, f->big_tris, f->counters + 2, ctx->d_status);
+    raster_big_kernel<<<ctx->num_sms * 4, 256, 0, s>>>(m->F, m->nv, (const int2*)f->XY, f->Zq, f->W, f->H,
+                                                        (unsigned long long*)f->visbuf, f->big_tris, f->counters + 2,
+                                                        ctx->d_status);
     size_t tiles = (size_t)((f->W + 7) / 8) * ((f->H + 3) / 4) * views;
     compact_kernel<<<exm_blocks(tiles * 32, 256), 256, 0, s>>>((const unsigned long long*)f->visbuf, views, f->W,
                                                                f->H, f->pixels, f->counters);
-    ctx->launches += 3;
+    ctx->launches += 4;
     return exm_cuda_check(cudaGetLastError(), "raster launch");
 }

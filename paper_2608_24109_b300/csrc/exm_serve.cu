@@ -67,8 +67,8 @@ struct Lane {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     bool busy = false;
-    ExmTraceJob* h_jobs = nullptr;  // pinned host, 2 x 2 x kMaxBatch (closest / any, 4- / 8-wide)
-    ExmTraceJob* d_jobs = nullptr;  // device, 2 x 2 x kMaxBatch
+    ExmTraceJob* h_jobs = nullptr;  // pinned host, 2 x kJobLayouts x kMaxBatch (closest / any, per layout)
+    ExmTraceJob* d_jobs = nullptr;  // device, the same
 };
 
 struct Result {
@@ -95,10 +95,11 @@ struct exm_server {
 
 // Device bytes of one frame: visibility keys and pixel list, pixel records (the 112-byte
 // shading record and the 48-byte adjoint sums), the texel of each direct sample, snapped
-// vertices, visibility bits, secondary hit ids, the ray queue of a chunk, cameras, counters.
+// vertices, visibility bits, secondary hit ids, the ray queue of a chunk, cameras, counters,
+// the large-triangle list of the raster.
 static size_t frame_bytes(size_t P, size_t views, size_t nv, int wd, int ws, int nb, size_t ray_cap) {
     return P * (8 + 4 + 16 * kPrec + 48) + P * (size_t)wd * 32 * 4 + views * nv * 12 + P * (size_t)(wd + ws) * 4 +
-           P * (size_t)nb * 4 + ray_cap * 32 + views * 80 + 64;
+           P * (size_t)nb * 4 + ray_cap * 32 + views * 80 + 64 + (size_t)kBigTriCap * 8;
 }
 
 // The queue a request's frame needs: all its rays (one chunk) when they fit a batched queue,
@@ -204,8 +205,8 @@ static void launch_batch(exm_server* s, Lane& lane, const std::vector<int>& slot
         bst = relight_trace_batch(ctx, live.data(), (int)live.size(), true, lane.h_jobs, lane.d_jobs, st_);
         for (exm_relight_pass* rp : live) relight_pass_shadow_rays(ctx, rp, st_);
         if (bst == EXM_OK)
-            bst = relight_trace_batch(ctx, live.data(), (int)live.size(), false, lane.h_jobs + 2 * kMaxBatch,
-                                      lane.d_jobs + 2 * kMaxBatch, st_);
+            bst = relight_trace_batch(ctx, live.data(), (int)live.size(), false, lane.h_jobs + kJobLayouts * kMaxBatch,
+                                      lane.d_jobs + kJobLayouts * kMaxBatch, st_);
     }
     for (size_t i = 0; i < n; ++i) {
         if (pass[i]) {
@@ -309,9 +310,9 @@ exm_status exm_server_create(exm_ctx* ctx, uint64_t hbm_budget_bytes, int max_sl
     for (Lane& ln : s->lanes)
         ok = ok && cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&ln.done, cudaEventDisableTiming) == cudaSuccess &&
-             cudaHostAlloc((void**)&ln.h_jobs, 4 * kMaxBatch * sizeof(ExmTraceJob), cudaHostAllocDefault) ==
+             cudaHostAlloc((void**)&ln.h_jobs, 2 * kJobLayouts * kMaxBatch * sizeof(ExmTraceJob), cudaHostAllocDefault) ==
                  cudaSuccess &&
-             exm_malloc((void**)&ln.d_jobs, 4 * kMaxBatch * sizeof(ExmTraceJob)) == cudaSuccess;
+             exm_malloc((void**)&ln.d_jobs, 2 * kJobLayouts * kMaxBatch * sizeof(ExmTraceJob)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         exm_server_destroy(s);

@@ -50,7 +50,7 @@ struct ShadeArgs {
     const float* tan;
     const float* fsign;
     BvhView bvh;
-    int bvh_width;  // 4: bvh.nodes4, 8: bvh.nodes8 (and bvh.tris in its order)
+    int bvh_layout;  // EXM_BVH_4: bvh.nodes4, _4Q: bvh.nodesq, _8Q: bvh.nodes8 (and bvh.tris in its order)
     // maps, env, frame
     MapView map;
     EnvView env;
@@ -538,13 +538,87 @@ __device__ __forceinline__ void node8_hits(const float4* N, const Ray& r, float 
 
 using TraceJob = ExmTraceJob;
 
+// Plane byte c of a word of quantised planes, as the float 2^23 + q (exact).
+__device__ __forceinline__ float qplane(uint32_t w, int c) {
+    return __uint_as_float(__byte_perm(w, 0x4B000000u, 0x7540u + (uint32_t)c));
+}
+
+// Box tests of the four children of 4-wide node `node`: their entry distances tc, which of
+// them the ray enters before tmax (hc) and their references.
+template <int LAYOUT>
+__device__ __forceinline__ void node4_test(const BvhView& bvh, int node, const Ray& r, float tmax, float tc[4],
+                                           bool hc[4], int ref[4]) {
+    if constexpr (LAYOUT == EXM_BVH_4Q) {
+        // two 32-byte loads (chunks skewed by bit 1 of the node index).  Plane q of axis a lies
+        // at t = q s_a + b_a with s_a = step_a / d_a (exact scaling by a power of two) and
+        // b_a = (p_a - o_a) / d_a; it is evaluated as fma(2^23 + q, s_a, b_a - 2^23 s_a), the
+        // byte placed under the exponent of 2^23 by one permutation.  The folded constant's
+        // rounding is at most half a grid step, inside the one-step margin the build adds.
+        const float4* N = bvh.nodesq + kNodeQ4 * (size_t)node;
+        const unsigned x = ((unsigned)node & 2u) << 4;
+        float4 a0, a1, b0, b1;
+        ldg32(chunk_at(N, x), a0, a1);
+        ldg32(chunk_at(N, x ^ 32u), b0, b1);
+        const float sx = a0.w * r.inv.x, sy = b1.z * r.inv.y, sz = b1.w * r.inv.z;
+        const float cx = fmaf(-8388608.0f, sx, fmaf(a0.x, r.inv.x, r.oinv.x));
+        const float cy = fmaf(-8388608.0f, sy, fmaf(a0.y, r.inv.y, r.oinv.y));
+        const float cz = fmaf(-8388608.0f, sz, fmaf(a0.z, r.inv.z, r.oinv.z));
+        const uint32_t lox = __float_as_uint(b0.x), loy = __float_as_uint(b0.y), loz = __float_as_uint(b0.z);
+        const uint32_t hix = __float_as_uint(b0.w), hiy = __float_as_uint(b1.x), hiz = __float_as_uint(b1.y);
+        // near / far plane words of each axis, by the ray's direction signs (four children at once)
+        const uint32_t nx = r.nx ? hix : lox, fx = r.nx ? lox : hix;
+        const uint32_t ny = r.ny ? hiy : loy, fy = r.ny ? loy : hiy;
+        const uint32_t nz = r.nz ? hiz : loz, fz = r.nz ? loz : hiz;
+        ref[0] = __float_as_int(a1.x); ref[1] = __float_as_int(a1.y);
+        ref[2] = __float_as_int(a1.z); ref[3] = __float_as_int(a1.w);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float t0 = fmaxf(fmax3(fmaf(qplane(nx, c), sx, cx), fmaf(qplane(ny, c), sy, cy),
+                                         fmaf(qplane(nz, c), sz, cz)), 0.0f);
+            const float t1 = fminf(fmin3(fmaf(qplane(fx, c), sx, cx), fmaf(qplane(fy, c), sy, cy),
+                                         fmaf(qplane(fz, c), sz, cz)), tmax);
+            tc[c] = t0;
+            hc[c] = t0 <= t1 && ref[c] != kEmptyChild;
+        }
+    } else {
+        // the six plane vectors in three 32-byte loads (chunks skewed by the node index), then
+        // the near / far planes of each axis chosen by the ray's direction signs
+        const float4* N = bvh.nodes4 + 8 * (size_t)node;
+        const unsigned sk = ((unsigned)node & 3u) << 5;
+        float4 lx, ly, lz, hx, hy, hz;
+        ldg32(chunk_at(N, sk), lx, ly);
+        ldg32(chunk_at(N, sk ^ 32u), lz, hx);
+        ldg32(chunk_at(N, sk ^ 64u), hy, hz);
+        const float4 rf = __ldg(chunk_at(N, sk ^ 96u));
+        const float4 qx = r.nx ? hx : lx, qy = r.ny ? hy : ly, qz = r.nz ? hz : lz;
+        const float4 fx = r.nx ? lx : hx, fy = r.ny ? ly : hy, fz = r.nz ? lz : hz;
+        ref[0] = __float_as_int(rf.x); ref[1] = __float_as_int(rf.y);
+        ref[2] = __float_as_int(rf.z); ref[3] = __float_as_int(rf.w);
+#define EXM_BOX(C, c)                                                                                              \
+    {                                                                                                              \
+        const float t0 = fmaxf(fmax3(fmaf(qx.c, r.inv.x, r.oinv.x), fmaf(qy.c, r.inv.y, r.oinv.y),                    \
+                                     fmaf(qz.c, r.inv.z, r.oinv.z)), 0.0f);                                        \
+        const float t1 = fminf(fmin3(fmaf(fx.c, r.inv.x, r.oinv.x), fmaf(fy.c, r.inv.y, r.oinv.y),                    \
+                                     fmaf(fz.c, r.inv.z, r.oinv.z)), tmax);                                        \
+        tc[C] = t0;                                                                                                \
+        hc[C] = t0 <= t1 && ref[C] != kEmptyChild;                                                                 \
+    }
+        EXM_BOX(0, x)
+        EXM_BOX(1, y)
+        EXM_BOX(2, z)
+        EXM_BOX(3, w)
+#undef EXM_BOX
+    }
+}
+
 // The traversal loop.  Single queue (BATCH false): the chunk's queue of A, claimed kPool rays at
 // a time.  Batched: the queues of `jobs`, whose pools are numbered one after another; a warp
 // claims a pool number, finds its queue, and each lane keeps the BVH of the queue its ray came
 // from, so the lanes of a warp may trace rays of different assets.
-template <bool CLOSEST, bool COUNT, bool BATCH, bool W8>
+template <bool CLOSEST, bool COUNT, bool BATCH, int LAYOUT>
 __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* __restrict__ jobs, int njobs,
                                            uint32_t* batch_cursor) {
+    constexpr bool W8 = LAYOUT == EXM_BVH_8Q;
     int stack[W8 ? kStackSize8 : kStackSize4];
     __shared__ uint32_t s_pool_end[BATCH ? kMaxBatch : 1];  // BATCH: pools of queues 0..j
     __shared__ uint32_t s_count[BATCH ? kMaxBatch : 1];     // BATCH: rays of queue j
@@ -623,6 +697,7 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                     rays = jobs[job].rays;
                     bvh.nodes4 = jobs[job].nodes4;
                     bvh.nodes8 = jobs[job].nodes4;
+                    bvh.nodesq = jobs[job].nodes4;
                     bvh.tris = jobs[job].tris;
                     bvh.sphere = jobs[job].sphere;
                 }
@@ -697,36 +772,10 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                     }
                 } else {
                     ++c_nodes;
-                    const float4* N = bvh.nodes4 + 8 * (size_t)node;
-                    // the six plane vectors in three 32-byte loads (chunks skewed by the node
-                    // index), then the near / far planes of each axis chosen by the ray's
-                    // direction signs
-                    const unsigned sk = ((unsigned)node & 3u) << 5;
-                    float4 lx, ly, lz, hx, hy, hz;
-                    ldg32(chunk_at(N, sk), lx, ly);
-                    ldg32(chunk_at(N, sk ^ 32u), lz, hx);
-                    ldg32(chunk_at(N, sk ^ 64u), hy, hz);
-                    const float4 rf = __ldg(chunk_at(N, sk ^ 96u));
-                    const float4 qx = r.nx ? hx : lx, qy = r.ny ? hy : ly, qz = r.nz ? hz : lz;
-                    const float4 fx = r.nx ? lx : hx, fy = r.ny ? ly : hy, fz = r.nz ? lz : hz;
-                    const float tmax = CLOSEST ? fminf(bt, tclip) : tclip;
                     float tc[4];
-                    const int ref[4] = {__float_as_int(rf.x), __float_as_int(rf.y), __float_as_int(rf.z), __float_as_int(rf.w)};
+                    int ref[4];
                     bool hc[4];
-    #define EXM_BOX(C, c)                                                                                          \
-        {                                                                                                          \
-            const float t0 = fmaxf(fmax3(fmaf(qx.c, r.inv.x, r.oinv.x), fmaf(qy.c, r.inv.y, r.oinv.y),                \
-                                         fmaf(qz.c, r.inv.z, r.oinv.z)), 0.0f);                                    \
-            const float t1 = fminf(fmin3(fmaf(fx.c, r.inv.x, r.oinv.x), fmaf(fy.c, r.inv.y, r.oinv.y),                \
-                                         fmaf(fz.c, r.inv.z, r.oinv.z)), tmax);                                    \
-            tc[C] = t0;                                                                                            \
-            hc[C] = t0 <= t1 && ref[C] != kEmptyChild;                                                             \
-        }
-                    EXM_BOX(0, x)
-                    EXM_BOX(1, y)
-                    EXM_BOX(2, z)
-                    EXM_BOX(3, w)
-    #undef EXM_BOX
+                    node4_test<LAYOUT>(bvh, node, r, CLOSEST ? fminf(bt, tclip) : tclip, tc, hc, ref);
                     // closest hit: continue with the nearest hit child; any hit: with the first in slot
                     // order (an unoccluded shadow ray opens every box it crosses whatever the order,
                     // so the sort is skipped); push the others
@@ -776,17 +825,17 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
     }
 }
 
-template <bool CLOSEST, bool COUNT, bool W8>
+template <bool CLOSEST, bool COUNT, int LAYOUT>
 __global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
-    trace_body<CLOSEST, COUNT, false, W8>(A, nullptr, 0, nullptr);
+    trace_body<CLOSEST, COUNT, false, LAYOUT>(A, nullptr, 0, nullptr);
 }
 
 // The batched tracer: one persistent launch over the ray queues of several relight requests
-// (whose assets all use W8 nodes or all 4-wide ones).
-template <bool CLOSEST, bool W8>
+// (whose assets all use one BVH layout).
+template <bool CLOSEST, int LAYOUT>
 __global__ void __launch_bounds__(kTraceThreads, 8) trace_batch_kernel(ShadeArgs A, const TraceJob* __restrict__ jobs,
                                                                        int njobs, uint32_t* cursor) {
-    trace_body<CLOSEST, false, true, W8>(A, jobs, njobs, cursor);
+    trace_body<CLOSEST, false, true, LAYOUT>(A, jobs, njobs, cursor);
 }
 
 // ------------------------------------------------------------------ shading (warp per pixel)
@@ -1383,11 +1432,12 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     ShadeArgs A{};
     A.V = m->V; A.F = m->F; A.UV = m->UV; A.Fuv = m->Fuv;
     A.nrm = m->nrm; A.tan = m->tan; A.fsign = m->fsign;
-    A.bvh.tris = m->width == 8 ? m->tris8 : m->tris;
+    A.bvh.tris = m->layout == EXM_BVH_8Q ? m->tris8 : m->tris;
     A.bvh.nodes4 = m->nodes4;
     A.bvh.nodes8 = m->nodes8;
+    A.bvh.nodesq = m->nodesq;
     A.bvh.sphere = m->sphere;
-    A.bvh_width = m->width;
+    A.bvh_layout = m->layout;
     A.map.data = maps; A.map.W = mapW; A.map.H = mapH; A.map.wrap_u = (p->flags & EXM_FLAG_WRAP_U) != 0;
     A.env.texel = e->texel; A.env.cdf = e->cdf; A.env.rguide = e->rguide; A.env.cguide = e->cguide;
     A.env.W = e->W; A.env.H = e->H;
@@ -1507,12 +1557,15 @@ static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const 
     const int blocks = ctx->num_sms * 8;
     time_begin(f, p, CLOSEST ? 1 : 0, s);
     const bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
-    if (A.bvh_width == 8) {
-        if (count) trace_kernel<CLOSEST, true, true><<<blocks, kTraceThreads, 0, s>>>(A);
-        else trace_kernel<CLOSEST, false, true><<<blocks, kTraceThreads, 0, s>>>(A);
+    if (A.bvh_layout == EXM_BVH_8Q) {
+        if (count) trace_kernel<CLOSEST, true, EXM_BVH_8Q><<<blocks, kTraceThreads, 0, s>>>(A);
+        else trace_kernel<CLOSEST, false, EXM_BVH_8Q><<<blocks, kTraceThreads, 0, s>>>(A);
+    } else if (A.bvh_layout == EXM_BVH_4Q) {
+        if (count) trace_kernel<CLOSEST, true, EXM_BVH_4Q><<<blocks, kTraceThreads, 0, s>>>(A);
+        else trace_kernel<CLOSEST, false, EXM_BVH_4Q><<<blocks, kTraceThreads, 0, s>>>(A);
     } else {
-        if (count) trace_kernel<CLOSEST, true, false><<<blocks, kTraceThreads, 0, s>>>(A);
-        else trace_kernel<CLOSEST, false, false><<<blocks, kTraceThreads, 0, s>>>(A);
+        if (count) trace_kernel<CLOSEST, true, EXM_BVH_4><<<blocks, kTraceThreads, 0, s>>>(A);
+        else trace_kernel<CLOSEST, false, EXM_BVH_4><<<blocks, kTraceThreads, 0, s>>>(A);
     }
     time_end(f, p, s);
     ctx->launches += 1;
@@ -1753,31 +1806,31 @@ uint64_t relight_queue_rays(int views, int W, int H, const exm_params* p) {
     return P32 * per_pixel;
 }
 
-static exm_status relight_trace_batch_width(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
-                                            int width, ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s);
+static exm_status relight_trace_batch_layout(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
+                                             int layout, ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s);
 
 exm_status relight_trace_batch(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
                                ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s) {
     if (n < 1 || n > kMaxBatch) return exm_fail(EXM_ERR_ARG, "relight batch: size");
-    // one launch for the assets with 4-wide nodes, one for those with 8-wide nodes
-    for (const int width : {4, 8}) {
-        exm_status st = relight_trace_batch_width(ctx, passes, n, closest, width, h_jobs + (width == 8 ? n : 0),
-                                                  d_jobs + (width == 8 ? n : 0), s);
+    // one launch per BVH layout among the batch's assets
+    for (int l = 0; l < kJobLayouts; ++l) {
+        exm_status st = relight_trace_batch_layout(ctx, passes, n, closest, EXM_BVH_4 + l, h_jobs + l * n,
+                                                   d_jobs + l * n, s);
         if (st != EXM_OK) return st;
     }
     return EXM_OK;
 }
 
-static exm_status relight_trace_batch_width(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
-                                            int width, ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s) {
+static exm_status relight_trace_batch_layout(exm_ctx* ctx, exm_relight_pass* const* passes, int n, bool closest,
+                                             int layout, ExmTraceJob* h_jobs, ExmTraceJob* d_jobs, cudaStream_t s) {
     int k = 0;
     uint32_t* cursor = nullptr;
     for (int i = 0; i < n; ++i) {
         const ShadeArgs& A = passes[i]->A;
         if (closest && !passes[i]->c.indirect) continue;
-        if (A.bvh_width != width) continue;
+        if (A.bvh_layout != layout) continue;
         TraceJob& j = h_jobs[k++];
-        j.nodes4 = width == 8 ? A.bvh.nodes8 : A.bvh.nodes4;
+        j.nodes4 = layout == EXM_BVH_8Q ? A.bvh.nodes8 : (layout == EXM_BVH_4Q ? A.bvh.nodesq : A.bvh.nodes4);
         j.tris = A.bvh.tris;
         j.sphere = A.bvh.sphere;
         j.rays = A.rays;
@@ -1794,12 +1847,15 @@ static exm_status relight_trace_batch_width(exm_ctx* ctx, exm_relight_pass* cons
     if (st != EXM_OK) return st;
     ShadeArgs A = passes[0]->A;
     const int blocks = ctx->num_sms * 8;
-    if (width == 8) {
-        if (closest) trace_batch_kernel<true, true><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
-        else trace_batch_kernel<false, true><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+    if (layout == EXM_BVH_8Q) {
+        if (closest) trace_batch_kernel<true, EXM_BVH_8Q><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+        else trace_batch_kernel<false, EXM_BVH_8Q><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+    } else if (layout == EXM_BVH_4Q) {
+        if (closest) trace_batch_kernel<true, EXM_BVH_4Q><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+        else trace_batch_kernel<false, EXM_BVH_4Q><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
     } else {
-        if (closest) trace_batch_kernel<true, false><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
-        else trace_batch_kernel<false, false><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+        if (closest) trace_batch_kernel<true, EXM_BVH_4><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
+        else trace_batch_kernel<false, EXM_BVH_4><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
     }
     ctx->launches += 1;
     return exm_cuda_check(cudaGetLastError(), "relight batch: trace");

@@ -1,8 +1,9 @@
-"""The 8-wide compressed BVH (child boxes quantised to 8 bits on a per-node grid, rounded
-outwards) against the 4-wide one and the oracle.  Its box tests are conservative and its
-triangle tests are the same watertight tests, so every decision -- visibility bits, secondary
-hit ids -- and hence every radiance value is bit-identical to the 4-wide tree's, and equal to
-the brute-force oracle's."""
+"""The three BVH layouts against each other and the oracle: 4-wide nodes with FP32 boxes, the
+same 4-wide tree with child boxes quantised to 8 bits per plane (64-byte nodes), and the 8-wide
+compressed tree (child boxes quantised on a per-node grid, rounded outwards).  The box tests of
+all three are conservative and their triangle tests are the same watertight tests, so every
+decision -- visibility bits, secondary hit ids -- and hence every radiance value is
+bit-identical across layouts, and equal to the brute-force oracle's."""
 import numpy as np
 import pytest
 import torch
@@ -18,9 +19,9 @@ def _dev(a, dtype=torch.float32):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def _render(sc, width, maps=None, env=None, dtype=torch.float32):
+def _render(sc, width, maps=None, env=None, dtype=torch.float32, layout=None):
     from paper_2608_24109_b300.render import Renderer
-    r = Renderer.from_scene(sc, bvh_width=width)
+    r = Renderer.from_scene(sc, bvh_width=width, bvh_layout=layout)
     M = torch.as_tensor(sc.maps if maps is None else maps).to(dtype).cuda().contiguous()
     E = _dev(sc.env if env is None else env)
     out = r.forward(M, E).clone()
@@ -30,28 +31,32 @@ def _render(sc, width, maps=None, env=None, dtype=torch.float32):
 
 @pytest.mark.parametrize("name,kw", [("geometry", {}), ("indirect", {"views": 2}), ("precision", {"views": 2}),
                                       ("tiny", {})])
-def test_widths_give_bit_identical_images(name, kw):
-    """Full-size workloads (fewer views for the larger two): the forward images of the two
-    trees are equal bit for bit, and so are the decisions behind them."""
+def test_layouts_give_bit_identical_images(name, kw):
+    """Full-size workloads (fewer views for the larger two): the forward images of the three
+    layouts are equal bit for bit, and so are the decisions behind them."""
+    from paper_2608_24109_b300 import native as N
     sc = scenes.config(name, **kw)
-    r4, out4 = _render(sc, 4)
-    r8, out8 = _render(sc, 8)
-    assert torch.equal(out4, out8)
-    # the covered-pixel lists hold the same pixels in the order the compaction wrote them
+    r4, out4 = _render(sc, None, layout=N.BVH_4)
     p4, d4, s4, h4 = r4.saved_state()
-    p8, d8, s8, h8 = r8.saved_state()
-    o4, o8 = torch.argsort(p4), torch.argsort(p8)
-    assert torch.equal(p4[o4], p8[o8])
-    assert torch.equal(d4[o4], d8[o8]) and torch.equal(s4[o4], s8[o8])
-    assert (h4 is None and h8 is None) or torch.equal(h4[o4], h8[o8])
+    o4 = torch.argsort(p4)
+    for layout in (N.BVH_4Q, N.BVH_8Q):
+        rq, outq = _render(sc, None, layout=layout)
+        assert torch.equal(out4, outq)
+        # the covered-pixel lists hold the same pixels in the order the compaction wrote them
+        pq, dq, sq, hq = rq.saved_state()
+        oq = torch.argsort(pq)
+        assert torch.equal(p4[o4], pq[oq])
+        assert torch.equal(d4[o4], dq[oq]) and torch.equal(s4[o4], sq[oq])
+        assert (h4 is None and hq is None) or torch.equal(h4[o4], hq[oq])
+        rq.close()
     r4.close()
-    r8.close()
 
 
-def test_eight_wide_decisions_equal_the_oracles():
+@pytest.mark.parametrize("layout", [2, 3])  # BVH_4Q, BVH_8Q
+def test_quantised_layout_decisions_equal_the_oracles(layout):
     sc = scenes.config("indirect", n=24, map_res=128, env_w=64, env_h=32, views=2, res=56, n_direct=40, n_bounce=6,
                        n_light=3)
-    r, out = _render(sc, 8)
+    r, out = _render(sc, None, layout=layout)
     pixels, dbits, sbits, hits = r.saved_state()
     p = pixels.cpu().numpy()
     view, rem = p // (sc.width * sc.height), p % (sc.width * sc.height)
@@ -92,11 +97,12 @@ def test_eight_wide_single_triangle_and_occluder():
     floor = scenes._finish("floor", np.array(Vf, float), np.array(Ff), np.array(UVf), np.array(Ff), maps, maps, env,
                            cam2[None], 56, 48, seed=5, n_direct=64, n_bounce=4, n_light=2)
     for sc in (one, floor):
-        r4, out4 = _render(sc, 4)
-        r8, out8 = _render(sc, 8)
-        assert torch.equal(out4, out8) and float(out8.abs().sum()) > 0
+        r4, out4 = _render(sc, None, layout=1)
+        for layout in (2, 3):
+            rq, outq = _render(sc, None, layout=layout)
+            assert torch.equal(out4, outq) and float(outq.abs().sum()) > 0
+            rq.close()
         r4.close()
-        r8.close()
 
 
 def test_eight_wide_asset_round_trip_and_cycle():
@@ -130,6 +136,105 @@ def test_eight_wide_asset_round_trip_and_cycle():
     assert e.value.code == N.EXM_ERR_TRAVERSAL_LIMIT
     # an out-of-range child base is refused at import
     nodes[0, 4] = info.n_nodes
+    with pytest.raises(N.ExmError) as e:
+        assets.import_mesh(r.ctx, info, secs)
+    assert e.value.code == N.EXM_ERR_ARG
+    for m in (good, bad):
+        N.exm_mesh_destroy(m)
+    r.close()
+
+
+def _unskew(a, n_nodes, per_node):
+    """Records of `per_node` float4 (4 or 8) in their logical order: chunk j (two float4) of node
+    q is stored at j xor (q mod 4) (128-byte nodes) or j xor (q/2 mod 2) (64-byte nodes)."""
+    a = a.reshape(n_nodes, per_node // 2, 8)
+    q = np.arange(n_nodes)
+    out = np.empty_like(a)
+    for j in range(per_node // 2):
+        pos = j ^ (q & 3) if per_node == 8 else j ^ ((q >> 1) & 1)
+        out[:, j] = a[q, pos]
+    return out.reshape(n_nodes, per_node * 4)
+
+
+def test_quantised_boxes_contain_the_fp32_boxes_with_a_step_of_margin():
+    """The same tree in both 4-wide layouts (the builds number the nodes in a different order, so
+    the nodes are paired by walking both trees from the root): each pair has the same leaf
+    references, and every decoded 8-bit child box of the quantised node contains the FP32 child
+    box with at least one grid step on every side (the margin that covers the traversal's folded
+    plane evaluation)."""
+    from paper_2608_24109_b300 import assets
+    from paper_2608_24109_b300 import native as N
+    sc = scenes.config("geometry", views=1, res=64)
+    r4, _ = _render(sc, None, layout=N.BVH_4)
+    rq, _ = _render(sc, None, layout=N.BVH_4Q)
+    i4, s4 = assets.export_mesh(r4.mesh)
+    iq, sq = assets.export_mesh(rq.mesh)
+    assert i4.node_bytes == 128 and iq.node_bytes == 64 and i4.n_nodes == iq.n_nodes
+    n = i4.n_nodes
+    f4 = _unskew(s4[4].view(np.float32), n, 8)       # lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4] ref[4] pad
+    fq = _unskew(sq[4].view(np.float32), n, 4)       # p.xyz step.x ref[4] qlo.xyz qhi.x qhi.y qhi.z step.y step.z
+    ref4 = f4[:, 24:28].view(np.int32)
+    refq = fq[:, 4:8].view(np.int32)
+    # pair the nodes: root with root, then child slot by child slot
+    pair = np.full(n, -1, np.int64)
+    pair[0] = 0
+    todo = [0]
+    while todo:
+        a = todo.pop()
+        b = pair[a]
+        ra, rb = ref4[a], refq[b]
+        assert np.array_equal(ra < 0, rb < 0) and np.array_equal(ra[ra < 0], rb[rb < 0])
+        assert np.array_equal(ra == 0x7FFFFFFF, rb == 0x7FFFFFFF)
+        for c in range(4):
+            if 0 <= ra[c] < 0x7FFFFFFF:
+                assert pair[ra[c]] == -1
+                pair[ra[c]] = rb[c]
+                todo.append(int(ra[c]))
+    assert (pair >= 0).all() and len(set(pair.tolist())) == n
+    fq = fq[pair]
+    p = fq[:, 0:3].astype(np.float64)
+    step = np.stack([fq[:, 3], fq[:, 14], fq[:, 15]], 1).astype(np.float64)
+    assert (np.log2(step) == np.round(np.log2(step))).all()   # powers of two
+    qw = fq[:, 8:14].view(np.uint32)                           # qlo.x qlo.y qlo.z qhi.x qhi.y qhi.z
+    qb = ((qw[:, :, None] >> (8 * np.arange(4))) & 0xFF).astype(np.float64)   # [node, word, child]
+    live = ref4 != 0x7FFFFFFF
+    assert np.array_equal(live, fq[:, 4:8].view(np.int32) != 0x7FFFFFFF)
+    for a in range(3):
+        lo4 = f4[:, 4 * a:4 * a + 4].astype(np.float64)
+        hi4 = f4[:, 12 + 4 * a:16 + 4 * a].astype(np.float64)
+        dlo = p[:, a:a + 1] + qb[:, a] * step[:, a:a + 1]
+        dhi = p[:, a:a + 1] + qb[:, 3 + a] * step[:, a:a + 1]
+        assert (dlo[live] <= lo4[live] - step[:, a:a + 1].repeat(4, 1)[live]).all()
+        assert (dhi[live] >= hi4[live] + step[:, a:a + 1].repeat(4, 1)[live]).all()
+        # empty slots decode to inverted boxes
+        assert (qb[:, a][~live] == 255).all() and (qb[:, 3 + a][~live] == 0).all()
+    r4.close()
+    rq.close()
+
+
+def test_quantised_four_wide_asset_round_trip_and_cycle():
+    from paper_2608_24109_b300 import assets
+    from paper_2608_24109_b300 import native as N
+    sc = scenes.config("tiny", res=24, views=1, n_direct=4)
+    r, ref = _render(sc, None, layout=N.BVH_4Q)
+    info, secs = assets.export_mesh(r.mesh)
+    assert info.node_bytes == 64
+    M = _dev(sc.maps)
+    good = assets.import_mesh(r.ctx, info, secs)
+    out = torch.empty_like(ref)
+    N.exm_render_forward(r.ctx, good, M, r.env, r.cams, r.params, r.frame, out)
+    r.sync()
+    assert torch.equal(out, ref)
+    # node 0 (unskewed: chunk 0 first): the root's node children made the root
+    refs = secs[4].view(np.int32).reshape(info.n_nodes, 16)[0, 4:8]
+    refs[(refs >= 0) & (refs != 0x7FFFFFFF)] = 0
+    bad = assets.import_mesh(r.ctx, info, secs)
+    N.exm_render_forward(r.ctx, bad, M, r.env, r.cams, r.params, r.frame, out)
+    with pytest.raises(N.ExmError) as e:
+        r.sync()
+    assert e.value.code == N.EXM_ERR_TRAVERSAL_LIMIT
+    # an out-of-range node reference, and more nodes than a tree over nf leaves has, are refused
+    refs[0] = info.n_nodes
     with pytest.raises(N.ExmError) as e:
         assets.import_mesh(r.ctx, info, secs)
     assert e.value.code == N.EXM_ERR_ARG

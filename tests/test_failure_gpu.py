@@ -61,8 +61,11 @@ def test_asset_file_round_trip_renders_bit_for_bit(tmp_path):
     r.close()
 
 
-def _nodes(secs, info):
-    return secs[4].view(np.int32).reshape(info.n_nodes, 8, 4)
+def _root_refs(secs, info):
+    """The root's four child references in an exported 4-wide node section (node 0 is stored
+    unskewed: after its six plane vectors in 128-byte nodes, after p and step.x in 64-byte ones)."""
+    words = secs[4].view(np.int32).reshape(info.n_nodes, info.node_bytes // 4)
+    return words[0, 24:28] if info.node_bytes == 128 else words[0, 4:8]
 
 
 def test_bvh_with_a_cycle_ends_at_the_traversal_cap():
@@ -78,7 +81,7 @@ def test_bvh_with_a_cycle_ends_at_the_traversal_cap():
     ref = _render_with(r, r.mesh, M).clone()
     r.sync()
     info, secs = assets.export_mesh(r.mesh)
-    refs = _nodes(secs, info)[0, 6]
+    refs = _root_refs(secs, info)
     refs[(refs >= 0) & (refs != 0x7FFFFFFF)] = 0
     bad = assets.import_mesh(r.ctx, info, secs)
     _render_with(r, bad, M)
@@ -113,16 +116,20 @@ def test_corrupt_asset_injector_gives_the_same_error():
     r.close()
 
 
-@pytest.mark.parametrize("what", ["node_ref", "leaf_ref", "face_index", "version"])
+@pytest.mark.parametrize("what", ["node_ref", "leaf_ref", "face_index", "version", "node_count"])
 def test_import_refuses_out_of_range_assets(what):
     from paper_2608_24109_b300 import assets
     from paper_2608_24109_b300 import native as N
     sc, r = _tiny()
     info, secs = assets.export_mesh(r.mesh)
     if what == "node_ref":
-        _nodes(secs, info)[0, 6, 0] = info.n_nodes + 5
+        _root_refs(secs, info)[0] = info.n_nodes + 5
     elif what == "leaf_ref":
-        _nodes(secs, info)[0, 6, 0] = ~(info.nf + 3)
+        _root_refs(secs, info)[0] = ~(info.nf + 3)
+    elif what == "node_count":   # more 4-wide nodes than a tree over nf leaves has
+        info.n_nodes = info.nf
+        secs[4] = np.zeros(info.nf * info.node_bytes, np.uint8)
+        info.bytes[4] = secs[4].size
     elif what == "face_index":
         secs[1].view(np.int32)[7] = info.nv
     else:
@@ -171,10 +178,10 @@ def test_fault_variable_is_read_from_the_environment():
 
 # ------------------------------------------------------------------ serving
 
-def _server(slots=2):
+def _server(slots=2, budget=2 << 30):
     from paper_2608_24109_b300.serve import RelightServer
     sc = scenes.config("tiny", res=48, views=1, n_direct=16)
-    srv = RelightServer(hbm_budget_bytes=2 << 30, max_slots=slots)
+    srv = RelightServer(hbm_budget_bytes=budget, max_slots=slots)
     aid = srv.add_asset(sc.V, sc.F, sc.UV, sc.Fuv, torch.as_tensor(sc.maps))
     env = torch.as_tensor(sc.env, device="cuda")
     return srv, aid, env, sc
@@ -216,20 +223,21 @@ def test_slow_request_wait_times_out_then_completes():
 
 
 def test_cancel_queued_and_in_flight_requests():
-    """One slot: the first request is launched at once, the second waits in the queue.
-    Cancelling both gives EXM_ERR_CANCELLED for each (the launched one finishes on the device,
-    its result dropped: the server has not observed its completion before the cancel); the
-    server then serves a new request normally."""
+    """One slot: the first request (768^2 pixels x 64 samples, several milliseconds of device
+    work) is launched at once, the second waits in the queue.  Cancelling both while the server
+    still reports the first in flight (its completion not yet observed) gives EXM_ERR_CANCELLED
+    for each: the launched one finishes on the device and its result is dropped.  The server
+    then serves a new request normally."""
     from paper_2608_24109_b300 import native as N
-    srv, aid, env, sc = _server(slots=1)
-    t1 = srv.submit(srv.request(aid, env, sc.cams, 48, 48, 16, seed=1))
-    assert srv.stats()["in_flight"] == 1
+    srv, aid, env, sc = _server(slots=1, budget=8 << 30)
+    t1 = srv.submit(srv.request(aid, env, sc.cams, 768, 768, 64, seed=1))
     N.exm_debug_fault(N.FAULT_SLOW, 300)
     t2 = srv.submit(srv.request(aid, env, sc.cams, 48, 48, 16, seed=2))
     N.exm_debug_fault(N.FAULT_SLOW, 0)
-    assert srv.stats()["queued"] == 1
+    st = srv.stats()
+    assert st["queued"] == 1 and st["in_flight"] == 1
+    srv.cancel(t1)   # no scheduler step between the check and the cancel
     srv.cancel(t2)
-    srv.cancel(t1)
     for t in (t1, t2):
         with pytest.raises(N.ExmError) as e:
             srv.wait(t, 30_000)

@@ -107,6 +107,34 @@ def test_visibility_buffer_bit_exact_blob():
     assert np.array_equal(keys_u64(r.visbuf()), keys)
 
 
+def _box_pixels(sc):
+    """Pixel-box sizes of the front-facing triangles as projected (float64, without snapping)."""
+    cam = sc.cams[0].astype(np.float64)
+    d = sc.V.astype(np.float64) - cam[0:3]
+    w = d @ cam[9:12]
+    sx = cam[14] + cam[12] * (d @ cam[3:6]) / w
+    sy = cam[15] - cam[13] * (d @ cam[6:9]) / w
+    X, Y = sx[sc.F], sy[sc.F]
+    area = (Y[:, 1] - Y[:, 0]) * (X[:, 2] - X[:, 0]) - (X[:, 1] - X[:, 0]) * (Y[:, 2] - Y[:, 0])
+    return ((X.max(1) - X.min(1)) * (Y.max(1) - Y.min(1)))[area > 0]
+
+
+@pytest.mark.parametrize("eye,size", [((0.0, 0.3, 1.45), (256, 192)), ((0.9, 0.25, 0.95), (97, 61)),
+                                      ((0.0, 0.0, 1.3), (640, 480))])
+def test_visibility_buffer_bit_exact_close_camera(eye, size):
+    """A camera close to the surface: many triangles have pixel boxes of more than 256 pixels,
+    which the raster hands to its warp-per-triangle kernel; the keys stay bit-exact."""
+    W, H = size
+    sc = scenes.config("tiny", n_direct=8)
+    sc.cams, sc.width, sc.height = scenes.look_at_camera(eye, W, H)[None], W, H
+    assert (_box_pixels(sc) > 400).sum() >= 20
+    r, M, E, out = gpu_forward(sc)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, W, H)
+    assert st == 0
+    assert np.array_equal(keys_u64(r.visbuf()), keys)
+    r.close()
+
+
 def test_env_distribution_total_matches():
     from paper_2608_24109_b300 import native as N
     for (w, h, sig) in [(64, 32, 1.0), (256, 128, 1.5), (13, 7, 2.0)]:
