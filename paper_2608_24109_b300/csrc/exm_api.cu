@@ -483,6 +483,7 @@ extern "C" {
 exm_status exm_render_forward(exm_ctx* c, const exm_mesh* m, const void* maps, exm_dtype dt, int mapW, int mapH,
                               const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
                               exm_frame* f, float* out_rgb, void* stream) {
+    ExmRange range("exm_render_forward");
     exm_status st = check_render(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, "exm_render_forward");
     if (st != EXM_OK) return st;
     if (!out_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_forward: out_rgb is NULL");
@@ -492,7 +493,10 @@ exm_status exm_render_forward(exm_ctx* c, const exm_mesh* m, const void* maps, e
         return exm_render_forward_halfres(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, out_rgb, s);
     st = upload_cameras(f, cams, views, s);
     if (st != EXM_OK) return st;
-    st = exm_raster_impl(c, m, f, views, s);
+    {
+        ExmRange r("raster");
+        st = exm_raster_impl(c, m, f, views, s);
+    }
     if (st != EXM_OK) return st;
     return exm_shade_forward_impl(c, m, maps, dt, mapW, mapH, e, f, p, out_rgb, s);
 }
@@ -501,6 +505,7 @@ exm_status exm_render_backward(exm_ctx* c, const exm_mesh* m, const void* maps, 
                                const exm_env* e, const exm_camera* cams, int views, const exm_params* p,
                                exm_frame* f, const float* grad_rgb, float* grad_maps, float* grad_env, float* grad_V,
                                void* stream) {
+    ExmRange range("exm_render_backward");
     exm_status st = check_render(c, m, maps, dt, mapW, mapH, e, cams, views, p, f, "exm_render_backward");
     if (st != EXM_OK) return st;
     if (!grad_rgb) return exm_fail(EXM_ERR_ARG, "exm_render_backward: grad_rgb is NULL");

@@ -495,6 +495,7 @@ __global__ void seed4_kernel(int2* in, uint32_t* n_in, uint32_t* n_nodes) {
 using namespace exm;
 
 exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
+    ExmRange range("BVH build");
     int n = m->nf;
     if (!m->codes) {
         size_t nn = (size_t)n;

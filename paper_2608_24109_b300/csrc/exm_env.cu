@@ -145,6 +145,7 @@ __global__ void env_col_guide_kernel(const uint64_t* __restrict__ cdf, int W, in
 using namespace exm;
 
 exm_status exm_env_prepare_impl(exm_env* e, const void* E, exm_dtype dt, cudaStream_t s) {
+    ExmRange range("environment distribution");
     int n = e->W * e->H;
     cudaMemsetAsync(e->wmax, 0, 4, s);
     int blocks = exm_blocks(n, 256);

@@ -7,7 +7,19 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/exmesh.h"
+
+// A named NVTX range over a scope of host code: the library's entry points and stages show up
+// as ranges in Nsight tools (and ncu can select kernels by them: --nvtx --nvtx-include).
+// Without a tool attached the calls return at once.
+struct ExmRange {
+    explicit ExmRange(const char* name) { nvtxRangePushA(name); }
+    ~ExmRange() { nvtxRangePop(); }
+    ExmRange(const ExmRange&) = delete;
+    ExmRange& operator=(const ExmRange&) = delete;
+};
 
 struct exm_ctx {
     int device = 0;

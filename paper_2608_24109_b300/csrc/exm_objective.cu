@@ -440,6 +440,7 @@ using namespace exm;
 
 exm_status exm_image_loss_impl(exm_ctx* ctx, const float* pred, const float* target, int views, int W, int H,
                                float lambda_ssim, float* loss, float* grad, cudaStream_t s) {
+    ExmRange range("image loss");
     const size_t n = (size_t)views * W * H * 3, planes = (size_t)views * 3, plane_total = planes * W * H;
     if (!ensure_acc(ctx) || !ensure(&ctx->scratch, &ctx->scratch_cap, 3 * plane_total))
         return exm_fail(EXM_ERR_OOM, "exm_image_loss: scratch");
@@ -513,6 +514,7 @@ exm_status exm_env_regularizers_impl(exm_ctx* ctx, const float* E, int W, int H,
 exm_status exm_adam_step_impl(exm_ctx* ctx, float* param, const float* grad, float* m, float* v, size_t rows,
                               int channels, float lr, float beta1, float beta2, float eps, int step, const float* lo,
                               const float* hi, cudaStream_t s) {
+    ExmRange range("Adam step");
     AdamArgs a;
     a.lr = lr;
     a.beta1 = beta1;

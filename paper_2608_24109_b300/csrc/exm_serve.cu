@@ -165,6 +165,7 @@ static exm_status slot_state(exm_server* s, Slot& sl, const exm_relight_req& r, 
 // stream instead.  Returns per request the status of its enqueueing.
 static void launch_batch(exm_server* s, Lane& lane, const std::vector<int>& slot_ids, std::vector<Pending>& reqs,
                          std::vector<exm_status>& status) {
+    ExmRange range("relight batch");
     exm_ctx* ctx = s->ctx;
     cudaStream_t st_ = lane.stream;
     const size_t n = reqs.size();

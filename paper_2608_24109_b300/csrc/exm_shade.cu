@@ -1618,6 +1618,7 @@ static ChunkPlan plan_chunks(const exm_frame* f, const exm_params* p) {
 // shadow rays of the direct samples and of the secondary hits' light samples, as bits.
 static void trace_chunk(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ChunkPlan& c, ShadeArgs& A,
                         size_t ch, cudaStream_t s) {
+    ExmRange range("chunk: ray generation and tracing");
     A.chunk_begin = (uint32_t)(ch * c.Pc);
     A.chunk_pixels = c.Pc;
     A.ctr = f->ctr + 4 * ch;
@@ -1670,16 +1671,21 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
         if (c.indirect) cudaMemsetAsync(f->hits, 0xff, P * (size_t)c.nb * sizeof(int32_t), s);
     }
     if (p->flags & EXM_FLAG_COUNT_WORK) cudaMemsetAsync(f->work, 0, 4 * sizeof(unsigned long long), s);
-    launch_surface(ctx, f, p, A, dt, false, s);
+    {
+        ExmRange r("pixel records");
+        launch_surface(ctx, f, p, A, dt, false, s);
+    }
     for (size_t ch = 0; ch < c.nchunks; ++ch) {
         trace_chunk(ctx, f, p, c, A, ch, s);
         if (c.recompute) {  // shade the chunk while its state is resident
+            ExmRange r("shade");
             A.shade_begin = A.chunk_begin;
             A.shade_end = A.chunk_begin + c.Pc;
             launch_samples<false>(ctx, f, p, A, dt, s);
         }
     }
     if (!c.recompute) {
+        ExmRange r("shade");
         A.state_base = 0;
         A.shade_begin = 0;
         A.shade_end = 0xffffffffu;
@@ -1901,6 +1907,7 @@ exm_status exm_check_backward(const exm_frame* f, const exm_mesh* m, const exm_e
 // only buffers the frame's forward pass allocated.
 static exm_status backward_core(exm_ctx* ctx, exm_frame* f, const exm_params* p, ShadeArgs& A, exm_dtype dt,
                                 cudaStream_t s) {
+    ExmRange range("adjoint");
     ChunkPlan c = plan_chunks(f, p);
     c.recompute = f->fwd_recompute;  // the forward's split, whatever the limits are now
     c.Pc = f->fwd_chunk;

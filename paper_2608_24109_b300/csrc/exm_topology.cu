@@ -690,6 +690,7 @@ exm_status exm_face_render_counts(exm_frame* f, int nf, uint32_t* counts, void* 
 exm_status exm_topology_round(exm_topology* t, const float* V, int nv, const int32_t* F, int nf, const float* UV,
                               int nuv, const int32_t* Fuv, const float* ema, const float* grad_V,
                               const uint32_t* render_counts, const exm_topology_params* p, void* stream) {
+    ExmRange range("exm_topology_round");
     if (!t || !V || !F || !UV || !Fuv || !ema || !grad_V || !render_counts || !p || nv < 3 || nf < 1 || nuv < 1)
         return exm_fail(EXM_ERR_ARG, "exm_topology_round: bad argument");
     if (p->split_percent < 0 || p->split_percent > 100 || p->max_faces < 1 || (long long)nf * 3 >= INT_MAX / 2)
