@@ -227,8 +227,9 @@ void exm_frame_destroy(exm_frame* frame);
  * default of 2^27 = 4 GiB of 32-byte rays; at most 2^27); a chunk is the pixels whose worst-case
  * ray count fits it, at least 32 pixels, so a cap below 32 pixels' rays overflows
  * (EXM_ERR_QUEUE_OVERFLOW from exm_sync).  saved_budget_bytes: bytes of per-sample state (4 per
- * direct sample, 4 per visibility word, 4 per secondary ray, per frame pixel) the frame keeps for
- * the whole frame (0: the default of 16 GiB); above it the frame works as with
+ * direct sample, 4 per secondary light sample when the indirect term is active, 4 per visibility
+ * word, 4 per secondary ray, per frame pixel) the frame keeps for the whole frame (0: the
+ * default of 16 GiB); above it the frame works as with
  * EXM_FLAG_RECOMPUTE, with chunks whose state fits the budget.  Takes effect at the next forward
  * pass; a backward pass follows the split of its forward pass. */
 exm_status exm_frame_set_limits(exm_frame* frame, uint32_t ray_cap, uint64_t saved_budget_bytes);
@@ -265,8 +266,9 @@ exm_status exm_frame_saved_state(exm_frame* frame, const uint32_t** pixels, cons
  * the visibility buffer for the backward pass.  The frame grows its wavefront buffers on the
  * first forward of a size and sample count and keeps them until destroyed: per frame pixel
  * 160 bytes (the 112-byte shading record and the backward's 48-byte adjoint sums); the
- * per-sample state -- 4 bytes per direct sample (the texel it picked), one bit per direct and
- * per secondary light sample, and 4 bytes per secondary ray -- per frame pixel, or per pixel of
+ * per-sample state -- 4 bytes per direct and per secondary light sample (the texel it picked),
+ * one bit per direct and per secondary light sample, and 4 bytes per secondary ray -- per frame
+ * pixel, or per pixel of
  * one chunk when it is recomputed (EXM_FLAG_RECOMPUTE, exm_frame_set_limits); plus one ray
  * queue of at most 2^27 rays x 32 bytes (4 GiB), sized down to the rays a chunk can produce. */
 exm_status exm_render_forward(exm_ctx* ctx, const exm_mesh* mesh, const void* maps, exm_dtype map_dtype,

@@ -332,7 +332,7 @@ exm_status exm_env_total(exm_env* e, uint64_t* Q) {
 static void frame_free(exm_frame* f) {
     void* ptrs[] = {f->visbuf, f->pixels, f->counters, f->samples, f->work, f->cams, f->XY,   f->Zq,
                     f->genv,   f->gnrm,   f->gtan,     f->bits,    f->hits, f->rays, f->ctr, f->prec,
-                    f->pacc,   f->tsel, f->tv_gbuf, f->tv_inv, f->half_img, f->half_grad, f->big_tris};
+                    f->pacc,   f->tsel, f->tv_gbuf, f->tv_inv, f->half_img, f->half_grad, f->big_tris, f->tsel2};
     for (void* p : ptrs) cudaFree(p);
     if (f->half) {
         frame_free(f->half);

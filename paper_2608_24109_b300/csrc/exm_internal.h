@@ -131,6 +131,8 @@ struct exm_frame {
     size_t pacc_cap = 0;
     uint32_t* tsel = nullptr;     // [P * Nd] texel picked by each queued direct sample
     size_t tsel_cap = 0;
+    uint32_t* tsel2 = nullptr;    // [P * Nb * Ns] texel picked by each queued secondary light sample
+    size_t tsel2_cap = 0;
     uint32_t* bits = nullptr;     // visibility bits: [P * wd] direct, then [P * ws] secondary
     size_t bits_cap = 0;
     int32_t* hits = nullptr;      // [P * Nb] secondary closest front-facing hit, -1 if none

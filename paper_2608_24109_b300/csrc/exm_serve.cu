@@ -94,12 +94,12 @@ struct exm_server {
 };
 
 // Device bytes of one frame: visibility keys and pixel list, pixel records (the 112-byte
-// shading record and the 48-byte adjoint sums), the texel of each direct sample, snapped
-// vertices, visibility bits, secondary hit ids, the ray queue of a chunk, cameras, counters,
-// the large-triangle list of the raster.
-static size_t frame_bytes(size_t P, size_t views, size_t nv, int wd, int ws, int nb, size_t ray_cap) {
-    return P * (8 + 4 + 16 * kPrec + 48) + P * (size_t)wd * 32 * 4 + views * nv * 12 + P * (size_t)(wd + ws) * 4 +
-           P * (size_t)nb * 4 + ray_cap * 32 + views * 80 + 64 + (size_t)kBigTriCap * 8;
+// shading record and the 48-byte adjoint sums), the texel of each direct sample and of each
+// secondary light sample (nbs = N_b N_s of them), snapped vertices, visibility bits, secondary
+// hit ids, the ray queue of a chunk, cameras, counters, the large-triangle list of the raster.
+static size_t frame_bytes(size_t P, size_t views, size_t nv, int wd, int ws, int nb, int nbs, size_t ray_cap) {
+    return P * (8 + 4 + 16 * kPrec + 48) + P * (size_t)wd * 32 * 4 + P * (size_t)nbs * 4 + views * nv * 12 +
+           P * (size_t)(wd + ws) * 4 + P * (size_t)nb * 4 + ray_cap * 32 + views * 80 + 64 + (size_t)kBigTriCap * 8;
 }
 
 // The queue a request's frame needs: all its rays (one chunk) when they fit a batched queue,
@@ -122,10 +122,12 @@ static size_t request_footprint(const exm_server* s, const exm_relight_req& r) {
         pd.n_bounce = 0;
         ph.n_direct = 0;
         const size_t Ph = (size_t)r.views * ((r.width + 1) / 2) * ((r.height + 1) / 2);
-        frame = frame_bytes(P, r.views, nv, wd, 0, 0, request_queue(r, pd)) +
-                frame_bytes(Ph, r.views, nv, 0, ws, r.params.n_bounce, kBatchQueueMax) + Ph * 12;
+        frame = frame_bytes(P, r.views, nv, wd, 0, 0, 0, request_queue(r, pd)) +
+                frame_bytes(Ph, r.views, nv, 0, ws, r.params.n_bounce, r.params.n_bounce * r.params.n_light,
+                            kBatchQueueMax) + Ph * 12;
     } else {
-        frame = frame_bytes(P, r.views, nv, wd, ws, ind ? r.params.n_bounce : 0, request_queue(r, r.params));
+        frame = frame_bytes(P, r.views, nv, wd, ws, ind ? r.params.n_bounce : 0,
+                            ind ? r.params.n_bounce * r.params.n_light : 0, request_queue(r, r.params));
     }
     const size_t n = (size_t)r.env_w * r.env_h;
     int rb = 1, cb = 1;

@@ -74,11 +74,12 @@ struct ShadeArgs {
     float4* prec;        // [P * kPrec] per-pixel shading record
     float* pacc;         // [P * 12] backward: per-pixel sums of the sample adjoints
     uint32_t* tsel;      // [P * Nd] texel picked by each queued direct sample (gen_direct)
+    uint32_t* tsel2;     // [P * Nb * Ns] texel picked by each queued secondary light sample (gen_seclight)
     float4* rays;        // queue: [ray_cap * 2]
     uint32_t ray_cap;
     uint32_t* ctr;       // per chunk: [0] queued, [1] fetch cursor (x2: closest, any)
     uint32_t chunk_begin, chunk_pixels;
-    // per-sample state (tsel, visibility bits, hits) holds pixels [state_base, ...): the whole
+    // per-sample state (tsel, tsel2, visibility bits, hits) holds pixels [state_base, ...): the whole
     // frame (state_base 0) or, when it is recomputed chunk by chunk, the current chunk
     uint32_t state_base;
     uint32_t shade_begin, shade_end;  // covered-pixel range of a shade launch
@@ -189,11 +190,14 @@ __device__ __forceinline__ float3 brdf_cos(float3 ns, float3 wi, float3 wo, floa
     return ci * res;
 }
 
-// Adjoint of brdf_cos for an upstream RGB gradient G3; accumulates into gns, gwo, ga, gr, gm.
-__device__ __forceinline__ void brdf_cos_adjoint(float3 ns, float3 wi, float3 wo, float3 a, float r, float m, float3 G3,
-                                                 float3& gns, float3& gwo, float3& ga, float& gr, float& gm) {
+// Adjoint of brdf_cos for an upstream RGB gradient G3; accumulates into gns, gwo, ga, gr, gm and
+// returns the value brdf_cos would (computed on the way, through reciprocals: equal to it up to
+// rounding), so the backward pass needs no separate forward evaluation.
+__device__ __forceinline__ float3 brdf_cos_adjoint(float3 ns, float3 wi, float3 wo, float3 a, float r, float m,
+                                                   float3 G3, float3& gns, float3& gwo, float3& ga, float& gr,
+                                                   float& gm) {
     float ci = dot(ns, wi), co = dot(ns, wo);
-    if (ci <= 0.0f) return;
+    if (ci <= 0.0f) return f3(0.f, 0.f, 0.f);
     float om = 1.0f - m;
     float3 fd = (om * kInvPi) * a;
     float3 res = fd;
@@ -250,6 +254,7 @@ __device__ __forceinline__ void brdf_cos_adjoint(float3 ns, float3 wi, float3 wo
     }
     gci += dot(G3, res);
     gns += gci * wi;
+    return ci * res;
 }
 
 // Material and shading normal from 8 fetched channels and the interpolated frame.
@@ -451,6 +456,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
                     const LightSample ls = light_sample(env, h, (uint32_t)s, A.nxs, A.nys);
                     if (sdot(ngy, ls.dir) > 0.0f) {
                         want |= 1u << u;
+                        A.tsel2[(size_t)(i - A.state_base) * A.Nb * A.Ns + j * A.Ns + s] = ls.texel;
                         sd[u][0][lane] = ls.dir.x; sd[u][1][lane] = ls.dir.y; sd[u][2][lane] = ls.dir.z;
                     }
                 }
@@ -492,6 +498,12 @@ constexpr uint32_t kPool = 256;
 constexpr int kRound = 24;  // node visits between refills
 
 constexpr int kTraceThreads = 128;
+// Resident tracer blocks per SM (the persistent grid is this many per SM): 9 blocks of 4 warps
+// hold the registers to 56 per thread with a few bytes of spills, and traced the 2M-triangle
+// workload 0.9% faster than 8 blocks at 64 registers; 10 blocks (48 registers) were 6% slower.
+// The batched tracer, whose lanes also carry their ray's BVH, keeps 8 blocks (64 registers).
+constexpr int kTraceBlocksPerSM = 9;
+constexpr int kTraceBatchBlocksPerSM = 8;
 
 // Byte c of a pair of words (children 0-3 in .x, 4-7 in .y) as a float: one byte permutation
 // puts it under the exponent of 2^23, and subtracting 2^23 leaves the byte's value (exact).
@@ -826,14 +838,14 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
 }
 
 template <bool CLOSEST, bool COUNT, int LAYOUT>
-__global__ void __launch_bounds__(kTraceThreads, 8) trace_kernel(ShadeArgs A) {
+__global__ void __launch_bounds__(kTraceThreads, kTraceBlocksPerSM) trace_kernel(ShadeArgs A) {
     trace_body<CLOSEST, COUNT, false, LAYOUT>(A, nullptr, 0, nullptr);
 }
 
 // The batched tracer: one persistent launch over the ray queues of several relight requests
 // (whose assets all use one BVH layout).
 template <bool CLOSEST, int LAYOUT>
-__global__ void __launch_bounds__(kTraceThreads, 8) trace_batch_kernel(ShadeArgs A, const TraceJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kTraceThreads, kTraceBatchBlocksPerSM) trace_batch_kernel(ShadeArgs A, const TraceJob* __restrict__ jobs,
                                                                        int njobs, uint32_t* cursor) {
     trace_body<CLOSEST, false, true, LAYOUT>(A, jobs, njobs, cursor);
 }
@@ -1098,13 +1110,13 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                     const float3 wi = normalize(tof(ls.dir));
                     const float w = ls.inv_pdf * invNd;
                     ++c_brdf;
-                    const float3 fc = brdf_cos(sns, wi, wo, sa, sr, sm);
                     if (!BWD) {
-                        L += w * (ls.E * fc);
+                        L += w * (ls.E * brdf_cos(sns, wi, wo, sa, sr, sm));
                     } else {
+                        const float3 fc =
+                            brdf_cos_adjoint(sns, wi, wo, sa, sr, sm, w * (g * ls.E), gns, gwo, ga, gr, gm);
                         const float3 gE = w * (g * fc);
                         atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
-                        brdf_cos_adjoint(sns, wi, wo, sa, sr, sm, w * (g * ls.E), gns, gwo, ga, gr, gm);
                     }
                 }
             }
@@ -1212,7 +1224,14 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                         const float3 fdyj = f3(hr[HF_X][hl], hr[HF_Y][hl], hr[HF_Z][hl]);
                         const float3 nsyj = f3(hr[HN_X][hl], hr[HN_Y][hl], hr[HN_Z][hl]);
                         const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
-                        const LightSample ls = light_sample(env, h2, (uint32_t)s, A.nxs, A.nys);
+                        // the texel gen_seclight's search picked (a live sample was queued, so it
+                        // was recorded), its row by one corrected FP32 quotient as for direct samples
+                        const uint32_t t = A.tsel2[si * A.Nb * A.Ns + bit];
+                        uint32_t row = (uint32_t)((float)t * invW);
+                        if (row * (uint32_t)env.W > t) --row;
+                        else if ((row + 1u) * (uint32_t)env.W <= t) ++row;
+                        LightSample ls;
+                        finish_sample(env, h2, row, t - row * (uint32_t)env.W, &ls);
                         const float3 wl = normalize(tof(ls.dir));
                         const float cs = dot(nsyj, wl);
                         if (cs <= 0.0f) continue;
@@ -1464,6 +1483,7 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     A.prec = f->prec;
     A.pacc = f->pacc;
     A.tsel = f->tsel;
+    A.tsel2 = f->tsel2;
     A.visbits = f->bits;
     A.secbits = f->bits ? f->bits + P * A.wd : nullptr;
     A.hits = f->hits;
@@ -1554,7 +1574,7 @@ static void launch_samples(exm_ctx* ctx, exm_frame* f, const exm_params* p, cons
 
 template <bool CLOSEST>
 static void launch_trace(exm_ctx* ctx, exm_frame* f, const exm_params* p, const ShadeArgs& A, cudaStream_t s) {
-    const int blocks = ctx->num_sms * 8;
+    const int blocks = ctx->num_sms * kTraceBlocksPerSM;
     time_begin(f, p, CLOSEST ? 1 : 0, s);
     const bool count = (p->flags & EXM_FLAG_COUNT_WORK) != 0;
     if (A.bvh_layout == EXM_BVH_8Q) {
@@ -1603,7 +1623,8 @@ static ChunkPlan plan_chunks(const exm_frame* f, const exm_params* p) {
     const size_t per_pixel = std::max((size_t)c.wd * 32 + (size_t)c.ws * 32, (size_t)std::max(c.nb, 1));
     const size_t P32 = (c.P + 31) & ~(size_t)31;
     size_t Pc = std::max((size_t)32, std::min(P32, (cap_max / per_pixel) & ~(size_t)31));
-    c.state_per_px = std::max((size_t)1, 4 * (size_t)p->n_direct + 4 * (size_t)(c.wd + c.ws) + 4 * (size_t)c.nb);
+    c.state_per_px = std::max((size_t)1, 4 * (size_t)p->n_direct + 4 * (size_t)(c.wd + c.ws) + 4 * (size_t)c.nb +
+                                             (c.indirect ? 4 * (size_t)p->n_bounce * p->n_light : 0));
     const uint64_t budget = f->saved_budget ? f->saved_budget : kSavedBudgetDefault;
     c.recompute = (p->flags & EXM_FLAG_RECOMPUTE) != 0 || (uint64_t)c.P * c.state_per_px > budget;
     if (c.recompute) Pc = std::max((size_t)32, std::min(Pc, (size_t)(budget / c.state_per_px) & ~(size_t)31));
@@ -1652,6 +1673,7 @@ exm_status exm_shade_forward_impl(exm_ctx* ctx, const exm_mesh* m, const void* m
     f->last_nd = -1;  // no valid saved state until this pass is enqueued
     if (!ensure(&f->prec, &f->prec_cap, P * (size_t)kPrec) || !ensure(&f->pacc, &f->pacc_cap, P * (size_t)12) ||
         (p->n_direct > 0 && !ensure(&f->tsel, &f->tsel_cap, c.Ps * (size_t)p->n_direct)) ||
+        (c.indirect && !ensure(&f->tsel2, &f->tsel2_cap, c.Ps * (size_t)p->n_bounce * p->n_light)) ||
         !ensure(&f->bits, &f->bits_cap, c.Ps * (size_t)(c.wd + c.ws)) ||
         !ensure(&f->rays, &f->rays_cap, (size_t)c.ray_cap * 2) ||
         (c.indirect && !ensure(&f->hits, &f->hits_cap, c.Ps * (size_t)c.nb)))
@@ -1734,6 +1756,7 @@ exm_status relight_pass_begin(exm_ctx* ctx, const exm_mesh* m, const void* maps,
     f->last_nd = -1;
     if (!ensure(&f->prec, &f->prec_cap, c.P * (size_t)kPrec) || !ensure(&f->pacc, &f->pacc_cap, c.P * (size_t)12) ||
         (p->n_direct > 0 && !ensure(&f->tsel, &f->tsel_cap, c.Ps * (size_t)p->n_direct)) ||
+        (c.indirect && !ensure(&f->tsel2, &f->tsel2_cap, c.Ps * (size_t)p->n_bounce * p->n_light)) ||
         !ensure(&f->bits, &f->bits_cap, c.Ps * (size_t)(c.wd + c.ws)) ||
         !ensure(&f->rays, &f->rays_cap, (size_t)c.ray_cap * 2) ||
         (c.indirect && !ensure(&f->hits, &f->hits_cap, c.Ps * (size_t)c.nb)) || !ensure(&f->ctr, &f->ctr_cap, 4))
@@ -1852,7 +1875,7 @@ static exm_status relight_trace_batch_layout(exm_ctx* ctx, exm_relight_pass* con
                                                    cudaMemcpyHostToDevice, s), "relight batch: job table");
     if (st != EXM_OK) return st;
     ShadeArgs A = passes[0]->A;
-    const int blocks = ctx->num_sms * 8;
+    const int blocks = ctx->num_sms * kTraceBatchBlocksPerSM;
     if (layout == EXM_BVH_8Q) {
         if (closest) trace_batch_kernel<true, EXM_BVH_8Q><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);
         else trace_batch_kernel<false, EXM_BVH_8Q><<<blocks, kTraceThreads, 0, s>>>(A, d_jobs, k, cursor);

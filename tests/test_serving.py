@@ -58,17 +58,21 @@ def test_same_alone_and_in_the_mix():
         t = srv.submit(srv.request(**r))
         outs, _ = _wait(srv, [t])
         alone.append(outs[t].clone())
+    from paper_2608_24109_b300 import native as N
     b0, r0 = srv.batches()
-    tickets = [srv.submit(srv.request(**r)) for r in reqs]
-    peak = srv.stats()["in_flight"]
+    # the first request is held 200 ms on the host, so the others queue behind it (FIFO) and the
+    # mix is launched as batches of several requests in flight together
+    N.exm_debug_fault(N.FAULT_SLOW, 200)
+    tickets = [srv.submit(srv.request(**reqs[0]))]
+    N.exm_debug_fault(N.FAULT_SLOW, 0)
+    tickets += [srv.submit(srv.request(**r)) for r in reqs[1:]]
     outs, lats = _wait(srv, tickets)
     for k, t in enumerate(tickets):
         assert torch.equal(outs[t], alone[k]), f"request {k} differs in the mix"
         assert outs[t].abs().sum() > 0
         assert lats[t] > 0
-    assert peak >= 2  # several requests were in flight together
     b1, r1 = srv.batches()
-    assert r1 - r0 == len(reqs) and b1 - b0 <= len(reqs)
+    assert r1 - r0 == len(reqs) and b1 - b0 < len(reqs)  # some batch held several requests
     srv.close()
 
 
