@@ -252,15 +252,17 @@ def timed_steps(args, r, N, M, E, target, stream, flush, world):
     base_flags = r.params.flags
     r.params.flags = base_flags | N.FLAG_ZERO_GRADS
 
-    def step(ev=None):
-        r.prepare_env(E)
-        r.forward(M, out=img)
+    def step(ev=None, Mx=M, Ex=E, before_loss=None):
+        r.prepare_env(Ex)
+        r.forward(Mx, out=img)
         if ev is not None:
             ev[0].record(stream)
+        if before_loss is not None:  # the previous step's results are still being copied out
+            stream.wait_event(before_loss)
         r.l1_loss(img, target, loss, grad)
         if ev is not None:
             ev[1].record(stream)
-        r.backward(M, grad, gm, gE, gV)
+        r.backward(Mx, grad, gm, gE, gV)
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -305,9 +307,15 @@ def timed_steps(args, r, N, M, E, target, stream, flush, world):
     barrier(world)
     ms = dist_max(statistics.mean(t_step), world)
 
-    # end to end through the public API: the step's inputs (maps, environment) copied in from
+    # end to end through the public API: every step's inputs (maps, environment) copied in from
     # pinned host memory and its results (loss and the gradients into maps, environment and
-    # vertices) copied back, every step
+    # vertices) copied back.  Two schedules:
+    # - serial: copy in, step, copy out, synchronise;
+    # - pipelined (the headline e2e): the inputs of step k+1 are copied into a second device buffer
+    #   on a copy stream while step k computes, and the results of step k are copied out on
+    #   another copy stream while step k+1 runs its forward pass (step k+1's loss and backward,
+    #   which overwrite the results, wait for that copy).  The time per step is the wall time of
+    #   the whole pipelined run, its first copy-in and last copy-out included, over its steps.
     e2e = None
     if not args.no_e2e:
         Mh = M.cpu().pin_memory()
@@ -327,12 +335,53 @@ def timed_steps(args, r, N, M, E, target, stream, flush, world):
             torch.cuda.synchronize()
             if k >= args.warmup:
                 te.append(time.perf_counter() - t0)
-        r.sync()
-        ems = dist_max(statistics.mean(te), world)
-        e2e = {"value": samples * world / ems, "unit": "samples/s",
+        serial = dist_max(statistics.mean(te), world)
+
+        Mb, Eb = [M, torch.empty_like(M)], [E, torch.empty_like(E)]
+        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+        def pipelined(n):
+            in_ev = [torch.cuda.Event(), torch.cuda.Event()]
+            done_ev = [torch.cuda.Event(), torch.cuda.Event()]
+            out_ev = None
+            with torch.cuda.stream(s_in):
+                Mb[0].copy_(Mh, non_blocking=True)
+                Eb[0].copy_(Eh, non_blocking=True)
+                in_ev[0].record(s_in)
+            for k in range(n):
+                a = k & 1
+                if k + 1 < n:  # prefetch the next step's inputs into the other buffer
+                    with torch.cuda.stream(s_in):
+                        if k >= 1:
+                            s_in.wait_event(done_ev[1 - a])  # step k-1 is done with that buffer
+                        Mb[1 - a].copy_(Mh, non_blocking=True)
+                        Eb[1 - a].copy_(Eh, non_blocking=True)
+                        in_ev[1 - a].record(s_in)
+                flush.zero_()
+                stream.wait_event(in_ev[a])
+                step(Mx=Mb[a], Ex=Eb[a], before_loss=out_ev)
+                done_ev[a].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(done_ev[a])
+                    for h, t in zip(hosts, outs):
+                        h.copy_(t, non_blocking=True)
+                    out_ev = torch.cuda.Event()
+                    out_ev.record(s_out)
+            torch.cuda.synchronize()
+
+        pipelined(max(args.warmup, 2))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pipelined(args.steps)
+        piped = dist_max((time.perf_counter() - t0) / args.steps, world)
+        e2e = {"value": samples * world / piped, "unit": "samples/s",
                "h2d_bytes_per_step": Mh.numel() * Mh.element_size() + Eh.numel() * Eh.element_size(),
                "d2h_bytes_per_step": sum(h.numel() * h.element_size() for h in hosts),
-               "ms_per_step": 1e3 * ems}
+               "ms_per_step": 1e3 * piped,
+               "schedule": "pipelined: step k+1's inputs copied in and step k's results copied out on two copy "
+                           "streams while the steps compute; first copy-in and last copy-out inside the timed run",
+               "serial": {"value": samples * world / serial, "ms_per_step": 1e3 * serial,
+                          "schedule": "copy in, step, copy out, synchronise, every step"}}
     r.params.flags = base_flags
     return {"ms": ms, "covered": covered, "samples": samples, "work_fwd": work_fwd, "work_bwd": work_bwd,
             "kms": kms, "clocks": ck, "launches": launches, "ms_forward": statistics.mean(t_fwd),

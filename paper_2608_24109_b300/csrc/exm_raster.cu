@@ -141,9 +141,10 @@ __global__ void raster_big_kernel(const int32_t* __restrict__ F, int nv, const i
         TriSetup t;
         if (!tri_setup(F, f, nv, XY + (size_t)c * nv, Zq + (size_t)c * nv, W, H, status, &t)) continue;
         unsigned long long* vb = visbuf + (size_t)c * W * H;
+        // the box lies inside the image (at most 16384^2 = 2^28 pixels): 32-bit indices
         const uint32_t bw = (uint32_t)(t.x1 - t.x0 + 1);
-        const uint64_t area = (uint64_t)bw * (uint32_t)(t.y1 - t.y0 + 1);
-        for (uint64_t i = lane; i < area; i += 32)
+        const uint32_t area = bw * (uint32_t)(t.y1 - t.y0 + 1);
+        for (uint32_t i = lane; i < area; i += 32)
             raster_pixel(t, f, t.x0 + (int)(i % bw), t.y0 + (int)(i / bw), W, vb);
     }
 }
