@@ -447,10 +447,10 @@ def test_guard_band_error_from_device():
 
 
 @pytest.mark.parametrize("mdt", [torch.bfloat16, torch.float16])
-def test_precision_form_sampled(mdt):
-    """2M-triangle precision workload with maps stored in BF16/FP16 and the environment in
-    FP16 (shading, accumulation and gradients in FP32): radiance on pixels sampled from the
-    256^2 centre crop of view 0 against the FP64 oracle fed the same rounded values."""
+def test_precision_form_one_view_radiance(mdt):
+    """2M-triangle precision workload, one view, with maps stored in BF16/FP16 and the environment
+    in FP16 (shading and accumulation in FP32): the primary keys and radiance on pixels sampled
+    from the 256^2 centre crop against the FP64 oracle fed the same rounded values."""
     sc = scenes.config("precision", views=1)
     Mq = torch.as_tensor(sc.maps).to(mdt)
     Eq = torch.as_tensor(sc.env).to(torch.float16)
