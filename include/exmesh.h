@@ -134,6 +134,16 @@ exm_status exm_ctx_set_bvh_layout(exm_ctx* ctx, int layout);
 /* The same by node width: 4 (EXM_BVH_4), 8 (EXM_BVH_8Q) or 0 (EXM_BVH_AUTO); EXM_BVH_WIDTH (4 or
  * 8) in the environment sets it at exm_create. */
 exm_status exm_ctx_set_bvh_width(exm_ctx* ctx, int width);
+/* How the binary tree is cut into 4-wide nodes (layouts EXM_BVH_4 and EXM_BVH_4Q) for the meshes
+ * `ctx` builds from now on: EXM_BVH_COLLAPSE_GREEDY opens the child with the largest box until a
+ * node holds four; EXM_BVH_COLLAPSE_SAH minimises the surface-area cost of the node and triangle
+ * visits by dynamic programming over the slots each subtree may take; EXM_BVH_COLLAPSE_AUTO is
+ * the library's default (EXM_BVH_COLLAPSE_SAH).  EXM_BVH_COLLAPSE (greedy or sah) in the
+ * environment sets it at exm_create.  Both render the same images bit for bit. */
+#define EXM_BVH_COLLAPSE_AUTO 0
+#define EXM_BVH_COLLAPSE_GREEDY 1
+#define EXM_BVH_COLLAPSE_SAH 2
+exm_status exm_ctx_set_bvh_collapse(exm_ctx* ctx, int mode);
 
 /* Uploads the fixed mesh-UV carrier (V*, F*, U*, Phi* of Sec. 5): V float32 [nv,3],
  * F int32 [nf,3] (counter-clockwise seen from outside), UV float32 [nuv,2] (u right,

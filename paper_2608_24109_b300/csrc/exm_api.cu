@@ -131,6 +131,10 @@ exm_status exm_create(int device, exm_ctx** out) {
     c->device = device;
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
     if (const char* w = getenv("EXM_BVH_WIDTH")) c->bvh_layout = atoi(w) == 8 ? EXM_BVH_8Q : (atoi(w) == 4 ? EXM_BVH_4 : 0);
+    if (const char* k = getenv("EXM_BVH_COLLAPSE")) {
+        const std::string v(k);
+        c->bvh_collapse = v == "greedy" ? EXM_BVH_COLLAPSE_GREEDY : (v == "sah" ? EXM_BVH_COLLAPSE_SAH : 0);
+    }
     if (const char* l = getenv("EXM_BVH_LAYOUT")) {
         const std::string v(l);
         c->bvh_layout = v == "4" ? EXM_BVH_4 : v == "4q" ? EXM_BVH_4Q : v == "8" ? EXM_BVH_8Q : c->bvh_layout;
@@ -156,6 +160,13 @@ void exm_destroy(exm_ctx* c) {
 exm_status exm_ctx_set_bvh_layout(exm_ctx* c, int layout) {
     if (!c || layout < EXM_BVH_AUTO || layout > EXM_BVH_8Q) return exm_fail(EXM_ERR_ARG, "exm_ctx_set_bvh_layout");
     c->bvh_layout = layout;
+    return EXM_OK;
+}
+
+exm_status exm_ctx_set_bvh_collapse(exm_ctx* c, int mode) {
+    if (!c || mode < EXM_BVH_COLLAPSE_AUTO || mode > EXM_BVH_COLLAPSE_SAH)
+        return exm_fail(EXM_ERR_ARG, "exm_ctx_set_bvh_collapse");
+    c->bvh_collapse = mode;
     return EXM_OK;
 }
 
@@ -189,7 +200,7 @@ static void mesh_free(exm_mesh* m) {
     void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nfix, m->tfix,
                     m->tris, m->codes, m->codes_sorted, m->ids, m->ids_sorted, m->child, m->bounds,
                     m->scene_box, m->sort_tmp, m->nodes4, m->sphere, m->frontier, m->frontier_cnt, m->nodes8,
-                    m->tris8, m->n_tris8, m->nodesq,
+                    m->tris8, m->n_tris8, m->nodesq, m->sah_cost, m->sah_code,
                     m->ploc_c, m->ploc_nn, m->ploc_flag, m->ploc_scan, m->scan_tmp};
     for (void* p : ptrs) cudaFree(p);
 }

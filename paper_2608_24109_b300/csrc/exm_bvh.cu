@@ -100,6 +100,7 @@ __global__ void init_box_kernel(uint32_t* box) {
 // the lower position and the cluster array is compacted.  Node ids are handed out from
 // n-2 downwards in scan order, so the last merge, the root, is node 0.
 constexpr int kDefaultLayout = EXM_BVH_4;  // the BVH layout of EXM_BVH_AUTO
+constexpr int kDefaultCollapse = EXM_BVH_COLLAPSE_SAH;  // the 4-wide collapse of EXM_BVH_COLLAPSE_AUTO
 constexpr int kPlocR = 16;
 constexpr int kPlocBlock = 256;
 constexpr int kPlocMaxRounds = 4096;
@@ -210,6 +211,34 @@ constexpr int kEmpty4 = 0x7fffffff;
 
 __device__ __forceinline__ int bounds_index(int n, int c) { return c < 0 ? n - 1 + ~c : c; }
 
+// Writes 4-wide node q with the given slots (binary nodes >= 0 or leaves ~k, in slot order);
+// each internal slot becomes a new node, queued on the next frontier.
+__device__ void emit4_node(int n, const int32_t* slots, int ns, const float* __restrict__ bounds, int q, int2* out,
+                           uint32_t* n_out, uint32_t* n_nodes, float4* nodes4) {
+    float v[6][4];
+    int refs[4];
+    for (int k = 0; k < 4; ++k) {
+        if (k < ns) {
+            const float* bb = bounds + 6 * (size_t)bounds_index(n, slots[k]);
+            for (int a = 0; a < 6; ++a) v[a][k] = bb[a];
+            if (slots[k] < 0) refs[k] = slots[k];
+            else {
+                const uint32_t idx = atomicAdd(n_nodes, 1u);
+                refs[k] = (int)idx;
+                const uint32_t o = atomicAdd(n_out, 1u);
+                out[o] = make_int2(slots[k], (int)idx);
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) { v[a][k] = 0.0f; v[3 + a][k] = 0.0f; }
+            refs[k] = kEmpty4;
+        }
+    }
+    for (int a = 0; a < 6; ++a) nodes4[node4_at(q, a)] = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
+    nodes4[node4_at(q, 6)] = make_float4(__int_as_float(refs[0]), __int_as_float(refs[1]), __int_as_float(refs[2]),
+                                         __int_as_float(refs[3]));
+    nodes4[node4_at(q, 7)] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
 __global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
                                  const int2* __restrict__ in, const uint32_t* __restrict__ n_in, int2* out,
                                  uint32_t* n_out, uint32_t* n_nodes, float4* nodes4) {
@@ -235,28 +264,112 @@ __global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const
         slots[pick] = child[2 * c];
         slots[ns++] = child[2 * c + 1];
     }
-    float v[6][4];
-    int refs[4];
-    for (int k = 0; k < 4; ++k) {
-        if (k < ns) {
-            const float* bb = bounds + 6 * (size_t)bounds_index(n, slots[k]);
-            for (int a = 0; a < 6; ++a) v[a][k] = bb[a];
-            if (slots[k] < 0) refs[k] = slots[k];
-            else {
-                const uint32_t idx = atomicAdd(n_nodes, 1u);
-                refs[k] = (int)idx;
-                const uint32_t o = atomicAdd(n_out, 1u);
-                out[o] = make_int2(slots[k], (int)idx);
-            }
-        } else {
-            for (int a = 0; a < 3; ++a) { v[a][k] = 0.0f; v[3 + a][k] = 0.0f; }
-            refs[k] = kEmpty4;
-        }
+    emit4_node(n, slots, ns, bounds, q, out, n_out, n_nodes, nodes4);
+}
+
+// ---- SAH collapse (EXM_BVH_COLLAPSE=sah): the binary tree cut into 4-wide nodes by dynamic
+// programming over slot counts (the collapse of Ylitie, Karras and Laine, HPG 2017, restated for
+// four slots).  C(x, i) is the least expected cost of the subtree of x when it may take up to i
+// slots of its parent node, with A(x) the surface area of x's box:
+//   leaf x:      C(x, i) = c_tri A(x)
+//   internal x:  D(x, k) = min over j = 1..k-1 of C(l, j) + C(r, k - j)   (l, r: its children)
+//                C(x, 1) = c_node A(x) + D(x, 4)                          (x becomes a 4-wide node)
+//                C(x, i) = min(C(x, 1), D(x, i)) for i = 2..4
+// The costs are evaluated bottom-up: a thread per leaf climbs towards the root, and of the two
+// threads that reach a binary node the second evaluates it.  The nodes are then emitted
+// top-down, level by level, each 4-wide node's slots read back from the recorded choices.
+// c_node / c_tri is the tracer's measured cost of a node visit against a triangle test.
+constexpr float kSahNode = 1.0f, kSahTri = 0.6f;
+
+__device__ __forceinline__ float box_area(const float* bb) {
+    const float dx = bb[3] - bb[0], dy = bb[4] - bb[1], dz = bb[5] - bb[2];
+    return dx * dy + dy * dz + dz * dx;
+}
+
+__global__ void parents_kernel(int n, const int32_t* __restrict__ child, int32_t* parent_int, int32_t* parent_leaf) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n - 1) return;
+    if (b == 0) parent_int[0] = -1;
+    for (int e = 0; e < 2; ++e) {
+        const int c = child[2 * b + e];
+        if (c >= 0) parent_int[c] = b;
+        else parent_leaf[~c] = b;
     }
-    for (int a = 0; a < 6; ++a) nodes4[node4_at(q, a)] = make_float4(v[a][0], v[a][1], v[a][2], v[a][3]);
-    nodes4[node4_at(q, 6)] = make_float4(__int_as_float(refs[0]), __int_as_float(refs[1]), __int_as_float(refs[2]),
-                                         __int_as_float(refs[3]));
-    nodes4[node4_at(q, 7)] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// C(c, i) of a child: a leaf's from its box, an internal node's from the table (written by
+// another thread before its release; read through L2).
+__device__ __forceinline__ float child_cost(int n, int c, int i, const float* __restrict__ bounds, const float4* cost) {
+    if (c < 0) return kSahTri * box_area(bounds + 6 * (size_t)(n - 1 + ~c));
+    const float4 v = __ldcg(cost + c);
+    return i == 1 ? v.x : (i == 2 ? v.y : (i == 3 ? v.z : v.w));
+}
+
+// code[x]: bits 2(k-2)..2(k-2)+1 hold j - 1 of the best split of D(x, k), k = 2..4; bit 6 + i - 2
+// is set when C(x, i) = C(x, 1) (x kept as a node with i slots available), i = 2..4.
+__global__ void sah_cost_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
+                                const int32_t* __restrict__ parent_int, const int32_t* __restrict__ parent_leaf,
+                                uint32_t* cnt, float4* cost, uint32_t* code) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    int b = parent_leaf[k];
+    while (b >= 0) {
+        __threadfence();                                  // release this thread's last node
+        if (atomicAdd(cnt + b, 1u) == 0u) return;         // the other child is not evaluated yet
+        __threadfence();                                  // acquire the other child's
+        const int l = child[2 * b], r = child[2 * b + 1];
+        float cl[5], cr[5];
+        for (int i = 1; i <= 4; ++i) {
+            cl[i] = child_cost(n, l, i, bounds, cost);
+            cr[i] = child_cost(n, r, i, bounds, cost);
+        }
+        float D[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        int J[5] = {1, 1, 1, 1, 1};
+        for (int kk = 2; kk <= 4; ++kk) {
+            D[kk] = INFINITY;
+            for (int j = 1; j < kk; ++j) {
+                const float v = cl[j] + cr[kk - j];
+                if (v < D[kk]) { D[kk] = v; J[kk] = j; }
+            }
+        }
+        const float c1 = kSahNode * box_area(bounds + 6 * (size_t)b) + D[4];
+        float C[5];
+        C[1] = c1;
+        uint32_t cd = (uint32_t)(J[2] - 1) | ((uint32_t)(J[3] - 1) << 2) | ((uint32_t)(J[4] - 1) << 4);
+        for (int i = 2; i <= 4; ++i) {
+            if (c1 <= D[i]) { C[i] = c1; cd |= 1u << (6 + i - 2); }
+            else C[i] = D[i];
+        }
+        cost[b] = make_float4(C[1], C[2], C[3], C[4]);
+        code[b] = cd;
+        b = parent_int[b];
+    }
+}
+
+__global__ void collapse4_sah_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
+                                     const uint32_t* __restrict__ code, const int2* __restrict__ in,
+                                     const uint32_t* __restrict__ n_in, int2* out, uint32_t* n_out, uint32_t* n_nodes,
+                                     float4* nodes4) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *n_in) return;
+    const int b = in[t].x, q = in[t].y;
+    // the slots of D(b, 4): a stack of (subtree, slots it may take), at most 4 entries since
+    // every entry takes at least one of the 4 slots
+    int sx[4], si[4], sp = 0;
+    const int j4 = (int)((code[b] >> 4) & 3u) + 1;
+    sx[sp] = child[2 * b + 1]; si[sp++] = 4 - j4;
+    sx[sp] = child[2 * b];     si[sp++] = j4;
+    int slots[4];
+    int ns = 0;
+    while (sp > 0 && ns < 4) {
+        --sp;
+        const int x = sx[sp], i = si[sp];
+        if (x < 0 || i == 1 || ((code[x] >> (6 + i - 2)) & 1u)) { slots[ns++] = x; continue; }
+        const int j = (int)((code[x] >> (2 * (i - 2))) & 3u) + 1;
+        sx[sp] = child[2 * x + 1]; si[sp++] = i - j;
+        sx[sp] = child[2 * x];     si[sp++] = j;
+    }
+    emit4_node(n, slots, ns, bounds, q, out, n_out, n_nodes, nodes4);
 }
 
 // ---- 8-wide compressed nodes (the node format of Ylitie, Karras and Laine, "Efficient
@@ -599,7 +712,23 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
         sphere_radius_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(m->tris, n, m->sphere);
         return exm_cuda_check(cudaGetLastError(), "BVH build launch");
     }
-    // collapse to 4-wide nodes, level by level (the frontier size is read back per level)
+    // collapse to 4-wide nodes, level by level (the frontier size is read back per level): by the
+    // SAH dynamic programme or by opening the largest child box (EXM_BVH_COLLAPSE)
+    const bool sah = (m->ctx->bvh_collapse ? m->ctx->bvh_collapse : kDefaultCollapse) == EXM_BVH_COLLAPSE_SAH;
+    if (sah && n > 1) {
+        if (!m->sah_cost && (exm_malloc((void**)&m->sah_cost, (size_t)(n - 1) * sizeof(float4)) != cudaSuccess ||
+                             exm_malloc((void**)&m->sah_code, (size_t)(n - 1) * sizeof(uint32_t)) != cudaSuccess))
+            return exm_fail(EXM_ERR_OOM, "BVH buffers (SAH collapse)");
+        // the clustering's scratch is free now: parents of internal nodes and leaves, and one
+        // arrival counter per internal node
+        int32_t* parent_int = m->ploc_c;
+        uint32_t* arrivals = reinterpret_cast<uint32_t*>(m->ploc_c + n);
+        int32_t* parent_leaf = m->ploc_nn;
+        parents_kernel<<<exm_blocks(n - 1, 256), 256, 0, s>>>(n, m->child, parent_int, parent_leaf);
+        cudaMemsetAsync(arrivals, 0, (size_t)(n - 1) * sizeof(uint32_t), s);
+        sah_cost_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(n, m->child, m->bounds, parent_int, parent_leaf, arrivals,
+                                                           m->sah_cost, m->sah_code);
+    }
     if (n == 1) {
         single4_kernel<<<1, 1, 0, s>>>(m->bounds, m->nodes4);
     } else {
@@ -614,8 +743,12 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
             if (3 * (level + 1) > kStackSize4)
                 return exm_fail(EXM_ERR_TRAVERSAL_LIMIT, "BVH deeper than the traversal stack allows");
             cudaMemsetAsync(cnt + 1, 0, 4, s);
-            collapse4_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, fin, cnt, fout, cnt + 1,
-                                                                  cnt + 2, m->nodes4);
+            if (sah)
+                collapse4_sah_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, m->sah_code, fin,
+                                                                          cnt, fout, cnt + 1, cnt + 2, m->nodes4);
+            else
+                collapse4_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, fin, cnt, fout, cnt + 1,
+                                                                      cnt + 2, m->nodes4);
             cudaMemcpyAsync(cnt, cnt + 1, 4, cudaMemcpyDeviceToDevice, s);
             if (cudaMemcpyAsync(&n_in, cnt + 1, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
                 cudaStreamSynchronize(s) != cudaSuccess)

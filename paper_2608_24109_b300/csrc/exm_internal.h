@@ -25,6 +25,7 @@ struct exm_ctx {
     int device = 0;
     int num_sms = 0;
     int bvh_layout = 0;            // BVH layout of new meshes: EXM_BVH_4 / _4Q / _8Q, 0 = the default
+    int bvh_collapse = 0;          // 4-wide collapse: EXM_BVH_COLLAPSE_GREEDY / _SAH, 0 = the default
     uint32_t* d_status = nullptr;  // latched device error bits
     unsigned long long launches = 0;  // kernels launched by the library on this context
     unsigned long long* d_acc = nullptr;  // 64-bit fixed-point accumulators of the objective calls
@@ -59,6 +60,8 @@ struct exm_mesh {
     uint32_t n_nodes = 0;      // nodes of the BVH in use (in nodes4, nodesq or nodes8)
     int layout = EXM_BVH_4;    // BVH in use: EXM_BVH_4 (nodes4, tris), _4Q (nodesq, tris), _8Q (nodes8, tris8)
     float4* nodesq = nullptr;  // [n_nodes * 4] 4-wide nodes with quantised child boxes
+    float4* sah_cost = nullptr;   // [nf - 1] SAH collapse: C(x, 1..4) per binary node (exm_bvh.cu)
+    uint32_t* sah_code = nullptr; // [nf - 1] SAH collapse: the choices behind them
     float4* nodes8 = nullptr;  // [n_nodes * 5] 8-wide compressed nodes
     float4* tris8 = nullptr;   // [nf * 4] triangle records in the 8-wide nodes' order
     uint32_t* n_tris8 = nullptr;

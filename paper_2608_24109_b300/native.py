@@ -28,6 +28,7 @@ EXM_ERR_CANCELLED = -9
 FAULT_ALLOC, FAULT_ADMIT, FAULT_SLOW, FAULT_CANCEL, FAULT_CORRUPT = 1, 2, 3, 4, 5
 ASSET_VERSION = 3
 BVH_AUTO, BVH_4, BVH_4Q, BVH_8Q = 0, 1, 2, 3
+BVH_COLLAPSE_AUTO, BVH_COLLAPSE_GREEDY, BVH_COLLAPSE_SAH = 0, 1, 2
 ASSET_SECTIONS = 7
 
 EXM_F32, EXM_BF16, EXM_F16 = 0, 1, 2
@@ -42,7 +43,7 @@ FLAG_RECOMPUTE = 128
 
 EXPORTS = [
     "exm_create", "exm_destroy", "exm_last_error", "exm_sync", "exm_debug_fault", "exm_ctx_set_bvh_width",
-    "exm_ctx_set_bvh_layout",
+    "exm_ctx_set_bvh_layout", "exm_ctx_set_bvh_collapse",
     "exm_mesh_create", "exm_mesh_update_vertices", "exm_bvh_build", "exm_mesh_destroy", "exm_mesh_frames",
     "exm_mesh_export_info", "exm_mesh_export", "exm_mesh_import",
     "exm_env_create", "exm_env_prepare", "exm_env_destroy", "exm_env_total",
@@ -110,6 +111,7 @@ def lib():
         "exm_debug_fault": ([I, ctypes.c_uint32], I),
         "exm_ctx_set_bvh_width": ([P, I], I),
         "exm_ctx_set_bvh_layout": ([P, I], I),
+        "exm_ctx_set_bvh_collapse": ([P, I], I),
         "exm_mesh_export_info": ([P, ctypes.POINTER(AssetInfo)], I),
         "exm_mesh_export": ([P, ctypes.POINTER(ctypes.c_void_p * ASSET_SECTIONS), P], I),
         "exm_mesh_import": ([P, ctypes.POINTER(AssetInfo), ctypes.POINTER(ctypes.c_void_p * ASSET_SECTIONS), P, PP], I),
@@ -218,6 +220,10 @@ def exm_ctx_set_bvh_width(ctx, width):
 
 def exm_ctx_set_bvh_layout(ctx, layout):
     return check(lib().exm_ctx_set_bvh_layout(ctx, int(layout)))
+
+
+def exm_ctx_set_bvh_collapse(ctx, mode):
+    return check(lib().exm_ctx_set_bvh_collapse(ctx, int(mode)))
 
 
 def exm_debug_fault(kind, count):

@@ -16,7 +16,7 @@ class Renderer:
 
     def __init__(self, V, F, UV, Fuv, env_w, env_h, cams, width, height, n_direct, n_bounce=0, n_light=0,
                  lambda_ind=1.0, seed=0, wrap_u=False, metallic=True, secondary_material=True,
-                 half_res_indirect=False, bvh_width=None, bvh_layout=None, device=0):
+                 half_res_indirect=False, bvh_width=None, bvh_layout=None, bvh_collapse=None, device=0):
         self.device = torch.device("cuda", device)
         dev = self.device
         self.V = torch.as_tensor(np.asarray(V), dtype=torch.float32, device=dev).contiguous()
@@ -36,6 +36,8 @@ class Renderer:
             N.exm_ctx_set_bvh_width(self.ctx, bvh_width)
         if bvh_layout is not None:
             N.exm_ctx_set_bvh_layout(self.ctx, bvh_layout)
+        if bvh_collapse is not None:
+            N.exm_ctx_set_bvh_collapse(self.ctx, bvh_collapse)
         self.mesh = N.exm_mesh_create(self.ctx, self.V, self.F, self.UV, self.Fuv)
         self.env = N.exm_env_create(self.ctx, env_w, env_h)
         self.frame = N.exm_frame_create(self.ctx, self.views, width, height)

@@ -19,9 +19,9 @@ def _dev(a, dtype=torch.float32):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def _render(sc, width, maps=None, env=None, dtype=torch.float32, layout=None):
+def _render(sc, width, maps=None, env=None, dtype=torch.float32, layout=None, collapse=None):
     from paper_2608_24109_b300.render import Renderer
-    r = Renderer.from_scene(sc, bvh_width=width, bvh_layout=layout)
+    r = Renderer.from_scene(sc, bvh_width=width, bvh_layout=layout, bvh_collapse=collapse)
     M = torch.as_tensor(sc.maps if maps is None else maps).to(dtype).cuda().contiguous()
     E = _dev(sc.env if env is None else env)
     out = r.forward(M, E).clone()
@@ -241,3 +241,36 @@ def test_quantised_four_wide_asset_round_trip_and_cycle():
     for m in (good, bad):
         N.exm_mesh_destroy(m)
     r.close()
+
+
+@pytest.mark.parametrize("name,kw", [("geometry", {"views": 2}), ("indirect", {"views": 1}), ("tiny", {})])
+def test_sah_and_greedy_collapses_render_the_same_images(name, kw):
+    """The SAH and the greedy 4-wide collapse of the same binary tree: the same decisions and
+    images bit for bit; both trees pass the import checks (every reference in range), and the
+    SAH one is not worse by its own cost measure (node visits plus 0.6 triangle tests, counted
+    over the frame's rays), up to 2%."""
+    from paper_2608_24109_b300 import assets
+    from paper_2608_24109_b300 import native as N
+    sc = scenes.config(name, **kw)
+    outs, work = [], []
+    for mode in (N.BVH_COLLAPSE_GREEDY, N.BVH_COLLAPSE_SAH):
+        r, out = _render(sc, None, layout=N.BVH_4, collapse=mode)
+        info, secs = assets.export_mesh(r.mesh)
+        m2 = assets.import_mesh(r.ctx, info, secs)
+        N.exm_mesh_destroy(m2)
+        # a tree: every node but the root referenced once, every triangle record once
+        refs = _unskew(secs[4].view(np.float32), info.n_nodes, 8)[:, 24:28].view(np.int32).ravel()
+        refs = refs[refs != 0x7FFFFFFF]
+        inner, leaves = refs[refs >= 0], ~refs[refs < 0]
+        assert np.array_equal(np.sort(inner), np.arange(1, info.n_nodes))
+        assert np.array_equal(np.sort(leaves), np.arange(info.nf))
+        r.params.flags |= N.FLAG_COUNT_WORK
+        M = torch.as_tensor(sc.maps).cuda().contiguous()
+        r.forward(M, _dev(sc.env))
+        r.sync()
+        work.append(N.exm_frame_work(r.frame))
+        outs.append(out)
+        r.close()
+    assert torch.equal(outs[0], outs[1])
+    cost_g, cost_s = (w[0] + 0.6 * w[1] for w in work)  # node visits + c_tri / c_node x triangle tests
+    assert cost_s <= cost_g * 1.02
