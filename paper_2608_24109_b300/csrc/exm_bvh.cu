@@ -278,7 +278,9 @@ __global__ void collapse4_kernel(int n, const int32_t* __restrict__ child, const
 // The costs are evaluated bottom-up: a thread per leaf climbs towards the root, and of the two
 // threads that reach a binary node the second evaluates it.  The nodes are then emitted
 // top-down, level by level, each 4-wide node's slots read back from the recorded choices.
-// c_node / c_tri is the tracer's measured cost of a node visit against a triangle test.
+// With one triangle per leaf the triangle term is the same for every collapse (each triangle is
+// tested when its leaf box is hit), so the programme minimises the nodes' summed surface area;
+// c_tri is kept for the cost's meaning.
 constexpr float kSahNode = 1.0f, kSahTri = 0.6f;
 
 __device__ __forceinline__ float box_area(const float* bb) {
