@@ -632,6 +632,9 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                                            uint32_t* batch_cursor) {
     constexpr bool W8 = LAYOUT == EXM_BVH_8Q;
     int stack[W8 ? kStackSize8 : kStackSize4];
+    // closest hit, 4-wide: the entry distance of each stacked box, so that a pop skips the boxes
+    // that begin beyond the nearest hit found since the push without loading them
+
     __shared__ uint32_t s_pool_end[BATCH ? kMaxBatch : 1];  // BATCH: pools of queues 0..j
     __shared__ uint32_t s_count[BATCH ? kMaxBatch : 1];     // BATCH: rays of queue j
     uint32_t n = 0;          // single queue: its rays
@@ -788,26 +791,34 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                     int ref[4];
                     bool hc[4];
                     node4_test<LAYOUT>(bvh, node, r, CLOSEST ? fminf(bt, tclip) : tclip, tc, hc, ref);
-                    // closest hit: continue with the nearest hit child; any hit: with the first in slot
-                    // order (an unoccluded shadow ray opens every box it crosses whatever the order,
-                    // so the sort is skipped); push the others
-                    int nc = -1;
+                    // a node pushes at most 3 children; the build keeps 3 entries per level within the stack
+                    if (sp > kStackSize4 - 3) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
                     if (CLOSEST) {
+                        // continue with the nearest hit child; push the others (storing their
+                        // entry distances to skip boxes beyond the nearest hit at pop time, or
+                        // pushing them farthest first, cost more than they saved: the secondary
+                        // rays mostly leave the mesh)
+                        int nc = -1;
                         float tn = INFINITY;
     #pragma unroll
                         for (int c = 0; c < 4; ++c)
                             if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
+    #pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (hc[c] && c != nc) stack[sp++] = ref[c];
+                        if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
                     } else {
+                        // any hit: continue with the first hit child in slot order (an unoccluded
+                        // shadow ray opens every box it crosses whatever the order, so no sort)
+                        int nc = -1;
     #pragma unroll
                         for (int c = 3; c >= 0; --c)
                             if (hc[c]) nc = c;
-                    }
-                    // a node pushes at most 3 children; the build keeps 3 entries per level within the stack
-                    if (sp > kStackSize4 - 3) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
     #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (hc[c] && c != nc) stack[sp++] = ref[c];
-                    if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
+                        for (int c = 0; c < 4; ++c)
+                            if (hc[c] && c != nc) stack[sp++] = ref[c];
+                        if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
+                    }
                 }
                 if (next == INT_MIN) {
                     if (sp == 0) { done = true; break; }
