@@ -135,6 +135,37 @@ def test_visibility_buffer_bit_exact_close_camera(eye, size):
     r.close()
 
 
+def test_visibility_buffer_bit_exact_when_the_large_triangle_list_is_full():
+    """600,000 front-facing triangles, over 300,000 of them with pixel boxes of several hundred
+    pixels: more than the raster's list of 2^18 large triangles holds.  The overflow is
+    rasterised by the triangles' own threads, and the keys stay bit-exact with the oracle."""
+    rng = np.random.default_rng(21)
+    W = H = 64
+    K = 600_000
+    cam = scenes.look_at_camera((0.0, 0.0, 3.0), W, H)
+    c = rng.uniform(-0.9, 0.9, (K, 1, 3)) * np.array([1.0, 1.0, 0.5])
+    V = (c + rng.uniform(-0.8, 0.8, (K, 3, 3)) * np.array([1.0, 1.0, 0.2])).reshape(-1, 3)
+    F = np.arange(3 * K).reshape(K, 3)
+    sc = scenes._finish("overlap", V, F, rng.uniform(0.0, 1.0, (3 * K, 2)), F, scenes.material_maps(rng, 32),
+                        scenes.material_maps(rng, 32), scenes.env_map(rng, 32, 16, 1.0), cam[None], W, H, seed=3,
+                        n_direct=4)
+    # wind every triangle counter-clockwise on screen (y down), so that none is culled
+    d = sc.V.astype(np.float64) - cam[0:3]
+    w = d @ cam[9:12]
+    X = (cam[14] + cam[12] * (d @ cam[3:6]) / w)[sc.F]
+    Y = (cam[15] - cam[13] * (d @ cam[6:9]) / w)[sc.F]
+    a2 = (Y[:, 1] - Y[:, 0]) * (X[:, 2] - X[:, 0]) - (X[:, 1] - X[:, 0]) * (Y[:, 2] - Y[:, 0])
+    flip = a2 < 0
+    sc.F[flip] = sc.F[flip][:, [0, 2, 1]]
+    box = (np.minimum(X.max(1), W) - np.maximum(X.min(1), 0)) * (np.minimum(Y.max(1), H) - np.maximum(Y.min(1), 0))
+    assert (box > 300).sum() > (1 << 18) + 1000
+    r, M, E, out = gpu_forward(sc)
+    st, keys = oracle.raster_full(sc.V, sc.F, sc.cams, W, H)
+    assert st == 0
+    assert np.array_equal(keys_u64(r.visbuf()), keys)
+    r.close()
+
+
 def test_env_distribution_total_matches():
     from paper_2608_24109_b300 import native as N
     for (w, h, sig) in [(64, 32, 1.0), (256, 128, 1.5), (13, 7, 2.0)]:
