@@ -170,15 +170,15 @@ exm_status exm_mesh_frames(const exm_mesh* mesh, const float** normals, const fl
  * the original face id in the first .w, then padding to 64 bytes) and its bounding sphere (float4
  * centre, R^2).  Triangle record k holds its two 32-byte halves swapped when bit 1 of k is set.
  * A node of node_bytes 128 is 4-wide: child boxes lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4]
- * hi.z[4], then four int32 child references (>= 0 a node, < 0 the triangle record ~k,
- * 0x7fffffff an empty slot), padded to 128 bytes; node q stores its 32-byte quarter j (j = 0..3
+ * hi.z[4], then four int32 child references (>= 0 a node; < 0 a leaf ~(k | (c - 1) << 28) of the
+ * c = 1..4 consecutive triangle records from k; 0x7fffffff an empty slot), padded to 128 bytes; node q stores its 32-byte quarter j (j = 0..3
  * in that order) at quarter j xor (q mod 4) of its 128 bytes (node 0 as listed).
  * A node of node_bytes 80 is 8-wide compressed: float origin p.xyz and the biased exponents e of
  * the per-axis grid steps 2^(e-127) in bytes 0-2 of word 3; then uint32 child_base, tri_base and
  * ni | nt << 8; then the child boxes quantised on that grid, qlo.x[8] qlo.y[8] qlo.z[8] qhi.x[8]
  * qhi.y[8] qhi.z[8] (bytes; plane = p + q 2^(e-127)): slots 0..ni-1 are the nodes child_base + c,
  * slots ni..ni+nt-1 the triangle records tri_base + c - ni. */
-#define EXM_ASSET_VERSION 3
+#define EXM_ASSET_VERSION 4
 #define EXM_ASSET_SECTIONS 7
 typedef struct {
     uint32_t version;    /* EXM_ASSET_VERSION */

@@ -200,7 +200,7 @@ static void mesh_free(exm_mesh* m) {
     void* ptrs[] = {m->V, m->F, m->UV, m->Fuv, m->nacc, m->nrm, m->tacc, m->tan, m->fsign, m->nfix, m->tfix,
                     m->tris, m->codes, m->codes_sorted, m->ids, m->ids_sorted, m->child, m->bounds,
                     m->scene_box, m->sort_tmp, m->nodes4, m->sphere, m->frontier, m->frontier_cnt, m->nodes8,
-                    m->tris8, m->n_tris8, m->nodesq, m->sah_cost, m->sah_code,
+                    m->tris8, m->n_tris8, m->nodesq, m->sah_cost, m->sah_code, m->sah_span,
                     m->ploc_c, m->ploc_nn, m->ploc_flag, m->ploc_scan, m->scan_tmp};
     for (void* p : ptrs) cudaFree(p);
 }

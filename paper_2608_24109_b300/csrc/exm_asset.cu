@@ -40,7 +40,11 @@ __global__ void asset_check_kernel(const int32_t* __restrict__ F, const int32_t*
         const int ref[4] = {__float_as_int(r.x), __float_as_int(r.y), __float_as_int(r.z), __float_as_int(r.w)};
         for (int k = 0; k < 4; ++k) {
             const int c = ref[k];
-            const bool ok = c == kEmptyRef || (c >= 0 && (uint32_t)c < n_nodes) || (c < 0 && ~c < nf);
+            // a leaf: ~(k | (count - 1) << kLeafCountShift), records k .. k + count - 1
+            const uint32_t lt = ~(uint32_t)c;
+            const uint32_t k0 = lt & ((1u << kLeafCountShift) - 1u), cntl = (lt >> kLeafCountShift) + 1u;
+            const bool ok = c == kEmptyRef || (c >= 0 && (uint32_t)c < n_nodes) ||
+                            (c < 0 && cntl <= (uint32_t)kMaxLeafTris && (uint64_t)k0 + cntl <= (uint64_t)nf);
             if (!ok) b |= 2u;
         }
     }

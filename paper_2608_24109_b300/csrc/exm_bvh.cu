@@ -208,13 +208,16 @@ __global__ void ploc_merge_kernel(int n, int m, int id_top, const int32_t* __res
 // whose candidates are all leaves keeps fewer).  128-byte node: child boxes as lo.x[4] lo.y[4] lo.z[4] hi.x[4] hi.y[4] hi.z[4],
 // then the four child references (>= 0: node, < 0: leaf ~k, kEmpty: unused slot).
 constexpr int kEmpty4 = 0x7fffffff;
+constexpr uint32_t kSahLeafBit = 1u << 9;  // sah_code: the binary node is cut as one leaf
 
 __device__ __forceinline__ int bounds_index(int n, int c) { return c < 0 ? n - 1 + ~c : c; }
 
 // Writes 4-wide node q with the given slots (binary nodes >= 0 or leaves ~k, in slot order);
-// each internal slot becomes a new node, queued on the next frontier.
+// each internal slot becomes a new node, queued on the next frontier, unless the SAH collapse
+// made it a leaf of several triangles (`leaf_span` non-null: its first record and count).
 __device__ void emit4_node(int n, const int32_t* slots, int ns, const float* __restrict__ bounds, int q, int2* out,
-                           uint32_t* n_out, uint32_t* n_nodes, float4* nodes4) {
+                           uint32_t* n_out, uint32_t* n_nodes, float4* nodes4, const uint32_t* __restrict__ code = nullptr,
+                           const int2* __restrict__ leaf_span = nullptr) {
     float v[6][4];
     int refs[4];
     for (int k = 0; k < 4; ++k) {
@@ -222,7 +225,10 @@ __device__ void emit4_node(int n, const int32_t* slots, int ns, const float* __r
             const float* bb = bounds + 6 * (size_t)bounds_index(n, slots[k]);
             for (int a = 0; a < 6; ++a) v[a][k] = bb[a];
             if (slots[k] < 0) refs[k] = slots[k];
-            else {
+            else if (leaf_span && (code[slots[k]] & kSahLeafBit)) {
+                const int2 sp = leaf_span[slots[k]];  // first triangle record, triangles
+                refs[k] = ~(sp.x | ((sp.y - 1) << kLeafCountShift));
+            } else {
                 const uint32_t idx = atomicAdd(n_nodes, 1u);
                 refs[k] = (int)idx;
                 const uint32_t o = atomicAdd(n_out, 1u);
@@ -308,10 +314,15 @@ __device__ __forceinline__ float child_cost(int n, int c, int i, const float* __
 }
 
 // code[x]: bits 2(k-2)..2(k-2)+1 hold j - 1 of the best split of D(x, k), k = 2..4; bit 6 + i - 2
-// is set when C(x, i) = C(x, 1) (x kept as a node with i slots available), i = 2..4.
+// is set when C(x, i) = C(x, 1) (x kept as one slot with i slots available), i = 2..4; bit 9
+// (kSahLeafBit) when that one slot is a leaf of x's triangles rather than a 4-wide node.
+// span[x]: x's first leaf (its triangle record, in leaf order) and leaf count, -1 for the first
+// when x's leaves are not consecutive records.  A leaf of several triangles costs c_tri n A(x):
+// all its triangles are tested when its box is hit.  It is allowed for up to kMaxLeafTris
+// consecutive records, not at the root.
 __global__ void sah_cost_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
                                 const int32_t* __restrict__ parent_int, const int32_t* __restrict__ parent_leaf,
-                                uint32_t* cnt, float4* cost, uint32_t* code) {
+                                uint32_t* cnt, float4* cost, uint32_t* code, int2* span) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     int b = parent_leaf[k];
@@ -325,6 +336,15 @@ __global__ void sah_cost_kernel(int n, const int32_t* __restrict__ child, const 
             cl[i] = child_cost(n, l, i, bounds, cost);
             cr[i] = child_cost(n, r, i, bounds, cost);
         }
+        const int2 sl = l < 0 ? make_int2(~l, 1) : __ldcg(span + l);
+        const int2 sr = r < 0 ? make_int2(~r, 1) : __ldcg(span + r);
+        // consecutive records when both halves are and they abut (in either order)
+        int first = -1;
+        if (sl.x >= 0 && sr.x >= 0) {
+            if (sl.x + sl.y == sr.x) first = sl.x;
+            else if (sr.x + sr.y == sl.x) first = sr.x;
+        }
+        const int leaves = sl.y + sr.y;
         float D[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
         int J[5] = {1, 1, 1, 1, 1};
         for (int kk = 2; kk <= 4; ++kk) {
@@ -334,24 +354,30 @@ __global__ void sah_cost_kernel(int n, const int32_t* __restrict__ child, const 
                 if (v < D[kk]) { D[kk] = v; J[kk] = j; }
             }
         }
-        const float c1 = kSahNode * box_area(bounds + 6 * (size_t)b) + D[4];
+        const float A = box_area(bounds + 6 * (size_t)b);
+        float c1 = kSahNode * A + D[4];
+        uint32_t cd = (uint32_t)(J[2] - 1) | ((uint32_t)(J[3] - 1) << 2) | ((uint32_t)(J[4] - 1) << 4);
+        if (b != 0 && first >= 0 && leaves <= kMaxLeafTris) {
+            const float cleaf = kSahTri * (float)leaves * A;
+            if (cleaf < c1) { c1 = cleaf; cd |= kSahLeafBit; }
+        }
         float C[5];
         C[1] = c1;
-        uint32_t cd = (uint32_t)(J[2] - 1) | ((uint32_t)(J[3] - 1) << 2) | ((uint32_t)(J[4] - 1) << 4);
         for (int i = 2; i <= 4; ++i) {
             if (c1 <= D[i]) { C[i] = c1; cd |= 1u << (6 + i - 2); }
             else C[i] = D[i];
         }
         cost[b] = make_float4(C[1], C[2], C[3], C[4]);
         code[b] = cd;
+        span[b] = make_int2(first, leaves);
         b = parent_int[b];
     }
 }
 
 __global__ void collapse4_sah_kernel(int n, const int32_t* __restrict__ child, const float* __restrict__ bounds,
-                                     const uint32_t* __restrict__ code, const int2* __restrict__ in,
-                                     const uint32_t* __restrict__ n_in, int2* out, uint32_t* n_out, uint32_t* n_nodes,
-                                     float4* nodes4) {
+                                     const uint32_t* __restrict__ code, const int2* __restrict__ span,
+                                     const int2* __restrict__ in, const uint32_t* __restrict__ n_in, int2* out,
+                                     uint32_t* n_out, uint32_t* n_nodes, float4* nodes4) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= *n_in) return;
     const int b = in[t].x, q = in[t].y;
@@ -371,7 +397,7 @@ __global__ void collapse4_sah_kernel(int n, const int32_t* __restrict__ child, c
         sx[sp] = child[2 * x + 1]; si[sp++] = i - j;
         sx[sp] = child[2 * x];     si[sp++] = j;
     }
-    emit4_node(n, slots, ns, bounds, q, out, n_out, n_nodes, nodes4);
+    emit4_node(n, slots, ns, bounds, q, out, n_out, n_nodes, nodes4, code, span);
 }
 
 // ---- 8-wide compressed nodes (the node format of Ylitie, Karras and Laine, "Efficient
@@ -719,7 +745,8 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
     const bool sah = (m->ctx->bvh_collapse ? m->ctx->bvh_collapse : kDefaultCollapse) == EXM_BVH_COLLAPSE_SAH;
     if (sah && n > 1) {
         if (!m->sah_cost && (exm_malloc((void**)&m->sah_cost, (size_t)(n - 1) * sizeof(float4)) != cudaSuccess ||
-                             exm_malloc((void**)&m->sah_code, (size_t)(n - 1) * sizeof(uint32_t)) != cudaSuccess))
+                             exm_malloc((void**)&m->sah_code, (size_t)(n - 1) * sizeof(uint32_t)) != cudaSuccess ||
+                             exm_malloc((void**)&m->sah_span, (size_t)(n - 1) * sizeof(int2)) != cudaSuccess))
             return exm_fail(EXM_ERR_OOM, "BVH buffers (SAH collapse)");
         // the clustering's scratch is free now: parents of internal nodes and leaves, and one
         // arrival counter per internal node
@@ -729,7 +756,7 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
         parents_kernel<<<exm_blocks(n - 1, 256), 256, 0, s>>>(n, m->child, parent_int, parent_leaf);
         cudaMemsetAsync(arrivals, 0, (size_t)(n - 1) * sizeof(uint32_t), s);
         sah_cost_kernel<<<exm_blocks(n, 256), 256, 0, s>>>(n, m->child, m->bounds, parent_int, parent_leaf, arrivals,
-                                                           m->sah_cost, m->sah_code);
+                                                           m->sah_cost, m->sah_code, m->sah_span);
     }
     if (n == 1) {
         single4_kernel<<<1, 1, 0, s>>>(m->bounds, m->nodes4);
@@ -746,8 +773,9 @@ exm_status exm_bvh_build_impl(exm_mesh* m, cudaStream_t s) {
                 return exm_fail(EXM_ERR_TRAVERSAL_LIMIT, "BVH deeper than the traversal stack allows");
             cudaMemsetAsync(cnt + 1, 0, 4, s);
             if (sah)
-                collapse4_sah_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, m->sah_code, fin,
-                                                                          cnt, fout, cnt + 1, cnt + 2, m->nodes4);
+                collapse4_sah_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, m->sah_code,
+                                                                          m->sah_span, fin, cnt, fout, cnt + 1,
+                                                                          cnt + 2, m->nodes4);
             else
                 collapse4_kernel<<<exm_blocks(n_in, 128), 128, 0, s>>>(n, m->child, m->bounds, fin, cnt, fout, cnt + 1,
                                                                       cnt + 2, m->nodes4);

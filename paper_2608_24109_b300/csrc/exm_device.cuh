@@ -381,8 +381,8 @@ __device__ __forceinline__ void light_sample2(const EnvView& e, uint4 ha, uint32
 
 // ----------------------------------------------------------------------- BVH
 // 4-wide BVH, 128-byte nodes (8 float4): the four child boxes as lo.x[4] lo.y[4] lo.z[4]
-// hi.x[4] hi.y[4] hi.z[4], then the four child references (>= 0: node, < 0: leaf ~k =
-// triangle k in leaf order, kEmptyChild: unused slot).  Triangles in leaf order, 64-byte
+// hi.x[4] hi.y[4] hi.z[4], then the four child references (>= 0: node, < 0: a leaf of one to
+// kMaxLeafTris consecutive triangles in leaf order (encoding below), kEmptyChild: unused slot).  Triangles in leaf order, 64-byte
 // records (p0 + original id bits in .w, p1, p2, padding).
 //
 // Bank skew.  The lanes of a warp read different nodes with the same load instruction.  Were
@@ -409,6 +409,10 @@ struct BvhView {
 // [p_a + qlo_c step_a, p_a + qhi_c step_a] with power-of-two steps.  An empty slot has qlo 255,
 // qhi 0 and ref kEmptyChild.
 constexpr int kNodeQ4 = 4;     // float4 per quantised 4-wide node
+// A 4-wide leaf reference ~(k | (c - 1) << kLeafCountShift) names c consecutive triangle records
+// from k (c = 1..kMaxLeafTris; k < 2^28).
+constexpr int kLeafCountShift = 28;
+constexpr int kMaxLeafTris = 4;
 constexpr int kNode8 = 5;      // float4 per 8-wide compressed node
 constexpr int kTri = 4;        // float4 per triangle record: the vertices (original id in the first .w), padding
 constexpr int kStackSize8 = 64;  // node groups on the 8-wide traversal stack: one per level

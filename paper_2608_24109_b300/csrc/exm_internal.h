@@ -62,6 +62,7 @@ struct exm_mesh {
     float4* nodesq = nullptr;  // [n_nodes * 4] 4-wide nodes with quantised child boxes
     float4* sah_cost = nullptr;   // [nf - 1] SAH collapse: C(x, 1..4) per binary node (exm_bvh.cu)
     uint32_t* sah_code = nullptr; // [nf - 1] SAH collapse: the choices behind them
+    int2* sah_span = nullptr;     // [nf - 1] SAH collapse: first leaf record and leaf count
     float4* nodes8 = nullptr;  // [n_nodes * 5] 8-wide compressed nodes
     float4* tris8 = nullptr;   // [nf * 4] triangle records in the 8-wide nodes' order
     uint32_t* n_tris8 = nullptr;

@@ -775,16 +775,20 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
             }
         } else {
             for (int it = 0; it < kRound && !done; ++it) {
-                int next = INT_MIN;  // none: pop (leaf ~k is negative, ~0 == -1)
+                int next = INT_MIN;  // none: pop (a leaf reference is negative, ~0 == -1)
                 if (node < 0) {
+                    // a leaf of c consecutive triangle records from k, ~(k | (c - 1) << 28): one
+                    // triangle per iteration, the rest of the leaf as the next item
+                    const uint32_t lt = ~(uint32_t)node;
                     ++c_tris;
                     float T, det;
                     int id;
-                    if (tri_test(bvh, ~node, r, &T, &det, &id)) {
+                    if (tri_test(bvh, (int)(lt & ((1u << kLeafCountShift) - 1u)), r, &T, &det, &id)) {
                         if (!CLOSEST) { hit = true; done = true; break; }
                         const float t = sdiv(T, det);
                         if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
                     }
+                    if (lt >> kLeafCountShift) next = (int)~(lt - ((1u << kLeafCountShift) - 1u));
                 } else {
                     ++c_nodes;
                     float tc[4];

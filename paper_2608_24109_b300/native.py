@@ -26,7 +26,7 @@ EXM_ERR_BUSY = -7
 EXM_ERR_QUEUE_OVERFLOW = -8
 EXM_ERR_CANCELLED = -9
 FAULT_ALLOC, FAULT_ADMIT, FAULT_SLOW, FAULT_CANCEL, FAULT_CORRUPT = 1, 2, 3, 4, 5
-ASSET_VERSION = 3
+ASSET_VERSION = 4
 BVH_AUTO, BVH_4, BVH_4Q, BVH_8Q = 0, 1, 2, 3
 BVH_COLLAPSE_AUTO, BVH_COLLAPSE_GREEDY, BVH_COLLAPSE_SAH = 0, 1, 2
 ASSET_SECTIONS = 7

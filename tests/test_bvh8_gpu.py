@@ -245,10 +245,11 @@ def test_quantised_four_wide_asset_round_trip_and_cycle():
 
 @pytest.mark.parametrize("name,kw", [("geometry", {"views": 2}), ("indirect", {"views": 1}), ("tiny", {})])
 def test_sah_and_greedy_collapses_render_the_same_images(name, kw):
-    """The SAH and the greedy 4-wide collapse of the same binary tree: the same decisions and
-    images bit for bit; both trees pass the import checks (every reference in range), and the
-    SAH one is not worse by its own cost measure (node visits plus 0.6 triangle tests, counted
-    over the frame's rays), up to 2%."""
+    """The SAH and the greedy 4-wide collapse of the same binary tree (the SAH one with leaves of
+    up to four consecutive triangle records): the same decisions and images bit for bit; both
+    trees pass the import checks (every reference in range) and reference every node and
+    triangle record exactly once, and the SAH one is not worse by its own cost measure (node
+    visits plus 0.6 triangle tests, counted over the frame's rays), up to 2%."""
     from paper_2608_24109_b300 import assets
     from paper_2608_24109_b300 import native as N
     sc = scenes.config(name, **kw)
@@ -258,12 +259,18 @@ def test_sah_and_greedy_collapses_render_the_same_images(name, kw):
         info, secs = assets.export_mesh(r.mesh)
         m2 = assets.import_mesh(r.ctx, info, secs)
         N.exm_mesh_destroy(m2)
-        # a tree: every node but the root referenced once, every triangle record once
+        # a tree: every node but the root referenced once, every triangle record once (a leaf
+        # ~(k | (c - 1) << 28) names the c records from k)
         refs = _unskew(secs[4].view(np.float32), info.n_nodes, 8)[:, 24:28].view(np.int32).ravel()
         refs = refs[refs != 0x7FFFFFFF]
-        inner, leaves = refs[refs >= 0], ~refs[refs < 0]
+        inner, lt = refs[refs >= 0], (~refs[refs < 0]).astype(np.int64)
+        first, count = lt & ((1 << 28) - 1), (lt >> 28) + 1
+        assert count.max() <= 4 and (mode == N.BVH_COLLAPSE_SAH or count.max() == 1)
+        records = np.concatenate([np.arange(f, f + c) for f, c in zip(first, count)])
         assert np.array_equal(np.sort(inner), np.arange(1, info.n_nodes))
-        assert np.array_equal(np.sort(leaves), np.arange(info.nf))
+        assert np.array_equal(np.sort(records), np.arange(info.nf))
+        if mode == N.BVH_COLLAPSE_SAH:
+            assert (count > 1).any()  # some leaves hold several triangles
         r.params.flags |= N.FLAG_COUNT_WORK
         M = torch.as_tensor(sc.maps).cuda().contiguous()
         r.forward(M, _dev(sc.env))

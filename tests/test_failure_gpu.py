@@ -116,7 +116,7 @@ def test_corrupt_asset_injector_gives_the_same_error():
     r.close()
 
 
-@pytest.mark.parametrize("what", ["node_ref", "leaf_ref", "face_index", "version", "node_count"])
+@pytest.mark.parametrize("what", ["node_ref", "leaf_ref", "leaf_span", "face_index", "version", "node_count"])
 def test_import_refuses_out_of_range_assets(what):
     from paper_2608_24109_b300 import assets
     from paper_2608_24109_b300 import native as N
@@ -126,6 +126,8 @@ def test_import_refuses_out_of_range_assets(what):
         _root_refs(secs, info)[0] = info.n_nodes + 5
     elif what == "leaf_ref":
         _root_refs(secs, info)[0] = ~(info.nf + 3)
+    elif what == "leaf_span":   # a leaf of 4 records from the last one: past the end
+        _root_refs(secs, info)[0] = ~((info.nf - 1) | (3 << 28))
     elif what == "node_count":   # more 4-wide nodes than a tree over nf leaves has
         info.n_nodes = info.nf
         secs[4] = np.zeros(info.nf * info.node_bytes, np.uint8)

@@ -317,7 +317,9 @@ def test_autograd_function_matches_direct_backward():
     r.sync()
     assert torch.allclose(M.grad, gm, rtol=1e-4, atol=1e-6)
     assert torch.allclose(E.grad, gE, rtol=1e-4, atol=1e-6)
-    assert torch.allclose(V.grad, gV, rtol=1e-3, atol=1e-5)
+    # the vertex gradients sum contributions of up to ~1e4 by float atomics in either order, so an
+    # entry that cancels to near zero carries their rounding: compare against the tensor's scale
+    assert float((V.grad - gV).abs().max()) <= 1e-5 * float(gV.abs().max())
 
 
 def test_l1_loss():
