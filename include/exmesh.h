@@ -137,7 +137,8 @@ exm_status exm_ctx_set_bvh_width(exm_ctx* ctx, int width);
 /* How the binary tree is cut into 4-wide nodes (layouts EXM_BVH_4 and EXM_BVH_4Q) for the meshes
  * `ctx` builds from now on: EXM_BVH_COLLAPSE_GREEDY opens the child with the largest box until a
  * node holds four; EXM_BVH_COLLAPSE_SAH minimises the surface-area cost of the node and triangle
- * visits by dynamic programming over the slots each subtree may take; EXM_BVH_COLLAPSE_AUTO is
+ * visits by dynamic programming over the slots each subtree may take, and may cut a subtree of
+ * up to four consecutive triangle records as one leaf; EXM_BVH_COLLAPSE_AUTO is
  * the library's default (EXM_BVH_COLLAPSE_SAH).  EXM_BVH_COLLAPSE (greedy or sah) in the
  * environment sets it at exm_create.  Both render the same images bit for bit. */
 #define EXM_BVH_COLLAPSE_AUTO 0
