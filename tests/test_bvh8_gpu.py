@@ -281,3 +281,29 @@ def test_sah_and_greedy_collapses_render_the_same_images(name, kw):
     assert torch.equal(outs[0], outs[1])
     cost_g, cost_s = (w[0] + 0.6 * w[1] for w in work)  # node visits + c_tri / c_node x triangle tests
     assert cost_s <= cost_g * 1.02
+
+
+@pytest.mark.parametrize("nf", [2, 3, 4, 5, 7, 9, 17])
+def test_small_meshes_all_trees_agree(nf):
+    """Meshes of a few triangles (a binary tree of one or two levels, where the SAH collapse may
+    cut leaves of several triangles below the root): the greedy and SAH 4-wide trees and the
+    8-wide tree render the same image, and it is not empty."""
+    from paper_2608_24109_b300 import native as N
+    rng = np.random.default_rng(nf)
+    c = rng.uniform(-0.6, 0.6, (nf, 1, 3))
+    V = (c + rng.uniform(-0.5, 0.5, (nf, 3, 3))).reshape(-1, 3)
+    F = np.arange(3 * nf).reshape(nf, 3)
+    maps = scenes.material_maps(rng, 32)
+    env = scenes.env_map(rng, 32, 16, 1.0)
+    cams = np.stack([scenes.look_at_camera((0.3, 0.4, 2.5), 40, 40), scenes.look_at_camera((-0.4, 0.2, -2.5), 40, 40)])
+    sc = scenes._finish("few", V, F, rng.uniform(0.0, 1.0, (3 * nf, 2)), F, maps, maps, env, cams, 40, 40, seed=nf,
+                        n_direct=32, n_bounce=2, n_light=2)
+    outs = []
+    for layout, collapse in ((N.BVH_4, N.BVH_COLLAPSE_GREEDY), (N.BVH_4, N.BVH_COLLAPSE_SAH),
+                             (N.BVH_4Q, N.BVH_COLLAPSE_SAH), (N.BVH_8Q, None)):
+        r, out = _render(sc, None, layout=layout, collapse=collapse)
+        outs.append(out)
+        r.close()
+    assert float(outs[0].abs().sum()) > 0
+    for o in outs[1:]:
+        assert torch.equal(outs[0], o)
