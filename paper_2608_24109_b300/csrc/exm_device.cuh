@@ -244,10 +244,46 @@ struct EnvView {
     const uint32_t* rguide;  // [Gr+1]: row picked at U1 = g * 2^(32-rbits)
     const uint32_t* cguide;  // [H*(Gc+1)]: column picked in row i at U2 = g * 2^(32-cbits)
     const uint64_t* Qp;      // total of the integer weights (device)
+    const uint64_t* rowpre;  // [H] exclusive prefix of the row sums
+    const uint64_t* rowsum;  // [H] row sums
     uint64_t Q;              // loaded from Qp once per thread
     int W, H;
     int rbits, cbits;
+    // the row phase of a texel pick from shared memory, when a kernel staged it there
+    // (env_rows_to_shared): the CDF at each row's end and the row guide; null: from global memory
+    const uint64_t* srowend;
+    const uint32_t* srguide;
 };
+
+// Bytes of shared memory env_rows_to_shared needs, or 0 when they exceed `limit` (the search then
+// reads global memory).
+__host__ __device__ __forceinline__ size_t env_rows_shared_bytes(int H, int rbits, size_t limit) {
+    const size_t b = (size_t)H * 8 + (((size_t)1 << rbits) + 1) * 4;
+    return b <= limit ? b : 0;
+}
+
+// Stages the row phase of the texel search in shared memory `s` (env_rows_shared_bytes of them,
+// 8-byte aligned): the inclusive CDF at the end of each row, rowpre + rowsum (the same integers
+// as cdf[row W + W - 1]), then the row guide.  Every thread of the block calls it (it
+// synchronises); afterwards pick_texel reads those values there.
+__device__ __forceinline__ void env_rows_to_shared(EnvView& e, void* s) {
+    uint64_t* rowend = reinterpret_cast<uint64_t*>(s);
+    uint32_t* guide = reinterpret_cast<uint32_t*>(rowend + e.H);
+    for (int t = threadIdx.x; t < e.H; t += blockDim.x) rowend[t] = __ldg(e.rowpre + t) + __ldg(e.rowsum + t);
+    const int G = (1 << e.rbits) + 1;
+    for (int t = threadIdx.x; t < G; t += blockDim.x) guide[t] = __ldg(e.rguide + t);
+    __syncthreads();
+    e.srowend = rowend;
+    e.srguide = guide;
+}
+
+// The CDF at the end of row r and the row guide entry g, from shared memory when staged.
+__device__ __forceinline__ uint64_t env_rowend(const EnvView& e, uint32_t r) {
+    return e.srowend ? e.srowend[r] : __ldg(e.cdf + (size_t)r * e.W + e.W - 1);
+}
+__device__ __forceinline__ uint32_t env_rguide(const EnvView& e, uint32_t g) {
+    return e.srguide ? e.srguide[g] : __ldg(e.rguide + g);
+}
 
 __device__ __forceinline__ uint64_t scaled_target(uint32_t U, uint64_t X) {
     return (uint64_t)U * (X >> 32) + (((uint64_t)U * (X & 0xffffffffull)) >> 32);
@@ -269,15 +305,15 @@ __device__ __forceinline__ void pick_texel(const EnvView& e, uint32_t U1, uint32
                                            uint32_t* col_out) {
     const uint64_t tr = scaled_target(U1, e.Q);
     const uint32_t g = U1 >> (32 - e.rbits);
-    uint32_t lo = __ldg(e.rguide + g), hi = __ldg(e.rguide + g + 1);
+    uint32_t lo = env_rguide(e, g), hi = env_rguide(e, g + 1);
     while (lo < hi) {
         const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(e.cdf + (size_t)mid * e.W + e.W - 1) > tr) hi = mid; else lo = mid + 1;
+        if (env_rowend(e, mid) > tr) hi = mid; else lo = mid + 1;
     }
     const uint32_t row = lo;
     const uint64_t* rc = e.cdf + (size_t)row * e.W;
-    const uint64_t pre = row ? __ldg(rc - 1) : 0ull;
-    const uint64_t tc = pre + scaled_target(U2, __ldg(rc + e.W - 1) - pre);
+    const uint64_t pre = row ? env_rowend(e, row - 1) : 0ull;
+    const uint64_t tc = pre + scaled_target(U2, env_rowend(e, row) - pre);
     const uint32_t* cg = e.cguide + (size_t)row * ((1u << e.cbits) + 1);
     const uint32_t g2 = U2 >> (32 - e.cbits);
     lo = __ldg(cg + g2);
@@ -297,21 +333,21 @@ __device__ __forceinline__ void pick_texel2(const EnvView& e, uint32_t U1a, uint
                                             uint32_t* cb) {
     const uint64_t tra = scaled_target(U1a, e.Q), trb = scaled_target(U1b, e.Q);
     const uint32_t ga = U1a >> (32 - e.rbits), gb = U1b >> (32 - e.rbits);
-    uint32_t loa = __ldg(e.rguide + ga), hia = __ldg(e.rguide + ga + 1);
-    uint32_t lob = __ldg(e.rguide + gb), hib = __ldg(e.rguide + gb + 1);
+    uint32_t loa = env_rguide(e, ga), hia = env_rguide(e, ga + 1);
+    uint32_t lob = env_rguide(e, gb), hib = env_rguide(e, gb + 1);
     while (loa < hia || lob < hib) {
         const bool aa = loa < hia, ab = lob < hib;
         const uint32_t ma = loa + ((hia - loa) >> 1), mb = lob + ((hib - lob) >> 1);
-        const uint64_t va = aa ? __ldg(e.cdf + (size_t)ma * e.W + e.W - 1) : 0ull;
-        const uint64_t vb = ab ? __ldg(e.cdf + (size_t)mb * e.W + e.W - 1) : 0ull;
+        const uint64_t va = aa ? env_rowend(e, ma) : 0ull;
+        const uint64_t vb = ab ? env_rowend(e, mb) : 0ull;
         if (aa) { if (va > tra) hia = ma; else loa = ma + 1; }
         if (ab) { if (vb > trb) hib = mb; else lob = mb + 1; }
     }
     const uint32_t rowa = loa, rowb = lob;
     const uint64_t* rca = e.cdf + (size_t)rowa * e.W;
     const uint64_t* rcb = e.cdf + (size_t)rowb * e.W;
-    const uint64_t prea = rowa ? __ldg(rca - 1) : 0ull, preb = rowb ? __ldg(rcb - 1) : 0ull;
-    const uint64_t enda = __ldg(rca + e.W - 1), endb = __ldg(rcb + e.W - 1);
+    const uint64_t prea = rowa ? env_rowend(e, rowa - 1) : 0ull, preb = rowb ? env_rowend(e, rowb - 1) : 0ull;
+    const uint64_t enda = env_rowend(e, rowa), endb = env_rowend(e, rowb);
     const uint64_t tca = prea + scaled_target(U2a, enda - prea), tcb = preb + scaled_target(U2b, endb - preb);
     const uint32_t stride = (1u << e.cbits) + 1;
     const uint32_t g2a = U2a >> (32 - e.cbits), g2b = U2b >> (32 - e.cbits);

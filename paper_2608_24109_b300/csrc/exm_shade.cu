@@ -54,6 +54,7 @@ struct ShadeArgs {
     // maps, env, frame
     MapView map;
     EnvView env;
+    uint32_t env_smem;  // bytes of shared memory that stage the row phase of the texel search, 0: none
     const Cam* cams;
     const unsigned long long* visbuf;
     const uint32_t* pixels;
@@ -295,6 +296,10 @@ __device__ __forceinline__ Surface make_surface(const float att[8], float3 ni, f
 constexpr int kGenK = 32;     // sample indices per warp of gen_direct
 constexpr int kGenBatch = 8;  // sample indices per queue append of a warp
 constexpr int kGenThreads = 256;
+// Shared memory the ray generation kernels may take for the row phase of the texel search
+// (env_rows_to_shared), beside their 24 KB of staged directions: 16 KB holds it for environments
+// of up to 1024 rows; taller ones search global memory.
+constexpr size_t kEnvSharedMax = 20u << 10;
 
 // One shadow ray per (pixel, k) whose direction is above the geometric horizon (Eq. 17).
 // A warp appends the rays of kGenBatch sample indices at once: their directions wait in
@@ -302,6 +307,10 @@ constexpr int kGenThreads = 256;
 // reserves their slots, so the counter sees one request per batch instead of one per sample.
 __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
     __shared__ float s_dir[kGenThreads / 32][kGenBatch][3][32];
+    extern __shared__ __align__(8) unsigned char s_env_rows[];
+    EnvView env = A.env;
+    env.Q = *A.env.Qp;
+    if (A.env_smem) env_rows_to_shared(env, s_env_rows);  // before any thread returns
     const uint32_t total = *A.count;
     const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
     if (A.chunk_begin >= end) return;
@@ -314,8 +323,6 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
     float (*sd)[3][32] = s_dir[threadIdx.x >> 5];
     const uint32_t i = A.chunk_begin + group * 32 + lane;
     const bool valid = i < end;
-    EnvView env = A.env;
-    env.Q = *A.env.Qp;
     int c = 0, px, py;
     uint32_t rem = 0;
     S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
@@ -414,6 +421,10 @@ __global__ void __launch_bounds__(256) gen_secondary_kernel(ShadeArgs A) {
 // appended kGenBatch light samples at a time like gen_direct's.
 __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) {
     __shared__ float s_dir[kGenThreads / 32][kGenBatch][3][32];
+    extern __shared__ __align__(8) unsigned char s_env_rows[];
+    EnvView env = A.env;
+    env.Q = *A.env.Qp;
+    if (A.env_smem) env_rows_to_shared(env, s_env_rows);  // before any thread returns
     const uint32_t total = *A.count;
     const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
     if (A.chunk_begin >= end) return;
@@ -424,8 +435,6 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
     float (*sd)[3][32] = s_dir[threadIdx.x >> 5];
     const uint32_t i = A.chunk_begin + group * 32 + lane;
     const bool valid = i < end;
-    EnvView env = A.env;
-    env.Q = *A.env.Qp;
     int c = 0, px, py;
     uint32_t rem = 0;
     S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
@@ -1474,6 +1483,9 @@ static ShadeArgs make_args(exm_ctx* ctx, const exm_mesh* m, const void* maps, in
     A.bvh_layout = m->layout;
     A.map.data = maps; A.map.W = mapW; A.map.H = mapH; A.map.wrap_u = (p->flags & EXM_FLAG_WRAP_U) != 0;
     A.env.texel = e->texel; A.env.cdf = e->cdf; A.env.rguide = e->rguide; A.env.cguide = e->cguide;
+    A.env.rowpre = e->rowpre; A.env.rowsum = e->rowsum;
+    A.env.srowend = nullptr; A.env.srguide = nullptr;
+    A.env_smem = env_rows_shared_bytes(e->H, e->rbits, kEnvSharedMax);
     A.env.W = e->W; A.env.H = e->H;
     A.env.rbits = e->rbits; A.env.cbits = e->cbits;
     A.env.Qp = e->total;
@@ -1670,11 +1682,11 @@ static void trace_chunk(exm_ctx* ctx, exm_frame* f, const exm_params* p, const C
     }
     if (p->n_direct > 0) {  // 0 in the indirect-only half-resolution pass
         gen_direct_kernel<<<exm_blocks((size_t)c.Pc * ((p->n_direct + kGenK - 1) / kGenK), kGenThreads), kGenThreads,
-                            0, s>>>(A);
+                            A.env_smem, s>>>(A);
         ctx->launches += 1;
     }
     if (c.indirect) {
-        gen_seclight_kernel<<<exm_blocks((size_t)c.Pc, kGenThreads), kGenThreads, 0, s>>>(A);
+        gen_seclight_kernel<<<exm_blocks((size_t)c.Pc, kGenThreads), kGenThreads, A.env_smem, s>>>(A);
         ctx->launches += 1;
     }
     launch_trace<false>(ctx, f, p, A, s);
@@ -1814,11 +1826,11 @@ void relight_pass_shadow_rays(exm_ctx* ctx, exm_relight_pass* rp, cudaStream_t s
     const ShadeArgs& A = rp->A;
     if (rp->p.n_direct > 0) {
         gen_direct_kernel<<<exm_blocks((size_t)rp->c.Pc * ((rp->p.n_direct + kGenK - 1) / kGenK), kGenThreads),
-                            kGenThreads, 0, s>>>(A);
+                            kGenThreads, A.env_smem, s>>>(A);
         ctx->launches += 1;
     }
     if (rp->c.indirect) {
-        gen_seclight_kernel<<<exm_blocks((size_t)rp->c.Pc, kGenThreads), kGenThreads, 0, s>>>(A);
+        gen_seclight_kernel<<<exm_blocks((size_t)rp->c.Pc, kGenThreads), kGenThreads, A.env_smem, s>>>(A);
         ctx->launches += 1;
     }
 }
