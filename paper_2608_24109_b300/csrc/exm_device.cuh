@@ -277,12 +277,17 @@ __device__ __forceinline__ void env_rows_to_shared(EnvView& e, void* s) {
     e.srguide = guide;
 }
 
-// The CDF at the end of row r and the row guide entry g, from shared memory when staged.
+// The CDF at the end of row r and the row guide entry g: from shared memory when the kernel
+// staged them (SR), else from global memory.
+template <bool SR>
 __device__ __forceinline__ uint64_t env_rowend(const EnvView& e, uint32_t r) {
-    return e.srowend ? e.srowend[r] : __ldg(e.cdf + (size_t)r * e.W + e.W - 1);
+    if constexpr (SR) return e.srowend[r];
+    else return __ldg(e.cdf + (size_t)r * e.W + e.W - 1);
 }
+template <bool SR>
 __device__ __forceinline__ uint32_t env_rguide(const EnvView& e, uint32_t g) {
-    return e.srguide ? e.srguide[g] : __ldg(e.rguide + g);
+    if constexpr (SR) return e.srguide[g];
+    else return __ldg(e.rguide + g);
 }
 
 __device__ __forceinline__ uint64_t scaled_target(uint32_t U, uint64_t X) {
@@ -301,19 +306,20 @@ __host__ __device__ __forceinline__ void strata2(uint32_t n, uint32_t* nx, uint3
 // Texel chosen by the row fraction U1 and column fraction U2: the row is the smallest i
 // whose inclusive row prefix exceeds floor(U1 Q / 2^32); the column the smallest j of row i
 // whose in-row prefix exceeds floor(U2 rowsum_i / 2^32) (guide tables bound both searches).
+template <bool SR = false>
 __device__ __forceinline__ void pick_texel(const EnvView& e, uint32_t U1, uint32_t U2, uint32_t* row_out,
                                            uint32_t* col_out) {
     const uint64_t tr = scaled_target(U1, e.Q);
     const uint32_t g = U1 >> (32 - e.rbits);
-    uint32_t lo = env_rguide(e, g), hi = env_rguide(e, g + 1);
+    uint32_t lo = env_rguide<SR>(e, g), hi = env_rguide<SR>(e, g + 1);
     while (lo < hi) {
         const uint32_t mid = lo + ((hi - lo) >> 1);
-        if (env_rowend(e, mid) > tr) hi = mid; else lo = mid + 1;
+        if (env_rowend<SR>(e, mid) > tr) hi = mid; else lo = mid + 1;
     }
     const uint32_t row = lo;
     const uint64_t* rc = e.cdf + (size_t)row * e.W;
-    const uint64_t pre = row ? env_rowend(e, row - 1) : 0ull;
-    const uint64_t tc = pre + scaled_target(U2, env_rowend(e, row) - pre);
+    const uint64_t pre = row ? env_rowend<SR>(e, row - 1) : 0ull;
+    const uint64_t tc = pre + scaled_target(U2, env_rowend<SR>(e, row) - pre);
     const uint32_t* cg = e.cguide + (size_t)row * ((1u << e.cbits) + 1);
     const uint32_t g2 = U2 >> (32 - e.cbits);
     lo = __ldg(cg + g2);
@@ -328,26 +334,27 @@ __device__ __forceinline__ void pick_texel(const EnvView& e, uint32_t U1, uint32
 
 // Two texel picks in lockstep: the same arithmetic as pick_texel for each, with the loads of
 // both searches issued together so that their latencies overlap.
+template <bool SR = false>
 __device__ __forceinline__ void pick_texel2(const EnvView& e, uint32_t U1a, uint32_t U2a, uint32_t U1b,
                                             uint32_t U2b, uint32_t* ra, uint32_t* ca, uint32_t* rb,
                                             uint32_t* cb) {
     const uint64_t tra = scaled_target(U1a, e.Q), trb = scaled_target(U1b, e.Q);
     const uint32_t ga = U1a >> (32 - e.rbits), gb = U1b >> (32 - e.rbits);
-    uint32_t loa = env_rguide(e, ga), hia = env_rguide(e, ga + 1);
-    uint32_t lob = env_rguide(e, gb), hib = env_rguide(e, gb + 1);
+    uint32_t loa = env_rguide<SR>(e, ga), hia = env_rguide<SR>(e, ga + 1);
+    uint32_t lob = env_rguide<SR>(e, gb), hib = env_rguide<SR>(e, gb + 1);
     while (loa < hia || lob < hib) {
         const bool aa = loa < hia, ab = lob < hib;
         const uint32_t ma = loa + ((hia - loa) >> 1), mb = lob + ((hib - lob) >> 1);
-        const uint64_t va = aa ? env_rowend(e, ma) : 0ull;
-        const uint64_t vb = ab ? env_rowend(e, mb) : 0ull;
+        const uint64_t va = aa ? env_rowend<SR>(e, ma) : 0ull;
+        const uint64_t vb = ab ? env_rowend<SR>(e, mb) : 0ull;
         if (aa) { if (va > tra) hia = ma; else loa = ma + 1; }
         if (ab) { if (vb > trb) hib = mb; else lob = mb + 1; }
     }
     const uint32_t rowa = loa, rowb = lob;
     const uint64_t* rca = e.cdf + (size_t)rowa * e.W;
     const uint64_t* rcb = e.cdf + (size_t)rowb * e.W;
-    const uint64_t prea = rowa ? env_rowend(e, rowa - 1) : 0ull, preb = rowb ? env_rowend(e, rowb - 1) : 0ull;
-    const uint64_t enda = env_rowend(e, rowa), endb = env_rowend(e, rowb);
+    const uint64_t prea = rowa ? env_rowend<SR>(e, rowa - 1) : 0ull, preb = rowb ? env_rowend<SR>(e, rowb - 1) : 0ull;
+    const uint64_t enda = env_rowend<SR>(e, rowa), endb = env_rowend<SR>(e, rowb);
     const uint64_t tca = prea + scaled_target(U2a, enda - prea), tcb = preb + scaled_target(U2b, endb - preb);
     const uint32_t stride = (1u << e.cbits) + 1;
     const uint32_t g2a = U2a >> (32 - e.cbits), g2b = U2b >> (32 - e.cbits);
@@ -394,22 +401,24 @@ __device__ __forceinline__ void finish_sample(const EnvView& e, uint4 h, uint32_
     s->texel = t;
 }
 
+template <bool SR = false>
 __device__ __forceinline__ LightSample light_sample(const EnvView& e, uint4 h, uint32_t k, uint32_t nx, uint32_t ny) {
     LightSample s;
     uint32_t kx, ky, i, j;
     strata_of(k, nx, &kx, &ky);
-    pick_texel(e, stratified32(ky, ny, h.x), stratified32(kx, nx, h.w), &i, &j);
+    pick_texel<SR>(e, stratified32(ky, ny, h.x), stratified32(kx, nx, h.w), &i, &j);
     finish_sample(e, h, i, j, &s);
     return s;
 }
 
 // Light samples ka and kb together (pick_texel2): each equal to light_sample's.
+template <bool SR = false>
 __device__ __forceinline__ void light_sample2(const EnvView& e, uint4 ha, uint32_t ka, uint4 hb, uint32_t kb,
                                               uint32_t nx, uint32_t ny, LightSample* sa, LightSample* sb) {
     uint32_t kxa, kya, kxb, kyb, ia, ja, ib, jb;
     strata_of(ka, nx, &kxa, &kya);
     strata_of(kb, nx, &kxb, &kyb);
-    pick_texel2(e, stratified32(kya, ny, ha.x), stratified32(kxa, nx, ha.w), stratified32(kyb, ny, hb.x),
+    pick_texel2<SR>(e, stratified32(kya, ny, ha.x), stratified32(kxa, nx, ha.w), stratified32(kyb, ny, hb.x),
                 stratified32(kxb, nx, hb.w), &ia, &ja, &ib, &jb);
     finish_sample(e, ha, ia, ja, sa);
     finish_sample(e, hb, ib, jb, sb);

@@ -305,12 +305,13 @@ constexpr size_t kEnvSharedMax = 20u << 10;
 // A warp appends the rays of kGenBatch sample indices at once: their directions wait in
 // shared memory (each lane its own column) while one atomic on the chunk's queue counter
 // reserves their slots, so the counter sees one request per batch instead of one per sample.
+template <bool SR>
 __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
     __shared__ float s_dir[kGenThreads / 32][kGenBatch][3][32];
     extern __shared__ __align__(8) unsigned char s_env_rows[];
     EnvView env = A.env;
     env.Q = *A.env.Qp;
-    if (A.env_smem) env_rows_to_shared(env, s_env_rows);  // before any thread returns
+    if (SR) env_rows_to_shared(env, s_env_rows);  // before any thread returns
     const uint32_t total = *A.count;
     const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
     if (A.chunk_begin >= end) return;
@@ -346,7 +347,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_direct_kernel(ShadeArgs A) {
             const uint4 ha = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
             const uint4 hb = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k2, 0u), A.key);
             LightSample sa, sb;
-            light_sample2(env, ha, (uint32_t)k, hb, (uint32_t)k2, A.nxd, A.nyd, &sa, &sb);
+            light_sample2<SR>(env, ha, (uint32_t)k, hb, (uint32_t)k2, A.nxd, A.nyd, &sa, &sb);
             if (sdot(ngs, sa.dir) > 0.0f) {
                 want |= 1u << u;
                 A.tsel[(size_t)(i - A.state_base) * A.Nd + k] = sa.texel;
@@ -419,12 +420,13 @@ __global__ void __launch_bounds__(256) gen_secondary_kernel(ShadeArgs A) {
 
 // One shadow ray per (valid secondary hit, s) above the hit's geometric horizon (Eq. 18),
 // appended kGenBatch light samples at a time like gen_direct's.
+template <bool SR>
 __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) {
     __shared__ float s_dir[kGenThreads / 32][kGenBatch][3][32];
     extern __shared__ __align__(8) unsigned char s_env_rows[];
     EnvView env = A.env;
     env.Q = *A.env.Qp;
-    if (A.env_smem) env_rows_to_shared(env, s_env_rows);  // before any thread returns
+    if (SR) env_rows_to_shared(env, s_env_rows);  // before any thread returns
     const uint32_t total = *A.count;
     const uint32_t end = min(A.chunk_begin + A.chunk_pixels, total);
     if (A.chunk_begin >= end) return;
@@ -462,7 +464,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
                 for (int u = 0; u < sn; ++u) {
                     const int s = sb + u;
                     const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(j * A.Ns + s), 2u), A.key);
-                    const LightSample ls = light_sample(env, h, (uint32_t)s, A.nxs, A.nys);
+                    const LightSample ls = light_sample<SR>(env, h, (uint32_t)s, A.nxs, A.nys);
                     if (sdot(ngy, ls.dir) > 0.0f) {
                         want |= 1u << u;
                         A.tsel2[(size_t)(i - A.state_base) * A.Nb * A.Ns + j * A.Ns + s] = ls.texel;
@@ -1681,12 +1683,15 @@ static void trace_chunk(exm_ctx* ctx, exm_frame* f, const exm_params* p, const C
         launch_trace<true>(ctx, f, p, A, s);
     }
     if (p->n_direct > 0) {  // 0 in the indirect-only half-resolution pass
-        gen_direct_kernel<<<exm_blocks((size_t)c.Pc * ((p->n_direct + kGenK - 1) / kGenK), kGenThreads), kGenThreads,
-                            A.env_smem, s>>>(A);
+        const unsigned gb = exm_blocks((size_t)c.Pc * ((p->n_direct + kGenK - 1) / kGenK), kGenThreads);
+        if (A.env_smem) gen_direct_kernel<true><<<gb, kGenThreads, A.env_smem, s>>>(A);
+        else gen_direct_kernel<false><<<gb, kGenThreads, 0, s>>>(A);
         ctx->launches += 1;
     }
     if (c.indirect) {
-        gen_seclight_kernel<<<exm_blocks((size_t)c.Pc, kGenThreads), kGenThreads, A.env_smem, s>>>(A);
+        const unsigned sb = exm_blocks((size_t)c.Pc, kGenThreads);
+        if (A.env_smem) gen_seclight_kernel<true><<<sb, kGenThreads, A.env_smem, s>>>(A);
+        else gen_seclight_kernel<false><<<sb, kGenThreads, 0, s>>>(A);
         ctx->launches += 1;
     }
     launch_trace<false>(ctx, f, p, A, s);
@@ -1825,12 +1830,15 @@ bool relight_pass_indirect(const exm_relight_pass* rp) { return rp->c.indirect; 
 void relight_pass_shadow_rays(exm_ctx* ctx, exm_relight_pass* rp, cudaStream_t s) {
     const ShadeArgs& A = rp->A;
     if (rp->p.n_direct > 0) {
-        gen_direct_kernel<<<exm_blocks((size_t)rp->c.Pc * ((rp->p.n_direct + kGenK - 1) / kGenK), kGenThreads),
-                            kGenThreads, A.env_smem, s>>>(A);
+        const unsigned gb = exm_blocks((size_t)rp->c.Pc * ((rp->p.n_direct + kGenK - 1) / kGenK), kGenThreads);
+        if (A.env_smem) gen_direct_kernel<true><<<gb, kGenThreads, A.env_smem, s>>>(A);
+        else gen_direct_kernel<false><<<gb, kGenThreads, 0, s>>>(A);
         ctx->launches += 1;
     }
     if (rp->c.indirect) {
-        gen_seclight_kernel<<<exm_blocks((size_t)rp->c.Pc, kGenThreads), kGenThreads, A.env_smem, s>>>(A);
+        if (A.env_smem)
+            gen_seclight_kernel<true><<<exm_blocks((size_t)rp->c.Pc, kGenThreads), kGenThreads, A.env_smem, s>>>(A);
+        else gen_seclight_kernel<false><<<exm_blocks((size_t)rp->c.Pc, kGenThreads), kGenThreads, 0, s>>>(A);
         ctx->launches += 1;
     }
 }
