@@ -225,14 +225,14 @@ def test_slow_request_wait_times_out_then_completes():
 
 
 def test_cancel_queued_and_in_flight_requests():
-    """One slot: the first request (768^2 pixels x 64 samples, several milliseconds of device
-    work) is launched at once, the second waits in the queue.  Cancelling both while the server
+    """One slot: the first request (1024^2 pixels x 128 samples, 2^27 shadow rays: tens of
+    milliseconds of device work) is launched at once, the second waits in the queue.  Cancelling both while the server
     still reports the first in flight (its completion not yet observed) gives EXM_ERR_CANCELLED
     for each: the launched one finishes on the device and its result is dropped.  The server
     then serves a new request normally."""
     from paper_2608_24109_b300 import native as N
     srv, aid, env, sc = _server(slots=1, budget=8 << 30)
-    t1 = srv.submit(srv.request(aid, env, sc.cams, 768, 768, 64, seed=1))
+    t1 = srv.submit(srv.request(aid, env, sc.cams, 1024, 1024, 128, seed=1))
     N.exm_debug_fault(N.FAULT_SLOW, 300)
     t2 = srv.submit(srv.request(aid, env, sc.cams, 48, 48, 16, seed=2))
     N.exm_debug_fault(N.FAULT_SLOW, 0)
