@@ -193,6 +193,21 @@ def test_forward_parity_tiny_ragged_full_frame():
     assert (out.cpu().numpy()[bg] == 0).all()
 
 
+@pytest.mark.parametrize("env_w,env_h", [(24, 1024), (20, 1100)])
+def test_forward_parity_tall_environments(env_w, env_h):
+    """The ray-generation kernels stage the row phase of the texel search in shared memory for
+    environments of up to 1024 rows and search global memory above: both sides of that limit,
+    with indirect light (both kernels), against the oracle."""
+    sc = small_cavity(res=40, views=1, n=16, n_direct=24, n_bounce=4, n_light=3)
+    sc.env = scenes.env_map(np.random.default_rng(env_h), env_w, env_h, 1.5)
+    r, M, E, out = gpu_forward(sc)
+    keys, tab, dec, V, Mo, Eo = oracle_full(sc)
+    I = shade.render_image(sc, tab, dec, V, Mo, Eo).numpy()
+    g = out.cpu().numpy()[dec.pix[:, 0], dec.pix[:, 1], dec.pix[:, 2]]
+    check_radiance(g, I, f"env {env_w}x{env_h}")
+    r.close()
+
+
 def test_forward_parity_tiny_full_size_sampled():
     sc = scenes.config("tiny")
     r, M, E, out = gpu_forward(sc)
