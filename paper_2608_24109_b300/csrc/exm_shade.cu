@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(kGenThreads) gen_seclight_kernel(ShadeArgs A) 
 // lanes, shorter ones refill more often; 24 measured best.  Each ray is clipped where it
 // leaves the triangles' bounding sphere (sphere_exit).
 constexpr uint32_t kPool = 256;
-constexpr int kRound = 24;  // node visits between refills
+constexpr int kRound = 32;  // traversal iterations between refills
 
 constexpr int kTraceThreads = 128;
 // Resident tracer blocks per SM (the persistent grid is this many per SM): 9 blocks of 4 warps
@@ -673,6 +673,7 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
     const unsigned lt = (1u << lane) - 1u;
     uint32_t err = 0, c_nodes = 0, c_tris = 0, c_rays = 0;
     int sp = 0, node = 0, best = -1, steps = 0;
+    int leaf = INT_MIN;  // any hit, 4-wide: the leaf set aside while the lane opens nodes (none: INT_MIN)
     // 8-wide traversal: the current group of node children (base, mask of those left to visit)
     // and of triangle children (base, mask of those left to test)
     uint32_t gbase = 0, gmask = 0, tbase = 0, tmask = 0;
@@ -732,7 +733,7 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                 r = make_ray(s3(a.x, a.y, a.z), s3(a.w, b.x, b.y));
                 tclip = sphere_exit(r.o, r.d, __ldg(bvh.sphere));
                 slot = (uint64_t)__float_as_uint(b.z) | ((uint64_t)__float_as_uint(b.w) << 32);
-                sp = 0; node = 0; best = -1; steps = 0; bt = INFINITY; bdet = 0.0f;
+                sp = 0; node = 0; leaf = INT_MIN; best = -1; steps = 0; bt = INFINITY; bdet = 0.0f;
                 gbase = 0; gmask = 1u; tmask = 0u;  // 8-wide: the root alone
                 active = true;
                 ++c_rays;
@@ -745,10 +746,9 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
         }
         if (!active) continue;
         bool done = false, hit = false;
-        // one item per iteration: a 4-wide node (node >= 0) or one triangle (node < 0, ~k);
-        // hit leaves are pushed like inner nodes, so a warp runs at most one triangle test
-        // per iteration whatever its lanes found in their last node
-        steps += kRound;  // the cap is checked once per round: at most kTraversalCap + kRound items
+        // a round of at most kRound iterations, each one traversal item (a node or a triangle)
+        // per lane that takes part
+        steps += kRound;  // the cap is checked once per round: at most kTraversalCap + kRound iterations
         if (steps > kTraversalCap) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; }
         if constexpr (W8) {
             // one item per iteration: an 8-wide node (the next child of the current node group)
@@ -784,7 +784,55 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                 node8_hits(bvh.nodes8 + kNode8 * (size_t)nd, r, CLOSEST ? fminf(bt, tclip) : tclip, &gbase, &tbase,
                            &gmask, &tmask);
             }
+        } else if constexpr (!CLOSEST) {
+            // any hit: a leaf met while opening nodes is set aside in `leaf` and the lane goes on
+            // opening nodes (an unoccluded ray opens every box it crosses in any order, so the
+            // work is wasted only on rays that turn out occluded).  Each iteration the warp runs
+            // node tests or triangle tests, not both: triangles once the lanes holding a leaf
+            // are at least 3/4 of those with a node to open (a triangle test costs less than a
+            // node test; 1/2 and 1 measured slower, and so did a second leaf in hand).  `node`
+            // holds the next node, or a second leaf that waits for the first, or none.
+            for (int it = 0; it < kRound; ++it) {
+                if (node == INT_MIN && sp > 0) node = stack[--sp];
+                if (leaf == INT_MIN && node < 0 && node != INT_MIN) { leaf = node; node = INT_MIN; }
+                if (node == INT_MIN && leaf == INT_MIN) { done = true; break; }
+                const unsigned m = __activemask();
+                const int ntri = __popc(__ballot_sync(m, leaf != INT_MIN));
+                const int nnode = __popc(__ballot_sync(m, node >= 0));
+                if (4 * ntri >= 3 * nnode) {
+                    if (leaf != INT_MIN) {
+                        // a leaf of c consecutive triangle records from k, ~(k | (c - 1) << 28): one
+                        // triangle per iteration, the rest of the leaf kept in the hand
+                        const uint32_t lt = ~(uint32_t)leaf;
+                        ++c_tris;
+                        float T, det;
+                        int id;
+                        if (tri_test(bvh, (int)(lt & ((1u << kLeafCountShift) - 1u)), r, &T, &det, &id)) {
+                            hit = true; done = true; break;
+                        }
+                        leaf = (lt >> kLeafCountShift) ? (int)~(lt - ((1u << kLeafCountShift) - 1u)) : INT_MIN;
+                    }
+                } else if (node >= 0) {
+                    ++c_nodes;
+                    float tc[4];
+                    int ref[4];
+                    bool hc[4];
+                    node4_test<LAYOUT>(bvh, node, r, tclip, tc, hc, ref);
+                    if (sp > kStackSize4 - 3) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
+                    // the first hit child in slot order goes on, the others are pushed
+                    int nc = -1;
+#pragma unroll
+                    for (int c = 3; c >= 0; --c)
+                        if (hc[c]) nc = c;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (hc[c] && c != nc) stack[sp++] = ref[c];
+                    node = nc < 0 ? INT_MIN : nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
+                }
+            }
         } else {
+            // closest hit: one item per iteration, a 4-wide node (node >= 0) or one triangle
+            // (node < 0); hit leaves are pushed like inner nodes
             for (int it = 0; it < kRound && !done; ++it) {
                 int next = INT_MIN;  // none: pop (a leaf reference is negative, ~0 == -1)
                 if (node < 0) {
@@ -795,7 +843,6 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                     float T, det;
                     int id;
                     if (tri_test(bvh, (int)(lt & ((1u << kLeafCountShift) - 1u)), r, &T, &det, &id)) {
-                        if (!CLOSEST) { hit = true; done = true; break; }
                         const float t = sdiv(T, det);
                         if (t < bt || (t == bt && id < best)) { bt = t; best = id; bdet = det; }
                     }
@@ -805,35 +852,22 @@ __device__ __forceinline__ void trace_body(const ShadeArgs& A, const TraceJob* _
                     float tc[4];
                     int ref[4];
                     bool hc[4];
-                    node4_test<LAYOUT>(bvh, node, r, CLOSEST ? fminf(bt, tclip) : tclip, tc, hc, ref);
+                    node4_test<LAYOUT>(bvh, node, r, fminf(bt, tclip), tc, hc, ref);
                     // a node pushes at most 3 children; the build keeps 3 entries per level within the stack
                     if (sp > kStackSize4 - 3) { err |= ERRBIT_TRAVERSAL; hit = true; done = true; break; }
-                    if (CLOSEST) {
-                        // continue with the nearest hit child; push the others (storing their
-                        // entry distances to skip boxes beyond the nearest hit at pop time, or
-                        // pushing them farthest first, cost more than they saved: the secondary
-                        // rays mostly leave the mesh)
-                        int nc = -1;
-                        float tn = INFINITY;
-    #pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
-    #pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (hc[c] && c != nc) stack[sp++] = ref[c];
-                        if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
-                    } else {
-                        // any hit: continue with the first hit child in slot order (an unoccluded
-                        // shadow ray opens every box it crosses whatever the order, so no sort)
-                        int nc = -1;
-    #pragma unroll
-                        for (int c = 3; c >= 0; --c)
-                            if (hc[c]) nc = c;
-    #pragma unroll
-                        for (int c = 0; c < 4; ++c)
-                            if (hc[c] && c != nc) stack[sp++] = ref[c];
-                        if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
-                    }
+                    // continue with the nearest hit child; push the others (storing their entry
+                    // distances to skip boxes beyond the nearest hit at pop time, or pushing them
+                    // farthest first, cost more than they saved: the secondary rays mostly leave
+                    // the mesh)
+                    int nc = -1;
+                    float tn = INFINITY;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (hc[c] && tc[c] < tn) { tn = tc[c]; nc = c; }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (hc[c] && c != nc) stack[sp++] = ref[c];
+                    if (nc >= 0) next = nc == 0 ? ref[0] : nc == 1 ? ref[1] : nc == 2 ? ref[2] : ref[3];
                 }
                 if (next == INT_MIN) {
                     if (sp == 0) { done = true; break; }
