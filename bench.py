@@ -44,7 +44,7 @@ RAY_BYTES = 32.0
 # one- or two-view case of the same scene; profiles/trace_kernel_<workload>.md): DRAM bytes
 # (read + write) per traced ray, L2 sector throughput and issue-slot use as fractions of peak.
 TRACE_NCU = {
-    "precision": {"dram_bytes_per_ray": 39.9, "l2_frac": 0.117, "issue_frac": 0.714, "l1_frac": 0.749,
+    "precision": {"dram_bytes_per_ray": 40.5, "l2_frac": 0.125, "issue_frac": 0.711, "l1_frac": 0.759,
                   "source": "ncu, any-hit launch of the 1-view precision case"},
 }
 RAY_QUEUE_MAX = 1 << 27  # rays per chunk at most (the library's default queue)
