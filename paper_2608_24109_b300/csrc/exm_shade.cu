@@ -1100,12 +1100,176 @@ __global__ void __launch_bounds__(256) pixel_surface_kernel(ShadeArgs A) {
 // backward sums, over the pixel's samples, the adjoints of E (scattered per sample) and of
 // n_s, w_o, a, r and m, which shade_epilogue_kernel carries back to the maps and vertices.
 // Fields of the per-hit records of the indirect loop (one column per secondary ray of a batch of
-// 32): the forward's first seven, then the backward's hit state and its adjoint sums.
+// 32 rays, of one pixel or of a group of pixels): the forward's first seven, then the
+// backward's hit state and its adjoint sums.
 enum : int {
     HWB, HF_X, HF_Y, HF_Z, HN_X, HN_Y, HN_Z, kHitFwd,
     HJ_X = kHitFwd, HJ_Y, HJ_Z, HPBS, HA_X, HA_Y, HA_Z, HM, HT_X, HT_Y, HT_Z, HB_X, HB_Y, HB_Z, HN_X2, HN_Y2, HN_Z2,
     HNT_X, HNT_Y, HNT_Z, HQL, HFP0, HFP1, HFP2, HFP3, HFS, HFT, GFD_X, GFD_Y, GFD_Z, GNS_X, GNS_Y, GNS_Z, kHitBwd
 };
+
+// Hit record of secondary ray j of a pixel (what depends on j alone: its direction, the hit
+// point's double-word barycentrics, the material and frame at y) into column `col` of the
+// warp's records.  wb = 0 marks a ray without live samples (no valid hit, or n_s(x).w_j <= 0).
+template <typename T, bool BWD>
+__device__ __forceinline__ void ind_record(const ShadeArgs& A, size_t si, uint32_t rem, int c, int j, S3 org, S3 ngs,
+                                           float3 sns, float (*hr)[32], int col) {
+    const int gtri = A.hits[si * A.Nb + j];
+    float wb = 0.0f;
+    float3 fdy = f3(0.f, 0.f, 0.f), nsy = f3(0.f, 0.f, 1.f);
+    if (gtri >= 0) {
+        float xi1;
+        const S3 wjs = secondary_dir(A, rem, c, j, ngs, &xi1);
+        const float3 wj = normalize(tof(wjs));
+        const float cxj = dot(sns, wj);
+        if (cxj > 0.0f) {
+            const float pbs = (A.lambda / (float)A.Nb) * (kPi / __fsqrt_rn(ssub(1.0f, xi1)));  // lambda / (N_b p_b)
+            wb = pbs * cxj;
+            const int q0 = __ldg(A.F + 3 * gtri), q1 = __ldg(A.F + 3 * gtri + 1), q2 = __ldg(A.F + 3 * gtri + 2);
+            const int v0 = __ldg(A.Fuv + 3 * gtri), v1 = __ldg(A.Fuv + 3 * gtri + 1), v2 = __ldg(A.Fuv + 3 * gtri + 2);
+            const float3 Q0 = ld3(A.V + 3 * q0), Q1 = ld3(A.V + 3 * q1), Q2 = ld3(A.V + 3 * q2);
+            FF by[3];
+            bary_ff(ff3_sub(f3(org.x, org.y, org.z), Q0), FF3{ff(wjs.x), ff(wjs.y), ff(wjs.z)}, Q0, Q1, Q2, by);
+            int ti, tj;
+            float fs, ft;
+            texel_coord(by, __ldg(A.UV + 2 * v0), __ldg(A.UV + 2 * v1), __ldg(A.UV + 2 * v2), A.map.W, &ti, &fs);
+            texel_coord(by, __ldg(A.UV + 2 * v0 + 1), __ldg(A.UV + 2 * v1 + 1), __ldg(A.UV + 2 * v2 + 1), A.map.H,
+                        &tj, &ft);
+            const Footprint fpy = footprint_i(A.map, ti, tj, fs, ft);
+            float atty[8];
+            if (A.sec_material) {
+                fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
+            } else {
+                // constant default material: grey diffuse, flat tangent-space normal
+                atty[0] = atty[1] = atty[2] = 0.5f;
+                atty[3] = 0.5f;
+                atty[4] = 0.0f;
+                atty[5] = atty[6] = 0.0f;
+                atty[7] = 1.0f;
+            }
+            const float b0 = ff_f(by[0]), b1 = ff_f(by[1]), b2 = ff_f(by[2]);
+            const float3 niy = b0 * ld3(A.nrm + 3 * q0) + b1 * ld3(A.nrm + 3 * q1) + b2 * ld3(A.nrm + 3 * q2);
+            const float3 tiy = b0 * ld3(A.tan + 3 * v0) + b1 * ld3(A.tan + 3 * v1) + b2 * ld3(A.tan + 3 * v2);
+            const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
+            fdy = ((1.0f - sy.m) * kInvPi) * sy.a;
+            nsy = sy.ns;
+            if (BWD) {
+                hr[HJ_X][col] = wj.x; hr[HJ_Y][col] = wj.y; hr[HJ_Z][col] = wj.z;
+                hr[HPBS][col] = pbs;
+                hr[HA_X][col] = sy.a.x; hr[HA_Y][col] = sy.a.y; hr[HA_Z][col] = sy.a.z;
+                hr[HM][col] = sy.m;
+                hr[HT_X][col] = sy.T.x; hr[HT_Y][col] = sy.T.y; hr[HT_Z][col] = sy.T.z;
+                hr[HB_X][col] = sy.B.x; hr[HB_Y][col] = sy.B.y; hr[HB_Z][col] = sy.B.z;
+                hr[HN_X2][col] = sy.n.x; hr[HN_Y2][col] = sy.n.y; hr[HN_Z2][col] = sy.n.z;
+                hr[HNT_X][col] = sy.nt.x; hr[HNT_Y][col] = sy.nt.y; hr[HNT_Z][col] = sy.nt.z;
+                hr[HQL][col] = sy.ql;
+                hr[HFP0][col] = __uint_as_float(fpy.t[0]); hr[HFP1][col] = __uint_as_float(fpy.t[1]);
+                hr[HFP2][col] = __uint_as_float(fpy.t[2]); hr[HFP3][col] = __uint_as_float(fpy.t[3]);
+                hr[HFS][col] = fpy.fs; hr[HFT][col] = fpy.ft;
+                hr[GFD_X][col] = 0.f; hr[GFD_Y][col] = 0.f; hr[GFD_Z][col] = 0.f;
+                hr[GNS_X][col] = 0.f; hr[GNS_Y][col] = 0.f; hr[GNS_Z][col] = 0.f;
+            }
+        }
+    }
+    hr[HWB][col] = wb;
+    hr[HF_X][col] = fdy.x; hr[HF_Y][col] = fdy.y; hr[HF_Z][col] = fdy.z;
+    hr[HN_X][col] = nsy.x; hr[HN_Y][col] = nsy.y; hr[HN_Z][col] = nsy.z;
+}
+
+// The backward's last step for one hit record: its summed material adjoint to the map
+// footprint at y, once per hit.
+__device__ __forceinline__ void ind_scatter(const ShadeArgs& A, const float (*hr)[32], int col) {
+    const float3 gfd = f3(hr[GFD_X][col], hr[GFD_Y][col], hr[GFD_Z][col]);
+    const float3 gny = f3(hr[GNS_X][col], hr[GNS_Y][col], hr[GNS_Z][col]);
+    const float my = hr[HM][col];
+    const float3 ay = f3(hr[HA_X][col], hr[HA_Y][col], hr[HA_Z][col]);
+    const float3 nty = f3(hr[HNT_X][col], hr[HNT_Y][col], hr[HNT_Z][col]);
+    float gy[8];
+    const float3 gay = ((1.0f - my) * kInvPi) * gfd;
+    gy[0] = gay.x; gy[1] = gay.y; gy[2] = gay.z; gy[3] = 0.0f;
+    gy[4] = A.metallic ? -dot(gfd, ay) * kInvPi : 0.0f;
+    const float3 gnt = f3(dot(f3(hr[HT_X][col], hr[HT_Y][col], hr[HT_Z][col]), gny),
+                          dot(f3(hr[HB_X][col], hr[HB_Y][col], hr[HB_Z][col]), gny),
+                          dot(f3(hr[HN_X2][col], hr[HN_Y2][col], hr[HN_Z2][col]), gny));
+    const float3 gq = (1.0f / hr[HQL][col]) * (gnt - dot(gnt, nty) * nty);
+    gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
+    Footprint fpy;
+    fpy.t[0] = __float_as_uint(hr[HFP0][col]); fpy.t[1] = __float_as_uint(hr[HFP1][col]);
+    fpy.t[2] = __float_as_uint(hr[HFP2][col]); fpy.t[3] = __float_as_uint(hr[HFP3][col]);
+    fpy.fs = hr[HFS][col];
+    fpy.ft = hr[HFT][col];
+    scatter8(A.gmaps, fpy, gy);
+}
+
+// The live (j, s) light samples of secondary rays jb .. jend - 1 of one pixel (bits
+// [jb N_s, jend N_s) of its secondary visibility words), one per lane; ray jj's record sits in
+// column cb + jj - jb.  The forward adds to L; the backward scatters the samples' E adjoints,
+// adds to the pixel's a, m and n_s adjoints and sums each hit's material adjoint in its record.
+template <bool BWD>
+__device__ __forceinline__ void ind_pairs(const ShadeArgs& A, const EnvView& env, size_t si, uint32_t rem, int c,
+                                          int jb, int jend, int cb, float (*hr)[32], uint16_t* list, float3 g,
+                                          float3 sa, float sm, float3& L, float3& ga, float& gm, float3& gns,
+                                          uint32_t& c_brdf) {
+    const int lane = threadIdx.x & 31;
+    const float3 fdx = ((1.0f - sm) * kInvPi) * sa;
+    const float invNs = 1.0f / (float)A.Ns;
+    const float invW = 1.0f / (float)env.W;
+    const uint32_t* sb = A.secbits + si * A.ws;
+    const int blo = jb * A.Ns, bhi = jend * A.Ns;
+    for (int wbase = blo >> 5; wbase < ((bhi + 31) >> 5); wbase += 32) {
+        const int tot = enumerate_bits_in(sb, wbase, (bhi + 31) >> 5, blo, bhi, list);
+        for (int t0 = 0; t0 < tot; t0 += 32) {
+            const int e = t0 + lane;
+            if (e >= tot) continue;
+            const int bit = wbase * 32 + list[e];
+            const int jj = bit / A.Ns, s = bit - jj * A.Ns;
+            const int hl = cb + jj - jb;
+            const float wbj = hr[HWB][hl];
+            if (wbj == 0.0f) continue;
+            const float3 fdyj = f3(hr[HF_X][hl], hr[HF_Y][hl], hr[HF_Z][hl]);
+            const float3 nsyj = f3(hr[HN_X][hl], hr[HN_Y][hl], hr[HN_Z][hl]);
+            const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
+            // the texel gen_seclight's search picked (a live sample was queued, so it was
+            // recorded), its row by one corrected FP32 quotient as for direct samples
+            const uint32_t t = A.tsel2[si * A.Nb * A.Ns + bit];
+            uint32_t row = (uint32_t)((float)t * invW);
+            if (row * (uint32_t)env.W > t) --row;
+            else if ((row + 1u) * (uint32_t)env.W <= t) ++row;
+            LightSample ls;
+            finish_sample(env, h2, row, t - row * (uint32_t)env.W, &ls);
+            const float3 wl = normalize(tof(ls.dir));
+            const float cs = dot(nsyj, wl);
+            if (cs <= 0.0f) continue;
+            ++c_brdf;
+            const float term = ls.inv_pdf * invNs * cs;
+            const float3 ET = term * ls.E;
+            if (!BWD) {
+                L += wbj * (fdx * (fdyj * ET));
+            } else {
+                // E of the light sample
+                const float3 gE = (wbj * term) * (g * (fdx * fdyj));
+                atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
+                // f_d(x) and n_s(x) through max(n_s(x).w_j, 0)
+                const float3 gfdx = wbj * (g * (fdyj * ET));
+                ga += ((1.0f - sm) * kInvPi) * gfdx;
+                gm += -dot(gfdx, sa) * kInvPi;
+                gns += (hr[HPBS][hl] * dot(g, fdx * (fdyj * ET))) * f3(hr[HJ_X][hl], hr[HJ_Y][hl], hr[HJ_Z][hl]);
+                // the material at y (its geometry is a constant of the derivative): the
+                // adjoints of f_d(y) and n_s(y), summed per hit
+                const float3 gLsec = wbj * (g * fdx);
+                const float3 gfdy = gLsec * ET;
+                const float3 gnsy = (ls.inv_pdf * invNs * dot(gLsec, fdyj * ls.E)) * wl;
+                atomicAdd(&hr[GFD_X][hl], gfdy.x);
+                atomicAdd(&hr[GFD_Y][hl], gfdy.y);
+                atomicAdd(&hr[GFD_Z][hl], gfdy.z);
+                atomicAdd(&hr[GNS_X][hl], gnsy.x);
+                atomicAdd(&hr[GNS_Y][hl], gnsy.y);
+                atomicAdd(&hr[GNS_Z][hl], gnsy.z);
+            }
+        }
+        __syncwarp();
+    }
+}
 
 template <typename T, bool BWD, bool COUNT, bool IND>
 __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) shade_kernel(ShadeArgs A) {
@@ -1114,6 +1278,7 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
     const int lane = threadIdx.x & 31;
     const int hw = threadIdx.x >> 5;
     uint16_t* list = s_list[hw];
+    float (*hr)[32] = hit[hw];
     const uint32_t total = *A.count;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     EnvView env = A.env;
@@ -1121,247 +1286,145 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
     unsigned long long my_samples = 0;
     uint32_t c_brdf = 0;
     const uint32_t end = min(A.shade_end, total);
-    for (uint32_t i = A.shade_begin + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); i < end; i += nwarps) {
-        const uint32_t pid = A.pixels[i];
-        const size_t si = (size_t)(i - A.state_base);  // the pixel's row of the per-sample state
-        int c, px, py;
-        uint32_t rem;
-        pixel_of(A, pid, &c, &px, &py, &rem);
-        float3 g = f3(0.f, 0.f, 0.f);
-        if (BWD) {
-            g = ld3(A.grad_rgb + 3 * (size_t)pid);
-            if (g.x == 0.0f && g.y == 0.0f && g.z == 0.0f) continue;
-        }
-        const float4* R = A.prec + kPrec * (size_t)i;
-        S3 org = s3(0.f, 0.f, 0.f), ngs = s3(0.f, 0.f, 1.f);
-        if (IND) {
-            const float4 r3 = R[3], r4 = R[4];
-            org = s3(r3.x, r3.y, r3.z);
-            ngs = s3(r3.w, r4.x, r4.y);
-        }
-        // shading state at x (Eqs. 10-11) from the pixel's record
-        const float4 r1 = R[1], r5 = R[5], r6 = R[6];
-        const float3 wo = f3(r1.x, r1.y, r1.z);
-        const float3 sa = f3(r5.x, r5.y, r5.z), sns = f3(r6.y, r6.z, r6.w);
-        const float sr = r5.w, sm = r6.x;
-        float3 L = f3(0.f, 0.f, 0.f);
-        float3 gns = f3(0.f, 0.f, 0.f), gwo = f3(0.f, 0.f, 0.f), ga = f3(0.f, 0.f, 0.f);
-        float gr = 0.f, gm = 0.f;
-        // ---- direct light (Eq. 17): the pixel's unoccluded samples, one per lane
-        const float invNd = 1.0f / (float)A.Nd;
-        const float invW = 1.0f / (float)env.W;
-        const uint32_t* vb = A.visbits + si * A.wd;
-        for (int wbase = 0; wbase < A.wd; wbase += 32) {
-            const int tot = enumerate_bits(vb, wbase, A.wd, list);
-            for (int t0 = 0; t0 < tot; t0 += 32) {
-                const int e = t0 + lane;
-                if (e < tot) {
-                    const int k = wbase * 32 + list[e];
-                    const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
-                    // the texel gen_direct's search picked for this sample (a live sample was
-                    // queued, so it was recorded); t < 2^22 is exact in FP32, and one step
-                    // corrects the rounded quotient
-                    const uint32_t t = A.tsel[si * A.Nd + k];
-                    uint32_t row = (uint32_t)((float)t * invW);
-                    if (row * (uint32_t)env.W > t) --row;
-                    else if ((row + 1u) * (uint32_t)env.W <= t) ++row;
-                    LightSample ls;
-                    finish_sample(env, h, row, t - row * (uint32_t)env.W, &ls);
-                    const float3 wi = normalize(tof(ls.dir));
-                    const float w = ls.inv_pdf * invNd;
-                    ++c_brdf;
-                    if (!BWD) {
-                        L += w * (ls.E * brdf_cos(sns, wi, wo, sa, sr, sm));
-                    } else {
-                        const float3 fc =
-                            brdf_cos_adjoint(sns, wi, wo, sa, sr, sm, w * (g * ls.E), gns, gwo, ga, gr, gm);
-                        const float3 gE = w * (g * fc);
-                        atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
-                    }
+    const bool ind = IND && A.Nb > 0 && A.lambda != 0.0f;
+    // A warp takes PB consecutive pixels at a time.  With N_b <= 16 secondary rays per pixel it
+    // first evaluates the hit records of all PB = 32 / N_b pixels, one lane per (pixel, ray),
+    // so that the lanes are not idle for 32 - N_b of the 32 columns; with more it takes one
+    // pixel and evaluates its records 32 rays at a time inside the pixel's loop.
+    const int PB = (ind && A.Nb <= 16) ? 32 / A.Nb : 1;
+    const bool grouped = ind && A.Nb <= 16;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    for (uint32_t i0 = A.shade_begin + warp * (uint32_t)PB; i0 < end; i0 += nwarps * (uint32_t)PB) {
+        const uint32_t i_end = min(i0 + (uint32_t)PB, end);
+        if (IND && grouped) {
+            // ---- the hit records of the group: lane l takes ray l mod N_b of pixel i0 + l / N_b
+            const int p = lane / A.Nb, j = lane - p * A.Nb;
+            const uint32_t ip = i0 + (uint32_t)p;
+            bool live = p < PB && ip < i_end;
+            uint32_t rem = 0;
+            int c = 0;
+            if (live) {
+                const uint32_t pid = A.pixels[ip];
+                int px, py;
+                pixel_of(A, pid, &c, &px, &py, &rem);
+                if (BWD) {
+                    const float3 g = ld3(A.grad_rgb + 3 * (size_t)pid);
+                    live = !(g.x == 0.0f && g.y == 0.0f && g.z == 0.0f);  // a pixel the backward skips
                 }
+            }
+            if (live) {
+                const float4* R = A.prec + kPrec * (size_t)ip;
+                const float4 r3 = R[3], r4 = R[4], r6 = R[6];
+                ind_record<T, BWD>(A, (size_t)(ip - A.state_base), rem, c, j, s3(r3.x, r3.y, r3.z),
+                                   s3(r3.w, r4.x, r4.y), f3(r6.y, r6.z, r6.w), hr, lane);
+            } else {
+                hr[HWB][lane] = 0.0f;
             }
             __syncwarp();
         }
-        if (!BWD && lane == 0) my_samples += (unsigned long long)A.Nd;
-        // ---- one-bounce indirect (Eqs. 18-19), 32 secondary rays at a time: first one lane per
-        // ray j evaluates what depends on j alone -- the direction, the hit point's double-word
-        // barycentrics, the material and frame at y -- into the warp's records; then the lanes
-        // take the live (j, s) pairs of those rays (named by the visibility bits)
-        if (IND && A.Nb > 0 && A.lambda != 0.0f) {
-            const float3 fdx = ((1.0f - sm) * kInvPi) * sa;
-            const float scale = A.lambda / (float)A.Nb;
-            const float invNs = 1.0f / (float)A.Ns;
-            if (!BWD) {
-                int valid = 0;
-                for (int j0 = 0; j0 < A.Nb; j0 += 32) {
-                    const int j = j0 + lane;
-                    valid += __popc(__ballot_sync(0xffffffffu, j < A.Nb && A.hits[si * A.Nb + j] >= 0));
-                }
-                if (lane == 0) my_samples += (unsigned long long)A.Nb + (unsigned long long)valid * A.Ns;
+        for (uint32_t i = i0; i < i_end; ++i) {
+            const uint32_t pid = A.pixels[i];
+            const size_t si = (size_t)(i - A.state_base);  // the pixel's row of the per-sample state
+            int c, px, py;
+            uint32_t rem;
+            pixel_of(A, pid, &c, &px, &py, &rem);
+            float3 g = f3(0.f, 0.f, 0.f);
+            if (BWD) {
+                g = ld3(A.grad_rgb + 3 * (size_t)pid);
+                if (g.x == 0.0f && g.y == 0.0f && g.z == 0.0f) continue;
             }
-            const uint32_t* sb = A.secbits + si * A.ws;
-            for (int jb = 0; jb < A.Nb; jb += 32) {
-                const int j = jb + lane;
-                const int gtri = j < A.Nb ? A.hits[si * A.Nb + j] : -1;
-                float wb = 0.0f;  // 0: no live samples (no valid hit, or n_s(x).w_j <= 0)
-                float3 fdy = f3(0.f, 0.f, 0.f), nsy = f3(0.f, 0.f, 1.f);
-                if (gtri >= 0) {
-                    float xi1;
-                    const S3 wjs = secondary_dir(A, rem, c, j, ngs, &xi1);
-                    const float3 wj = normalize(tof(wjs));
-                    const float cxj = dot(sns, wj);
-                    if (cxj > 0.0f) {
-                        const float pbs = scale * (kPi / __fsqrt_rn(ssub(1.0f, xi1)));  // lambda / (N_b p_b)
-                        wb = pbs * cxj;
-                        const int q0 = __ldg(A.F + 3 * gtri), q1 = __ldg(A.F + 3 * gtri + 1), q2 = __ldg(A.F + 3 * gtri + 2);
-                        const int v0 = __ldg(A.Fuv + 3 * gtri), v1 = __ldg(A.Fuv + 3 * gtri + 1), v2 = __ldg(A.Fuv + 3 * gtri + 2);
-                        const float3 Q0 = ld3(A.V + 3 * q0), Q1 = ld3(A.V + 3 * q1), Q2 = ld3(A.V + 3 * q2);
-                        FF by[3];
-                        bary_ff(ff3_sub(f3(org.x, org.y, org.z), Q0), FF3{ff(wjs.x), ff(wjs.y), ff(wjs.z)}, Q0, Q1, Q2, by);
-                        int ti, tj;
-                        float fs, ft;
-                        texel_coord(by, __ldg(A.UV + 2 * v0), __ldg(A.UV + 2 * v1), __ldg(A.UV + 2 * v2), A.map.W, &ti, &fs);
-                        texel_coord(by, __ldg(A.UV + 2 * v0 + 1), __ldg(A.UV + 2 * v1 + 1), __ldg(A.UV + 2 * v2 + 1),
-                                    A.map.H, &tj, &ft);
-                        const Footprint fpy = footprint_i(A.map, ti, tj, fs, ft);
-                        float atty[8];
-                        if (A.sec_material) {
-                            fetch8<T>(A.map, fpy, atty, nullptr, nullptr);
-                        } else {
-                            // constant default material: grey diffuse, flat tangent-space normal
-                            atty[0] = atty[1] = atty[2] = 0.5f;
-                            atty[3] = 0.5f;
-                            atty[4] = 0.0f;
-                            atty[5] = atty[6] = 0.0f;
-                            atty[7] = 1.0f;
-                        }
-                        const float b0 = ff_f(by[0]), b1 = ff_f(by[1]), b2 = ff_f(by[2]);
-                        const float3 niy = b0 * ld3(A.nrm + 3 * q0) + b1 * ld3(A.nrm + 3 * q1) + b2 * ld3(A.nrm + 3 * q2);
-                        const float3 tiy = b0 * ld3(A.tan + 3 * v0) + b1 * ld3(A.tan + 3 * v1) + b2 * ld3(A.tan + 3 * v2);
-                        const Surface sy = make_surface(atty, niy, tiy, __ldg(A.fsign + gtri), A.metallic);
-                        fdy = ((1.0f - sy.m) * kInvPi) * sy.a;
-                        nsy = sy.ns;
-                        if (BWD) {
-                            float (*hr)[32] = hit[hw];
-                            hr[HJ_X][lane] = wj.x; hr[HJ_Y][lane] = wj.y; hr[HJ_Z][lane] = wj.z;
-                            hr[HPBS][lane] = pbs;
-                            hr[HA_X][lane] = sy.a.x; hr[HA_Y][lane] = sy.a.y; hr[HA_Z][lane] = sy.a.z;
-                            hr[HM][lane] = sy.m;
-                            hr[HT_X][lane] = sy.T.x; hr[HT_Y][lane] = sy.T.y; hr[HT_Z][lane] = sy.T.z;
-                            hr[HB_X][lane] = sy.B.x; hr[HB_Y][lane] = sy.B.y; hr[HB_Z][lane] = sy.B.z;
-                            hr[HN_X2][lane] = sy.n.x; hr[HN_Y2][lane] = sy.n.y; hr[HN_Z2][lane] = sy.n.z;
-                            hr[HNT_X][lane] = sy.nt.x; hr[HNT_Y][lane] = sy.nt.y; hr[HNT_Z][lane] = sy.nt.z;
-                            hr[HQL][lane] = sy.ql;
-                            hr[HFP0][lane] = __uint_as_float(fpy.t[0]); hr[HFP1][lane] = __uint_as_float(fpy.t[1]);
-                            hr[HFP2][lane] = __uint_as_float(fpy.t[2]); hr[HFP3][lane] = __uint_as_float(fpy.t[3]);
-                            hr[HFS][lane] = fpy.fs; hr[HFT][lane] = fpy.ft;
-                            hr[GFD_X][lane] = 0.f; hr[GFD_Y][lane] = 0.f; hr[GFD_Z][lane] = 0.f;
-                            hr[GNS_X][lane] = 0.f; hr[GNS_Y][lane] = 0.f; hr[GNS_Z][lane] = 0.f;
-                        }
-                    }
-                }
-                {
-                    float (*hr)[32] = hit[hw];
-                    hr[HWB][lane] = wb;
-                    hr[HF_X][lane] = fdy.x; hr[HF_Y][lane] = fdy.y; hr[HF_Z][lane] = fdy.z;
-                    hr[HN_X][lane] = nsy.x; hr[HN_Y][lane] = nsy.y; hr[HN_Z][lane] = nsy.z;
-                }
-                __syncwarp();
-                // the live (j, s) of rays jb .. jend - 1: bits [jb N_s, jend N_s)
-                const int jend = min(jb + 32, A.Nb);
-                const int blo = jb * A.Ns, bhi = jend * A.Ns;
-                for (int wbase = blo >> 5; wbase < ((bhi + 31) >> 5); wbase += 32) {
-                    const int tot = enumerate_bits_in(sb, wbase, (bhi + 31) >> 5, blo, bhi, list);
-                    for (int t0 = 0; t0 < tot; t0 += 32) {
-                        const int e = t0 + lane;
-                        if (e >= tot) continue;
-                        const int bit = wbase * 32 + list[e];
-                        const int jj = bit / A.Ns, s = bit - jj * A.Ns;
-                        const float (*hr)[32] = hit[hw];
-                        const int hl = jj - jb;
-                        const float wbj = hr[HWB][hl];
-                        if (wbj == 0.0f) continue;
-                        const float3 fdyj = f3(hr[HF_X][hl], hr[HF_Y][hl], hr[HF_Z][hl]);
-                        const float3 nsyj = f3(hr[HN_X][hl], hr[HN_Y][hl], hr[HN_Z][hl]);
-                        const uint4 h2 = philox(make_uint4(rem, (uint32_t)c, (uint32_t)(jj * A.Ns + s), 2u), A.key);
-                        // the texel gen_seclight's search picked (a live sample was queued, so it
-                        // was recorded), its row by one corrected FP32 quotient as for direct samples
-                        const uint32_t t = A.tsel2[si * A.Nb * A.Ns + bit];
+            const float4* R = A.prec + kPrec * (size_t)i;
+            // shading state at x (Eqs. 10-11) from the pixel's record
+            const float4 r1 = R[1], r5 = R[5], r6 = R[6];
+            const float3 wo = f3(r1.x, r1.y, r1.z);
+            const float3 sa = f3(r5.x, r5.y, r5.z), sns = f3(r6.y, r6.z, r6.w);
+            const float sr = r5.w, sm = r6.x;
+            float3 L = f3(0.f, 0.f, 0.f);
+            float3 gns = f3(0.f, 0.f, 0.f), gwo = f3(0.f, 0.f, 0.f), ga = f3(0.f, 0.f, 0.f);
+            float gr = 0.f, gm = 0.f;
+            // ---- direct light (Eq. 17): the pixel's unoccluded samples, one per lane
+            const float invNd = 1.0f / (float)A.Nd;
+            const float invW = 1.0f / (float)env.W;
+            const uint32_t* vb = A.visbits + si * A.wd;
+            for (int wbase = 0; wbase < A.wd; wbase += 32) {
+                const int tot = enumerate_bits(vb, wbase, A.wd, list);
+                for (int t0 = 0; t0 < tot; t0 += 32) {
+                    const int e = t0 + lane;
+                    if (e < tot) {
+                        const int k = wbase * 32 + list[e];
+                        const uint4 h = philox(make_uint4(rem, (uint32_t)c, (uint32_t)k, 0u), A.key);
+                        // the texel gen_direct's search picked for this sample (a live sample was
+                        // queued, so it was recorded); t < 2^22 is exact in FP32, and one step
+                        // corrects the rounded quotient
+                        const uint32_t t = A.tsel[si * A.Nd + k];
                         uint32_t row = (uint32_t)((float)t * invW);
                         if (row * (uint32_t)env.W > t) --row;
                         else if ((row + 1u) * (uint32_t)env.W <= t) ++row;
                         LightSample ls;
-                        finish_sample(env, h2, row, t - row * (uint32_t)env.W, &ls);
-                        const float3 wl = normalize(tof(ls.dir));
-                        const float cs = dot(nsyj, wl);
-                        if (cs <= 0.0f) continue;
+                        finish_sample(env, h, row, t - row * (uint32_t)env.W, &ls);
+                        const float3 wi = normalize(tof(ls.dir));
+                        const float w = ls.inv_pdf * invNd;
                         ++c_brdf;
-                        const float term = ls.inv_pdf * invNs * cs;
-                        const float3 ET = term * ls.E;
                         if (!BWD) {
-                            L += wbj * (fdx * (fdyj * ET));
+                            L += w * (ls.E * brdf_cos(sns, wi, wo, sa, sr, sm));
                         } else {
-                            // E of the light sample
-                            const float3 gE = (wbj * term) * (g * (fdx * fdyj));
+                            const float3 fc =
+                                brdf_cos_adjoint(sns, wi, wo, sa, sr, sm, w * (g * ls.E), gns, gwo, ga, gr, gm);
+                            const float3 gE = w * (g * fc);
                             atomicAdd(A.genv + ls.texel, make_float4(gE.x, gE.y, gE.z, 0.0f));
-                            // f_d(x) and n_s(x) through max(n_s(x).w_j, 0)
-                            const float3 gfdx = wbj * (g * (fdyj * ET));
-                            ga += ((1.0f - sm) * kInvPi) * gfdx;
-                            gm += -dot(gfdx, sa) * kInvPi;
-                            gns += (hr[HPBS][hl] * dot(g, fdx * (fdyj * ET))) * f3(hr[HJ_X][hl], hr[HJ_Y][hl], hr[HJ_Z][hl]);
-                            // the material at y (its geometry is a constant of the derivative): the
-                            // adjoints of f_d(y) and n_s(y), summed per hit
-                            const float3 gLsec = wbj * (g * fdx);
-                            const float3 gfdy = gLsec * ET;
-                            const float3 gnsy = (ls.inv_pdf * invNs * dot(gLsec, fdyj * ls.E)) * wl;
-                            float (*hw_acc)[32] = hit[hw];
-                            atomicAdd(&hw_acc[GFD_X][hl], gfdy.x);
-                            atomicAdd(&hw_acc[GFD_Y][hl], gfdy.y);
-                            atomicAdd(&hw_acc[GFD_Z][hl], gfdy.z);
-                            atomicAdd(&hw_acc[GNS_X][hl], gnsy.x);
-                            atomicAdd(&hw_acc[GNS_Y][hl], gnsy.y);
-                            atomicAdd(&hw_acc[GNS_Z][hl], gnsy.z);
                         }
                     }
-                    __syncwarp();
-                }
-                // backward: each hit's summed material adjoint to its map footprint, once
-                if (BWD && wb != 0.0f && A.gmaps && A.sec_material) {
-                    const float (*hr)[32] = hit[hw];
-                    const float3 gfd = f3(hr[GFD_X][lane], hr[GFD_Y][lane], hr[GFD_Z][lane]);
-                    const float3 gny = f3(hr[GNS_X][lane], hr[GNS_Y][lane], hr[GNS_Z][lane]);
-                    const float my = hr[HM][lane];
-                    const float3 ay = f3(hr[HA_X][lane], hr[HA_Y][lane], hr[HA_Z][lane]);
-                    const float3 nty = f3(hr[HNT_X][lane], hr[HNT_Y][lane], hr[HNT_Z][lane]);
-                    float gy[8];
-                    const float3 gay = ((1.0f - my) * kInvPi) * gfd;
-                    gy[0] = gay.x; gy[1] = gay.y; gy[2] = gay.z; gy[3] = 0.0f;
-                    gy[4] = A.metallic ? -dot(gfd, ay) * kInvPi : 0.0f;
-                    const float3 gnt = f3(dot(f3(hr[HT_X][lane], hr[HT_Y][lane], hr[HT_Z][lane]), gny),
-                                          dot(f3(hr[HB_X][lane], hr[HB_Y][lane], hr[HB_Z][lane]), gny),
-                                          dot(f3(hr[HN_X2][lane], hr[HN_Y2][lane], hr[HN_Z2][lane]), gny));
-                    const float3 gq = (1.0f / hr[HQL][lane]) * (gnt - dot(gnt, nty) * nty);
-                    gy[5] = gq.x; gy[6] = gq.y; gy[7] = gq.z;
-                    Footprint fpy;
-                    fpy.t[0] = __float_as_uint(hr[HFP0][lane]); fpy.t[1] = __float_as_uint(hr[HFP1][lane]);
-                    fpy.t[2] = __float_as_uint(hr[HFP2][lane]); fpy.t[3] = __float_as_uint(hr[HFP3][lane]);
-                    fpy.fs = hr[HFS][lane];
-                    fpy.ft = hr[HFT][lane];
-                    scatter8(A.gmaps, fpy, gy);
                 }
                 __syncwarp();
             }
+            if (!BWD && lane == 0) my_samples += (unsigned long long)A.Nd;
+            // ---- one-bounce indirect (Eqs. 18-19): the live (j, s) pairs of the pixel's rays
+            // (named by the visibility bits), against the hit records of those rays
+            if (IND && ind) {
+                if (!BWD) {
+                    int valid = 0;
+                    for (int j0 = 0; j0 < A.Nb; j0 += 32) {
+                        const int j = j0 + lane;
+                        valid += __popc(__ballot_sync(0xffffffffu, j < A.Nb && A.hits[si * A.Nb + j] >= 0));
+                    }
+                    if (lane == 0) my_samples += (unsigned long long)A.Nb + (unsigned long long)valid * A.Ns;
+                }
+                if (grouped) {
+                    ind_pairs<BWD>(A, env, si, rem, c, 0, A.Nb, (int)(i - i0) * A.Nb, hr, list, g, sa, sm, L, ga,
+                                   gm, gns, c_brdf);
+                } else {
+                    const float4 r3 = R[3], r4 = R[4];
+                    const S3 org = s3(r3.x, r3.y, r3.z), ngs = s3(r3.w, r4.x, r4.y);
+                    for (int jb = 0; jb < A.Nb; jb += 32) {
+                        const int j = jb + lane;
+                        if (j < A.Nb) ind_record<T, BWD>(A, si, rem, c, j, org, ngs, sns, hr, lane);
+                        else hr[HWB][lane] = 0.0f;
+                        __syncwarp();
+                        ind_pairs<BWD>(A, env, si, rem, c, jb, min(jb + 32, A.Nb), 0, hr, list, g, sa, sm, L, ga,
+                                       gm, gns, c_brdf);
+                        // backward: each hit's summed material adjoint to its map footprint, once
+                        if (BWD && A.gmaps && A.sec_material && hr[HWB][lane] != 0.0f) ind_scatter(A, hr, lane);
+                        __syncwarp();
+                    }
+                }
+            }
+            if (!BWD) {
+                float v[4] = {L.x, L.y, L.z, 0.0f};
+                const float t = warp_sum_spread<4>(v);  // lanes 0, 8, 16: L.x, L.y, L.z
+                if ((lane & 7) == 0 && lane < 24) A.out[3 * (size_t)pid + (lane >> 3)] = t;
+                continue;
+            }
+            // ---- the pixel's sums of the sample adjoints, for the epilogue
+            float v[16] = {gns.x, gns.y, gns.z, gwo.x, gwo.y, gwo.z, ga.x, ga.y, ga.z, gr, gm, 0.f, 0.f, 0.f, 0.f, 0.f};
+            const float t = warp_sum_spread<16>(v);  // lanes 2q and 2q + 1: value q
+            if ((lane & 1) == 0 && lane < 22) A.pacc[12 * (size_t)i + (lane >> 1)] = t;
         }
-        if (!BWD) {
-            float v[4] = {L.x, L.y, L.z, 0.0f};
-            const float t = warp_sum_spread<4>(v);  // lanes 0, 8, 16: L.x, L.y, L.z
-            if ((lane & 7) == 0 && lane < 24) A.out[3 * (size_t)pid + (lane >> 3)] = t;
-            continue;
+        if (IND && grouped) {
+            // backward: each hit's summed material adjoint to its map footprint, once
+            __syncwarp();
+            if (BWD && A.gmaps && A.sec_material && hr[HWB][lane] != 0.0f) ind_scatter(A, hr, lane);
+            __syncwarp();
         }
-        // ---- the pixel's sums of the sample adjoints, for the epilogue
-        float v[16] = {gns.x, gns.y, gns.z, gwo.x, gwo.y, gwo.z, ga.x, ga.y, ga.z, gr, gm, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const float t = warp_sum_spread<16>(v);  // lanes 2q and 2q + 1: value q
-        if ((lane & 1) == 0 && lane < 22) A.pacc[12 * (size_t)i + (lane >> 1)] = t;
     }
     if (!BWD) {
         if (lane == 0 && my_samples) atomicAdd(A.samples, my_samples);

@@ -576,6 +576,17 @@ def test_parity_sample_counts_without_powers_of_two():
     assert (dec.stri >= 0).sum() > 50
 
 
+@pytest.mark.parametrize("n_bounce", [5, 16, 17, 40])
+def test_parity_secondary_ray_counts_around_the_record_batches(n_bounce):
+    """The shade kernels evaluate the secondary hits' records for 32 / N_b pixels at once when
+    N_b <= 16 (5: six pixels and two idle lanes; 16: two pixels) and pixel by pixel, 32 rays at a
+    time, above (17: one partial batch; 40: a full batch of 32 and a tail of 8); forward and
+    backward against the oracle in each case."""
+    sc = small_cavity(res=40, views=2, n_direct=16, n_bounce=n_bounce, n_light=2)
+    dec = _forward_and_backward_full(sc, f"N_b {n_bounce}")
+    assert (dec.stri >= 0).sum() > 50 * n_bounce // 5
+
+
 def test_parity_more_direct_samples_than_one_list_round():
     """N_d = 1100 takes 35 visibility words per pixel; the shade kernels list a pixel's live
     samples 32 words (1024 samples) at a time, so every pixel needs a second, partial round.
