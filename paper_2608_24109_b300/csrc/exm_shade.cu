@@ -1389,9 +1389,12 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                     }
                     if (lane == 0) my_samples += (unsigned long long)A.Nb + (unsigned long long)valid * A.Ns;
                 }
+                // a ray whose record has wb = 0 adds nothing, so a pixel (or batch) whose rays all
+                // have it skips the listing of its light samples
                 if (grouped) {
-                    ind_pairs<BWD>(A, env, si, rem, c, 0, A.Nb, (int)(i - i0) * A.Nb, hr, list, g, sa, sm, L, ga,
-                                   gm, gns, c_brdf);
+                    const int cb = (int)(i - i0) * A.Nb;
+                    if (__any_sync(0xffffffffu, lane < A.Nb && hr[HWB][cb + lane] != 0.0f))
+                        ind_pairs<BWD>(A, env, si, rem, c, 0, A.Nb, cb, hr, list, g, sa, sm, L, ga, gm, gns, c_brdf);
                 } else {
                     const float4 r3 = R[3], r4 = R[4];
                     const S3 org = s3(r3.x, r3.y, r3.z), ngs = s3(r3.w, r4.x, r4.y);
@@ -1400,8 +1403,9 @@ __global__ void __launch_bounds__(kShadeWarps * 32, shade_min_blocks(BWD, IND)) 
                         if (j < A.Nb) ind_record<T, BWD>(A, si, rem, c, j, org, ngs, sns, hr, lane);
                         else hr[HWB][lane] = 0.0f;
                         __syncwarp();
-                        ind_pairs<BWD>(A, env, si, rem, c, jb, min(jb + 32, A.Nb), 0, hr, list, g, sa, sm, L, ga,
-                                       gm, gns, c_brdf);
+                        if (__any_sync(0xffffffffu, hr[HWB][lane] != 0.0f))
+                            ind_pairs<BWD>(A, env, si, rem, c, jb, min(jb + 32, A.Nb), 0, hr, list, g, sa, sm, L, ga,
+                                           gm, gns, c_brdf);
                         // backward: each hit's summed material adjoint to its map footprint, once
                         if (BWD && A.gmaps && A.sec_material && hr[HWB][lane] != 0.0f) ind_scatter(A, hr, lane);
                         __syncwarp();
